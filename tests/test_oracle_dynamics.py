@@ -1,0 +1,371 @@
+"""Pins of the oracle's time step against closed forms and invariants (CPU only).
+
+Lattice Boltzmann half (Sec. IV, App. B): rest and uniform-flow fixed points,
+shear-wave decay at viscosity c_s^2 tau, exact momentum input of a body force,
+exact decay of the forcing-stress defect, conservation, equipartition of every
+non-conserved mode.  Order-parameter half (Sec. V): exact one-step
+amplification of a Fourier mode (diffusion, advection, both integrators, both
+schemes), conservation, Lyapunov decrease of the free energy, interface
+profile (Eqs. tanh, intthick) and the static structure factor (Eqs. test1,
+test2)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import theory as T
+
+CS2 = 1.0 / 3.0
+
+
+def _coords(p):
+    return np.meshgrid(np.arange(p.shape[0]), np.arange(p.shape[1]), np.arange(p.shape[2]), indexing="ij")
+
+
+# ----------------------------------------------------------------- LB half
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_rest_and_uniform_flow_are_fixed_points(dim, q):
+    p = O.Params(dim=dim, q=q, nx=5, ny=4, nz=3, kT=0.0, tau=0.7, coupling=2, A=0.1, K=0.02)
+    s = O.State.rest(p)
+    f0 = s.f.copy()
+    s.advance(4)
+    assert np.abs(s.f - f0).max() < 1e-15
+    u0 = np.array([0.03, -0.02, 0.01 if dim == 3 else 0.0])
+    s = O.State.rest(p, u=np.repeat(u0[:, None], p.n, axis=1))
+    f0 = s.f.copy()
+    s.advance(4)
+    assert np.abs(s.f - f0).max() < 1e-15
+    assert np.allclose(s.u[:dim], u0[:dim, None], atol=1e-15)
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("tau", [0.3, 0.8, 1.0])
+def test_shear_wave_decay(dim, q, tau):
+    # u_x = U sin(k y) decays as exp(-nu k^2 t) with nu = c_s^2 tau (paper's tau, App. B)
+    n = 128
+    p = O.Params(dim=dim, q=q, nx=2, ny=n, nz=2, kT=0.0, tau=tau, coupling=0)
+    z, y, x = _coords(p)
+    u = np.zeros((3,) + p.shape)
+    u[0] = 1e-4 * np.sin(2 * np.pi * y / n)
+    s = O.State.rest(p, u=u.reshape(3, -1))
+
+    def amp():
+        _, j, _ = O.moments(p, s.f)
+        return float(np.sum(j[0].reshape(p.shape) * np.sin(2 * np.pi * y / n)))
+
+    s.advance(40)
+    a1 = amp()
+    s.advance(600)
+    a2 = amp()
+    k = 2 * np.pi / n
+    rate = -np.log(a2 / a1) / 600
+    assert abs(rate / (CS2 * tau * k * k) - 1) < 5e-3
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_shear_wave_advected_by_uniform_flow(dim, q):
+    # Galilean check of streaming: a transverse wave u_y = eps sin(k x) on a uniform
+    # flow U along x travels at U and decays at nu k^2 (Sec. VI.B at low Mach)
+    n, U, eps = 64, 0.05, 1e-5
+    p = O.Params(dim=dim, q=q, nx=n, ny=2, nz=2, kT=0.0, tau=0.8, coupling=0)
+    z, y, x = _coords(p)
+    u = np.zeros((3,) + p.shape)
+    u[0] = U
+    u[1] = eps * np.sin(2 * np.pi * x / n)
+    s = O.State.rest(p, u=u.reshape(3, -1))
+    k = 2 * np.pi / n
+
+    def phase():
+        _, j, _ = O.moments(p, s.f)
+        jy = j[1].reshape(p.shape)[0, 0, :]
+        c = np.sum(jy * np.exp(-1j * k * np.arange(n)))
+        return np.angle(c), np.abs(c)
+
+    s.advance(50)
+    ph1, a1 = phase()
+    T = 400
+    s.advance(T)
+    ph2, a2 = phase()
+    shift = -np.angle(np.exp(1j * (ph2 - ph1))) / k        # distance travelled along +x
+    assert abs(shift / (U * T) - 1) < 0.02
+    assert abs(-np.log(a2 / a1) / T / (CS2 * p.tau * k * k) - 1) < 0.02
+
+
+def test_fd_link_noise_orientation():
+    # convention of the real-space FD noise: eta(r) = sum_l [zeta_l(r - c_l) - zeta_l(r)]
+    # with zeta_l(r) = sqrt(2 kT M a_l) g_l(r) and g from Philox stream 1 of site r;
+    # the law cannot tell the orientation apart, so it is checked directly
+    p = O.Params(dim=3, q=19, nx=4, ny=3, nz=5, kT=0.3, M=0.2, seed=9)
+    links = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1),
+             (0, 1, -1), (1, 1, 1), (1, 1, -1), (1, -1, 1), (1, -1, -1)]
+    a = {1: 6 / 22, 2: 3 / 22, 3: 1 / 22}
+    nz, ny, nx = p.shape
+    G = np.array([O.gaussians(p.seed, 4, s, 1, 4) for s in range(p.n)]).reshape(nz, ny, nx, 16)
+    eta = O.fd_noise(p, 4).reshape(p.shape)
+    for (zz, yy, xx) in [(0, 0, 0), (4, 2, 3), (2, 1, 1)]:
+        acc = 0.0
+        for l, cl in enumerate(links):
+            sd = np.sqrt(2 * p.kT * p.M * a[sum(map(abs, cl))])
+            acc += sd * (G[(zz - cl[2]) % nz, (yy - cl[1]) % ny, (xx - cl[0]) % nx, l] - G[zz, yy, xx, l])
+        assert abs(acc - eta[zz, yy, xx]) < 1e-13
+
+
+def test_body_force_momentum_and_stress():
+    # a uniform force density g adds exactly g per site and step to the momentum
+    # (A = sum fbar c + F dt, App. B); the stress defect
+    # D = S - (rho v v - (v F + F v)/2) of the auxiliary distribution shrinks by
+    # exactly gamma per step -- gamma_shear on the traceless part and
+    # gamma_bulk on the trace -- which pins the forcing term (1 - omega/2)(vF + Fv).
+    g = np.array([1e-3, -2e-3, 5e-4])
+    p = O.Params(dim=3, q=19, nx=3, ny=2, nz=2, kT=0.0, tau=0.8, gamma_bulk=-0.2, coupling=0, gext=tuple(g))
+    s = O.State.rest(p)
+    c, w = O.lattice(3, 19)
+    Q = np.einsum("ia,ib->iab", c, c) - np.eye(3) / 3
+
+    def defect():
+        rho, j, _ = O.moments(p, s.f)
+        v = (j[:, 0] + g / 2) / rho[0]
+        S = np.einsum("i,iab->ab", s.f[:, 0], Q)
+        D = S - (rho[0] * np.outer(v, v) - 0.5 * (np.outer(v, g) + np.outer(g, v)))
+        tr = np.trace(D) / 3
+        return D - tr * np.eye(3), tr
+
+    gs = 1 - 1 / (p.tau + 0.5)
+    for _ in range(4):
+        j0 = O.moments(p, s.f)[1].sum(axis=1)
+        d0, t0 = defect()
+        s.advance(1)
+        j1 = O.moments(p, s.f)[1].sum(axis=1)
+        d1, t1 = defect()
+        assert np.allclose((j1 - j0) / p.n, g, rtol=1e-12, atol=0)
+        assert np.allclose(d1, gs * d0, atol=2e-15)
+        assert abs(t1 - p.gamma_bulk * t0) < 2e-15
+        assert np.abs(d0).max() > 1e-9 and abs(t0) > 1e-9
+
+
+@pytest.mark.parametrize("dim,q,scheme", [(2, 9, 0), (3, 19, 1), (3, 19, 0)])
+def test_conservation_with_noise_and_coupling(dim, q, scheme):
+    # mass, psi and (for B = 0) momentum are conserved to round-off (Sec. I);
+    # for B != 0 the momentum changes by exactly the summed force
+    p = O.Params(dim=dim, q=q, nx=7, ny=6, nz=5, kT=3e-4, tau=0.8, A=0.05, B=0.0, K=0.04, M=0.1,
+                 scheme=scheme, integrator=2, seed=11)
+    rng = np.random.default_rng(1)
+    s = O.State.rest(p, psi=0.05 * rng.normal(size=p.n))
+    t0 = O.totals(p, s.f, s.psi)
+    s.advance(20)
+    t1 = O.totals(p, s.f, s.psi)
+    assert abs(t1["mass"] - t0["mass"]) < 1e-12 * p.n
+    assert np.abs(t1["momentum"] - t0["momentum"]).max() < 1e-12 * p.n
+    assert abs(t1["psi"] - t0["psi"]) < 1e-12 * np.abs(s.psi).sum()
+    p2 = O.Params(**{**p.__dict__, "B": 0.3, "A": -0.05})
+    s2 = O.State.rest(p2, psi=0.5 * rng.normal(size=p.n))
+    for _ in range(3):
+        F = O.force(p2, s2.psi).sum(axis=1)
+        j0 = O.moments(p2, s2.f)[1].sum(axis=1)
+        s2.advance(1)
+        j1 = O.moments(p2, s2.f)[1].sum(axis=1)
+        assert np.allclose(j1 - j0, F, atol=1e-13 * p.n)
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_equipartition_all_modes(dim, q):
+    # linear FLBE at rest: every non-conserved mode has <m_k^2> = mu b_k with
+    # mu = rho kT / c_s^2, and <u_a^2> = kT / rho0 (adhikari2005, Sec. III)
+    n = 24 if dim == 2 else 10
+    p = O.Params(dim=dim, q=q, nx=n, ny=n, nz=n, kT=2e-4, tau=0.6, gamma_bulk=-0.5, gamma_ghost=0.3,
+                 coupling=0, seed=5)
+    s = O.State.rest(p)
+    s.advance(200)
+    E, b = O.moment_basis(dim, q)
+    acc = np.zeros(q)
+    u2 = np.zeros(3)
+    ns = 300
+    for _ in range(ns):
+        s.advance(1)
+        _, _, m = O.moments(p, s.f)
+        acc += np.mean(m ** 2, axis=1)
+        u2 += np.mean(s.u ** 2, axis=1)
+    ratio = acc / ns / (p.rho0 * p.kT / CS2 * b)
+    assert np.all(np.abs(ratio[1:] - 1) < 0.03), ratio
+    assert np.all(np.abs(ratio[dim + 1:] - 1) < 0.02), ratio
+    assert np.all(np.abs(u2[:dim] / ns / p.kT - 1) < 0.03)
+
+
+def test_force_sign_lowers_free_energy():
+    # The advective change of the free energy over one step is sum mu (-div(u psi))
+    # = sum psi u . grad mu to first order, so a velocity along -psi grad mu lowers
+    # it and one along +psi grad mu raises it (Sec. II.B).  With M = 0 and no
+    # noise psi changes by advection only; the first coupled step starts from
+    # rest and must create u = F/2 with F = -psi grad_CD mu (the reading of the
+    # force sign) -- the free-energy-lowering direction.
+    p = O.Params(dim=2, q=9, nx=32, ny=32, kT=0.0, A=-0.05, B=0.05, K=0.04, M=0.0, scheme=1,
+                 integrator=2, coupling=3, tau=0.8)
+    z, y, x = _coords(p)
+    psi = (0.6 * np.sin(2 * np.pi * x / 32) * np.cos(4 * np.pi * y / 32)
+           + 0.2 * np.cos(2 * np.pi * (x + y) / 32)).reshape(-1)
+    Fe0 = O.free_energy(p, psi)
+    F = O.force(p, psi)
+    assert np.abs(F).max() > 1e-4
+    for sign, lowers in ((1.0, True), (-1.0, False)):
+        pp = O.Params(**{**p.__dict__, "lb_on": 0})
+        st = O.State(pp, O.equilibrium(pp), psi.copy(), sign * 0.5 * F, 0)
+        st.advance(1)
+        assert (O.free_energy(pp, st.psi) < Fe0) == lowers
+    s = O.State.rest(p, psi=psi)
+    s.advance(1)
+    assert np.allclose(s.u[:2], 0.5 * F[:2], rtol=0, atol=1e-15)
+    assert O.free_energy(p, s.psi) < Fe0
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_lyapunov_noise_free_coupled(scheme):
+    # kT = 0, B > 0: free energy + kinetic energy never grows (Sec. II; no noise)
+    p = O.Params(dim=2, q=9, nx=24, ny=24, kT=0.0, A=-0.05, B=0.05, K=0.04, M=0.1, scheme=scheme,
+                 integrator=2, coupling=3, tau=0.8)
+    rng = np.random.default_rng(4)
+    s = O.State.rest(p, psi=0.3 * rng.normal(size=p.n))
+    prev = O.free_energy(p, s.psi) + O.kinetic_energy(p, s.f)
+    for _ in range(60):
+        s.advance(5)
+        cur = O.free_energy(p, s.psi) + O.kinetic_energy(p, s.f)
+        assert cur <= prev + 1e-12 * abs(prev)
+        prev = cur
+
+
+# ----------------------------------------------------------------- psi half
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_single_mode_exact_amplification(dim, q, scheme, integrator):
+    # B = 0, no noise, u uniform: psi = Re[eps e^{iq.r}] is multiplied each step by
+    # 1 + z (Euler) or 1 + z + z^2/2 (Heun) with
+    # z = M L_mob(q) (A - K L_SO(q)) - i theta(q);  theta = sum_a u_a sin q_a (FD,
+    # central-difference advection) or u . G(q) (FV, Eq. fvft)
+    p = O.Params(dim=dim, q=q, nx=8, ny=6, nz=4, kT=0.0, A=0.07, B=0.0, K=0.05, M=0.3, scheme=scheme,
+                 integrator=integrator, coupling=2, tau=0.9)
+    c, w = O.lattice(dim, q)
+    z, y, x = _coords(p)
+    u0 = np.array([0.04, -0.03, 0.02 if dim == 3 else 0.0])
+    for kv in ([1, 0, 0], [2, 1, 1], [3, 2, 1], [4, 3, 2]):
+        qv = 2 * np.pi * np.array([kv[0] / p.shape[2], kv[1] / p.shape[1], (kv[2] / p.shape[0]) if dim == 3 else 0.0])
+        phase = qv[0] * x + qv[1] * y + qv[2] * z
+        s = O.State.rest(p, psi=(1e-3 * np.cos(phase)).reshape(-1), u=np.repeat(u0[:, None], p.n, axis=1))
+        Lso = T.L_so(qv) if dim == 3 else T.L_so_2d(qv)
+        if scheme == 0:
+            Lm = Lso
+            theta = float(np.sum(u0[:dim] * np.sin(qv[:dim])))
+        else:
+            Lm = T.L_fv(qv, c, w)
+            theta = float(np.dot(u0, T.fv_gradient_symbol(qv, c, w)))
+        zz = p.M * Lm * (p.A - p.K * Lso) - 1j * theta
+        g = T.amplification(zz, integrator)
+        nst = 7
+        s.advance(nst)
+        expect = (1e-3 * g ** nst * np.exp(1j * phase)).real
+        assert np.abs(s.psi.reshape(p.shape) - expect).max() < 1e-15
+
+
+def test_interface_profile_is_tanh():
+    # noise-free relaxation keeps the two-interface profile tanh((z-z1)/l) tanh((z2-z)/l)
+    # with l = sqrt(2K/|A|) and psi_+- = sqrt(|A|/B) (Eqs. tanh, intthick)
+    A, B, K = -0.02, 0.02, 0.16        # l = 4: wide enough for the continuum form to hold on the lattice
+    nz = 96
+    p = O.Params(dim=2, q=9, nx=2, ny=nz, kT=0.0, A=A, B=B, K=K, M=0.5, scheme=0, integrator=2,
+                 coupling=0, lb_on=0)
+    l = T.interface_width(A, K)
+    zc = np.arange(nz) + 0.0
+    prof = np.tanh((zc - 24) / (0.8 * l)) * np.tanh((72 - zc) / (0.8 * l))   # start too sharp
+    psi = np.repeat(prof[:, None], 2, axis=1)
+    s = O.State.rest(p, psi=psi.reshape(-1))
+    s.advance(20000)
+    got = s.psi.reshape(p.shape)[0, :, 0]
+    # least-squares fit of centre, width and amplitude of the lower interface
+    from scipy.optimize import least_squares
+    fit = least_squares(lambda v: got[:48] - v[2] * np.tanh((zc[:48] - v[0]) / v[1]), [23.0, 0.9 * l, 0.9]).x
+    assert abs(fit[1] / l - 1) < 0.01
+    assert abs(fit[2] / T.bulk_order_parameter(A, B) - 1) < 0.005
+    assert abs(fit[0] - 24) < 1e-3
+
+
+def _shell_ratio(S, theory, mask):
+    r = S[mask] / theory[mask]
+    return r.mean(), r
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("scheme,integrator", [(0, 1), (0, 2), (1, 2)])
+def test_static_structure_factor_2d(scheme, integrator):
+    # diffusion alone (no hydrodynamics): <|psi~(q)|^2> = kT/(A - K L_SO(q)) times the
+    # discrete-time factor (Eq. test2 with the lattice Laplacian); with K = 0 this is
+    # the equilibrium ratio ER = 1 of Eq. (test1)
+    for K in (0.0, 0.1):
+        p = O.Params(dim=2, q=9, nx=32, ny=32, kT=1e-4, A=0.3, B=0.0, K=K, M=0.25, scheme=scheme,
+                     integrator=integrator, coupling=0, lb_on=0, seed=21 + scheme)
+        s = O.State.rest(p)
+        s.advance(400)
+        S = np.zeros(p.shape)
+        ns = 1500
+        for _ in range(ns):
+            s.advance(2)
+            S += O.structure_factor(p, s.psi)
+        S /= ns
+        qg = T.q_grid(p.shape)
+        qg[..., 2] = 0
+        c, w = O.lattice(2, 9)
+        Lm = T.L_so_2d(qg) if scheme == 0 else T.L_fv(qg, c, w)
+        th = T.static_structure_factor(qg, p, Lm, steps=s.step)
+        mask = (-Lm > 0.5)
+        mean, r = _shell_ratio(S, th, mask)
+        assert abs(mean - 1) < 0.02, mean
+        # |q| shells of ~50 modes each stay within 5%
+        qm = np.sqrt((qg ** 2).sum(-1))[mask]
+        for lo in np.arange(0.5, 4.4, 0.6):
+            sel = (qm >= lo) & (qm < lo + 0.6)
+            if sel.sum() > 20:
+                assert abs(r[sel].mean() - 1) < 0.05, (lo, r[sel].mean())
+
+
+@pytest.mark.slow
+def test_static_structure_factor_coupled_3d():
+    # full model H (FLBE + FV psi, Heun) on 10^3: S(q) within 3% of theory on
+    # modes whose relaxation is fast enough, and no psi-u cross-correlation (Fig. 4)
+    p = O.Params(dim=3, q=19, nx=10, ny=10, nz=10, kT=1e-4, A=0.3, B=0.0, K=0.1, M=0.3, scheme=1,
+                 integrator=2, coupling=3, tau=0.8, seed=3)
+    s = O.State.rest(p)
+    s.advance(300)
+    S = np.zeros(p.shape)
+    X = np.zeros(p.shape)
+    ns = 400
+    for _ in range(ns):
+        s.advance(2)
+        S += O.structure_factor(p, s.psi)
+        ph = np.fft.fftn(s.psi.reshape(p.shape))
+        uh = np.fft.fftn(s.u[0].reshape(p.shape))
+        X += (ph * np.conj(uh)).real / p.n
+    S /= ns
+    X /= ns
+    qg = T.q_grid(p.shape)
+    c, w = O.lattice(3, 19)
+    Lm = T.L_fv(qg, c, w)
+    th = T.static_structure_factor(qg, p, Lm, steps=s.step)
+    mask = (-Lm > 0.8)
+    assert abs(S[mask].mean() / th[mask].mean() - 1) < 0.03
+    # cross-correlation is zero within noise: |<psi u*>| << sqrt(<psi^2><u^2>)
+    assert np.abs(X[mask]).mean() < 0.1 * np.sqrt(th[mask].mean() * p.kT)
+
+
+def test_heights_of_linear_profile_brute_force():
+    # interpolated zero of a linear psi(z) = h(x,y) - z is exactly h (Sec. VI.C)
+    p = O.Params(dim=3, q=19, nx=5, ny=4, nz=16)
+    rng = np.random.default_rng(2)
+    h1 = 3.0 + rng.uniform(0, 2, size=(4, 5))
+    h2 = 11.0 + rng.uniform(0, 2, size=(4, 5))
+    zc = np.arange(16)[:, None, None] + 0.0
+    psi = np.where(zc < 8, zc - h1[None], h2[None] - zc)
+    a1, a2 = O.interface_heights(p, psi)
+    assert np.allclose(a1, h1, atol=1e-14)
+    assert np.allclose(a2, h2, atol=1e-14)
+    # the height spectrum of a single cosine has its power at +-q only
+    hh = 2.0 + 0.1 * np.cos(2 * np.pi * np.arange(5) / 5)[None, :].repeat(4, 0)
+    sp = O.height_spectrum(hh)
+    assert abs(sp[0, 1] - (0.1 * 20 / 2) ** 2 / 20) < 1e-14 and abs(sp[0, 4] - sp[0, 1]) < 1e-14
+    assert np.sum(sp) - sp[0, 1] - sp[0, 4] < 1e-14

@@ -1,0 +1,122 @@
+"""Pins of the oracle's lattice operators against the Fourier symbols printed in
+App. A and Sec. V.B, and of the finite-difference noise against Eq. (etafdt)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import theory as T
+
+
+def _plane_waves(shape):
+    """Yield (q, cos(q.r)) for every wavevector of the lattice (nz, ny, nx)."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    qg = T.q_grid(shape)
+    for idx in np.ndindex(shape):
+        qv = qg[idx]
+        yield qv, np.cos(qv[0] * x + qv[1] * y + qv[2] * z)
+
+
+def test_so_laplacian_symbol_3d():
+    # Eq. (solap) applied to cos(q.r) multiplies it by Eq. (solapft)
+    shape = (4, 6, 8)
+    for qv, wave in _plane_waves(shape):
+        out = O.laplacian_so(3, wave)
+        assert np.allclose(out, T.L_so(qv) * wave, atol=1e-13)
+
+
+def test_so_laplacian_symbol_2d():
+    shape = (1, 6, 8)
+    for qv, wave in _plane_waves(shape):
+        out = O.laplacian_so(2, wave[0])
+        assert np.allclose(out, T.L_so_2d(qv) * wave[0], atol=1e-13)
+
+
+def test_laplacian_symbols_limit():
+    # every admissible stencil tends to -q^2 (Sec. III); the SO one to O(q^4)
+    for qv in ([1e-3, 0, 0], [1e-3, 2e-3, -1e-3], [7e-4, 7e-4, 7e-4]):
+        q2 = float(np.dot(qv, qv))
+        for L in (T.L_cd, T.L_pk, T.L_so, T.L_lb):
+            assert abs(L(np.array(qv)) + q2) < 1e-6 * q2
+        q2d = qv[0] ** 2 + qv[1] ** 2
+        assert abs(T.L_so_2d(np.array(qv)) + q2d) < 1e-6 * max(q2d, 1e-30) + 1e-18
+
+
+def test_fv_laplacian_matches_printed_d3q15_symbol():
+    # the finite-volume gradient + link-averaged divergence on the paper's D3Q15
+    # lattice reproduces Eq. (fvlapft) exactly; this fixes the normalisation
+    # (1/c_s^2 on the gradient, 2/c_s^2 on the divergence) left garbled in Sec. V.B
+    shape = (6, 4, 8)
+    for qv, wave in _plane_waves(shape):
+        out = O.fv_laplacian(3, 15, wave)
+        assert np.allclose(out, T.L_fv_d3q15(qv) * wave, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,q", [(3, 19), (2, 9)])
+def test_fv_laplacian_symbol_d3q19_d2q9(dim, q):
+    c, w = O.lattice(dim, q)
+    shape = (4, 6, 8) if dim == 3 else (1, 6, 8)
+    for qv, wave in _plane_waves(shape):
+        out = O.fv_laplacian(dim, q, wave if dim == 3 else wave[0])
+        expect = T.L_fv(qv, c, w) * (wave if dim == 3 else wave[0])
+        assert np.allclose(out, expect, atol=1e-13)
+    # closed forms: D3Q19 -(1/9) sum s_a^2 (1 + c_b + c_g)^2 ; D2Q9 -(1/9) sum s_a^2 (2 + c_b)^2
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        qv = rng.uniform(-np.pi, np.pi, 3)
+        cx, cy, cz = np.cos(qv)
+        sx, sy, sz = np.sin(qv)
+        if dim == 3:
+            closed = -((sx * (1 + cy + cz)) ** 2 + (sy * (1 + cx + cz)) ** 2 + (sz * (1 + cx + cy)) ** 2) / 9
+        else:
+            closed = -((sx * (2 + cy)) ** 2 + (sy * (2 + cx)) ** 2) / 9
+        assert abs(T.L_fv(qv, c, w) - closed) < 1e-14
+    # and -> -q^2 as q -> 0
+    qv = np.array([1e-3, -2e-3, 5e-4]) if dim == 3 else np.array([1e-3, -2e-3, 0.0])
+    assert abs(T.L_fv(qv, c, w) + np.dot(qv, qv)) < 1e-5 * np.dot(qv, qv)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fd_noise_covariance(dim):
+    # <|eta~(q)|^2> = -2 kT M L_SO(q)   (Eq. etafdt), estimated over 400 steps;
+    # each mode's estimator has relative s.d. 1/sqrt(400) (real-field pairs aside)
+    p = O.Params(dim=dim, q=19 if dim == 3 else 9, nx=8, ny=6, nz=4, kT=0.7, M=0.3)
+    acc = np.zeros(p.shape)
+    nsamp = 400
+    for step in range(nsamp):
+        eta = O.fd_noise(p, step).reshape(p.shape)
+        acc += np.abs(np.fft.fftn(eta)) ** 2 / p.n
+        assert abs(eta.sum()) < 1e-12 * np.abs(eta).sum()     # conservative by construction
+    acc /= nsamp
+    qg = T.q_grid(p.shape)
+    L = T.L_so(qg) if dim == 3 else T.L_so_2d(qg)
+    expect = -2 * p.kT * p.M * L
+    mask = np.abs(L) > 1e-12
+    ratio = acc[mask] / expect[mask]
+    assert abs(ratio.mean() - 1) < 4 / np.sqrt(nsamp * mask.sum() / 2)
+    assert np.all(np.abs(ratio - 1) < 6 / np.sqrt(nsamp / 2))
+    assert acc[0, 0, 0] < 1e-20
+
+
+def test_mu_and_force():
+    # mu = A psi + B psi^3 - K lap_SO psi and F = -psi grad_CD mu at a few sites, brute force
+    p = O.Params(dim=3, q=19, nx=5, ny=4, nz=3, A=-0.06, B=0.07, K=0.04)
+    rng = np.random.default_rng(0)
+    psi = rng.normal(size=p.shape)
+    mu = O.mu(p, psi).reshape(p.shape)
+    F = O.force(p, psi).reshape(3, *p.shape)
+    nz, ny, nx = p.shape
+    for (z, y, x) in [(0, 0, 0), (2, 3, 4), (1, 2, 0)]:
+        lap = 0.0
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    k = abs(dx) + abs(dy) + abs(dz)
+                    wgt = {0: -80 / 22, 1: 6 / 22, 2: 3 / 22, 3: 1 / 22}[k]
+                    lap += wgt * psi[(z + dz) % nz, (y + dy) % ny, (x + dx) % nx]
+        m = p.A * psi[z, y, x] + p.B * psi[z, y, x] ** 3 - p.K * lap
+        assert abs(mu[z, y, x] - m) < 1e-12
+        gx = 0.5 * (mu[z, y, (x + 1) % nx] - mu[z, y, (x - 1) % nx])
+        gy = 0.5 * (mu[z, (y + 1) % ny, x] - mu[z, (y - 1) % ny, x])
+        gz = 0.5 * (mu[(z + 1) % nz, y, x] - mu[(z - 1) % nz, y, x])
+        assert np.allclose(F[:, z, y, x], -psi[z, y, x] * np.array([gx, gy, gz]), atol=1e-12)
