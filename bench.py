@@ -1,0 +1,298 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled model-H step (fluctuating LB + stochastic psi step).
+
+Default workload: the D3Q19 512^3 spinodal quench (A -0.0625, B 0.0625, K 0.04,
+M 0.1, kT 1e-5, psi0 uniform in [-0.01, 0.01], u0 = 0), FP32 population
+deviations, finite-volume psi scheme, Heun integrator, structure factor
+|k_a| <= 8 accumulated every 10 steps.  One "step" advances every lattice site
+once in both equations.  Metric: coupled lattice-site updates per second
+(MLUPS), whole job.  Replicas only: with N GPUs every rank advances its own
+512^3 box (weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU checker on a bounded sample of the same
+workload (a 48^3 box with the same parameters) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALG_BYTES_SITE = {0: 160, 1: 84}          # populations in+out + psi in+out, FP32 / FP16 deviations
+LB_ALG_BYTES_SITE = {0: 152, 1: 76}       # populations in+out (the LB kernel's share)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=512, help="edge of the cubic box")
+    ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(size: int, storage: int):
+    from paper_1104_0078_gb300 import inputs as I
+    d = dict(I.WORKLOADS["quench"])
+    d.update(nx=size, ny=size, nz=size)
+    name = f"D3Q19 {size}^3 spinodal quench, {'FP32' if storage == 0 else 'FP16'} deviations, FV, Heun"
+    return d, name
+
+
+def oracle_mlups(d: dict, box: int, budget_s: float, nsteps=None):
+    """Time the FP64 checker on a box^3 sample with the workload's parameters."""
+    import oracle as O
+    from paper_1104_0078_gb300 import inputs as I
+    p = O.Params(dim=3, q=19, nx=box, ny=box, nz=box, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"],
+                 M=d["M"], scheme=1, integrator=2, coupling=3, seed=d["seed"])
+    st = O.State.rest(p, psi=I.uniform_field(p.n, -0.01, 0.01, 11))
+    t0 = time.perf_counter()
+    st.advance(1)
+    t1 = time.perf_counter() - t0
+    n = nsteps if nsteps is not None else max(1, int(budget_s / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    st.advance(n)
+    dt = time.perf_counter() - t0
+    return p.n * n / dt / 1e6, n, dt, O.threads()
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (t, l) in self.lines if t0 - 0.15 <= t <= t1 + 0.15] or [l for (_, l) in self.lines[-3:]]
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in rows:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def lb_traffic(storage: int, n_sites: int):
+    """DRAM bytes per LB launch from the committed ncu summary, if it was taken on
+    the current kernel source; scaled by sites when the capture was smaller."""
+    path = os.path.join(ROOT, "profiles", "lb_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_1104_0078_gb300", "csrc", "flb_lb.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") != sha or rec.get("storage") != storage:
+            return None
+        return rec["dram_bytes_per_launch"] * n_sites / rec["sites"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    storage = 0 if args.storage == "f32" else 1
+    d, name = workload(args.size, storage)
+    box = 48
+    # each step: one checker step on a 48^3 sample of the workload
+    for _ in range(max(args.warmup, 0)):
+        oracle_mlups(d, box, 0, nsteps=1)
+    mlups, n, dt, cores = oracle_mlups(d, box, 0, nsteps=args.steps)
+    line = {
+        "impl": "reference", "metric": "coupled lattice-site updates/s", "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / n * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "sample": f"{box}^3 box, same parameters"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} steps of a {box}^3 box"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1104_0078_gb300 as F
+    from paper_1104_0078_gb300 import inputs as I
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    storage = F.FLB_F32_DEV if args.storage == "f32" else F.FLB_F16_DEV
+    d, name = workload(args.size, storage)
+    p = F.flb_params_default(nx=d["nx"], ny=d["ny"], nz=d["nz"], tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"],
+                             K=d["K"], M=d["M"], psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, storage=storage,
+                             seed=d["seed"] + rank, sq_kmax=8)
+    N = p.nx * p.ny * p.nz
+    s = F.Solver(p, device=f"cuda:{local}")
+    psi0 = I.uniform_field(N, -0.01, 0.01, 11 + rank)
+    s.set_fields(psi=psi0)
+    s.set_sampling(10, 1)
+    s.step(args.warmup)
+    s.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    l0 = s.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.perf_counter()
+    ev0.record(s.stream)
+    s.step(args.steps)
+    ev1.record(s.stream)
+    ev1.synchronize()
+    tw1 = time.perf_counter()
+    barrier()
+    launches = s.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    sampler.stop()
+    clocks = sampler.summary(tw0, tw1)
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * args.steps * ws / (ms / 1e3) / 1e6
+
+    # live per-kernel timing on the library's stream (CUDA events around each launch)
+    s.set_profiling(True)
+    kp = min(args.steps, 20)
+    s.step(kp)
+    kms, kcnt = s.kernel_times()
+    s.set_profiling(False)
+    lb_ms = kms["lb"] / max(kcnt["lb"], 1)
+    peak, peak_kind = measured_peak()
+    lb_bytes = LB_ALG_BYTES_SITE[storage] * N
+    achieved = lb_bytes / (lb_ms / 1e3) / 1e9
+    step_ms = ms / args.steps
+    step_gbs = ALG_BYTES_SITE[storage] * N / (step_ms / 1e3) / 1e9
+
+    # end to end through the public API: upload the initial field, step, read totals
+    e2e = None
+    if not args.no_e2e:
+        s2 = s  # reuse the handle and workspace; set_fields re-initialises the state
+        barrier()
+        t0 = time.perf_counter()
+        s2.set_fields(psi=psi0)
+        s2.step(args.steps)
+        tot, u2, rc = s2.moments()
+        t1 = time.perf_counter()
+        P = (p.nx + 8) * (p.ny + 6) * (p.nz + 6)
+        h2d = 4 * P * (1 + 3)
+        e2e = {"value": N * args.steps / (t1 - t0) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 72 / args.steps}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{n} coupled steps of a 64^3 box with the workload's parameters, FP64"}
+    if rank == 0:
+        line = {
+            "metric": "coupled lattice-site updates/s", "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if storage == 0 else "f16-storage/f32",
+            "data": "synthetic",
+            "config": {"workload": name, "box": [p.nx, p.ny, p.nz], "lattice": "D3Q19", "psi_scheme": "FV",
+                       "integrator": "Heun", "sampling": "S(q) |k_a|<=8 every 10 steps",
+                       "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 19 * N * (4 if storage == 0 else 2) / 1e9),
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": lb_traffic(storage, N),
+                         "kernel": "LB collide-stream", "peak_kind": peak_kind,
+                         "alg_bytes_per_site": LB_ALG_BYTES_SITE[storage], "kernel_ms": lb_ms},
+            "step_roofline": {"alg_bytes_per_site": ALG_BYTES_SITE[storage], "achieved_gbs": step_gbs,
+                              "frac": step_gbs / peak, "kernel_ms_per_step": {k: v / kp for k, v in kms.items()}},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

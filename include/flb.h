@@ -1,0 +1,212 @@
+/*
+ * flb.h -- C ABI of the GB300 library for the hybrid model-H solver of
+ * Sumesh, Pagonabarraga & Adhikari, "Lattice Boltzmann - Langevin simulations
+ * of binary mixtures" (arXiv:1104.0078).
+ *
+ * One time step advances, in this order and both from the state at time n
+ * (Sec. VI, "alternate marching"):
+ *   1. the fluctuating lattice Boltzmann equation for the momentum (Sec. IV,
+ *      App. B): pull-streaming of the auxiliary populations fbar, moments
+ *      rho = sum fbar, rho v = sum fbar c + F/2, moment-space relaxation with
+ *      the order-parameter force F = -psi grad mu and Landau-Lifshitz noise on
+ *      every stress and ghost mode (Eq. bab, adhikari2005);
+ *   2. the stochastic method-of-lines step of the order parameter psi
+ *      (Sec. V): d psi/dt = -div(u psi) + M lap mu + div xi, with
+ *      mu = A psi + B psi^3 - K lap_SO psi (Sec. II.A, App. A), in the
+ *      finite-difference (Sec. V.A) or finite-volume (Sec. V.B) form, noise
+ *      held fixed over a Runge-Kutta step (Sec. V, wilkie2004).
+ *
+ * Units: lattice units, dx = dt = 1, c_s^2 = 1/3, periodic boundaries.
+ * Threading: a handle is not thread-safe; calls on one handle must be
+ * serialised by the caller.  All device work is issued on the stream given to
+ * flb_init; functions documented as synchronising wait for that stream.
+ * Memory: the library never allocates device memory.  The caller allocates one
+ * device workspace of flb_workspace_bytes() bytes (e.g. a torch uint8 tensor)
+ * and keeps it alive until flb_destroy().  Host buffers passed to any call are
+ * caller-owned and are not retained after the call returns.
+ * Errors: every int-returning call returns FLB_OK (0) or a negative FLB_E*
+ * code; flb_strerror() names it.  Faults detected on the device (non-finite
+ * values, a timed-out wait) are latched in a device status word and reported
+ * by the next synchronising call.
+ */
+#ifndef FLB_H
+#define FLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FLB_OK 0
+#define FLB_EINVAL (-1)        /* invalid argument or parameter combination */
+#define FLB_ENOSPC (-2)        /* workspace or host buffer too small */
+#define FLB_ECUDA (-3)         /* a CUDA runtime call failed */
+#define FLB_ENONFINITE (-4)    /* a reduction met NaN or Inf in the fields */
+#define FLB_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define FLB_EUNSUPPORTED (-6)  /* valid request this build does not provide */
+
+/* ---- enumerations ---- */
+#define FLB_FD 0               /* finite-difference psi scheme, Sec. V.A */
+#define FLB_FV 1               /* finite-volume psi scheme, Sec. V.B */
+#define FLB_EULER 1            /* one-stage integrator */
+#define FLB_HEUN 2             /* two-stage (RK2) integrator, noise held fixed */
+#define FLB_F32_DEV 0          /* populations stored as FP32 deviations fbar_i - w_i rho0 */
+#define FLB_F16_DEV 1          /* populations stored as FP16 deviations */
+#define FLB_COUPLE_FORCE 1     /* psi exerts -psi grad mu on the fluid */
+#define FLB_COUPLE_ADVECT 2    /* the fluid advects psi */
+#define FLB_SQ_PSI 0           /* structure factor of psi */
+#define FLB_SQ_HEIGHT 1        /* capillary spectrum of the two psi = 0 surfaces */
+#define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
+#define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
+
+/*
+ * Parameters of one lattice (one replica).  Names follow the paper.
+ *   dim, q      : 2 and 9 (D2Q9) or 3 and 19 (D3Q19).
+ *   nx, ny, nz  : lattice size, each >= 4 (nz is ignored and taken as 1 in 2D);
+ *                 nx*ny*nz < 2^31.
+ *   rho0        : reference density, > 0 (the populations are stored as
+ *                 deviations from w_i rho0).
+ *   tau         : the paper's relaxation time (App. B): omega = 1/(tau + 1/2),
+ *                 shear viscosity c_s^2 tau; > 0.
+ *   gamma_bulk  : relaxation factor of the trace of the stress, in (-1, 1);
+ *                 NaN selects the shear factor 1 - omega (the paper's choice).
+ *   gamma_ghost : relaxation factor of the ghost modes, in (-1, 1); 0 projects
+ *                 them out before they are thermalised (Eq. bab, Sec. III).
+ *   kT          : temperature, >= 0 (0 switches all noise off).
+ *   A, B, K, M  : free energy f = A/2 psi^2 + B/4 psi^4 + K/2 |grad psi|^2
+ *                 (Eqs. Feng, feng) and mobility M >= 0.
+ *   psi_scheme  : FLB_FD or FLB_FV.
+ *   integrator  : FLB_EULER or FLB_HEUN.
+ *   storage     : FLB_F32_DEV or FLB_F16_DEV.
+ *   coupling    : bit mask of FLB_COUPLE_FORCE | FLB_COUPLE_ADVECT (3 = model H;
+ *                 0 = "diffusion alone" of Sec. VI.A).
+ *   seed        : Philox key of this replica.
+ *   sq_kmax     : structure-factor window: wavevector indices |k_a| <= sq_kmax
+ *                 on every axis; <= 0 or >= n_a/2 keeps the whole axis.
+ */
+typedef struct flb_params {
+    int32_t dim, q;
+    int32_t nx, ny, nz;
+    double rho0, tau;
+    double gamma_bulk, gamma_ghost;
+    double kT, A, B, K, M;
+    int32_t psi_scheme, integrator, storage, coupling;
+    uint64_t seed;
+    int32_t sq_kmax;
+    int32_t reserved;
+} flb_params;
+
+typedef struct flb_handle flb_handle;
+
+/* Fill *p with the defaults: D3Q19 32^3, rho0 1, tau 0.8, gamma_bulk NaN,
+ * gamma_ghost 0, kT 0, A 0.05, B 0, K 0.04, M 0.1, FV, Heun, FP32, coupling 3,
+ * seed 1, sq_kmax 0. */
+void flb_params_default(flb_params *p);
+
+/* Device workspace needed for nrep replicas p[0..nrep-1]; 0 if any parameter
+ * set is invalid.  Replicas may differ in size, seed and physical constants but
+ * must share dim, q, psi_scheme, integrator and storage. */
+size_t flb_workspace_bytes(const flb_params *p, int32_t nrep);
+
+/* Create a handle.  dev_ws: device pointer, 256-byte aligned, ws_bytes >=
+ * flb_workspace_bytes(p, nrep), caller-owned.  cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream).  Every replica starts at rest (fbar = w rho0,
+ * u = 0, psi = 0) at step 0.  Synchronising.  Errors: EINVAL, ENOSPC, ECUDA. */
+int flb_init(const flb_params *p, int32_t nrep, void *dev_ws, size_t ws_bytes, void *cuda_stream,
+             flb_handle **out);
+
+/* Equilibrium initialisation of replica rep from host fields (FP64, site-major
+ * s = x + nx*(y + ny*z)): rho[N] (NULL: rho0), u[dim][N] (NULL: 0), psi[N]
+ * (NULL: 0).  fbar = w (rho + rho u.c/c_s^2 + rho uu:Q/(2 c_s^4)).  Also sets
+ * the stored velocity to u.  Synchronising. */
+int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *u, const double *psi);
+
+/* Physical populations fbar_i(x, t) after streaming, FP64 [q][N], the state the
+ * paper's App. B evolves; set replaces the populations (psi and u are kept).
+ * Synchronising. */
+int flb_get_populations(flb_handle *h, int32_t rep, double *f);
+int flb_set_populations(flb_handle *h, int32_t rep, const double *f);
+
+/* Order parameter psi(t) [N] and the velocity u [dim][N] that the last psi
+ * step used (time t-1; the initial field before the first step).  Either pointer
+ * may be NULL.  Synchronising. */
+int flb_get_psi_u(flb_handle *h, int32_t rep, double *psi, double *u);
+
+/* A periodic window of replica rep: origin (x0,y0,z0), size wx*wy*wz, populations
+ * f[q][W] and psi[W] in window site order (either may be NULL).  Synchronising. */
+int flb_get_window(flb_handle *h, int32_t rep, int32_t x0, int32_t y0, int32_t z0, int32_t wx, int32_t wy,
+                   int32_t wz, double *f, double *psi);
+
+/* Advance every replica by n >= 0 steps.  Asynchronous on the stream. */
+int flb_step(flb_handle *h, int64_t n);
+
+/* Current step counter of replica rep. */
+int flb_get_step(flb_handle *h, int32_t rep, int64_t *step);
+
+/* Conserved totals and velocity variance of replica rep, reduced on the device
+ * in FP64: totals = {sum rho, sum j_x, sum j_y, [sum j_z,] sum psi} (2 + dim
+ * values; j = sum fbar c), u2 = {<u_x^2>, <u_y^2>, [<u_z^2>]} of the stored
+ * velocity.  Either pointer may be NULL.  Synchronising; returns ENONFINITE if
+ * any population, psi or u value was NaN or Inf. */
+int flb_moments(flb_handle *h, int32_t rep, double *totals, double *u2);
+
+/* Sampling of the structure factors during flb_step: every every_m steps
+ * (0 = never) the psi spectrum (mask bit 1) and/or the interface-height
+ * spectrum (mask bit 2) of every replica is accumulated in FP64. */
+int flb_set_sampling(flb_handle *h, int32_t every_m, int32_t mask);
+
+/* Take one sample now (same mask bits).  Asynchronous. */
+int flb_sample(flb_handle *h, int32_t mask);
+
+/* Accumulated mean spectrum of replica rep.  which = FLB_SQ_PSI: out has
+ * Kz*Ky*Kx values <|psi~(q)|^2> with psi~(q) = N^-1/2 sum psi e^{-iq.r}
+ * (Eqs. test1, test2); each axis lists indices k = 0..kmax then n-kmax..n-1
+ * (all n indices when the whole axis is kept), x fastest.  which =
+ * FLB_SQ_HEIGHT: out has ny*nx values <|h~(q)|^2> (Eq. flucinterf) averaged over
+ * the two interfaces of a slab normal to z.  *nsamples receives the sample
+ * count.  Synchronising. */
+int flb_structure_factor(flb_handle *h, int32_t rep, int32_t which, double *out, int64_t *nsamples);
+
+/* Number of values flb_structure_factor writes for `which`. */
+int64_t flb_structure_factor_size(flb_handle *h, int32_t rep, int32_t which);
+
+/* Zero the accumulated spectra of replica rep (-1: all). */
+int flb_sq_reset(flb_handle *h, int32_t rep);
+
+/* Launch mode for flb_step: FLB_MODE_PLAIN or FLB_MODE_BATCHED. */
+int flb_set_mode(flb_handle *h, int32_t mode);
+
+/* Bitwise checkpoint of replica rep: flb_state_bytes() bytes holding the step
+ * counter, the stored populations and psi exactly as kept on the device.
+ * Restoring gives a bitwise-identical continuation (the noise is
+ * counter-based).  Synchronising. */
+size_t flb_state_bytes(flb_handle *h, int32_t rep);
+int flb_get_state(flb_handle *h, int32_t rep, void *host, size_t bytes);
+int flb_set_state(flb_handle *h, int32_t rep, const void *host, size_t bytes);
+
+/* Wait for the stream and return any latched device error. */
+int flb_synchronize(flb_handle *h);
+
+/* Kernel launches issued by this handle since creation (for accounting). */
+int64_t flb_launch_count(flb_handle *h);
+
+/* Per-phase device timing.  While on, flb_step records CUDA events around the
+ * lattice Boltzmann kernel and around the psi kernels of every replica step.
+ * flb_kernel_times() synchronises and returns the summed milliseconds and
+ * launch counts of {LB kernel, psi kernels (incl. mu), sampling} since the
+ * last flb_set_profiling(h, 1), which clears them.  ms and counts: 3 entries. */
+int flb_set_profiling(flb_handle *h, int32_t on);
+int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts);
+
+const char *flb_strerror(int code);
+
+/* Release the handle (not the caller's workspace or stream). */
+void flb_destroy(flb_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLB_H */

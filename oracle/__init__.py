@@ -65,6 +65,7 @@ def lib():
         L = ctypes.CDLL(path)
         P = ctypes.POINTER
         dp = P(ctypes.c_double)
+        L.ora_threads.restype = ctypes.c_int
         L.ora_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
         L.ora_gaussians.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_int32, dp]
@@ -139,6 +140,11 @@ class Params:
         p.gnx, p.gny, p.gnz = self.gdims
         p.ox, p.oy, p.oz = self.origin
         return p
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's site loops use."""
+    return int(lib().ora_threads())
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

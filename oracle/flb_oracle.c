@@ -28,6 +28,19 @@
 #include <string.h>
 
 #include "flb_oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the site loops use (OpenMP), for reporting the CPU baseline. */
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   */

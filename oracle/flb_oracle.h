@@ -29,6 +29,7 @@ typedef struct {
     int32_t ox, oy, oz;     /* origin of this box inside the global lattice */
 } ora_params;
 
+int ora_threads(void);
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream, int32_t nblocks, double *g);
 int ora_lattice(int32_t dim, int32_t q, int32_t *c, double *w);

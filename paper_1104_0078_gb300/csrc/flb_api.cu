@@ -1,0 +1,885 @@
+// flb_api.cu -- host runtime behind the C ABI of include/flb.h: parameter
+// validation, carving of the caller's device workspace, equilibrium and state
+// import/export, the per-step launch sequence and the observables.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <algorithm>
+#include <vector>
+
+#include "flb_internal.cuh"
+#include "flb_obs.cuh"
+
+using namespace flb;
+
+namespace {
+
+// ---- velocity sets in the kernels' plane order ----------------------------
+const int C19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+                        {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+                        {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+const int C9[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                      {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+
+inline const int *cvec(int q, int i) { return q == 19 ? C19[i] : C9[i]; }
+inline double wgt(int q, int i)
+{
+    const int *c = cvec(q, i);
+    const int l2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    if (q == 19) return l2 == 0 ? 1.0 / 3.0 : l2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
+    return l2 == 0 ? 4.0 / 9.0 : l2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0;
+}
+
+// norms of the noisy modes in noise order (hand-derived from the monomials)
+const double NORM19[15] = {2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 2.0 / 27, 2.0 / 27,
+                           2.0 / 27, 2.0 / 9, 2.0 / 9, 2.0 / 9, 2.0 / 9, 1.0 / 3, 1.0 / 9};
+const double NORM9[6] = {4.0 / 9, 4.0 / 9, 1.0 / 9, 2.0 / 27, 2.0 / 27, 16.0 / 81};
+
+constexpr long long WIN_MAX = 32768;  // sites of one flb_get_window call
+constexpr int RED_MAX_BLOCKS = 1024;
+
+struct Rep {
+    flb_params p;
+    Geom g;
+    int q = 0, dim = 0;
+    size_t pop_elem = 4;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *psi[2] = {nullptr, nullptr};
+    int pcur = 0;
+    float *psis = nullptr, *mu = nullptr, *mus = nullptr, *u = nullptr, *J = nullptr, *eta = nullptr, *E = nullptr;
+    double *sq = nullptr, *hsq = nullptr;
+    int Kx = 0, Ky = 0, Kz = 0;
+    int64_t sq_n = 0, h_n = 0;
+    int64_t step = 0;
+    float omega_s = 0, omega_b = 0, gamma_g = 0;
+    float namp[16] = {0};
+};
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int axis_K(int n, int kmax) { return (kmax <= 0 || 2 * kmax + 1 >= n) ? n : 2 * kmax + 1; }
+
+bool valid(const flb_params &p)
+{
+    if (!((p.dim == 3 && p.q == 19) || (p.dim == 2 && p.q == 9))) return false;
+    const long long nz = p.dim == 3 ? p.nz : 1;
+    if (p.nx < 4 || p.ny < 4 || (p.dim == 3 && p.nz < 4)) return false;
+    if ((long long)p.nx * p.ny * nz >= (1LL << 31)) return false;
+    if (!(p.rho0 > 0) || !(p.tau > 0) || !std::isfinite(p.tau) || !std::isfinite(p.rho0)) return false;
+    if (!std::isnan(p.gamma_bulk) && !(std::fabs(p.gamma_bulk) < 1.0)) return false;
+    if (!(std::fabs(p.gamma_ghost) < 1.0)) return false;
+    if (!(p.kT >= 0) || !(p.M >= 0) || !std::isfinite(p.kT) || !std::isfinite(p.M)) return false;
+    if (!std::isfinite(p.A) || !std::isfinite(p.B) || !std::isfinite(p.K)) return false;
+    if (p.psi_scheme != FLB_FD && p.psi_scheme != FLB_FV) return false;
+    if (p.integrator != FLB_EULER && p.integrator != FLB_HEUN) return false;
+    if (p.storage != FLB_F32_DEV && p.storage != FLB_F16_DEV) return false;
+    if (p.coupling < 0 || p.coupling > 3) return false;
+    if (p.sq_kmax < 0) return false;
+    return true;
+}
+
+Geom make_geom(const flb_params &p)
+{
+    Geom g;
+    g.dim = p.dim;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.nz = p.dim == 3 ? p.nz : 1;
+    g.gz = p.dim == 3 ? GZ3 : 0;
+    g.px = g.nx + 2 * GX;
+    g.py = g.ny + 2 * GY;
+    g.pz = g.nz + 2 * g.gz;
+    g.n = (long long)g.nx * g.ny * g.nz;
+    g.pn = (long long)g.px * g.py * g.pz;
+    return g;
+}
+
+// Assign the replica's device arrays from the carver (base may be null for sizing).
+void carve_rep(Rep &r, Carver &cv)
+{
+    const Geom &g = r.g;
+    const size_t N = (size_t)g.n, P = (size_t)g.pn;
+    r.f[0] = cv.take<char>((size_t)r.q * N * r.pop_elem);
+    r.f[1] = cv.take<char>((size_t)r.q * N * r.pop_elem);
+    r.psi[0] = cv.take<float>(P);
+    r.psi[1] = cv.take<float>(P);
+    r.mu = cv.take<float>(P);
+    r.u = cv.take<float>((size_t)r.dim * P);
+    r.eta = cv.take<float>(N);
+    if (r.p.integrator == FLB_HEUN) {
+        r.psis = cv.take<float>(P);
+        r.mus = cv.take<float>(P);
+        r.E = cv.take<float>(N);
+    }
+    if (r.p.psi_scheme == FLB_FV) r.J = cv.take<float>((size_t)r.dim * P);
+    r.Kx = axis_K(g.nx, r.p.sq_kmax);
+    r.Ky = axis_K(g.ny, r.p.sq_kmax);
+    r.Kz = r.dim == 3 ? axis_K(g.nz, r.p.sq_kmax) : 1;
+    r.sq = cv.take<double>((size_t)r.Kx * r.Ky * r.Kz);
+    if (r.dim == 3) r.hsq = cv.take<double>((size_t)g.nx * g.ny);
+}
+
+void init_rep_consts(Rep &r, const flb_params &p)
+{
+    r.p = p;
+    r.q = p.q;
+    r.dim = p.dim;
+    r.g = make_geom(p);
+    r.pop_elem = p.storage == FLB_F16_DEV ? 2 : 4;
+    const double ws = 1.0 / (p.tau + 0.5);
+    const double gs = 1.0 - ws;
+    const double gb = std::isnan(p.gamma_bulk) ? gs : p.gamma_bulk;
+    r.omega_s = (float)ws;
+    r.omega_b = (float)(1.0 - gb);
+    r.gamma_g = (float)p.gamma_ghost;
+    const int nn = p.q == 19 ? 15 : 6;
+    const int nstress = p.q == 19 ? 6 : 3;
+    for (int t = 0; t < nn; ++t) {
+        const double gam = t == 0 ? gb : (t < nstress ? gs : p.gamma_ghost);
+        const double b = p.q == 19 ? NORM19[t] : NORM9[t];
+        r.namp[t] = (float)std::sqrt((1.0 - gam * gam) / b);
+    }
+}
+
+}  // namespace
+
+struct flb_handle {
+    std::vector<Rep> reps;
+    cudaStream_t st = nullptr;
+    int mode = FLB_MODE_PLAIN;
+    int sample_every = 0, sample_mask = 0;
+    int64_t launches = 0;
+    double *red_partial = nullptr, *red_out = nullptr;
+    float2 *X1 = nullptr, *X2 = nullptr;
+    float *heights = nullptr, *win = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    // per-phase timing (flb_set_profiling)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
+    int64_t phase_launches[3] = {0, 0, 0};
+    ~flb_handle()
+    {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+size_t carve_all(flb_handle &h, char *base)
+{
+    Carver cv{base};
+    size_t cap1 = 0, cap2 = 0, hcap = 0;
+    long long maxq = 0;
+    for (Rep &r : h.reps) {
+        carve_rep(r, cv);
+        const Geom &g = r.g;
+        cap1 = std::max(cap1, (size_t)g.nz * g.ny * r.Kx);
+        cap2 = std::max(cap2, (size_t)g.nz * r.Ky * r.Kx);
+        if (r.dim == 3) {
+            cap1 = std::max(cap1, (size_t)g.ny * g.nx);
+            cap2 = std::max(cap2, (size_t)g.ny * g.nx);
+            hcap = std::max(hcap, (size_t)2 * g.nx * g.ny);
+        }
+        maxq = std::max<long long>(maxq, r.q);
+    }
+    h.red_partial = cv.take<double>((size_t)RED_MAX_BLOCKS * NRED);
+    h.red_out = cv.take<double>(NRED);
+    h.X1 = cv.take<float2>(cap1);
+    h.X2 = cv.take<float2>(cap2);
+    h.heights = cv.take<float>(std::max<size_t>(hcap, 1));
+    h.win = cv.take<float>((size_t)WIN_MAX * (maxq + 1));
+    return cv.off + 256;
+}
+
+int cuerr(cudaError_t e) { return e == cudaSuccess ? FLB_OK : FLB_ECUDA; }
+
+// Record a timing event on the handle's stream (no-op unless profiling).
+cudaEvent_t mark(flb_handle *h)
+{
+    if (!h->profiling) return nullptr;
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    cudaEvent_t e = h->ev_pool[h->ev_used++];
+    cudaEventRecord(e, h->st);
+    return e;
+}
+
+void span(flb_handle *h, int phase, cudaEvent_t a, cudaEvent_t b, int launches)
+{
+    if (!h->profiling || !a || !b) return;
+    h->spans[phase].push_back({a, b});
+    h->phase_launches[phase] += launches;
+}
+
+// physical fbar (FP64, [q][N]) -> stored post-collision deviations at origin sites
+void phys_to_stored(const Rep &r, const double *f, std::vector<float> &out)
+{
+    const Geom &g = r.g;
+    const long long N = g.n;
+    out.resize((size_t)r.q * N);
+    for (int i = 0; i < r.q; ++i) {
+        const int *c = cvec(r.q, i);
+        const double wr = wgt(r.q, i) * r.p.rho0;
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    // stored_i(y) = fbar_i(y + c_i)
+                    const long long src = g.sidx(wrapi(x + c[0], g.nx), wrapi(y + c[1], g.ny),
+                                                 g.dim == 3 ? wrapi(z + c[2], g.nz) : 0);
+                    out[(size_t)i * N + g.sidx(x, y, z)] = (float)(f[(size_t)i * N + src] - wr);
+                }
+    }
+}
+
+int upload_pops(flb_handle *h, Rep &r, const std::vector<float> &dev)
+{
+    const size_t n = dev.size();
+    if (r.pop_elem == 4) return cuerr(cudaMemcpyAsync(r.f[r.cur], dev.data(), n * 4, cudaMemcpyHostToDevice, h->st));
+    std::vector<__half> hv(n);
+    for (size_t k = 0; k < n; ++k) hv[k] = __float2half_rn(dev[k]);
+    int rc = cuerr(cudaMemcpyAsync(r.f[r.cur], hv.data(), n * 2, cudaMemcpyHostToDevice, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    return rc;
+}
+
+int download_pops(flb_handle *h, Rep &r, std::vector<float> &dev)
+{
+    const size_t n = (size_t)r.q * r.g.n;
+    dev.resize(n);
+    if (r.pop_elem == 4) {
+        int rc = cuerr(cudaMemcpyAsync(dev.data(), r.f[r.cur], n * 4, cudaMemcpyDeviceToHost, h->st));
+        return rc == FLB_OK ? cuerr(cudaStreamSynchronize(h->st)) : rc;
+    }
+    std::vector<__half> hv(n);
+    int rc = cuerr(cudaMemcpyAsync(hv.data(), r.f[r.cur], n * 2, cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    for (size_t k = 0; k < n; ++k) dev[k] = __half2float(hv[k]);
+    return rc;
+}
+
+// interior values (FP32, [N]) -> padded plane with every ghost cell filled periodically
+void to_padded(const Geom &g, const float *in, std::vector<float> &out)
+{
+    out.assign((size_t)g.pn, 0.f);
+    for (int z = -g.gz; z < g.nz + g.gz; ++z)
+        for (int y = -GY; y < g.ny + GY; ++y)
+            for (int x = -GX; x < g.nx + GX; ++x)
+                out[(size_t)g.pidx(x, y, z)] =
+                    in[g.sidx(((x % g.nx) + g.nx) % g.nx, ((y % g.ny) + g.ny) % g.ny, ((z % g.nz) + g.nz) % g.nz)];
+}
+
+int upload_padded(flb_handle *h, const Geom &g, float *dst, const float *interior)
+{
+    std::vector<float> pad;
+    to_padded(g, interior, pad);
+    int rc = cuerr(cudaMemcpyAsync(dst, pad.data(), pad.size() * 4, cudaMemcpyHostToDevice, h->st));
+    return rc == FLB_OK ? cuerr(cudaStreamSynchronize(h->st)) : rc;
+}
+
+int download_interior(flb_handle *h, const Geom &g, const float *src, std::vector<float> &out)
+{
+    std::vector<float> pad((size_t)g.pn);
+    int rc = cuerr(cudaMemcpyAsync(pad.data(), src, pad.size() * 4, cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    out.resize((size_t)g.n);
+    for (int z = 0; z < g.nz; ++z)
+        for (int y = 0; y < g.ny; ++y)
+            for (int x = 0; x < g.nx; ++x) out[(size_t)g.sidx(x, y, z)] = pad[(size_t)g.pidx(x, y, z)];
+    return rc;
+}
+
+#define FLB_TRY(expr)                     \
+    do {                                  \
+        const cudaError_t e_ = (expr);    \
+        ++h->launches;                    \
+        if (e_ != cudaSuccess) return FLB_ECUDA; \
+    } while (0)
+
+// One coupled step of one replica: LB (reads psi^n, mu^n; writes u^n), then psi.
+int step_rep(flb_handle *h, Rep &r)
+{
+    const Geom &g = r.g;
+    const flb_params &p = r.p;
+    cudaStream_t st = h->st;
+    float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
+    const int64_t l0 = h->launches;
+    cudaEvent_t e0 = mark(h);
+    FLB_TRY(launch_mu(g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+    cudaEvent_t e1 = mark(h);
+
+    LBArgs la;
+    la.g = g;
+    la.fin = r.f[r.cur];
+    la.fout = r.f[r.cur ^ 1];
+    la.psi = psi_n;
+    la.mu = r.mu;
+    la.u = r.u;
+    la.rho0 = (float)p.rho0;
+    la.omega_s = r.omega_s;
+    la.omega_b = r.omega_b;
+    la.gamma_g = r.gamma_g;
+    la.kT = (float)p.kT;
+    std::memcpy(la.namp, r.namp, sizeof(la.namp));
+    la.coupling = p.coupling;
+    la.seed = p.seed;
+    la.step = r.step;
+    FLB_TRY(launch_lb(la, r.q, p.storage, st));
+    cudaEvent_t e2 = mark(h);
+    const int64_t l2 = h->launches;
+
+    const bool noisy = p.kT > 0 && p.M > 0;
+    if (noisy) {
+        NoiseArgs na;
+        na.g = g;
+        na.eta = r.eta;
+        na.kT = (float)p.kT;
+        na.M = (float)p.M;
+        na.scheme = p.psi_scheme;
+        na.seed = p.seed;
+        na.step = r.step;
+        FLB_TRY(launch_noise(na, st));
+    }
+    if (p.psi_scheme == FLB_FV) FLB_TRY(launch_flux(g, r.q, psi_n, r.mu, r.u, r.J, (float)p.M, p.coupling, st));
+    PsiArgs pa;
+    pa.g = g;
+    pa.psi = psi_n;
+    pa.mu = r.mu;
+    pa.u = r.u;
+    pa.J = r.J;
+    pa.eta = noisy ? r.eta : nullptr;
+    pa.psi0 = nullptr;
+    pa.out = p.integrator == FLB_HEUN ? r.psis : psi_np1;
+    pa.acc = r.E;
+    pa.A = (float)p.A;
+    pa.B = (float)p.B;
+    pa.K = (float)p.K;
+    pa.M = (float)p.M;
+    pa.coupling = p.coupling;
+    pa.scheme = p.psi_scheme;
+    pa.stage = 1;
+    pa.integrator = p.integrator;
+    FLB_TRY(launch_psi_update(pa, r.q, st));
+    if (p.integrator == FLB_HEUN) {
+        FLB_TRY(launch_mu(g, r.psis, r.mus, (float)p.A, (float)p.B, (float)p.K, st));
+        if (p.psi_scheme == FLB_FV)
+            FLB_TRY(launch_flux(g, r.q, r.psis, r.mus, r.u, r.J, (float)p.M, p.coupling, st));
+        pa.psi = r.psis;
+        pa.mu = r.mus;
+        pa.psi0 = r.E;
+        pa.out = psi_np1;
+        pa.stage = 2;
+        FLB_TRY(launch_psi_update(pa, r.q, st));
+    }
+    cudaEvent_t e3 = mark(h);
+    span(h, 0, e1, e2, 1);
+    span(h, 1, e0, e1, 1);
+    span(h, 1, e2, e3, (int)(h->launches - l2));
+    (void)l0;
+    r.cur ^= 1;
+    r.pcur ^= 1;
+    r.step += 1;
+    return FLB_OK;
+}
+
+int sample_rep(flb_handle *h, Rep &r, int mask)
+{
+    const Geom &g = r.g;
+    cudaEvent_t e0 = mark(h);
+    const int64_t l0 = h->launches;
+    struct Close {
+        flb_handle *h;
+        cudaEvent_t e0;
+        int64_t l0;
+        ~Close() { span(h, 2, e0, mark(h), (int)(h->launches - l0)); }
+    } close_{h, e0, l0};
+    if (mask & 1) {
+        DftArgs d;
+        d.in = r.psi[r.pcur];
+        d.off = g.pidx(0, 0, 0);
+        d.sy = g.px;
+        d.sz = (long long)g.px * g.py;
+        d.nx = g.nx;
+        d.ny = g.ny;
+        d.nz = g.nz;
+        d.Kx = r.Kx;
+        d.Ky = r.Ky;
+        d.Kz = r.Kz;
+        d.X1 = h->X1;
+        d.X2 = h->X2;
+        d.S = r.sq;
+        d.scale = 1.0 / (double)g.n;
+        const cudaError_t e = launch_dft_accumulate(d, h->st);
+        h->launches += 3;
+        if (e != cudaSuccess) return FLB_ECUDA;
+        r.sq_n += 1;
+    }
+    if ((mask & 2) && r.dim == 3) {
+        FLB_TRY(launch_heights(g, r.psi[r.pcur], h->heights, h->st));
+        for (int part = 0; part < 2; ++part) {
+            DftArgs d;
+            d.in = h->heights;
+            d.off = (long long)part * g.nx * g.ny;
+            d.sy = g.nx;
+            d.sz = 0;
+            d.nx = g.nx;
+            d.ny = g.ny;
+            d.nz = 1;
+            d.Kx = g.nx;
+            d.Ky = g.ny;
+            d.Kz = 1;
+            d.X1 = h->X1;
+            d.X2 = h->X2;
+            d.S = r.hsq;
+            d.scale = 0.5 / ((double)g.nx * g.ny);
+            const cudaError_t e = launch_dft_accumulate(d, h->st);
+            h->launches += 3;
+            if (e != cudaSuccess) return FLB_ECUDA;
+        }
+        r.h_n += 1;
+    }
+    return FLB_OK;
+}
+
+Rep *get_rep(flb_handle *h, int32_t rep)
+{
+    if (!h || rep < 0 || rep >= (int32_t)h->reps.size()) return nullptr;
+    return &h->reps[(size_t)rep];
+}
+
+}  // namespace
+
+// window gather (flb_obs.cu)
+namespace flb {
+cudaError_t launch_window(const Geom &g, int q, int storage, const void *f, const float *psi, int x0, int y0, int z0,
+                          int wx, int wy, int wz, float *out, cudaStream_t s);
+}
+
+extern "C" {
+
+void flb_params_default(flb_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = 3;
+    p->q = 19;
+    p->nx = p->ny = p->nz = 32;
+    p->rho0 = 1.0;
+    p->tau = 0.8;
+    p->gamma_bulk = NAN;
+    p->gamma_ghost = 0.0;
+    p->kT = 0.0;
+    p->A = 0.05;
+    p->B = 0.0;
+    p->K = 0.04;
+    p->M = 0.1;
+    p->psi_scheme = FLB_FV;
+    p->integrator = FLB_HEUN;
+    p->storage = FLB_F32_DEV;
+    p->coupling = FLB_COUPLE_FORCE | FLB_COUPLE_ADVECT;
+    p->seed = 1;
+    p->sq_kmax = 0;
+}
+
+static bool valid_set(const flb_params *p, int32_t nrep)
+{
+    if (!p || nrep <= 0) return false;
+    for (int32_t k = 0; k < nrep; ++k) {
+        if (!valid(p[k])) return false;
+        if (p[k].dim != p[0].dim || p[k].q != p[0].q || p[k].psi_scheme != p[0].psi_scheme ||
+            p[k].integrator != p[0].integrator || p[k].storage != p[0].storage)
+            return false;
+    }
+    return true;
+}
+
+size_t flb_workspace_bytes(const flb_params *p, int32_t nrep)
+{
+    if (!valid_set(p, nrep)) return 0;
+    flb_handle h;
+    h.reps.resize((size_t)nrep);
+    for (int32_t k = 0; k < nrep; ++k) init_rep_consts(h.reps[(size_t)k], p[k]);
+    return carve_all(h, nullptr);
+}
+
+int flb_init(const flb_params *p, int32_t nrep, void *dev_ws, size_t ws_bytes, void *cuda_stream, flb_handle **out)
+{
+    if (!out) return FLB_EINVAL;
+    *out = nullptr;
+    if (!valid_set(p, nrep) || !dev_ws || ((uintptr_t)dev_ws & 255)) return FLB_EINVAL;
+    flb_handle *h = new (std::nothrow) flb_handle();
+    if (!h) return FLB_EINVAL;
+    h->reps.resize((size_t)nrep);
+    for (int32_t k = 0; k < nrep; ++k) init_rep_consts(h->reps[(size_t)k], p[k]);
+    const size_t need = carve_all(*h, nullptr);
+    if (ws_bytes < need) {
+        delete h;
+        return FLB_ENOSPC;
+    }
+    h->ws = (char *)dev_ws;
+    h->ws_bytes = ws_bytes;
+    h->st = (cudaStream_t)cuda_stream;
+    carve_all(*h, (char *)dev_ws);
+    // zero the whole workspace, then every replica starts at rest
+    int rc = cuerr(cudaMemsetAsync(dev_ws, 0, need, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return FLB_OK;
+}
+
+int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *u, const double *psi)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r) return FLB_EINVAL;
+    const Geom &g = r->g;
+    const long long N = g.n;
+    std::vector<float> tmp((size_t)N);
+    for (long long s = 0; s < N; ++s) tmp[(size_t)s] = psi ? (float)psi[s] : 0.f;
+    int rc = upload_padded(h, g, r->psi[r->pcur], tmp.data());
+    for (int a = 0; a < r->dim && rc == FLB_OK; ++a) {
+        for (long long s = 0; s < N; ++s) tmp[(size_t)s] = u ? (float)u[a * N + s] : 0.f;
+        rc = upload_padded(h, g, r->u + (size_t)a * g.pn, tmp.data());
+    }
+    if (rc == FLB_OK && rho) {
+        for (long long s = 0; s < N; ++s) tmp[(size_t)s] = (float)rho[s];
+        rc = upload_padded(h, g, r->mu, tmp.data());  // mu is free scratch between steps
+    }
+    if (rc != FLB_OK) return rc;
+    const cudaError_t e = launch_init_eq(g, r->q, r->p.storage, rho ? r->mu : nullptr, r->u, (float)r->p.rho0,
+                                         r->f[r->cur], h->st);
+    ++h->launches;
+    if (e != cudaSuccess) return FLB_ECUDA;
+    return cuerr(cudaStreamSynchronize(h->st));
+}
+
+int flb_get_populations(flb_handle *h, int32_t rep, double *f)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !f) return FLB_EINVAL;
+    std::vector<float> dev;
+    const int rc = download_pops(h, *r, dev);
+    if (rc != FLB_OK) return rc;
+    const Geom &g = r->g;
+    const long long N = g.n;
+    for (int i = 0; i < r->q; ++i) {
+        const int *c = cvec(r->q, i);
+        const double wr = wgt(r->q, i) * r->p.rho0;
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const long long src = g.sidx(wrapi(x - c[0], g.nx), wrapi(y - c[1], g.ny),
+                                                 g.dim == 3 ? wrapi(z - c[2], g.nz) : 0);
+                    f[(size_t)i * N + g.sidx(x, y, z)] = wr + (double)dev[(size_t)i * N + src];
+                }
+    }
+    return FLB_OK;
+}
+
+int flb_set_populations(flb_handle *h, int32_t rep, const double *f)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !f) return FLB_EINVAL;
+    std::vector<float> dev;
+    phys_to_stored(*r, f, dev);
+    const int rc = upload_pops(h, *r, dev);
+    return rc == FLB_OK ? cuerr(cudaStreamSynchronize(h->st)) : rc;
+}
+
+int flb_get_psi_u(flb_handle *h, int32_t rep, double *psi, double *u)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r) return FLB_EINVAL;
+    const Geom &g = r->g;
+    std::vector<float> tmp;
+    if (psi) {
+        const int rc = download_interior(h, g, r->psi[r->pcur], tmp);
+        if (rc != FLB_OK) return rc;
+        for (long long s = 0; s < g.n; ++s) psi[s] = tmp[(size_t)s];
+    }
+    if (u)
+        for (int a = 0; a < r->dim; ++a) {
+            const int rc = download_interior(h, g, r->u + (size_t)a * g.pn, tmp);
+            if (rc != FLB_OK) return rc;
+            for (long long s = 0; s < g.n; ++s) u[a * g.n + s] = tmp[(size_t)s];
+        }
+    return FLB_OK;
+}
+
+int flb_get_window(flb_handle *h, int32_t rep, int32_t x0, int32_t y0, int32_t z0, int32_t wx, int32_t wy,
+                   int32_t wz, double *f, double *psi)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || wx <= 0 || wy <= 0 || wz <= 0) return FLB_EINVAL;
+    if (r->dim == 2 && wz != 1) return FLB_EINVAL;
+    const long long W = (long long)wx * wy * wz;
+    if (W > WIN_MAX) return FLB_ENOSPC;
+    const Geom &g = r->g;
+    const int xw = wrapi(((x0 % g.nx) + g.nx) % g.nx, g.nx), yw = ((y0 % g.ny) + g.ny) % g.ny,
+              zw = ((z0 % g.nz) + g.nz) % g.nz;
+    cudaError_t e = launch_window(g, r->q, r->p.storage, r->f[r->cur], r->psi[r->pcur], xw, yw, zw, wx, wy, wz,
+                                  h->win, h->st);
+    ++h->launches;
+    if (e != cudaSuccess) return FLB_ECUDA;
+    std::vector<float> buf((size_t)W * (r->q + 1));
+    int rc = cuerr(cudaMemcpyAsync(buf.data(), h->win, buf.size() * 4, cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    if (f)
+        for (int i = 0; i < r->q; ++i) {
+            const double wr = wgt(r->q, i) * r->p.rho0;
+            for (long long k = 0; k < W; ++k) f[i * W + k] = wr + (double)buf[(size_t)i * W + k];
+        }
+    if (psi)
+        for (long long k = 0; k < W; ++k) psi[k] = buf[(size_t)r->q * W + k];
+    return FLB_OK;
+}
+
+int flb_step(flb_handle *h, int64_t n)
+{
+    if (!h || n < 0) return FLB_EINVAL;
+    if (h->mode != FLB_MODE_PLAIN) return FLB_EUNSUPPORTED;
+    for (int64_t k = 0; k < n; ++k) {
+        for (Rep &r : h->reps) {
+            const int rc = step_rep(h, r);
+            if (rc != FLB_OK) return rc;
+            if (h->sample_every > 0 && h->sample_mask && r.step % h->sample_every == 0) {
+                const int rs = sample_rep(h, r, h->sample_mask);
+                if (rs != FLB_OK) return rs;
+            }
+        }
+    }
+    return FLB_OK;
+}
+
+int flb_get_step(flb_handle *h, int32_t rep, int64_t *step)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !step) return FLB_EINVAL;
+    *step = r->step;
+    return FLB_OK;
+}
+
+int flb_moments(flb_handle *h, int32_t rep, double *totals, double *u2)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r) return FLB_EINVAL;
+    const Geom &g = r->g;
+    const int nb = (int)std::min<long long>(RED_MAX_BLOCKS, (g.n + 255) / 256);
+    cudaError_t e = launch_totals(g, r->q, r->p.storage, r->f[r->cur], r->psi[r->pcur], r->u, h->red_partial, nb,
+                                  h->red_out, h->st);
+    h->launches += 2;
+    if (e != cudaSuccess) return FLB_ECUDA;
+    double out[NRED];
+    int rc = cuerr(cudaMemcpyAsync(out, h->red_out, sizeof(out), cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    if (totals) {
+        totals[0] = (double)g.n * r->p.rho0 + out[0];
+        for (int a = 0; a < r->dim; ++a) totals[1 + a] = out[1 + a];
+        totals[1 + r->dim] = out[4];
+    }
+    if (u2)
+        for (int a = 0; a < r->dim; ++a) u2[a] = out[5 + a] / (double)g.n;
+    return out[8] > 0 ? FLB_ENONFINITE : FLB_OK;
+}
+
+int flb_set_sampling(flb_handle *h, int32_t every_m, int32_t mask)
+{
+    if (!h || every_m < 0 || mask < 0 || mask > 3) return FLB_EINVAL;
+    h->sample_every = every_m;
+    h->sample_mask = mask;
+    return FLB_OK;
+}
+
+int flb_sample(flb_handle *h, int32_t mask)
+{
+    if (!h || mask < 0 || mask > 3) return FLB_EINVAL;
+    for (Rep &r : h->reps) {
+        const int rc = sample_rep(h, r, mask);
+        if (rc != FLB_OK) return rc;
+    }
+    return FLB_OK;
+}
+
+int64_t flb_structure_factor_size(flb_handle *h, int32_t rep, int32_t which)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r) return -1;
+    if (which == FLB_SQ_PSI) return (int64_t)r->Kx * r->Ky * r->Kz;
+    if (which == FLB_SQ_HEIGHT) return r->dim == 3 ? (int64_t)r->g.nx * r->g.ny : 0;
+    return -1;
+}
+
+int flb_structure_factor(flb_handle *h, int32_t rep, int32_t which, double *out, int64_t *nsamples)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !out || (which != FLB_SQ_PSI && which != FLB_SQ_HEIGHT)) return FLB_EINVAL;
+    if (which == FLB_SQ_HEIGHT && r->dim != 3) return FLB_EINVAL;
+    const int64_t cnt = flb_structure_factor_size(h, rep, which);
+    const double *src = which == FLB_SQ_PSI ? r->sq : r->hsq;
+    const int64_t ns = which == FLB_SQ_PSI ? r->sq_n : r->h_n;
+    int rc = cuerr(cudaMemcpyAsync(out, src, (size_t)cnt * 8, cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    for (int64_t k = 0; k < cnt; ++k) out[k] = ns > 0 ? out[k] / (double)ns : 0.0;
+    if (which == FLB_SQ_HEIGHT) out[0] = 0.0;  // the mean height carries no capillary mode
+    if (nsamples) *nsamples = ns;
+    return FLB_OK;
+}
+
+int flb_sq_reset(flb_handle *h, int32_t rep)
+{
+    if (!h) return FLB_EINVAL;
+    for (int32_t k = 0; k < (int32_t)h->reps.size(); ++k) {
+        if (rep >= 0 && k != rep) continue;
+        Rep &r = h->reps[(size_t)k];
+        int rc = cuerr(cudaMemsetAsync(r.sq, 0, (size_t)r.Kx * r.Ky * r.Kz * 8, h->st));
+        if (rc == FLB_OK && r.hsq) rc = cuerr(cudaMemsetAsync(r.hsq, 0, (size_t)r.g.nx * r.g.ny * 8, h->st));
+        if (rc != FLB_OK) return rc;
+        r.sq_n = r.h_n = 0;
+    }
+    return cuerr(cudaStreamSynchronize(h->st));
+}
+
+int flb_set_mode(flb_handle *h, int32_t mode)
+{
+    if (!h || (mode != FLB_MODE_PLAIN && mode != FLB_MODE_BATCHED)) return FLB_EINVAL;
+    h->mode = mode;
+    return FLB_OK;
+}
+
+size_t flb_state_bytes(flb_handle *h, int32_t rep)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r) return 0;
+    const size_t N = (size_t)r->g.n;
+    return 8 + (size_t)r->q * N * r->pop_elem + N * 4 + (size_t)r->dim * N * 4;
+}
+
+int flb_get_state(flb_handle *h, int32_t rep, void *host, size_t bytes)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !host) return FLB_EINVAL;
+    if (bytes < flb_state_bytes(h, rep)) return FLB_ENOSPC;
+    char *o = (char *)host;
+    std::memcpy(o, &r->step, 8);
+    o += 8;
+    const size_t pb = (size_t)r->q * r->g.n * r->pop_elem;
+    int rc = cuerr(cudaMemcpyAsync(o, r->f[r->cur], pb, cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    o += pb;
+    std::vector<float> tmp;
+    rc = download_interior(h, r->g, r->psi[r->pcur], tmp);
+    if (rc != FLB_OK) return rc;
+    std::memcpy(o, tmp.data(), tmp.size() * 4);
+    o += tmp.size() * 4;
+    for (int a = 0; a < r->dim; ++a) {
+        rc = download_interior(h, r->g, r->u + (size_t)a * r->g.pn, tmp);
+        if (rc != FLB_OK) return rc;
+        std::memcpy(o, tmp.data(), tmp.size() * 4);
+        o += tmp.size() * 4;
+    }
+    return FLB_OK;
+}
+
+int flb_set_state(flb_handle *h, int32_t rep, const void *host, size_t bytes)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !host) return FLB_EINVAL;
+    if (bytes < flb_state_bytes(h, rep)) return FLB_ENOSPC;
+    const char *o = (const char *)host;
+    std::memcpy(&r->step, o, 8);
+    o += 8;
+    const size_t pb = (size_t)r->q * r->g.n * r->pop_elem;
+    int rc = cuerr(cudaMemcpyAsync(r->f[r->cur], o, pb, cudaMemcpyHostToDevice, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    o += pb;
+    const size_t N = (size_t)r->g.n;
+    rc = upload_padded(h, r->g, r->psi[r->pcur], (const float *)o);
+    o += N * 4;
+    for (int a = 0; a < r->dim && rc == FLB_OK; ++a) {
+        rc = upload_padded(h, r->g, r->u + (size_t)a * r->g.pn, (const float *)o);
+        o += N * 4;
+    }
+    return rc;
+}
+
+int flb_synchronize(flb_handle *h)
+{
+    if (!h) return FLB_EINVAL;
+    return cuerr(cudaStreamSynchronize(h->st));
+}
+
+int64_t flb_launch_count(flb_handle *h) { return h ? h->launches : -1; }
+
+int flb_set_profiling(flb_handle *h, int32_t on)
+{
+    if (!h) return FLB_EINVAL;
+    const int rc = cuerr(cudaStreamSynchronize(h->st));
+    h->profiling = on != 0;
+    h->ev_used = 0;
+    for (auto &s : h->spans) s.clear();
+    for (auto &c : h->phase_launches) c = 0;
+    return rc;
+}
+
+int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts)
+{
+    if (!h || !ms) return FLB_EINVAL;
+    const int rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    for (int k = 0; k < 3; ++k) {
+        double t = 0.0;
+        for (auto &pr : h->spans[k]) {
+            float x = 0.f;
+            if (cudaEventElapsedTime(&x, pr.first, pr.second) != cudaSuccess) return FLB_ECUDA;
+            t += x;
+        }
+        ms[k] = t;
+        if (counts) counts[k] = h->phase_launches[k];
+    }
+    return FLB_OK;
+}
+
+const char *flb_strerror(int code)
+{
+    switch (code) {
+    case FLB_OK: return "ok";
+    case FLB_EINVAL: return "invalid argument";
+    case FLB_ENOSPC: return "workspace or buffer too small";
+    case FLB_ECUDA: return "CUDA runtime error";
+    case FLB_ENONFINITE: return "non-finite value in the fields";
+    case FLB_ETIMEOUT: return "device-side wait timed out";
+    case FLB_EUNSUPPORTED: return "unsupported in this build";
+    default: return "unknown error";
+    }
+}
+
+void flb_destroy(flb_handle *h) { delete h; }
+
+}  // extern "C"

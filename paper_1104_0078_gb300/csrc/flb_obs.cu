@@ -1,0 +1,269 @@
+// flb_obs.cu -- observables of Sec. VI of arXiv:1104.0078 reduced on the device:
+// conserved totals and velocity variance (FP64, deterministic two-pass
+// reduction), the static structure factor <|psi~(q)|^2> by a separable direct
+// DFT accumulated in FP64, and the capillary spectrum of the two psi = 0
+// surfaces of a slab (linear interpolation of the zero in every column).
+#include "flb_obs.cuh"
+
+namespace flb {
+
+constexpr int RED_BS = 256;
+
+template <typename T>
+__device__ __forceinline__ float ldv(const T *p, long long i);
+template <>
+__device__ __forceinline__ float ldv<float>(const float *p, long long i) { return p[i]; }
+template <>
+__device__ __forceinline__ float ldv<__half>(const __half *p, long long i) { return __half2float(p[i]); }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Pass 1: every block reduces a grid-stride share of the sites into NRED doubles:
+// {sum dev, sum j_x, sum j_y, sum j_z, sum psi, sum u_x^2, sum u_y^2, sum u_z^2, non-finite count}.
+template <typename T>
+__global__ void __launch_bounds__(RED_BS) totals_kernel(const Geom g, int q, const T *__restrict__ f,
+                                                        const float *__restrict__ psi, const float *__restrict__ u,
+                                                        double *__restrict__ partial)
+{
+    double acc[NRED];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) acc[k] = 0.0;
+    const long long N = g.n;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+        float m = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        int bad = 0;
+        float fi[19];
+        for (int i = 0; i < q; ++i) {
+            fi[i] = ldv(f, (long long)i * N + s);
+            bad |= !isfinite(fi[i]);
+        }
+        if (q == 19) {
+            m = fi[0];
+            for (int i = 1; i < 19; ++i) m += fi[i];
+            jx = (fi[1] - fi[2]) + (fi[7] - fi[8]) + (fi[9] - fi[10]) + (fi[11] - fi[12]) + (fi[13] - fi[14]);
+            jy = (fi[3] - fi[4]) + (fi[7] - fi[8]) - (fi[9] - fi[10]) + (fi[15] - fi[16]) + (fi[17] - fi[18]);
+            jz = (fi[5] - fi[6]) + (fi[11] - fi[12]) - (fi[13] - fi[14]) + (fi[15] - fi[16]) - (fi[17] - fi[18]);
+        } else {
+            m = fi[0];
+            for (int i = 1; i < 9; ++i) m += fi[i];
+            jx = (fi[1] - fi[2]) + (fi[5] - fi[6]) + (fi[7] - fi[8]);
+            jy = (fi[3] - fi[4]) + (fi[5] - fi[6]) - (fi[7] - fi[8]);
+        }
+        const long long pi = g.pidx(x, y, z);
+        const float ps = psi[pi];
+        const float ux = u[pi], uy = u[g.pn + pi], uz = g.dim == 3 ? u[2 * g.pn + pi] : 0.f;
+        bad |= !isfinite(ps) | !isfinite(ux) | !isfinite(uy) | !isfinite(uz);
+        acc[0] += m;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] += jz;
+        acc[4] += ps;
+        acc[5] += (double)ux * ux;
+        acc[6] += (double)uy * uy;
+        acc[7] += (double)uz * uz;
+        acc[8] += bad;
+    }
+    __shared__ double sh[RED_BS / 32][NRED];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        double t = 0.0;
+        for (int w = 0; w < RED_BS / 32; ++w) t += sh[w][threadIdx.x];
+        partial[(long long)blockIdx.x * NRED + threadIdx.x] = t;
+    }
+}
+
+// Pass 2: one block sums the per-block partials in a fixed order.
+__global__ void totals_final_kernel(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= NRED) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[(long long)b * NRED + k];
+    out[k] = t;
+}
+
+cudaError_t launch_totals(const Geom &g, int q, int storage, const void *f, const float *psi, const float *u,
+                          double *partial, int nblocks, double *out, cudaStream_t s)
+{
+    if (storage == FLB_F16_DEV)
+        totals_kernel<__half><<<nblocks, RED_BS, 0, s>>>(g, q, (const __half *)f, psi, u, partial);
+    else
+        totals_kernel<float><<<nblocks, RED_BS, 0, s>>>(g, q, (const float *)f, psi, u, partial);
+    totals_final_kernel<<<1, 32, 0, s>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Separable DFT.  Axis lists: index j of an axis of length n with window kmax
+// (K = 2 kmax + 1 < n) is k = j for j <= kmax and n - (K - j) otherwise; with
+// K = n every k is kept.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kval(int j, int n, int K) { return (K >= n || j <= K / 2) ? j : n - (K - j); }
+
+__device__ __forceinline__ float2 twiddle(int k, int x, int n)
+{
+    // e^{-2 pi i k x / n}, argument reduced exactly in integers first
+    const int m = (int)(((long long)k * x) % n);
+    float s, c;
+    sincospif(2.0f * (float)m / (float)n, &s, &c);
+    return make_float2(c, -s);
+}
+
+// X1[(z*ny + y)*Kx + jx] = sum_x in(x,y,z) e^{-i qx x}
+__global__ void dft_x_kernel(DftArgs a)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)a.Kx * a.ny * a.nz;
+    if (t >= tot) return;
+    const int jx = (int)(t % a.Kx);
+    const long long row = t / a.Kx;  // z*ny + y
+    const int y = (int)(row % a.ny), z = (int)(row / a.ny);
+    const int k = kval(jx, a.nx, a.Kx);
+    const float *src = a.in + a.off + (long long)y * a.sy + (long long)z * a.sz;
+    float re = 0.f, im = 0.f;
+    for (int x = 0; x < a.nx; ++x) {
+        const float v = src[x];
+        const float2 w = twiddle(k, x, a.nx);
+        re = fmaf(v, w.x, re);
+        im = fmaf(v, w.y, im);
+    }
+    a.X1[t] = make_float2(re, im);
+}
+
+// X2[(z*Ky + jy)*Kx + jx] = sum_y X1[(z*ny + y)*Kx + jx] e^{-i qy y}
+__global__ void dft_y_kernel(DftArgs a)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)a.Kx * a.Ky * a.nz;
+    if (t >= tot) return;
+    const int jx = (int)(t % a.Kx);
+    const int jy = (int)((t / a.Kx) % a.Ky);
+    const int z = (int)(t / ((long long)a.Kx * a.Ky));
+    const int k = kval(jy, a.ny, a.Ky);
+    float re = 0.f, im = 0.f;
+    for (int y = 0; y < a.ny; ++y) {
+        const float2 v = a.X1[((long long)z * a.ny + y) * a.Kx + jx];
+        const float2 w = twiddle(k, y, a.ny);
+        re += v.x * w.x - v.y * w.y;
+        im += v.x * w.y + v.y * w.x;
+    }
+    a.X2[t] = make_float2(re, im);
+}
+
+// S[(jz*Ky + jy)*Kx + jx] += scale |sum_z X2[(z*Ky + jy)*Kx + jx] e^{-i qz z}|^2  (FP64)
+__global__ void dft_z_acc_kernel(DftArgs a)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)a.Kx * a.Ky * a.Kz;
+    if (t >= tot) return;
+    const long long plane = (long long)a.Kx * a.Ky;
+    const long long xy = t % plane;
+    const int jz = (int)(t / plane);
+    const int k = kval(jz, a.nz, a.Kz);
+    double re = 0.0, im = 0.0;
+    for (int z = 0; z < a.nz; ++z) {
+        const float2 v = a.X2[(long long)z * plane + xy];
+        const float2 w = twiddle(k, z, a.nz);
+        re += (double)v.x * w.x - (double)v.y * w.y;
+        im += (double)v.x * w.y + (double)v.y * w.x;
+    }
+    a.S[t] += a.scale * (re * re + im * im);
+}
+
+cudaError_t launch_dft_accumulate(const DftArgs &a, cudaStream_t s)
+{
+    const int bs = 256;
+    long long n1 = (long long)a.Kx * a.ny * a.nz, n2 = (long long)a.Kx * a.Ky * a.nz, n3 = (long long)a.Kx * a.Ky * a.Kz;
+    dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, 0, s>>>(a);
+    dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, 0, s>>>(a);
+    dft_z_acc_kernel<<<(unsigned)((n3 + bs - 1) / bs), bs, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Heights of the two psi = 0 surfaces of a slab normal to z: in every column the
+// first sign change in z in [0, nz/2) and in [nz/2, nz) (the next node wrapping
+// periodically), located by linear interpolation; a half-column without a sign
+// change reports the centre of its half.
+__global__ void heights_kernel(const Geom g, const float *__restrict__ psi, float *__restrict__ h)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ncol = (long long)g.nx * g.ny;
+    if (c >= ncol) return;
+    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    const int half = g.nz / 2;
+    for (int part = 0; part < 2; ++part) {
+        const int lo = part == 0 ? 0 : half, hi = part == 0 ? half : g.nz;
+        float hv = 0.5f * (float)(lo + hi);
+        for (int z = lo; z < hi; ++z) {
+            const float v0 = psi[g.pidx(x, y, z)], v1 = psi[g.pidx(x, y, z + 1 == g.nz ? 0 : z + 1)];
+            if ((v0 < 0.f) != (v1 < 0.f)) {
+                hv = (float)z + v0 / (v0 - v1);
+                break;
+            }
+        }
+        h[part * ncol + c] = hv;
+    }
+}
+
+cudaError_t launch_heights(const Geom &g, const float *psi, float *h, cudaStream_t s)
+{
+    const long long ncol = (long long)g.nx * g.ny;
+    heights_kernel<<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(g, psi, h);
+    return cudaGetLastError();
+}
+
+}  // namespace flb
+
+namespace flb {
+
+__constant__ int8_t kWin19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                     {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                     {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                     {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+__constant__ int8_t kWin9[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                   {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+
+// Gather the physical (streamed) population deviations and psi of a periodic window.
+template <typename T>
+__global__ void window_kernel(const Geom g, int q, const T *__restrict__ f, const float *__restrict__ psi, int x0,
+                              int y0, int z0, int wx, int wy, int wz, float *__restrict__ out)
+{
+    const long long W = (long long)wx * wy * wz;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= W) return;
+    const int x = (x0 + (int)(k % wx)) % g.nx;
+    const int y = (y0 + (int)((k / wx) % wy)) % g.ny;
+    const int z = (z0 + (int)(k / ((long long)wx * wy))) % g.nz;
+    for (int i = 0; i < q; ++i) {
+        const int8_t *c = q == 19 ? kWin19[i] : kWin9[i];
+        const long long src = g.sidx(wrapi(x - c[0], g.nx), wrapi(y - c[1], g.ny), g.dim == 3 ? wrapi(z - c[2], g.nz) : 0);
+        out[(long long)i * W + k] = ldv(f, (long long)i * g.n + src);
+    }
+    out[(long long)q * W + k] = psi[g.pidx(x, y, z)];
+}
+
+cudaError_t launch_window(const Geom &g, int q, int storage, const void *f, const float *psi, int x0, int y0, int z0,
+                          int wx, int wy, int wz, float *out, cudaStream_t s)
+{
+    const long long W = (long long)wx * wy * wz;
+    const unsigned grid = (unsigned)((W + 255) / 256);
+    if (storage == FLB_F16_DEV)
+        window_kernel<__half><<<grid, 256, 0, s>>>(g, q, (const __half *)f, psi, x0, y0, z0, wx, wy, wz, out);
+    else
+        window_kernel<float><<<grid, 256, 0, s>>>(g, q, (const float *)f, psi, x0, y0, z0, wx, wy, wz, out);
+    return cudaGetLastError();
+}
+
+}  // namespace flb

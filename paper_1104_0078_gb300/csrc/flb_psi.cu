@@ -1,0 +1,249 @@
+// flb_psi.cu -- stochastic method-of-lines step of the order parameter psi
+// (Sec. V of arXiv:1104.0078): chemical potential, noise increment, node
+// fluxes and the Runge-Kutta stage update, finite-difference and finite-volume.
+//
+//   mu  = A psi + B psi^3 - K lap_SO psi                  (Sec. II.A, App. A)
+//   FD: dpsi/dt = M lap_SO mu - div_CD(u psi) + eta,     (Sec. V.A)
+//       eta(r) = sum_l [zeta_l(r - c_l) - zeta_l(r)], zeta_l ~ N(0, 2 kT M a_l)
+//       on the 13 (2D: 4) half-links of the SO stencil, a_l its coefficients --
+//       real-space noise with the covariance -2 kT M L_SO(q) of Eq. (etafdt).
+//   FV: dpsi/dt = (2/c_s^2) sum_i w_i c_i . (J(r) + J(r + c_i))/2,       (Sec. V.B)
+//       J = M grad mu - u psi + xi, grad mu = (1/c_s^2) sum_i w_i c_i mu(r + c_i),
+//       xi ~ N(0, 2 kT M) per node and component (Eqs. fvdiff - fvgrad).
+// The noise is drawn once per step (Philox stream 1) and held fixed over the
+// Runge-Kutta stages (Sec. V, wilkie2004).
+#include "flb_internal.cuh"
+
+namespace flb {
+
+// SO Laplacian of a padded field at (x,y,z); needs the field within 1 cell.
+__device__ __forceinline__ float lap_so(const float *f, const Geom &g, int x, int y, int z)
+{
+    if (g.dim == 3) {
+        float n1 = 0.f, n2 = 0.f, n3 = 0.f;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int cls = (dx != 0) + (dy != 0) + (dz != 0);
+                    const float v = f[g.pidx(x + dx, y + dy, z + dz)];
+                    if (cls == 1) n1 += v;
+                    else if (cls == 2) n2 += v;
+                    else if (cls == 3) n3 += v;
+                }
+        return (6.f * n1 + 3.f * n2 + n3 - 80.f * f[g.pidx(x, y, z)]) * (1.0f / 22.0f);
+    }
+    const float n1 = f[g.pidx(x + 1, y, 0)] + f[g.pidx(x - 1, y, 0)] + f[g.pidx(x, y + 1, 0)] + f[g.pidx(x, y - 1, 0)];
+    const float n2 = f[g.pidx(x + 1, y + 1, 0)] + f[g.pidx(x - 1, y - 1, 0)] + f[g.pidx(x + 1, y - 1, 0)] +
+                     f[g.pidx(x - 1, y + 1, 0)];
+    return (2.f * n1 + n2 - 12.f * f[g.pidx(x, y, 0)]) * 0.25f;
+}
+
+// velocity sets of the FV scheme (no rest vector)
+__constant__ int8_t kC19[18][3] = {{1, 0, 0},  {-1, 0, 0},  {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                   {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1},
+                                   {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+__constant__ int8_t kC9[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+
+// FD half-links: x, y, z, (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1),
+// (1,1,1), (1,1,-1), (1,-1,1), (1,-1,-1); 2D: x, y, (1,1), (1,-1).
+__constant__ int8_t kL13[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
+                                   {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                   {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+__constant__ int8_t kL4[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+
+// ---------------------------------------------------------------------------
+__global__ void mu_kernel(const Geom g, const float *__restrict__ psi, float *__restrict__ mu, float A, float B,
+                          float K)
+{
+    const int ex = g.nx + 4, ey = g.ny + 4, ez = g.dim == 3 ? g.nz + 4 : 1;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)ex * ey * ez) return;
+    const int x = (int)(i % ex) - 2;
+    const int y = (int)((i / ex) % ey) - 2;
+    const int z = g.dim == 3 ? (int)(i / ((long long)ex * ey)) - 2 : 0;
+    const float p = psi[g.pidx(x, y, z)];
+    mu[g.pidx(x, y, z)] = A * p + B * p * p * p - K * lap_so(psi, g, x, y, z);
+}
+
+__global__ void noise_kernel(const NoiseArgs a)
+{
+    const Geom &g = a.g;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= g.n) return;
+    const int x = (int)(site % g.nx);
+    const int y = (int)((site / g.nx) % g.ny);
+    const int z = (int)(site / ((long long)g.nx * g.ny));
+    float eta = 0.f;
+    if (a.scheme == FLB_FD) {
+        const int nl = g.dim == 3 ? 13 : 4;
+        float own[16];
+        for (int b = 0; b < (nl + 3) / 4; ++b) normals4(a.seed, a.step, (uint32_t)site, 1u, (uint32_t)b, own + 4 * b);
+        for (int l = 0; l < nl; ++l) {
+            int cx, cy, cz = 0;
+            if (g.dim == 3) { cx = kL13[l][0]; cy = kL13[l][1]; cz = kL13[l][2]; }
+            else { cx = kL4[l][0]; cy = kL4[l][1]; }
+            const int cls = (cx != 0) + (cy != 0) + (cz != 0);
+            const float al = g.dim == 3 ? (cls == 1 ? 6.f / 22.f : cls == 2 ? 3.f / 22.f : 1.f / 22.f)
+                                        : (cls == 1 ? 0.5f : 0.25f);
+            const float sd = sqrtf(2.f * a.kT * a.M * al);
+            const long long nb = g.sidx(wrapi(x - cx, g.nx), wrapi(y - cy, g.ny), g.dim == 3 ? wrapi(z - cz, g.nz) : 0);
+            float gn[4];
+            normals4(a.seed, a.step, (uint32_t)nb, 1u, (uint32_t)(l >> 2), gn);
+            eta += sd * (gn[l & 3] - own[l]);
+        }
+    } else {
+        const float sd = sqrtf(2.f * a.kT * a.M);
+        float own[4];
+        normals4(a.seed, a.step, (uint32_t)site, 1u, 0u, own);
+        const int nq = g.dim == 3 ? 18 : 8;
+        float acc = 0.f;
+        for (int i = 0; i < nq; ++i) {
+            int cx, cy, cz = 0;
+            float w;
+            if (g.dim == 3) {
+                cx = kC19[i][0]; cy = kC19[i][1]; cz = kC19[i][2];
+                w = (abs(cx) + abs(cy) + abs(cz)) == 1 ? 1.f / 18.f : 1.f / 36.f;
+            } else {
+                cx = kC9[i][0]; cy = kC9[i][1];
+                w = (abs(cx) + abs(cy)) == 1 ? 1.f / 9.f : 1.f / 36.f;
+            }
+            const long long nb = g.sidx(wrapi(x + cx, g.nx), wrapi(y + cy, g.ny), g.dim == 3 ? wrapi(z + cz, g.nz) : 0);
+            float gn[4];
+            normals4(a.seed, a.step, (uint32_t)nb, 1u, 0u, gn);
+            float link = cx * (own[0] + gn[0]) + cy * (own[1] + gn[1]);
+            if (g.dim == 3) link += cz * (own[2] + gn[2]);
+            acc += w * link;
+        }
+        eta = 3.f * sd * acc;  // (2/c_s^2) * (1/2) * sum_i w_i c_i.(xi(r) + xi(r+c_i))
+    }
+    a.eta[site] = eta;
+}
+
+// FV deterministic node flux J = M grad_FV mu - u psi on the interior and one ghost layer.
+__global__ void flux_kernel(const Geom g, const float *__restrict__ psi, const float *__restrict__ mu,
+                            const float *__restrict__ u, float *__restrict__ J, float M, int advect)
+{
+    const int ex = g.nx + 2, ey = g.ny + 2, ez = g.dim == 3 ? g.nz + 2 : 1;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)ex * ey * ez) return;
+    const int x = (int)(i % ex) - 1;
+    const int y = (int)((i / ex) % ey) - 1;
+    const int z = g.dim == 3 ? (int)(i / ((long long)ex * ey)) - 1 : 0;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    const int nq = g.dim == 3 ? 18 : 8;
+    for (int k = 0; k < nq; ++k) {
+        int cx, cy, cz = 0;
+        float w;
+        if (g.dim == 3) {
+            cx = kC19[k][0]; cy = kC19[k][1]; cz = kC19[k][2];
+            w = (abs(cx) + abs(cy) + abs(cz)) == 1 ? 1.f / 18.f : 1.f / 36.f;
+        } else {
+            cx = kC9[k][0]; cy = kC9[k][1];
+            w = (abs(cx) + abs(cy)) == 1 ? 1.f / 9.f : 1.f / 36.f;
+        }
+        const float m = w * mu[g.pidx(x + cx, y + cy, z + cz)];
+        gx += cx * m;
+        gy += cy * m;
+        gz += cz * m;
+    }
+    const long long pi = g.pidx(x, y, z);
+    const float ps = psi[pi];
+    float jx = 3.f * M * gx, jy = 3.f * M * gy, jz = 3.f * M * gz;
+    if (advect) {
+        jx -= u[pi] * ps;
+        jy -= u[g.pn + pi] * ps;
+        if (g.dim == 3) jz -= u[2 * g.pn + pi] * ps;
+    }
+    J[pi] = jx;
+    J[g.pn + pi] = jy;
+    if (g.dim == 3) J[2 * g.pn + pi] = jz;
+}
+
+__global__ void psi_update_kernel(const PsiArgs a)
+{
+    const Geom &g = a.g;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= g.n) return;
+    const int x = (int)(site % g.nx);
+    const int y = (int)((site / g.nx) % g.ny);
+    const int z = (int)(site / ((long long)g.nx * g.ny));
+    const long long pi = g.pidx(x, y, z);
+    float D;
+    if (a.scheme == FLB_FD) {
+        D = a.M * lap_so(a.mu, g, x, y, z);
+        if (a.coupling & FLB_COUPLE_ADVECT) {
+            const float *ps = a.psi;
+            float adv = a.u[g.pidx(x + 1, y, z)] * ps[g.pidx(x + 1, y, z)] - a.u[g.pidx(x - 1, y, z)] * ps[g.pidx(x - 1, y, z)];
+            adv += a.u[g.pn + g.pidx(x, y + 1, z)] * ps[g.pidx(x, y + 1, z)] -
+                   a.u[g.pn + g.pidx(x, y - 1, z)] * ps[g.pidx(x, y - 1, z)];
+            if (g.dim == 3)
+                adv += a.u[2 * g.pn + g.pidx(x, y, z + 1)] * ps[g.pidx(x, y, z + 1)] -
+                       a.u[2 * g.pn + g.pidx(x, y, z - 1)] * ps[g.pidx(x, y, z - 1)];
+            D -= 0.5f * adv;
+        }
+    } else {
+        const float *J = a.J;
+        const float J0x = J[pi], J0y = J[g.pn + pi], J0z = g.dim == 3 ? J[2 * g.pn + pi] : 0.f;
+        const int nq = g.dim == 3 ? 18 : 8;
+        float acc = 0.f;
+        for (int k = 0; k < nq; ++k) {
+            int cx, cy, cz = 0;
+            float w;
+            if (g.dim == 3) {
+                cx = kC19[k][0]; cy = kC19[k][1]; cz = kC19[k][2];
+                w = (abs(cx) + abs(cy) + abs(cz)) == 1 ? 1.f / 18.f : 1.f / 36.f;
+            } else {
+                cx = kC9[k][0]; cy = kC9[k][1];
+                w = (abs(cx) + abs(cy)) == 1 ? 1.f / 9.f : 1.f / 36.f;
+            }
+            const long long pn = g.pidx(x + cx, y + cy, z + cz);
+            float link = cx * (J0x + J[pn]) + cy * (J0y + J[g.pn + pn]);
+            if (g.dim == 3) link += cz * (J0z + J[2 * g.pn + pn]);
+            acc += w * link;
+        }
+        D = 3.f * acc;  // (2/c_s^2) * (1/2) sum_i w_i c_i.(J(r) + J(r + c_i))
+    }
+    const float eta = a.eta ? a.eta[site] : 0.f;
+    float out;
+    if (a.stage == 1) {
+        const float p = a.psi[pi];
+        out = p + D + eta;
+        if (a.integrator == FLB_HEUN) a.acc[site] = p + 0.5f * D + eta;
+    } else {
+        out = a.psi0[site] + 0.5f * D;
+    }
+    store_padded(a.out, g, x, y, z, out, 3);
+}
+
+static unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t s)
+{
+    const long long ext = (long long)(g.nx + 4) * (g.ny + 4) * (g.dim == 3 ? g.nz + 4 : 1);
+    mu_kernel<<<blocks_for(ext, 256), 256, 0, s>>>(g, psi, mu, A, B, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s)
+{
+    noise_kernel<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux(const Geom &g, int q, const float *psi, const float *mu, const float *u, float *J, float M,
+                        int coupling, cudaStream_t s)
+{
+    (void)q;
+    const long long ext = (long long)(g.nx + 2) * (g.ny + 2) * (g.dim == 3 ? g.nz + 2 : 1);
+    flux_kernel<<<blocks_for(ext, 256), 256, 0, s>>>(g, psi, mu, u, J, M, (coupling & FLB_COUPLE_ADVECT) ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi_update(const PsiArgs &a, int q, cudaStream_t s)
+{
+    (void)q;
+    psi_update_kernel<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace flb

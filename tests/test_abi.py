@@ -1,0 +1,105 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/flb.h declares, the ctypes mirror of flb_params has the C layout, and
+the host-only entry points validate their arguments (no device calls here)."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_1104_0078_gb300 as F
+from paper_1104_0078_gb300 import build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h")]
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(flb_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return F.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", F.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = sorted(n for n in names if n not in exported)
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_params_layout_matches_c():
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "flb.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(flb_params), offsetof(flb_params, rho0),
+             offsetof(flb_params, kT), offsetof(flb_params, psi_scheme), offsetof(flb_params, seed),
+             offsetof(flb_params, sq_kmax));
+      return 0; }
+    """
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
+    P = F.FlbParams
+    assert vals == [ctypes.sizeof(P), P.rho0.offset, P.kT.offset, P.psi_scheme.offset, P.seed.offset,
+                    P.sq_kmax.offset]
+
+
+def test_defaults_and_workspace_sizing(lib):
+    p = F.flb_params_default()
+    assert (p.dim, p.q, p.nx, p.psi_scheme, p.integrator, p.coupling) == (3, 19, 32, F.FLB_FV, F.FLB_HEUN, 3)
+    assert math.isnan(p.gamma_bulk)
+    n32 = F.flb_workspace_bytes(p)
+    N = 32 ** 3
+    assert n32 > 2 * 19 * N * 4           # two population buffers at least
+    p16 = F.flb_params_default(storage=F.FLB_F16_DEV)
+    assert F.flb_workspace_bytes(p16) < n32
+    # replicas of different sizes share one workspace
+    ps = [F.flb_params_default(nx=n, ny=n, nz=n) for n in (16, 24)]
+    assert F.flb_workspace_bytes(ps) > F.flb_workspace_bytes(ps[:1])
+
+
+@pytest.mark.parametrize("field,value", [("nx", 3), ("q", 15), ("tau", 0.0), ("gamma_ghost", 1.0), ("kT", -1.0),
+                                         ("psi_scheme", 2), ("integrator", 3), ("storage", 2), ("coupling", 4),
+                                         ("M", -0.1), ("sq_kmax", -1)])
+def test_invalid_parameters_rejected(lib, field, value):
+    p = F.flb_params_default(**{field: value})
+    assert F.flb_workspace_bytes(p) == 0
+
+
+def test_mixed_replica_structure_rejected(lib):
+    a = F.flb_params_default()
+    b = F.flb_params_default(psi_scheme=F.FLB_FD)
+    assert F.flb_workspace_bytes([a, b]) == 0
+
+
+def test_init_argument_checks_without_device(lib):
+    p = F.flb_params_default()
+    h = ctypes.c_void_p()
+    arr = (F.FlbParams * 1)(p)
+    assert lib.flb_init(arr, 1, None, 1 << 30, None, ctypes.byref(h)) == F.FLB_EINVAL
+    assert lib.flb_init(arr, 1, ctypes.c_void_p(0x1001), 1 << 30, None, ctypes.byref(h)) == F.FLB_EINVAL
+    assert lib.flb_init(arr, 1, ctypes.c_void_p(0x100000), 16, None, ctypes.byref(h)) == F.FLB_ENOSPC
+    assert lib.flb_step(None, 1) == F.FLB_EINVAL
+    assert F.flb_strerror(F.FLB_ENONFINITE).startswith("non-finite")

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element, from the
+same seeded binary32-exact inputs, through the C ABI (flb_* via the binding).
+
+Tolerance: per-step field error <= 1e-5 (max |gpu - oracle| over the RMS
+deviation of the oracle field) -- the FP32 path rounds every quantity at
+~6e-8 relative and the dynamics is contractive, so after tens to a hundred
+steps the accumulated error stays two orders below that bound."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1104_0078_gb300 as F
+from paper_1104_0078_gb300 import inputs as I
+
+from gpu_helpers import field_error, flb_params, oracle_params, weights_column
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _run_pair(d, nsteps, amp_f=2e-3, amp_psi=0.05, seed=7):
+    """Advance the same random start nsteps on the GPU and in the oracle."""
+    fp = flb_params(d)
+    op = oracle_params(d)
+    N = op.n
+    w = weights_column(op.q)
+    f0 = w * op.rho0 + I.random_deviations(op.q, N, amp_f, seed)
+    psi0 = I.random_field(N, amp_psi, seed + 1)
+    s = F.Solver(fp)
+    s.set_fields(psi=psi0)
+    s.set_populations(f0)
+    s.step(nsteps)
+    s.synchronize()
+    fg = s.get_populations()
+    pg, ug = s.get_psi_u()
+    st = O.State(op, f0.copy(), psi0.copy(), np.zeros((3, N)), 0)
+    st.advance(nsteps)
+    return s, (fg, pg, ug), st, w * op.rho0
+
+
+CASES = []
+for dim, q, shape in ((2, 9, (13, 10, 1)), (3, 19, (11, 7, 9)), (3, 19, (37, 23, 19))):
+    for scheme in (0, 1):
+        for integ in (1, 2):
+            if shape == (37, 23, 19) and (scheme, integ) != (1, 2):
+                continue
+            CASES.append((dim, q, shape, scheme, integ))
+
+
+@pytest.mark.parametrize("dim,q,shape,scheme,integ", CASES)
+def test_coupled_step_matches_oracle(dim, q, shape, scheme, integ):
+    d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1,
+             scheme=scheme, integrator=integ, coupling=3, seed=3)
+    s, (fg, pg, ug), st, feq = _run_pair(d, 25)
+    assert field_error(fg, st.f, feq) < TOL
+    assert field_error(pg, st.psi) < TOL
+    assert field_error(ug[:dim], st.u[:dim]) < TOL
+    assert s.get_step() == 25
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_relaxation_variants_match_oracle(dim, q):
+    # bulk rate different from shear, partially relaxed ghosts, only advection coupling
+    shape = (9, 8, 6)
+    for extra in (dict(gamma_bulk=-0.4, gamma_ghost=0.35), dict(coupling=2, gamma_ghost=-0.2),
+                  dict(coupling=0, kT=0.0), dict(M=0.0, coupling=1)):
+        d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.6, kT=2e-4, A=-0.02, B=0.1, K=0.03,
+                 M=0.2, scheme=1, integrator=2, coupling=3, seed=11)
+        d.update(extra)
+        s, (fg, pg, ug), st, feq = _run_pair(d, 15)
+        assert field_error(fg, st.f, feq) < TOL, extra
+        assert field_error(pg, st.psi) < TOL, extra
+
+
+def test_bulk_3d_100_steps_from_rest():
+    # D3Q19 64^3, tau 0.8, kT 1e-5, A 0.05, B 0, K 0.04, M 0.1, FV, Heun, from rest:
+    # field error after 100 steps <= 1e-5 for populations, psi and u
+    d = dict(I.WORKLOADS["bulk_3d"], integrator=2)
+    fp = flb_params(d)
+    op = oracle_params(d)
+    s = F.Solver(fp)
+    s.step(100)
+    s.synchronize()
+    fg = s.get_populations()
+    pg, ug = s.get_psi_u()
+    st = O.State.rest(op)
+    st.advance(100)
+    feq = weights_column(19) * op.rho0
+    assert field_error(fg, st.f, feq) < TOL
+    assert field_error(pg, st.psi) < TOL
+    assert field_error(ug, st.u) < TOL
+
+
+def test_conserved_totals_drift():
+    # mass, momentum (B = 0) and psi drift over 400 steps on the GPU, reduced in FP64
+    d = dict(I.WORKLOADS["bulk_3d"], nx=32, ny=32, nz=32, kT=1e-4)
+    s = F.Solver(flb_params(d))
+    N = 32 ** 3
+    s.set_fields(psi=I.random_field(N, 0.1, 5))
+    t0, _, rc0 = s.moments()
+    s.step(400)
+    t1, u2, rc1 = s.moments()
+    assert rc0 == rc1 == F.FLB_OK
+    f = s.get_populations()
+    c, _ = O.lattice(3, 19)
+    jabs = np.abs(np.einsum("ia,in->an", c.astype(float), f)).sum()
+    psi, _ = s.get_psi_u()
+    assert abs(t1[0] - t0[0]) / (N * 1.0) < 1e-6
+    assert np.abs(t1[1:4] - t0[1:4]).max() / jabs < 1e-6
+    assert abs(t1[4] - t0[4]) / np.abs(psi).sum() < 1e-6
+
+
+def test_structure_factor_matches_oracle():
+    # same seed: accumulated S(q) on the GPU (separable DFT, FP64 sums) against the
+    # oracle's FFT of its own trajectory, every 5 steps over 100 steps
+    d = dict(dim=3, q=19, nx=16, ny=12, nz=10, tau=0.8, kT=1e-4, A=0.1, B=0.0, K=0.04, M=0.2, scheme=1,
+             integrator=2, seed=2)
+    s = F.Solver(flb_params(d))
+    s.set_sampling(5, 1)
+    s.step(100)
+    S_gpu, ns = s.structure_factor()
+    op = oracle_params(d)
+    st = O.State.rest(op)
+    acc = np.zeros(op.shape)
+    for _ in range(20):
+        st.advance(5)
+        acc += O.structure_factor(op, st.psi)
+    acc /= 20
+    assert ns == 20
+    S_gpu = S_gpu.reshape(op.shape)
+    big = acc > 1e-3 * acc.max()
+    assert np.max(np.abs(S_gpu[big] - acc[big]) / acc[big]) < 1e-4
+
+
+def test_structure_factor_window():
+    # sq_kmax keeps |k_a| <= kmax on every axis, in FFT order; sampled at step 0
+    # from a seeded field, against the oracle's FFT of the same field
+    d = dict(dim=3, q=19, nx=16, ny=16, nz=12, tau=0.8, kT=1e-4, A=0.1, B=0.0, K=0.04, M=0.2, scheme=0,
+             integrator=1, seed=4, sq_kmax=3)
+    s = F.Solver(flb_params(d))
+    psi0 = I.random_field(16 * 16 * 12, 0.2, 12)
+    s.set_fields(psi=psi0)
+    s.sample(1)
+    s.sample(1)
+    S_gpu, ns = s.structure_factor()
+    op = oracle_params(d)
+    full = O.structure_factor(op, psi0)
+    ks = lambda n: list(range(0, 4)) + list(range(n - 3, n))
+    sel = full[np.ix_(ks(12), ks(16), ks(16))]
+    assert S_gpu.size == 7 * 7 * 7 and ns == 2
+    assert np.allclose(S_gpu.reshape(7, 7, 7), sel, rtol=1e-4, atol=1e-6 * sel.max())
+    s.sq_reset()
+    S0, n0 = s.structure_factor()
+    assert n0 == 0 and not S0.any()
+
+
+def test_interface_heights_match_oracle():
+    # slab with two tanh interfaces, a few noisy steps, heights spectrum GPU vs oracle
+    d = dict(dim=3, q=19, nx=16, ny=12, nz=32, tau=0.8, kT=2e-5, A=-0.0625, B=0.0625, K=0.04, M=0.1, scheme=1,
+             integrator=2, seed=9)
+    op = oracle_params(d)
+    psi0 = I.slab_profile(16, 12, 32, d["A"], d["B"], d["K"], 8.0, 24.0)
+    s = F.Solver(flb_params(d))
+    s.set_fields(psi=psi0)
+    s.step(20)
+    s.sample(2)
+    H_gpu, ns = s.structure_factor(which=F.FLB_SQ_HEIGHT)
+    st = O.State.rest(op, psi=psi0)
+    st.advance(20)
+    h1, h2 = O.interface_heights(op, st.psi)
+    assert not np.isnan(h1).any() and not np.isnan(h2).any()
+    H = 0.5 * (O.height_spectrum(h1) + O.height_spectrum(h2))
+    H[0, 0] = 0.0
+    assert ns == 1
+    H_gpu = H_gpu.reshape(12, 16)
+    # heights located from FP32 psi carry an absolute error dh <~ 2e-5 lattice units
+    # (psi error <~ 1e-5 over an interface slope >~ 0.5); |h~|^2 then moves by at
+    # most 2 |h~| dh + dh^2 per mode
+    dh = 2e-5
+    assert np.all(np.abs(H_gpu - H) <= 2 * np.sqrt(H) * dh + dh * dh)
+    assert H.max() > 1e-4
+
+
+def test_checkpoint_resume_bitwise():
+    d = dict(dim=3, q=19, nx=12, ny=10, nz=8, tau=0.8, kT=1e-4, A=0.05, B=0.2, K=0.04, M=0.1, scheme=1,
+             integrator=2, seed=5)
+    a = F.Solver(flb_params(d))
+    a.set_fields(psi=I.random_field(960, 0.1, 1))
+    a.step(50)
+    blob = a.get_state()
+    a.step(50)
+    fa = a.get_populations()
+    pa, ua = a.get_psi_u()
+    b = F.Solver(flb_params(d))
+    b.set_state(blob)
+    assert b.get_step() == 50
+    b.step(50)
+    fb = b.get_populations()
+    pb, ub = b.get_psi_u()
+    assert np.array_equal(fa, fb) and np.array_equal(pa, pb) and np.array_equal(ua, ub)
+
+
+def test_determinism_two_runs():
+    d = dict(dim=2, q=9, nx=20, ny=16, tau=1.0, kT=1e-4, A=0.05, B=0.1, K=0.04, M=0.1, scheme=0, integrator=2,
+             seed=8)
+    out = []
+    for _ in range(2):
+        s = F.Solver(flb_params(d))
+        s.step(30)
+        out.append((s.get_populations(), s.get_psi_u()[0]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_minimum_box_and_errors():
+    # the smallest admitted box (4^3) still matches; invalid calls return codes
+    d = dict(dim=3, q=19, nx=4, ny=4, nz=4, tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1, scheme=0,
+             integrator=2, seed=3)
+    s, (fg, pg, ug), st, feq = _run_pair(d, 10)
+    assert field_error(fg, st.f, feq) < TOL and field_error(pg, st.psi) < TOL
+    lib = F.load_library()
+    assert lib.flb_step(s.h, -1) == F.FLB_EINVAL
+    assert lib.flb_get_window(s.h, 0, 0, 0, 0, 64, 64, 64, None, None) == F.FLB_ENOSPC
+    assert lib.flb_set_mode(s.h, 7) == F.FLB_EINVAL
+
+
+def test_nonfinite_is_reported():
+    d = dict(dim=2, q=9, nx=8, ny=8, tau=1.0, kT=0.0, A=0.05, B=0.0, K=0.04, M=0.1, scheme=0, integrator=1)
+    s = F.Solver(flb_params(d))
+    psi = np.zeros(64)
+    psi[5] = np.nan
+    s.set_fields(psi=psi)
+    _, _, rc = s.moments()
+    assert rc == F.FLB_ENONFINITE
