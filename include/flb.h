@@ -201,6 +201,35 @@ int64_t flb_launch_count(flb_handle *h);
 int flb_set_profiling(flb_handle *h, int32_t on);
 int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts);
 
+/*
+ * Structure factor of one device field without any device allocation.
+ * No counterpart in the paper: this serves callers that cannot obtain device
+ * memory where they want a spectrum (a memory pool that forbids cudaMalloc, a
+ * plug-in given only pointers and a stream, a loop that must not allocate).
+ *   psi_dev : device pointer, FP32, nz*ny*nx values, x fastest (caller-owned).
+ *   kmax    : wavevector window per axis as flb_params.sq_kmax.
+ *   S_dev   : device pointer, FP64, Kz*Ky*Kx values (the layout of
+ *             flb_structure_factor), WRITTEN (not accumulated) with
+ *             |psi~(q)|^2 = |sum psi e^{-iq.r}|^2 / N.
+ *   cuda_stream : cudaStream_t (NULL: legacy default stream); asynchronous.
+ * Scratch: the two DFT intermediates use a fixed array in device memory that the
+ * library declares at file scope (2 x FLB_NOALLOC_MAX_VALUES complex FP32 values,
+ * 8 MiB), held by every GPU that loads the library until the process exits.
+ * Limit: Kx*ny*nz and Kx*Ky*nz must each be <= FLB_NOALLOC_MAX_VALUES, else the
+ * call returns FLB_ENOSPC without launching anything (e.g. 64^3 whole grid fits;
+ * 128^3 needs kmax <= 15).  Other errors: EINVAL (null pointer, size < 1, kmax < 0,
+ * N >= 2^31), ECUDA.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  Its first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls on a device share the array,
+ * which keeps the last call's contents; calls that overlap on the GPU (on
+ * different streams, or from several threads) race on it and must be ordered by
+ * the caller.
+ */
+#define FLB_NOALLOC_MAX_VALUES (1 << 19)
+int flb_structure_factor_noalloc(const float *psi_dev, int32_t nx, int32_t ny, int32_t nz, int32_t kmax,
+                                 double *S_dev, void *cuda_stream);
+
 const char *flb_strerror(int code);
 
 /* Release the handle (not the caller's workspace or stream). */

@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
         "flb_launch_count": (c_i64, [H]),
         "flb_set_profiling": (c_int, [H, ctypes.c_int32]),
         "flb_kernel_times": (c_int, [H, dp, P(c_i64)]),
+        "flb_structure_factor_noalloc": (c_int, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32, vp, vp]),
         "flb_strerror": (ctypes.c_char_p, [c_int]),
         "flb_destroy": (None, [H]),
     }
