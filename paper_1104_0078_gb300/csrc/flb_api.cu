@@ -79,6 +79,7 @@ bool valid(const flb_params &p)
     const long long nz = p.dim == 3 ? p.nz : 1;
     if (p.nx < 4 || p.ny < 4 || (p.dim == 3 && p.nz < 4)) return false;
     if ((long long)p.nx * p.ny * nz >= (1LL << 31)) return false;
+    if ((long long)(p.nx + 2 * GX + 3) * (p.ny + 2 * GY) * (nz + (p.dim == 3 ? 2 * GZ3 : 0)) >= (1LL << 31)) return false;
     if (!(p.rho0 > 0) || !(p.tau > 0) || !std::isfinite(p.tau) || !std::isfinite(p.rho0)) return false;
     if (!std::isnan(p.gamma_bulk) && !(std::fabs(p.gamma_bulk) < 1.0)) return false;
     if (!(std::fabs(p.gamma_ghost) < 1.0)) return false;
@@ -100,7 +101,7 @@ Geom make_geom(const flb_params &p)
     g.ny = p.ny;
     g.nz = p.dim == 3 ? p.nz : 1;
     g.gz = p.dim == 3 ? GZ3 : 0;
-    g.px = g.nx + 2 * GX;
+    g.px = ((g.nx + 2 * GX + 3) / 4) * 4;  // row pitch a multiple of 16 bytes (TMA)
     g.py = g.ny + 2 * GY;
     g.pz = g.nz + 2 * g.gz;
     g.n = (long long)g.nx * g.ny * g.nz;
@@ -119,13 +120,15 @@ void carve_rep(Rep &r, Carver &cv)
     r.psi[1] = cv.take<float>(P);
     r.mu = cv.take<float>(P);
     r.u = cv.take<float>((size_t)r.dim * P);
-    r.eta = cv.take<float>(N);
     if (r.p.integrator == FLB_HEUN) {
         r.psis = cv.take<float>(P);
-        r.mus = cv.take<float>(P);
         r.E = cv.take<float>(N);
     }
-    if (r.p.psi_scheme == FLB_FV) r.J = cv.take<float>((size_t)r.dim * P);
+    if (r.dim == 2) {  // the 2D path keeps mu*, the noise increment and the FV flux in HBM
+        r.eta = cv.take<float>(N);
+        if (r.p.integrator == FLB_HEUN) r.mus = cv.take<float>(P);
+        if (r.p.psi_scheme == FLB_FV) r.J = cv.take<float>((size_t)r.dim * P);
+    }
     r.Kx = axis_K(g.nx, r.p.sq_kmax);
     r.Ky = axis_K(g.ny, r.p.sq_kmax);
     r.Kz = r.dim == 3 ? axis_K(g.nz, r.p.sq_kmax) : 1;
@@ -164,6 +167,7 @@ struct flb_handle {
     int sample_every = 0, sample_mask = 0;
     int64_t launches = 0;
     double *red_partial = nullptr, *red_out = nullptr;
+    int *status = nullptr;  // device status word: kernels latch FLB_ETIMEOUT here
     float2 *X1 = nullptr, *X2 = nullptr;
     float *heights = nullptr, *win = nullptr;
     char *ws = nullptr;
@@ -201,6 +205,7 @@ size_t carve_all(flb_handle &h, char *base)
     }
     h.red_partial = cv.take<double>((size_t)RED_MAX_BLOCKS * NRED);
     h.red_out = cv.take<double>(NRED);
+    h.status = cv.take<int>(1);
     h.X1 = cv.take<float2>(cap1);
     h.X2 = cv.take<float2>(cap2);
     h.heights = cv.take<float>(std::max<size_t>(hcap, 1));
@@ -316,19 +321,11 @@ int download_interior(flb_handle *h, const Geom &g, const float *src, std::vecto
     } while (0)
 
 // One coupled step of one replica: LB (reads psi^n, mu^n; writes u^n), then psi.
-int step_rep(flb_handle *h, Rep &r)
+LBArgs lb_args(const Rep &r, float *psi_n)
 {
-    const Geom &g = r.g;
     const flb_params &p = r.p;
-    cudaStream_t st = h->st;
-    float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
-    const int64_t l0 = h->launches;
-    cudaEvent_t e0 = mark(h);
-    FLB_TRY(launch_mu(g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
-    cudaEvent_t e1 = mark(h);
-
     LBArgs la;
-    la.g = g;
+    la.g = r.g;
     la.fin = r.f[r.cur];
     la.fout = r.f[r.cur ^ 1];
     la.psi = psi_n;
@@ -341,8 +338,57 @@ int step_rep(flb_handle *h, Rep &r)
     la.kT = (float)p.kT;
     std::memcpy(la.namp, r.namp, sizeof(la.namp));
     la.coupling = p.coupling;
-    la.seed = p.seed;
+    la.key = philox_key(p.seed);
     la.step = r.step;
+    return la;
+}
+
+// 3D step: the LB kernel derives mu and the force from psi in shared memory;
+// each Runge-Kutta stage of psi is one fused launch.
+int step_rep3(flb_handle *h, Rep &r)
+{
+    const flb_params &p = r.p;
+    cudaStream_t st = h->st;
+    float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
+    const LBArgs la = lb_args(r, psi_n);
+    cudaEvent_t e0 = mark(h);
+    if (p.coupling & FLB_COUPLE_FORCE) FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+    cudaEvent_t e1 = mark(h);
+    FLB_TRY(launch_lb3d(la, p.storage, st));
+    cudaEvent_t e2 = mark(h);
+    const int64_t l2 = h->launches;
+    const bool noisy = p.kT > 0 && p.M > 0;
+    const bool heun = p.integrator == FLB_HEUN;
+    const int advect = (p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
+    const PhiloxKey key = philox_key(p.seed);
+    FLB_TRY(launch_psi3(r.g, p.psi_scheme, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
+                        (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, h->status, st));
+    if (heun)
+        FLB_TRY(launch_psi3(r.g, p.psi_scheme, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
+                            (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, h->status, st));
+    cudaEvent_t e3 = mark(h);
+    span(h, 0, e1, e2, 1);
+    span(h, 1, e0, e1, (p.coupling & FLB_COUPLE_FORCE) ? 1 : 0);
+    span(h, 1, e2, e3, (int)(h->launches - l2));
+    r.cur ^= 1;
+    r.pcur ^= 1;
+    r.step += 1;
+    return FLB_OK;
+}
+
+int step_rep(flb_handle *h, Rep &r)
+{
+    if (r.dim == 3) return step_rep3(h, r);
+    const Geom &g = r.g;
+    const flb_params &p = r.p;
+    cudaStream_t st = h->st;
+    float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
+    const int64_t l0 = h->launches;
+    cudaEvent_t e0 = mark(h);
+    FLB_TRY(launch_mu(g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+    cudaEvent_t e1 = mark(h);
+
+    const LBArgs la = lb_args(r, psi_n);
     FLB_TRY(launch_lb(la, r.q, p.storage, st));
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
@@ -355,7 +401,7 @@ int step_rep(flb_handle *h, Rep &r)
         na.kT = (float)p.kT;
         na.M = (float)p.M;
         na.scheme = p.psi_scheme;
-        na.seed = p.seed;
+        na.key = philox_key(p.seed);
         na.step = r.step;
         FLB_TRY(launch_noise(na, st));
     }
@@ -458,6 +504,16 @@ int sample_rep(flb_handle *h, Rep &r, int mask)
         r.h_n += 1;
     }
     return FLB_OK;
+}
+
+// Read and clear the device status word (after the stream has drained).
+int take_status(flb_handle *h)
+{
+    int s = 0;
+    if (cudaMemcpyAsync(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st) != cudaSuccess) return FLB_ECUDA;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return FLB_ECUDA;
+    if (s != 0 && cudaMemsetAsync(h->status, 0, sizeof(int), h->st) != cudaSuccess) return FLB_ECUDA;
+    return s;
 }
 
 Rep *get_rep(flb_handle *h, int32_t rep)
@@ -703,6 +759,8 @@ int flb_moments(flb_handle *h, int32_t rep, double *totals, double *u2)
     }
     if (u2)
         for (int a = 0; a < r->dim; ++a) u2[a] = out[5 + a] / (double)g.n;
+    const int st = take_status(h);
+    if (st != FLB_OK) return st;
     return out[8] > 0 ? FLB_ENONFINITE : FLB_OK;
 }
 
@@ -832,7 +890,8 @@ int flb_set_state(flb_handle *h, int32_t rep, const void *host, size_t bytes)
 int flb_synchronize(flb_handle *h)
 {
     if (!h) return FLB_EINVAL;
-    return cuerr(cudaStreamSynchronize(h->st));
+    const int rc = cuerr(cudaStreamSynchronize(h->st));
+    return rc != FLB_OK ? rc : take_status(h);
 }
 
 int64_t flb_launch_count(flb_handle *h) { return h ? h->launches : -1; }

@@ -19,42 +19,64 @@ struct u32x4 {
     uint32_t x, y, z, w;
 };
 
-__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1)
+// Round keys of one seed: round r uses (seed_lo + r W0, seed_hi + r W1).  They
+// are computed on the host and passed in the kernel parameters, so every round
+// XORs a constant operand.
+struct PhiloxKey {
+    uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKey philox_key(uint64_t seed)
 {
-    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    PhiloxKey K;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = a;
+        K.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxKey &K)
+{
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-        c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = u32x4{(uint32_t)(p1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.k1[r],
+                  (uint32_t)p0};
     }
     return c;
 }
 
-// Uniform in (0,1): ((x >> 9) + 1/2) 2^-23, exact in binary32.
+// Uniform in (0,1): ((x >> 9) + 1/2) 2^-23, exact in binary32.  Built from the
+// bits: 1 + k 2^-23 (k = x >> 9) minus (1 - 2^-24) is exactly k 2^-23 + 2^-24.
 __device__ __forceinline__ float u01(uint32_t x)
 {
-    return fmaf(__uint2float_rn(x >> 9), 1.0f / 8388608.0f, 1.0f / 16777216.0f);
+    return __int_as_float((x >> 9) | 0x3f800000u) - __int_as_float(0x3f7fffffu);
 }
 
-// Four standard normals of one Philox block by Box-Muller on (x,y) and (z,w).
-__device__ __forceinline__ void normals4(uint64_t seed, int64_t step, uint32_t site, uint32_t stream, uint32_t block,
-                                         float g[4])
+// Box-Muller: r = sqrt(-2 ln a), (r cos 2 pi b, r sin 2 pi b).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
+{
+    const float e = -2.0f * logf(u01(a));  // e >= 1.19e-7 > 0
+    const float rad = e * rsqrtf(e);
+    float s, c;
+    sincospif(2.0f * u01(b), &s, &c);
+    g0 = rad * c;
+    g1 = rad * s;
+}
+
+// Four standard normals of one Philox block (Box-Muller on (x,y) and (z,w)).
+__device__ __forceinline__ void normals4(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
+                                         uint32_t block, float g[4])
 {
     const u32x4 r = philox4x32_10(
-        u32x4{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)},
-        (uint32_t)seed, (uint32_t)(seed >> 32));
-    float s, c;
-    float rad = sqrtf(-2.0f * logf(u01(r.x)));
-    sincospif(2.0f * u01(r.y), &s, &c);
-    g[0] = rad * c;
-    g[1] = rad * s;
-    rad = sqrtf(-2.0f * logf(u01(r.z)));
-    sincospif(2.0f * u01(r.w), &s, &c);
-    g[2] = rad * c;
-    g[3] = rad * s;
+        u32x4{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)}, K);
+    box_muller(r.x, r.y, g[0], g[1]);
+    box_muller(r.z, r.w, g[2], g[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -76,6 +98,10 @@ struct Geom {
     {
         return (long long)(x + GX) + (long long)px * ((long long)(y + GY) + (long long)py * (long long)(z + gz));
     }
+    __host__ __device__ __forceinline__ int pidx32(int x, int y, int z) const
+    {
+        return (x + GX) + px * ((y + GY) + py * (z + gz));
+    }
     __host__ __device__ __forceinline__ long long sidx(int x, int y, int z) const
     {
         return (long long)x + (long long)nx * ((long long)y + (long long)ny * (long long)z);
@@ -83,22 +109,27 @@ struct Geom {
 };
 
 // Store v at interior site (x,y,z) of a padded plane and at every periodic image
-// of it that lies in the ghost frame within `rad` cells of the interior.
+// of it that lies in the ghost frame within `rad` cells of the interior.  The
+// candidate images are unrolled with predicates (no local memory).
 __device__ __forceinline__ void store_padded(float *a, const Geom &g, int x, int y, int z, float v, int rad)
 {
-    int xs[3] = {x, x, x}, ys[3] = {y, y, y}, zs[3] = {z, z, z};
-    int nxi = 1, nyi = 1, nzi = 1;
-    if (x < rad) xs[nxi++] = x + g.nx;
-    if (x >= g.nx - rad) xs[nxi++] = x - g.nx;
-    if (y < rad) ys[nyi++] = y + g.ny;
-    if (y >= g.ny - rad) ys[nyi++] = y - g.ny;
-    if (g.dim == 3) {
-        if (z < rad) zs[nzi++] = z + g.nz;
-        if (z >= g.nz - rad) zs[nzi++] = z - g.nz;
+    if (x >= rad && x < g.nx - rad && y >= rad && y < g.ny - rad && (g.dim == 2 || (z >= rad && z < g.nz - rad))) {
+        a[g.pidx32(x, y, z)] = v;
+        return;
     }
-    for (int k = 0; k < nzi; ++k)
-        for (int j = 0; j < nyi; ++j)
-            for (int i = 0; i < nxi; ++i) a[g.pidx(xs[i], ys[j], zs[k])] = v;
+    const int xs[3] = {x, x + g.nx, x - g.nx};
+    const bool vx[3] = {true, x < rad, x >= g.nx - rad};
+    const int ys[3] = {y, y + g.ny, y - g.ny};
+    const bool vy[3] = {true, y < rad, y >= g.ny - rad};
+    const int zs[3] = {z, z + g.nz, z - g.nz};
+    const bool vz[3] = {true, g.dim == 3 && z < rad, g.dim == 3 && z >= g.nz - rad};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (vz[k] && vy[j] && vx[i]) a[g.pidx(xs[i], ys[j], zs[k])] = v;
 }
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
@@ -119,7 +150,7 @@ struct LBArgs {
     float kT;
     float namp[16];            // sqrt((1 - gamma_k^2)/b_k) of the noisy modes, in noise order
     int coupling;
-    uint64_t seed;
+    PhiloxKey key;
     int64_t step;
 };
 
@@ -145,12 +176,20 @@ struct NoiseArgs {
     float *eta;            // [N]
     float kT, M;
     int scheme;
-    uint64_t seed;
+    PhiloxKey key;
     int64_t step;
 };
 
 // host launchers (flb_lb.cu, flb_psi.cu, flb_obs.cu)
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);
+// D3Q19 collide-stream that computes mu and the force itself from psi (flb_lb3d.cu)
+cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t s);
+// one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu)
+cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
+                        float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
+                        const PhiloxKey &key, int64_t step, int *status, cudaStream_t st);
+// mu on the interior and one ghost layer of a 3D box (flb_lb3d.cu)
+cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,
                            cudaStream_t st);
 cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t s);

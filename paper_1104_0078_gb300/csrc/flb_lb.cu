@@ -160,10 +160,10 @@ __global__ void __launch_bounds__(256) lb_d3q19_kernel(const LBArgs a)
     if (a.kT > 0.f) {
         float G[16];
         const uint32_t sid = (uint32_t)site;
-        normals4(a.seed, a.step, sid, 0u, 0u, G);
-        normals4(a.seed, a.step, sid, 0u, 1u, G + 4);
-        normals4(a.seed, a.step, sid, 0u, 2u, G + 8);
-        normals4(a.seed, a.step, sid, 0u, 3u, G + 12);
+        normals4(a.key, a.step, sid, 0u, 0u, G);
+        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
+        normals4(a.key, a.step, sid, 0u, 2u, G + 8);
+        normals4(a.key, a.step, sid, 0u, 3u, G + 12);
         const float sq = sqrtf(3.0f * rho * a.kT);
         float n[15];
 #pragma unroll
@@ -322,8 +322,8 @@ __global__ void __launch_bounds__(256) lb_d2q9_kernel(const LBArgs a)
     if (a.kT > 0.f) {
         float G[8];
         const uint32_t sid = (uint32_t)site;
-        normals4(a.seed, a.step, sid, 0u, 0u, G);
-        normals4(a.seed, a.step, sid, 0u, 1u, G + 4);
+        normals4(a.key, a.step, sid, 0u, 0u, G);
+        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
         const float sq = sqrtf(3.0f * rho * a.kT);
         float n[6];
 #pragma unroll

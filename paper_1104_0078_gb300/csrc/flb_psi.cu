@@ -77,7 +77,7 @@ __global__ void noise_kernel(const NoiseArgs a)
     if (a.scheme == FLB_FD) {
         const int nl = g.dim == 3 ? 13 : 4;
         float own[16];
-        for (int b = 0; b < (nl + 3) / 4; ++b) normals4(a.seed, a.step, (uint32_t)site, 1u, (uint32_t)b, own + 4 * b);
+        for (int b = 0; b < (nl + 3) / 4; ++b) normals4(a.key, a.step, (uint32_t)site, 1u, (uint32_t)b, own + 4 * b);
         for (int l = 0; l < nl; ++l) {
             int cx, cy, cz = 0;
             if (g.dim == 3) { cx = kL13[l][0]; cy = kL13[l][1]; cz = kL13[l][2]; }
@@ -88,13 +88,13 @@ __global__ void noise_kernel(const NoiseArgs a)
             const float sd = sqrtf(2.f * a.kT * a.M * al);
             const long long nb = g.sidx(wrapi(x - cx, g.nx), wrapi(y - cy, g.ny), g.dim == 3 ? wrapi(z - cz, g.nz) : 0);
             float gn[4];
-            normals4(a.seed, a.step, (uint32_t)nb, 1u, (uint32_t)(l >> 2), gn);
+            normals4(a.key, a.step, (uint32_t)nb, 1u, (uint32_t)(l >> 2), gn);
             eta += sd * (gn[l & 3] - own[l]);
         }
     } else {
         const float sd = sqrtf(2.f * a.kT * a.M);
         float own[4];
-        normals4(a.seed, a.step, (uint32_t)site, 1u, 0u, own);
+        normals4(a.key, a.step, (uint32_t)site, 1u, 0u, own);
         const int nq = g.dim == 3 ? 18 : 8;
         float acc = 0.f;
         for (int i = 0; i < nq; ++i) {
@@ -109,7 +109,7 @@ __global__ void noise_kernel(const NoiseArgs a)
             }
             const long long nb = g.sidx(wrapi(x + cx, g.nx), wrapi(y + cy, g.ny), g.dim == 3 ? wrapi(z + cz, g.nz) : 0);
             float gn[4];
-            normals4(a.seed, a.step, (uint32_t)nb, 1u, 0u, gn);
+            normals4(a.key, a.step, (uint32_t)nb, 1u, 0u, gn);
             float link = cx * (own[0] + gn[0]) + cy * (own[1] + gn[1]);
             if (g.dim == 3) link += cz * (own[2] + gn[2]);
             acc += w * link;

@@ -1,0 +1,532 @@
+// flb_psi3d.cu -- one Runge-Kutta stage of the order-parameter equation (Sec. V
+// of arXiv:1104.0078) on a 3D box, fused in one pass with z-marching (2.5D)
+// blocking.
+//
+// A block owns a TX x TY column tile and a chunk of ZC planes.  Rolling rings of
+// planes in shared memory hold psi (tile + 3 ghost cells), the chemical
+// potential mu = A psi + B psi^3 - K lap_SO psi (tile + 2), and for the finite-
+// volume scheme the node flux J = M grad mu - u psi (tile + 1) and the node
+// noise xi (tile + 1); the stage output at plane z is formed from the three
+// flux planes z-1, z, z+1.  Nothing but psi, u and the Heun accumulator touches
+// HBM.  In the finite-volume kernel the psi and velocity planes arrive by TMA
+// (cp.async.bulk.tensor) two planes ahead of use.
+//
+//   FV (Sec. V.B):  grad mu = (1/c_s^2) sum_i w_i c_i mu(r + c_i)
+//                   D(r)    = (1/c_s^2) sum_i w_i c_i . J(r + c_i)
+//                   (the link average (J(r) + J(r+c_i))/2 of Eq. fvflux with
+//                    the 2/c_s^2 divergence; sum_i w_i c_i = 0 removes J(r)),
+//                   xi_a ~ N(0, 2 kT M) per node and component.
+//   FD (Sec. V.A):  D(r)    = M lap_SO mu - div_CD(u psi),
+//                   eta(r)  = sum_l [zeta_l(r - c_l) - zeta_l(r)] over the 13
+//                   half-links of the SO stencil, zeta_l ~ N(0, 2 kT M a_l).
+// Stage 1 writes psi* = psi + D + eta and (Heun) E = psi + D/2 + eta; stage 2
+// writes psi^{n+1} = E + D(psi*)/2 (the noise is held fixed over the step).
+#include <cudaTypedefs.h>
+
+#include "flb_internal.cuh"
+#include "flb_tma.cuh"
+
+namespace flb {
+
+constexpr int PS_TX = 32, PS_TY = 16, PS_ZC = 64;
+constexpr int PS_NT = PS_TX * PS_TY;
+constexpr int H3X = PS_TX + 6, H3Y = PS_TY + 6, H3N = H3X * H3Y;  // psi: tile + 3
+constexpr int H2X = PS_TX + 4, H2Y = PS_TY + 4, H2N = H2X * H2Y;  // mu: tile + 2
+constexpr int H1X = PS_TX + 2, H1Y = PS_TY + 2, H1N = H1X * H1Y;  // flux / noise: tile + 1
+constexpr int S3 = (H3N + PS_NT - 1) / PS_NT, S2 = (H2N + PS_NT - 1) / PS_NT, S1 = (H1N + PS_NT - 1) / PS_NT;
+
+__device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
+__device__ __forceinline__ int ring4(int p) { return p & 3; }  // two's complement: correct for negative p
+
+// mu = A psi + B psi^3 - (K/22)(6 N1 + 3 N2 + N3 - 80 psi) at offset c of three
+// psi planes with row pitch PX (with A = B = 0 and k22 = -1/22 it is lap_SO)
+template <int PX>
+__device__ __forceinline__ float mu_point(const float *pm, const float *p0, const float *pp, int c, float A, float B,
+                                          float k22)
+{
+    const float n1 = (p0[c - 1] + p0[c + 1]) + (p0[c - PX] + p0[c + PX]) + (pm[c] + pp[c]);
+    const float n2 = ((p0[c - 1 - PX] + p0[c + 1 - PX]) + (p0[c - 1 + PX] + p0[c + 1 + PX])) +
+                     ((pm[c - 1] + pm[c + 1]) + (pm[c - PX] + pm[c + PX])) +
+                     ((pp[c - 1] + pp[c + 1]) + (pp[c - PX] + pp[c + PX]));
+    const float n3 = ((pm[c - 1 - PX] + pm[c + 1 - PX]) + (pm[c - 1 + PX] + pm[c + 1 + PX])) +
+                     ((pp[c - 1 - PX] + pp[c + 1 - PX]) + (pp[c - 1 + PX] + pp[c + 1 + PX]));
+    const float ps = p0[c];
+    return A * ps + B * ps * ps * ps - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * ps);
+}
+
+struct Psi3Args {
+    Geom g;
+    const float *psi;  // padded stage input
+    const float *u;    // padded velocity (images to radius 1)
+    float *out;        // padded stage output (images to radius 3)
+    float *E;          // [N] Heun accumulator: written by stage 1, read by stage 2
+    float A, B, K, M, kT;
+    int advect, heun;
+    PhiloxKey key;
+    int64_t step;
+};
+
+// Per-thread view of the block's halo regions, computed once: for every slot the
+// in-plane offset of the padded field it loads (psi, u) and the in-plane counter
+// id of its periodic image (noise).
+struct Regions {
+    int g3[S3];                 // psi region: padded in-plane offsets (-1: no slot)
+    int c2[S2];                 // mu region: centre offset in the psi tile frame (-1: none)
+    int c1[S1], p1[S1], u1[S1], n1[S1];  // flux region: mu-frame centre, psi-frame centre, u offset, noise id
+};
+
+__device__ __forceinline__ void make_regions(Regions &R, const Geom &g, int x0, int y0)
+{
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < S3; ++j) {
+        const int k = t + j * PS_NT;
+        const int gx = min(x0 - 3 + k % H3X, g.nx + GX - 1), gy = min(y0 - 3 + k / H3X, g.ny + GY - 1);
+        R.g3[j] = k < H3N ? (gx + GX) + g.px * (gy + GY) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < S2; ++j) {
+        const int k = t + j * PS_NT;
+        R.c2[j] = k < H2N ? (k % H2X + 1) + H3X * (k / H2X + 1) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < S1; ++j) {
+        const int k = t + j * PS_NT;
+        const int lx = k % H1X, ly = k / H1X;
+        const int gx = min(x0 - 1 + lx, g.nx + GX - 1), gy = min(y0 - 1 + ly, g.ny + GY - 1);
+        R.c1[j] = k < H1N ? (lx + 1) + H2X * (ly + 1) : -1;
+        R.p1[j] = (lx + 2) + H3X * (ly + 2);
+        R.u1[j] = (gx + GX) + g.px * (gy + GY);
+        R.n1[j] = wrapi(gx, g.nx) + g.nx * wrapi(gy, g.ny);
+    }
+}
+
+// divergence (1/c_s^2) sum_i w_i c_i . V(r + c_i) of a vector field held in three
+// planes (z-1, z, z+1) of the tile + 1 frame: (1/6) axis + (1/12) diagonal links
+__device__ __forceinline__ float fv_div(const float *xm, const float *x0, const float *xp, const float *ym,
+                                        const float *y0, const float *yp, const float *zm, const float *z0,
+                                        const float *zp, int c)
+{
+    (void)z0;
+    const float ax = (x0[c + 1] - x0[c - 1]) + (y0[c + H1X] - y0[c - H1X]) + (zp[c] - zm[c]);
+    float dg = (x0[c + 1 + H1X] + y0[c + 1 + H1X]) - (x0[c - 1 - H1X] + y0[c - 1 - H1X]);
+    dg += (x0[c + 1 - H1X] - y0[c + 1 - H1X]) - (x0[c - 1 + H1X] - y0[c - 1 + H1X]);
+    dg += (xp[c + 1] + zp[c + 1]) - (xm[c - 1] + zm[c - 1]);
+    dg += (xm[c + 1] - zm[c + 1]) - (xp[c - 1] - zp[c - 1]);
+    dg += (yp[c + H1X] + zp[c + H1X]) - (ym[c - H1X] + zm[c - H1X]);
+    dg += (ym[c + H1X] - zm[c + H1X]) - (yp[c - H1X] - zp[c - H1X]);
+    return (1.f / 6.f) * ax + (1.f / 12.f) * dg;
+}
+
+// ---------------------------------------------------------------------------
+// Finite difference.  Shared memory: psi ring 4 x H3N, mu ring 3 x H2N and
+// (stage 1 with noise) the 13 link noises of one plane, 13 x H1N floats.
+// ---------------------------------------------------------------------------
+// half-links: x, y, z, (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1),
+// (1,1,1), (1,1,-1), (1,-1,1), (1,-1,-1); coefficients 6/22, 3/22, 1/22
+__constant__ int8_t kFDL[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
+                                   {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                   {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+
+template <int STAGE, bool NOISE>
+__global__ void __launch_bounds__(PS_NT) psi3_fd_kernel(const Psi3Args a)
+{
+    extern __shared__ float smem[];
+    float *sps = smem;           // [4][H3N]
+    float *smu = sps + 4 * H3N;  // [3][H2N]
+    float *sZ = smu + 3 * H2N;   // [13][H1N] when NOISE
+    const Geom &g = a.g;
+    const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
+    const int x0 = blockIdx.x * PS_TX, y0 = blockIdx.y * PS_TY, z0 = blockIdx.z * PS_ZC;
+    const int z1 = min(z0 + PS_ZC, g.nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < g.nx && y < g.ny;
+    const float k22 = a.K * (1.0f / 22.0f);
+    const int plane = g.px * g.py;
+    Regions R;
+    make_regions(R, g, x0, y0);
+    float accm = 0.f, acc0 = 0.f, accp = 0.f;  // eta of planes p-2, p-1, p
+
+    for (int p = z0 - 2; p <= z1 + 1; ++p) {
+        __syncthreads();
+        {
+            const float *src = a.psi + (size_t)plane * (p + g.gz);
+            float *dst = sps + ring4(p) * H3N;
+#pragma unroll
+            for (int j = 0; j < S3; ++j)
+                if (R.g3[j] >= 0) dst[threadIdx.x + j * PS_NT] = __ldg(src + R.g3[j]);
+        }
+        __syncthreads();
+        const int q = p - 1;
+        if (q >= z0 - 1) {
+            // mu(q) on tile + 1, stored at its place in the tile + 2 frame
+            const float *pm = sps + ring4(q - 1) * H3N, *p0 = sps + ring4(q) * H3N, *pp = sps + ring4(q + 1) * H3N;
+            float *dst = smu + ring3(q) * H2N;
+#pragma unroll
+            for (int j = 0; j < S1; ++j) {
+                const int c = R.c1[j];
+                if (c < 0) continue;
+                dst[c] = mu_point<H3X>(pm, p0, pp, R.p1[j], a.A, a.B, k22);
+            }
+            if (NOISE) {
+                const int zid = g.nx * g.ny * wrapi(q, g.nz);
+#pragma unroll
+                for (int j = 0; j < S1; ++j) {
+                    if (R.c1[j] < 0) continue;
+                    const int k = threadIdx.x + j * PS_NT;
+                    const uint32_t sid = (uint32_t)(R.n1[j] + zid);
+                    float G[16];
+                    normals4(a.key, a.step, sid, 1u, 0u, G);
+                    normals4(a.key, a.step, sid, 1u, 1u, G + 4);
+                    normals4(a.key, a.step, sid, 1u, 2u, G + 8);
+                    normals4(a.key, a.step, sid, 1u, 3u, G + 12);
+#pragma unroll
+                    for (int l = 0; l < 13; ++l) {
+                        const float al = l < 3 ? 6.f / 22.f : (l < 9 ? 3.f / 22.f : 1.f / 22.f);
+                        sZ[l * H1N + k] = sqrtf(2.0f * a.kT * a.M * al) * G[l];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (NOISE && q >= z0 - 1 && active) {
+            // zeta(q) feeds eta(q) (own links, in-plane neighbours), eta(q+1)
+            // (links with c_z = +1) and eta(q-1) (links with c_z = -1)
+            const int c = (tx + 1) + H1X * (ty + 1);
+            float own = 0.f, in0 = 0.f, up = 0.f, dn = 0.f;
+#pragma unroll
+            for (int l = 0; l < 13; ++l) {
+                own += sZ[l * H1N + c];
+                const float v = sZ[l * H1N + c - kFDL[l][0] - H1X * kFDL[l][1]];
+                if (kFDL[l][2] == 0) in0 += v;
+                else if (kFDL[l][2] > 0) up += v;
+                else dn += v;
+            }
+            accm += dn;
+            acc0 += in0 - own;
+            accp += up;
+        }
+        const int z = p - 2;
+        if (z >= z0 && active) {
+            const float *mm = smu + ring3(z - 1) * H2N, *m0 = smu + ring3(z) * H2N, *mp = smu + ring3(z + 1) * H2N;
+            const int c = (tx + 2) + H2X * (ty + 2);
+            float D = a.M * mu_point<H2X>(mm, m0, mp, c, 0.f, 0.f, -1.0f / 22.0f);
+            if (a.advect) {
+                const float *P0 = sps + ring4(z) * H3N, *Pm = sps + ring4(z - 1) * H3N, *Pp = sps + ring4(z + 1) * H3N;
+                const int cp = (tx + 3) + H3X * (ty + 3);
+                const int pi = g.pidx32(x, y, z);
+                const int sy = g.px, sz = g.px * g.py;
+                const float *u = a.u;
+                const float adv = (u[pi + 1] * P0[cp + 1] - u[pi - 1] * P0[cp - 1]) +
+                                  (u[g.pn + pi + sy] * P0[cp + H3X] - u[g.pn + pi - sy] * P0[cp - H3X]) +
+                                  (u[2 * g.pn + pi + sz] * Pp[cp] - u[2 * g.pn + pi - sz] * Pm[cp]);
+                D -= 0.5f * adv;
+            }
+            const int si = x + g.nx * (y + g.ny * z);
+            float out;
+            if (STAGE == 1) {
+                const float eta = NOISE ? accm : 0.f;
+                const float pv = sps[ring4(z) * H3N + (tx + 3) + H3X * (ty + 3)];
+                out = pv + D + eta;
+                if (a.heun) a.E[si] = pv + 0.5f * D + eta;
+            } else {
+                out = a.E[si] + 0.5f * D;
+            }
+            store_padded(a.out, g, x, y, z, out, 3);
+        }
+        accm = acc0;
+        acc0 = accp;
+        accp = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finite volume with TMA staging.  psi planes (tile + 4 in x, + 3 in y) and the
+// three velocity components of a plane (tile + 4 in x, + 1 in y) are copied by
+// cp.async.bulk.tensor two planes ahead of their use into rings of shared-memory
+// slots, each completed on its own mbarrier; the compute phases are those of
+// psi3_fv_kernel.
+//   psi slot:  [TY+6][TX+8] floats, column c <-> x = x0 - 4 + c, row r <-> y = y0 - 3 + r
+//   u slot:    [3][TY+2][TX+8],     column c <-> x = x0 - 4 + c, row r <-> y = y0 - 1 + r
+// ---------------------------------------------------------------------------
+constexpr int TB_X = PS_TX + 8;                            // TMA box width (x0-4 .. x0+TX+3)
+constexpr int TP_N = TB_X * H3Y;                           // psi slot floats
+constexpr int TP_SLOT = ((TP_N * 4 + 127) / 128) * 32;     // floats, 128-byte multiple
+constexpr int TU_N = 3 * TB_X * H1Y;                       // u slot floats
+constexpr int TU_SLOT = ((TU_N * 4 + 127) / 128) * 32;
+constexpr int T_PSI_DEPTH = 6, T_U_DEPTH = 3;
+
+struct TmaArgs {
+    Psi3Args a;
+    int *status;
+};
+
+template <int STAGE, bool NOISE>
+__global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
+                                                            const __grid_constant__ CUtensorMap u_map,
+                                                            const TmaArgs ta)
+{
+    extern __shared__ __align__(1024) float tsmem[];
+    const Psi3Args &a = ta.a;
+    if (ta.status && *(volatile int *)ta.status != 0) return;  // an earlier block timed out: skip the work
+    float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
+    float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
+    float *smu = tus + T_U_DEPTH * TU_SLOT;              // [3][H2N]
+    float *sJ = smu + 3 * H2N;                           // [3][3][H1N]
+    float *sX = sJ + 9 * H1N;                            // [3][3][H1N] when NOISE
+    __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH];
+    __shared__ int s_bad;
+    const Geom &g = a.g;
+    const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
+    const int x0 = blockIdx.x * PS_TX, y0 = blockIdx.y * PS_TY, z0 = blockIdx.z * PS_ZC;
+    const int z1 = min(z0 + PS_ZC, g.nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < g.nx && y < g.ny;
+    const float k22 = a.K * (1.0f / 22.0f);
+    const float sdx = sqrtf(2.0f * a.kT * a.M);
+    const int pbase = z0 - 3, ubase = z0 - 1;             // first psi / u plane of the chunk
+    // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
+    // psi-slot centre, u-slot offset, noise counter id
+    int c2[S2], c1[S1], p1[S1], u1[S1], n1[S1];
+#pragma unroll
+    for (int j = 0; j < S2; ++j) {
+        const int k = threadIdx.x + j * PS_NT;
+        c2[j] = k < H2N ? (k % H2X + 2) + TB_X * (k / H2X + 1) : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < S1; ++j) {
+        const int k = threadIdx.x + j * PS_NT;
+        const int lx = k % H1X, ly = k / H1X;
+        c1[j] = k < H1N ? (lx + 1) + H2X * (ly + 1) : -1;
+        p1[j] = (lx + 3) + TB_X * (ly + 2);
+        u1[j] = (lx + 3) + TB_X * ly;
+        n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
+        for (int s = 0; s < T_U_DEPTH; ++s) mbar_init(&bar_u[s], 1);
+        s_bad = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue_psi = [&](int pp) {
+        const int s = (pp - pbase) % T_PSI_DEPTH;
+        mbar_expect_tx(&bar_p[s], TP_N * 4);
+        tma_load_3d(tps + s * TP_SLOT, &psi_map, &bar_p[s], x0, y0, pp + g.gz);
+    };
+    auto issue_u = [&](int qq) {
+        const int s = (qq - ubase) % T_U_DEPTH;
+        mbar_expect_tx(&bar_u[s], TU_N * 4);
+        tma_load_4d(tus + s * TU_SLOT, &u_map, &bar_u[s], x0, y0 + GY - 1, qq + g.gz, 0);
+    };
+    if (threadIdx.x == 0) {
+        issue_psi(pbase);
+        issue_psi(pbase + 1);
+    }
+    int last_p = pbase + 1, last_u = ubase - 1;  // highest plane issued (thread 0)
+    int waited_p = pbase - 1, waited_u = ubase - 1;
+
+    for (int p = z0 - 3; p <= z1 + 2; ++p) {
+        __syncthreads();
+        if (s_bad) break;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
+            if (p >= ubase && p <= z1 && a.advect) { issue_u(p); last_u = p; }
+        }
+        {   // (a) psi plane p has landed
+            const int s = (p - pbase) % T_PSI_DEPTH;
+            if (!mbar_wait(&bar_p[s], ((p - pbase) / T_PSI_DEPTH) & 1, ta.status)) s_bad = 1;
+            waited_p = p;
+        }
+        if (p - 1 >= z0 - 2) {  // (b) mu plane p-1, tile + 2
+            const float *pm = tps + ((p - 2 - pbase) % T_PSI_DEPTH) * TP_SLOT;
+            const float *p0 = tps + ((p - 1 - pbase) % T_PSI_DEPTH) * TP_SLOT;
+            const float *pp = tps + ((p - pbase) % T_PSI_DEPTH) * TP_SLOT;
+            float *dst = smu + ring3(p - 1) * H2N;
+#pragma unroll
+            for (int j = 0; j < S2; ++j)
+                if (c2[j] >= 0) dst[threadIdx.x + j * PS_NT] = mu_point<TB_X>(pm, p0, pp, c2[j], a.A, a.B, k22);
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int q = p - 2;
+        if (q >= z0 - 1) {  // (c) node flux (and noise) on plane q, tile + 1
+            const float *uq = tus;
+            if (a.advect) {
+                const int s = (q - ubase) % T_U_DEPTH;
+                if (!mbar_wait(&bar_u[s], ((q - ubase) / T_U_DEPTH) & 1, ta.status)) s_bad = 1;
+                waited_u = q;
+                uq = tus + s * TU_SLOT;
+            }
+            const float *mm = smu + ring3(q - 1) * H2N, *m0 = smu + ring3(q) * H2N, *mp = smu + ring3(q + 1) * H2N;
+            const float *ps = tps + ((q - pbase) % T_PSI_DEPTH) * TP_SLOT;
+            float *J = sJ + ring3(q) * 3 * H1N;
+            const int zid = g.nx * g.ny * wrapi(q, g.nz);
+#pragma unroll
+            for (int j = 0; j < S1; ++j) {
+                const int c = c1[j];
+                if (c < 0) continue;
+                const int k = threadIdx.x + j * PS_NT;
+                const float gx = (1.f / 6.f) * (m0[c + 1] - m0[c - 1]) +
+                                 (1.f / 12.f) * ((m0[c + 1 + H2X] + m0[c + 1 - H2X] - m0[c - 1 + H2X] - m0[c - 1 - H2X]) +
+                                                 (mp[c + 1] + mm[c + 1] - mp[c - 1] - mm[c - 1]));
+                const float gy = (1.f / 6.f) * (m0[c + H2X] - m0[c - H2X]) +
+                                 (1.f / 12.f) * ((m0[c + H2X + 1] + m0[c + H2X - 1] - m0[c - H2X + 1] - m0[c - H2X - 1]) +
+                                                 (mp[c + H2X] + mm[c + H2X] - mp[c - H2X] - mm[c - H2X]));
+                const float gz = (1.f / 6.f) * (mp[c] - mm[c]) +
+                                 (1.f / 12.f) * ((mp[c + 1] + mp[c - 1] - mm[c + 1] - mm[c - 1]) +
+                                                 (mp[c + H2X] + mp[c - H2X] - mm[c + H2X] - mm[c - H2X]));
+                float jx = a.M * gx, jy = a.M * gy, jz = a.M * gz;
+                if (a.advect) {
+                    const float pv = ps[p1[j]];
+                    jx -= uq[u1[j]] * pv;
+                    jy -= uq[TB_X * H1Y + u1[j]] * pv;
+                    jz -= uq[2 * TB_X * H1Y + u1[j]] * pv;
+                }
+                J[k] = jx;
+                J[H1N + k] = jy;
+                J[2 * H1N + k] = jz;
+                if (NOISE) {
+                    float G[4];
+                    normals4(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, G);
+                    float *X = sX + ring3(q) * 3 * H1N;
+                    X[k] = sdx * G[0];
+                    X[H1N + k] = sdx * G[1];
+                    X[2 * H1N + k] = sdx * G[2];
+                }
+            }
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int z = p - 3;
+        if (z >= z0 && active) {  // (d) stage output at plane z
+            const int c = (tx + 1) + H1X * (ty + 1);
+            const float *Jm = sJ + ring3(z - 1) * 3 * H1N, *J0 = sJ + ring3(z) * 3 * H1N, *Jp = sJ + ring3(z + 1) * 3 * H1N;
+            const float Dd = fv_div(Jm, J0, Jp, Jm + H1N, J0 + H1N, Jp + H1N, Jm + 2 * H1N, J0 + 2 * H1N,
+                                    Jp + 2 * H1N, c);
+            const int si = x + g.nx * (y + g.ny * z);
+            float out;
+            if (STAGE == 1) {
+                float Dn = 0.f;
+                if (NOISE) {
+                    const float *Xm = sX + ring3(z - 1) * 3 * H1N, *X0 = sX + ring3(z) * 3 * H1N,
+                                *Xp = sX + ring3(z + 1) * 3 * H1N;
+                    Dn = fv_div(Xm, X0, Xp, Xm + H1N, X0 + H1N, Xp + H1N, Xm + 2 * H1N, X0 + 2 * H1N, Xp + 2 * H1N, c);
+                }
+                const float pv = tps[((z - pbase) % T_PSI_DEPTH) * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
+                out = pv + Dd + Dn;
+                if (a.heun) a.E[si] = pv + 0.5f * Dd + Dn;
+            } else {
+                out = a.E[si] + 0.5f * Dd;
+            }
+            store_padded(a.out, g, x, y, z, out, 3);
+        }
+    }
+    // a bounded wait drains copies still in flight before the block exits
+    if (threadIdx.x == 0) {
+        for (int pp = waited_p + 1; pp <= last_p; ++pp)
+            mbar_wait(&bar_p[(pp - pbase) % T_PSI_DEPTH], ((pp - pbase) / T_PSI_DEPTH) & 1, nullptr);
+        for (int qq = waited_u + 1; qq <= last_u; ++qq)
+            mbar_wait(&bar_u[(qq - ubase) % T_U_DEPTH], ((qq - ubase) / T_U_DEPTH) & 1, nullptr);
+    }
+}
+
+template <typename K>
+static cudaError_t launch_dyn(K kernel, dim3 grid, size_t smem, cudaStream_t st, const Psi3Args &a)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, PS_NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                                  const uint64_t *strides_bytes, const uint32_t *box)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return cudaErrorNotSupported;
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    cuuint64_t d[5], str[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i > 0) str[i - 1] = strides_bytes[i - 1];
+    }
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d, str, bx,
+                          es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *status, cudaStream_t st)
+{
+    const Geom &g = a.g;
+    CUtensorMap pm, um;
+    const uint64_t pd[3] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz};
+    const uint64_t ps[2] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4};
+    const uint32_t pb[3] = {(uint32_t)TB_X, (uint32_t)H3Y, 1};
+    cudaError_t e = encode_tensor_map_f32(&pm, a.psi, 3, pd, ps, pb);
+    if (e != cudaSuccess) return e;
+    const uint64_t ud[4] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz, 3};
+    const uint64_t us[3] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4, (uint64_t)g.pn * 4};
+    const uint32_t ub[4] = {(uint32_t)TB_X, (uint32_t)H1Y, 1, 3};
+    e = encode_tensor_map_f32(&um, a.u, 4, ud, us, ub);
+    if (e != cudaSuccess) return e;
+    TmaArgs ta;
+    ta.a = a;
+    ta.status = status;
+    const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + PS_ZC - 1) / PS_ZC);
+    size_t sm = sizeof(float) * ((size_t)T_PSI_DEPTH * TP_SLOT + (size_t)T_U_DEPTH * TU_SLOT + 3 * H2N + 9 * H1N);
+    auto go = [&](auto kernel, size_t bytes) {
+        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (r != cudaSuccess) return r;
+        kernel<<<grid, PS_NT, bytes, st>>>(pm, um, ta);
+        return cudaGetLastError();
+    };
+    if (stage == 1) {
+        if (noise) return go(psi3_fv_tma_kernel<1, true>, sm + sizeof(float) * 9 * H1N);
+        return go(psi3_fv_tma_kernel<1, false>, sm);
+    }
+    return go(psi3_fv_tma_kernel<2, false>, sm);
+}
+
+cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
+                        float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
+                        const PhiloxKey &key, int64_t step, int *status, cudaStream_t st)
+{
+    Psi3Args a;
+    a.g = g;
+    a.psi = psi;
+    a.u = u;
+    a.out = out;
+    a.E = E;
+    a.A = A;
+    a.B = B;
+    a.K = K;
+    a.M = M;
+    a.kT = kT;
+    a.advect = advect;
+    a.heun = heun;
+    a.key = key;
+    a.step = step;
+    const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + PS_ZC - 1) / PS_ZC);
+    const size_t base = sizeof(float) * (4 * H3N + 3 * H2N);
+    if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, status, st);
+    if (stage == 1) {
+        if (noise) return launch_dyn(psi3_fd_kernel<1, true>, grid, base + sizeof(float) * 13 * H1N, st, a);
+        return launch_dyn(psi3_fd_kernel<1, false>, grid, base, st, a);
+    }
+    return launch_dyn(psi3_fd_kernel<2, false>, grid, base, st, a);
+}
+
+}  // namespace flb
