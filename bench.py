@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=40,
+                    help="steps of the 256-replica ensemble timed batched vs plain (0: skip)")
     return ap.parse_args()
 
 
@@ -153,6 +155,39 @@ def lb_traffic(storage: int, n_sites: int):
         return None
 
 
+def ensemble_batched_vs_plain(F, I, steps, local, rank):
+    """256 uneven D3Q19 replicas (64 each of 16^3, 24^3, 32^3, 48^3, kT_r in
+    [1e-5, 1e-4], seed 1 + r): aggregate MLUPS of the batched launch (one launch
+    per phase for all replicas, CUDA-graph replay) against the plain
+    per-replica launch sequence, same state, same number of steps."""
+    import torch
+    reps = I.ensemble()
+    ps = [F.flb_params_default(nx=d["nx"], ny=d["ny"], nz=d["nz"], tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"],
+                               K=d["K"], M=d["M"], psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, seed=d["seed"] + 1000 * rank)
+          for d in reps]
+    sites = sum(p.nx * p.ny * p.nz for p in ps)
+    out = {"workload": "256 D3Q19 replicas (64 each of 16^3, 24^3, 32^3, 48^3), FV, Heun", "sites": sites,
+           "steps": steps}
+    for mode, key in ((F.FLB_MODE_PLAIN, "plain"), (F.FLB_MODE_BATCHED, "batched")):
+        s = F.Solver(ps, device=f"cuda:{local}")
+        s.set_mode(mode)
+        s.step(3)
+        s.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[key + "_mlups"] = sites * steps / (ms / 1e3) / 1e6
+        out[key + "_ms_per_step"] = ms / steps
+        del s
+        torch.cuda.empty_cache()
+    out["ratio"] = out["batched_mlups"] / out["plain_mlups"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -258,6 +293,11 @@ def run_ours(args):
         h2d = 4 * P * (1 + 3)
         e2e = {"value": N * args.steps / (t1 - t0) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 72 / args.steps}
+    ens = None
+    if args.ensemble_steps > 0:
+        del s
+        torch.cuda.empty_cache()
+        ens = ensemble_batched_vs_plain(F, I, args.ensemble_steps, local, rank)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)
@@ -280,6 +320,7 @@ def run_ours(args):
             "step_roofline": {"alg_bytes_per_site": ALG_BYTES_SITE[storage], "achieved_gbs": step_gbs,
                               "frac": step_gbs / peak, "kernel_ms_per_step": {k: v / kp for k, v in kms.items()}},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "batched_vs_plain": ens,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -168,6 +168,16 @@ struct flb_handle {
     int64_t launches = 0;
     double *red_partial = nullptr, *red_out = nullptr;
     int *status = nullptr;  // device status word: kernels latch FLB_ETIMEOUT here
+    // batched mode: descriptor table, block lists, device step counter, captured graph
+    BatchRep *b_reps = nullptr;
+    BatchBlock *b_mu = nullptr, *b_lb = nullptr, *b_psi = nullptr;
+    int b_nmu = 0, b_nlb = 0, b_npsi = 0;
+    long long *b_dstep = nullptr;
+    std::vector<BatchRep> b_host;
+    std::vector<BatchBlock> b_blocks_host;
+    cudaGraph_t b_graph = nullptr;
+    cudaGraphExec_t b_exec = nullptr;
+    bool b_lists_ok = false;
     float2 *X1 = nullptr, *X2 = nullptr;
     float *heights = nullptr, *win = nullptr;
     char *ws = nullptr;
@@ -181,6 +191,8 @@ struct flb_handle {
     ~flb_handle()
     {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (b_exec) cudaGraphExecDestroy(b_exec);
+        if (b_graph) cudaGraphDestroy(b_graph);
     }
 };
 
@@ -203,6 +215,23 @@ size_t carve_all(flb_handle &h, char *base)
         }
         maxq = std::max<long long>(maxq, r.q);
     }
+    // batched-mode block lists (3D replicas only)
+    int nmu = 0, nlb = 0, npsi = 0;
+    for (Rep &r : h.reps) {
+        if (r.dim != 3) continue;
+        const Geom &g = r.g;
+        nmu += ((g.nx + 2 + LB_BX - 1) / LB_BX) * ((g.ny + 2 + LB_BY - 1) / LB_BY) * ((g.nz + 2 + LB_BZ - 1) / LB_BZ);
+        nlb += ((g.nx + LB_BX - 1) / LB_BX) * ((g.ny + LB_BY - 1) / LB_BY) * ((g.nz + LB_BZ - 1) / LB_BZ);
+        npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC - 1) / PS_ZC);
+    }
+    h.b_nmu = nmu;
+    h.b_nlb = nlb;
+    h.b_npsi = npsi;
+    h.b_reps = cv.take<BatchRep>(h.reps.size());
+    h.b_mu = cv.take<BatchBlock>((size_t)std::max(nmu, 1));
+    h.b_lb = cv.take<BatchBlock>((size_t)std::max(nlb, 1));
+    h.b_psi = cv.take<BatchBlock>((size_t)std::max(npsi, 1));
+    h.b_dstep = cv.take<long long>(1);
     h.red_partial = cv.take<double>((size_t)RED_MAX_BLOCKS * NRED);
     h.red_out = cv.take<double>(NRED);
     h.status = cv.take<int>(1);
@@ -516,12 +545,176 @@ int take_status(flb_handle *h)
     return s;
 }
 
+// ---- batched mode ---------------------------------------------------------
+bool batch_supported(const flb_handle *h)
+{
+    for (const Rep &r : h->reps)
+        if (r.dim != 3 || r.p.psi_scheme != FLB_FV) return false;
+    return !h->reps.empty();
+}
+
+int batch_upload_lists(flb_handle *h)
+{
+    std::vector<BatchBlock> &v = h->b_blocks_host;
+    v.clear();
+    for (int r = 0; r < (int)h->reps.size(); ++r) {
+        const Geom &g = h->reps[(size_t)r].g;
+        for (int bz = 0; bz < (g.nz + 2 + LB_BZ - 1) / LB_BZ; ++bz)
+            for (int by = 0; by < (g.ny + 2 + LB_BY - 1) / LB_BY; ++by)
+                for (int bx = 0; bx < (g.nx + 2 + LB_BX - 1) / LB_BX; ++bx) v.push_back({r, bx, by, bz});
+    }
+    const size_t nmu = v.size();
+    for (int r = 0; r < (int)h->reps.size(); ++r) {
+        const Geom &g = h->reps[(size_t)r].g;
+        for (int bz = 0; bz < (g.nz + LB_BZ - 1) / LB_BZ; ++bz)
+            for (int by = 0; by < (g.ny + LB_BY - 1) / LB_BY; ++by)
+                for (int bx = 0; bx < (g.nx + LB_BX - 1) / LB_BX; ++bx) v.push_back({r, bx, by, bz});
+    }
+    const size_t nlb = v.size() - nmu;
+    for (int r = 0; r < (int)h->reps.size(); ++r) {
+        const Geom &g = h->reps[(size_t)r].g;
+        for (int bz = 0; bz < (g.nz + PS_ZC - 1) / PS_ZC; ++bz)
+            for (int by = 0; by < (g.ny + PS_TY - 1) / PS_TY; ++by)
+                for (int bx = 0; bx < (g.nx + PS_TX - 1) / PS_TX; ++bx) v.push_back({r, bx, by, bz});
+    }
+    const size_t npsi = v.size() - nmu - nlb;
+    if ((int)nmu != h->b_nmu || (int)nlb != h->b_nlb || (int)npsi != h->b_npsi) return FLB_EINVAL;
+    int rc = cuerr(cudaMemcpyAsync(h->b_mu, v.data(), nmu * sizeof(BatchBlock), cudaMemcpyHostToDevice, h->st));
+    if (rc == FLB_OK)
+        rc = cuerr(cudaMemcpyAsync(h->b_lb, v.data() + nmu, nlb * sizeof(BatchBlock), cudaMemcpyHostToDevice, h->st));
+    if (rc == FLB_OK)
+        rc = cuerr(cudaMemcpyAsync(h->b_psi, v.data() + nmu + nlb, npsi * sizeof(BatchBlock), cudaMemcpyHostToDevice,
+                                   h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    h->b_lists_ok = rc == FLB_OK;
+    return rc;
+}
+
+// Write the descriptor table for the current state and reset the device step counter.
+int batch_upload_table(flb_handle *h)
+{
+    std::vector<BatchRep> &t = h->b_host;
+    t.assign(h->reps.size(), BatchRep());
+    for (size_t k = 0; k < h->reps.size(); ++k) {
+        Rep &r = h->reps[k];
+        BatchRep &d = t[k];
+        const Geom &g = r.g;
+        d.lb = lb_args(r, r.psi[r.pcur]);
+        d.psi[0] = r.psi[r.pcur];
+        d.psi[1] = r.psi[r.pcur ^ 1];
+        d.psis = r.psis;
+        d.E = r.E;
+        d.A = (float)r.p.A;
+        d.B = (float)r.p.B;
+        d.K = (float)r.p.K;
+        d.M = (float)r.p.M;
+        d.heun = r.p.integrator == FLB_HEUN;
+        d.advect = (r.p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
+        d.noise = r.p.kT > 0 && r.p.M > 0;
+        const uint64_t pd[3] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz};
+        const uint64_t ps[2] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4};
+        const uint32_t pb[3] = {(uint32_t)(PS_TX + 8), (uint32_t)(PS_TY + 6), 1};
+        for (int j = 0; j < 2; ++j)
+            if (encode_tensor_map_f32(&d.map_psi[j], d.psi[j], 3, pd, ps, pb) != cudaSuccess) return FLB_ECUDA;
+        if (d.heun && encode_tensor_map_f32(&d.map_psis, r.psis, 3, pd, ps, pb) != cudaSuccess) return FLB_ECUDA;
+        const uint64_t ud[4] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz, 3};
+        const uint64_t us[3] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4, (uint64_t)g.pn * 4};
+        const uint32_t ub[4] = {(uint32_t)(PS_TX + 8), (uint32_t)(PS_TY + 2), 1, 3};
+        if (encode_tensor_map_f32(&d.map_u, r.u, 4, ud, us, ub) != cudaSuccess) return FLB_ECUDA;
+    }
+    int rc = cuerr(cudaMemcpyAsync(h->b_reps, t.data(), t.size() * sizeof(BatchRep), cudaMemcpyHostToDevice, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaMemsetAsync(h->b_dstep, 0, sizeof(long long), h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    return rc;
+}
+
+BatchLists batch_lists(flb_handle *h)
+{
+    BatchLists L;
+    L.reps = h->b_reps;
+    L.mu = h->b_mu;
+    L.lb = h->b_lb;
+    L.psi = h->b_psi;
+    L.nmu = h->b_nmu;
+    L.nlb = h->b_nlb;
+    L.npsi = h->b_npsi;
+    L.dstep = h->b_dstep;
+    L.status = h->status;
+    return L;
+}
+
+int batch_kernels_per_step(const flb_handle *h)
+{
+    const flb_params &p = h->reps[0].p;
+    return 1 + 1 + 1 + (p.integrator == FLB_HEUN ? 1 : 0) + 1;
+}
+
+// Capture one batched step into a CUDA graph (once per handle).
+int batch_capture(flb_handle *h)
+{
+    if (h->b_exec) return FLB_OK;
+    bool ghost = false, force = false, noise = false;
+    for (const Rep &r : h->reps) {
+        ghost |= r.gamma_g != 0.f;
+        force |= (r.p.coupling & FLB_COUPLE_FORCE) != 0;
+        noise |= r.p.kT > 0 && r.p.M > 0;
+    }
+    const flb_params &p0 = h->reps[0].p;
+    const BatchLists L = batch_lists(h);
+    // the kernels' attributes are set by one launch outside the capture on a zero-block list
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return FLB_ECUDA;
+    const cudaError_t e = launch_batch_step(L, p0.storage, ghost, force, 1, p0.integrator == FLB_HEUN, noise, h->st);
+    const cudaError_t e2 = cudaStreamEndCapture(h->st, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return FLB_ECUDA;
+    }
+    if (cudaGraphInstantiate(&h->b_exec, gr, 0) != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        h->b_exec = nullptr;
+        return FLB_ECUDA;
+    }
+    h->b_graph = gr;
+    return FLB_OK;
+}
+
 Rep *get_rep(flb_handle *h, int32_t rep)
 {
     if (!h || rep < 0 || rep >= (int32_t)h->reps.size()) return nullptr;
     return &h->reps[(size_t)rep];
 }
 
+}  // namespace
+
+namespace {
+int step_batched(flb_handle *h, int64_t n)
+{
+    if (!batch_supported(h)) return FLB_EUNSUPPORTED;
+    int rc = FLB_OK;
+    if (!h->b_lists_ok) rc = batch_upload_lists(h);
+    if (rc == FLB_OK) rc = batch_upload_table(h);
+    if (rc == FLB_OK) rc = batch_capture(h);
+    if (rc != FLB_OK) return rc;
+    const int kps = batch_kernels_per_step(h);
+    for (int64_t k = 0; k < n; ++k) {
+        cudaEvent_t e0 = mark(h);
+        if (cudaGraphLaunch(h->b_exec, h->st) != cudaSuccess) return FLB_ECUDA;
+        h->launches += kps;
+        span(h, 0, e0, mark(h), kps);
+        for (Rep &r : h->reps) {
+            r.cur ^= 1;
+            r.pcur ^= 1;
+            r.step += 1;
+        }
+        if (h->sample_every > 0 && h->sample_mask && h->reps[0].step % h->sample_every == 0)
+            for (Rep &r : h->reps) {
+                const int rs = sample_rep(h, r, h->sample_mask);
+                if (rs != FLB_OK) return rs;
+            }
+    }
+    return FLB_OK;
+}
 }  // namespace
 
 // window gather (flb_obs.cu)
@@ -716,7 +909,7 @@ int flb_get_window(flb_handle *h, int32_t rep, int32_t x0, int32_t y0, int32_t z
 int flb_step(flb_handle *h, int64_t n)
 {
     if (!h || n < 0) return FLB_EINVAL;
-    if (h->mode != FLB_MODE_PLAIN) return FLB_EUNSUPPORTED;
+    if (h->mode == FLB_MODE_BATCHED) return n > 0 ? step_batched(h, n) : FLB_OK;
     for (int64_t k = 0; k < n; ++k) {
         for (Rep &r : h->reps) {
             const int rc = step_rep(h, r);

@@ -3,6 +3,7 @@
 // psi/mu/u fields, and the argument blocks the host passes to each kernel.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -87,6 +88,10 @@ __device__ __forceinline__ void normals4(const PhiloxKey &K, int64_t step, uint3
 constexpr int GX = 4;  // 16-byte aligned rows of FP32
 constexpr int GY = 3;
 constexpr int GZ3 = 3;
+
+// launch geometry of the 3D kernels (shared with the host for the batched block lists)
+constexpr int LB_BX = 32, LB_BY = 4, LB_BZ = 2;   // collide-stream and mu: one thread per site
+constexpr int PS_TX = 32, PS_TY = 16, PS_ZC = 64;  // psi stage: column tile and z chunk
 
 struct Geom {
     int dim, nx, ny, nz;   // nz = 1 in 2D
@@ -179,6 +184,42 @@ struct NoiseArgs {
     PhiloxKey key;
     int64_t step;
 };
+
+// ---------------------------------------------------------------------------
+// Batched mode: every replica of a handle advances in one launch per phase.
+// Each launch walks a block list (replica, block coordinates); per-replica data
+// sit in a device table of BatchRep records.  The step counter is a device
+// value (dstep, steps since the table was written), so one captured graph of a
+// step can be replayed: on even dstep the "A" buffers are current, on odd the
+// "B" buffers.
+// ---------------------------------------------------------------------------
+struct alignas(128) BatchRep {
+    CUtensorMap map_psi[2];  // tensor maps of psiA, psiB
+    CUtensorMap map_psis;    // tensor map of psi* (Heun)
+    CUtensorMap map_u;       // tensor map of u (3 components)
+    LBArgs lb;               // fin = fA, fout = fB, psi = psiA; step = step0
+    float *psi[2];           // psiA, psiB
+    float *psis, *E;
+    float A, B, K, M;
+    int heun, advect, noise;
+};
+
+struct BatchBlock {
+    int rep, bx, by, bz;
+};
+
+struct BatchLists {
+    const BatchRep *reps;
+    const BatchBlock *mu, *lb, *psi;
+    int nmu, nlb, npsi;
+    const long long *dstep;
+    int *status;
+};
+
+cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                                  const uint64_t *strides_bytes, const uint32_t *box);
+cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
+                              bool noise, cudaStream_t st);
 
 // host launchers (flb_lb.cu, flb_psi.cu, flb_obs.cu)
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);

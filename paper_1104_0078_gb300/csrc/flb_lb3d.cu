@@ -205,18 +205,18 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
 
 // One thread per site on a 3D grid of 32 x 4 x 2 blocks (a warp covers 32
 // consecutive x, so every population plane is read and written in full rows).
-constexpr int LB_BX = 32, LB_BY = 4, LB_BZ = 2;
 
+// One block of the collide-stream (block coordinates bx, by, bz of the 32 x 4 x 2 grid).
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_kernel(const LBArgs a)
+__device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int bz)
 {
     const Geom &g = a.g;
-    const int x = blockIdx.x * LB_BX + threadIdx.x;
-    const int y = blockIdx.y * LB_BY + threadIdx.y;
-    const int z = blockIdx.z * LB_BZ + threadIdx.z;
+    const int x = bx * LB_BX + threadIdx.x;
+    const int y = by * LB_BY + threadIdx.y;
+    const int z = bz * LB_BZ + threadIdx.z;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE) {
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) {
         // F = -psi grad_CD mu, mu read from its field (valid on the interior + 1)
         const int pi = g.pidx32(x, y, z);
         const int sy = g.px, sz = g.px * g.py;
@@ -229,13 +229,19 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_kernel(const LBArgs a
     lb_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
 }
 
-// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_kernel(const Geom g, const float *__restrict__ psi,
-                                                               float *__restrict__ mu, float A, float B, float K)
+template <typename T, bool GHOST_RELAX, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_kernel(const LBArgs a)
 {
-    const int x = (int)(blockIdx.x * LB_BX + threadIdx.x) - 1;
-    const int y = (int)(blockIdx.y * LB_BY + threadIdx.y) - 1;
-    const int z = (int)(blockIdx.z * LB_BZ + threadIdx.z) - 1;
+    lb3_block<T, GHOST_RELAX, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer
+__device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
+                                          float B, float K, int bx, int by, int bz)
+{
+    const int x = bx * LB_BX + (int)threadIdx.x - 1;
+    const int y = by * LB_BY + (int)threadIdx.y - 1;
+    const int z = bz * LB_BZ + (int)threadIdx.z - 1;
     if (x > g.nx || y > g.ny || z > g.nz) return;
     const int c = g.pidx32(x, y, z);
     const int Y = g.px, Z = g.px * g.py;
@@ -249,6 +255,68 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_kernel(const Geom g, 
                      ((__ldg(p + c - 1 - Y + Z) + __ldg(p + c + 1 - Y + Z)) + (__ldg(p + c - 1 + Y + Z) + __ldg(p + c + 1 + Y + Z)));
     const float ps = __ldg(p + c);
     mu[c] = A * ps + B * ps * ps * ps - K * (1.0f / 22.0f) * (6.f * n1 + 3.f * n2 + n3 - 80.f * ps);
+}
+
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_kernel(const Geom g, const float *__restrict__ psi,
+                                                               float *__restrict__ mu, float A, float B, float K)
+{
+    mu3_block(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_batch_kernel(const BatchLists L)
+{
+    const BatchBlock b = L.mu[blockIdx.x];
+    const BatchRep &r = L.reps[b.rep];
+    const int par = (int)(*L.dstep & 1);
+    mu3_block(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
+}
+
+template <typename T, bool GHOST_RELAX, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const BatchLists L)
+{
+    __shared__ LBArgs sa;
+    const BatchBlock b = L.lb[blockIdx.x];
+    const BatchRep &r = L.reps[b.rep];
+    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
+    {
+        const int *src = reinterpret_cast<const int *>(&r.lb);
+        int *dst = reinterpret_cast<int *>(&sa);
+        for (int k = tid; k < (int)(sizeof(LBArgs) / sizeof(int)); k += LB_BX * LB_BY * LB_BZ) dst[k] = src[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const long long ds = *L.dstep;
+        if (ds & 1) {
+            const void *t = sa.fin;
+            sa.fin = sa.fout;
+            sa.fout = const_cast<void *>(t);
+        }
+        sa.psi = r.psi[ds & 1];
+        sa.step = r.lb.step + ds;
+    }
+    __syncthreads();
+    lb3_block<T, GHOST_RELAX, FORCE>(sa, b.bx, b.by, b.bz);
+}
+
+cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)
+{
+    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    if (force && L.nmu > 0) {
+        mu3_batch_kernel<<<L.nmu, block, 0, st>>>(L);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+#define FLB_LB3B(T, G, F) lb3_batch_kernel<T, G, F><<<L.nlb, block, 0, st>>>(L)
+    if (storage == FLB_F16_DEV) {
+        if (ghost) { if (force) FLB_LB3B(__half, true, true); else FLB_LB3B(__half, true, false); }
+        else { if (force) FLB_LB3B(__half, false, true); else FLB_LB3B(__half, false, false); }
+    } else {
+        if (ghost) { if (force) FLB_LB3B(float, true, true); else FLB_LB3B(float, true, false); }
+        else { if (force) FLB_LB3B(float, false, true); else FLB_LB3B(float, false, false); }
+    }
+#undef FLB_LB3B
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)

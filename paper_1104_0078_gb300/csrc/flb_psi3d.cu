@@ -28,7 +28,6 @@
 
 namespace flb {
 
-constexpr int PS_TX = 32, PS_TY = 16, PS_ZC = 64;
 constexpr int PS_NT = PS_TX * PS_TY;
 constexpr int H3X = PS_TX + 6, H3Y = PS_TY + 6, H3N = H3X * H3Y;  // psi: tile + 3
 constexpr int H2X = PS_TX + 4, H2Y = PS_TY + 4, H2N = H2X * H2Y;  // mu: tile + 2
@@ -261,14 +260,15 @@ struct TmaArgs {
     int *status;
 };
 
+// One block (tile bx, by; z chunk bz).  psi_map / u_map: tensor maps of the stage
+// input psi and of the velocity (kernel parameters or global memory); tsmem: the
+// block's dynamic shared memory.
 template <int STAGE, bool NOISE>
-__global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
-                                                            const __grid_constant__ CUtensorMap u_map,
-                                                            const TmaArgs ta)
+__device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
+                                                  const Psi3Args &a, int *status, int bx, int by, int bz,
+                                                  float *tsmem)
 {
-    extern __shared__ __align__(1024) float tsmem[];
-    const Psi3Args &a = ta.a;
-    if (ta.status && *(volatile int *)ta.status != 0) return;  // an earlier block timed out: skip the work
+    if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
     float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
     float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
     float *smu = tus + T_U_DEPTH * TU_SLOT;              // [3][H2N]
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
     __shared__ int s_bad;
     const Geom &g = a.g;
     const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
-    const int x0 = blockIdx.x * PS_TX, y0 = blockIdx.y * PS_TY, z0 = blockIdx.z * PS_ZC;
+    const int x0 = bx * PS_TX, y0 = by * PS_TY, z0 = bz * PS_ZC;
     const int z1 = min(z0 + PS_ZC, g.nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < g.nx && y < g.ny;
@@ -312,12 +312,12 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
     auto issue_psi = [&](int pp) {
         const int s = (pp - pbase) % T_PSI_DEPTH;
         mbar_expect_tx(&bar_p[s], TP_N * 4);
-        tma_load_3d(tps + s * TP_SLOT, &psi_map, &bar_p[s], x0, y0, pp + g.gz);
+        tma_load_3d(tps + s * TP_SLOT, psi_map, &bar_p[s], x0, y0, pp + g.gz);
     };
     auto issue_u = [&](int qq) {
         const int s = (qq - ubase) % T_U_DEPTH;
         mbar_expect_tx(&bar_u[s], TU_N * 4);
-        tma_load_4d(tus + s * TU_SLOT, &u_map, &bar_u[s], x0, y0 + GY - 1, qq + g.gz, 0);
+        tma_load_4d(tus + s * TU_SLOT, u_map, &bar_u[s], x0, y0 + GY - 1, qq + g.gz, 0);
     };
     if (threadIdx.x == 0) {
         issue_psi(pbase);
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
         }
         {   // (a) psi plane p has landed
             const int s = (p - pbase) % T_PSI_DEPTH;
-            if (!mbar_wait(&bar_p[s], ((p - pbase) / T_PSI_DEPTH) & 1, ta.status)) s_bad = 1;
+            if (!mbar_wait(&bar_p[s], ((p - pbase) / T_PSI_DEPTH) & 1, status)) s_bad = 1;
             waited_p = p;
         }
         if (p - 1 >= z0 - 2) {  // (b) mu plane p-1, tile + 2
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
             const float *uq = tus;
             if (a.advect) {
                 const int s = (q - ubase) % T_U_DEPTH;
-                if (!mbar_wait(&bar_u[s], ((q - ubase) / T_U_DEPTH) & 1, ta.status)) s_bad = 1;
+                if (!mbar_wait(&bar_u[s], ((q - ubase) / T_U_DEPTH) & 1, status)) s_bad = 1;
                 waited_u = q;
                 uq = tus + s * TU_SLOT;
             }
@@ -430,6 +430,74 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
         for (int qq = waited_u + 1; qq <= last_u; ++qq)
             mbar_wait(&bar_u[(qq - ubase) % T_U_DEPTH], ((qq - ubase) / T_U_DEPTH) & 1, nullptr);
     }
+}
+
+template <int STAGE, bool NOISE>
+__global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
+                                                            const __grid_constant__ CUtensorMap u_map,
+                                                            const TmaArgs ta)
+{
+    extern __shared__ __align__(1024) float tsmem[];
+    psi3_fv_tma_block<STAGE, NOISE>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x, blockIdx.y, blockIdx.z, tsmem);
+}
+
+// batched: block b of the launch works on L.psi[b]
+template <int STAGE, bool NOISE>
+__global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLists L)
+{
+    extern __shared__ __align__(1024) float tsmem[];
+    __shared__ Psi3Args sa;
+    const BatchBlock b = L.psi[blockIdx.x];
+    const BatchRep &r = L.reps[b.rep];
+    const long long ds = *L.dstep;
+    const int par = (int)(ds & 1);
+    if (threadIdx.x == 0) {
+        sa.g = r.lb.g;
+        sa.psi = STAGE == 1 ? r.psi[par] : r.psis;
+        sa.u = r.lb.u;
+        sa.out = (STAGE == 1 && r.heun) ? r.psis : r.psi[par ^ 1];
+        sa.E = r.E;
+        sa.A = r.A;
+        sa.B = r.B;
+        sa.K = r.K;
+        sa.M = r.M;
+        sa.kT = r.noise ? r.lb.kT : 0.f;
+        sa.advect = r.advect;
+        sa.heun = r.heun;
+        sa.key = r.lb.key;
+        sa.step = r.lb.step + ds;
+    }
+    __syncthreads();
+    const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[par] : &r.map_psis;
+    psi3_fv_tma_block<STAGE, NOISE>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
+}
+
+__global__ void advance_kernel(long long *dstep) { *dstep += 1; }
+
+cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st);
+
+cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
+                              bool noise, cudaStream_t st)
+{
+    if (!scheme_fv) return cudaErrorNotSupported;
+    cudaError_t e = launch_lb3_batch(L, storage, ghost, force, st);
+    if (e != cudaSuccess) return e;
+    const size_t sm = sizeof(float) * ((size_t)T_PSI_DEPTH * TP_SLOT + (size_t)T_U_DEPTH * TU_SLOT + 3 * H2N + 9 * H1N);
+    auto go = [&](auto kernel, size_t bytes) {
+        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (r != cudaSuccess) return r;
+        kernel<<<L.npsi, PS_NT, bytes, st>>>(L);
+        return cudaGetLastError();
+    };
+    e = noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + sizeof(float) * 9 * H1N)
+              : go(psi3_fv_tma_batch_kernel<1, false>, sm);
+    if (e != cudaSuccess) return e;
+    if (heun) {
+        e = go(psi3_fv_tma_batch_kernel<2, false>, sm);
+        if (e != cudaSuccess) return e;
+    }
+    advance_kernel<<<1, 1, 0, st>>>(const_cast<long long *>(L.dstep));
+    return cudaGetLastError();
 }
 
 template <typename K>

@@ -1,0 +1,56 @@
+"""Parity at the full 512^3 quench size, in the launch configuration bench.py
+times: after two steps from the seeded start (rest populations, psi0 uniform in
+[-0.01, 0.01]) sampled sites are compared with the FP64 oracle run on a 32^3
+window around each (periodic window, counter ids of the global lattice).  Two
+steps of the FV/Heun path depend on psi0 within 12 cells and on the populations
+within 11, so the central 8^3 of each window is exact; plus conservation of mass
+and psi over the run."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1104_0078_gb300 as F
+from paper_1104_0078_gb300 import inputs as I
+
+from gpu_helpers import field_error
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def test_quench_512_windows_match_oracle():
+    d = dict(I.WORKLOADS["quench"])
+    n = 512
+    N = n ** 3
+    p = F.flb_params_default(nx=n, ny=n, nz=n, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
+                             psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, seed=d["seed"], sq_kmax=8)
+    psi0 = I.uniform_field(N, -0.01, 0.01, 11)
+    s = F.Solver(p)
+    s.set_fields(psi=psi0)
+    t0, _, _ = s.moments()
+    s.step(2)
+    t1, _, rc = s.moments()
+    assert rc == F.FLB_OK
+    assert abs(t1[0] - t0[0]) / N < 1e-6
+    psi_cube = psi0.reshape(n, n, n)
+    rng = np.random.default_rng(5)
+    W = 32
+    _, w = O.lattice(3, 19)
+    for origin in [(0, 0, 0), (n - 16, 100, 250), (240, 496, 8)] + [tuple(rng.integers(0, n, 3)) for _ in range(3)]:
+        x0, y0, z0 = (int(v) for v in origin)
+        fg, pg = s.get_window((x0, y0, z0), (W, W, W))
+        idx = [(np.arange(W) + o) % n for o in (z0, y0, x0)]
+        win_psi = psi_cube[np.ix_(*idx)].reshape(-1)
+        op = O.Params(dim=3, q=19, nx=W, ny=W, nz=W, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"],
+                      M=d["M"], scheme=1, integrator=2, coupling=3, seed=d["seed"], gdims=(n, n, n),
+                      origin=(x0, y0, z0))
+        st = O.State.rest(op, psi=win_psi)
+        st.advance(2)
+        c = slice(12, 20)
+        f_o = st.f.reshape(19, W, W, W)[:, c, c, c].reshape(19, -1)
+        f_g = fg.reshape(19, W, W, W)[:, c, c, c].reshape(19, -1)
+        p_o = st.psi.reshape(W, W, W)[c, c, c].reshape(-1)
+        p_g = pg.reshape(W, W, W)[c, c, c].reshape(-1)
+        assert field_error(f_g, f_o, w[:, None]) < TOL
+        assert field_error(p_g, p_o, p_o.mean()) < TOL

@@ -1,0 +1,108 @@
+"""Statistical checks of the GPU path against what the paper fixes:
+equipartition <u_a^2> = kT/rho0 and the lattice static structure factor
+S(q) = kT/(A - K L_SO(q)) (Eq. test2 with the SO symbol), including the exact
+discrete-time factor of the integrator and the transient from psi0 = 0, on the
+bulk 2D (D2Q9, FD) and bulk 3D (D3Q19, FV) workloads, and the acceptance test of
+FP16 population storage against the same theory."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1104_0078_gb300 as F
+from oracle import theory as T
+from paper_1104_0078_gb300 import inputs as I
+
+from gpu_helpers import flb_params, oracle_params
+
+pytestmark = [pytest.mark.gpu]
+
+
+def _measure(d, nsteps, t_start, every, storage=F.FLB_F32_DEV):
+    p = flb_params(d, storage=storage)
+    s = F.Solver(p)
+    s.step(t_start)
+    s.sq_reset()
+    u2 = np.zeros(p.dim)
+    nu = 0
+    times = []
+    for t in range(t_start, nsteps, every):
+        s.step(every)
+        s.sample(1)
+        times.append(t + every)
+        _, uu, rc = s.moments()
+        assert rc == F.FLB_OK
+        u2 += uu
+        nu += 1
+    S, ns = s.structure_factor()
+    return S, ns, u2 / nu, np.array(times)
+
+
+def _theory(d, times):
+    """Expected mean spectrum over the sample times, the mobility symbol, the
+    wavevectors and each mode's number of independent samples, ~ 2 lambda T
+    (capped by the sample count)."""
+    op = oracle_params(d)
+    qg = T.q_grid(op.shape)
+    if op.dim == 2:
+        qg[..., 2] = 0
+        Lso = T.L_so_2d(qg)
+    else:
+        Lso = T.L_so(qg)
+    c, w = O.lattice(op.dim, op.q)
+    Lm = Lso if op.scheme == 0 else T.L_fv(qg, c, w)
+    base = T.static_structure_factor(qg, op, Lm)
+    g = T.amplification(-T.lam(qg, op, Lm), op.integrator)
+    trans = np.mean([1.0 - g ** (2 * t) for t in times], axis=0)
+    lmb = T.lam(qg, op, Lm)
+    span = times[-1] - times[0]
+    n_ind = np.minimum(2 * lmb * span, len(times))
+    return base * trans, n_ind, qg
+
+
+def _shell_check(S, th, n_ind, qg, tol, min_eff=1e4):
+    """Mean of S/theory per |q| shell, over shells whose modes carry at least
+    min_eff independent samples in total (relative s.d. <= 1/sqrt(min_eff))."""
+    ok = n_ind > 2.0
+    qm = np.sqrt((qg ** 2).sum(-1))
+    edges = np.linspace(0, qm.max() + 1e-9, 13)
+    checked = 0
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = ok & (qm >= lo) & (qm < hi)
+        if n_ind[sel].sum() >= min_eff:
+            r = S[sel] / th[sel]
+            assert abs(r.mean() - 1) < tol, (lo, hi, r.mean(), sel.sum())
+            checked += 1
+    assert checked >= 4
+
+
+def test_bulk_2d_structure_factor_and_equipartition():
+    d = dict(I.WORKLOADS["bulk_2d"], integrator=2)
+    S, ns, u2, times = _measure(d, 20000, 2000, 10)
+    th, n_ind, qg = _theory(d, times)
+    _shell_check(S.reshape(1, 64, 64), th, n_ind, qg, tol=0.03)
+    assert np.all(np.abs(u2 / d["kT"] - 1) < 0.02)
+
+
+def test_bulk_3d_structure_factor_and_equipartition():
+    d = dict(I.WORKLOADS["bulk_3d"], integrator=2)
+    S, ns, u2, times = _measure(d, 10000, 1000, 10)
+    th, n_ind, qg = _theory(d, times)
+    _shell_check(S.reshape(64, 64, 64), th, n_ind, qg, tol=0.02)
+    assert np.all(np.abs(u2 / d["kT"] - 1) < 0.01)
+
+
+def test_fp16_storage_acceptance():
+    # FP16 deviations are accepted if equipartition and S(q) stay within the
+    # tolerances of the FP32 path: against theory, and shell by shell against an
+    # FP32 run of the same workload (bulk 3D parameters on 32^3)
+    d = dict(I.WORKLOADS["bulk_3d"], nx=32, ny=32, nz=32, integrator=2)
+    res = {}
+    for st in (F.FLB_F32_DEV, F.FLB_F16_DEV):
+        S, ns, u2, times = _measure(d, 12000, 1000, 10, storage=st)
+        res[st] = (S.reshape(32, 32, 32), u2)
+    th, n_ind, qg = _theory(d, times)
+    for st in res:
+        _shell_check(res[st][0], th, n_ind, qg, tol=0.03)
+        assert np.all(np.abs(res[st][1] / d["kT"] - 1) < 0.03)
+    _shell_check(res[F.FLB_F16_DEV][0], res[F.FLB_F32_DEV][0], n_ind, qg, tol=0.03)
+    assert np.all(np.abs(res[F.FLB_F16_DEV][1] / res[F.FLB_F32_DEV][1] - 1) < 0.03)
