@@ -144,7 +144,7 @@ def lb_traffic(storage: int, n_sites: int):
     """DRAM bytes per LB launch from the committed ncu summary, if it was taken on
     the current kernel source; scaled by sites when the capture was smaller."""
     path = os.path.join(ROOT, "profiles", "lb_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_1104_0078_gb300", "csrc", "flb_lb.cu")
+    src = os.path.join(ROOT, "paper_1104_0078_gb300", "csrc", "flb_lb3d.cu")
     try:
         rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
