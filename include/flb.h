@@ -65,8 +65,8 @@ extern "C" {
 /*
  * Parameters of one lattice (one replica).  Names follow the paper.
  *   dim, q      : 2 and 9 (D2Q9) or 3 and 19 (D3Q19).
- *   nx, ny, nz  : lattice size, each >= 4 (nz is ignored and taken as 1 in 2D);
- *                 nx*ny*nz < 2^31.
+ *   nx, ny, nz  : lattice size, each in [4, 4096] (nz is ignored and taken as 1
+ *                 in 2D); nx*ny*nz < 2^31.
  *   rho0        : reference density, > 0 (the populations are stored as
  *                 deviations from w_i rho0).
  *   tau         : the paper's relaxation time (App. B): omega = 1/(tau + 1/2),

@@ -90,6 +90,7 @@ bool valid(const flb_params &p)
     if (p.storage != FLB_F32_DEV && p.storage != FLB_F16_DEV) return false;
     if (p.coupling < 0 || p.coupling > 3) return false;
     if (p.sq_kmax < 0) return false;
+    if (p.nx > 4096 || p.ny > 4096 || (p.dim == 3 && p.nz > 4096)) return false;  // DFT twiddle tables
     return true;
 }
 

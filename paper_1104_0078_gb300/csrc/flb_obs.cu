@@ -121,9 +121,21 @@ __device__ __forceinline__ float2 twiddle(int k, int x, int n)
     return make_float2(c, -s);
 }
 
+// Twiddle table e^{-2 pi i m / n}, m < n, in shared memory (n <= TW_MAX); each
+// output then walks its phase index m = k x mod n by additions.
+constexpr int TW_MAX = 4096;
+
+__device__ __forceinline__ void fill_twiddles(float2 *tw, int n)
+{
+    for (int m = threadIdx.x; m < n; m += blockDim.x) tw[m] = twiddle(1, m, n);
+    __syncthreads();
+}
+
 // X1[(z*ny + y)*Kx + jx] = sum_x in(x,y,z) e^{-i qx x}
 __global__ void dft_x_kernel(DftArgs a)
 {
+    extern __shared__ float2 tw[];
+    fill_twiddles(tw, a.nx);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tot = (long long)a.Kx * a.ny * a.nz;
     if (t >= tot) return;
@@ -133,11 +145,14 @@ __global__ void dft_x_kernel(DftArgs a)
     const int k = kval(jx, a.nx, a.Kx);
     const float *src = a.in + a.off + (long long)y * a.sy + (long long)z * a.sz;
     float re = 0.f, im = 0.f;
+    int m = 0;
     for (int x = 0; x < a.nx; ++x) {
         const float v = src[x];
-        const float2 w = twiddle(k, x, a.nx);
+        const float2 w = tw[m];
         re = fmaf(v, w.x, re);
         im = fmaf(v, w.y, im);
+        m += k;
+        if (m >= a.nx) m -= a.nx;
     }
     a.X1[t] = make_float2(re, im);
 }
@@ -145,6 +160,8 @@ __global__ void dft_x_kernel(DftArgs a)
 // X2[(z*Ky + jy)*Kx + jx] = sum_y X1[(z*ny + y)*Kx + jx] e^{-i qy y}
 __global__ void dft_y_kernel(DftArgs a)
 {
+    extern __shared__ float2 tw[];
+    fill_twiddles(tw, a.ny);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tot = (long long)a.Kx * a.Ky * a.nz;
     if (t >= tot) return;
@@ -153,11 +170,14 @@ __global__ void dft_y_kernel(DftArgs a)
     const int z = (int)(t / ((long long)a.Kx * a.Ky));
     const int k = kval(jy, a.ny, a.Ky);
     float re = 0.f, im = 0.f;
+    int m = 0;
     for (int y = 0; y < a.ny; ++y) {
         const float2 v = a.X1[((long long)z * a.ny + y) * a.Kx + jx];
-        const float2 w = twiddle(k, y, a.ny);
+        const float2 w = tw[m];
         re += v.x * w.x - v.y * w.y;
         im += v.x * w.y + v.y * w.x;
+        m += k;
+        if (m >= a.ny) m -= a.ny;
     }
     a.X2[t] = make_float2(re, im);
 }
@@ -165,6 +185,8 @@ __global__ void dft_y_kernel(DftArgs a)
 // S[(jz*Ky + jy)*Kx + jx] += scale |sum_z X2[(z*Ky + jy)*Kx + jx] e^{-i qz z}|^2  (FP64)
 __global__ void dft_z_acc_kernel(DftArgs a)
 {
+    extern __shared__ float2 tw[];
+    fill_twiddles(tw, a.nz);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long tot = (long long)a.Kx * a.Ky * a.Kz;
     if (t >= tot) return;
@@ -173,11 +195,14 @@ __global__ void dft_z_acc_kernel(DftArgs a)
     const int jz = (int)(t / plane);
     const int k = kval(jz, a.nz, a.Kz);
     double re = 0.0, im = 0.0;
+    int m = 0;
     for (int z = 0; z < a.nz; ++z) {
         const float2 v = a.X2[(long long)z * plane + xy];
-        const float2 w = twiddle(k, z, a.nz);
+        const float2 w = tw[m];
         re += (double)v.x * w.x - (double)v.y * w.y;
         im += (double)v.x * w.y + (double)v.y * w.x;
+        m += k;
+        if (m >= a.nz) m -= a.nz;
     }
     a.S[t] += a.scale * (re * re + im * im);
 }
@@ -186,9 +211,10 @@ cudaError_t launch_dft_accumulate(const DftArgs &a, cudaStream_t s)
 {
     const int bs = 256;
     long long n1 = (long long)a.Kx * a.ny * a.nz, n2 = (long long)a.Kx * a.Ky * a.nz, n3 = (long long)a.Kx * a.Ky * a.Kz;
-    dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, 0, s>>>(a);
-    dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, 0, s>>>(a);
-    dft_z_acc_kernel<<<(unsigned)((n3 + bs - 1) / bs), bs, 0, s>>>(a);
+    if (a.nx > TW_MAX || a.ny > TW_MAX || a.nz > TW_MAX) return cudaErrorInvalidValue;
+    dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, sizeof(float2) * a.nx, s>>>(a);
+    dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, sizeof(float2) * a.ny, s>>>(a);
+    dft_z_acc_kernel<<<(unsigned)((n3 + bs - 1) / bs), bs, sizeof(float2) * a.nz, s>>>(a);
     return cudaGetLastError();
 }
 

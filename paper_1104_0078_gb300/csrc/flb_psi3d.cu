@@ -100,6 +100,20 @@ __device__ __forceinline__ void make_regions(Regions &R, const Geom &g, int x0, 
     }
 }
 
+// Point k of a W x H region (W >= 32): rows' first 32 columns first, then the
+// W - 32 remaining columns of every row.
+__device__ __forceinline__ void region_point(int k, int W, int H, int &lx, int &ly)
+{
+    if (k < 32 * H) {
+        lx = k & 31;
+        ly = k >> 5;
+    } else {
+        const int r = k - 32 * H, e = W - 32;
+        lx = 32 + r % e;
+        ly = r / e;
+    }
+}
+
 // divergence (1/c_s^2) sum_i w_i c_i . V(r + c_i) of a vector field held in three
 // planes (z-1, z, z+1) of the tile + 1 frame: (1/6) axis + (1/12) diagonal links
 __device__ __forceinline__ float fv_div(const float *xm, const float *x0, const float *xp, const float *ym,
@@ -287,17 +301,25 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const int pbase = z0 - 3, ubase = z0 - 1;             // first psi / u plane of the chunk
     // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
     // psi-slot centre, u-slot offset, noise counter id
-    int c2[S2], c1[S1], p1[S1], u1[S1], n1[S1];
+    // Region points are dealt to threads row segment by row segment: the first
+    // 32 columns of every row (a full warp reads 32 consecutive words, free of
+    // bank conflicts), then the few remaining columns of all rows.
+    int c2[S2], d2[S2], c1[S1], d1[S1], p1[S1], u1[S1], n1[S1];
 #pragma unroll
     for (int j = 0; j < S2; ++j) {
-        const int k = threadIdx.x + j * PS_NT;
-        c2[j] = k < H2N ? (k % H2X + 2) + TB_X * (k / H2X + 1) : -1;
+        int lx, ly;
+        region_point(threadIdx.x + j * PS_NT, H2X, H2Y, lx, ly);
+        const bool ok = threadIdx.x + j * PS_NT < H2N;
+        c2[j] = ok ? (lx + 2) + TB_X * (ly + 1) : -1;
+        d2[j] = lx + H2X * ly;
     }
 #pragma unroll
     for (int j = 0; j < S1; ++j) {
-        const int k = threadIdx.x + j * PS_NT;
-        const int lx = k % H1X, ly = k / H1X;
-        c1[j] = k < H1N ? (lx + 1) + H2X * (ly + 1) : -1;
+        int lx, ly;
+        region_point(threadIdx.x + j * PS_NT, H1X, H1Y, lx, ly);
+        const bool ok = threadIdx.x + j * PS_NT < H1N;
+        c1[j] = ok ? (lx + 1) + H2X * (ly + 1) : -1;
+        d1[j] = lx + H1X * ly;
         p1[j] = (lx + 3) + TB_X * (ly + 2);
         u1[j] = (lx + 3) + TB_X * ly;
         n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
@@ -346,7 +368,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             float *dst = smu + ring3(p - 1) * H2N;
 #pragma unroll
             for (int j = 0; j < S2; ++j)
-                if (c2[j] >= 0) dst[threadIdx.x + j * PS_NT] = mu_point<TB_X>(pm, p0, pp, c2[j], a.A, a.B, k22);
+                if (c2[j] >= 0) dst[d2[j]] = mu_point<TB_X>(pm, p0, pp, c2[j], a.A, a.B, k22);
         }
         __syncthreads();
         if (s_bad) break;
@@ -367,7 +389,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             for (int j = 0; j < S1; ++j) {
                 const int c = c1[j];
                 if (c < 0) continue;
-                const int k = threadIdx.x + j * PS_NT;
+                const int k = d1[j];
                 const float gx = (1.f / 6.f) * (m0[c + 1] - m0[c - 1]) +
                                  (1.f / 12.f) * ((m0[c + 1 + H2X] + m0[c + 1 - H2X] - m0[c - 1 + H2X] - m0[c - 1 - H2X]) +
                                                  (mp[c + 1] + mm[c + 1] - mp[c - 1] - mm[c - 1]));
