@@ -84,7 +84,7 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     const float Sxy = sp[4] - sp[5], Sxz = sp[6] - sp[7], Syz = sp[8] - sp[9];
 
     const float rho = a.rho0 + drho;
-    const float irho = 1.0f / rho;
+    const float irho = __fdividef(1.0f, rho);  // ~2 ulp
     const float vx = (jx + 0.5f * Fx) * irho, vy = (jy + 0.5f * Fy) * irho, vz = (jz + 0.5f * Fz) * irho;
     store_padded(a.u, g, x, y, z, vx, 1);
     store_padded(a.u + g.pn, g, x, y, z, vy, 1);
@@ -135,7 +135,8 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
         normals4(a.key, a.step, sid, 0u, 1u, G + 4);
         normals4(a.key, a.step, sid, 0u, 2u, G + 8);
         normals4(a.key, a.step, sid, 0u, 3u, G + 12);
-        const float sq = sqrtf(3.0f * rho * a.kT);
+        const float mun = 3.0f * rho * a.kT;
+        const float sq = mun * rsqrtf(mun);  // sqrt(rho kT / c_s^2), ~2 ulp
         float n[15];
 #pragma unroll
         for (int t = 0; t < 15; ++t) n[t] = sq * a.namp[t] * G[t];

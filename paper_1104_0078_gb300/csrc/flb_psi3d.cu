@@ -348,7 +348,17 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     int last_p = pbase + 1, last_u = ubase - 1;  // highest plane issued (thread 0)
     int waited_p = pbase - 1, waited_u = ubase - 1;
 
+    // Rotating ring positions, advanced once per plane (no divisions in the loop):
+    // psi plane p sits in slot r6 of phase ph6; plane x of the mu / flux rings in
+    // slot (x - pbase) mod 3, m3 being that of p; the velocity of plane q = p - 2
+    // in slot ru of phase uph once q >= ubase.
+    int r6 = 0, ph6 = 0, m3 = 0, ru = 0, uph = 0;
     for (int p = z0 - 3; p <= z1 + 2; ++p) {
+        const int s1 = r6 == 0 ? T_PSI_DEPTH - 1 : r6 - 1;  // psi slots of p-1, p-2, p-3
+        const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
+        const int s3 = s2 == 0 ? T_PSI_DEPTH - 1 : s2 - 1;
+        const int mm1 = m3 == 0 ? 2 : m3 - 1;                 // ring slots of p-1 (== p-4), p-2
+        const int mm2 = mm1 == 0 ? 2 : mm1 - 1;
         __syncthreads();
         if (s_bad) break;
         if (threadIdx.x == 0) {
@@ -356,16 +366,12 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
             if (p >= ubase && p <= z1 && a.advect) { issue_u(p); last_u = p; }
         }
-        {   // (a) psi plane p has landed
-            const int s = (p - pbase) % T_PSI_DEPTH;
-            if (!mbar_wait(&bar_p[s], ((p - pbase) / T_PSI_DEPTH) & 1, status)) s_bad = 1;
-            waited_p = p;
-        }
+        // (a) psi plane p has landed
+        if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
+        waited_p = p;
         if (p - 1 >= z0 - 2) {  // (b) mu plane p-1, tile + 2
-            const float *pm = tps + ((p - 2 - pbase) % T_PSI_DEPTH) * TP_SLOT;
-            const float *p0 = tps + ((p - 1 - pbase) % T_PSI_DEPTH) * TP_SLOT;
-            const float *pp = tps + ((p - pbase) % T_PSI_DEPTH) * TP_SLOT;
-            float *dst = smu + ring3(p - 1) * H2N;
+            const float *pm = tps + s2 * TP_SLOT, *p0 = tps + s1 * TP_SLOT, *pp = tps + r6 * TP_SLOT;
+            float *dst = smu + mm1 * H2N;
 #pragma unroll
             for (int j = 0; j < S2; ++j)
                 if (c2[j] >= 0) dst[d2[j]] = mu_point<TB_X>(pm, p0, pp, c2[j], a.A, a.B, k22);
@@ -376,14 +382,16 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         if (q >= z0 - 1) {  // (c) node flux (and noise) on plane q, tile + 1
             const float *uq = tus;
             if (a.advect) {
-                const int s = (q - ubase) % T_U_DEPTH;
-                if (!mbar_wait(&bar_u[s], ((q - ubase) / T_U_DEPTH) & 1, status)) s_bad = 1;
+                if (!mbar_wait(&bar_u[ru], uph, status)) s_bad = 1;
                 waited_u = q;
-                uq = tus + s * TU_SLOT;
+                uq = tus + ru * TU_SLOT;
+                ru = ru == T_U_DEPTH - 1 ? 0 : ru + 1;
+                uph ^= ru == 0;
             }
-            const float *mm = smu + ring3(q - 1) * H2N, *m0 = smu + ring3(q) * H2N, *mp = smu + ring3(q + 1) * H2N;
-            const float *ps = tps + ((q - pbase) % T_PSI_DEPTH) * TP_SLOT;
-            float *J = sJ + ring3(q) * 3 * H1N;
+            const float *mm = smu + m3 * H2N, *m0 = smu + mm2 * H2N, *mp = smu + mm1 * H2N;
+            const float *ps = tps + s2 * TP_SLOT;
+            float *J = sJ + mm2 * 3 * H1N;
+            float *X = sX + mm2 * 3 * H1N;
             const int zid = g.nx * g.ny * wrapi(q, g.nz);
 #pragma unroll
             for (int j = 0; j < S1; ++j) {
@@ -412,7 +420,6 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 if (NOISE) {
                     float G[4];
                     normals4(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, G);
-                    float *X = sX + ring3(q) * 3 * H1N;
                     X[k] = sdx * G[0];
                     X[H1N + k] = sdx * G[1];
                     X[2 * H1N + k] = sdx * G[2];
@@ -422,9 +429,9 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         __syncthreads();
         if (s_bad) break;
         const int z = p - 3;
-        if (z >= z0 && active) {  // (d) stage output at plane z
+        if (z >= z0 && active) {  // (d) stage output at plane z: flux planes z-1, z, z+1
             const int c = (tx + 1) + H1X * (ty + 1);
-            const float *Jm = sJ + ring3(z - 1) * 3 * H1N, *J0 = sJ + ring3(z) * 3 * H1N, *Jp = sJ + ring3(z + 1) * 3 * H1N;
+            const float *Jm = sJ + mm1 * 3 * H1N, *J0 = sJ + m3 * 3 * H1N, *Jp = sJ + mm2 * 3 * H1N;
             const float Dd = fv_div(Jm, J0, Jp, Jm + H1N, J0 + H1N, Jp + H1N, Jm + 2 * H1N, J0 + 2 * H1N,
                                     Jp + 2 * H1N, c);
             const int si = x + g.nx * (y + g.ny * z);
@@ -432,11 +439,10 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             if (STAGE == 1) {
                 float Dn = 0.f;
                 if (NOISE) {
-                    const float *Xm = sX + ring3(z - 1) * 3 * H1N, *X0 = sX + ring3(z) * 3 * H1N,
-                                *Xp = sX + ring3(z + 1) * 3 * H1N;
+                    const float *Xm = sX + mm1 * 3 * H1N, *X0 = sX + m3 * 3 * H1N, *Xp = sX + mm2 * 3 * H1N;
                     Dn = fv_div(Xm, X0, Xp, Xm + H1N, X0 + H1N, Xp + H1N, Xm + 2 * H1N, X0 + 2 * H1N, Xp + 2 * H1N, c);
                 }
-                const float pv = tps[((z - pbase) % T_PSI_DEPTH) * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
+                const float pv = tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
                 out = pv + Dd + Dn;
                 if (a.heun) a.E[si] = pv + 0.5f * Dd + Dn;
             } else {
@@ -444,6 +450,9 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             }
             store_padded(a.out, g, x, y, z, out, 3);
         }
+        r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
+        ph6 ^= r6 == 0;
+        m3 = m3 == 2 ? 0 : m3 + 1;
     }
     // a bounded wait drains copies still in flight before the block exits
     if (threadIdx.x == 0) {
