@@ -52,6 +52,7 @@ class OraParams(ctypes.Structure):
         ("gext", ctypes.c_double * 3),
         ("gnx", ctypes.c_int32), ("gny", ctypes.c_int32), ("gnz", ctypes.c_int32),
         ("ox", ctypes.c_int32), ("oy", ctypes.c_int32), ("oz", ctypes.c_int32),
+        ("force_grad", ctypes.c_int32),
     ]
 
 
@@ -117,6 +118,7 @@ class Params:
     gext: tuple = (0.0, 0.0, 0.0)
     gdims: tuple = (0, 0, 0)
     origin: tuple = (0, 0, 0)
+    force_grad: int = 0      # 1 central difference (Sec. IV), 2 FV gradient (Eq. fvgrad), 0 matched to scheme
 
     @property
     def n(self) -> int:
@@ -139,6 +141,7 @@ class Params:
             p.gext[a] = self.gext[a]
         p.gnx, p.gny, p.gnz = self.gdims
         p.ox, p.oy, p.oz = self.origin
+        p.force_grad = self.force_grad
         return p
 
 

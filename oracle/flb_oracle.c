@@ -365,14 +365,36 @@ void ora_mu(const ora_params *p, const double *psi, double *mu)
     free(lap);
 }
 
-/* Force density on the fluid from the order parameter (Sec. IV): F = -psi grad mu,
- * with the symmetric nearest-neighbour central difference for grad mu.
+/* Force density on the fluid from the order parameter (Sec. IV): F = -psi grad mu.
  * Reading of the sign: the paper prints +psi grad mu; only -psi grad mu makes
  * the advective work u.F cancel the advective change of the free energy, so
- * that free energy plus kinetic energy cannot grow without noise. */
+ * that free energy plus kinetic energy cannot grow without noise.
+ * Gradient (force_grad): 1 -- the symmetric nearest-neighbour central difference
+ * of Sec. IV; 2 -- the finite-volume lattice gradient of Eq. (fvgrad),
+ * (1/c_s^2) sum_i w_i c_i mu(r + c_i); 0 -- the one matched to the psi scheme
+ * (1 for FD, 2 for FV).  Reading: the cancellation above holds on the lattice
+ * only if the force uses the gradient whose negative adjoint is the divergence
+ * that advects psi.  For the FD scheme (central-difference advection, Sec. V.A)
+ * that is the central difference; for the FV scheme (advection through link
+ * averages, Eq. fvflux) it is the FV gradient.  With the unmatched pair the
+ * exchange leaves a residue that noise drives into growing short-wavelength
+ * modes at an interface. */
 void ora_force(const ora_params *p, const double *psi, const double *mu, double *F)
 {
     box_t g = box_of(p);
+    const int grad = p->force_grad == 0 ? (p->scheme == 1 ? 2 : 1) : p->force_grad;
+    if (grad == 2) {
+        int32_t c[3 * 19];
+        double w[19];
+        ora_lattice(p->dim, p->q, c, w);
+        double *grad = (double *)malloc(sizeof(double) * 3 * g.n);
+        memset(grad, 0, sizeof(double) * 3 * g.n);
+        fv_gradient(&g, p->q, c, w, mu, grad);
+        for (size_t s = 0; s < g.n; ++s)
+            for (int a = 0; a < 3; ++a) F[a * g.n + s] = a < g.dim ? -psi[s] * grad[a * g.n + s] : 0.0;
+        free(grad);
+        return;
+    }
     for (size_t s = 0; s < g.n; ++s) {
         int x, y, z;
         coords(&g, s, &x, &y, &z);

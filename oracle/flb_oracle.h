@@ -27,6 +27,8 @@ typedef struct {
     double gext[3];         /* extra uniform body-force density (operator tests only) */
     int32_t gnx, gny, gnz;  /* global lattice for counter ids (0: this box) */
     int32_t ox, oy, oz;     /* origin of this box inside the global lattice */
+    int32_t force_grad;     /* gradient of mu in the force: 1 central difference, 2 FV lattice
+                               gradient, 0 the one matched to the psi scheme */
 } ora_params;
 
 int ora_threads(void);

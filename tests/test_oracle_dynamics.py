@@ -195,8 +195,9 @@ def test_force_sign_lowers_free_energy():
     # = sum psi u . grad mu to first order, so a velocity along -psi grad mu lowers
     # it and one along +psi grad mu raises it (Sec. II.B).  With M = 0 and no
     # noise psi changes by advection only; the first coupled step starts from
-    # rest and must create u = F/2 with F = -psi grad_CD mu (the reading of the
-    # force sign) -- the free-energy-lowering direction.
+    # rest and must create u = F/2 with F = -psi grad mu (the reading of the
+    # force sign; FV lattice gradient for this FV run) -- the free-energy-lowering
+    # direction.
     p = O.Params(dim=2, q=9, nx=32, ny=32, kT=0.0, A=-0.05, B=0.05, K=0.04, M=0.0, scheme=1,
                  integrator=2, coupling=3, tau=0.8)
     z, y, x = _coords(p)

@@ -100,7 +100,7 @@ def test_fd_noise_covariance(dim):
 
 def test_mu_and_force():
     # mu = A psi + B psi^3 - K lap_SO psi and F = -psi grad_CD mu at a few sites, brute force
-    p = O.Params(dim=3, q=19, nx=5, ny=4, nz=3, A=-0.06, B=0.07, K=0.04)
+    p = O.Params(dim=3, q=19, nx=5, ny=4, nz=3, A=-0.06, B=0.07, K=0.04, force_grad=1)
     rng = np.random.default_rng(0)
     psi = rng.normal(size=p.shape)
     mu = O.mu(p, psi).reshape(p.shape)
@@ -120,3 +120,54 @@ def test_mu_and_force():
         gy = 0.5 * (mu[z, (y + 1) % ny, x] - mu[z, (y - 1) % ny, x])
         gz = 0.5 * (mu[(z + 1) % nz, y, x] - mu[(z - 1) % nz, y, x])
         assert np.allclose(F[:, z, y, x], -psi[z, y, x] * np.array([gx, gy, gz]), atol=1e-12)
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_fv_force_gradient_symbol(dim, q):
+    # force_grad 2: F = -psi G mu with G the FV gradient of Eq. (fvgrad), whose
+    # Fourier symbol is i (1/c_s^2) sum_i w_i c_i sin(q.c_i) (Eq. fvft); the
+    # gradient is applied here spectrally, independently of the stencil
+    shape = (5, 6, 7) if dim == 3 else (1, 6, 7)
+    p = O.Params(dim=dim, q=q, nx=shape[2], ny=shape[1], nz=shape[0], A=-0.06, B=0.07, K=0.04, force_grad=2)
+    rng = np.random.default_rng(3)
+    psi = rng.normal(size=shape)
+    mu = O.mu(p, psi).reshape(shape)
+    F = O.force(p, psi).reshape(3, *shape)
+    c, w = O.lattice(dim, q)
+    G = T.fv_gradient_symbol(T.q_grid(shape), c, w)
+    mk = np.fft.fftn(mu)
+    for a in range(3):
+        grad = np.fft.ifftn(1j * G[..., a] * mk).real
+        assert np.allclose(F[a], -psi * grad, atol=1e-12)
+    # force_grad 0 follows the psi scheme: FV -> FV gradient, FD -> central difference
+    Fm = O.force(O.Params(**{**p.__dict__, "force_grad": 0, "scheme": 1}), psi)
+    assert np.array_equal(Fm, F.reshape(3, -1))
+    Fd = O.force(O.Params(**{**p.__dict__, "force_grad": 0, "scheme": 0}), psi)
+    assert np.array_equal(Fd, O.force(O.Params(**{**p.__dict__, "force_grad": 1}), psi))
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_force_advection_energy_exchange(dim, q, scheme):
+    # Work done by the force on the fluid, sum u.F, equals the free energy the
+    # advection of psi removes, sum mu div(u psi), exactly on the lattice when
+    # the force gradient is the negative adjoint of the advecting divergence
+    # (Sec. II.B energy balance; central difference for FD, Sec. V.A; FV
+    # gradient of Eq. (fvgrad) for the link-averaged flux of Eq. (fvflux)).
+    # The unmatched pair leaves a residue of the order of the terms themselves.
+    shape = (5, 6, 7) if dim == 3 else (1, 9, 8)
+    p = O.Params(dim=dim, q=q, nx=shape[2], ny=shape[1], nz=shape[0], A=-0.06, B=0.07, K=0.04, M=0.0,
+                 kT=0.0, scheme=scheme, coupling=3)
+    rng = np.random.default_rng(5 + scheme)
+    psi = rng.normal(size=p.n)
+    u = np.zeros((3, p.n))
+    u[:dim] = 0.05 * rng.normal(size=(dim, p.n))
+    mu = O.mu(p, psi)
+    R = O.psi_rhs(p, psi, u)                       # = -div(u psi) with M = 0, no noise
+    work = np.sum(u * O.force(p, psi))
+    dfree = np.sum(mu * R)
+    scale = np.sum(np.abs(mu * R))
+    assert scale > 0.1
+    assert abs(work + dfree) < 1e-13 * scale
+    other = O.Params(**{**p.__dict__, "force_grad": 2 if scheme == 0 else 1})
+    assert abs(np.sum(u * O.force(other, psi)) + dfree) > 1e-2 * scale
