@@ -413,7 +413,9 @@ void ora_force(const ora_params *p, const double *psi, const double *mu, double 
 static int noisy_mode_count(int dim) { return dim == 3 ? 15 : 6; }
 
 /* One collision at every site followed by streaming.  F is the force density
- * (3 x N; may be NULL), u_out receives v = (sum fbar c + F/2)/rho (d x N).
+ * (3 x N; may be NULL).  u_out (d x N) receives the velocity of the streamed
+ * populations, v = (sum fbar c + F/2)/rho with the F just applied: the fluid
+ * velocity after this step, which advects psi (see ora_step).
  *
  *  Momentum relations (App. B, last paragraph): rho = sum fbar,
  *    rho v = sum fbar c + F dt/2.  Reading: the paper's "rho F" multiplies a
@@ -470,7 +472,6 @@ static void lb_collide_stream(const ora_params *p, const box_t *g, double *f, co
         }
         double v[3] = {0, 0, 0};
         for (int a = 0; a < d; ++a) v[a] = (j[a] + 0.5 * Fv[a]) / rho;
-        if (u_out) for (int a = 0; a < d; ++a) u_out[(size_t)a * N + s] = v[a];
 
         /* stress of the auxiliary distribution, S = sum fbar Q, Q = c c - c_s^2 delta */
         double S[3][3] = {{0}};
@@ -533,6 +534,23 @@ static void lb_collide_stream(const ora_params *p, const box_t *g, double *f, co
     }
     memcpy(f, fnew, sizeof(double) * (size_t)q * N);
     free(fnew);
+
+    /* velocity of the new fluid state, with the force density applied in this step */
+    if (u_out) {
+#pragma omp parallel for schedule(static)
+        for (long long ss = 0; ss < (long long)N; ++ss) {
+            size_t s = (size_t)ss;
+            double rho = 0.0, j[3] = {0, 0, 0};
+            for (int i = 0; i < q; ++i) {
+                rho += f[(size_t)i * N + s];
+                for (int a = 0; a < d; ++a) j[a] += f[(size_t)i * N + s] * c[3 * i + a];
+            }
+            for (int a = 0; a < d; ++a) {
+                double Fa = p->gext[a] + (F ? F[(size_t)a * N + s] : 0.0);
+                u_out[(size_t)a * N + s] = (j[a] + 0.5 * Fa) / rho;
+            }
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -686,9 +704,13 @@ static void psi_step(const ora_params *p, const box_t *g, double *psi, const dou
 
 /* ------------------------------------------------------------------------- */
 /* Coupled step (Sec. VI: FLBE and SMOL marched alternately every step).       */
-/* Reading of the order: both halves read the state at time n -- the LB step   */
-/* uses mu(psi^n) for its force and produces u^n = v at time n; the psi step   */
-/* then advances psi^n with that u^n.                                          */
+/* Reading of the order (Gauss-Seidel): the LB step takes the force of psi^n   */
+/* and advances the fluid to n+1; the psi step then advances psi^n with the    */
+/* velocity of that new fluid state, (sum fbar^{n+1} c + F^n/2)/rho^{n+1}.     */
+/* Advecting with the velocity of the fluid BEFORE it received F^n (both       */
+/* halves reading time n) leaves the lattice's undamped staggered momentum     */
+/* mode (k = pi, flipped by every streaming step) coupled to psi at an         */
+/* interface through the force and the advection, and that loop grows.         */
 /* ------------------------------------------------------------------------- */
 int ora_step(const ora_params *p, double *f, double *psi, double *u, int64_t step0, int64_t nsteps)
 {

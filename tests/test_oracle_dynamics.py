@@ -195,9 +195,9 @@ def test_force_sign_lowers_free_energy():
     # = sum psi u . grad mu to first order, so a velocity along -psi grad mu lowers
     # it and one along +psi grad mu raises it (Sec. II.B).  With M = 0 and no
     # noise psi changes by advection only; the first coupled step starts from
-    # rest and must create u = F/2 with F = -psi grad mu (the reading of the
-    # force sign; FV lattice gradient for this FV run) -- the free-energy-lowering
-    # direction.
+    # rest, gives the fluid the momentum F = -psi grad mu (the reading of the
+    # force sign; FV lattice gradient for this FV run) and must lower the free
+    # energy.
     p = O.Params(dim=2, q=9, nx=32, ny=32, kT=0.0, A=-0.05, B=0.05, K=0.04, M=0.0, scheme=1,
                  integrator=2, coupling=3, tau=0.8)
     z, y, x = _coords(p)
@@ -213,7 +213,11 @@ def test_force_sign_lowers_free_energy():
         assert (O.free_energy(pp, st.psi) < Fe0) == lowers
     s = O.State.rest(p, psi=psi)
     s.advance(1)
-    assert np.allclose(s.u[:2], 0.5 * F[:2], rtol=0, atol=1e-15)
+    # the velocity that advected psi is that of the streamed populations with
+    # the force just applied, (sum fbar c + F/2)/rho (Gauss-Seidel coupling)
+    rho, j, _ = O.moments(p, s.f)
+    assert np.allclose(s.u[:2], (j[:2] + 0.5 * F[:2]) / rho, rtol=0, atol=1e-15)
+    assert np.allclose(j[:2].sum(axis=1), F[:2].sum(axis=1), rtol=0, atol=1e-14)
     assert O.free_energy(p, s.psi) < Fe0
 
 
@@ -370,3 +374,36 @@ def test_heights_of_linear_profile_brute_force():
     sp = O.height_spectrum(hh)
     assert abs(sp[0, 1] - (0.1 * 20 / 2) ** 2 / 20) < 1e-14 and abs(sp[0, 4] - sp[0, 1]) < 1e-14
     assert np.sum(sp) - sp[0, 1] - sp[0, 4] < 1e-14
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_interface_staggered_mode_is_stable(scheme):
+    # Noise-free planar interfaces (Sec. VI.C parameters -A = B = 0.05, K = 0.2,
+    # M = 0.1, tau = 0.45) at their lattice fixed point, perturbed by 1e-10.
+    # Streaming flips the staggered (k = pi) momentum every step and collision
+    # conserves it, so nothing in the fluid damps it; with psi advected by the
+    # velocity of the fluid before it received the force of psi^n, the force and
+    # the advection close a loop through the interface that grows by ~1% per
+    # step.  With the Gauss-Seidel coupling (psi follows the fluid step) the
+    # perturbation stays at its size (Sec. VI: FLBE and SMOL marched alternately).
+    nz = 32
+    A, B, K, M = -0.05, 0.05, 0.2, 0.1
+    p0 = O.Params(dim=2, q=9, nx=1, ny=nz, tau=0.45, kT=0.0, A=A, B=B, K=K, M=M, scheme=scheme, integrator=2,
+                  coupling=0)
+    y = np.arange(nz) + 0.0
+    l = np.sqrt(2 * K / -A)                            # Eq. (intthick) with |A|
+    psi0 = np.sqrt(-A / B) * np.tanh((y - nz / 4 - 0.5) / l) * np.tanh((3 * nz / 4 + 0.5 - y) / l)
+    s = O.State.rest(p0, psi=psi0)
+    s.advance(30000)                                   # diffusion alone: the lattice equilibrium profile
+    p = O.Params(**{**p0.__dict__, "coupling": 3})
+    fixed = O.State(p, s.f.copy(), s.psi.copy(), np.zeros((3, p.n)), 0)
+    fixed.advance(1)                                   # a fixed point of the coupled step too
+    assert np.abs(fixed.u).max() < 1e-9 and np.abs(fixed.psi - s.psi).max() < 1e-9
+    rng = np.random.default_rng(2)
+    st = O.State(p, s.f + 1e-10 * rng.normal(size=s.f.shape), s.psi + 1e-10 * rng.normal(size=s.psi.shape),
+                 np.zeros((3, p.n)), 0)
+    st.advance(3000)
+    # the uniform flow settles at ~1e-7 (the lattice force of the quartic term
+    # does not sum to zero, reading P); the staggered part must stay at 1e-10
+    dev = st.u - st.u.mean(axis=1, keepdims=True)
+    assert np.isfinite(st.u).all() and np.abs(dev).max() < 1e-8 and np.abs(st.u).max() < 1e-6
