@@ -59,6 +59,9 @@ extern "C" {
 #define FLB_COUPLE_ADVECT 2    /* the fluid advects psi */
 #define FLB_SQ_PSI 0           /* structure factor of psi */
 #define FLB_SQ_HEIGHT 1        /* capillary spectrum of the two psi = 0 surfaces */
+#define FLB_FORCE_MATCHED 0     /* force gradient matched to the psi scheme */
+#define FLB_FORCE_CD 1          /* central difference of Sec. IV */
+#define FLB_FORCE_FV 2          /* FV lattice gradient of Eq. (fvgrad) */
 #define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
 #define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
 
@@ -86,6 +89,13 @@ extern "C" {
  *   seed        : Philox key of this replica.
  *   sq_kmax     : structure-factor window: wavevector indices |k_a| <= sq_kmax
  *                 on every axis; <= 0 or >= n_a/2 keeps the whole axis.
+ *   force_grad  : lattice gradient in the force F = -psi grad mu:
+ *                 FLB_FORCE_MATCHED (default) takes the central difference
+ *                 with FLB_FD and the FV gradient (1/c_s^2) sum_i w_i c_i
+ *                 mu(r + c_i) of Eq. (fvgrad) with FLB_FV -- the gradient whose
+ *                 negative adjoint is the divergence advecting psi, so that the
+ *                 work u.F equals the free energy advection removes (Sec. II.B).
+ *                 FLB_FORCE_CD or FLB_FORCE_FV force one choice.
  */
 typedef struct flb_params {
     int32_t dim, q;
@@ -96,14 +106,14 @@ typedef struct flb_params {
     int32_t psi_scheme, integrator, storage, coupling;
     uint64_t seed;
     int32_t sq_kmax;
-    int32_t reserved;
+    int32_t force_grad;
 } flb_params;
 
 typedef struct flb_handle flb_handle;
 
 /* Fill *p with the defaults: D3Q19 32^3, rho0 1, tau 0.8, gamma_bulk NaN,
  * gamma_ghost 0, kT 0, A 0.05, B 0, K 0.04, M 0.1, FV, Heun, FP32, coupling 3,
- * seed 1, sq_kmax 0. */
+ * seed 1, sq_kmax 0, force_grad FLB_FORCE_MATCHED. */
 void flb_params_default(flb_params *p);
 
 /* Device workspace needed for nrep replicas p[0..nrep-1]; 0 if any parameter
@@ -194,10 +204,12 @@ int flb_synchronize(flb_handle *h);
 int64_t flb_launch_count(flb_handle *h);
 
 /* Per-phase device timing.  While on, flb_step records CUDA events around the
- * lattice Boltzmann kernel and around the psi kernels of every replica step.
- * flb_kernel_times() synchronises and returns the summed milliseconds and
- * launch counts of {LB kernel, psi kernels (incl. mu), sampling} since the
- * last flb_set_profiling(h, 1), which clears them.  ms and counts: 3 entries. */
+ * lattice Boltzmann collide-stream kernel and around the other kernels of every
+ * replica step.  flb_kernel_times() synchronises and returns the summed
+ * milliseconds and launch counts of {collide-stream kernel, the other step
+ * kernels (mu, velocity of the new fluid state, psi stages), sampling} since the
+ * last flb_set_profiling(h, 1), which clears them.  ms and counts: 3 entries.
+ * In batched mode the whole graph-launched step counts as the first entry. */
 int flb_set_profiling(flb_handle *h, int32_t on);
 int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts);
 

@@ -89,6 +89,7 @@ bool valid(const flb_params &p)
     if (p.integrator != FLB_EULER && p.integrator != FLB_HEUN) return false;
     if (p.storage != FLB_F32_DEV && p.storage != FLB_F16_DEV) return false;
     if (p.coupling < 0 || p.coupling > 3) return false;
+    if (p.force_grad < FLB_FORCE_MATCHED || p.force_grad > FLB_FORCE_FV) return false;
     if (p.sq_kmax < 0) return false;
     if (p.nx > 4096 || p.ny > 4096 || (p.dim == 3 && p.nz > 4096)) return false;  // DFT twiddle tables
     return true;
@@ -368,13 +369,15 @@ LBArgs lb_args(const Rep &r, float *psi_n)
     la.kT = (float)p.kT;
     std::memcpy(la.namp, r.namp, sizeof(la.namp));
     la.coupling = p.coupling;
+    la.fv_force = p.force_grad == FLB_FORCE_FV || (p.force_grad == FLB_FORCE_MATCHED && p.psi_scheme == FLB_FV);
     la.key = philox_key(p.seed);
     la.step = r.step;
     return la;
 }
 
-// 3D step: the LB kernel derives mu and the force from psi in shared memory;
-// each Runge-Kutta stage of psi is one fused launch.
+// 3D step: mu of psi^n, the collide-stream with the force -psi grad mu, the
+// velocity of the new fluid state, then one fused launch per Runge-Kutta stage
+// of psi advected by that velocity (Gauss-Seidel coupling).
 int step_rep3(flb_handle *h, Rep &r)
 {
     const flb_params &p = r.p;
@@ -387,6 +390,7 @@ int step_rep3(flb_handle *h, Rep &r)
     FLB_TRY(launch_lb3d(la, p.storage, st));
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
+    FLB_TRY(launch_vel3(la, p.storage, st));
     const bool noisy = p.kT > 0 && p.M > 0;
     const bool heun = p.integrator == FLB_HEUN;
     const int advect = (p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
@@ -422,6 +426,7 @@ int step_rep(flb_handle *h, Rep &r)
     FLB_TRY(launch_lb(la, r.q, p.storage, st));
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
+    FLB_TRY(launch_vel2(la, p.storage, st));
 
     const bool noisy = p.kT > 0 && p.M > 0;
     if (noisy) {
@@ -647,7 +652,10 @@ BatchLists batch_lists(flb_handle *h)
 int batch_kernels_per_step(const flb_handle *h)
 {
     const flb_params &p = h->reps[0].p;
-    return 1 + 1 + 1 + (p.integrator == FLB_HEUN ? 1 : 0) + 1;
+    bool force = false;
+    for (const Rep &r : h->reps) force |= (r.p.coupling & FLB_COUPLE_FORCE) != 0;
+    // mu (when any replica is forced), collide-stream, velocity, psi stage(s), step counter
+    return (force ? 1 : 0) + 1 + 1 + 1 + (p.integrator == FLB_HEUN ? 1 : 0) + 1;
 }
 
 // Capture one batched step into a CUDA graph (once per handle).
@@ -748,6 +756,7 @@ void flb_params_default(flb_params *p)
     p->coupling = FLB_COUPLE_FORCE | FLB_COUPLE_ADVECT;
     p->seed = 1;
     p->sq_kmax = 0;
+    p->force_grad = FLB_FORCE_MATCHED;
 }
 
 static bool valid_set(const flb_params *p, int32_t nrep)

@@ -155,6 +155,7 @@ struct LBArgs {
     float kT;
     float namp[16];            // sqrt((1 - gamma_k^2)/b_k) of the noisy modes, in noise order
     int coupling;
+    int fv_force;              // 1: force uses the FV gradient of mu, 0: central difference
     PhiloxKey key;
     int64_t step;
 };
@@ -225,6 +226,9 @@ cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);
 // D3Q19 collide-stream that computes mu and the force itself from psi (flb_lb3d.cu)
 cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t s);
+// velocity of the streamed state after a step, written to a.u (flb_lb3d.cu, flb_lb.cu)
+cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t s);
+cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
 // one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu)
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,

@@ -3,13 +3,23 @@
 // The chemical potential mu = A psi + B psi^3 - K lap_SO psi (Sec. II.A; SO
 // stencil of App. A) is first written on the interior and one ghost layer by
 // mu3_kernel; the collide-stream kernel then forms the force density of Sec. IV,
-// F = -psi grad_CD mu, pulls its 19 populations, relaxes them in moment space
+// F = -psi grad mu (central difference, or the FV gradient of Eq. (fvgrad) when
+// psi moves by the FV scheme, so that the force is the negative adjoint of the
+// divergence that advects psi), pulls its 19 populations, relaxes them in moment space
 // with noise on the stress and ghost modes (Eq. bab, Sec. III) and writes the
-// post-collision populations and the velocity v = (j + F/2)/rho that the psi
-// step uses (reading: both halves of a step read the state at time n).
+// post-collision populations.  vel3_kernel then gathers the streamed
+// populations and writes the velocity (sum fbar c + F/2)/rho of the new fluid
+// state, which advects psi (Gauss-Seidel coupling: the psi step follows the
+// fluid step).
 //
 // Indices are 32-bit (N and the padded planes are < 2^31); population plane i
 // of N sites starts at fin + i*N.
+//
+// D3Q19.  Plane order: 0 rest; pairs (1,2) +-x, (3,4) +-y, (5,6) +-z,
+// (7,8) +-(1,1,0), (9,10) +-(1,-1,0), (11,12) +-(1,0,1), (13,14) +-(1,0,-1),
+// (15,16) +-(0,1,1), (17,18) +-(0,1,-1).
+// Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2, xy, yz, zx, three c^2 c_a ghosts,
+// three c_a(c_b^2-c_g^2) ghosts, c^4, c^2(3c_x^2-c^2), c^2(c_y^2-c_z^2).
 #include "flb_internal.cuh"
 
 namespace flb {
@@ -28,26 +38,20 @@ __device__ __forceinline__ void st3<float>(float *p, int i, float v) { p[i] = v;
 template <>
 __device__ __forceinline__ void st3<__half>(__half *p, int i, float v) { p[i] = __float2half_rn(v); }
 
-// One D3Q19 site: pull, moments, relaxation with force and noise, store.
-template <typename T, bool GHOST_RELAX>
-__device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
+// Pull of the 19 populations of site (x, y, z) from stored post-collision
+// planes fi: fbar_i(r) = stored_i(r - c_i).
+template <typename T>
+__device__ __forceinline__ void pull19(const T *fi, const Geom &g, int x, int y, int z, float f[19])
 {
-    const Geom &g = a.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int N = (int)g.n;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const int row = nx, pl = nx * ny;
-    const int s = x + row * y + pl * z;
     const int sY0 = row * y, sYm = row * ym, sYp = row * yp;
     const int sZ0 = pl * z, sZm = pl * zm, sZp = pl * zp;
-    const T *fin = (const T *)a.fin;
-    T *fout = (T *)a.fout;
-    const T *fi = fin;
-
-    float f[19];
-    f[0] = ld3(fi, s);
+    f[0] = ld3(fi, x + sY0 + sZ0);
     f[1] = ld3(fi + 1ll * N, xm + sY0 + sZ0);
     f[2] = ld3(fi + 2ll * N, xp + sY0 + sZ0);
     f[3] = ld3(fi + 3ll * N, x + sYm + sZ0);
@@ -66,6 +70,21 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     f[16] = ld3(fi + 16ll * N, x + sYp + sZp);
     f[17] = ld3(fi + 17ll * N, x + sYm + sZp);
     f[18] = ld3(fi + 18ll * N, x + sYp + sZm);
+}
+
+// One D3Q19 site: pull, moments, relaxation with force and noise, store.
+template <typename T, bool GHOST_RELAX>
+__device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
+{
+    const Geom &g = a.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int N = (int)g.n;
+    const int row = nx, pl = nx * ny;
+    const int s = x + row * y + pl * z;
+    T *fout = (T *)a.fout;
+
+    float f[19];
+    pull19((const T *)a.fin, g, x, y, z, f);
 
     float sp[10], dp[10];
 #pragma unroll
@@ -86,9 +105,6 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     const float rho = a.rho0 + drho;
     const float irho = __fdividef(1.0f, rho);  // ~2 ulp
     const float vx = (jx + 0.5f * Fx) * irho, vy = (jy + 0.5f * Fy) * irho, vz = (jz + 0.5f * Fz) * irho;
-    store_padded(a.u, g, x, y, z, vx, 1);
-    store_padded(a.u + g.pn, g, x, y, z, vy, 1);
-    store_padded(a.u + 2 * g.pn, g, x, y, z, vz, 1);
 
     const float ws = a.omega_s, wb = a.omega_b;
     const float cs = 1.0f - 0.5f * ws, cb = 1.0f - 0.5f * wb;
@@ -204,6 +220,42 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     st3(fo + 18ll * N, s, w2 * (E - O));
 }
 
+// Force density F = -psi grad mu of Sec. IV at an interior site.
+__device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, float &Fx, float &Fy, float &Fz)
+{
+    const Geom &g = a.g;
+    // F = -psi grad mu, mu read from its field (valid on the interior + 1,
+    // edges and corners included)
+    const int pi = g.pidx32(x, y, z);
+    const int sy = g.px, sz = g.px * g.py;
+    const float ps = __ldg(a.psi + pi);
+    const float *mu = a.mu;
+    const float dx = __ldg(mu + pi + 1) - __ldg(mu + pi - 1);
+    const float dy = __ldg(mu + pi + sy) - __ldg(mu + pi - sy);
+    const float dz = __ldg(mu + pi + sz) - __ldg(mu + pi - sz);
+    if (a.fv_force) {
+        // FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i), Eq. (fvgrad): with
+        // w = 1/18 (faces), 1/36 (edges) it is [2 (face difference) + sum of
+        // the 8 edge neighbours signed by c_a] / 12
+        const float xyp = __ldg(mu + pi + 1 + sy), xym = __ldg(mu + pi + 1 - sy);
+        const float yxp = __ldg(mu + pi - 1 + sy), yxm = __ldg(mu + pi - 1 - sy);
+        const float xzp = __ldg(mu + pi + 1 + sz), xzm = __ldg(mu + pi + 1 - sz);
+        const float zxp = __ldg(mu + pi - 1 + sz), zxm = __ldg(mu + pi - 1 - sz);
+        const float yzp = __ldg(mu + pi + sy + sz), yzm = __ldg(mu + pi + sy - sz);
+        const float zyp = __ldg(mu + pi - sy + sz), zym = __ldg(mu + pi - sy - sz);
+        // xyp = mu(+1,+1,0), xym = mu(+1,-1,0), yxp = mu(-1,+1,0), yxm = mu(-1,-1,0);
+        // likewise in the (x,z) and (y,z) planes
+        const float c = -ps * (1.0f / 12.0f);
+        Fx = c * (2.f * dx + ((xyp + xym) - (yxp + yxm)) + ((xzp + xzm) - (zxp + zxm)));
+        Fy = c * (2.f * dy + ((xyp - xym) + (yxp - yxm)) + ((yzp + yzm) - (zyp + zym)));
+        Fz = c * (2.f * dz + ((xzp - xzm) + (zxp - zxm)) + ((yzp - yzm) + (zyp - zym)));
+    } else {
+        Fx = -ps * 0.5f * dx;
+        Fy = -ps * 0.5f * dy;
+        Fz = -ps * 0.5f * dz;
+    }
+}
+
 // One thread per site on a 3D grid of 32 x 4 x 2 blocks (a warp covers 32
 // consecutive x, so every population plane is read and written in full rows).
 
@@ -217,16 +269,7 @@ __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int b
     const int z = bz * LB_BZ + threadIdx.z;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) {
-        // F = -psi grad_CD mu, mu read from its field (valid on the interior + 1)
-        const int pi = g.pidx32(x, y, z);
-        const int sy = g.px, sz = g.px * g.py;
-        const float ps = __ldg(a.psi + pi);
-        const float *mu = a.mu;
-        Fx = -ps * 0.5f * (__ldg(mu + pi + 1) - __ldg(mu + pi - 1));
-        Fy = -ps * 0.5f * (__ldg(mu + pi + sy) - __ldg(mu + pi - sy));
-        Fz = -ps * 0.5f * (__ldg(mu + pi + sz) - __ldg(mu + pi - sz));
-    }
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3(a, x, y, z, Fx, Fy, Fz);
     lb_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
 }
 
@@ -234,6 +277,44 @@ template <typename T, bool GHOST_RELAX, bool FORCE>
 __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_kernel(const LBArgs a)
 {
     lb3_block<T, GHOST_RELAX, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Velocity of the streamed state after the step: u = (sum fbar c + F/2)/rho
+// with fbar the populations the next step pulls (the planes just written, a.fout)
+// and F this step's force density -- the velocity that advects psi (Gauss-Seidel
+// coupling of Sec. VI: the psi step follows the fluid step).
+template <typename T, bool FORCE>
+__device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int bz)
+{
+    const Geom &g = a.g;
+    const int x = bx * LB_BX + threadIdx.x;
+    const int y = by * LB_BY + threadIdx.y;
+    const int z = bz * LB_BZ + threadIdx.z;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+    float f[19];
+    pull19((const T *)a.fout, g, x, y, z, f);
+    float sp[10], dp[10];
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) {
+        sp[p] = f[2 * p - 1] + f[2 * p];
+        dp[p] = f[2 * p - 1] - f[2 * p];
+    }
+    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
+    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
+    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
+    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3(a, x, y, z, Fx, Fy, Fz);
+    const float irho = __fdividef(1.0f, a.rho0 + drho);
+    store_padded(a.u, g, x, y, z, (jx + 0.5f * Fx) * irho, 1);
+    store_padded(a.u + g.pn, g, x, y, z, (jy + 0.5f * Fy) * irho, 1);
+    store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
+}
+
+template <typename T, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_kernel(const LBArgs a)
+{
+    vel3_block<T, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer
@@ -273,12 +354,11 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_batch_kernel(const Ba
     mu3_block(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
 }
 
-template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const BatchLists L)
+// Per-block LBArgs of a batched launch, in shared memory: the replica's
+// arguments with the population buffers swapped on odd device steps, the psi
+// buffer of the step and the step's noise counter.
+__device__ __forceinline__ void batch_lb_args(const BatchLists &L, const BatchRep &r, LBArgs &sa)
 {
-    __shared__ LBArgs sa;
-    const BatchBlock b = L.lb[blockIdx.x];
-    const BatchRep &r = L.reps[b.rep];
     const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
     {
         const int *src = reinterpret_cast<const int *>(&r.lb);
@@ -297,7 +377,24 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const Ba
         sa.step = r.lb.step + ds;
     }
     __syncthreads();
+}
+
+template <typename T, bool GHOST_RELAX, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const BatchLists L)
+{
+    __shared__ LBArgs sa;
+    const BatchBlock b = L.lb[blockIdx.x];
+    batch_lb_args(L, L.reps[b.rep], sa);
     lb3_block<T, GHOST_RELAX, FORCE>(sa, b.bx, b.by, b.bz);
+}
+
+template <typename T, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_batch_kernel(const BatchLists L)
+{
+    __shared__ LBArgs sa;
+    const BatchBlock b = L.lb[blockIdx.x];
+    batch_lb_args(L, L.reps[b.rep], sa);
+    vel3_block<T, FORCE>(sa, b.bx, b.by, b.bz);
 }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)
@@ -317,6 +414,15 @@ cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool 
         else { if (force) FLB_LB3B(float, false, true); else FLB_LB3B(float, false, false); }
     }
 #undef FLB_LB3B
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (storage == FLB_F16_DEV) {
+        if (force) vel3_batch_kernel<__half, true><<<L.nlb, block, 0, st>>>(L);
+        else vel3_batch_kernel<__half, false><<<L.nlb, block, 0, st>>>(L);
+    } else {
+        if (force) vel3_batch_kernel<float, true><<<L.nlb, block, 0, st>>>(L);
+        else vel3_batch_kernel<float, false><<<L.nlb, block, 0, st>>>(L);
+    }
     return cudaGetLastError();
 }
 
@@ -343,6 +449,21 @@ cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t st)
         else { if (force) FLB_LB3(float, false, true); else FLB_LB3(float, false, false); }
     }
 #undef FLB_LB3
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t st)
+{
+    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
+    const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;
+    if (storage == FLB_F16_DEV) {
+        if (force) vel3_kernel<__half, true><<<grid, block, 0, st>>>(a);
+        else vel3_kernel<__half, false><<<grid, block, 0, st>>>(a);
+    } else {
+        if (force) vel3_kernel<float, true><<<grid, block, 0, st>>>(a);
+        else vel3_kernel<float, false><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ def flb_params(d: dict, **kw) -> F.FlbParams:
     p.coupling = d.get("coupling", 3)
     p.seed = d.get("seed", 1)
     p.sq_kmax = d.get("sq_kmax", 0)
+    p.force_grad = d.get("force_grad", 0)
     return p
 
 
@@ -33,7 +34,7 @@ def oracle_params(d: dict, **kw) -> O.Params:
                     rho0=d.get("rho0", 1.0), tau=d["tau"], gamma_bulk=d.get("gamma_bulk", float("nan")),
                     gamma_ghost=d.get("gamma_ghost", 0.0), kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
                     scheme=d.get("scheme", 1), integrator=d.get("integrator", 2), coupling=d.get("coupling", 3),
-                    seed=d.get("seed", 1))
+                    seed=d.get("seed", 1), force_grad=d.get("force_grad", 0))
 
 
 def field_error(gpu, ora, eq=0.0):

@@ -60,6 +60,21 @@ def test_coupled_step_matches_oracle(dim, q, shape, scheme, integ):
 
 
 @pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("force_grad", [1, 2])
+def test_force_gradient_choices_match_oracle(dim, q, scheme, force_grad):
+    # both lattice gradients in the force with both psi schemes (the matched pair
+    # is the default of the cases above); a deep quench so the force is large
+    shape = (10, 9, 7)
+    d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.8, kT=1e-4, A=-0.05, B=0.3, K=0.04, M=0.1,
+             scheme=scheme, integrator=2, coupling=3, seed=13, force_grad=force_grad)
+    s, (fg, pg, ug), st, feq = _run_pair(d, 20, amp_psi=0.3)
+    assert field_error(fg, st.f, feq) < TOL
+    assert field_error(pg, st.psi) < TOL
+    assert field_error(ug[:dim], st.u[:dim]) < TOL
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
 def test_relaxation_variants_match_oracle(dim, q):
     # bulk rate different from shear, partially relaxed ghosts, only advection coupling
     shape = (9, 8, 6)
