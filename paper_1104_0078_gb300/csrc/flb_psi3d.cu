@@ -274,9 +274,29 @@ struct TmaArgs {
     int *status;
 };
 
+constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * H2N + 6 * H1N;
+constexpr int FV_NOISE_FLOATS = 6 * H1N;
+
 // One block (tile bx, by; z chunk bz).  psi_map / u_map: tensor maps of the stage
 // input psi and of the velocity (kernel parameters or global memory); tsmem: the
 // block's dynamic shared memory.
+//
+// Every stencil is split by plane.  A thread owns the same points of the mu,
+// flux and tile regions in every plane and keeps, in registers, what each new
+// plane contributes to the planes above and below it:
+//   lap_SO psi (z) = (6 n1 + 3 n2 + n3 - 80 psi) / 22 with, per plane P, the
+//     centre a, the 4 in-plane faces b and the 4 in-plane diagonals d:
+//     n1 = b(z) + a(z-1) + a(z+1),  n2 = d(z) + b(z-1) + b(z+1),  n3 = d(z-1) + d(z+1);
+//   12 grad mu (q) (Eq. fvgrad, w = 1/18, 1/36) with ex, ey the in-plane face
+//     differences, Dx, Dy the signed diagonal sums and Zp = 2 mu + 4 faces:
+//     x: 2 ex(q) + Dx(q) + ex(q-1) + ex(q+1),  y: likewise,  z: Zp(q+1) - Zp(q-1);
+//   12 div J (z) (the (2/c_s^2) link-average divergence, sum_i w_i c_i = 0 removes
+//     J(r)) with Hxy the in-plane face differences of Jx, Jy, Dg the in-plane
+//     diagonal terms, Zc = Jz(centre), Z4 = Jz at the 4 in-plane faces:
+//     2 Hxy(z) + Dg(z) + 2 (Zc(z+1) - Zc(z-1)) + Hxy(z+1) + Hxy(z-1) + Z4(z+1) - Z4(z-1).
+// Shared memory then holds only the current mu, flux and noise planes (two of
+// each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
+// formed, the flux of plane p-2, and the output of plane p-3 completes.
 template <int STAGE, bool NOISE>
 __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
                                                   const Psi3Args &a, int *status, int bx, int by, int bz,
@@ -285,9 +305,9 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
     float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
     float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
-    float *smu = tus + T_U_DEPTH * TU_SLOT;              // [3][H2N]
-    float *sJ = smu + 3 * H2N;                           // [3][3][H1N]
-    float *sX = sJ + 9 * H1N;                            // [3][3][H1N] when NOISE
+    float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][H2N]     mu plane, by parity
+    float *sJ = smu + 2 * H2N;                           // [2][3][H1N]  flux plane, by parity
+    float *sX = sJ + 6 * H1N;                            // [2][3][H1N]  noise plane, by parity (NOISE)
     __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH];
     __shared__ int s_bad;
     const Geom &g = a.g;
@@ -298,6 +318,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const bool active = x < g.nx && y < g.ny;
     const float k22 = a.K * (1.0f / 22.0f);
     const float sdx = sqrtf(2.0f * a.kT * a.M);
+    const float m12 = a.M * (1.0f / 12.0f);
     const int pbase = z0 - 3, ubase = z0 - 1;             // first psi / u plane of the chunk
     // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
     // psi-slot centre, u-slot offset, noise counter id
@@ -324,6 +345,17 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         u1[j] = (lx + 3) + TB_X * ly;
         n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
     }
+    // per-plane partial sums carried between planes (registers)
+    float pa[S2][2], pb[S2][2], pd[S2][2];  // psi: centre, faces, diagonals of planes p-2 [0], p-1 [1]
+    float G0[S1][3], G1[S1][3];            // 12 grad mu of planes m-1 and m, partly summed
+#pragma unroll
+    for (int j = 0; j < S2; ++j) pa[j][0] = pa[j][1] = pb[j][0] = pb[j][1] = pd[j][0] = pd[j][1] = 0.f;
+#pragma unroll
+    for (int j = 0; j < S1; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G0[j][k] = G1[j][k] = 0.f;
+    float D0 = 0.f, D1 = 0.f, N0 = 0.f, N1 = 0.f;  // 12 div of the flux / noise of planes q-1 and q
+
     if (threadIdx.x == 0) {
         for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
         for (int s = 0; s < T_U_DEPTH; ++s) mbar_init(&bar_u[s], 1);
@@ -349,110 +381,151 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     int waited_p = pbase - 1, waited_u = ubase - 1;
 
     // Rotating ring positions, advanced once per plane (no divisions in the loop):
-    // psi plane p sits in slot r6 of phase ph6; plane x of the mu / flux rings in
-    // slot (x - pbase) mod 3, m3 being that of p; the velocity of plane q = p - 2
-    // in slot ru of phase uph once q >= ubase.
-    int r6 = 0, ph6 = 0, m3 = 0, ru = 0, uph = 0;
+    // psi plane p sits in slot r6 of phase ph6; the velocity of the next flux plane
+    // in slot ru of phase uph.
+    int r6 = 0, ph6 = 0, ru = 0, uph = 0;
     for (int p = z0 - 3; p <= z1 + 2; ++p) {
         const int s1 = r6 == 0 ? T_PSI_DEPTH - 1 : r6 - 1;  // psi slots of p-1, p-2, p-3
         const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
         const int s3 = s2 == 0 ? T_PSI_DEPTH - 1 : s2 - 1;
-        const int mm1 = m3 == 0 ? 2 : m3 - 1;                 // ring slots of p-1 (== p-4), p-2
-        const int mm2 = mm1 == 0 ? 2 : mm1 - 1;
-        __syncthreads();
-        if (s_bad) break;
-        if (threadIdx.x == 0) {
-            fence_proxy_async();
-            if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
-            if (p >= ubase && p <= z1 && a.advect) { issue_u(p); last_u = p; }
-        }
-        // (a) psi plane p has landed
+        (void)s1;
+        // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
         if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
         waited_p = p;
-        if (p - 1 >= z0 - 2) {  // (b) mu plane p-1, tile + 2
-            const float *pm = tps + s2 * TP_SLOT, *p0 = tps + s1 * TP_SLOT, *pp = tps + r6 * TP_SLOT;
-            float *dst = smu + mm1 * H2N;
+        {
+            const float *P = tps + r6 * TP_SLOT;
+            float *dst = smu + ((p - 1) & 1) * H2N;
+            const bool emit = p - 1 >= z0 - 2;
 #pragma unroll
-            for (int j = 0; j < S2; ++j)
-                if (c2[j] >= 0) dst[d2[j]] = mu_point<TB_X>(pm, p0, pp, c2[j], a.A, a.B, k22);
+            for (int j = 0; j < S2; ++j) {
+                const int c = c2[j];
+                if (c < 0) continue;
+                const float ac = P[c];
+                const float bc = (P[c - 1] + P[c + 1]) + (P[c - TB_X] + P[c + TB_X]);
+                const float dc = (P[c - 1 - TB_X] + P[c + 1 - TB_X]) + (P[c - 1 + TB_X] + P[c + 1 + TB_X]);
+                if (emit) {
+                    const float ps = pa[j][1];
+                    const float nn1 = pb[j][1] + (pa[j][0] + ac);
+                    const float nn2 = pd[j][1] + (pb[j][0] + bc);
+                    const float nn3 = pd[j][0] + dc;
+                    dst[d2[j]] = a.A * ps + a.B * ps * ps * ps - k22 * (6.f * nn1 + 3.f * nn2 + nn3 - 80.f * ps);
+                }
+                pa[j][0] = pa[j][1];
+                pb[j][0] = pb[j][1];
+                pd[j][0] = pd[j][1];
+                pa[j][1] = ac;
+                pb[j][1] = bc;
+                pd[j][1] = dc;
+            }
         }
-        __syncthreads();
+        __syncthreads();  // mu plane p-1 complete; every read of the psi slot of p-4 and of the u slot of p-3 done
         if (s_bad) break;
-        const int q = p - 2;
-        if (q >= z0 - 1) {  // (c) node flux (and noise) on plane q, tile + 1
+        if (threadIdx.x == 0) {  // refill those slots: psi plane p+2 (used at p+2), u plane p (used at p+2)
+            fence_proxy_async();
+            if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
+            if (a.advect && p >= ubase && p <= z1) { issue_u(p); last_u = p; }
+        }
+        // (B) mu partials of plane m = p-1 at the flux points; flux (and noise) of plane m-1
+        const int m = p - 1;
+        if (m >= z0 - 2) {
+            const bool emit = m - 1 >= z0 - 1;
             const float *uq = tus;
-            if (a.advect) {
+            if (emit && a.advect) {
                 if (!mbar_wait(&bar_u[ru], uph, status)) s_bad = 1;
-                waited_u = q;
+                waited_u = m - 1;
                 uq = tus + ru * TU_SLOT;
                 ru = ru == T_U_DEPTH - 1 ? 0 : ru + 1;
                 uph ^= ru == 0;
             }
-            const float *mm = smu + m3 * H2N, *m0 = smu + mm2 * H2N, *mp = smu + mm1 * H2N;
-            const float *ps = tps + s2 * TP_SLOT;
-            float *J = sJ + mm2 * 3 * H1N;
-            float *X = sX + mm2 * 3 * H1N;
-            const int zid = g.nx * g.ny * wrapi(q, g.nz);
+            const float *Mu = smu + (m & 1) * H2N;
+            const float *ps = tps + s2 * TP_SLOT;  // psi plane m-1
+            float *J = sJ + ((m - 1) & 1) * 3 * H1N;
+            float *X = sX + ((m - 1) & 1) * 3 * H1N;
+            const int zid = g.nx * g.ny * wrapi(m - 1, g.nz);
 #pragma unroll
             for (int j = 0; j < S1; ++j) {
                 const int c = c1[j];
                 if (c < 0) continue;
-                const int k = d1[j];
-                const float gx = (1.f / 6.f) * (m0[c + 1] - m0[c - 1]) +
-                                 (1.f / 12.f) * ((m0[c + 1 + H2X] + m0[c + 1 - H2X] - m0[c - 1 + H2X] - m0[c - 1 - H2X]) +
-                                                 (mp[c + 1] + mm[c + 1] - mp[c - 1] - mm[c - 1]));
-                const float gy = (1.f / 6.f) * (m0[c + H2X] - m0[c - H2X]) +
-                                 (1.f / 12.f) * ((m0[c + H2X + 1] + m0[c + H2X - 1] - m0[c - H2X + 1] - m0[c - H2X - 1]) +
-                                                 (mp[c + H2X] + mm[c + H2X] - mp[c - H2X] - mm[c - H2X]));
-                const float gz = (1.f / 6.f) * (mp[c] - mm[c]) +
-                                 (1.f / 12.f) * ((mp[c + 1] + mp[c - 1] - mm[c + 1] - mm[c - 1]) +
-                                                 (mp[c + H2X] + mp[c - H2X] - mm[c + H2X] - mm[c - H2X]));
-                float jx = a.M * gx, jy = a.M * gy, jz = a.M * gz;
-                if (a.advect) {
-                    const float pv = ps[p1[j]];
-                    jx -= uq[u1[j]] * pv;
-                    jy -= uq[TB_X * H1Y + u1[j]] * pv;
-                    jz -= uq[2 * TB_X * H1Y + u1[j]] * pv;
-                }
-                J[k] = jx;
-                J[H1N + k] = jy;
-                J[2 * H1N + k] = jz;
-                if (NOISE) {
-                    float G[4];
-                    normals4(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, G);
-                    X[k] = sdx * G[0];
-                    X[H1N + k] = sdx * G[1];
-                    X[2 * H1N + k] = sdx * G[2];
+                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + H2X], mym = Mu[c - H2X];
+                const float mpp = Mu[c + 1 + H2X], mpm = Mu[c + 1 - H2X], mmp = Mu[c - 1 + H2X],
+                            mmm = Mu[c - 1 - H2X];
+                const float ex = mxp - mxm, ey = myp - mym;
+                const float Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
+                const float Zp = 2.f * Mu[c] + ((mxp + mxm) + (myp + mym));
+                const float gx = G0[j][0] + ex, gy = G0[j][1] + ey, gz = G0[j][2] + Zp;  // plane m-1, complete
+                G0[j][0] = G1[j][0] + (2.f * ex + Dx);
+                G0[j][1] = G1[j][1] + (2.f * ey + Dy);
+                G0[j][2] = G1[j][2];
+                G1[j][0] = ex;
+                G1[j][1] = ey;
+                G1[j][2] = -Zp;
+                if (emit) {
+                    const int k = d1[j];
+                    float jx = m12 * gx, jy = m12 * gy, jz = m12 * gz;
+                    if (a.advect) {
+                        const float pv = ps[p1[j]];
+                        jx -= uq[u1[j]] * pv;
+                        jy -= uq[TB_X * H1Y + u1[j]] * pv;
+                        jz -= uq[2 * TB_X * H1Y + u1[j]] * pv;
+                    }
+                    J[k] = jx;
+                    J[H1N + k] = jy;
+                    J[2 * H1N + k] = jz;
+                    if (NOISE) {
+                        float Gn[4];
+                        normals4(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn);
+                        X[k] = sdx * Gn[0];
+                        X[H1N + k] = sdx * Gn[1];
+                        X[2 * H1N + k] = sdx * Gn[2];
+                    }
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();  // flux plane p-2 complete
         if (s_bad) break;
-        const int z = p - 3;
-        if (z >= z0 && active) {  // (d) stage output at plane z: flux planes z-1, z, z+1
+        // (C) flux partials of plane q = p-2 at the tile point; the output of plane q-1 completes
+        const int q = p - 2;
+        if (q >= z0 - 1) {
             const int c = (tx + 1) + H1X * (ty + 1);
-            const float *Jm = sJ + mm1 * 3 * H1N, *J0 = sJ + m3 * 3 * H1N, *Jp = sJ + mm2 * 3 * H1N;
-            const float Dd = fv_div(Jm, J0, Jp, Jm + H1N, J0 + H1N, Jp + H1N, Jm + 2 * H1N, J0 + 2 * H1N,
-                                    Jp + 2 * H1N, c);
-            const int si = x + g.nx * (y + g.ny * z);
-            float out;
-            if (STAGE == 1) {
-                float Dn = 0.f;
-                if (NOISE) {
-                    const float *Xm = sX + mm1 * 3 * H1N, *X0 = sX + m3 * 3 * H1N, *Xp = sX + mm2 * 3 * H1N;
-                    Dn = fv_div(Xm, X0, Xp, Xm + H1N, X0 + H1N, Xp + H1N, Xm + 2 * H1N, X0 + 2 * H1N, Xp + 2 * H1N, c);
-                }
-                const float pv = tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
-                out = pv + Dd + Dn;
-                if (a.heun) a.E[si] = pv + 0.5f * Dd + Dn;
-            } else {
-                out = a.E[si] + 0.5f * Dd;
+            const float *Jx = sJ + (q & 1) * 3 * H1N, *Jy = Jx + H1N, *Jz = Jy + H1N;
+            const float hxy = (Jx[c + 1] - Jx[c - 1]) + (Jy[c + H1X] - Jy[c - H1X]);
+            const float dg = ((Jx[c + 1 + H1X] + Jy[c + 1 + H1X]) - (Jx[c - 1 - H1X] + Jy[c - 1 - H1X])) +
+                             ((Jx[c + 1 - H1X] - Jy[c + 1 - H1X]) - (Jx[c - 1 + H1X] - Jy[c - 1 + H1X]));
+            const float zc = Jz[c];
+            const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + H1X] + Jz[c - H1X]);
+            const float dd = D0 + (2.f * zc + hxy + z4);  // plane q-1, complete
+            D0 = D1 + (2.f * hxy + dg);
+            D1 = hxy - z4 - 2.f * zc;
+            float dn = 0.f;
+            if (NOISE) {
+                const float *Xx = sX + (q & 1) * 3 * H1N, *Xy = Xx + H1N, *Xz = Xy + H1N;
+                const float nxy = (Xx[c + 1] - Xx[c - 1]) + (Xy[c + H1X] - Xy[c - H1X]);
+                const float ng = ((Xx[c + 1 + H1X] + Xy[c + 1 + H1X]) - (Xx[c - 1 - H1X] + Xy[c - 1 - H1X])) +
+                                 ((Xx[c + 1 - H1X] - Xy[c + 1 - H1X]) - (Xx[c - 1 + H1X] - Xy[c - 1 + H1X]));
+                const float nzc = Xz[c];
+                const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + H1X] + Xz[c - H1X]);
+                dn = N0 + (2.f * nzc + nxy + nz4);
+                N0 = N1 + (2.f * nxy + ng);
+                N1 = nxy - nz4 - 2.f * nzc;
             }
-            store_padded(a.out, g, x, y, z, out, 3);
+            const int z = q - 1;
+            if (z >= z0 && active) {
+                const float Dd = dd * (1.f / 12.f);
+                const int si = x + g.nx * (y + g.ny * z);
+                float out;
+                if (STAGE == 1) {
+                    const float Dn = NOISE ? dn * (1.f / 12.f) : 0.f;
+                    const float pv = tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
+                    out = pv + Dd + Dn;
+                    if (a.heun) a.E[si] = pv + 0.5f * Dd + Dn;
+                } else {
+                    out = a.E[si] + 0.5f * Dd;
+                }
+                store_padded(a.out, g, x, y, z, out, 3);
+            }
         }
         r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
         ph6 ^= r6 == 0;
-        m3 = m3 == 2 ? 0 : m3 + 1;
     }
     // a bounded wait drains copies still in flight before the block exits
     if (threadIdx.x == 0) {
@@ -513,14 +586,14 @@ cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool
     if (!scheme_fv) return cudaErrorNotSupported;
     cudaError_t e = launch_lb3_batch(L, storage, ghost, force, st);
     if (e != cudaSuccess) return e;
-    const size_t sm = sizeof(float) * ((size_t)T_PSI_DEPTH * TP_SLOT + (size_t)T_U_DEPTH * TU_SLOT + 3 * H2N + 9 * H1N);
+    const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS;
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
         kernel<<<L.npsi, PS_NT, bytes, st>>>(L);
         return cudaGetLastError();
     };
-    e = noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + sizeof(float) * 9 * H1N)
+    e = noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + sizeof(float) * FV_NOISE_FLOATS)
               : go(psi3_fv_tma_batch_kernel<1, false>, sm);
     if (e != cudaSuccess) return e;
     if (heun) {
@@ -585,7 +658,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
     ta.a = a;
     ta.status = status;
     const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + PS_ZC - 1) / PS_ZC);
-    size_t sm = sizeof(float) * ((size_t)T_PSI_DEPTH * TP_SLOT + (size_t)T_U_DEPTH * TU_SLOT + 3 * H2N + 9 * H1N);
+    const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS;
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
@@ -593,7 +666,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
         return cudaGetLastError();
     };
     if (stage == 1) {
-        if (noise) return go(psi3_fv_tma_kernel<1, true>, sm + sizeof(float) * 9 * H1N);
+        if (noise) return go(psi3_fv_tma_kernel<1, true>, sm + sizeof(float) * FV_NOISE_FLOATS);
         return go(psi3_fv_tma_kernel<1, false>, sm);
     }
     return go(psi3_fv_tma_kernel<2, false>, sm);
