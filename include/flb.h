@@ -64,6 +64,7 @@ extern "C" {
 #define FLB_FORCE_FV 2          /* FV lattice gradient of Eq. (fvgrad) */
 #define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
 #define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
+#define FLB_TUNE_FORCE 1       /* flb_autotune: time every candidate even if the cache has an entry */
 
 /*
  * Parameters of one lattice (one replica).  Names follow the paper.
@@ -188,6 +189,36 @@ int flb_sq_reset(flb_handle *h, int32_t rep);
 
 /* Launch mode for flb_step: FLB_MODE_PLAIN or FLB_MODE_BATCHED. */
 int flb_set_mode(flb_handle *h, int32_t mode);
+
+/*
+ * Tiling of the 3D psi stage.  A psi block owns a 32 x 16 column of sites and
+ * marches psi_zchunk planes of it in z (default 64).  Smaller chunks give more
+ * blocks (small boxes fill the GPU) at the cost of recomputing the stencil halo
+ * of 6 planes per chunk.  The choice changes no result bit: every site's
+ * arithmetic is the same.  (A performance knob of this implementation; the
+ * paper has no counterpart.)
+ *
+ * flb_get_tuning / flb_set_tuning read / set psi_zchunk of replica rep (-1 sets
+ * every replica), 1 <= psi_zchunk <= 4096; EINVAL otherwise.  Setting it drops
+ * the batched mode's captured graph, which the next batched flb_step rebuilds.
+ *
+ * flb_autotune times the candidates 4, 8, ... (up to the first value that
+ * covers the box depth) on the handle's own buffers and keeps the fastest: in
+ * FLB_MODE_PLAIN per distinct replica configuration (box, lattice, scheme,
+ * integrator, noise, advection) on that replica's psi stages; in
+ * FLB_MODE_BATCHED one value for all replicas on the batched psi launches.  The
+ * timed launches write only step scratch and the spare psi buffer, so the state
+ * (populations, psi, step counters, spectra) is unchanged.  cache_path (may be
+ * NULL) names a text file of "key<TAB>planes" lines, keyed by the device name,
+ * its SM count and the configuration: entries found there are applied without
+ * timing (unless flags has FLB_TUNE_FORCE), new results are appended.  An
+ * unreadable or unwritable file only disables the cache.  Synchronising; call
+ * with the handle's device current and outside stream capture.  2D replicas are
+ * left as they are.
+ */
+int flb_get_tuning(flb_handle *h, int32_t rep, int32_t *psi_zchunk);
+int flb_set_tuning(flb_handle *h, int32_t rep, int32_t psi_zchunk);
+int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags);
 
 /* Bitwise checkpoint of replica rep: flb_state_bytes() bytes holding the step
  * counter, the stored populations and psi exactly as kept on the device.

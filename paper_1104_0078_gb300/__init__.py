@@ -29,6 +29,7 @@ FLB_COUPLE_FORCE, FLB_COUPLE_ADVECT = 1, 2
 FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV = 0, 1, 2
 FLB_SQ_PSI, FLB_SQ_HEIGHT = 0, 1
 FLB_MODE_PLAIN, FLB_MODE_BATCHED = 0, 1
+FLB_TUNE_FORCE = 1
 
 
 class FlbParams(ctypes.Structure):
@@ -85,6 +86,9 @@ def load_library(path: str = LIB_PATH):
         "flb_structure_factor_size": (c_i64, [H, ctypes.c_int32, ctypes.c_int32]),
         "flb_sq_reset": (c_int, [H, ctypes.c_int32]),
         "flb_set_mode": (c_int, [H, ctypes.c_int32]),
+        "flb_get_tuning": (c_int, [H, ctypes.c_int32, P(ctypes.c_int32)]),
+        "flb_set_tuning": (c_int, [H, ctypes.c_int32, ctypes.c_int32]),
+        "flb_autotune": (c_int, [H, ctypes.c_char_p, ctypes.c_int32]),
         "flb_state_bytes": (c_sz, [H, ctypes.c_int32]),
         "flb_get_state": (c_int, [H, ctypes.c_int32, vp, c_sz]),
         "flb_set_state": (c_int, [H, ctypes.c_int32, vp, c_sz]),
@@ -253,6 +257,22 @@ class Solver:
 
     def set_mode(self, mode):
         _check(self.lib.flb_set_mode(self.h, mode), "flb_set_mode")
+
+    def get_tuning(self, rep=0) -> int:
+        """Planes per psi block (the z chunk) of replica rep."""
+        v = ctypes.c_int32()
+        _check(self.lib.flb_get_tuning(self.h, rep, ctypes.byref(v)), "flb_get_tuning")
+        return int(v.value)
+
+    def set_tuning(self, psi_zchunk: int, rep: int = -1):
+        _check(self.lib.flb_set_tuning(self.h, rep, int(psi_zchunk)), "flb_set_tuning")
+
+    def autotune(self, cache=None, force=False):
+        """Time the psi z-chunk candidates on this handle (see flb_autotune); returns
+        the chosen value of every replica."""
+        path = os.fsencode(cache) if cache is not None else None
+        _check(self.lib.flb_autotune(self.h, path, FLB_TUNE_FORCE if force else 0), "flb_autotune")
+        return [self.get_tuning(r) for r in range(len(self.params))]
 
     def get_state(self, rep=0) -> bytes:
         n = int(self.lib.flb_state_bytes(self.h, rep))

@@ -7,6 +7,10 @@
 #include <new>
 #include <utility>
 #include <algorithm>
+#include <cstdio>
+#include <functional>
+#include <map>
+#include <string>
 #include <vector>
 
 #include "flb_internal.cuh"
@@ -56,6 +60,7 @@ struct Rep {
     int64_t step = 0;
     float omega_s = 0, omega_b = 0, gamma_g = 0;
     float namp[16] = {0};
+    int zc = PS_ZC;  // planes per psi block (3D), set by flb_set_tuning / flb_autotune
 };
 
 struct Carver {
@@ -173,7 +178,7 @@ struct flb_handle {
     // batched mode: descriptor table, block lists, device step counter, captured graph
     BatchRep *b_reps = nullptr;
     BatchBlock *b_mu = nullptr, *b_lb = nullptr, *b_psi = nullptr;
-    int b_nmu = 0, b_nlb = 0, b_npsi = 0;
+    int b_nmu = 0, b_nlb = 0, b_npsi = 0, b_npsi_cap = 0;
     long long *b_dstep = nullptr;
     std::vector<BatchRep> b_host;
     std::vector<BatchBlock> b_blocks_host;
@@ -224,11 +229,12 @@ size_t carve_all(flb_handle &h, char *base)
         const Geom &g = r.g;
         nmu += ((g.nx + 2 + LB_BX - 1) / LB_BX) * ((g.ny + 2 + LB_BY - 1) / LB_BY) * ((g.nz + 2 + LB_BZ - 1) / LB_BZ);
         nlb += ((g.nx + LB_BX - 1) / LB_BX) * ((g.ny + LB_BY - 1) / LB_BY) * ((g.nz + LB_BZ - 1) / LB_BZ);
-        npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC - 1) / PS_ZC);
+        npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC_MIN - 1) / PS_ZC_MIN);
     }
     h.b_nmu = nmu;
     h.b_nlb = nlb;
     h.b_npsi = npsi;
+    h.b_npsi_cap = npsi;
     h.b_reps = cv.take<BatchRep>(h.reps.size());
     h.b_mu = cv.take<BatchBlock>((size_t)std::max(nmu, 1));
     h.b_lb = cv.take<BatchBlock>((size_t)std::max(nlb, 1));
@@ -375,6 +381,28 @@ LBArgs lb_args(const Rep &r, float *psi_n)
     return la;
 }
 
+// The Runge-Kutta stages of psi (3D) for the current step of replica r, advected
+// by the velocity in r.u.  They write only step scratch (psi*, E) and the other
+// psi buffer, so repeating them leaves the state unchanged (the autotuner relies
+// on it).
+int launch_psi_stages(flb_handle *h, Rep &r)
+{
+    const flb_params &p = r.p;
+    cudaStream_t st = h->st;
+    float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
+    const bool noisy = p.kT > 0 && p.M > 0;
+    const bool heun = p.integrator == FLB_HEUN;
+    const int advect = (p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
+    const PhiloxKey key = philox_key(p.seed);
+    FLB_TRY(launch_psi3(r.g, p.psi_scheme, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
+                        (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, r.zc,
+                        h->status, st));
+    if (heun)
+        FLB_TRY(launch_psi3(r.g, p.psi_scheme, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
+                            (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, r.zc, h->status, st));
+    return FLB_OK;
+}
+
 // 3D step: mu of psi^n, the collide-stream with the force -psi grad mu, the
 // velocity of the new fluid state, then one fused launch per Runge-Kutta stage
 // of psi advected by that velocity (Gauss-Seidel coupling).
@@ -382,7 +410,7 @@ int step_rep3(flb_handle *h, Rep &r)
 {
     const flb_params &p = r.p;
     cudaStream_t st = h->st;
-    float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
+    float *psi_n = r.psi[r.pcur];
     const LBArgs la = lb_args(r, psi_n);
     cudaEvent_t e0 = mark(h);
     if (p.coupling & FLB_COUPLE_FORCE) FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
@@ -391,15 +419,8 @@ int step_rep3(flb_handle *h, Rep &r)
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
     FLB_TRY(launch_vel3(la, p.storage, st));
-    const bool noisy = p.kT > 0 && p.M > 0;
-    const bool heun = p.integrator == FLB_HEUN;
-    const int advect = (p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
-    const PhiloxKey key = philox_key(p.seed);
-    FLB_TRY(launch_psi3(r.g, p.psi_scheme, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
-                        (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, h->status, st));
-    if (heun)
-        FLB_TRY(launch_psi3(r.g, p.psi_scheme, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
-                            (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, h->status, st));
+    const int rc = launch_psi_stages(h, r);
+    if (rc != FLB_OK) return rc;
     cudaEvent_t e3 = mark(h);
     span(h, 0, e1, e2, 1);
     span(h, 1, e0, e1, (p.coupling & FLB_COUPLE_FORCE) ? 1 : 0);
@@ -579,12 +600,14 @@ int batch_upload_lists(flb_handle *h)
     const size_t nlb = v.size() - nmu;
     for (int r = 0; r < (int)h->reps.size(); ++r) {
         const Geom &g = h->reps[(size_t)r].g;
-        for (int bz = 0; bz < (g.nz + PS_ZC - 1) / PS_ZC; ++bz)
+        const int zc = h->reps[(size_t)r].zc;
+        for (int bz = 0; bz < (g.nz + zc - 1) / zc; ++bz)
             for (int by = 0; by < (g.ny + PS_TY - 1) / PS_TY; ++by)
                 for (int bx = 0; bx < (g.nx + PS_TX - 1) / PS_TX; ++bx) v.push_back({r, bx, by, bz});
     }
     const size_t npsi = v.size() - nmu - nlb;
-    if ((int)nmu != h->b_nmu || (int)nlb != h->b_nlb || (int)npsi != h->b_npsi) return FLB_EINVAL;
+    if ((int)nmu != h->b_nmu || (int)nlb != h->b_nlb || (int)npsi > h->b_npsi_cap) return FLB_EINVAL;
+    h->b_npsi = (int)npsi;
     int rc = cuerr(cudaMemcpyAsync(h->b_mu, v.data(), nmu * sizeof(BatchBlock), cudaMemcpyHostToDevice, h->st));
     if (rc == FLB_OK)
         rc = cuerr(cudaMemcpyAsync(h->b_lb, v.data() + nmu, nlb * sizeof(BatchBlock), cudaMemcpyHostToDevice, h->st));
@@ -617,6 +640,7 @@ int batch_upload_table(flb_handle *h)
         d.heun = r.p.integrator == FLB_HEUN;
         d.advect = (r.p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
         d.noise = r.p.kT > 0 && r.p.M > 0;
+        d.zc = r.zc;
         const uint64_t pd[3] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz};
         const uint64_t ps[2] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4};
         const uint32_t pb[3] = {(uint32_t)(PS_TX + 8), (uint32_t)(PS_TY + 6), 1};
@@ -1023,6 +1047,207 @@ int flb_sq_reset(flb_handle *h, int32_t rep)
         r.sq_n = r.h_n = 0;
     }
     return cuerr(cudaStreamSynchronize(h->st));
+}
+
+}  // extern "C"
+
+namespace {
+// Drop the batched mode's captured graph and block lists (rebuilt by the next batched step).
+void batch_reset(flb_handle *h)
+{
+    if (h->b_exec) cudaGraphExecDestroy(h->b_exec);
+    if (h->b_graph) cudaGraphDestroy(h->b_graph);
+    h->b_exec = nullptr;
+    h->b_graph = nullptr;
+    h->b_lists_ok = false;
+}
+
+std::string device_key()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+    for (char &c : name)
+        if (c == ' ' || c == '\t' || c == '|') c = '_';
+    return name + "|sm" + std::to_string(sms);
+}
+
+std::string rep_key(const Rep &r)
+{
+    char b[160];
+    std::snprintf(b, sizeof b, "%dx%dx%d|q%d|s%d|i%d|n%d|a%d", r.g.nx, r.g.ny, r.g.nz, r.q, r.p.psi_scheme,
+                  r.p.integrator, (r.p.kT > 0 && r.p.M > 0) ? 1 : 0, (r.p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0);
+    return b;
+}
+
+// Tuning cache: one "key<TAB>planes" line per tuned configuration; later lines win.
+std::map<std::string, int> read_cache(const char *path)
+{
+    std::map<std::string, int> m;
+    if (!path) return m;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return m;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char *tab = std::strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        const int v = std::atoi(tab + 1);
+        if (v >= PS_ZC_MIN && v <= 4096) m[line] = v;
+    }
+    std::fclose(f);
+    return m;
+}
+
+void append_cache(const char *path, const std::string &key, int zc)
+{
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s\t%d\n", key.c_str(), zc);
+    std::fclose(f);
+}
+
+// Average device time of launch() over reps runs after one untimed run, in ms;
+// < 0 if a launch failed.
+float time_launches(flb_handle *h, const std::function<int()> &launch, int reps)
+{
+    if (launch() != FLB_OK) return -1.f;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1.f;
+    float ms = -1.f;
+    bool ok = cudaEventRecord(a, h->st) == cudaSuccess;
+    for (int k = 0; ok && k < reps; ++k) ok = launch() == FLB_OK;
+    ok = ok && cudaEventRecord(b, h->st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+         cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ok ? ms / reps : -1.f;
+}
+
+// Candidate planes per psi block for a box nz deep: every listed value below nz
+// and the first one that covers the whole depth.
+std::vector<int> zc_candidates(int nz)
+{
+    static const int kList[] = {4, 8, 16, 32, 64, 128, 256, 512};
+    std::vector<int> v;
+    for (int c : kList) {
+        v.push_back(c);
+        if (c >= nz) break;
+    }
+    return v;
+}
+}  // namespace
+
+extern "C" {
+
+int flb_get_tuning(flb_handle *h, int32_t rep, int32_t *psi_zchunk)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !psi_zchunk) return FLB_EINVAL;
+    *psi_zchunk = r->zc;
+    return FLB_OK;
+}
+
+int flb_set_tuning(flb_handle *h, int32_t rep, int32_t psi_zchunk)
+{
+    if (!h || psi_zchunk < PS_ZC_MIN || psi_zchunk > 4096) return FLB_EINVAL;
+    if (rep == -1) {
+        for (Rep &r : h->reps) r.zc = psi_zchunk;
+    } else {
+        Rep *r = get_rep(h, rep);
+        if (!r) return FLB_EINVAL;
+        r->zc = psi_zchunk;
+    }
+    batch_reset(h);
+    return FLB_OK;
+}
+
+int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
+{
+    if (!h || (flags & ~FLB_TUNE_FORCE)) return FLB_EINVAL;
+    int rc = take_status(h);
+    if (rc != FLB_OK) return rc;
+    const bool force = (flags & FLB_TUNE_FORCE) != 0;
+    const std::map<std::string, int> cache = force ? std::map<std::string, int>() : read_cache(cache_path);
+    const std::string dk = device_key();
+    const int reps = 3;
+    if (h->mode == FLB_MODE_BATCHED && batch_supported(h)) {
+        // one value for every replica, timed on the batched psi launches
+        std::string all;
+        bool noise = false;
+        int nzmax = 1;
+        for (const Rep &r : h->reps) {
+            all += rep_key(r) + ";";
+            noise |= r.p.kT > 0 && r.p.M > 0;
+            nzmax = std::max(nzmax, r.g.nz);
+        }
+        uint64_t hash = 1469598103934665603ull;  // FNV-1a over the replica keys
+        for (unsigned char c : all) hash = (hash ^ c) * 1099511628211ull;
+        char key[256];
+        std::snprintf(key, sizeof key, "batched|%s|%zu|%016llx", dk.c_str(), h->reps.size(), (unsigned long long)hash);
+        const bool heun = h->reps[0].p.integrator == FLB_HEUN;
+        int best = PS_ZC;
+        const auto it = cache.find(key);
+        if (it != cache.end()) {
+            best = it->second;
+        } else {
+            float tbest = 0.f;
+            for (int zc : zc_candidates(nzmax)) {
+                for (Rep &r : h->reps) r.zc = zc;
+                batch_reset(h);
+                rc = batch_upload_lists(h);
+                if (rc == FLB_OK) rc = batch_upload_table(h);
+                if (rc != FLB_OK) return rc;
+                const BatchLists L = batch_lists(h);
+                const float t = time_launches(h, [&]() {
+                    h->launches += heun ? 2 : 1;
+                    return cuerr(launch_batch_psi(L, heun, noise, h->st));
+                }, reps);
+                if (t < 0.f) return FLB_ECUDA;
+                if (tbest == 0.f || t < tbest) {
+                    tbest = t;
+                    best = zc;
+                }
+            }
+            append_cache(cache_path, key, best);
+        }
+        for (Rep &r : h->reps) r.zc = best;
+    } else {
+        std::map<std::string, int> done;
+        for (Rep &r : h->reps) {
+            if (r.dim != 3) continue;
+            const std::string key = "plain|" + dk + "|" + rep_key(r);
+            auto d = done.find(key);
+            if (d != done.end()) {
+                r.zc = d->second;
+                continue;
+            }
+            const auto it = cache.find(key);
+            if (it != cache.end()) {
+                r.zc = it->second;
+            } else {
+                float tbest = 0.f;
+                int best = PS_ZC;
+                for (int zc : zc_candidates(r.g.nz)) {
+                    r.zc = zc;
+                    const float t = time_launches(h, [&]() { return launch_psi_stages(h, r); }, reps);
+                    if (t < 0.f) return FLB_ECUDA;
+                    if (tbest == 0.f || t < tbest) {
+                        tbest = t;
+                        best = zc;
+                    }
+                }
+                r.zc = best;
+                append_cache(cache_path, key, best);
+            }
+            done[key] = r.zc;
+        }
+    }
+    batch_reset(h);
+    return take_status(h);
 }
 
 int flb_set_mode(flb_handle *h, int32_t mode)

@@ -91,7 +91,9 @@ constexpr int GZ3 = 3;
 
 // launch geometry of the 3D kernels (shared with the host for the batched block lists)
 constexpr int LB_BX = 32, LB_BY = 4, LB_BZ = 2;   // collide-stream and mu: one thread per site
-constexpr int PS_TX = 32, PS_TY = 16, PS_ZC = 64;  // psi stage: column tile and z chunk
+constexpr int PS_TX = 32, PS_TY = 16;  // psi stage: column tile of a block
+constexpr int PS_ZC = 64;              // psi stage: default planes per block (the z chunk), tunable per replica
+constexpr int PS_ZC_MIN = 1;           // smallest z chunk (sizes the batched block lists)
 
 struct Geom {
     int dim, nx, ny, nz;   // nz = 1 in 2D
@@ -203,6 +205,7 @@ struct alignas(128) BatchRep {
     float *psis, *E;
     float A, B, K, M;
     int heun, advect, noise;
+    int zc;                  // planes per psi block
 };
 
 struct BatchBlock {
@@ -221,6 +224,8 @@ cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, 
                                   const uint64_t *strides_bytes, const uint32_t *box);
 cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
                               bool noise, cudaStream_t st);
+// the psi stage launches of a batched step alone (no state change: the autotuner times them)
+cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, cudaStream_t st);
 
 // host launchers (flb_lb.cu, flb_psi.cu, flb_obs.cu)
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);
@@ -232,7 +237,7 @@ cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
 // one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu)
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
-                        const PhiloxKey &key, int64_t step, int *status, cudaStream_t st);
+                        const PhiloxKey &key, int64_t step, int zc, int *status, cudaStream_t st);
 // mu on the interior and one ghost layer of a 3D box (flb_lb3d.cu)
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,

@@ -61,6 +61,7 @@ struct Psi3Args {
     float *E;          // [N] Heun accumulator: written by stage 1, read by stage 2
     float A, B, K, M, kT;
     int advect, heun;
+    int zc;            // planes per block (the z chunk)
     PhiloxKey key;
     int64_t step;
 };
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(PS_NT) psi3_fd_kernel(const Psi3Args a)
     float *sZ = smu + 3 * H2N;   // [13][H1N] when NOISE
     const Geom &g = a.g;
     const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
-    const int x0 = blockIdx.x * PS_TX, y0 = blockIdx.y * PS_TY, z0 = blockIdx.z * PS_ZC;
-    const int z1 = min(z0 + PS_ZC, g.nz);
+    const int x0 = blockIdx.x * PS_TX, y0 = blockIdx.y * PS_TY, z0 = blockIdx.z * a.zc;
+    const int z1 = min(z0 + a.zc, g.nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < g.nx && y < g.ny;
     const float k22 = a.K * (1.0f / 22.0f);
@@ -312,8 +313,8 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     __shared__ int s_bad;
     const Geom &g = a.g;
     const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
-    const int x0 = bx * PS_TX, y0 = by * PS_TY, z0 = bz * PS_ZC;
-    const int z1 = min(z0 + PS_ZC, g.nz);
+    const int x0 = bx * PS_TX, y0 = by * PS_TY, z0 = bz * a.zc;
+    const int z1 = min(z0 + a.zc, g.nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < g.nx && y < g.ny;
     const float k22 = a.K * (1.0f / 22.0f);
@@ -568,6 +569,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
         sa.kT = r.noise ? r.lb.kT : 0.f;
         sa.advect = r.advect;
         sa.heun = r.heun;
+        sa.zc = r.zc;
         sa.key = r.lb.key;
         sa.step = r.lb.step + ds;
     }
@@ -580,12 +582,8 @@ __global__ void advance_kernel(long long *dstep) { *dstep += 1; }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st);
 
-cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
-                              bool noise, cudaStream_t st)
+cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, cudaStream_t st)
 {
-    if (!scheme_fv) return cudaErrorNotSupported;
-    cudaError_t e = launch_lb3_batch(L, storage, ghost, force, st);
-    if (e != cudaSuccess) return e;
     const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS;
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -593,13 +591,20 @@ cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool
         kernel<<<L.npsi, PS_NT, bytes, st>>>(L);
         return cudaGetLastError();
     };
-    e = noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + sizeof(float) * FV_NOISE_FLOATS)
-              : go(psi3_fv_tma_batch_kernel<1, false>, sm);
+    cudaError_t e = noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + sizeof(float) * FV_NOISE_FLOATS)
+                          : go(psi3_fv_tma_batch_kernel<1, false>, sm);
+    if (e != cudaSuccess || !heun) return e;
+    return go(psi3_fv_tma_batch_kernel<2, false>, sm);
+}
+
+cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
+                              bool noise, cudaStream_t st)
+{
+    if (!scheme_fv) return cudaErrorNotSupported;
+    cudaError_t e = launch_lb3_batch(L, storage, ghost, force, st);
     if (e != cudaSuccess) return e;
-    if (heun) {
-        e = go(psi3_fv_tma_batch_kernel<2, false>, sm);
-        if (e != cudaSuccess) return e;
-    }
+    e = launch_batch_psi(L, heun, noise, st);
+    if (e != cudaSuccess) return e;
     advance_kernel<<<1, 1, 0, st>>>(const_cast<long long *>(L.dstep));
     return cudaGetLastError();
 }
@@ -657,7 +662,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
     TmaArgs ta;
     ta.a = a;
     ta.status = status;
-    const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + PS_ZC - 1) / PS_ZC);
+    const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + a.zc - 1) / a.zc);
     const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS;
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -674,8 +679,9 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
 
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
-                        const PhiloxKey &key, int64_t step, int *status, cudaStream_t st)
+                        const PhiloxKey &key, int64_t step, int zc, int *status, cudaStream_t st)
 {
+    if (zc < PS_ZC_MIN) return cudaErrorInvalidValue;
     Psi3Args a;
     a.g = g;
     a.psi = psi;
@@ -689,9 +695,10 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
     a.kT = kT;
     a.advect = advect;
     a.heun = heun;
+    a.zc = zc;
     a.key = key;
     a.step = step;
-    const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + PS_ZC - 1) / PS_ZC);
+    const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + zc - 1) / zc);
     const size_t base = sizeof(float) * (4 * H3N + 3 * H2N);
     if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, status, st);
     if (stage == 1) {
