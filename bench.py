@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default psi tile depth (64 planes)")
     ap.add_argument("--ensemble-steps", type=int, default=40,
                     help="steps of the 256-replica ensemble timed batched vs plain (0: skip)")
     return ap.parse_args()
@@ -155,7 +156,7 @@ def lb_traffic(storage: int, n_sites: int):
         return None
 
 
-def ensemble_batched_vs_plain(F, I, steps, local, rank):
+def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
     """256 uneven D3Q19 replicas (64 each of 16^3, 24^3, 32^3, 48^3, kT_r in
     [1e-5, 1e-4], seed 1 + r): aggregate MLUPS of the batched launch (one launch
     per phase for all replicas, CUDA-graph replay) against the plain
@@ -171,6 +172,8 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank):
     for mode, key in ((F.FLB_MODE_PLAIN, "plain"), (F.FLB_MODE_BATCHED, "batched")):
         s = F.Solver(ps, device=f"cuda:{local}")
         s.set_mode(mode)
+        if autotune:
+            out[key + "_psi_zchunk"] = sorted(set(s.autotune()))
         s.step(3)
         s.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -233,6 +236,7 @@ def run_ours(args):
     s = F.Solver(p, device=f"cuda:{local}")
     psi0 = I.uniform_field(N, -0.01, 0.01, 11 + rank)
     s.set_fields(psi=psi0)
+    zchunk = s.autotune()[0] if not args.no_autotune else s.get_tuning(0)
     s.set_sampling(10, 1)
     s.step(args.warmup)
     s.synchronize()
@@ -297,7 +301,7 @@ def run_ours(args):
     if args.ensemble_steps > 0:
         del s
         torch.cuda.empty_cache()
-        ens = ensemble_batched_vs_plain(F, I, args.ensemble_steps, local, rank)
+        ens = ensemble_batched_vs_plain(F, I, args.ensemble_steps, local, rank, autotune=not args.no_autotune)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)
@@ -312,7 +316,7 @@ def run_ours(args):
             "config": {"workload": name, "box": [p.nx, p.ny, p.nz], "lattice": "D3Q19", "psi_scheme": "FV",
                        "integrator": "Heun", "sampling": "S(q) |k_a|<=8 every 10 steps",
                        "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 19 * N * (4 if storage == 0 else 2) / 1e9),
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}", "psi_zchunk": zchunk},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": lb_traffic(storage, N),
                          "kernel": "LB collide-stream", "peak_kind": peak_kind,

@@ -227,7 +227,7 @@ size_t carve_all(flb_handle &h, char *base)
     for (Rep &r : h.reps) {
         if (r.dim != 3) continue;
         const Geom &g = r.g;
-        nmu += ((g.nx + 2 + LB_BX - 1) / LB_BX) * ((g.ny + 2 + LB_BY - 1) / LB_BY) * ((g.nz + 2 + LB_BZ - 1) / LB_BZ);
+        nmu += ((g.nx + 2 + MU_BX - 1) / MU_BX) * ((g.ny + 2 + MU_BY - 1) / MU_BY) * ((g.nz + 2 + MU_ZC - 1) / MU_ZC);
         nlb += ((g.nx + LB_BX - 1) / LB_BX) * ((g.ny + LB_BY - 1) / LB_BY) * ((g.nz + LB_BZ - 1) / LB_BZ);
         npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC_MIN - 1) / PS_ZC_MIN);
     }
@@ -586,9 +586,9 @@ int batch_upload_lists(flb_handle *h)
     v.clear();
     for (int r = 0; r < (int)h->reps.size(); ++r) {
         const Geom &g = h->reps[(size_t)r].g;
-        for (int bz = 0; bz < (g.nz + 2 + LB_BZ - 1) / LB_BZ; ++bz)
-            for (int by = 0; by < (g.ny + 2 + LB_BY - 1) / LB_BY; ++by)
-                for (int bx = 0; bx < (g.nx + 2 + LB_BX - 1) / LB_BX; ++bx) v.push_back({r, bx, by, bz});
+        for (int bz = 0; bz < (g.nz + 2 + MU_ZC - 1) / MU_ZC; ++bz)
+            for (int by = 0; by < (g.ny + 2 + MU_BY - 1) / MU_BY; ++by)
+                for (int bx = 0; bx < (g.nx + 2 + MU_BX - 1) / MU_BX; ++bx) v.push_back({r, bx, by, bz});
     }
     const size_t nmu = v.size();
     for (int r = 0; r < (int)h->reps.size(); ++r) {

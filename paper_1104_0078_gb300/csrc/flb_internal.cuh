@@ -91,6 +91,7 @@ constexpr int GZ3 = 3;
 
 // launch geometry of the 3D kernels (shared with the host for the batched block lists)
 constexpr int LB_BX = 32, LB_BY = 4, LB_BZ = 2;   // collide-stream and mu: one thread per site
+constexpr int MU_BX = 32, MU_BY = 4, MU_ZC = 16;  // mu: column tile and planes of a block (interior + 1)
 constexpr int PS_TX = 32, PS_TY = 16;  // psi stage: column tile of a block
 constexpr int PS_ZC = 64;              // psi stage: default planes per block (the z chunk), tunable per replica
 constexpr int PS_ZC_MIN = 1;           // smallest z chunk (sizes the batched block lists)
@@ -116,12 +117,30 @@ struct Geom {
 };
 
 // Store v at interior site (x,y,z) of a padded plane and at every periodic image
-// of it that lies in the ghost frame within `rad` cells of the interior.  The
-// candidate images are unrolled with predicates (no local memory).
+// of it that lies in the ghost frame within `rad` cells of the interior.  When
+// every edge is at least 2 rad long a site has at most one image per axis, and
+// the images are the (at most 7) combinations of those offsets; shorter edges
+// take the general path over all candidate images.  No local memory is used.
 __device__ __forceinline__ void store_padded(float *a, const Geom &g, int x, int y, int z, float v, int rad)
 {
-    if (x >= rad && x < g.nx - rad && y >= rad && y < g.ny - rad && (g.dim == 2 || (z >= rad && z < g.nz - rad))) {
-        a[g.pidx32(x, y, z)] = v;
+    const int c = g.pidx32(x, y, z);
+    a[c] = v;
+    const bool ix = x >= rad && x < g.nx - rad, iy = y >= rad && y < g.ny - rad;
+    const bool iz = g.dim == 2 || (z >= rad && z < g.nz - rad);
+    if (ix && iy && iz) return;
+    if (g.nx >= 2 * rad && g.ny >= 2 * rad && (g.dim == 2 || g.nz >= 2 * rad)) {
+        const int ox = ix ? 0 : (x < rad ? g.nx : -g.nx);
+        const int oy = iy ? 0 : (y < rad ? g.ny : -g.ny) * g.px;
+        const int oz = iz ? 0 : (z < rad ? g.nz : -g.nz) * g.px * g.py;
+        if (ox) a[c + ox] = v;
+        if (oy) a[c + oy] = v;
+        if (ox && oy) a[c + ox + oy] = v;
+        if (oz) {
+            a[c + oz] = v;
+            if (ox) a[c + oz + ox] = v;
+            if (oy) a[c + oz + oy] = v;
+            if (ox && oy) a[c + oz + ox + oy] = v;
+        }
         return;
     }
     const int xs[3] = {x, x + g.nx, x - g.nx};
@@ -136,7 +155,7 @@ __device__ __forceinline__ void store_padded(float *a, const Geom &g, int x, int
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                if (vz[k] && vy[j] && vx[i]) a[g.pidx(xs[i], ys[j], zs[k])] = v;
+                if ((i | j | k) && vz[k] && vy[j] && vx[i]) a[g.pidx(xs[i], ys[j], zs[k])] = v;
 }
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }

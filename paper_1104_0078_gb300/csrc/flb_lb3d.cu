@@ -317,36 +317,47 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_kernel(const LBArgs 
     vel3_block<T, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer
+// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer.  A
+// block owns a 32 x 4 column of (x, y) in [-1, nx] x [-1, ny] and marches
+// MU_ZC planes of z in [-1, nz]; each thread keeps, for the planes below and
+// at z, the centre a, the 4 in-plane faces b and the 4 in-plane diagonals d of
+// psi, so that (Eq. solap)
+//   22 lap_SO psi(z) = 6 [b(z) + a(z-1) + a(z+1)] + 3 [d(z) + b(z-1) + b(z+1)]
+//                      + d(z-1) + d(z+1) - 80 a(z)
+// takes 9 loads per plane instead of 27.
 __device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
                                           float B, float K, int bx, int by, int bz)
 {
-    const int x = bx * LB_BX + (int)threadIdx.x - 1;
-    const int y = by * LB_BY + (int)threadIdx.y - 1;
-    const int z = bz * LB_BZ + (int)threadIdx.z - 1;
-    if (x > g.nx || y > g.ny || z > g.nz) return;
-    const int c = g.pidx32(x, y, z);
+    const int x = bx * MU_BX + (int)threadIdx.x - 1;
+    const int y = by * MU_BY + (int)threadIdx.y - 1;
+    const int zb = bz * MU_ZC - 1;                          // first output plane
+    const int ze = min(zb + MU_ZC, g.nz + 1);               // one past the last
+    if (x > g.nx || y > g.ny || zb >= ze) return;
     const int Y = g.px, Z = g.px * g.py;
-    const float *p = psi;
-    const float n1 = (__ldg(p + c - 1) + __ldg(p + c + 1)) + (__ldg(p + c - Y) + __ldg(p + c + Y)) +
-                     (__ldg(p + c - Z) + __ldg(p + c + Z));
-    float n2 = (__ldg(p + c - 1 - Y) + __ldg(p + c + 1 - Y)) + (__ldg(p + c - 1 + Y) + __ldg(p + c + 1 + Y));
-    n2 += (__ldg(p + c - 1 - Z) + __ldg(p + c + 1 - Z)) + (__ldg(p + c - Y - Z) + __ldg(p + c + Y - Z));
-    n2 += (__ldg(p + c - 1 + Z) + __ldg(p + c + 1 + Z)) + (__ldg(p + c - Y + Z) + __ldg(p + c + Y + Z));
-    const float n3 = ((__ldg(p + c - 1 - Y - Z) + __ldg(p + c + 1 - Y - Z)) + (__ldg(p + c - 1 + Y - Z) + __ldg(p + c + 1 + Y - Z))) +
-                     ((__ldg(p + c - 1 - Y + Z) + __ldg(p + c + 1 - Y + Z)) + (__ldg(p + c - 1 + Y + Z) + __ldg(p + c + 1 + Y + Z)));
-    const float ps = __ldg(p + c);
-    mu[c] = A * ps + B * ps * ps * ps - K * (1.0f / 22.0f) * (6.f * n1 + 3.f * n2 + n3 - 80.f * ps);
+    const float k22 = K * (1.0f / 22.0f);
+    int c = g.pidx32(x, y, zb - 1);
+    float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f;  // planes p-2, p-1
+    for (int p = zb - 1; p <= ze; ++p, c += Z) {
+        const float a2 = __ldg(psi + c);
+        const float b2 = (__ldg(psi + c - 1) + __ldg(psi + c + 1)) + (__ldg(psi + c - Y) + __ldg(psi + c + Y));
+        const float d2 = (__ldg(psi + c - 1 - Y) + __ldg(psi + c + 1 - Y)) + (__ldg(psi + c - 1 + Y) + __ldg(psi + c + 1 + Y));
+        if (p - 1 >= zb) {
+            const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
+            mu[c - Z] = A * a1 + B * a1 * a1 * a1 - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * a1);
+        }
+        a0 = a1; b0 = b1; d0 = d1;
+        a1 = a2; b1 = b2; d1 = d2;
+    }
 }
 
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_kernel(const Geom g, const float *__restrict__ psi,
-                                                               float *__restrict__ mu, float A, float B, float K)
+__global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,
+                                                          float *__restrict__ mu, float A, float B, float K)
 {
     mu3_block(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) mu3_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchLists L)
 {
     const BatchBlock b = L.mu[blockIdx.x];
     const BatchRep &r = L.reps[b.rep];
@@ -401,7 +412,7 @@ cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool 
 {
     const dim3 block(LB_BX, LB_BY, LB_BZ);
     if (force && L.nmu > 0) {
-        mu3_batch_kernel<<<L.nmu, block, 0, st>>>(L);
+        mu3_batch_kernel<<<L.nmu, dim3(MU_BX, MU_BY, 1), 0, st>>>(L);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -428,8 +439,8 @@ cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool 
 
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
-    const dim3 grid((g.nx + 2 + LB_BX - 1) / LB_BX, (g.ny + 2 + LB_BY - 1) / LB_BY, (g.nz + 2 + LB_BZ - 1) / LB_BZ);
+    const dim3 block(MU_BX, MU_BY, 1);
+    const dim3 grid((g.nx + 2 + MU_BX - 1) / MU_BX, (g.ny + 2 + MU_BY - 1) / MU_BY, (g.nz + 2 + MU_ZC - 1) / MU_ZC);
     mu3_kernel<<<grid, block, 0, st>>>(g, psi, mu, A, B, K);
     return cudaGetLastError();
 }
