@@ -141,15 +141,24 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+LB_SOURCES = ("flb_lb3d.cu", "flb_site3d.cuh", "flb_internal.cuh")
+
+
+def lb_source_sha():
+    """sha256 over the sources the collide-stream kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in LB_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1104_0078_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def lb_traffic(storage: int, n_sites: int):
     """DRAM bytes per LB launch from the committed ncu summary, if it was taken on
-    the current kernel source; scaled by sites when the capture was smaller."""
+    the current kernel sources; scaled by sites when the capture was smaller."""
     path = os.path.join(ROOT, "profiles", "lb_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_1104_0078_gb300", "csrc", "flb_lb3d.cu")
     try:
         rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("source_sha256") != sha or rec.get("storage") != storage:
+        if rec.get("source_sha256") != lb_source_sha() or rec.get("storage") != storage:
             return None
         return rec["dram_bytes_per_launch"] * n_sites / rec["sites"]
     except (OSError, KeyError, ValueError):

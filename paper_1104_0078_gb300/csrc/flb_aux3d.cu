@@ -1,0 +1,151 @@
+// flb_aux3d.cu -- the two D3Q19 step kernels around the collide-stream.
+//
+// mu3_kernel writes the chemical potential mu = A psi + B psi^3 - K lap_SO psi
+// (Sec. II.A; SO stencil of App. A) on the interior and one ghost layer, for the
+// force density of the collide-stream.  vel3_kernel runs after it: it gathers
+// the populations the next step pulls (the planes just written) and writes the
+// velocity (sum fbar c + F/2)/rho of the new fluid state, which advects psi
+// (Gauss-Seidel coupling: the psi step follows the fluid step).  Both have a
+// batched variant that walks a block work list over all replicas.
+#include "flb_site3d.cuh"
+
+namespace flb {
+
+// Velocity of the streamed state after the step: u = (sum fbar c + F/2)/rho
+// with fbar the populations the next step pulls (the planes just written, a.fout)
+// and F this step's force density -- the velocity that advects psi (Gauss-Seidel
+// coupling of Sec. VI: the psi step follows the fluid step).
+template <typename T, bool FORCE>
+__device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int bz)
+{
+    const Geom &g = a.g;
+    const int x = bx * LB_BX + threadIdx.x;
+    const int y = by * LB_BY + threadIdx.y;
+    const int z = bz * LB_BZ + threadIdx.z;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+    float f[19];
+    pull19((const T *)a.fout, g, x, y, z, f);
+    float sp[10], dp[10];
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) {
+        sp[p] = f[2 * p - 1] + f[2 * p];
+        dp[p] = f[2 * p - 1] - f[2 * p];
+    }
+    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
+    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
+    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
+    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3(a, x, y, z, Fx, Fy, Fz);
+    const float irho = __fdividef(1.0f, a.rho0 + drho);
+    store_padded(a.u, g, x, y, z, (jx + 0.5f * Fx) * irho, 1);
+    store_padded(a.u + g.pn, g, x, y, z, (jy + 0.5f * Fy) * irho, 1);
+    store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
+}
+
+template <typename T, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_kernel(const LBArgs a)
+{
+    vel3_block<T, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer.  A
+// block owns a 32 x 4 column of (x, y) in [-1, nx] x [-1, ny] and marches
+// MU_ZC planes of z in [-1, nz]; each thread keeps, for the planes below and
+// at z, the centre a, the 4 in-plane faces b and the 4 in-plane diagonals d of
+// psi, so that (Eq. solap)
+//   22 lap_SO psi(z) = 6 [b(z) + a(z-1) + a(z+1)] + 3 [d(z) + b(z-1) + b(z+1)]
+//                      + d(z-1) + d(z+1) - 80 a(z)
+// takes 9 loads per plane instead of 27.
+__device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
+                                          float B, float K, int bx, int by, int bz)
+{
+    const int x = bx * MU_BX + (int)threadIdx.x - 1;
+    const int y = by * MU_BY + (int)threadIdx.y - 1;
+    const int zb = bz * MU_ZC - 1;                          // first output plane
+    const int ze = min(zb + MU_ZC, g.nz + 1);               // one past the last
+    if (x > g.nx || y > g.ny || zb >= ze) return;
+    const int Y = g.px, Z = g.px * g.py;
+    const float k22 = K * (1.0f / 22.0f);
+    int c = g.pidx32(x, y, zb - 1);
+    float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f;  // planes p-2, p-1
+    for (int p = zb - 1; p <= ze; ++p, c += Z) {
+        const float a2 = __ldg(psi + c);
+        const float b2 = (__ldg(psi + c - 1) + __ldg(psi + c + 1)) + (__ldg(psi + c - Y) + __ldg(psi + c + Y));
+        const float d2 = (__ldg(psi + c - 1 - Y) + __ldg(psi + c + 1 - Y)) + (__ldg(psi + c - 1 + Y) + __ldg(psi + c + 1 + Y));
+        if (p - 1 >= zb) {
+            const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
+            mu[c - Z] = A * a1 + B * a1 * a1 * a1 - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * a1);
+        }
+        a0 = a1; b0 = b1; d0 = d1;
+        a1 = a2; b1 = b2; d1 = d2;
+    }
+}
+
+__global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,
+                                                          float *__restrict__ mu, float A, float B, float K)
+{
+    mu3_block(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
+__global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchLists L)
+{
+    const BatchBlock b = L.mu[blockIdx.x];
+    const BatchRep &r = L.reps[b.rep];
+    const int par = (int)(*L.dstep & 1);
+    mu3_block(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
+}
+
+template <typename T, bool FORCE>
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_batch_kernel(const BatchLists L)
+{
+    __shared__ LBArgs sa;
+    const BatchBlock b = L.lb[blockIdx.x];
+    batch_lb_args(L, L.reps[b.rep], sa);
+    vel3_block<T, FORCE>(sa, b.bx, b.by, b.bz);
+}
+
+cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)
+{
+    const dim3 block(MU_BX, MU_BY, 1);
+    const dim3 grid((g.nx + 2 + MU_BX - 1) / MU_BX, (g.ny + 2 + MU_BY - 1) / MU_BY, (g.nz + 2 + MU_ZC - 1) / MU_ZC);
+    mu3_kernel<<<grid, block, 0, st>>>(g, psi, mu, A, B, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t st)
+{
+    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
+    const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;
+    if (storage == FLB_F16_DEV) {
+        if (force) vel3_kernel<__half, true><<<grid, block, 0, st>>>(a);
+        else vel3_kernel<__half, false><<<grid, block, 0, st>>>(a);
+    } else {
+        if (force) vel3_kernel<float, true><<<grid, block, 0, st>>>(a);
+        else vel3_kernel<float, false><<<grid, block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu3_batch(const BatchLists &L, cudaStream_t st)
+{
+    if (L.nmu > 0) mu3_batch_kernel<<<L.nmu, dim3(MU_BX, MU_BY, 1), 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vel3_batch(const BatchLists &L, int storage, bool force, cudaStream_t st)
+{
+    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    if (storage == FLB_F16_DEV) {
+        if (force) vel3_batch_kernel<__half, true><<<L.nlb, block, 0, st>>>(L);
+        else vel3_batch_kernel<__half, false><<<L.nlb, block, 0, st>>>(L);
+    } else {
+        if (force) vel3_batch_kernel<float, true><<<L.nlb, block, 0, st>>>(L);
+        else vel3_batch_kernel<float, false><<<L.nlb, block, 0, st>>>(L);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace flb

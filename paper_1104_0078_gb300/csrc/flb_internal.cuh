@@ -250,8 +250,11 @@ cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, cudaStr
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);
 // D3Q19 collide-stream that computes mu and the force itself from psi (flb_lb3d.cu)
 cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t s);
-// velocity of the streamed state after a step, written to a.u (flb_lb3d.cu, flb_lb.cu)
+// velocity of the streamed state after a step, written to a.u (flb_aux3d.cu, flb_lb.cu)
 cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t s);
+// batched mu and velocity over the work lists (flb_aux3d.cu)
+cudaError_t launch_mu3_batch(const BatchLists &L, cudaStream_t st);
+cudaError_t launch_vel3_batch(const BatchLists &L, int storage, bool force, cudaStream_t st);
 cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
 // one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu)
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,

@@ -1,76 +1,20 @@
 // flb_lb3d.cu -- D3Q19 fused collide-stream, one thread per site.
 //
-// The chemical potential mu = A psi + B psi^3 - K lap_SO psi (Sec. II.A; SO
-// stencil of App. A) is first written on the interior and one ghost layer by
-// mu3_kernel; the collide-stream kernel then forms the force density of Sec. IV,
-// F = -psi grad mu (central difference, or the FV gradient of Eq. (fvgrad) when
-// psi moves by the FV scheme, so that the force is the negative adjoint of the
-// divergence that advects psi), pulls its 19 populations, relaxes them in moment space
-// with noise on the stress and ghost modes (Eq. bab, Sec. III) and writes the
-// post-collision populations.  vel3_kernel then gathers the streamed
-// populations and writes the velocity (sum fbar c + F/2)/rho of the new fluid
-// state, which advects psi (Gauss-Seidel coupling: the psi step follows the
-// fluid step).
+// The kernel forms the force density of Sec. IV, F = -psi grad mu, from the mu
+// field (central difference, or the FV gradient of Eq. (fvgrad) when psi moves
+// by the FV scheme, so that the force is the negative adjoint of the divergence
+// that advects psi), pulls its 19 populations, relaxes them in moment space with
+// noise on the stress and ghost modes (Eq. bab, Sec. III) and writes the
+// post-collision populations.  mu comes from mu3_kernel and the velocity that
+// advects psi from vel3_kernel (flb_aux3d.cu).
 //
 // Indices are 32-bit (N and the padded planes are < 2^31); population plane i
-// of N sites starts at fin + i*N.
-//
-// D3Q19.  Plane order: 0 rest; pairs (1,2) +-x, (3,4) +-y, (5,6) +-z,
-// (7,8) +-(1,1,0), (9,10) +-(1,-1,0), (11,12) +-(1,0,1), (13,14) +-(1,0,-1),
-// (15,16) +-(0,1,1), (17,18) +-(0,1,-1).
-// Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2, xy, yz, zx, three c^2 c_a ghosts,
-// three c_a(c_b^2-c_g^2) ghosts, c^4, c^2(3c_x^2-c^2), c^2(c_y^2-c_z^2).
-#include "flb_internal.cuh"
+// of N sites starts at fin + i*N.  Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2,
+// xy, yz, zx, three c^2 c_a ghosts, three c_a(c_b^2-c_g^2) ghosts, c^4,
+// c^2(3c_x^2-c^2), c^2(c_y^2-c_z^2).
+#include "flb_site3d.cuh"
 
 namespace flb {
-
-template <typename T>
-__device__ __forceinline__ float ld3(const T *p, int i);
-template <>
-__device__ __forceinline__ float ld3<float>(const float *p, int i) { return __ldg(p + i); }
-template <>
-__device__ __forceinline__ float ld3<__half>(const __half *p, int i) { return __half2float(p[i]); }
-
-template <typename T>
-__device__ __forceinline__ void st3(T *p, int i, float v);
-template <>
-__device__ __forceinline__ void st3<float>(float *p, int i, float v) { p[i] = v; }
-template <>
-__device__ __forceinline__ void st3<__half>(__half *p, int i, float v) { p[i] = __float2half_rn(v); }
-
-// Pull of the 19 populations of site (x, y, z) from stored post-collision
-// planes fi: fbar_i(r) = stored_i(r - c_i).
-template <typename T>
-__device__ __forceinline__ void pull19(const T *fi, const Geom &g, int x, int y, int z, float f[19])
-{
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int N = (int)g.n;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    const int row = nx, pl = nx * ny;
-    const int sY0 = row * y, sYm = row * ym, sYp = row * yp;
-    const int sZ0 = pl * z, sZm = pl * zm, sZp = pl * zp;
-    f[0] = ld3(fi, x + sY0 + sZ0);
-    f[1] = ld3(fi + 1ll * N, xm + sY0 + sZ0);
-    f[2] = ld3(fi + 2ll * N, xp + sY0 + sZ0);
-    f[3] = ld3(fi + 3ll * N, x + sYm + sZ0);
-    f[4] = ld3(fi + 4ll * N, x + sYp + sZ0);
-    f[5] = ld3(fi + 5ll * N, x + sY0 + sZm);
-    f[6] = ld3(fi + 6ll * N, x + sY0 + sZp);
-    f[7] = ld3(fi + 7ll * N, xm + sYm + sZ0);
-    f[8] = ld3(fi + 8ll * N, xp + sYp + sZ0);
-    f[9] = ld3(fi + 9ll * N, xm + sYp + sZ0);
-    f[10] = ld3(fi + 10ll * N, xp + sYm + sZ0);
-    f[11] = ld3(fi + 11ll * N, xm + sY0 + sZm);
-    f[12] = ld3(fi + 12ll * N, xp + sY0 + sZp);
-    f[13] = ld3(fi + 13ll * N, xm + sY0 + sZp);
-    f[14] = ld3(fi + 14ll * N, xp + sY0 + sZm);
-    f[15] = ld3(fi + 15ll * N, x + sYm + sZm);
-    f[16] = ld3(fi + 16ll * N, x + sYp + sZp);
-    f[17] = ld3(fi + 17ll * N, x + sYm + sZp);
-    f[18] = ld3(fi + 18ll * N, x + sYp + sZm);
-}
 
 // One D3Q19 site: pull, moments, relaxation with force and noise, store.
 template <typename T, bool GHOST_RELAX>
@@ -220,42 +164,6 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     st3(fo + 18ll * N, s, w2 * (E - O));
 }
 
-// Force density F = -psi grad mu of Sec. IV at an interior site.
-__device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, float &Fx, float &Fy, float &Fz)
-{
-    const Geom &g = a.g;
-    // F = -psi grad mu, mu read from its field (valid on the interior + 1,
-    // edges and corners included)
-    const int pi = g.pidx32(x, y, z);
-    const int sy = g.px, sz = g.px * g.py;
-    const float ps = __ldg(a.psi + pi);
-    const float *mu = a.mu;
-    const float dx = __ldg(mu + pi + 1) - __ldg(mu + pi - 1);
-    const float dy = __ldg(mu + pi + sy) - __ldg(mu + pi - sy);
-    const float dz = __ldg(mu + pi + sz) - __ldg(mu + pi - sz);
-    if (a.fv_force) {
-        // FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i), Eq. (fvgrad): with
-        // w = 1/18 (faces), 1/36 (edges) it is [2 (face difference) + sum of
-        // the 8 edge neighbours signed by c_a] / 12
-        const float xyp = __ldg(mu + pi + 1 + sy), xym = __ldg(mu + pi + 1 - sy);
-        const float yxp = __ldg(mu + pi - 1 + sy), yxm = __ldg(mu + pi - 1 - sy);
-        const float xzp = __ldg(mu + pi + 1 + sz), xzm = __ldg(mu + pi + 1 - sz);
-        const float zxp = __ldg(mu + pi - 1 + sz), zxm = __ldg(mu + pi - 1 - sz);
-        const float yzp = __ldg(mu + pi + sy + sz), yzm = __ldg(mu + pi + sy - sz);
-        const float zyp = __ldg(mu + pi - sy + sz), zym = __ldg(mu + pi - sy - sz);
-        // xyp = mu(+1,+1,0), xym = mu(+1,-1,0), yxp = mu(-1,+1,0), yxm = mu(-1,-1,0);
-        // likewise in the (x,z) and (y,z) planes
-        const float c = -ps * (1.0f / 12.0f);
-        Fx = c * (2.f * dx + ((xyp + xym) - (yxp + yxm)) + ((xzp + xzm) - (zxp + zxm)));
-        Fy = c * (2.f * dy + ((xyp - xym) + (yxp - yxm)) + ((yzp + yzm) - (zyp + zym)));
-        Fz = c * (2.f * dz + ((xzp - xzm) + (zxp - zxm)) + ((yzp - yzm) + (zyp - zym)));
-    } else {
-        Fx = -ps * 0.5f * dx;
-        Fy = -ps * 0.5f * dy;
-        Fz = -ps * 0.5f * dz;
-    }
-}
-
 // One thread per site on a 3D grid of 32 x 4 x 2 blocks (a warp covers 32
 // consecutive x, so every population plane is read and written in full rows).
 
@@ -279,117 +187,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_kernel(const LBArgs a
     lb3_block<T, GHOST_RELAX, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Velocity of the streamed state after the step: u = (sum fbar c + F/2)/rho
-// with fbar the populations the next step pulls (the planes just written, a.fout)
-// and F this step's force density -- the velocity that advects psi (Gauss-Seidel
-// coupling of Sec. VI: the psi step follows the fluid step).
-template <typename T, bool FORCE>
-__device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int bz)
-{
-    const Geom &g = a.g;
-    const int x = bx * LB_BX + threadIdx.x;
-    const int y = by * LB_BY + threadIdx.y;
-    const int z = bz * LB_BZ + threadIdx.z;
-    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-    float f[19];
-    pull19((const T *)a.fout, g, x, y, z, f);
-    float sp[10], dp[10];
-#pragma unroll
-    for (int p = 1; p <= 9; ++p) {
-        sp[p] = f[2 * p - 1] + f[2 * p];
-        dp[p] = f[2 * p - 1] - f[2 * p];
-    }
-    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
-    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
-    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
-    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3(a, x, y, z, Fx, Fy, Fz);
-    const float irho = __fdividef(1.0f, a.rho0 + drho);
-    store_padded(a.u, g, x, y, z, (jx + 0.5f * Fx) * irho, 1);
-    store_padded(a.u + g.pn, g, x, y, z, (jy + 0.5f * Fy) * irho, 1);
-    store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
-}
-
-template <typename T, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_kernel(const LBArgs a)
-{
-    vel3_block<T, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
-}
-
-// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer.  A
-// block owns a 32 x 4 column of (x, y) in [-1, nx] x [-1, ny] and marches
-// MU_ZC planes of z in [-1, nz]; each thread keeps, for the planes below and
-// at z, the centre a, the 4 in-plane faces b and the 4 in-plane diagonals d of
-// psi, so that (Eq. solap)
-//   22 lap_SO psi(z) = 6 [b(z) + a(z-1) + a(z+1)] + 3 [d(z) + b(z-1) + b(z+1)]
-//                      + d(z-1) + d(z+1) - 80 a(z)
-// takes 9 loads per plane instead of 27.
-__device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
-                                          float B, float K, int bx, int by, int bz)
-{
-    const int x = bx * MU_BX + (int)threadIdx.x - 1;
-    const int y = by * MU_BY + (int)threadIdx.y - 1;
-    const int zb = bz * MU_ZC - 1;                          // first output plane
-    const int ze = min(zb + MU_ZC, g.nz + 1);               // one past the last
-    if (x > g.nx || y > g.ny || zb >= ze) return;
-    const int Y = g.px, Z = g.px * g.py;
-    const float k22 = K * (1.0f / 22.0f);
-    int c = g.pidx32(x, y, zb - 1);
-    float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f;  // planes p-2, p-1
-    for (int p = zb - 1; p <= ze; ++p, c += Z) {
-        const float a2 = __ldg(psi + c);
-        const float b2 = (__ldg(psi + c - 1) + __ldg(psi + c + 1)) + (__ldg(psi + c - Y) + __ldg(psi + c + Y));
-        const float d2 = (__ldg(psi + c - 1 - Y) + __ldg(psi + c + 1 - Y)) + (__ldg(psi + c - 1 + Y) + __ldg(psi + c + 1 + Y));
-        if (p - 1 >= zb) {
-            const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
-            mu[c - Z] = A * a1 + B * a1 * a1 * a1 - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * a1);
-        }
-        a0 = a1; b0 = b1; d0 = d1;
-        a1 = a2; b1 = b2; d1 = d2;
-    }
-}
-
-__global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,
-                                                          float *__restrict__ mu, float A, float B, float K)
-{
-    mu3_block(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
-}
-
-// ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
-__global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchLists L)
-{
-    const BatchBlock b = L.mu[blockIdx.x];
-    const BatchRep &r = L.reps[b.rep];
-    const int par = (int)(*L.dstep & 1);
-    mu3_block(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
-}
-
-// Per-block LBArgs of a batched launch, in shared memory: the replica's
-// arguments with the population buffers swapped on odd device steps, the psi
-// buffer of the step and the step's noise counter.
-__device__ __forceinline__ void batch_lb_args(const BatchLists &L, const BatchRep &r, LBArgs &sa)
-{
-    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    {
-        const int *src = reinterpret_cast<const int *>(&r.lb);
-        int *dst = reinterpret_cast<int *>(&sa);
-        for (int k = tid; k < (int)(sizeof(LBArgs) / sizeof(int)); k += LB_BX * LB_BY * LB_BZ) dst[k] = src[k];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const long long ds = *L.dstep;
-        if (ds & 1) {
-            const void *t = sa.fin;
-            sa.fin = sa.fout;
-            sa.fout = const_cast<void *>(t);
-        }
-        sa.psi = r.psi[ds & 1];
-        sa.step = r.lb.step + ds;
-    }
-    __syncthreads();
-}
-
+// ---- batched variant: block b of the launch works on L.lb[b] -------
 template <typename T, bool GHOST_RELAX, bool FORCE>
 __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const BatchLists L)
 {
@@ -399,21 +197,11 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const Ba
     lb3_block<T, GHOST_RELAX, FORCE>(sa, b.bx, b.by, b.bz);
 }
 
-template <typename T, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_batch_kernel(const BatchLists L)
-{
-    __shared__ LBArgs sa;
-    const BatchBlock b = L.lb[blockIdx.x];
-    batch_lb_args(L, L.reps[b.rep], sa);
-    vel3_block<T, FORCE>(sa, b.bx, b.by, b.bz);
-}
-
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)
 {
     const dim3 block(LB_BX, LB_BY, LB_BZ);
-    if (force && L.nmu > 0) {
-        mu3_batch_kernel<<<L.nmu, dim3(MU_BX, MU_BY, 1), 0, st>>>(L);
-        const cudaError_t e = cudaGetLastError();
+    if (force) {
+        const cudaError_t e = launch_mu3_batch(L, st);
         if (e != cudaSuccess) return e;
     }
 #define FLB_LB3B(T, G, F) lb3_batch_kernel<T, G, F><<<L.nlb, block, 0, st>>>(L)
@@ -425,24 +213,9 @@ cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool 
         else { if (force) FLB_LB3B(float, false, true); else FLB_LB3B(float, false, false); }
     }
 #undef FLB_LB3B
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (storage == FLB_F16_DEV) {
-        if (force) vel3_batch_kernel<__half, true><<<L.nlb, block, 0, st>>>(L);
-        else vel3_batch_kernel<__half, false><<<L.nlb, block, 0, st>>>(L);
-    } else {
-        if (force) vel3_batch_kernel<float, true><<<L.nlb, block, 0, st>>>(L);
-        else vel3_batch_kernel<float, false><<<L.nlb, block, 0, st>>>(L);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)
-{
-    const dim3 block(MU_BX, MU_BY, 1);
-    const dim3 grid((g.nx + 2 + MU_BX - 1) / MU_BX, (g.ny + 2 + MU_BY - 1) / MU_BY, (g.nz + 2 + MU_ZC - 1) / MU_ZC);
-    mu3_kernel<<<grid, block, 0, st>>>(g, psi, mu, A, B, K);
-    return cudaGetLastError();
+    return launch_vel3_batch(L, storage, force, st);
 }
 
 cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t st)
@@ -460,21 +233,6 @@ cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t st)
         else { if (force) FLB_LB3(float, false, true); else FLB_LB3(float, false, false); }
     }
 #undef FLB_LB3
-    return cudaGetLastError();
-}
-
-cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t st)
-{
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
-    const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
-    const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;
-    if (storage == FLB_F16_DEV) {
-        if (force) vel3_kernel<__half, true><<<grid, block, 0, st>>>(a);
-        else vel3_kernel<__half, false><<<grid, block, 0, st>>>(a);
-    } else {
-        if (force) vel3_kernel<float, true><<<grid, block, 0, st>>>(a);
-        else vel3_kernel<float, false><<<grid, block, 0, st>>>(a);
-    }
     return cudaGetLastError();
 }
 
