@@ -167,9 +167,10 @@ def lb_traffic(storage: int, n_sites: int):
 
 def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
     """256 uneven D3Q19 replicas (64 each of 16^3, 24^3, 32^3, 48^3, kT_r in
-    [1e-5, 1e-4], seed 1 + r): aggregate MLUPS of the batched launch (one launch
-    per phase for all replicas, CUDA-graph replay) against the plain
-    per-replica launch sequence, same state, same number of steps."""
+    [1e-5, 1e-4], seed 1 + r): aggregate MLUPS of the plain per-replica launch
+    sequence, of the batched mode (one launch per phase for all replicas,
+    CUDA-graph replay) and of the persistent mode (one cooperative launch for
+    all replicas and all steps), same state, same number of steps."""
     import torch
     reps = I.ensemble()
     ps = [F.flb_params_default(nx=d["nx"], ny=d["ny"], nz=d["nz"], tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"],
@@ -178,7 +179,8 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
     sites = sum(p.nx * p.ny * p.nz for p in ps)
     out = {"workload": "256 D3Q19 replicas (64 each of 16^3, 24^3, 32^3, 48^3), FV, Heun", "sites": sites,
            "steps": steps}
-    for mode, key in ((F.FLB_MODE_PLAIN, "plain"), (F.FLB_MODE_BATCHED, "batched")):
+    for mode, key in ((F.FLB_MODE_PLAIN, "plain"), (F.FLB_MODE_BATCHED, "batched"),
+                      (F.FLB_MODE_PERSISTENT, "persistent")):
         s = F.Solver(ps, device=f"cuda:{local}")
         s.set_mode(mode)
         if autotune:
@@ -197,6 +199,7 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
         del s
         torch.cuda.empty_cache()
     out["ratio"] = out["batched_mlups"] / out["plain_mlups"]
+    out["persistent_vs_plain"] = out["persistent_mlups"] / out["plain_mlups"]
     return out
 
 

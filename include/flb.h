@@ -64,6 +64,7 @@ extern "C" {
 #define FLB_FORCE_FV 2          /* FV lattice gradient of Eq. (fvgrad) */
 #define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
 #define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
+#define FLB_MODE_PERSISTENT 2  /* all replicas, n steps, one cooperative launch (FV, FP32 storage) */
 #define FLB_TUNE_FORCE 1       /* flb_autotune: time every candidate even if the cache has an entry */
 
 /*
@@ -187,8 +188,28 @@ int64_t flb_structure_factor_size(flb_handle *h, int32_t rep, int32_t which);
 /* Zero the accumulated spectra of replica rep (-1: all). */
 int flb_sq_reset(flb_handle *h, int32_t rep);
 
-/* Launch mode for flb_step: FLB_MODE_PLAIN or FLB_MODE_BATCHED. */
+/*
+ * Launch mode for flb_step:
+ *   FLB_MODE_PLAIN       every replica's kernels launched one replica after another;
+ *   FLB_MODE_BATCHED     all replicas in one launch per phase (mu, collide-stream,
+ *                        velocity, psi stages), replayed as a CUDA graph (3D, FV);
+ *   FLB_MODE_PERSISTENT  all replicas advanced the n steps of one flb_step call
+ *                        by one cooperative launch per stretch between sampling
+ *                        steps (3D, FV, FP32 storage).  Its blocks take tile tasks
+ *                        from a list in order and wait, per replica, for the
+ *                        previous phase of that replica only (a per-replica phase
+ *                        barrier), each wait bounded by flb_set_wait_limit.
+ * All three give bitwise identical results.  flb_step returns EUNSUPPORTED when
+ * the replicas do not fit the chosen mode.
+ */
 int flb_set_mode(flb_handle *h, int32_t mode);
+
+/* Limit of one inter-block wait of FLB_MODE_PERSISTENT, in seconds (default 1,
+ * at most 60).  A wait that runs out latches FLB_ETIMEOUT in the handle's status
+ * word and ends the launch (every block stops taking tasks), leaving the step in
+ * progress incomplete; the next synchronising call returns FLB_ETIMEOUT.  The
+ * state must then be set again (flb_set_fields / flb_set_state) before stepping. */
+int flb_set_wait_limit(flb_handle *h, double seconds);
 
 /*
  * Tiling of the 3D psi stage.  A psi block owns a 32 x 16 column of sites and
@@ -206,7 +227,8 @@ int flb_set_mode(flb_handle *h, int32_t mode);
  * covers the box depth) on the handle's own buffers and keeps the fastest: in
  * FLB_MODE_PLAIN per distinct replica configuration (box, lattice, scheme,
  * integrator, noise, advection) on that replica's psi stages; in
- * FLB_MODE_BATCHED one value for all replicas on the batched psi launches.  The
+ * FLB_MODE_BATCHED and FLB_MODE_PERSISTENT one value for all replicas on the
+ * batched psi launches.  The
  * timed launches write only step scratch and the spare psi buffer, so the state
  * (populations, psi, step counters, spectra) is unchanged.  cache_path (may be
  * NULL) names a text file of "key<TAB>planes" lines, keyed by the device name,

@@ -28,7 +28,7 @@ FLB_F32_DEV, FLB_F16_DEV = 0, 1
 FLB_COUPLE_FORCE, FLB_COUPLE_ADVECT = 1, 2
 FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV = 0, 1, 2
 FLB_SQ_PSI, FLB_SQ_HEIGHT = 0, 1
-FLB_MODE_PLAIN, FLB_MODE_BATCHED = 0, 1
+FLB_MODE_PLAIN, FLB_MODE_BATCHED, FLB_MODE_PERSISTENT = 0, 1, 2
 FLB_TUNE_FORCE = 1
 
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "flb_get_tuning": (c_int, [H, ctypes.c_int32, P(ctypes.c_int32)]),
         "flb_set_tuning": (c_int, [H, ctypes.c_int32, ctypes.c_int32]),
         "flb_autotune": (c_int, [H, ctypes.c_char_p, ctypes.c_int32]),
+        "flb_set_wait_limit": (c_int, [H, ctypes.c_double]),
         "flb_state_bytes": (c_sz, [H, ctypes.c_int32]),
         "flb_get_state": (c_int, [H, ctypes.c_int32, vp, c_sz]),
         "flb_set_state": (c_int, [H, ctypes.c_int32, vp, c_sz]),
@@ -257,6 +258,9 @@ class Solver:
 
     def set_mode(self, mode):
         _check(self.lib.flb_set_mode(self.h, mode), "flb_set_mode")
+
+    def set_wait_limit(self, seconds: float):
+        _check(self.lib.flb_set_wait_limit(self.h, float(seconds)), "flb_set_wait_limit")
 
     def get_tuning(self, rep=0) -> int:
         """Planes per psi block (the z chunk) of replica rep."""

@@ -185,6 +185,15 @@ struct flb_handle {
     cudaGraph_t b_graph = nullptr;
     cudaGraphExec_t b_exec = nullptr;
     bool b_lists_ok = false;
+    // persistent mode: one step's task list, dispatch and completion counters
+    PTask *p_tasks = nullptr;
+    size_t p_cap = 0;
+    int p_ntask = 0;
+    unsigned *p_ticket = nullptr, *p_done = nullptr;
+    int *p_abort = nullptr;
+    std::vector<int> p_pstep;
+    bool p_ok = false;
+    unsigned long long wait_ns = 1000000000ull;  // 1 s per inter-block wait
     float2 *X1 = nullptr, *X2 = nullptr;
     float *heights = nullptr, *win = nullptr;
     char *ws = nullptr;
@@ -240,6 +249,19 @@ size_t carve_all(flb_handle &h, char *base)
     h.b_lb = cv.take<BatchBlock>((size_t)std::max(nlb, 1));
     h.b_psi = cv.take<BatchBlock>((size_t)std::max(npsi, 1));
     h.b_dstep = cv.take<long long>(1);
+    // persistent-mode task list, sized for the smallest psi depth
+    size_t ptask = 0;
+    for (Rep &r : h.reps) {
+        if (r.dim != 3) continue;
+        int c[PH_COUNT];
+        persist_tiles(r.g, PS_ZC_MIN, FLB_COUPLE_FORCE, 1, c);
+        for (int k = 0; k < PH_COUNT; ++k) ptask += (size_t)c[k];
+    }
+    h.p_cap = ptask;
+    h.p_tasks = cv.take<PTask>(std::max<size_t>(ptask, 1));
+    h.p_ticket = cv.take<unsigned>(1);
+    h.p_abort = cv.take<int>(1);
+    h.p_done = cv.take<unsigned>(h.reps.size());
     h.red_partial = cv.take<double>((size_t)RED_MAX_BLOCKS * NRED);
     h.red_out = cv.take<double>(NRED);
     h.status = cv.take<int>(1);
@@ -641,6 +663,7 @@ int batch_upload_table(flb_handle *h)
         d.advect = (r.p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
         d.noise = r.p.kT > 0 && r.p.M > 0;
         d.zc = r.zc;
+        d.pstep_tasks = k < h->p_pstep.size() ? h->p_pstep[k] : 0;
         const uint64_t pd[3] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz};
         const uint64_t ps[2] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4};
         const uint32_t pb[3] = {(uint32_t)(PS_TX + 8), (uint32_t)(PS_TY + 6), 1};
@@ -740,6 +763,86 @@ int step_batched(flb_handle *h, int64_t n)
             r.pcur ^= 1;
             r.step += 1;
         }
+        if (h->sample_every > 0 && h->sample_mask && h->reps[0].step % h->sample_every == 0)
+            for (Rep &r : h->reps) {
+                const int rs = sample_rep(h, r, h->sample_mask);
+                if (rs != FLB_OK) return rs;
+            }
+    }
+    return FLB_OK;
+}
+
+bool persist_supported(const flb_handle *h)
+{
+    if (!batch_supported(h)) return false;
+    for (const Rep &r : h->reps)
+        if (r.p.storage != FLB_F32_DEV) return false;
+    return true;
+}
+
+// One step's task list: phase by phase, replica by replica, tile by tile; the
+// need of a task counts the tasks of its replica listed before it.
+int persist_build(flb_handle *h)
+{
+    std::vector<PTask> v;
+    const size_t nr = h->reps.size();
+    std::vector<int> need(nr, 0);
+    for (int ph = 0; ph < PH_COUNT; ++ph)
+        for (size_t k = 0; k < nr; ++k) {
+            const Rep &r = h->reps[k];
+            int c[PH_COUNT];
+            persist_tiles(r.g, r.zc, r.p.coupling, r.p.integrator == FLB_HEUN ? 1 : 0, c);
+            if (c[ph] == 0) continue;
+            persist_tasks(v, (int)k, ph, r.g, r.zc, need[k]);
+            need[k] += c[ph];
+        }
+    if (v.size() > h->p_cap) return FLB_EINVAL;
+    h->p_pstep = need;
+    h->p_ntask = (int)v.size();
+    int rc = cuerr(cudaMemcpyAsync(h->p_tasks, v.data(), v.size() * sizeof(PTask), cudaMemcpyHostToDevice, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    h->p_ok = rc == FLB_OK;
+    return rc;
+}
+
+// n steps of every replica, one cooperative launch per stretch between sampling steps.
+int step_persistent(flb_handle *h, int64_t n)
+{
+    if (!persist_supported(h)) return FLB_EUNSUPPORTED;
+    int rc = h->p_ok ? FLB_OK : persist_build(h);
+    if (rc == FLB_OK) rc = batch_upload_table(h);  // descriptors of the current buffers; device step 0
+    if (rc != FLB_OK) return rc;
+    int64_t done = 0;
+    while (done < n) {
+        int64_t k = n - done;
+        const int64_t st0 = h->reps[0].step;
+        if (h->sample_every > 0 && h->sample_mask) k = std::min<int64_t>(k, h->sample_every - st0 % h->sample_every);
+        k = std::min<int64_t>(k, 1 << 20);
+        rc = cuerr(cudaMemsetAsync(h->p_ticket, 0, sizeof(unsigned), h->st));
+        if (rc == FLB_OK) rc = cuerr(cudaMemsetAsync(h->p_abort, 0, sizeof(int), h->st));
+        if (rc == FLB_OK) rc = cuerr(cudaMemsetAsync(h->p_done, 0, h->reps.size() * sizeof(unsigned), h->st));
+        if (rc != FLB_OK) return rc;
+        PersistArgs a;
+        a.L = batch_lists(h);
+        a.tasks = h->p_tasks;
+        a.ntask = h->p_ntask;
+        a.nsteps = (int)k;
+        a.ds0 = done;
+        a.ticket = h->p_ticket;
+        a.done = h->p_done;
+        a.abort = h->p_abort;
+        a.status = h->status;
+        a.wait_ns = h->wait_ns;
+        cudaEvent_t e0 = mark(h);
+        ++h->launches;
+        if (launch_persist(a, h->st) != cudaSuccess) return FLB_ECUDA;
+        span(h, 0, e0, mark(h), 1);
+        for (Rep &r : h->reps) {
+            r.cur ^= (int)(k & 1);
+            r.pcur ^= (int)(k & 1);
+            r.step += k;
+        }
+        done += k;
         if (h->sample_every > 0 && h->sample_mask && h->reps[0].step % h->sample_every == 0)
             for (Rep &r : h->reps) {
                 const int rs = sample_rep(h, r, h->sample_mask);
@@ -944,6 +1047,7 @@ int flb_step(flb_handle *h, int64_t n)
 {
     if (!h || n < 0) return FLB_EINVAL;
     if (h->mode == FLB_MODE_BATCHED) return n > 0 ? step_batched(h, n) : FLB_OK;
+    if (h->mode == FLB_MODE_PERSISTENT) return n > 0 ? step_persistent(h, n) : FLB_OK;
     for (int64_t k = 0; k < n; ++k) {
         for (Rep &r : h->reps) {
             const int rc = step_rep(h, r);
@@ -1060,6 +1164,7 @@ void batch_reset(flb_handle *h)
     h->b_exec = nullptr;
     h->b_graph = nullptr;
     h->b_lists_ok = false;
+    h->p_ok = false;
 }
 
 std::string device_key()
@@ -1174,7 +1279,7 @@ int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
     const std::map<std::string, int> cache = force ? std::map<std::string, int>() : read_cache(cache_path);
     const std::string dk = device_key();
     const int reps = 3;
-    if (h->mode == FLB_MODE_BATCHED && batch_supported(h)) {
+    if ((h->mode == FLB_MODE_BATCHED || h->mode == FLB_MODE_PERSISTENT) && batch_supported(h)) {
         // one value for every replica, timed on the batched psi launches
         std::string all;
         bool noise = false;
@@ -1250,9 +1355,16 @@ int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
     return take_status(h);
 }
 
+int flb_set_wait_limit(flb_handle *h, double seconds)
+{
+    if (!h || !(seconds >= 0.0) || seconds > 60.0) return FLB_EINVAL;
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    return FLB_OK;
+}
+
 int flb_set_mode(flb_handle *h, int32_t mode)
 {
-    if (!h || (mode != FLB_MODE_PLAIN && mode != FLB_MODE_BATCHED)) return FLB_EINVAL;
+    if (!h || (mode != FLB_MODE_PLAIN && mode != FLB_MODE_BATCHED && mode != FLB_MODE_PERSISTENT)) return FLB_EINVAL;
     h->mode = mode;
     return FLB_OK;
 }

@@ -23,24 +23,7 @@ __device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int 
     const int y = by * LB_BY + threadIdx.y;
     const int z = bz * LB_BZ + threadIdx.z;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-    float f[19];
-    pull19((const T *)a.fout, g, x, y, z, f);
-    float sp[10], dp[10];
-#pragma unroll
-    for (int p = 1; p <= 9; ++p) {
-        sp[p] = f[2 * p - 1] + f[2 * p];
-        dp[p] = f[2 * p - 1] - f[2 * p];
-    }
-    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
-    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
-    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
-    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3(a, x, y, z, Fx, Fy, Fz);
-    const float irho = __fdividef(1.0f, a.rho0 + drho);
-    store_padded(a.u, g, x, y, z, (jx + 0.5f * Fx) * irho, 1);
-    store_padded(a.u + g.pn, g, x, y, z, (jy + 0.5f * Fy) * irho, 1);
-    store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
+    vel3_site<T, FORCE, false>(a, x, y, z);
 }
 
 template <typename T, bool FORCE>
@@ -65,21 +48,7 @@ __device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict
     const int zb = bz * MU_ZC - 1;                          // first output plane
     const int ze = min(zb + MU_ZC, g.nz + 1);               // one past the last
     if (x > g.nx || y > g.ny || zb >= ze) return;
-    const int Y = g.px, Z = g.px * g.py;
-    const float k22 = K * (1.0f / 22.0f);
-    int c = g.pidx32(x, y, zb - 1);
-    float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f;  // planes p-2, p-1
-    for (int p = zb - 1; p <= ze; ++p, c += Z) {
-        const float a2 = __ldg(psi + c);
-        const float b2 = (__ldg(psi + c - 1) + __ldg(psi + c + 1)) + (__ldg(psi + c - Y) + __ldg(psi + c + Y));
-        const float d2 = (__ldg(psi + c - 1 - Y) + __ldg(psi + c + 1 - Y)) + (__ldg(psi + c - 1 + Y) + __ldg(psi + c + 1 + Y));
-        if (p - 1 >= zb) {
-            const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
-            mu[c - Z] = A * a1 + B * a1 * a1 * a1 - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * a1);
-        }
-        a0 = a1; b0 = b1; d0 = d1;
-        a1 = a2; b1 = b2; d1 = d2;
-    }
+    mu3_column<false>(g, psi, mu, A, B, K, x, y, zb, ze);
 }
 
 __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,

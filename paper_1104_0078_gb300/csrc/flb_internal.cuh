@@ -3,6 +3,8 @@
 // psi/mu/u fields, and the argument blocks the host passes to each kernel.
 #pragma once
 
+#include <vector>
+
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -225,6 +227,7 @@ struct alignas(128) BatchRep {
     float A, B, K, M;
     int heun, advect, noise;
     int zc;                  // planes per psi block
+    int pstep_tasks;         // persistent mode: tasks of this replica per step
 };
 
 struct BatchBlock {
@@ -245,6 +248,33 @@ cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool
                               bool noise, cudaStream_t st);
 // the psi stage launches of a batched step alone (no state change: the autotuner times them)
 cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, cudaStream_t st);
+
+// ---- persistent batched mode (flb_persist.cu) --------------------------------
+enum { PH_MU = 0, PH_LB = 1, PH_VEL = 2, PH_S1 = 3, PH_S2 = 4, PH_COUNT = 5 };
+
+struct PTask {
+    int rep;       // replica
+    int need;      // tasks of this replica listed before this one within a step
+    short bx, by, bz;
+    char phase, pad;
+};
+
+struct PersistArgs {
+    BatchLists L;            // replica descriptors (pstep_tasks filled in)
+    const PTask *tasks;      // one step's task list
+    int ntask, nsteps;       // tasks per step, steps of this launch
+    long long ds0;           // device step of the first step
+    unsigned *ticket;        // dispatch counter, zero at launch
+    unsigned *done;          // completed tasks per replica, zero at launch
+    int *abort;              // raised by a block whose wait ran out, zero at launch
+    int *status;             // handle status word (FLB_ETIMEOUT on a timeout)
+    unsigned long long wait_ns;
+};
+
+size_t persist_smem_bytes();
+void persist_tiles(const Geom &g, int zc, int coupling, int heun, int counts[PH_COUNT]);
+void persist_tasks(std::vector<PTask> &v, int rep, int ph, const Geom &g, int zc, int need);
+cudaError_t launch_persist(const PersistArgs &a, cudaStream_t st);
 
 // host launchers (flb_lb.cu, flb_psi.cu, flb_obs.cu)
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);

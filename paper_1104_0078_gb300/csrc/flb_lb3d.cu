@@ -16,154 +16,6 @@
 
 namespace flb {
 
-// One D3Q19 site: pull, moments, relaxation with force and noise, store.
-template <typename T, bool GHOST_RELAX>
-__device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
-{
-    const Geom &g = a.g;
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int N = (int)g.n;
-    const int row = nx, pl = nx * ny;
-    const int s = x + row * y + pl * z;
-    T *fout = (T *)a.fout;
-
-    float f[19];
-    pull19((const T *)a.fin, g, x, y, z, f);
-
-    float sp[10], dp[10];
-#pragma unroll
-    for (int p = 1; p <= 9; ++p) {
-        sp[p] = f[2 * p - 1] + f[2 * p];
-        dp[p] = f[2 * p - 1] - f[2 * p];
-    }
-    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
-    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
-    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
-    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
-    const float third = drho * (1.0f / 3.0f);
-    const float Sxx = sp[1] + (sp[4] + sp[5]) + (sp[6] + sp[7]) - third;
-    const float Syy = sp[2] + (sp[4] + sp[5]) + (sp[8] + sp[9]) - third;
-    const float Szz = sp[3] + (sp[6] + sp[7]) + (sp[8] + sp[9]) - third;
-    const float Sxy = sp[4] - sp[5], Sxz = sp[6] - sp[7], Syz = sp[8] - sp[9];
-
-    const float rho = a.rho0 + drho;
-    const float irho = __fdividef(1.0f, rho);  // ~2 ulp
-    const float vx = (jx + 0.5f * Fx) * irho, vy = (jy + 0.5f * Fy) * irho, vz = (jz + 0.5f * Fz) * irho;
-
-    const float ws = a.omega_s, wb = a.omega_b;
-    const float cs = 1.0f - 0.5f * ws, cb = 1.0f - 0.5f * wb;
-    const float Xxx = rho * vx * vx - Sxx, Xyy = rho * vy * vy - Syy, Xzz = rho * vz * vz - Szz;
-    const float trX3 = (Xxx + Xyy + Xzz) * (1.0f / 3.0f);
-    const float Txx = 2.f * vx * Fx, Tyy = 2.f * vy * Fy, Tzz = 2.f * vz * Fz;
-    const float trT3 = (Txx + Tyy + Tzz) * (1.0f / 3.0f);
-    const float isoB = (wb - ws) * trX3 + (cb - cs) * trT3;
-    float Bxx = Sxx + ws * Xxx + cs * Txx + isoB;
-    float Byy = Syy + ws * Xyy + cs * Tyy + isoB;
-    float Bzz = Szz + ws * Xzz + cs * Tzz + isoB;
-    float Bxy = Sxy + ws * (rho * vx * vy - Sxy) + cs * (vx * Fy + Fx * vy);
-    float Bxz = Sxz + ws * (rho * vx * vz - Sxz) + cs * (vx * Fz + Fx * vz);
-    float Byz = Syz + ws * (rho * vy * vz - Syz) + cs * (vy * Fz + Fy * vz);
-    const float Ax = jx + Fx, Ay = jy + Fy, Az = jz + Fz;
-
-    float g10 = 0.f, g11 = 0.f, g12 = 0.f, g13 = 0.f, g14 = 0.f, g15 = 0.f, g16 = 0.f, g17 = 0.f, g18 = 0.f;
-    if (GHOST_RELAX) {
-        const float gg = a.gamma_g;
-        const float m10 = (dp[4] + dp[5] + dp[6] + dp[7]) * (1.f / 3.f) - dp[1] * (2.f / 3.f);
-        const float m11 = (dp[4] - dp[5] + dp[8] + dp[9]) * (1.f / 3.f) - dp[2] * (2.f / 3.f);
-        const float m12 = (dp[6] - dp[7] + dp[8] - dp[9]) * (1.f / 3.f) - dp[3] * (2.f / 3.f);
-        const float m13 = dp[4] + dp[5] - dp[6] - dp[7];
-        const float m14 = -dp[4] + dp[5] + dp[8] + dp[9];
-        const float m15 = dp[6] - dp[7] - dp[8] + dp[9];
-        const float m16 = (f[0] + sp[4] + sp[5] + sp[6] + sp[7] + sp[8] + sp[9]) * (1.f / 3.f) -
-                          (sp[1] + sp[2] + sp[3]) * (2.f / 3.f);
-        const float m17 = -sp[1] + 0.5f * (sp[2] + sp[3] + sp[4] + sp[5] + sp[6] + sp[7]) - (sp[8] + sp[9]);
-        const float m18 = 0.5f * (-sp[2] + sp[3] + sp[4] + sp[5] - sp[6] - sp[7]);
-        g10 = gg * m10 * 13.5f;
-        g11 = gg * m11 * 13.5f;
-        g12 = gg * m12 * 13.5f;
-        g13 = gg * m13 * 4.5f;
-        g14 = gg * m14 * 4.5f;
-        g15 = gg * m15 * 4.5f;
-        g16 = gg * m16 * 4.5f;
-        g17 = gg * m17 * 3.0f;
-        g18 = gg * m18 * 9.0f;
-    }
-    if (a.kT > 0.f) {
-        float G[16];
-        const uint32_t sid = (uint32_t)s;
-        normals4(a.key, a.step, sid, 0u, 0u, G);
-        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
-        normals4(a.key, a.step, sid, 0u, 2u, G + 8);
-        normals4(a.key, a.step, sid, 0u, 3u, G + 12);
-        const float mun = 3.0f * rho * a.kT;
-        const float sq = mun * rsqrtf(mun);  // sqrt(rho kT / c_s^2), ~2 ulp
-        float n[15];
-#pragma unroll
-        for (int t = 0; t < 15; ++t) n[t] = sq * a.namp[t] * G[t];
-        const float two9 = 2.0f / 9.0f, one9 = 1.0f / 9.0f;
-        Bxx += two9 * (n[0] + 2.f * n[1]);
-        Byy += two9 * (n[0] - n[1] + n[2]);
-        Bzz += two9 * (n[0] - n[1] - n[2]);
-        Bxy += one9 * n[3];
-        Byz += one9 * n[4];
-        Bxz += one9 * n[5];
-        g10 += n[6];
-        g11 += n[7];
-        g12 += n[8];
-        g13 += n[9];
-        g14 += n[10];
-        g15 += n[11];
-        g16 += n[12];
-        g17 += n[13];
-        g18 += n[14];
-    }
-
-    const float tb = (Bxx + Byy + Bzz) * (1.0f / 3.0f);
-    const float e0 = 4.5f * tb;
-    const float h1 = 1.f / 3.f, h2 = 2.f / 3.f;
-    const float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
-    T *fo = fout;
-    st3(fo, s, (1.f / 3.f) * (drho - e0 + h1 * g16));
-    float E, O;
-    E = drho + 4.5f * Bxx - e0 - h2 * g16 - g17;
-    O = 3.f * Ax - h2 * g10;
-    st3(fo + 1ll * N, s, w1 * (E + O));
-    st3(fo + 2ll * N, s, w1 * (E - O));
-    E = drho + 4.5f * Byy - e0 - h2 * g16 + 0.5f * g17 - 0.5f * g18;
-    O = 3.f * Ay - h2 * g11;
-    st3(fo + 3ll * N, s, w1 * (E + O));
-    st3(fo + 4ll * N, s, w1 * (E - O));
-    E = drho + 4.5f * Bzz - e0 - h2 * g16 + 0.5f * g17 + 0.5f * g18;
-    O = 3.f * Az - h2 * g12;
-    st3(fo + 5ll * N, s, w1 * (E + O));
-    st3(fo + 6ll * N, s, w1 * (E - O));
-    const float Gev = h1 * g16 + 0.5f * g17;
-    E = drho + 4.5f * (Bxx + Byy + 2.f * Bxy) - e0 + Gev + 0.5f * g18;
-    O = 3.f * (Ax + Ay) + h1 * (g10 + g11) + g13 - g14;
-    st3(fo + 7ll * N, s, w2 * (E + O));
-    st3(fo + 8ll * N, s, w2 * (E - O));
-    E = drho + 4.5f * (Bxx + Byy - 2.f * Bxy) - e0 + Gev + 0.5f * g18;
-    O = 3.f * (Ax - Ay) + h1 * (g10 - g11) + g13 + g14;
-    st3(fo + 9ll * N, s, w2 * (E + O));
-    st3(fo + 10ll * N, s, w2 * (E - O));
-    E = drho + 4.5f * (Bxx + Bzz + 2.f * Bxz) - e0 + Gev - 0.5f * g18;
-    O = 3.f * (Ax + Az) + h1 * (g10 + g12) - g13 + g15;
-    st3(fo + 11ll * N, s, w2 * (E + O));
-    st3(fo + 12ll * N, s, w2 * (E - O));
-    E = drho + 4.5f * (Bxx + Bzz - 2.f * Bxz) - e0 + Gev - 0.5f * g18;
-    O = 3.f * (Ax - Az) + h1 * (g10 - g12) - g13 - g15;
-    st3(fo + 13ll * N, s, w2 * (E + O));
-    st3(fo + 14ll * N, s, w2 * (E - O));
-    E = drho + 4.5f * (Byy + Bzz + 2.f * Byz) - e0 + h1 * g16 - g17;
-    O = 3.f * (Ay + Az) + h1 * (g11 + g12) + g14 - g15;
-    st3(fo + 15ll * N, s, w2 * (E + O));
-    st3(fo + 16ll * N, s, w2 * (E - O));
-    E = drho + 4.5f * (Byy + Bzz - 2.f * Byz) - e0 + h1 * g16 - g17;
-    O = 3.f * (Ay - Az) + h1 * (g11 - g12) + g14 + g15;
-    st3(fo + 17ll * N, s, w2 * (E + O));
-    st3(fo + 18ll * N, s, w2 * (E - O));
-}
-
 // One thread per site on a 3D grid of 32 x 4 x 2 blocks (a warp covers 32
 // consecutive x, so every population plane is read and written in full rows).
 
@@ -177,7 +29,7 @@ __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int b
     const int z = bz * LB_BZ + threadIdx.z;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3(a, x, y, z, Fx, Fy, Fz);
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3<false>(a, x, y, z, Fx, Fy, Fz);
     lb_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
 }
 

@@ -23,16 +23,9 @@
 // writes psi^{n+1} = E + D(psi*)/2 (the noise is held fixed over the step).
 #include <cudaTypedefs.h>
 
-#include "flb_internal.cuh"
-#include "flb_tma.cuh"
+#include "flb_psi3d.cuh"
 
 namespace flb {
-
-constexpr int PS_NT = PS_TX * PS_TY;
-constexpr int H3X = PS_TX + 6, H3Y = PS_TY + 6, H3N = H3X * H3Y;  // psi: tile + 3
-constexpr int H2X = PS_TX + 4, H2Y = PS_TY + 4, H2N = H2X * H2Y;  // mu: tile + 2
-constexpr int H1X = PS_TX + 2, H1Y = PS_TY + 2, H1N = H1X * H1Y;  // flux / noise: tile + 1
-constexpr int S3 = (H3N + PS_NT - 1) / PS_NT, S2 = (H2N + PS_NT - 1) / PS_NT, S1 = (H1N + PS_NT - 1) / PS_NT;
 
 __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 __device__ __forceinline__ int ring4(int p) { return p & 3; }  // two's complement: correct for negative p
@@ -52,19 +45,6 @@ __device__ __forceinline__ float mu_point(const float *pm, const float *p0, cons
     const float ps = p0[c];
     return A * ps + B * ps * ps * ps - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * ps);
 }
-
-struct Psi3Args {
-    Geom g;
-    const float *psi;  // padded stage input
-    const float *u;    // padded velocity (images to radius 1)
-    float *out;        // padded stage output (images to radius 3)
-    float *E;          // [N] Heun accumulator: written by stage 1, read by stage 2
-    float A, B, K, M, kT;
-    int advect, heun;
-    int zc;            // planes per block (the z chunk)
-    PhiloxKey key;
-    int64_t step;
-};
 
 // Per-thread view of the block's halo regions, computed once: for every slot the
 // in-plane offset of the padded field it loads (psi, u) and the in-plane counter
@@ -99,37 +79,6 @@ __device__ __forceinline__ void make_regions(Regions &R, const Geom &g, int x0, 
         R.u1[j] = (gx + GX) + g.px * (gy + GY);
         R.n1[j] = wrapi(gx, g.nx) + g.nx * wrapi(gy, g.ny);
     }
-}
-
-// Point k of a W x H region (W >= 32): rows' first 32 columns first, then the
-// W - 32 remaining columns of every row.
-__device__ __forceinline__ void region_point(int k, int W, int H, int &lx, int &ly)
-{
-    if (k < 32 * H) {
-        lx = k & 31;
-        ly = k >> 5;
-    } else {
-        const int r = k - 32 * H, e = W - 32;
-        lx = 32 + r % e;
-        ly = r / e;
-    }
-}
-
-// divergence (1/c_s^2) sum_i w_i c_i . V(r + c_i) of a vector field held in three
-// planes (z-1, z, z+1) of the tile + 1 frame: (1/6) axis + (1/12) diagonal links
-__device__ __forceinline__ float fv_div(const float *xm, const float *x0, const float *xp, const float *ym,
-                                        const float *y0, const float *yp, const float *zm, const float *z0,
-                                        const float *zp, int c)
-{
-    (void)z0;
-    const float ax = (x0[c + 1] - x0[c - 1]) + (y0[c + H1X] - y0[c - H1X]) + (zp[c] - zm[c]);
-    float dg = (x0[c + 1 + H1X] + y0[c + 1 + H1X]) - (x0[c - 1 - H1X] + y0[c - 1 - H1X]);
-    dg += (x0[c + 1 - H1X] - y0[c + 1 - H1X]) - (x0[c - 1 + H1X] - y0[c - 1 + H1X]);
-    dg += (xp[c + 1] + zp[c + 1]) - (xm[c - 1] + zm[c - 1]);
-    dg += (xm[c + 1] - zm[c + 1]) - (xp[c - 1] - zp[c - 1]);
-    dg += (yp[c + H1X] + zp[c + H1X]) - (ym[c - H1X] + zm[c - H1X]);
-    dg += (ym[c + H1X] - zm[c + H1X]) - (yp[c - H1X] - zp[c - H1X]);
-    return (1.f / 6.f) * ax + (1.f / 12.f) * dg;
 }
 
 // ---------------------------------------------------------------------------
@@ -254,288 +203,10 @@ __global__ void __launch_bounds__(PS_NT) psi3_fd_kernel(const Psi3Args a)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Finite volume with TMA staging.  psi planes (tile + 4 in x, + 3 in y) and the
-// three velocity components of a plane (tile + 4 in x, + 1 in y) are copied by
-// cp.async.bulk.tensor two planes ahead of their use into rings of shared-memory
-// slots, each completed on its own mbarrier; the compute phases are those of
-// psi3_fv_kernel.
-//   psi slot:  [TY+6][TX+8] floats, column c <-> x = x0 - 4 + c, row r <-> y = y0 - 3 + r
-//   u slot:    [3][TY+2][TX+8],     column c <-> x = x0 - 4 + c, row r <-> y = y0 - 1 + r
-// ---------------------------------------------------------------------------
-constexpr int TB_X = PS_TX + 8;                            // TMA box width (x0-4 .. x0+TX+3)
-constexpr int TP_N = TB_X * H3Y;                           // psi slot floats
-constexpr int TP_SLOT = ((TP_N * 4 + 127) / 128) * 32;     // floats, 128-byte multiple
-constexpr int TU_N = 3 * TB_X * H1Y;                       // u slot floats
-constexpr int TU_SLOT = ((TU_N * 4 + 127) / 128) * 32;
-constexpr int T_PSI_DEPTH = 6, T_U_DEPTH = 3;
-
 struct TmaArgs {
     Psi3Args a;
     int *status;
 };
-
-constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * H2N + 6 * H1N;
-constexpr int FV_NOISE_FLOATS = 6 * H1N;
-
-// One block (tile bx, by; z chunk bz).  psi_map / u_map: tensor maps of the stage
-// input psi and of the velocity (kernel parameters or global memory); tsmem: the
-// block's dynamic shared memory.
-//
-// Every stencil is split by plane.  A thread owns the same points of the mu,
-// flux and tile regions in every plane and keeps, in registers, what each new
-// plane contributes to the planes above and below it:
-//   lap_SO psi (z) = (6 n1 + 3 n2 + n3 - 80 psi) / 22 with, per plane P, the
-//     centre a, the 4 in-plane faces b and the 4 in-plane diagonals d:
-//     n1 = b(z) + a(z-1) + a(z+1),  n2 = d(z) + b(z-1) + b(z+1),  n3 = d(z-1) + d(z+1);
-//   12 grad mu (q) (Eq. fvgrad, w = 1/18, 1/36) with ex, ey the in-plane face
-//     differences, Dx, Dy the signed diagonal sums and Zp = 2 mu + 4 faces:
-//     x: 2 ex(q) + Dx(q) + ex(q-1) + ex(q+1),  y: likewise,  z: Zp(q+1) - Zp(q-1);
-//   12 div J (z) (the (2/c_s^2) link-average divergence, sum_i w_i c_i = 0 removes
-//     J(r)) with Hxy the in-plane face differences of Jx, Jy, Dg the in-plane
-//     diagonal terms, Zc = Jz(centre), Z4 = Jz at the 4 in-plane faces:
-//     2 Hxy(z) + Dg(z) + 2 (Zc(z+1) - Zc(z-1)) + Hxy(z+1) + Hxy(z-1) + Z4(z+1) - Z4(z-1).
-// Shared memory then holds only the current mu, flux and noise planes (two of
-// each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
-// formed, the flux of plane p-2, and the output of plane p-3 completes.
-template <int STAGE, bool NOISE>
-__device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
-                                                  const Psi3Args &a, int *status, int bx, int by, int bz,
-                                                  float *tsmem)
-{
-    if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
-    float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
-    float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
-    float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][H2N]     mu plane, by parity
-    float *sJ = smu + 2 * H2N;                           // [2][3][H1N]  flux plane, by parity
-    float *sX = sJ + 6 * H1N;                            // [2][3][H1N]  noise plane, by parity (NOISE)
-    __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH];
-    __shared__ int s_bad;
-    const Geom &g = a.g;
-    const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
-    const int x0 = bx * PS_TX, y0 = by * PS_TY, z0 = bz * a.zc;
-    const int z1 = min(z0 + a.zc, g.nz);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < g.nx && y < g.ny;
-    const float k22 = a.K * (1.0f / 22.0f);
-    const float sdx = sqrtf(2.0f * a.kT * a.M);
-    const float m12 = a.M * (1.0f / 12.0f);
-    const int pbase = z0 - 3, ubase = z0 - 1;             // first psi / u plane of the chunk
-    // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
-    // psi-slot centre, u-slot offset, noise counter id
-    // Region points are dealt to threads row segment by row segment: the first
-    // 32 columns of every row (a full warp reads 32 consecutive words, free of
-    // bank conflicts), then the few remaining columns of all rows.
-    int c2[S2], d2[S2], c1[S1], d1[S1], p1[S1], u1[S1], n1[S1];
-#pragma unroll
-    for (int j = 0; j < S2; ++j) {
-        int lx, ly;
-        region_point(threadIdx.x + j * PS_NT, H2X, H2Y, lx, ly);
-        const bool ok = threadIdx.x + j * PS_NT < H2N;
-        c2[j] = ok ? (lx + 2) + TB_X * (ly + 1) : -1;
-        d2[j] = lx + H2X * ly;
-    }
-#pragma unroll
-    for (int j = 0; j < S1; ++j) {
-        int lx, ly;
-        region_point(threadIdx.x + j * PS_NT, H1X, H1Y, lx, ly);
-        const bool ok = threadIdx.x + j * PS_NT < H1N;
-        c1[j] = ok ? (lx + 1) + H2X * (ly + 1) : -1;
-        d1[j] = lx + H1X * ly;
-        p1[j] = (lx + 3) + TB_X * (ly + 2);
-        u1[j] = (lx + 3) + TB_X * ly;
-        n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
-    }
-    // per-plane partial sums carried between planes (registers)
-    float pa[S2][2], pb[S2][2], pd[S2][2];  // psi: centre, faces, diagonals of planes p-2 [0], p-1 [1]
-    float G0[S1][3], G1[S1][3];            // 12 grad mu of planes m-1 and m, partly summed
-#pragma unroll
-    for (int j = 0; j < S2; ++j) pa[j][0] = pa[j][1] = pb[j][0] = pb[j][1] = pd[j][0] = pd[j][1] = 0.f;
-#pragma unroll
-    for (int j = 0; j < S1; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) G0[j][k] = G1[j][k] = 0.f;
-    float D0 = 0.f, D1 = 0.f, N0 = 0.f, N1 = 0.f;  // 12 div of the flux / noise of planes q-1 and q
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
-        for (int s = 0; s < T_U_DEPTH; ++s) mbar_init(&bar_u[s], 1);
-        s_bad = 0;
-        fence_barrier_init();
-    }
-    __syncthreads();
-    auto issue_psi = [&](int pp) {
-        const int s = (pp - pbase) % T_PSI_DEPTH;
-        mbar_expect_tx(&bar_p[s], TP_N * 4);
-        tma_load_3d(tps + s * TP_SLOT, psi_map, &bar_p[s], x0, y0, pp + g.gz);
-    };
-    auto issue_u = [&](int qq) {
-        const int s = (qq - ubase) % T_U_DEPTH;
-        mbar_expect_tx(&bar_u[s], TU_N * 4);
-        tma_load_4d(tus + s * TU_SLOT, u_map, &bar_u[s], x0, y0 + GY - 1, qq + g.gz, 0);
-    };
-    if (threadIdx.x == 0) {
-        issue_psi(pbase);
-        issue_psi(pbase + 1);
-    }
-    int last_p = pbase + 1, last_u = ubase - 1;  // highest plane issued (thread 0)
-    int waited_p = pbase - 1, waited_u = ubase - 1;
-
-    // Rotating ring positions, advanced once per plane (no divisions in the loop):
-    // psi plane p sits in slot r6 of phase ph6; the velocity of the next flux plane
-    // in slot ru of phase uph.
-    int r6 = 0, ph6 = 0, ru = 0, uph = 0;
-    for (int p = z0 - 3; p <= z1 + 2; ++p) {
-        const int s1 = r6 == 0 ? T_PSI_DEPTH - 1 : r6 - 1;  // psi slots of p-1, p-2, p-3
-        const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
-        const int s3 = s2 == 0 ? T_PSI_DEPTH - 1 : s2 - 1;
-        (void)s1;
-        // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
-        if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
-        waited_p = p;
-        {
-            const float *P = tps + r6 * TP_SLOT;
-            float *dst = smu + ((p - 1) & 1) * H2N;
-            const bool emit = p - 1 >= z0 - 2;
-#pragma unroll
-            for (int j = 0; j < S2; ++j) {
-                const int c = c2[j];
-                if (c < 0) continue;
-                const float ac = P[c];
-                const float bc = (P[c - 1] + P[c + 1]) + (P[c - TB_X] + P[c + TB_X]);
-                const float dc = (P[c - 1 - TB_X] + P[c + 1 - TB_X]) + (P[c - 1 + TB_X] + P[c + 1 + TB_X]);
-                if (emit) {
-                    const float ps = pa[j][1];
-                    const float nn1 = pb[j][1] + (pa[j][0] + ac);
-                    const float nn2 = pd[j][1] + (pb[j][0] + bc);
-                    const float nn3 = pd[j][0] + dc;
-                    dst[d2[j]] = a.A * ps + a.B * ps * ps * ps - k22 * (6.f * nn1 + 3.f * nn2 + nn3 - 80.f * ps);
-                }
-                pa[j][0] = pa[j][1];
-                pb[j][0] = pb[j][1];
-                pd[j][0] = pd[j][1];
-                pa[j][1] = ac;
-                pb[j][1] = bc;
-                pd[j][1] = dc;
-            }
-        }
-        __syncthreads();  // mu plane p-1 complete; every read of the psi slot of p-4 and of the u slot of p-3 done
-        if (s_bad) break;
-        if (threadIdx.x == 0) {  // refill those slots: psi plane p+2 (used at p+2), u plane p (used at p+2)
-            fence_proxy_async();
-            if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
-            if (a.advect && p >= ubase && p <= z1) { issue_u(p); last_u = p; }
-        }
-        // (B) mu partials of plane m = p-1 at the flux points; flux (and noise) of plane m-1
-        const int m = p - 1;
-        if (m >= z0 - 2) {
-            const bool emit = m - 1 >= z0 - 1;
-            const float *uq = tus;
-            if (emit && a.advect) {
-                if (!mbar_wait(&bar_u[ru], uph, status)) s_bad = 1;
-                waited_u = m - 1;
-                uq = tus + ru * TU_SLOT;
-                ru = ru == T_U_DEPTH - 1 ? 0 : ru + 1;
-                uph ^= ru == 0;
-            }
-            const float *Mu = smu + (m & 1) * H2N;
-            const float *ps = tps + s2 * TP_SLOT;  // psi plane m-1
-            float *J = sJ + ((m - 1) & 1) * 3 * H1N;
-            float *X = sX + ((m - 1) & 1) * 3 * H1N;
-            const int zid = g.nx * g.ny * wrapi(m - 1, g.nz);
-#pragma unroll
-            for (int j = 0; j < S1; ++j) {
-                const int c = c1[j];
-                if (c < 0) continue;
-                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + H2X], mym = Mu[c - H2X];
-                const float mpp = Mu[c + 1 + H2X], mpm = Mu[c + 1 - H2X], mmp = Mu[c - 1 + H2X],
-                            mmm = Mu[c - 1 - H2X];
-                const float ex = mxp - mxm, ey = myp - mym;
-                const float Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
-                const float Zp = 2.f * Mu[c] + ((mxp + mxm) + (myp + mym));
-                const float gx = G0[j][0] + ex, gy = G0[j][1] + ey, gz = G0[j][2] + Zp;  // plane m-1, complete
-                G0[j][0] = G1[j][0] + (2.f * ex + Dx);
-                G0[j][1] = G1[j][1] + (2.f * ey + Dy);
-                G0[j][2] = G1[j][2];
-                G1[j][0] = ex;
-                G1[j][1] = ey;
-                G1[j][2] = -Zp;
-                if (emit) {
-                    const int k = d1[j];
-                    float jx = m12 * gx, jy = m12 * gy, jz = m12 * gz;
-                    if (a.advect) {
-                        const float pv = ps[p1[j]];
-                        jx -= uq[u1[j]] * pv;
-                        jy -= uq[TB_X * H1Y + u1[j]] * pv;
-                        jz -= uq[2 * TB_X * H1Y + u1[j]] * pv;
-                    }
-                    J[k] = jx;
-                    J[H1N + k] = jy;
-                    J[2 * H1N + k] = jz;
-                    if (NOISE) {
-                        float Gn[4];
-                        normals4(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn);
-                        X[k] = sdx * Gn[0];
-                        X[H1N + k] = sdx * Gn[1];
-                        X[2 * H1N + k] = sdx * Gn[2];
-                    }
-                }
-            }
-        }
-        __syncthreads();  // flux plane p-2 complete
-        if (s_bad) break;
-        // (C) flux partials of plane q = p-2 at the tile point; the output of plane q-1 completes
-        const int q = p - 2;
-        if (q >= z0 - 1) {
-            const int c = (tx + 1) + H1X * (ty + 1);
-            const float *Jx = sJ + (q & 1) * 3 * H1N, *Jy = Jx + H1N, *Jz = Jy + H1N;
-            const float hxy = (Jx[c + 1] - Jx[c - 1]) + (Jy[c + H1X] - Jy[c - H1X]);
-            const float dg = ((Jx[c + 1 + H1X] + Jy[c + 1 + H1X]) - (Jx[c - 1 - H1X] + Jy[c - 1 - H1X])) +
-                             ((Jx[c + 1 - H1X] - Jy[c + 1 - H1X]) - (Jx[c - 1 + H1X] - Jy[c - 1 + H1X]));
-            const float zc = Jz[c];
-            const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + H1X] + Jz[c - H1X]);
-            const float dd = D0 + (2.f * zc + hxy + z4);  // plane q-1, complete
-            D0 = D1 + (2.f * hxy + dg);
-            D1 = hxy - z4 - 2.f * zc;
-            float dn = 0.f;
-            if (NOISE) {
-                const float *Xx = sX + (q & 1) * 3 * H1N, *Xy = Xx + H1N, *Xz = Xy + H1N;
-                const float nxy = (Xx[c + 1] - Xx[c - 1]) + (Xy[c + H1X] - Xy[c - H1X]);
-                const float ng = ((Xx[c + 1 + H1X] + Xy[c + 1 + H1X]) - (Xx[c - 1 - H1X] + Xy[c - 1 - H1X])) +
-                                 ((Xx[c + 1 - H1X] - Xy[c + 1 - H1X]) - (Xx[c - 1 + H1X] - Xy[c - 1 + H1X]));
-                const float nzc = Xz[c];
-                const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + H1X] + Xz[c - H1X]);
-                dn = N0 + (2.f * nzc + nxy + nz4);
-                N0 = N1 + (2.f * nxy + ng);
-                N1 = nxy - nz4 - 2.f * nzc;
-            }
-            const int z = q - 1;
-            if (z >= z0 && active) {
-                const float Dd = dd * (1.f / 12.f);
-                const int si = x + g.nx * (y + g.ny * z);
-                float out;
-                if (STAGE == 1) {
-                    const float Dn = NOISE ? dn * (1.f / 12.f) : 0.f;
-                    const float pv = tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
-                    out = pv + Dd + Dn;
-                    if (a.heun) a.E[si] = pv + 0.5f * Dd + Dn;
-                } else {
-                    out = a.E[si] + 0.5f * Dd;
-                }
-                store_padded(a.out, g, x, y, z, out, 3);
-            }
-        }
-        r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
-        ph6 ^= r6 == 0;
-    }
-    // a bounded wait drains copies still in flight before the block exits
-    if (threadIdx.x == 0) {
-        for (int pp = waited_p + 1; pp <= last_p; ++pp)
-            mbar_wait(&bar_p[(pp - pbase) % T_PSI_DEPTH], ((pp - pbase) / T_PSI_DEPTH) & 1, nullptr);
-        for (int qq = waited_u + 1; qq <= last_u; ++qq)
-            mbar_wait(&bar_u[(qq - ubase) % T_U_DEPTH], ((qq - ubase) / T_U_DEPTH) & 1, nullptr);
-    }
-}
 
 template <int STAGE, bool NOISE>
 __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
@@ -555,26 +226,9 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
     const BatchBlock b = L.psi[blockIdx.x];
     const BatchRep &r = L.reps[b.rep];
     const long long ds = *L.dstep;
-    const int par = (int)(ds & 1);
-    if (threadIdx.x == 0) {
-        sa.g = r.lb.g;
-        sa.psi = STAGE == 1 ? r.psi[par] : r.psis;
-        sa.u = r.lb.u;
-        sa.out = (STAGE == 1 && r.heun) ? r.psis : r.psi[par ^ 1];
-        sa.E = r.E;
-        sa.A = r.A;
-        sa.B = r.B;
-        sa.K = r.K;
-        sa.M = r.M;
-        sa.kT = r.noise ? r.lb.kT : 0.f;
-        sa.advect = r.advect;
-        sa.heun = r.heun;
-        sa.zc = r.zc;
-        sa.key = r.lb.key;
-        sa.step = r.lb.step + ds;
-    }
+    if (threadIdx.x == 0) psi_batch_args(r, ds, STAGE, sa);
     __syncthreads();
-    const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[par] : &r.map_psis;
+    const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[(int)(ds & 1)] : &r.map_psis;
     psi3_fv_tma_block<STAGE, NOISE>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
 }
 

@@ -1,7 +1,9 @@
-// flb_site3d.cuh -- per-site pieces shared by the D3Q19 collide-stream and the
-// velocity kernel: population loads and stores (FP32 or FP16 storage), the
-// 19-population pull, the force density of Sec. IV and the per-block arguments
-// of a batched launch.
+// flb_site3d.cuh -- the per-site work of the D3Q19 step kernels, shared by the
+// per-phase kernels (flb_lb3d.cu, flb_aux3d.cu) and the persistent batched
+// kernel (flb_persist.cu): population loads and stores (FP32 or FP16 storage),
+// the 19-population pull, the force density of Sec. IV, the collide-stream of
+// one site, the velocity of the new fluid state at one site, one column of the
+// mu field, and the per-block arguments of a batched launch.
 //
 // D3Q19.  Plane order: 0 rest; pairs (1,2) +-x, (3,4) +-y, (5,6) +-z,
 // (7,8) +-(1,1,0), (9,10) +-(1,-1,0), (11,12) +-(1,0,1), (13,14) +-(1,0,-1),
@@ -12,12 +14,26 @@
 
 namespace flb {
 
-template <typename T>
-__device__ __forceinline__ float ld3(const T *p, int i);
-template <>
-__device__ __forceinline__ float ld3<float>(const float *p, int i) { return __ldg(p + i); }
-template <>
-__device__ __forceinline__ float ld3<__half>(const __half *p, int i) { return __half2float(p[i]); }
+// Loads of fields written by earlier launches take the read-only path (COH
+// false).  Inside the persistent batched kernel a field may have been written
+// by another block of the same launch, so loads go to L2 (COH true): the
+// read-only path and L1 are not coherent within a launch.
+template <bool COH>
+__device__ __forceinline__ float ldf(const float *p)
+{
+    if (COH) return __ldcg(p);
+    return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ float ld3(const float *p, int i)
+{
+    return ldf<COH>(p + i);
+}
+template <bool COH>
+__device__ __forceinline__ float ld3(const __half *p, int i)
+{
+    return __half2float(COH ? __ldcg(p + i) : p[i]);
+}
 
 template <typename T>
 __device__ __forceinline__ void st3(T *p, int i, float v);
@@ -28,7 +44,7 @@ __device__ __forceinline__ void st3<__half>(__half *p, int i, float v) { p[i] = 
 
 // Pull of the 19 populations of site (x, y, z) from stored post-collision
 // planes fi: fbar_i(r) = stored_i(r - c_i).
-template <typename T>
+template <typename T, bool COH = false>
 __device__ __forceinline__ void pull19(const T *fi, const Geom &g, int x, int y, int z, float f[19])
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -39,28 +55,29 @@ __device__ __forceinline__ void pull19(const T *fi, const Geom &g, int x, int y,
     const int row = nx, pl = nx * ny;
     const int sY0 = row * y, sYm = row * ym, sYp = row * yp;
     const int sZ0 = pl * z, sZm = pl * zm, sZp = pl * zp;
-    f[0] = ld3(fi, x + sY0 + sZ0);
-    f[1] = ld3(fi + 1ll * N, xm + sY0 + sZ0);
-    f[2] = ld3(fi + 2ll * N, xp + sY0 + sZ0);
-    f[3] = ld3(fi + 3ll * N, x + sYm + sZ0);
-    f[4] = ld3(fi + 4ll * N, x + sYp + sZ0);
-    f[5] = ld3(fi + 5ll * N, x + sY0 + sZm);
-    f[6] = ld3(fi + 6ll * N, x + sY0 + sZp);
-    f[7] = ld3(fi + 7ll * N, xm + sYm + sZ0);
-    f[8] = ld3(fi + 8ll * N, xp + sYp + sZ0);
-    f[9] = ld3(fi + 9ll * N, xm + sYp + sZ0);
-    f[10] = ld3(fi + 10ll * N, xp + sYm + sZ0);
-    f[11] = ld3(fi + 11ll * N, xm + sY0 + sZm);
-    f[12] = ld3(fi + 12ll * N, xp + sY0 + sZp);
-    f[13] = ld3(fi + 13ll * N, xm + sY0 + sZp);
-    f[14] = ld3(fi + 14ll * N, xp + sY0 + sZm);
-    f[15] = ld3(fi + 15ll * N, x + sYm + sZm);
-    f[16] = ld3(fi + 16ll * N, x + sYp + sZp);
-    f[17] = ld3(fi + 17ll * N, x + sYm + sZp);
-    f[18] = ld3(fi + 18ll * N, x + sYp + sZm);
+    f[0] = ld3<COH>(fi, x + sY0 + sZ0);
+    f[1] = ld3<COH>(fi + 1ll * N, xm + sY0 + sZ0);
+    f[2] = ld3<COH>(fi + 2ll * N, xp + sY0 + sZ0);
+    f[3] = ld3<COH>(fi + 3ll * N, x + sYm + sZ0);
+    f[4] = ld3<COH>(fi + 4ll * N, x + sYp + sZ0);
+    f[5] = ld3<COH>(fi + 5ll * N, x + sY0 + sZm);
+    f[6] = ld3<COH>(fi + 6ll * N, x + sY0 + sZp);
+    f[7] = ld3<COH>(fi + 7ll * N, xm + sYm + sZ0);
+    f[8] = ld3<COH>(fi + 8ll * N, xp + sYp + sZ0);
+    f[9] = ld3<COH>(fi + 9ll * N, xm + sYp + sZ0);
+    f[10] = ld3<COH>(fi + 10ll * N, xp + sYm + sZ0);
+    f[11] = ld3<COH>(fi + 11ll * N, xm + sY0 + sZm);
+    f[12] = ld3<COH>(fi + 12ll * N, xp + sY0 + sZp);
+    f[13] = ld3<COH>(fi + 13ll * N, xm + sY0 + sZp);
+    f[14] = ld3<COH>(fi + 14ll * N, xp + sY0 + sZm);
+    f[15] = ld3<COH>(fi + 15ll * N, x + sYm + sZm);
+    f[16] = ld3<COH>(fi + 16ll * N, x + sYp + sZp);
+    f[17] = ld3<COH>(fi + 17ll * N, x + sYm + sZp);
+    f[18] = ld3<COH>(fi + 18ll * N, x + sYp + sZm);
 }
 
 // Force density F = -psi grad mu of Sec. IV at an interior site.
+template <bool COH = false>
 __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, float &Fx, float &Fy, float &Fz)
 {
     const Geom &g = a.g;
@@ -68,21 +85,21 @@ __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, flo
     // edges and corners included)
     const int pi = g.pidx32(x, y, z);
     const int sy = g.px, sz = g.px * g.py;
-    const float ps = __ldg(a.psi + pi);
+    const float ps = ldf<COH>(a.psi + pi);
     const float *mu = a.mu;
-    const float dx = __ldg(mu + pi + 1) - __ldg(mu + pi - 1);
-    const float dy = __ldg(mu + pi + sy) - __ldg(mu + pi - sy);
-    const float dz = __ldg(mu + pi + sz) - __ldg(mu + pi - sz);
+    const float dx = ldf<COH>(mu + pi + 1) - ldf<COH>(mu + pi - 1);
+    const float dy = ldf<COH>(mu + pi + sy) - ldf<COH>(mu + pi - sy);
+    const float dz = ldf<COH>(mu + pi + sz) - ldf<COH>(mu + pi - sz);
     if (a.fv_force) {
         // FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i), Eq. (fvgrad): with
         // w = 1/18 (faces), 1/36 (edges) it is [2 (face difference) + sum of
         // the 8 edge neighbours signed by c_a] / 12
-        const float xyp = __ldg(mu + pi + 1 + sy), xym = __ldg(mu + pi + 1 - sy);
-        const float yxp = __ldg(mu + pi - 1 + sy), yxm = __ldg(mu + pi - 1 - sy);
-        const float xzp = __ldg(mu + pi + 1 + sz), xzm = __ldg(mu + pi + 1 - sz);
-        const float zxp = __ldg(mu + pi - 1 + sz), zxm = __ldg(mu + pi - 1 - sz);
-        const float yzp = __ldg(mu + pi + sy + sz), yzm = __ldg(mu + pi + sy - sz);
-        const float zyp = __ldg(mu + pi - sy + sz), zym = __ldg(mu + pi - sy - sz);
+        const float xyp = ldf<COH>(mu + pi + 1 + sy), xym = ldf<COH>(mu + pi + 1 - sy);
+        const float yxp = ldf<COH>(mu + pi - 1 + sy), yxm = ldf<COH>(mu + pi - 1 - sy);
+        const float xzp = ldf<COH>(mu + pi + 1 + sz), xzm = ldf<COH>(mu + pi + 1 - sz);
+        const float zxp = ldf<COH>(mu + pi - 1 + sz), zxm = ldf<COH>(mu + pi - 1 - sz);
+        const float yzp = ldf<COH>(mu + pi + sy + sz), yzm = ldf<COH>(mu + pi + sy - sz);
+        const float zyp = ldf<COH>(mu + pi - sy + sz), zym = ldf<COH>(mu + pi - sy - sz);
         // xyp = mu(+1,+1,0), xym = mu(+1,-1,0), yxp = mu(-1,+1,0), yxm = mu(-1,-1,0);
         // likewise in the (x,z) and (y,z) planes
         const float c = -ps * (1.0f / 12.0f);
@@ -119,6 +136,202 @@ __device__ __forceinline__ void batch_lb_args(const BatchLists &L, const BatchRe
         sa.step = r.lb.step + ds;
     }
     __syncthreads();
+}
+
+// One D3Q19 site: pull, moments, relaxation with force and noise, store.
+template <typename T, bool GHOST_RELAX, bool COH = false>
+__device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
+{
+    const Geom &g = a.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int N = (int)g.n;
+    const int row = nx, pl = nx * ny;
+    const int s = x + row * y + pl * z;
+    T *fout = (T *)a.fout;
+
+    float f[19];
+    pull19<T, COH>((const T *)a.fin, g, x, y, z, f);
+
+    float sp[10], dp[10];
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) {
+        sp[p] = f[2 * p - 1] + f[2 * p];
+        dp[p] = f[2 * p - 1] - f[2 * p];
+    }
+    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
+    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
+    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
+    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
+    const float third = drho * (1.0f / 3.0f);
+    const float Sxx = sp[1] + (sp[4] + sp[5]) + (sp[6] + sp[7]) - third;
+    const float Syy = sp[2] + (sp[4] + sp[5]) + (sp[8] + sp[9]) - third;
+    const float Szz = sp[3] + (sp[6] + sp[7]) + (sp[8] + sp[9]) - third;
+    const float Sxy = sp[4] - sp[5], Sxz = sp[6] - sp[7], Syz = sp[8] - sp[9];
+
+    const float rho = a.rho0 + drho;
+    const float irho = __fdividef(1.0f, rho);  // ~2 ulp
+    const float vx = (jx + 0.5f * Fx) * irho, vy = (jy + 0.5f * Fy) * irho, vz = (jz + 0.5f * Fz) * irho;
+
+    const float ws = a.omega_s, wb = a.omega_b;
+    const float cs = 1.0f - 0.5f * ws, cb = 1.0f - 0.5f * wb;
+    const float Xxx = rho * vx * vx - Sxx, Xyy = rho * vy * vy - Syy, Xzz = rho * vz * vz - Szz;
+    const float trX3 = (Xxx + Xyy + Xzz) * (1.0f / 3.0f);
+    const float Txx = 2.f * vx * Fx, Tyy = 2.f * vy * Fy, Tzz = 2.f * vz * Fz;
+    const float trT3 = (Txx + Tyy + Tzz) * (1.0f / 3.0f);
+    const float isoB = (wb - ws) * trX3 + (cb - cs) * trT3;
+    float Bxx = Sxx + ws * Xxx + cs * Txx + isoB;
+    float Byy = Syy + ws * Xyy + cs * Tyy + isoB;
+    float Bzz = Szz + ws * Xzz + cs * Tzz + isoB;
+    float Bxy = Sxy + ws * (rho * vx * vy - Sxy) + cs * (vx * Fy + Fx * vy);
+    float Bxz = Sxz + ws * (rho * vx * vz - Sxz) + cs * (vx * Fz + Fx * vz);
+    float Byz = Syz + ws * (rho * vy * vz - Syz) + cs * (vy * Fz + Fy * vz);
+    const float Ax = jx + Fx, Ay = jy + Fy, Az = jz + Fz;
+
+    float g10 = 0.f, g11 = 0.f, g12 = 0.f, g13 = 0.f, g14 = 0.f, g15 = 0.f, g16 = 0.f, g17 = 0.f, g18 = 0.f;
+    if (GHOST_RELAX) {
+        const float gg = a.gamma_g;
+        const float m10 = (dp[4] + dp[5] + dp[6] + dp[7]) * (1.f / 3.f) - dp[1] * (2.f / 3.f);
+        const float m11 = (dp[4] - dp[5] + dp[8] + dp[9]) * (1.f / 3.f) - dp[2] * (2.f / 3.f);
+        const float m12 = (dp[6] - dp[7] + dp[8] - dp[9]) * (1.f / 3.f) - dp[3] * (2.f / 3.f);
+        const float m13 = dp[4] + dp[5] - dp[6] - dp[7];
+        const float m14 = -dp[4] + dp[5] + dp[8] + dp[9];
+        const float m15 = dp[6] - dp[7] - dp[8] + dp[9];
+        const float m16 = (f[0] + sp[4] + sp[5] + sp[6] + sp[7] + sp[8] + sp[9]) * (1.f / 3.f) -
+                          (sp[1] + sp[2] + sp[3]) * (2.f / 3.f);
+        const float m17 = -sp[1] + 0.5f * (sp[2] + sp[3] + sp[4] + sp[5] + sp[6] + sp[7]) - (sp[8] + sp[9]);
+        const float m18 = 0.5f * (-sp[2] + sp[3] + sp[4] + sp[5] - sp[6] - sp[7]);
+        g10 = gg * m10 * 13.5f;
+        g11 = gg * m11 * 13.5f;
+        g12 = gg * m12 * 13.5f;
+        g13 = gg * m13 * 4.5f;
+        g14 = gg * m14 * 4.5f;
+        g15 = gg * m15 * 4.5f;
+        g16 = gg * m16 * 4.5f;
+        g17 = gg * m17 * 3.0f;
+        g18 = gg * m18 * 9.0f;
+    }
+    if (a.kT > 0.f) {
+        float G[16];
+        const uint32_t sid = (uint32_t)s;
+        normals4(a.key, a.step, sid, 0u, 0u, G);
+        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
+        normals4(a.key, a.step, sid, 0u, 2u, G + 8);
+        normals4(a.key, a.step, sid, 0u, 3u, G + 12);
+        const float mun = 3.0f * rho * a.kT;
+        const float sq = mun * rsqrtf(mun);  // sqrt(rho kT / c_s^2), ~2 ulp
+        float n[15];
+#pragma unroll
+        for (int t = 0; t < 15; ++t) n[t] = sq * a.namp[t] * G[t];
+        const float two9 = 2.0f / 9.0f, one9 = 1.0f / 9.0f;
+        Bxx += two9 * (n[0] + 2.f * n[1]);
+        Byy += two9 * (n[0] - n[1] + n[2]);
+        Bzz += two9 * (n[0] - n[1] - n[2]);
+        Bxy += one9 * n[3];
+        Byz += one9 * n[4];
+        Bxz += one9 * n[5];
+        g10 += n[6];
+        g11 += n[7];
+        g12 += n[8];
+        g13 += n[9];
+        g14 += n[10];
+        g15 += n[11];
+        g16 += n[12];
+        g17 += n[13];
+        g18 += n[14];
+    }
+
+    const float tb = (Bxx + Byy + Bzz) * (1.0f / 3.0f);
+    const float e0 = 4.5f * tb;
+    const float h1 = 1.f / 3.f, h2 = 2.f / 3.f;
+    const float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
+    T *fo = fout;
+    st3(fo, s, (1.f / 3.f) * (drho - e0 + h1 * g16));
+    float E, O;
+    E = drho + 4.5f * Bxx - e0 - h2 * g16 - g17;
+    O = 3.f * Ax - h2 * g10;
+    st3(fo + 1ll * N, s, w1 * (E + O));
+    st3(fo + 2ll * N, s, w1 * (E - O));
+    E = drho + 4.5f * Byy - e0 - h2 * g16 + 0.5f * g17 - 0.5f * g18;
+    O = 3.f * Ay - h2 * g11;
+    st3(fo + 3ll * N, s, w1 * (E + O));
+    st3(fo + 4ll * N, s, w1 * (E - O));
+    E = drho + 4.5f * Bzz - e0 - h2 * g16 + 0.5f * g17 + 0.5f * g18;
+    O = 3.f * Az - h2 * g12;
+    st3(fo + 5ll * N, s, w1 * (E + O));
+    st3(fo + 6ll * N, s, w1 * (E - O));
+    const float Gev = h1 * g16 + 0.5f * g17;
+    E = drho + 4.5f * (Bxx + Byy + 2.f * Bxy) - e0 + Gev + 0.5f * g18;
+    O = 3.f * (Ax + Ay) + h1 * (g10 + g11) + g13 - g14;
+    st3(fo + 7ll * N, s, w2 * (E + O));
+    st3(fo + 8ll * N, s, w2 * (E - O));
+    E = drho + 4.5f * (Bxx + Byy - 2.f * Bxy) - e0 + Gev + 0.5f * g18;
+    O = 3.f * (Ax - Ay) + h1 * (g10 - g11) + g13 + g14;
+    st3(fo + 9ll * N, s, w2 * (E + O));
+    st3(fo + 10ll * N, s, w2 * (E - O));
+    E = drho + 4.5f * (Bxx + Bzz + 2.f * Bxz) - e0 + Gev - 0.5f * g18;
+    O = 3.f * (Ax + Az) + h1 * (g10 + g12) - g13 + g15;
+    st3(fo + 11ll * N, s, w2 * (E + O));
+    st3(fo + 12ll * N, s, w2 * (E - O));
+    E = drho + 4.5f * (Bxx + Bzz - 2.f * Bxz) - e0 + Gev - 0.5f * g18;
+    O = 3.f * (Ax - Az) + h1 * (g10 - g12) - g13 - g15;
+    st3(fo + 13ll * N, s, w2 * (E + O));
+    st3(fo + 14ll * N, s, w2 * (E - O));
+    E = drho + 4.5f * (Byy + Bzz + 2.f * Byz) - e0 + h1 * g16 - g17;
+    O = 3.f * (Ay + Az) + h1 * (g11 + g12) + g14 - g15;
+    st3(fo + 15ll * N, s, w2 * (E + O));
+    st3(fo + 16ll * N, s, w2 * (E - O));
+    E = drho + 4.5f * (Byy + Bzz - 2.f * Byz) - e0 + h1 * g16 - g17;
+    O = 3.f * (Ay - Az) + h1 * (g11 - g12) + g14 + g15;
+    st3(fo + 17ll * N, s, w2 * (E + O));
+    st3(fo + 18ll * N, s, w2 * (E - O));
+}
+
+// Velocity of the streamed state at (x, y, z): u = (sum fbar c + F/2)/rho with
+// fbar the populations the next step pulls (a.fout) and F this step's force.
+template <typename T, bool FORCE, bool COH = false>
+__device__ __forceinline__ void vel3_site(const LBArgs &a, int x, int y, int z)
+{
+    const Geom &g = a.g;
+    float f[19];
+    pull19<T, COH>((const T *)a.fout, g, x, y, z, f);
+    float sp[10], dp[10];
+#pragma unroll
+    for (int p = 1; p <= 9; ++p) {
+        sp[p] = f[2 * p - 1] + f[2 * p];
+        dp[p] = f[2 * p - 1] - f[2 * p];
+    }
+    const float drho = f[0] + ((sp[1] + sp[2] + sp[3]) + ((sp[4] + sp[5]) + (sp[6] + sp[7]) + (sp[8] + sp[9])));
+    const float jx = dp[1] + (dp[4] + dp[5]) + (dp[6] + dp[7]);
+    const float jy = dp[2] + (dp[4] - dp[5]) + (dp[8] + dp[9]);
+    const float jz = dp[3] + (dp[6] - dp[7]) + (dp[8] - dp[9]);
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3<COH>(a, x, y, z, Fx, Fy, Fz);
+    const float irho = __fdividef(1.0f, a.rho0 + drho);
+    store_padded(a.u, g, x, y, z, (jx + 0.5f * Fx) * irho, 1);
+    store_padded(a.u + g.pn, g, x, y, z, (jy + 0.5f * Fy) * irho, 1);
+    store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
+}
+
+// The column (x, y), output planes zb .. ze-1 of the mu field.
+template <bool COH = false>
+__device__ __forceinline__ void mu3_column(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
+                                           float B, float K, int x, int y, int zb, int ze)
+{
+    const int Y = g.px, Z = g.px * g.py;
+    const float k22 = K * (1.0f / 22.0f);
+    int c = g.pidx32(x, y, zb - 1);
+    float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f;  // planes p-2, p-1
+    for (int p = zb - 1; p <= ze; ++p, c += Z) {
+        const float a2 = ldf<COH>(psi + c);
+        const float b2 = (ldf<COH>(psi + c - 1) + ldf<COH>(psi + c + 1)) + (ldf<COH>(psi + c - Y) + ldf<COH>(psi + c + Y));
+        const float d2 = (ldf<COH>(psi + c - 1 - Y) + ldf<COH>(psi + c + 1 - Y)) + (ldf<COH>(psi + c - 1 + Y) + ldf<COH>(psi + c + 1 + Y));
+        if (p - 1 >= zb) {
+            const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
+            mu[c - Z] = A * a1 + B * a1 * a1 * a1 - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * a1);
+        }
+        a0 = a1; b0 = b1; d0 = d1;
+        a1 = a2; b1 = b2; d1 = d2;
+    }
 }
 
 }  // namespace flb
