@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default psi tile depth (64 planes)")
+    ap.add_argument("--variant-steps", type=int, default=10,
+                    help="steps timed for each variant of the path (FD scheme, FP16 storage, D2Q9); 0 skips them")
     ap.add_argument("--ensemble-steps", type=int, default=40,
                     help="steps of the 256-replica ensemble timed batched vs plain (0: skip)")
     return ap.parse_args()
@@ -203,6 +205,45 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
     return out
 
 
+def path_variants(F, I, local, steps, peak):
+    """Throughput of the other forms of the path, each on its own handle after 3
+    warm-up steps, inputs larger than L2: the FD psi scheme and the FP16 storage
+    variant on the 512^3 quench, and the D2Q9 path on a 4096^2 quench (same free
+    energy, FD as in the 2D workload).  MLUPS and the fraction of the HBM roofline
+    on the algorithmic bytes of that form."""
+    import torch
+    d = dict(I.WORKLOADS["quench"])
+    forms = [
+        ("fd_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FD), 160),
+        ("fp16_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, storage=F.FLB_F16_DEV), 84),
+        ("d2q9_4096", dict(dim=2, q=9, nx=4096, ny=4096, nz=1, psi_scheme=F.FLB_FD), 80),
+    ]
+    out = {}
+    for key, kw, alg in forms:
+        p = F.flb_params_default(tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
+                                 integrator=F.FLB_HEUN, seed=d["seed"], **kw)
+        N = p.nx * p.ny * p.nz
+        s = F.Solver(p, device=f"cuda:{local}")
+        s.set_fields(psi=I.uniform_field(N, -0.01, 0.01, 11))
+        if p.dim == 3:
+            s.autotune()
+        s.step(3)
+        s.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        mlups = N / (ms / 1e3) / 1e6
+        out[key] = {"mlups": mlups, "ms_per_step": ms, "alg_bytes_per_site": alg,
+                    "step_frac_of_peak": alg * N / (ms / 1e3) / 1e9 / peak}
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -314,6 +355,9 @@ def run_ours(args):
         del s
         torch.cuda.empty_cache()
         ens = ensemble_batched_vs_plain(F, I, args.ensemble_steps, local, rank, autotune=not args.no_autotune)
+    variants = None
+    if args.variant_steps > 0 and rank == 0:
+        variants = path_variants(F, I, local, args.variant_steps, peak)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)
@@ -336,7 +380,7 @@ def run_ours(args):
             "step_roofline": {"alg_bytes_per_site": ALG_BYTES_SITE[storage], "achieved_gbs": step_gbs,
                               "frac": step_gbs / peak, "kernel_ms_per_step": {k: v / kp for k, v in kms.items()}},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-            "batched_vs_plain": ens,
+            "batched_vs_plain": ens, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
