@@ -59,6 +59,7 @@ extern "C" {
 #define FLB_COUPLE_ADVECT 2    /* the fluid advects psi */
 #define FLB_SQ_PSI 0           /* structure factor of psi */
 #define FLB_SQ_HEIGHT 1        /* capillary spectrum of the two psi = 0 surfaces */
+#define FLB_SQ_DYNAMIC 2       /* dynamic structure factor S(q, tau) of psi */
 #define FLB_FORCE_MATCHED 0     /* force gradient matched to the psi scheme */
 #define FLB_FORCE_CD 1          /* central difference of Sec. IV */
 #define FLB_FORCE_FV 2          /* FV lattice gradient of Eq. (fvgrad) */
@@ -91,6 +92,8 @@ extern "C" {
  *   seed        : Philox key of this replica.
  *   sq_kmax     : structure-factor window: wavevector indices |k_a| <= sq_kmax
  *                 on every axis; <= 0 or >= n_a/2 keeps the whole axis.
+ *   sq_lags     : lags kept for the dynamic structure factor S(q, tau) (0 = none,
+ *                 at most 4096); lag l is l sampling intervals (flb_set_sampling).
  *   force_grad  : lattice gradient in the force F = -psi grad mu:
  *                 FLB_FORCE_MATCHED (default) takes the central difference
  *                 with FLB_FD and the FV gradient (1/c_s^2) sum_i w_i c_i
@@ -109,13 +112,15 @@ typedef struct flb_params {
     uint64_t seed;
     int32_t sq_kmax;
     int32_t force_grad;
+    int32_t sq_lags;
+    int32_t reserved;        /* set to 0 */
 } flb_params;
 
 typedef struct flb_handle flb_handle;
 
 /* Fill *p with the defaults: D3Q19 32^3, rho0 1, tau 0.8, gamma_bulk NaN,
  * gamma_ghost 0, kT 0, A 0.05, B 0, K 0.04, M 0.1, FV, Heun, FP32, coupling 3,
- * seed 1, sq_kmax 0, force_grad FLB_FORCE_MATCHED. */
+ * seed 1, sq_kmax 0, force_grad FLB_FORCE_MATCHED, sq_lags 0. */
 void flb_params_default(flb_params *p);
 
 /* Device workspace needed for nrep replicas p[0..nrep-1]; 0 if any parameter
@@ -166,8 +171,10 @@ int flb_get_step(flb_handle *h, int32_t rep, int64_t *step);
 int flb_moments(flb_handle *h, int32_t rep, double *totals, double *u2);
 
 /* Sampling of the structure factors during flb_step: every every_m steps
- * (0 = never) the psi spectrum (mask bit 1) and/or the interface-height
- * spectrum (mask bit 2) of every replica is accumulated in FP64. */
+ * (0 = never) the psi spectrum (mask bit 1), the interface-height spectrum
+ * (mask bit 2) and/or the dynamic structure factor (mask bit 4: the psi
+ * spectrum's Fourier components are kept for the last sq_lags samples and
+ * correlated with every new one) of every replica are accumulated in FP64. */
 int flb_set_sampling(flb_handle *h, int32_t every_m, int32_t mask);
 
 /* Take one sample now (same mask bits).  Asynchronous. */
@@ -178,8 +185,12 @@ int flb_sample(flb_handle *h, int32_t mask);
  * (Eqs. test1, test2); each axis lists indices k = 0..kmax then n-kmax..n-1
  * (all n indices when the whole axis is kept), x fastest.  which =
  * FLB_SQ_HEIGHT: out has ny*nx values <|h~(q)|^2> (Eq. flucinterf) averaged over
- * the two interfaces of a slab normal to z.  *nsamples receives the sample
- * count.  Synchronising. */
+ * the two interfaces of a slab normal to z.  which = FLB_SQ_DYNAMIC: out has
+ * sq_lags blocks of Kz*Ky*Kx values (lag slowest), block l holding
+ * S(q, l m) = < Re psi~(q, t) psi~(q, t - l m)^* > over the samples t that
+ * have a sample l intervals before them (the paper's S(q, tau), Sec. VI.A,
+ * Eq. strf; the same window and normalisation as FLB_SQ_PSI).  *nsamples
+ * receives the sample count (of lag 0 for FLB_SQ_DYNAMIC).  Synchronising. */
 int flb_structure_factor(flb_handle *h, int32_t rep, int32_t which, double *out, int64_t *nsamples);
 
 /* Number of values flb_structure_factor writes for `which`. */

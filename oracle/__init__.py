@@ -297,6 +297,20 @@ def structure_factor(p: Params, psi: np.ndarray) -> np.ndarray:
     return np.abs(np.fft.fftn(a)) ** 2 / p.n
 
 
+def dynamic_structure_factor(p: Params, psis, nlags: int) -> np.ndarray:
+    """S(q, l) = mean over samples t with t >= l of Re[psi~(q, t) conj(psi~(q, t - l))],
+    psi~(q) = N^-1/2 sum_r psi(r) e^{-iq.r}: the paper's S(q, tau) of Sec. VI.A
+    (Eq. strf) for the lag tau = l sampling intervals, from the sampled fields
+    psis (oldest first).  Full FFT grid, shape (nlags, nz, ny, nx)."""
+    F = [np.fft.fftn(np.asarray(s, dtype=np.float64).reshape(p.shape)) for s in psis]
+    out = np.zeros((nlags,) + tuple(p.shape))
+    for l in range(nlags):
+        terms = [np.real(F[t] * np.conj(F[t - l])) for t in range(l, len(F))]
+        if terms:
+            out[l] = np.mean(terms, axis=0) / p.n
+    return out
+
+
 def interface_heights(p: Params, psi: np.ndarray):
     """Heights of the two psi = 0 surfaces of a slab normal to z (Sec. VI.C).
 

@@ -27,7 +27,7 @@ FLB_EULER, FLB_HEUN = 1, 2
 FLB_F32_DEV, FLB_F16_DEV = 0, 1
 FLB_COUPLE_FORCE, FLB_COUPLE_ADVECT = 1, 2
 FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV = 0, 1, 2
-FLB_SQ_PSI, FLB_SQ_HEIGHT = 0, 1
+FLB_SQ_PSI, FLB_SQ_HEIGHT, FLB_SQ_DYNAMIC = 0, 1, 2
 FLB_MODE_PLAIN, FLB_MODE_BATCHED, FLB_MODE_PERSISTENT = 0, 1, 2
 FLB_TUNE_FORCE = 1
 
@@ -45,6 +45,7 @@ class FlbParams(ctypes.Structure):
         ("storage", ctypes.c_int32), ("coupling", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("sq_kmax", ctypes.c_int32), ("force_grad", ctypes.c_int32),
+        ("sq_lags", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

@@ -57,6 +57,10 @@ struct Rep {
     double *sq = nullptr, *hsq = nullptr;
     int Kx = 0, Ky = 0, Kz = 0;
     int64_t sq_n = 0, h_n = 0;
+    float2 *dring = nullptr;   // dynamic S(q, tau): last sq_lags Fourier snapshots
+    double *dacc = nullptr;    // and the lag accumulators, sq_lags x K
+    int dslot = -1;
+    int64_t d_n = 0;
     int64_t step = 0;
     float omega_s = 0, omega_b = 0, gamma_g = 0;
     float namp[16] = {0};
@@ -96,6 +100,7 @@ bool valid(const flb_params &p)
     if (p.coupling < 0 || p.coupling > 3) return false;
     if (p.force_grad < FLB_FORCE_MATCHED || p.force_grad > FLB_FORCE_FV) return false;
     if (p.sq_kmax < 0) return false;
+    if (p.sq_lags < 0 || p.sq_lags > 4096 || p.reserved != 0) return false;
     if (p.nx > 4096 || p.ny > 4096 || (p.dim == 3 && p.nz > 4096)) return false;  // DFT twiddle tables
     return true;
 }
@@ -141,6 +146,11 @@ void carve_rep(Rep &r, Carver &cv)
     r.Kz = r.dim == 3 ? axis_K(g.nz, r.p.sq_kmax) : 1;
     r.sq = cv.take<double>((size_t)r.Kx * r.Ky * r.Kz);
     if (r.dim == 3) r.hsq = cv.take<double>((size_t)g.nx * g.ny);
+    if (r.p.sq_lags > 0) {
+        const size_t K = (size_t)r.Kx * r.Ky * r.Kz;
+        r.dring = cv.take<float2>(K * (size_t)r.p.sq_lags);
+        r.dacc = cv.take<double>(K * (size_t)r.p.sq_lags);
+    }
 }
 
 void init_rep_consts(Rep &r, const flb_params &p)
@@ -536,7 +546,8 @@ int sample_rep(flb_handle *h, Rep &r, int mask)
         int64_t l0;
         ~Close() { span(h, 2, e0, mark(h), (int)(h->launches - l0)); }
     } close_{h, e0, l0};
-    if (mask & 1) {
+    const bool dyn = (mask & 4) && r.dring;
+    if ((mask & 1) || dyn) {
         DftArgs d;
         d.in = r.psi[r.pcur];
         d.off = g.pidx(0, 0, 0);
@@ -550,12 +561,22 @@ int sample_rep(flb_handle *h, Rep &r, int mask)
         d.Kz = r.Kz;
         d.X1 = h->X1;
         d.X2 = h->X2;
-        d.S = r.sq;
+        d.S = (mask & 1) ? r.sq : nullptr;
         d.scale = 1.0 / (double)g.n;
+        const long long K = (long long)r.Kx * r.Ky * r.Kz;
+        const int L = r.p.sq_lags;
+        const int slot = dyn ? (r.dslot + 1) % L : 0;
+        d.snap = dyn ? r.dring + (size_t)slot * K : nullptr;
         const cudaError_t e = launch_dft_accumulate(d, h->st);
         h->launches += 3;
         if (e != cudaSuccess) return FLB_ECUDA;
-        r.sq_n += 1;
+        if (mask & 1) r.sq_n += 1;
+        if (dyn) {
+            const int nlag = (int)std::min<int64_t>(r.d_n + 1, L);
+            FLB_TRY(launch_dyn_corr(r.dring, L, slot, nlag, K, r.dacc, 1.0 / (double)g.n, h->st));
+            r.dslot = slot;
+            r.d_n += 1;
+        }
     }
     if ((mask & 2) && r.dim == 3) {
         FLB_TRY(launch_heights(g, r.psi[r.pcur], h->heights, h->st));
@@ -1097,7 +1118,7 @@ int flb_moments(flb_handle *h, int32_t rep, double *totals, double *u2)
 
 int flb_set_sampling(flb_handle *h, int32_t every_m, int32_t mask)
 {
-    if (!h || every_m < 0 || mask < 0 || mask > 3) return FLB_EINVAL;
+    if (!h || every_m < 0 || mask < 0 || mask > 7) return FLB_EINVAL;
     h->sample_every = every_m;
     h->sample_mask = mask;
     return FLB_OK;
@@ -1105,7 +1126,7 @@ int flb_set_sampling(flb_handle *h, int32_t every_m, int32_t mask)
 
 int flb_sample(flb_handle *h, int32_t mask)
 {
-    if (!h || mask < 0 || mask > 3) return FLB_EINVAL;
+    if (!h || mask < 0 || mask > 7) return FLB_EINVAL;
     for (Rep &r : h->reps) {
         const int rc = sample_rep(h, r, mask);
         if (rc != FLB_OK) return rc;
@@ -1119,20 +1140,31 @@ int64_t flb_structure_factor_size(flb_handle *h, int32_t rep, int32_t which)
     if (!r) return -1;
     if (which == FLB_SQ_PSI) return (int64_t)r->Kx * r->Ky * r->Kz;
     if (which == FLB_SQ_HEIGHT) return r->dim == 3 ? (int64_t)r->g.nx * r->g.ny : 0;
+    if (which == FLB_SQ_DYNAMIC) return (int64_t)r->Kx * r->Ky * r->Kz * r->p.sq_lags;
     return -1;
 }
 
 int flb_structure_factor(flb_handle *h, int32_t rep, int32_t which, double *out, int64_t *nsamples)
 {
     Rep *r = get_rep(h, rep);
-    if (!r || !out || (which != FLB_SQ_PSI && which != FLB_SQ_HEIGHT)) return FLB_EINVAL;
+    if (!r || !out || (which != FLB_SQ_PSI && which != FLB_SQ_HEIGHT && which != FLB_SQ_DYNAMIC)) return FLB_EINVAL;
     if (which == FLB_SQ_HEIGHT && r->dim != 3) return FLB_EINVAL;
+    if (which == FLB_SQ_DYNAMIC && !r->dacc) return FLB_EINVAL;
     const int64_t cnt = flb_structure_factor_size(h, rep, which);
-    const double *src = which == FLB_SQ_PSI ? r->sq : r->hsq;
-    const int64_t ns = which == FLB_SQ_PSI ? r->sq_n : r->h_n;
+    const double *src = which == FLB_SQ_PSI ? r->sq : which == FLB_SQ_HEIGHT ? r->hsq : r->dacc;
+    const int64_t ns = which == FLB_SQ_PSI ? r->sq_n : which == FLB_SQ_HEIGHT ? r->h_n : r->d_n;
     int rc = cuerr(cudaMemcpyAsync(out, src, (size_t)cnt * 8, cudaMemcpyDeviceToHost, h->st));
     if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
     if (rc != FLB_OK) return rc;
+    if (which == FLB_SQ_DYNAMIC) {
+        const int64_t K = (int64_t)r->Kx * r->Ky * r->Kz;
+        for (int64_t l = 0; l < r->p.sq_lags; ++l) {
+            const int64_t nl = ns - l;  // samples with a partner l intervals earlier
+            for (int64_t k = 0; k < K; ++k) out[l * K + k] = nl > 0 ? out[l * K + k] / (double)nl : 0.0;
+        }
+        if (nsamples) *nsamples = ns;
+        return FLB_OK;
+    }
     for (int64_t k = 0; k < cnt; ++k) out[k] = ns > 0 ? out[k] / (double)ns : 0.0;
     if (which == FLB_SQ_HEIGHT) out[0] = 0.0;  // the mean height carries no capillary mode
     if (nsamples) *nsamples = ns;
@@ -1147,8 +1179,11 @@ int flb_sq_reset(flb_handle *h, int32_t rep)
         Rep &r = h->reps[(size_t)k];
         int rc = cuerr(cudaMemsetAsync(r.sq, 0, (size_t)r.Kx * r.Ky * r.Kz * 8, h->st));
         if (rc == FLB_OK && r.hsq) rc = cuerr(cudaMemsetAsync(r.hsq, 0, (size_t)r.g.nx * r.g.ny * 8, h->st));
+        if (rc == FLB_OK && r.dacc)
+            rc = cuerr(cudaMemsetAsync(r.dacc, 0, (size_t)r.Kx * r.Ky * r.Kz * r.p.sq_lags * 8, h->st));
         if (rc != FLB_OK) return rc;
-        r.sq_n = r.h_n = 0;
+        r.sq_n = r.h_n = r.d_n = 0;
+        r.dslot = -1;
     }
     return cuerr(cudaStreamSynchronize(h->st));
 }

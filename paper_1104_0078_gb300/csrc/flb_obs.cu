@@ -204,7 +204,32 @@ __global__ void dft_z_acc_kernel(DftArgs a)
         m += k;
         if (m >= a.nz) m -= a.nz;
     }
-    a.S[t] += a.scale * (re * re + im * im);
+    if (a.S) a.S[t] += a.scale * (re * re + im * im);
+    if (a.snap) a.snap[t] = make_float2((float)re, (float)im);
+}
+
+// Dynamic structure factor: correlate the newest Fourier components with those
+// of the nlag - 1 samples before them, in FP64.
+__global__ void dyn_corr_kernel(const float2 *__restrict__ ring, int L, int slot, int nlag, long long K,
+                                double *__restrict__ acc, double scale)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    const float2 c = ring[(long long)slot * K + t];
+    int s = slot;
+    for (int l = 0; l < nlag; ++l) {
+        const float2 p = ring[(long long)s * K + t];
+        acc[(long long)l * K + t] += scale * ((double)c.x * p.x + (double)c.y * p.y);
+        s = s == 0 ? L - 1 : s - 1;
+    }
+}
+
+cudaError_t launch_dyn_corr(const float2 *ring, int L, int slot, int nlag, long long K, double *acc, double scale,
+                            cudaStream_t s)
+{
+    const int bs = 256;
+    dyn_corr_kernel<<<(unsigned)((K + bs - 1) / bs), bs, 0, s>>>(ring, L, slot, nlag, K, acc, scale);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dft_accumulate(const DftArgs &a, cudaStream_t s)

@@ -24,6 +24,7 @@ def flb_params(d: dict, **kw) -> F.FlbParams:
     p.coupling = d.get("coupling", 3)
     p.seed = d.get("seed", 1)
     p.sq_kmax = d.get("sq_kmax", 0)
+    p.sq_lags = d.get("sq_lags", 0)
     p.force_grad = d.get("force_grad", 0)
     return p
 

@@ -50,9 +50,9 @@ def test_params_layout_matches_c():
     #include <stddef.h>
     #include "flb.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(flb_params), offsetof(flb_params, rho0),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(flb_params), offsetof(flb_params, rho0),
              offsetof(flb_params, kT), offsetof(flb_params, psi_scheme), offsetof(flb_params, seed),
-             offsetof(flb_params, sq_kmax), offsetof(flb_params, force_grad));
+             offsetof(flb_params, sq_kmax), offsetof(flb_params, force_grad), offsetof(flb_params, sq_lags));
       return 0; }
     """
     with tempfile.TemporaryDirectory() as d:
@@ -63,7 +63,7 @@ def test_params_layout_matches_c():
         vals = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
     P = F.FlbParams
     assert vals == [ctypes.sizeof(P), P.rho0.offset, P.kT.offset, P.psi_scheme.offset, P.seed.offset,
-                    P.sq_kmax.offset, P.force_grad.offset]
+                    P.sq_kmax.offset, P.force_grad.offset, P.sq_lags.offset]
 
 
 def test_defaults_and_workspace_sizing(lib):
@@ -83,7 +83,8 @@ def test_defaults_and_workspace_sizing(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 3), ("q", 15), ("tau", 0.0), ("gamma_ghost", 1.0), ("kT", -1.0),
                                          ("psi_scheme", 2), ("integrator", 3), ("storage", 2), ("coupling", 4),
-                                         ("M", -0.1), ("sq_kmax", -1), ("force_grad", 3), ("force_grad", -1)])
+                                         ("M", -0.1), ("sq_kmax", -1), ("force_grad", 3), ("force_grad", -1),
+                                         ("sq_lags", -1), ("sq_lags", 5000), ("reserved", 1)])
 def test_invalid_parameters_rejected(lib, field, value):
     p = F.flb_params_default(**{field: value})
     assert F.flb_workspace_bytes(p) == 0

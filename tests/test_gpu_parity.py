@@ -148,6 +148,37 @@ def test_structure_factor_matches_oracle():
     assert np.max(np.abs(S_gpu[big] - acc[big]) / acc[big]) < 1e-4
 
 
+@pytest.mark.parametrize("kmax", [0, 3])
+def test_dynamic_structure_factor_matches_oracle(kmax):
+    # same seed: S(q, l) accumulated on the GPU (Fourier snapshots kept on the
+    # device, FP64 lag sums) against the oracle's estimator on its own trajectory,
+    # sampled every 4 steps over 80 steps, 6 lags; full grid and a window
+    d = dict(dim=3, q=19, nx=16, ny=12, nz=10, tau=0.8, kT=1e-4, A=0.1, B=0.0, K=0.04, M=0.2, scheme=1,
+             integrator=2, seed=4)
+    fp = flb_params(d, sq_kmax=kmax)
+    fp.sq_lags = 6
+    s = F.Solver(fp)
+    s.set_sampling(4, 1 | 4)
+    s.step(80)
+    S_gpu, ns = s.structure_factor(which=F.FLB_SQ_DYNAMIC)
+    S_static, _ = s.structure_factor()
+    assert ns == 20
+    op = oracle_params(d)
+    st = O.State.rest(op)
+    psis = []
+    for _ in range(20):
+        st.advance(4)
+        psis.append(st.psi.copy())
+    ref = O.dynamic_structure_factor(op, psis, 6)
+    if kmax:
+        sel = [np.r_[0:kmax + 1, n - kmax:n] for n in op.shape]
+        ref = ref[:, sel[0]][:, :, sel[1]][:, :, :, sel[2]]
+    S_gpu = S_gpu.reshape(ref.shape)
+    assert np.allclose(S_gpu[0].ravel(), S_static, rtol=1e-6, atol=0)   # lag 0 is the static S(q)
+    scale = np.abs(ref[0]).max()
+    assert np.max(np.abs(S_gpu - ref)) < 2e-4 * scale
+
+
 def test_structure_factor_window():
     # sq_kmax keeps |k_a| <= kmax on every axis, in FFT order; sampled at step 0
     # from a seeded field, against the oracle's FFT of the same field

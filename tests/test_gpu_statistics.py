@@ -17,9 +17,12 @@ from gpu_helpers import flb_params, oracle_params
 pytestmark = [pytest.mark.gpu]
 
 
-def _measure(d, nsteps, t_start, every, storage=F.FLB_F32_DEV):
+def _measure(d, nsteps, t_start, every, storage=F.FLB_F32_DEV, u0=None):
     p = flb_params(d, storage=storage)
     s = F.Solver(p)
+    if u0 is not None:                    # a uniform flow (Sec. VI.B)
+        N = p.nx * p.ny * p.nz
+        s.set_fields(u=np.repeat(np.asarray(u0, dtype=np.float64)[:p.dim, None], N, axis=1))
     s.step(t_start)
     s.sq_reset()
     u2 = np.zeros(p.dim)
@@ -91,6 +94,19 @@ def test_bulk_3d_structure_factor_and_equipartition():
     assert np.all(np.abs(u2 / d["kT"] - 1) < 0.01)
 
 
+def test_galilean_invariance_small_mach():
+    # Sec. VI.B: a uniform flow along the x = y diagonal at Ma = |u|/c_s = 0.08
+    # leaves the static structure factor on the equilibrium theory (the bulk 3D
+    # workload); the fluctuations around the flow keep <u_a^2> - u0_a^2 = kT/rho0
+    d = dict(I.WORKLOADS["bulk_3d"], integrator=2)
+    u = 0.08 * np.sqrt(1.0 / 3.0) / np.sqrt(2.0)
+    u0 = np.array([u, u, 0.0])
+    S, ns, u2, times = _measure(d, 10000, 1000, 10, u0=u0)
+    th, n_ind, qg = _theory(d, times)
+    _shell_check(S.reshape(64, 64, 64), th, n_ind, qg, tol=0.02)
+    assert np.all(np.abs((u2 - u0 ** 2) / d["kT"] - 1) < 0.02)
+
+
 def test_fp16_storage_acceptance():
     # FP16 deviations are accepted if equipartition and S(q) stay within the
     # tolerances of the FP32 path: against theory, and shell by shell against an
@@ -106,3 +122,42 @@ def test_fp16_storage_acceptance():
         assert np.all(np.abs(res[st][1] / d["kT"] - 1) < 0.03)
     _shell_check(res[F.FLB_F16_DEV][0], res[F.FLB_F32_DEV][0], n_ind, qg, tol=0.03)
     assert np.all(np.abs(res[F.FLB_F16_DEV][1] / res[F.FLB_F32_DEV][1] - 1) < 0.03)
+
+
+@pytest.mark.parametrize("scheme,coupling", [(1, 0), (1, 3), (0, 3)])
+def test_dynamic_structure_factor_decay(scheme, coupling):
+    # Eq. (strf): S(q, tau) = S(q) exp(-tau / tau(q)); in discrete time the mode is
+    # multiplied by the integrator's amplification g(q) per step, so
+    # S(q, l m) / S(q, 0) = g(q)^(l m).  The paper's parameters of the test (Sec.
+    # VI.A): A = 0.065, B = 0, K = 0.04, M = 0.095 on 32^3, from equilibrium (the
+    # modes tested relax within the first 3000 steps).  Modes are pooled by decay
+    # per sampling interval (four pools of equal size); each pool's mean ratio must
+    # follow g^(l m) within 0.02 (the statistical s.d. of a pool is below 0.005).
+    d = dict(dim=3, q=19, nx=32, ny=32, nz=32, tau=0.8, kT=1e-4, A=0.065, B=0.0, K=0.04, M=0.095,
+             scheme=scheme, integrator=2, coupling=coupling, seed=21)
+    m, nlags = 5, 8
+    p = flb_params(d, sq_lags=nlags)
+    s = F.Solver(p)
+    s.step(3000)
+    s.sq_reset()
+    s.set_sampling(m, 4)
+    s.step(30000)
+    S, ns = s.structure_factor(which=F.FLB_SQ_DYNAMIC)
+    assert ns == 6000
+    op = oracle_params(d)
+    qg = T.q_grid(op.shape)
+    c, w = O.lattice(3, 19)
+    Lm = T.L_so(qg) if scheme == 0 else T.L_fv(qg, c, w)
+    g = T.amplification(-T.lam(qg, op, Lm), 2)
+    S = S.reshape((nlags,) + op.shape)
+    gm = g ** m
+    # four pools of equal size over the modes whose decay over the 7 lags is measurable
+    sel = (gm > 0.3) & (gm < 0.985)
+    edges = np.quantile(gm[sel], [0.0, 0.25, 0.5, 0.75, 1.0])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        pool = sel & (gm >= lo) & (gm <= hi)
+        assert pool.sum() >= 1000
+        for l in range(1, nlags):
+            r = S[l][pool] / S[0][pool]
+            expect = gm[pool] ** l
+            assert abs(r.mean() - expect.mean()) < 0.02, (lo, hi, l, r.mean(), expect.mean(), pool.sum())

@@ -171,3 +171,31 @@ def test_force_advection_energy_exchange(dim, q, scheme):
     assert abs(work + dfree) < 1e-13 * scale
     other = O.Params(**{**p.__dict__, "force_grad": 2 if scheme == 0 else 1})
     assert abs(np.sum(u * O.force(other, psi)) + dfree) > 1e-2 * scale
+
+
+@pytest.mark.parametrize("dim,q,scheme", [(2, 9, 0), (3, 19, 1)])
+def test_dynamic_structure_factor_exact_decay(dim, q, scheme):
+    # Without noise, with B = 0 and diffusion alone, each Fourier mode is multiplied
+    # every step by the integrator's amplification g(q) (Eq. strf's decay, discrete
+    # time), so S(q, l m) = g(q)^(l m) <|psi~(q, t - l m)|^2> exactly: this fixes the
+    # lag direction, the conjugate and the 1/N of the estimator.
+    shape = (1, 16, 12) if dim == 2 else (6, 5, 8)
+    p = O.Params(dim=dim, q=q, nx=shape[2], ny=shape[1], nz=shape[0], kT=0.0, A=0.05, B=0.0, K=0.04, M=0.1,
+                 scheme=scheme, integrator=2, coupling=0)
+    rng = np.random.default_rng(7)
+    s = O.State.rest(p, psi=rng.normal(size=p.n))
+    m, nsamp, nlags = 3, 7, 4
+    psis = []
+    for _ in range(nsamp):
+        psis.append(s.psi.copy())
+        s.advance(m)
+    S = O.dynamic_structure_factor(p, psis, nlags)
+    qg = T.q_grid(shape)
+    c, w = O.lattice(dim, q)
+    Lmob = (T.L_so_2d(qg) if dim == 2 else T.L_so(qg)) if scheme == 0 else T.L_fv(qg, c, w)
+    g = T.amplification(-T.lam(qg, p, Lmob), 2)
+    P = [np.abs(np.fft.fftn(x.reshape(shape))) ** 2 / p.n for x in psis]
+    for l in range(nlags):
+        expect = g ** (l * m) * np.mean(P[:nsamp - l], axis=0)
+        assert np.allclose(S[l], expect, rtol=1e-10, atol=1e-14 * np.max(P[0]))
+    assert np.allclose(S[0], np.mean(P, axis=0), rtol=1e-13)
