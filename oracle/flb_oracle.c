@@ -365,6 +365,53 @@ void ora_mu(const ora_params *p, const double *psi, double *mu)
     free(lap);
 }
 
+/* Force density as the divergence of the order-parameter stress (Sec. IV,
+ * Eq. muf), F = -div sigma with
+ *   sigma_ab = K d_a psi d_b psi
+ *            + delta_ab [A/2 psi^2 + 3B/4 psi^4 - K psi lap psi - K/2 |grad psi|^2]
+ * (psi f' - f = A/2 psi^2 + 3B/4 psi^4 for f = A/2 psi^2 + B/4 psi^4), whose
+ * continuum divergence is psi grad mu.  Reading: gradients by the symmetric
+ * central difference, lap by the SO stencil (as in mu), and the divergence by
+ * the central difference, so that sum_r F = 0 exactly (momentum is conserved
+ * for B != 0 too) while F = -psi grad mu + O(h^2). */
+static void stress_force(const ora_params *p, const box_t *g, const double *psi, double *F)
+{
+    const size_t N = g->n;
+    const int d = g->dim;
+    double *lap = (double *)malloc(sizeof(double) * N);
+    double *sig = (double *)malloc(sizeof(double) * 9 * N);
+    ora_laplacian_so(p->dim, p->nx, p->ny, p->nz, psi, lap);
+    for (size_t s = 0; s < N; ++s) {
+        int x, y, z;
+        coords(g, s, &x, &y, &z);
+        double gr[3] = {0.5 * (psi[site_at(g, x + 1, y, z)] - psi[site_at(g, x - 1, y, z)]),
+                        0.5 * (psi[site_at(g, x, y + 1, z)] - psi[site_at(g, x, y - 1, z)]),
+                        d == 3 ? 0.5 * (psi[site_at(g, x, y, z + 1)] - psi[site_at(g, x, y, z - 1)]) : 0.0};
+        const double ps = psi[s];
+        const double g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+        const double iso = 0.5 * p->A * ps * ps + 0.75 * p->B * ps * ps * ps * ps - p->K * ps * lap[s] - 0.5 * p->K * g2;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) sig[(size_t)(3 * a + b) * N + s] = p->K * gr[a] * gr[b] + (a == b ? iso : 0.0);
+    }
+    for (size_t s = 0; s < N; ++s) {
+        int x, y, z;
+        coords(g, s, &x, &y, &z);
+        for (int a = 0; a < 3; ++a) {
+            double div = 0.0;
+            if (a < d)
+                for (int b = 0; b < d; ++b) {
+                    int e[3] = {0, 0, 0};
+                    e[b] = 1;
+                    const double *sab = sig + (size_t)(3 * a + b) * N;
+                    div += 0.5 * (sab[site_at(g, x + e[0], y + e[1], z + e[2])] - sab[site_at(g, x - e[0], y - e[1], z - e[2])]);
+                }
+            F[(size_t)a * N + s] = -div;
+        }
+    }
+    free(lap);
+    free(sig);
+}
+
 /* Force density on the fluid from the order parameter (Sec. IV): F = -psi grad mu.
  * Reading of the sign: the paper prints +psi grad mu; only -psi grad mu makes
  * the advective work u.F cancel the advective change of the free energy, so
@@ -372,7 +419,8 @@ void ora_mu(const ora_params *p, const double *psi, double *mu)
  * Gradient (force_grad): 1 -- the symmetric nearest-neighbour central difference
  * of Sec. IV; 2 -- the finite-volume lattice gradient of Eq. (fvgrad),
  * (1/c_s^2) sum_i w_i c_i mu(r + c_i); 0 -- the one matched to the psi scheme
- * (1 for FD, 2 for FV).  Reading: the cancellation above holds on the lattice
+ * (1 for FD, 2 for FV); 3 -- no gradient of mu: the divergence of the stress
+ * (stress_force above).  Reading: the cancellation above holds on the lattice
  * only if the force uses the gradient whose negative adjoint is the divergence
  * that advects psi.  For the FD scheme (central-difference advection, Sec. V.A)
  * that is the central difference; for the FV scheme (advection through link
@@ -383,6 +431,10 @@ void ora_force(const ora_params *p, const double *psi, const double *mu, double 
 {
     box_t g = box_of(p);
     const int grad = p->force_grad == 0 ? (p->scheme == 1 ? 2 : 1) : p->force_grad;
+    if (grad == 3) {
+        stress_force(p, &g, psi, F);
+        return;
+    }
     if (grad == 2) {
         int32_t c[3 * 19];
         double w[19];

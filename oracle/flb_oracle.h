@@ -28,7 +28,8 @@ typedef struct {
     int32_t gnx, gny, gnz;  /* global lattice for counter ids (0: this box) */
     int32_t ox, oy, oz;     /* origin of this box inside the global lattice */
     int32_t force_grad;     /* gradient of mu in the force: 1 central difference, 2 FV lattice
-                               gradient, 0 the one matched to the psi scheme */
+                               gradient, 0 the one matched to the psi scheme; 3 the
+                               divergence of the order-parameter stress instead */
 } ora_params;
 
 int ora_threads(void);

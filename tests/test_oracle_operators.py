@@ -199,3 +199,36 @@ def test_dynamic_structure_factor_exact_decay(dim, q, scheme):
         expect = g ** (l * m) * np.mean(P[:nsamp - l], axis=0)
         assert np.allclose(S[l], expect, rtol=1e-10, atol=1e-14 * np.max(P[0]))
     assert np.allclose(S[0], np.mean(P, axis=0), rtol=1e-13)
+
+
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_stress_force_sums_to_zero(dim, q):
+    # force_grad 3: F = -div sigma (Sec. IV, Eq. muf) with a central-difference
+    # divergence telescopes to sum_r F = 0 for any psi, also for B != 0, where
+    # -psi grad mu leaves a net force (reading P)
+    shape = (1, 11, 9) if dim == 2 else (7, 6, 5)
+    p = O.Params(dim=dim, q=q, nx=shape[2], ny=shape[1], nz=shape[0], A=-0.06, B=0.3, K=0.04, force_grad=3)
+    rng = np.random.default_rng(11)
+    psi = rng.normal(size=p.n)
+    F = O.force(p, psi)
+    assert np.abs(F[:dim].sum(axis=1)).max() < 1e-13 * np.abs(F).sum()
+    assert dim == 3 or np.abs(F[dim:]).max() == 0.0
+    Fc = O.force(O.Params(**{**p.__dict__, "force_grad": 1}), psi)
+    assert np.abs(Fc[:dim].sum(axis=1)).max() > 1e-3 * np.abs(Fc).sum() / p.n
+
+
+def test_stress_force_second_order_consistency():
+    # The divergence of sigma equals psi grad mu in the continuum, so on a smooth
+    # field the two lattice forces differ by O(h^2): doubling the wavelength (and
+    # the box) divides their difference, relative to the force, by about 4.  A
+    # wrong coefficient in sigma leaves an O(1) difference instead.
+    errs = []
+    for n in (16, 32):
+        p = O.Params(dim=3, q=19, nx=n, ny=n, nz=n, A=-0.05, B=0.3, K=0.04, force_grad=3)
+        z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        k = 2 * np.pi / n
+        psi = (0.6 * np.sin(k * x + 0.3) + 0.4 * np.cos(k * y) * np.sin(k * z + 1.0)).ravel()
+        Fs = O.force(p, psi)
+        Fc = O.force(O.Params(**{**p.__dict__, "force_grad": 1}), psi)
+        errs.append(np.abs(Fs - Fc).max() / np.abs(Fc).max())
+    assert errs[0] < 0.2 and 3.0 < errs[0] / errs[1] < 5.0, errs
