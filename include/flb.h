@@ -63,6 +63,7 @@ extern "C" {
 #define FLB_FORCE_MATCHED 0     /* force gradient matched to the psi scheme */
 #define FLB_FORCE_CD 1          /* central difference of Sec. IV */
 #define FLB_FORCE_FV 2          /* FV lattice gradient of Eq. (fvgrad) */
+#define FLB_FORCE_STRESS 3      /* F = -div sigma, the order-parameter stress of Eq. (muf) */
 #define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
 #define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
 #define FLB_MODE_PERSISTENT 2  /* all replicas, n steps, one cooperative launch (FV, FP32 storage) */
@@ -101,6 +102,14 @@ extern "C" {
  *                 negative adjoint is the divergence advecting psi, so that the
  *                 work u.F equals the free energy advection removes (Sec. II.B).
  *                 FLB_FORCE_CD or FLB_FORCE_FV force one choice.
+ *                 FLB_FORCE_STRESS takes instead F = -div sigma with
+ *                 sigma_ab = K d_a psi d_b psi + delta_ab [A/2 psi^2 + 3B/4 psi^4
+ *                 - K psi lap_SO psi - K/2 |grad psi|^2] (Sec. IV, Eq. muf),
+ *                 central differences for the gradient and the divergence: the
+ *                 total momentum is then conserved exactly for B != 0 as well,
+ *                 F = -psi grad mu + O(h^2), but the force is not the adjoint
+ *                 of the psi advection (with FLB_FV, rough fields of amplitude
+ *                 ~0.5 can go non-finite).
  */
 typedef struct flb_params {
     int32_t dim, q;

@@ -26,7 +26,7 @@ FLB_FD, FLB_FV = 0, 1
 FLB_EULER, FLB_HEUN = 1, 2
 FLB_F32_DEV, FLB_F16_DEV = 0, 1
 FLB_COUPLE_FORCE, FLB_COUPLE_ADVECT = 1, 2
-FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV = 0, 1, 2
+FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV, FLB_FORCE_STRESS = 0, 1, 2, 3
 FLB_SQ_PSI, FLB_SQ_HEIGHT, FLB_SQ_DYNAMIC = 0, 1, 2
 FLB_MODE_PLAIN, FLB_MODE_BATCHED, FLB_MODE_PERSISTENT = 0, 1, 2
 FLB_TUNE_FORCE = 1

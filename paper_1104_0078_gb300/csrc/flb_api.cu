@@ -54,6 +54,7 @@ struct Rep {
     float *psi[2] = {nullptr, nullptr};
     int pcur = 0;
     float *psis = nullptr, *mu = nullptr, *mus = nullptr, *u = nullptr, *J = nullptr, *eta = nullptr, *E = nullptr;
+    float *sig = nullptr;  // stress-form force: sigma planes (3D xx, yy, zz, xy, xz, yz; 2D xx, yy, xy)
     double *sq = nullptr, *hsq = nullptr;
     int Kx = 0, Ky = 0, Kz = 0;
     int64_t sq_n = 0, h_n = 0;
@@ -98,7 +99,7 @@ bool valid(const flb_params &p)
     if (p.integrator != FLB_EULER && p.integrator != FLB_HEUN) return false;
     if (p.storage != FLB_F32_DEV && p.storage != FLB_F16_DEV) return false;
     if (p.coupling < 0 || p.coupling > 3) return false;
-    if (p.force_grad < FLB_FORCE_MATCHED || p.force_grad > FLB_FORCE_FV) return false;
+    if (p.force_grad < FLB_FORCE_MATCHED || p.force_grad > FLB_FORCE_STRESS) return false;
     if (p.sq_kmax < 0) return false;
     if (p.sq_lags < 0 || p.sq_lags > 4096 || p.reserved != 0) return false;
     if (p.nx > 4096 || p.ny > 4096 || (p.dim == 3 && p.nz > 4096)) return false;  // DFT twiddle tables
@@ -141,6 +142,7 @@ void carve_rep(Rep &r, Carver &cv)
         if (r.p.integrator == FLB_HEUN) r.mus = cv.take<float>(P);
         if (r.p.psi_scheme == FLB_FV) r.J = cv.take<float>((size_t)r.dim * P);
     }
+    if (r.p.force_grad == FLB_FORCE_STRESS) r.sig = cv.take<float>((size_t)(r.dim == 3 ? 6 : 3) * P);
     r.Kx = axis_K(g.nx, r.p.sq_kmax);
     r.Ky = axis_K(g.ny, r.p.sq_kmax);
     r.Kz = r.dim == 3 ? axis_K(g.nz, r.p.sq_kmax) : 1;
@@ -407,7 +409,10 @@ LBArgs lb_args(const Rep &r, float *psi_n)
     la.kT = (float)p.kT;
     std::memcpy(la.namp, r.namp, sizeof(la.namp));
     la.coupling = p.coupling;
-    la.fv_force = p.force_grad == FLB_FORCE_FV || (p.force_grad == FLB_FORCE_MATCHED && p.psi_scheme == FLB_FV);
+    la.force_kind = p.force_grad == FLB_FORCE_STRESS ? 2
+                    : (p.force_grad == FLB_FORCE_FV || (p.force_grad == FLB_FORCE_MATCHED && p.psi_scheme == FLB_FV)) ? 1
+                                                                                                                   : 0;
+    la.sig = r.sig;
     la.key = philox_key(p.seed);
     la.step = r.step;
     return la;
@@ -445,7 +450,12 @@ int step_rep3(flb_handle *h, Rep &r)
     float *psi_n = r.psi[r.pcur];
     const LBArgs la = lb_args(r, psi_n);
     cudaEvent_t e0 = mark(h);
-    if (p.coupling & FLB_COUPLE_FORCE) FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+    if (p.coupling & FLB_COUPLE_FORCE) {
+        if (p.force_grad == FLB_FORCE_STRESS)
+            FLB_TRY(launch_sigma3(r.g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
+        else
+            FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+    }
     cudaEvent_t e1 = mark(h);
     FLB_TRY(launch_lb3d(la, p.storage, st));
     cudaEvent_t e2 = mark(h);
@@ -473,6 +483,8 @@ int step_rep(flb_handle *h, Rep &r)
     const int64_t l0 = h->launches;
     cudaEvent_t e0 = mark(h);
     FLB_TRY(launch_mu(g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+    if ((p.coupling & FLB_COUPLE_FORCE) && p.force_grad == FLB_FORCE_STRESS)
+        FLB_TRY(launch_sigma2(g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
     cudaEvent_t e1 = mark(h);
 
     const LBArgs la = lb_args(r, psi_n);

@@ -1,8 +1,9 @@
-// flb_aux3d.cu -- the two D3Q19 step kernels around the collide-stream.
+// flb_aux3d.cu -- the D3Q19 step kernels around the collide-stream.
 //
 // mu3_kernel writes the chemical potential mu = A psi + B psi^3 - K lap_SO psi
 // (Sec. II.A; SO stencil of App. A) on the interior and one ghost layer, for the
-// force density of the collide-stream.  vel3_kernel runs after it: it gathers
+// force density of the collide-stream; with the stress-form force sigma3_kernel
+// writes the order-parameter stress (Eq. muf) there instead.  vel3_kernel runs after it: it gathers
 // the populations the next step pulls (the planes just written) and writes the
 // velocity (sum fbar c + F/2)/rho of the new fluid state, which advects psi
 // (Gauss-Seidel coupling: the psi step follows the fluid step).  Both have a
@@ -51,6 +52,17 @@ __device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict
     mu3_column<false>(g, psi, mu, A, B, K, x, y, zb, ze);
 }
 
+__global__ void __launch_bounds__(MU_BX *MU_BY) sigma3_kernel(const Geom g, const float *__restrict__ psi,
+                                                             float *__restrict__ sig, float A, float B, float K)
+{
+    const int x = blockIdx.x * MU_BX + (int)threadIdx.x - 1;
+    const int y = blockIdx.y * MU_BY + (int)threadIdx.y - 1;
+    const int zb = blockIdx.z * MU_ZC - 1;
+    const int ze = min(zb + MU_ZC, g.nz + 1);
+    if (x > g.nx || y > g.ny || zb >= ze) return;
+    sigma3_column<false>(g, psi, sig, A, B, K, x, y, zb, ze);
+}
+
 __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,
                                                           float *__restrict__ mu, float A, float B, float K)
 {
@@ -63,6 +75,14 @@ __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchList
     const BatchBlock b = L.mu[blockIdx.x];
     const BatchRep &r = L.reps[b.rep];
     const int par = (int)(*L.dstep & 1);
+    if (r.lb.force_kind == 2) {  // stress form: sigma instead of mu
+        const Geom &g = r.lb.g;
+        const int x = b.bx * MU_BX + (int)threadIdx.x - 1, y = b.by * MU_BY + (int)threadIdx.y - 1;
+        const int zb = b.bz * MU_ZC - 1, ze = min(zb + MU_ZC, g.nz + 1);
+        if (x <= g.nx && y <= g.ny && zb < ze)
+            sigma3_column<false>(g, r.psi[par], const_cast<float *>(r.lb.sig), r.A, r.B, r.K, x, y, zb, ze);
+        return;
+    }
     mu3_block(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
 }
 
@@ -80,6 +100,14 @@ cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, floa
     const dim3 block(MU_BX, MU_BY, 1);
     const dim3 grid((g.nx + 2 + MU_BX - 1) / MU_BX, (g.ny + 2 + MU_BY - 1) / MU_BY, (g.nz + 2 + MU_ZC - 1) / MU_ZC);
     mu3_kernel<<<grid, block, 0, st>>>(g, psi, mu, A, B, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma3(const Geom &g, const float *psi, float *sig, float A, float B, float K, cudaStream_t st)
+{
+    const dim3 block(MU_BX, MU_BY, 1);
+    const dim3 grid((g.nx + 2 + MU_BX - 1) / MU_BX, (g.ny + 2 + MU_BY - 1) / MU_BY, (g.nz + 2 + MU_ZC - 1) / MU_ZC);
+    sigma3_kernel<<<grid, block, 0, st>>>(g, psi, sig, A, B, K);
     return cudaGetLastError();
 }
 

@@ -178,7 +178,8 @@ struct LBArgs {
     float kT;
     float namp[16];            // sqrt((1 - gamma_k^2)/b_k) of the noisy modes, in noise order
     int coupling;
-    int fv_force;              // 1: force uses the FV gradient of mu, 0: central difference
+    int force_kind;            // 0: -psi grad_CD mu, 1: -psi grad_FV mu, 2: -div sigma (stress form)
+    const float *sig;          // stress form: padded sigma planes xx, yy, zz, xy, xz, yz (2D: xx, yy, xy)
     PhiloxKey key;
     int64_t step;
 };
@@ -280,6 +281,9 @@ cudaError_t launch_persist(const PersistArgs &a, cudaStream_t st);
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);
 // D3Q19 collide-stream that computes mu and the force itself from psi (flb_lb3d.cu)
 cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t s);
+// order-parameter stress sigma on the interior + 1 ghost layer (flb_aux3d.cu, flb_psi.cu)
+cudaError_t launch_sigma3(const Geom &g, const float *psi, float *sig, float A, float B, float K, cudaStream_t st);
+cudaError_t launch_sigma2(const Geom &g, const float *psi, float *sig, float A, float B, float K, cudaStream_t st);
 // velocity of the streamed state after a step, written to a.u (flb_aux3d.cu, flb_lb.cu)
 cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t s);
 // batched mu and velocity over the work lists (flb_aux3d.cu)

@@ -58,17 +58,24 @@ __device__ __forceinline__ void pull9(const T *fi, const Geom &g, int x, int y, 
     f[8] = ldpop(fi, 8 * N + g.sidx(xp, ym, 0));
 }
 
-// Force density F = -psi grad mu at (x, y): central difference, or for the FV
-// psi scheme the FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i) of Eq. (fvgrad)
-// = [4 (mu(+x) - mu(-x)) + diagonals] / 12 for D2Q9.
+// Force density at (x, y): F = -psi grad mu with the central difference, or for
+// the FV psi scheme the FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i) of
+// Eq. (fvgrad) = [4 (mu(+x) - mu(-x)) + diagonals] / 12 for D2Q9; or
+// F = -div sigma (stress form).
 __device__ __forceinline__ void force2(const LBArgs &a, int x, int y, float &Fx, float &Fy)
 {
     const Geom &g = a.g;
+    if (a.force_kind == 2) {  // F = -div sigma (stress form), sigma planes xx, yy, xy
+        const float *xx = a.sig, *yy = xx + g.pn, *xy = yy + g.pn;
+        Fx = -0.5f * ((xx[g.pidx(x + 1, y, 0)] - xx[g.pidx(x - 1, y, 0)]) + (xy[g.pidx(x, y + 1, 0)] - xy[g.pidx(x, y - 1, 0)]));
+        Fy = -0.5f * ((xy[g.pidx(x + 1, y, 0)] - xy[g.pidx(x - 1, y, 0)]) + (yy[g.pidx(x, y + 1, 0)] - yy[g.pidx(x, y - 1, 0)]));
+        return;
+    }
     const float ps = a.psi[g.pidx(x, y, 0)];
     const float *mu = a.mu;
     const float dx = mu[g.pidx(x + 1, y, 0)] - mu[g.pidx(x - 1, y, 0)];
     const float dy = mu[g.pidx(x, y + 1, 0)] - mu[g.pidx(x, y - 1, 0)];
-    if (a.fv_force) {
+    if (a.force_kind == 1) {
         const float pp = mu[g.pidx(x + 1, y + 1, 0)], pm = mu[g.pidx(x + 1, y - 1, 0)];
         const float mp = mu[g.pidx(x - 1, y + 1, 0)], mm = mu[g.pidx(x - 1, y - 1, 0)];
         Fx = -ps * (1.0f / 12.0f) * (4.f * dx + ((pp + pm) - (mp + mm)));

@@ -114,8 +114,12 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
             const Geom &g = r.lb.g;
             const int x = task.bx * 32 + (t & 31) - 1, y = task.by * PM_BY + (t >> 5) - 1;
             const int zb = task.bz * MU_ZC - 1, ze = min(zb + MU_ZC, g.nz + 1);
-            if (x <= g.nx && y <= g.ny)
-                mu3_column<true>(g, r.psi[ds & 1], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, x, y, zb, ze);
+            if (x <= g.nx && y <= g.ny) {
+                if (r.lb.force_kind == 2)
+                    sigma3_column<true>(g, r.psi[ds & 1], const_cast<float *>(r.lb.sig), r.A, r.B, r.K, x, y, zb, ze);
+                else
+                    mu3_column<true>(g, r.psi[ds & 1], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, x, y, zb, ze);
+            }
         } else if (task.phase == PH_LB || task.phase == PH_VEL) {
             lb_args_at(r, ds, sla);
             const Geom &g = sla.g;

@@ -65,6 +65,27 @@ __global__ void mu_kernel(const Geom g, const float *__restrict__ psi, float *__
     mu[g.pidx(x, y, z)] = A * p + B * p * p * p - K * lap_so(psi, g, x, y, z);
 }
 
+// Order-parameter stress (Sec. IV, Eq. muf) in 2D on the interior + 1 ghost
+// layer: planes xx, yy, xy of sigma_ab = K g_a g_b + delta_ab [A/2 psi^2
+// + 3B/4 psi^4 - K psi lap_SO psi - K/2 |g|^2], g the central difference.
+__global__ void sigma2_kernel(const Geom g, const float *__restrict__ psi, float *__restrict__ sig, float A, float B,
+                              float K)
+{
+    const int ex = g.nx + 2, ey = g.ny + 2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)ex * ey) return;
+    const int x = (int)(i % ex) - 1, y = (int)(i / ex) - 1;
+    const float p = psi[g.pidx(x, y, 0)];
+    const float gx = 0.5f * (psi[g.pidx(x + 1, y, 0)] - psi[g.pidx(x - 1, y, 0)]);
+    const float gy = 0.5f * (psi[g.pidx(x, y + 1, 0)] - psi[g.pidx(x, y - 1, 0)]);
+    const float p2 = p * p;
+    const float iso = 0.5f * A * p2 + 0.75f * B * p2 * p2 - K * p * lap_so(psi, g, x, y, 0) - 0.5f * K * (gx * gx + gy * gy);
+    const long long o = g.pidx(x, y, 0);
+    sig[o] = K * gx * gx + iso;
+    sig[o + g.pn] = K * gy * gy + iso;
+    sig[o + 2 * g.pn] = K * gx * gy;
+}
+
 __global__ void noise_kernel(const NoiseArgs a)
 {
     const Geom &g = a.g;
@@ -221,6 +242,13 @@ cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float
 {
     const long long ext = (long long)(g.nx + 4) * (g.ny + 4) * (g.dim == 3 ? g.nz + 4 : 1);
     mu_kernel<<<blocks_for(ext, 256), 256, 0, s>>>(g, psi, mu, A, B, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma2(const Geom &g, const float *psi, float *sig, float A, float B, float K, cudaStream_t s)
+{
+    const long long ext = (long long)(g.nx + 2) * (g.ny + 2);
+    sigma2_kernel<<<blocks_for(ext, 256), 256, 0, s>>>(g, psi, sig, A, B, K);
     return cudaGetLastError();
 }
 

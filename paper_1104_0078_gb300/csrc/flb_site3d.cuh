@@ -76,11 +76,25 @@ __device__ __forceinline__ void pull19(const T *fi, const Geom &g, int x, int y,
     f[18] = ld3<COH>(fi + 18ll * N, x + sYp + sZm);
 }
 
-// Force density F = -psi grad mu of Sec. IV at an interior site.
+// Force density of Sec. IV at an interior site: F = -psi grad mu with the
+// central difference or the FV gradient of mu, or F = -div sigma (stress form).
 template <bool COH = false>
 __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, float &Fx, float &Fy, float &Fz)
 {
     const Geom &g = a.g;
+    if (a.force_kind == 2) {
+        // F = -div sigma by central differences (stress form); sigma valid on the interior + 1
+        const int pi = g.pidx32(x, y, z);
+        const int sy = g.px, sz = g.px * g.py, pn = (int)g.pn;
+        const float *xx = a.sig, *yy = xx + pn, *zz = yy + pn, *xy = zz + pn, *xz = xy + pn, *yz = xz + pn;
+        Fx = -0.5f * ((ldf<COH>(xx + pi + 1) - ldf<COH>(xx + pi - 1)) + (ldf<COH>(xy + pi + sy) - ldf<COH>(xy + pi - sy)) +
+                      (ldf<COH>(xz + pi + sz) - ldf<COH>(xz + pi - sz)));
+        Fy = -0.5f * ((ldf<COH>(xy + pi + 1) - ldf<COH>(xy + pi - 1)) + (ldf<COH>(yy + pi + sy) - ldf<COH>(yy + pi - sy)) +
+                      (ldf<COH>(yz + pi + sz) - ldf<COH>(yz + pi - sz)));
+        Fz = -0.5f * ((ldf<COH>(xz + pi + 1) - ldf<COH>(xz + pi - 1)) + (ldf<COH>(yz + pi + sy) - ldf<COH>(yz + pi - sy)) +
+                      (ldf<COH>(zz + pi + sz) - ldf<COH>(zz + pi - sz)));
+        return;
+    }
     // F = -psi grad mu, mu read from its field (valid on the interior + 1,
     // edges and corners included)
     const int pi = g.pidx32(x, y, z);
@@ -90,7 +104,7 @@ __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, flo
     const float dx = ldf<COH>(mu + pi + 1) - ldf<COH>(mu + pi - 1);
     const float dy = ldf<COH>(mu + pi + sy) - ldf<COH>(mu + pi - sy);
     const float dz = ldf<COH>(mu + pi + sz) - ldf<COH>(mu + pi - sz);
-    if (a.fv_force) {
+    if (a.force_kind == 1) {
         // FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i), Eq. (fvgrad): with
         // w = 1/18 (faces), 1/36 (edges) it is [2 (face difference) + sum of
         // the 8 edge neighbours signed by c_a] / 12
@@ -331,6 +345,46 @@ __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restric
         }
         a0 = a1; b0 = b1; d0 = d1;
         a1 = a2; b1 = b2; d1 = d2;
+    }
+}
+
+// The column (x, y), planes zb .. ze-1, of the order-parameter stress (Sec. IV,
+// Eq. muf): sigma_ab = K g_a g_b + delta_ab [A/2 psi^2 + 3B/4 psi^4
+// - K psi lap_SO psi - K/2 |g|^2], g the central-difference gradient of psi.
+// Per plane a thread keeps the centre, the faces and the diagonals of psi (the
+// SO stencil, as in mu3_column) and the in-plane face differences.
+template <bool COH = false>
+__device__ __forceinline__ void sigma3_column(const Geom &g, const float *__restrict__ psi, float *__restrict__ sig,
+                                              float A, float B, float K, int x, int y, int zb, int ze)
+{
+    const int Y = g.px, Z = g.px * g.py, pn = (int)g.pn;
+    int c = g.pidx32(x, y, zb - 1);
+    float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f, gx1 = 0.f, gy1 = 0.f;
+    for (int p = zb - 1; p <= ze; ++p, c += Z) {
+        const float a2 = ldf<COH>(psi + c);
+        const float xm = ldf<COH>(psi + c - 1), xp = ldf<COH>(psi + c + 1);
+        const float ym = ldf<COH>(psi + c - Y), yp = ldf<COH>(psi + c + Y);
+        const float b2 = (xm + xp) + (ym + yp);
+        const float d2 = (ldf<COH>(psi + c - 1 - Y) + ldf<COH>(psi + c + 1 - Y)) + (ldf<COH>(psi + c - 1 + Y) + ldf<COH>(psi + c + 1 + Y));
+        if (p - 1 >= zb) {  // plane p-1: centre a1, gradient (gx1, gy1, gz)
+            const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
+            const float lap = (6.f * n1 + 3.f * n2 + n3 - 80.f * a1) * (1.0f / 22.0f);
+            const float gz = 0.5f * (a2 - a0);
+            const float ps2 = a1 * a1;
+            const float iso = 0.5f * A * ps2 + 0.75f * B * ps2 * ps2 - K * a1 * lap -
+                              0.5f * K * (gx1 * gx1 + gy1 * gy1 + gz * gz);
+            const int o = c - Z;
+            sig[o] = K * gx1 * gx1 + iso;
+            sig[o + pn] = K * gy1 * gy1 + iso;
+            sig[o + 2 * pn] = K * gz * gz + iso;
+            sig[o + 3 * pn] = K * gx1 * gy1;
+            sig[o + 4 * pn] = K * gx1 * gz;
+            sig[o + 5 * pn] = K * gy1 * gz;
+        }
+        a0 = a1; b0 = b1; d0 = d1;
+        a1 = a2; b1 = b2; d1 = d2;
+        gx1 = 0.5f * (xp - xm);
+        gy1 = 0.5f * (yp - ym);
     }
 }
 

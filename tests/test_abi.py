@@ -83,7 +83,7 @@ def test_defaults_and_workspace_sizing(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 3), ("q", 15), ("tau", 0.0), ("gamma_ghost", 1.0), ("kT", -1.0),
                                          ("psi_scheme", 2), ("integrator", 3), ("storage", 2), ("coupling", 4),
-                                         ("M", -0.1), ("sq_kmax", -1), ("force_grad", 3), ("force_grad", -1),
+                                         ("M", -0.1), ("sq_kmax", -1), ("force_grad", 4), ("force_grad", -1),
                                          ("sq_lags", -1), ("sq_lags", 5000), ("reserved", 1)])
 def test_invalid_parameters_rejected(lib, field, value):
     p = F.flb_params_default(**{field: value})

@@ -55,6 +55,15 @@ def test_batched_equals_plain(integrator):
         assert np.array_equal(pa, s.get_psi_u(r)[0])
 
 
+def test_batched_stress_force_equals_plain():
+    ps = _replicas(A=-0.05, B=0.3, force_grad=3)
+    plain, _, _ = _run(F.FLB_MODE_PLAIN, ps, 6)
+    batched, _, _ = _run(F.FLB_MODE_BATCHED, ps, 6)
+    for (fa, pa, _), (fb, pb, _) in zip(plain, batched):
+        assert np.array_equal(fa, fb)
+        assert np.array_equal(pa, pb)
+
+
 def test_batched_sampling_and_launch_count():
     ps = _replicas(kT=2e-4)
     _, sq_plain, sp = _run(F.FLB_MODE_PLAIN, ps, 12, sample=4)

@@ -61,7 +61,7 @@ def test_coupled_step_matches_oracle(dim, q, shape, scheme, integ):
 
 @pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
 @pytest.mark.parametrize("scheme", [0, 1])
-@pytest.mark.parametrize("force_grad", [1, 2])
+@pytest.mark.parametrize("force_grad", [1, 2, 3])
 def test_force_gradient_choices_match_oracle(dim, q, scheme, force_grad):
     # both lattice gradients in the force with both psi schemes (the matched pair
     # is the default of the cases above); a deep quench so the force is large
@@ -124,6 +124,26 @@ def test_conserved_totals_drift():
     assert abs(t1[0] - t0[0]) / (N * 1.0) < 1e-6
     assert np.abs(t1[1:4] - t0[1:4]).max() / jabs < 1e-6
     assert abs(t1[4] - t0[4]) / np.abs(psi).sum() < 1e-6
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_stress_force_conserves_momentum(scheme):
+    # force_grad 3 (F = -div sigma): with B != 0 and noise the total momentum,
+    # reduced in FP64 on the device, stays at zero to FP32 round-off over 300
+    # steps (the stored populations' rounding walks it to ~1e-6), while
+    # -psi grad mu drives a net momentum thousands of times larger
+    d = dict(dim=3, q=19, nx=24, ny=20, nz=18, tau=0.8, kT=1e-4, A=-0.05, B=0.3, K=0.04, M=0.1, scheme=scheme,
+             integrator=2, coupling=3, seed=9)
+    N = 24 * 20 * 18
+    out = {}
+    for fg in (3, 0):
+        s = F.Solver(flb_params(d, force_grad=fg))
+        s.set_fields(psi=I.random_field(N, 0.05, 21))
+        s.step(300)
+        t1, _, rc = s.moments()
+        assert rc == F.FLB_OK
+        out[fg] = np.abs(t1[1:4]).max()
+    assert out[3] < 1e-2 * out[0] and out[3] < 1e-9 * N
 
 
 def test_structure_factor_matches_oracle():

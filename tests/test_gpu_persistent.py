@@ -70,6 +70,7 @@ def test_persistent_mixed_zchunks_and_coupling():
     ps = _replicas()
     ps[1].coupling = F.FLB_COUPLE_ADVECT     # a replica without force: no mu tasks
     ps[2].gamma_ghost = 0.3                  # ghost relaxation path
+    ps[3].force_grad = F.FLB_FORCE_STRESS    # stress-form force: sigma instead of mu
     chunks = [4, 7, 64, 16, 3]
     plain = _solver(F.FLB_MODE_PLAIN, ps)
     pers = _solver(F.FLB_MODE_PERSISTENT, ps, chunks=chunks)
