@@ -723,7 +723,8 @@ static void psi_rhs(const ora_params *p, const box_t *g, const double *psi, cons
 
 /* One step of psi with u frozen.  Time integration (Sec. V, ref. wilkie2004:
  * Runge-Kutta with the noise held constant over the step).  Reading: the order
- * is not given; Euler (integrator 1) and Heun/RK2 (integrator 2) are offered. */
+ * is not given; Euler (integrator 1), Heun/RK2 (integrator 2) and the classical
+ * RK4 (integrator 4) are offered. */
 static void psi_step(const ora_params *p, const box_t *g, double *psi, const double *u, int64_t step)
 {
     const size_t N = g->n;
@@ -741,6 +742,32 @@ static void psi_step(const ora_params *p, const box_t *g, double *psi, const dou
     psi_rhs(p, g, psi, u, noise, R0);
     if (p->integrator == 1) {
         for (size_t s = 0; s < N; ++s) psi[s] += R0[s];
+    } else if (p->integrator == 4) {
+        /* classical fourth-order Runge-Kutta with the noise held fixed over the
+         * step (Wilkie): k1 = R(psi), k2 = R(psi + k1/2), k3 = R(psi + k2/2),
+         * k4 = R(psi + k3), psi += (k1 + 2 k2 + 2 k3 + k4)/6 */
+        double *ps = (double *)malloc(sizeof(double) * N);
+        double *K = (double *)malloc(sizeof(double) * N);
+        double *sum = (double *)malloc(sizeof(double) * N);
+        for (size_t s = 0; s < N; ++s) {
+            sum[s] = R0[s];
+            ps[s] = psi[s] + 0.5 * R0[s];
+        }
+        psi_rhs(p, g, ps, u, noise, K);
+        for (size_t s = 0; s < N; ++s) {
+            sum[s] += 2.0 * K[s];
+            ps[s] = psi[s] + 0.5 * K[s];
+        }
+        psi_rhs(p, g, ps, u, noise, K);
+        for (size_t s = 0; s < N; ++s) {
+            sum[s] += 2.0 * K[s];
+            ps[s] = psi[s] + K[s];
+        }
+        psi_rhs(p, g, ps, u, noise, K);
+        for (size_t s = 0; s < N; ++s) psi[s] += (sum[s] + K[s]) / 6.0;
+        free(ps);
+        free(K);
+        free(sum);
     } else {
         double *pst = (double *)malloc(sizeof(double) * N);
         double *R1 = (double *)malloc(sizeof(double) * N);
@@ -768,7 +795,9 @@ int ora_step(const ora_params *p, double *f, double *psi, double *u, int64_t ste
 {
     if (!((p->dim == 3 && p->q == 19) || (p->dim == 2 && p->q == 9))) return -1;
     if (p->nx <= 0 || p->ny <= 0 || (p->dim == 3 && p->nz <= 0)) return -1;
-    if (!(p->tau > 0.0) || p->integrator < 1 || p->integrator > 2 || p->scheme < 0 || p->scheme > 1) return -1;
+    if (!(p->tau > 0.0) || !(p->integrator == 1 || p->integrator == 2 || p->integrator == 4) || p->scheme < 0 ||
+        p->scheme > 1)
+        return -1;
     box_t g = box_of(p);
     const size_t N = g.n;
     double *mu = (double *)malloc(sizeof(double) * N);

@@ -83,18 +83,32 @@ def lam(q, p, L_mob):
 
 
 def amplification(z, integrator):
-    """Exact one-step amplification of dpsi/dt = z psi: Euler 1 + z, Heun 1 + z + z^2/2."""
-    return 1.0 + z if integrator == 1 else 1.0 + z + 0.5 * z * z
+    """Exact one-step amplification of dpsi/dt = z psi: Euler 1 + z, Heun 1 + z + z^2/2,
+    RK4 1 + z + z^2/2 + z^3/6 + z^4/24."""
+    if integrator == 1:
+        return 1.0 + z
+    if integrator == 4:
+        return 1.0 + z + z * z / 2.0 + z ** 3 / 6.0 + z ** 4 / 24.0
+    return 1.0 + z + 0.5 * z * z
 
 
 def discrete_variance_factor(lmb, integrator):
-    """Stationary variance of psi_{n+1} = g psi_n + h eta_n divided by the
-    continuous-time value, with the noise held fixed over the step:
-    Euler 1/(1 - lambda/2); Heun (2 - lambda)/(2 - lambda + lambda^2/2)."""
+    """Stationary variance of psi_{n+1} = R psi_n + S eta_n divided by the
+    continuous-time value, with the noise held fixed over the step (for
+    dpsi/dt = -lambda psi + noise, R the amplification and S = (R - 1)/z the
+    noise gain at z = -lambda): 2 lambda S^2 / (1 - R^2).  This is Euler
+    1/(1 - lambda/2) and Heun (2 - lambda)/(2 - lambda + lambda^2/2)."""
     lmb = np.asarray(lmb, dtype=np.float64)
     if integrator == 1:
         return 1.0 / (1.0 - 0.5 * lmb)
-    return (2.0 - lmb) / (2.0 - lmb + 0.5 * lmb * lmb)
+    if integrator == 2:
+        return (2.0 - lmb) / (2.0 - lmb + 0.5 * lmb * lmb)
+    z = -lmb
+    R = amplification(z, integrator)
+    S = 1.0 + z / 2.0 + z * z / 6.0 + z ** 3 / 24.0
+    den = 1.0 - R * R
+    small = np.abs(lmb) < 1e-12          # a mode that does not decay: the limit lambda -> 0 is 1
+    return np.where(small, 1.0, 2.0 * lmb * S * S / np.where(small, 1.0, den))
 
 
 def static_structure_factor(q, p, L_mob, steps=None):

@@ -239,10 +239,10 @@ def test_lyapunov_noise_free_coupled(scheme):
 # ----------------------------------------------------------------- psi half
 @pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
 @pytest.mark.parametrize("scheme", [0, 1])
-@pytest.mark.parametrize("integrator", [1, 2])
+@pytest.mark.parametrize("integrator", [1, 2, 4])
 def test_single_mode_exact_amplification(dim, q, scheme, integrator):
     # B = 0, no noise, u uniform: psi = Re[eps e^{iq.r}] is multiplied each step by
-    # 1 + z (Euler) or 1 + z + z^2/2 (Heun) with
+    # 1 + z (Euler), 1 + z + z^2/2 (Heun) or 1 + z + z^2/2 + z^3/6 + z^4/24 (RK4) with
     # z = M L_mob(q) (A - K L_SO(q)) - i theta(q);  theta = sum_a u_a sin q_a (FD,
     # central-difference advection) or u . G(q) (FV, Eq. fvft)
     p = O.Params(dim=dim, q=q, nx=8, ny=6, nz=4, kT=0.0, A=0.07, B=0.0, K=0.05, M=0.3, scheme=scheme,
@@ -297,7 +297,7 @@ def _shell_ratio(S, theory, mask):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("scheme,integrator", [(0, 1), (0, 2), (1, 2)])
+@pytest.mark.parametrize("scheme,integrator", [(0, 1), (0, 2), (1, 2), (0, 4), (1, 4)])
 def test_static_structure_factor_2d(scheme, integrator):
     # diffusion alone (no hydrodynamics): <|psi~(q)|^2> = kT/(A - K L_SO(q)) times the
     # discrete-time factor (Eq. test2 with the lattice Laplacian); with K = 0 this is

@@ -232,3 +232,17 @@ def test_stress_force_second_order_consistency():
         Fc = O.force(O.Params(**{**p.__dict__, "force_grad": 1}), psi)
         errs.append(np.abs(Fs - Fc).max() / np.abs(Fc).max())
     assert errs[0] < 0.2 and 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_discrete_variance_factor_general_form():
+    # The general stationary factor 2 lambda S^2 / (1 - R^2) (R the amplification,
+    # S = (R - 1)/z the noise gain) reduces to the hand-derived Euler and Heun forms
+    lmb = np.linspace(0.01, 1.2, 25)
+    z = -lmb
+    for integ, S in ((1, np.ones_like(z)), (2, 1 + z / 2)):
+        R = T.amplification(z, integ)
+        assert np.allclose(2 * lmb * S ** 2 / (1 - R ** 2), T.discrete_variance_factor(lmb, integ), rtol=1e-13)
+    R4 = T.amplification(z, 4)
+    assert np.allclose((R4 - 1) / z, 1 + z / 2 + z ** 2 / 6 + z ** 3 / 24, rtol=1e-13)
+    f4 = T.discrete_variance_factor(lmb, 4)
+    assert np.all(np.abs(f4 - 1) < np.abs(T.discrete_variance_factor(lmb, 2) - 1) + 1e-15)
