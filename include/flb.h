@@ -53,6 +53,7 @@ extern "C" {
 #define FLB_FV 1               /* finite-volume psi scheme, Sec. V.B */
 #define FLB_EULER 1            /* one-stage integrator */
 #define FLB_HEUN 2             /* two-stage (RK2) integrator, noise held fixed */
+#define FLB_RK4 4              /* classical fourth-order Runge-Kutta, noise held fixed */
 #define FLB_F32_DEV 0          /* populations stored as FP32 deviations fbar_i - w_i rho0 */
 #define FLB_F16_DEV 1          /* populations stored as FP16 deviations */
 #define FLB_COUPLE_FORCE 1     /* psi exerts -psi grad mu on the fluid */
@@ -86,7 +87,9 @@ extern "C" {
  *   A, B, K, M  : free energy f = A/2 psi^2 + B/4 psi^4 + K/2 |grad psi|^2
  *                 (Eqs. Feng, feng) and mobility M >= 0.
  *   psi_scheme  : FLB_FD or FLB_FV.
- *   integrator  : FLB_EULER or FLB_HEUN.
+ *   integrator  : FLB_EULER, FLB_HEUN or FLB_RK4 (the noise is drawn once per
+ *                 step and held fixed in every stage, Sec. V).  FLB_RK4 runs in
+ *                 FLB_MODE_PLAIN only.
  *   storage     : FLB_F32_DEV or FLB_F16_DEV.
  *   coupling    : bit mask of FLB_COUPLE_FORCE | FLB_COUPLE_ADVECT (3 = model H;
  *                 0 = "diffusion alone" of Sec. VI.A).

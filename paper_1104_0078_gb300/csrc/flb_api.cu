@@ -55,6 +55,7 @@ struct Rep {
     int pcur = 0;
     float *psis = nullptr, *mu = nullptr, *mus = nullptr, *u = nullptr, *J = nullptr, *eta = nullptr, *E = nullptr;
     float *sig = nullptr;  // stress-form force: sigma planes (3D xx, yy, zz, xy, xz, yz; 2D xx, yy, xy)
+    float *Dn = nullptr;   // RK4 (3D): the step's noise increment per site
     double *sq = nullptr, *hsq = nullptr;
     int Kx = 0, Ky = 0, Kz = 0;
     int64_t sq_n = 0, h_n = 0;
@@ -96,7 +97,7 @@ bool valid(const flb_params &p)
     if (!(p.kT >= 0) || !(p.M >= 0) || !std::isfinite(p.kT) || !std::isfinite(p.M)) return false;
     if (!std::isfinite(p.A) || !std::isfinite(p.B) || !std::isfinite(p.K)) return false;
     if (p.psi_scheme != FLB_FD && p.psi_scheme != FLB_FV) return false;
-    if (p.integrator != FLB_EULER && p.integrator != FLB_HEUN) return false;
+    if (p.integrator != FLB_EULER && p.integrator != FLB_HEUN && p.integrator != FLB_RK4) return false;
     if (p.storage != FLB_F32_DEV && p.storage != FLB_F16_DEV) return false;
     if (p.coupling < 0 || p.coupling > 3) return false;
     if (p.force_grad < FLB_FORCE_MATCHED || p.force_grad > FLB_FORCE_STRESS) return false;
@@ -133,13 +134,14 @@ void carve_rep(Rep &r, Carver &cv)
     r.psi[1] = cv.take<float>(P);
     r.mu = cv.take<float>(P);
     r.u = cv.take<float>((size_t)r.dim * P);
-    if (r.p.integrator == FLB_HEUN) {
+    if (r.p.integrator == FLB_HEUN || r.p.integrator == FLB_RK4) {
         r.psis = cv.take<float>(P);
         r.E = cv.take<float>(N);
     }
+    if (r.p.integrator == FLB_RK4 && r.dim == 3) r.Dn = cv.take<float>(N);
     if (r.dim == 2) {  // the 2D path keeps mu*, the noise increment and the FV flux in HBM
         r.eta = cv.take<float>(N);
-        if (r.p.integrator == FLB_HEUN) r.mus = cv.take<float>(P);
+        if (r.p.integrator != FLB_EULER) r.mus = cv.take<float>(P);
         if (r.p.psi_scheme == FLB_FV) r.J = cv.take<float>((size_t)r.dim * P);
     }
     if (r.p.force_grad == FLB_FORCE_STRESS) r.sig = cv.take<float>((size_t)(r.dim == 3 ? 6 : 3) * P);
@@ -431,12 +433,23 @@ int launch_psi_stages(flb_handle *h, Rep &r)
     const bool heun = p.integrator == FLB_HEUN;
     const int advect = (p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
     const PhiloxKey key = philox_key(p.seed);
+    if (p.integrator == FLB_RK4) {
+        // stage inputs and outputs alternate between psi* and the spare psi buffer
+        const float *in[4] = {psi_n, r.psis, psi_np1, r.psis};
+        float *out[4] = {r.psis, psi_np1, r.psis, psi_np1};
+        for (int s = 0; s < 4; ++s)
+            FLB_TRY(launch_psi3(r.g, p.psi_scheme, s == 0 ? 1 : 2, s == 0 && noisy, in[s], r.u, out[s], r.E,
+                                (float)p.A, (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, 0, key, r.step,
+                                r.zc, s + 1, psi_n, r.Dn, h->status, st));
+        return FLB_OK;
+    }
     FLB_TRY(launch_psi3(r.g, p.psi_scheme, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
-                        (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, r.zc,
-                        h->status, st));
+                        (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, r.zc, 0,
+                        nullptr, nullptr, h->status, st));
     if (heun)
         FLB_TRY(launch_psi3(r.g, p.psi_scheme, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
-                            (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, r.zc, h->status, st));
+                            (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, r.zc, 0, nullptr, nullptr,
+                            h->status, st));
     return FLB_OK;
 }
 
@@ -514,8 +527,9 @@ int step_rep(flb_handle *h, Rep &r)
     pa.J = r.J;
     pa.eta = noisy ? r.eta : nullptr;
     pa.psi0 = nullptr;
-    pa.out = p.integrator == FLB_HEUN ? r.psis : psi_np1;
+    pa.out = p.integrator == FLB_EULER ? psi_np1 : r.psis;
     pa.acc = r.E;
+    pa.base = psi_n;
     pa.A = (float)p.A;
     pa.B = (float)p.B;
     pa.K = (float)p.K;
@@ -525,6 +539,20 @@ int step_rep(flb_handle *h, Rep &r)
     pa.stage = 1;
     pa.integrator = p.integrator;
     FLB_TRY(launch_psi_update(pa, r.q, st));
+    if (p.integrator == FLB_RK4) {  // stages 2-4 alternate between psi* and the spare psi buffer
+        float *in[3] = {r.psis, psi_np1, r.psis};
+        float *out[3] = {psi_np1, r.psis, psi_np1};
+        for (int s = 0; s < 3; ++s) {
+            FLB_TRY(launch_mu(g, in[s], r.mus, (float)p.A, (float)p.B, (float)p.K, st));
+            if (p.psi_scheme == FLB_FV)
+                FLB_TRY(launch_flux(g, r.q, in[s], r.mus, r.u, r.J, (float)p.M, p.coupling, st));
+            pa.psi = in[s];
+            pa.mu = r.mus;
+            pa.out = out[s];
+            pa.stage = s + 2;
+            FLB_TRY(launch_psi_update(pa, r.q, st));
+        }
+    }
     if (p.integrator == FLB_HEUN) {
         FLB_TRY(launch_mu(g, r.psis, r.mus, (float)p.A, (float)p.B, (float)p.K, st));
         if (p.psi_scheme == FLB_FV)
@@ -631,7 +659,7 @@ int take_status(flb_handle *h)
 bool batch_supported(const flb_handle *h)
 {
     for (const Rep &r : h->reps)
-        if (r.dim != 3 || r.p.psi_scheme != FLB_FV) return false;
+        if (r.dim != 3 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4) return false;
     return !h->reps.empty();
 }
 

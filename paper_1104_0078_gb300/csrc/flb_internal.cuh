@@ -193,11 +193,12 @@ struct PsiArgs {
     const float *eta;      // noise increment per site [N]
     const float *psi0;     // stage 2: Heun accumulator E [N]
     float *out;            // padded psi output (images to the full frame)
-    float *acc;            // stage 1 of Heun: E = psi + D/2 + eta [N]
+    float *acc;            // stage 1 of Heun: E = psi + D/2 + eta [N]; RK4: the running sum
+    const float *base;     // RK4: padded psi^n
     float A, B, K, M;
     int coupling;
     int scheme;
-    int stage;             // 1 or 2
+    int stage;             // 1 or 2 (RK4: 1 to 4)
     int integrator;
 };
 
@@ -293,7 +294,8 @@ cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
 // one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu)
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
-                        const PhiloxKey &key, int64_t step, int zc, int *status, cudaStream_t st);
+                        const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
+                        int *status, cudaStream_t st);
 // mu on the interior and one ghost layer of a 3D box (flb_lb3d.cu)
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,

@@ -226,7 +226,18 @@ __global__ void psi_update_kernel(const PsiArgs a)
     }
     const float eta = a.eta ? a.eta[site] : 0.f;
     float out;
-    if (a.stage == 1) {
+    if (a.integrator == FLB_RK4) {  // k_s = D_s + eta with eta fixed over the step
+        if (a.stage == 1) {
+            const float p = a.psi[pi];
+            out = p + 0.5f * (D + eta);
+            a.acc[site] = p + eta + D * (1.f / 6.f);
+        } else if (a.stage == 4) {
+            out = a.acc[site] + D * (1.f / 6.f);
+        } else {
+            out = a.base[pi] + (a.stage == 2 ? 0.5f : 1.f) * (D + eta);
+            a.acc[site] += D * (1.f / 3.f);
+        }
+    } else if (a.stage == 1) {
         const float p = a.psi[pi];
         out = p + D + eta;
         if (a.integrator == FLB_HEUN) a.acc[site] = p + 0.5f * D + eta;

@@ -186,16 +186,9 @@ __global__ void __launch_bounds__(PS_NT) psi3_fd_kernel(const Psi3Args a)
                 D -= 0.5f * adv;
             }
             const int si = x + g.nx * (y + g.ny * z);
-            float out;
-            if (STAGE == 1) {
-                const float eta = NOISE ? accm : 0.f;
-                const float pv = sps[ring4(z) * H3N + (tx + 3) + H3X * (ty + 3)];
-                out = pv + D + eta;
-                if (a.heun) a.E[si] = pv + 0.5f * D + eta;
-            } else {
-                out = a.E[si] + 0.5f * D;
-            }
-            store_padded(a.out, g, x, y, z, out, 3);
+            const float eta = (STAGE == 1 && NOISE) ? accm : 0.f;
+            const float pv = STAGE == 1 ? sps[ring4(z) * H3N + (tx + 3) + H3X * (ty + 3)] : 0.f;
+            store_padded(a.out, g, x, y, z, rk_stage_out<STAGE, false>(a, x, y, z, si, pv, D, eta), 3);
         }
         accm = acc0;
         acc0 = accp;
@@ -333,10 +326,14 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
 
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
-                        const PhiloxKey &key, int64_t step, int zc, int *status, cudaStream_t st)
+                        const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
+                        int *status, cudaStream_t st)
 {
     if (zc < PS_ZC_MIN) return cudaErrorInvalidValue;
     Psi3Args a;
+    a.rk4 = rk4;
+    a.base = base;
+    a.Dn = Dn;
     a.g = g;
     a.psi = psi;
     a.u = u;
@@ -353,13 +350,13 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
     a.key = key;
     a.step = step;
     const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + zc - 1) / zc);
-    const size_t base = sizeof(float) * (4 * H3N + 3 * H2N);
+    const size_t smem = sizeof(float) * (4 * H3N + 3 * H2N);
     if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, status, st);
     if (stage == 1) {
-        if (noise) return launch_dyn(psi3_fd_kernel<1, true>, grid, base + sizeof(float) * 13 * H1N, st, a);
-        return launch_dyn(psi3_fd_kernel<1, false>, grid, base, st, a);
+        if (noise) return launch_dyn(psi3_fd_kernel<1, true>, grid, smem + sizeof(float) * 13 * H1N, st, a);
+        return launch_dyn(psi3_fd_kernel<1, false>, grid, smem, st, a);
     }
-    return launch_dyn(psi3_fd_kernel<2, false>, grid, base, st, a);
+    return launch_dyn(psi3_fd_kernel<2, false>, grid, smem, st, a);
 }
 
 }  // namespace flb

@@ -20,13 +20,49 @@ struct Psi3Args {
     const float *psi;  // padded stage input
     const float *u;    // padded velocity (images to radius 1)
     float *out;        // padded stage output (images to radius 3)
-    float *E;          // [N] Heun accumulator: written by stage 1, read by stage 2
+    float *E;          // [N] accumulator: Heun E = psi + D/2 + noise; RK4 psi + noise + sum of weighted D
     float A, B, K, M, kT;
     int advect, heun;
     int zc;            // planes per block (the z chunk)
+    int rk4;           // RK4: 0 off, else the stage 1..4
+    const float *base; // RK4: padded psi^n (stages 2, 3)
+    float *Dn;         // RK4: [N] noise increment, written in stage 1, read in stages 2, 3
     PhiloxKey key;
     int64_t step;
 };
+
+// Output of a Runge-Kutta stage at interior site (x, y, z), site index si: pv the
+// stage input there (stage 1), D the deterministic increment, eta the noise
+// increment (generated in stage 1; Sec. V holds it fixed over the step).
+//   Euler / Heun (Sec. V): stage 1 psi + D + eta (Heun also E = psi + D/2 + eta),
+//     stage 2 E + D/2.
+//   RK4: k_s = D_s + eta; stage 1 writes psi + k1/2 and E = psi + eta + D1/6 and
+//     keeps eta; stages 2, 3 write psi^n + k2/2, psi^n + k3 and add D_s/3 to E;
+//     stage 4 writes E + D4/6 = psi^n + (k1 + 2 k2 + 2 k3 + k4)/6.
+template <int STAGE, bool COH>
+__device__ __forceinline__ float rk_stage_out(const Psi3Args &a, int x, int y, int z, int si, float pv, float D,
+                                              float eta)
+{
+    if (a.rk4) {
+        constexpr float sixth = 1.f / 6.f, third = 1.f / 3.f;
+        if (a.rk4 == 1) {
+            a.E[si] = pv + eta + sixth * D;
+            a.Dn[si] = eta;
+            return pv + 0.5f * (D + eta);
+        }
+        const float e = COH ? __ldcg(a.E + si) : a.E[si];
+        if (a.rk4 == 4) return e + sixth * D;
+        const float n = COH ? __ldcg(a.Dn + si) : a.Dn[si];
+        const float b = COH ? __ldcg(a.base + a.g.pidx32(x, y, z)) : a.base[a.g.pidx32(x, y, z)];
+        a.E[si] = e + third * D;
+        return a.rk4 == 2 ? b + 0.5f * (D + n) : b + D + n;
+    }
+    if (STAGE == 1) {
+        if (a.heun) a.E[si] = pv + 0.5f * D + eta;
+        return pv + D + eta;
+    }
+    return (COH ? __ldcg(a.E + si) : a.E[si]) + 0.5f * D;
+}
 
 // Point k of a W x H region (W >= 32): rows' first 32 columns first, then the
 // W - 32 remaining columns of every row.
@@ -296,16 +332,9 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             if (z >= z0 && active) {
                 const float Dd = dd * (1.f / 12.f);
                 const int si = x + g.nx * (y + g.ny * z);
-                float out;
-                if (STAGE == 1) {
-                    const float Dn = NOISE ? dn * (1.f / 12.f) : 0.f;
-                    const float pv = tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)];
-                    out = pv + Dd + Dn;
-                    if (a.heun) a.E[si] = pv + 0.5f * Dd + Dn;
-                } else {
-                    out = (COH ? __ldcg(a.E + si) : a.E[si]) + 0.5f * Dd;
-                }
-                store_padded(a.out, g, x, y, z, out, 3);
+                const float Dn = (STAGE == 1 && NOISE) ? dn * (1.f / 12.f) : 0.f;
+                const float pv = STAGE == 1 ? tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)] : 0.f;
+                store_padded(a.out, g, x, y, z, rk_stage_out<STAGE, COH>(a, x, y, z, si, pv, Dd, Dn), 3);
             }
         }
         r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
@@ -340,6 +369,9 @@ __device__ __forceinline__ void psi_batch_args(const BatchRep &r, long long ds, 
     sa.advect = r.advect;
     sa.heun = r.heun;
     sa.zc = r.zc;
+    sa.rk4 = 0;
+    sa.base = nullptr;
+    sa.Dn = nullptr;
     sa.key = r.lb.key;
     sa.step = r.lb.step + ds;
 }

@@ -100,7 +100,7 @@ def test_persistent_wait_that_runs_out():
 
 
 def test_persistent_unsupported_configurations():
-    for kw in (dict(storage=F.FLB_F16_DEV), dict(scheme=0)):
+    for kw in (dict(storage=F.FLB_F16_DEV), dict(scheme=0), dict(integrator=4)):
         s = _solver(F.FLB_MODE_PERSISTENT, _replicas(**kw))
         with pytest.raises(F.FlbError) as e:
             s.step(1)
