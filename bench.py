@@ -207,21 +207,25 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
 
 def path_variants(F, I, local, steps, peak):
     """Throughput of the other forms of the path, each on its own handle after 3
-    warm-up steps, inputs larger than L2: the FD psi scheme and the FP16 storage
-    variant on the 512^3 quench, and the D2Q9 path on a 4096^2 quench (same free
-    energy, FD as in the 2D workload).  MLUPS and the fraction of the HBM roofline
-    on the algorithmic bytes of that form."""
+    warm-up steps, inputs larger than L2: the FD psi scheme, the FP16 storage
+    variant, the RK4 integrator and the stress-form force on the 512^3 quench,
+    and the D2Q9 path on a 4096^2 quench (same free energy, FD as in the 2D
+    workload).  MLUPS and the fraction of the HBM roofline on the algorithmic
+    bytes of that form."""
     import torch
     d = dict(I.WORKLOADS["quench"])
     forms = [
         ("fd_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FD), 160),
         ("fp16_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, storage=F.FLB_F16_DEV), 84),
+        ("rk4_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, integrator=F.FLB_RK4), 160),
+        ("stress_force_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, force_grad=F.FLB_FORCE_STRESS), 160),
         ("d2q9_4096", dict(dim=2, q=9, nx=4096, ny=4096, nz=1, psi_scheme=F.FLB_FD), 80),
     ]
     out = {}
     for key, kw, alg in forms:
+        kw = {"integrator": F.FLB_HEUN, **kw}
         p = F.flb_params_default(tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
-                                 integrator=F.FLB_HEUN, seed=d["seed"], **kw)
+                                 seed=d["seed"], **kw)
         N = p.nx * p.ny * p.nz
         s = F.Solver(p, device=f"cuda:{local}")
         s.set_fields(psi=I.uniform_field(N, -0.01, 0.01, 11))
