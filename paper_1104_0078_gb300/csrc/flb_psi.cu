@@ -86,58 +86,53 @@ __global__ void sigma2_kernel(const Geom g, const float *__restrict__ psi, float
     sig[o + 2 * g.pn] = K * gx * gy;
 }
 
-__global__ void noise_kernel(const NoiseArgs a)
+// Noise increment eta of one 2D step (Sec. V), held fixed over the step's
+// Runge-Kutta stages.  A block of 32 x 16 threads first draws, once per point,
+// the four normals of every point of its tile and a one-point halo into shared
+// memory (counter: the point's site id, Philox stream 1, block 0), then
+//   FD: eta(r) = sum_l sqrt(2 kT M a_l) [zeta_l(r - c_l) - zeta_l(r)] over the
+//       half-links (1,0), (0,1), (1,1), (1,-1) (a_l = 1/2, 1/2, 1/4, 1/4);
+//   FV: eta(r) = (2/c_s^2) sum_i w_i c_i . (xi(r) + xi(r + c_i)) / 2, xi_a the
+//       first two normals times sqrt(2 kT M).
+__global__ void __launch_bounds__(512) noise2_kernel(const NoiseArgs a)
 {
+    constexpr int TX = 32, TY = 16, HX = TX + 2, HY = TY + 2;
+    __shared__ float zs[4][HY][HX];
     const Geom &g = a.g;
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= g.n) return;
-    const int x = (int)(site % g.nx);
-    const int y = (int)((site / g.nx) % g.ny);
-    const int z = (int)(site / ((long long)g.nx * g.ny));
-    float eta = 0.f;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int t = threadIdx.x + TX * threadIdx.y;
+    for (int k = t; k < HX * HY; k += TX * TY) {
+        const int lx = k % HX, ly = k / HX;
+        const int gx = ((x0 - 1 + lx) % g.nx + g.nx) % g.nx, gy = ((y0 - 1 + ly) % g.ny + g.ny) % g.ny;
+        float G[4];
+        normals4(a.key, a.step, (uint32_t)(gx + g.nx * gy), 1u, 0u, G);
+        zs[0][ly][lx] = G[0];
+        zs[1][ly][lx] = G[1];
+        zs[2][ly][lx] = G[2];
+        zs[3][ly][lx] = G[3];
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+    float eta;
     if (a.scheme == FLB_FD) {
-        const int nl = g.dim == 3 ? 13 : 4;
-        float own[16];
-        for (int b = 0; b < (nl + 3) / 4; ++b) normals4(a.key, a.step, (uint32_t)site, 1u, (uint32_t)b, own + 4 * b);
-        for (int l = 0; l < nl; ++l) {
-            int cx, cy, cz = 0;
-            if (g.dim == 3) { cx = kL13[l][0]; cy = kL13[l][1]; cz = kL13[l][2]; }
-            else { cx = kL4[l][0]; cy = kL4[l][1]; }
-            const int cls = (cx != 0) + (cy != 0) + (cz != 0);
-            const float al = g.dim == 3 ? (cls == 1 ? 6.f / 22.f : cls == 2 ? 3.f / 22.f : 1.f / 22.f)
-                                        : (cls == 1 ? 0.5f : 0.25f);
-            const float sd = sqrtf(2.f * a.kT * a.M * al);
-            const long long nb = g.sidx(wrapi(x - cx, g.nx), wrapi(y - cy, g.ny), g.dim == 3 ? wrapi(z - cz, g.nz) : 0);
-            float gn[4];
-            normals4(a.key, a.step, (uint32_t)nb, 1u, (uint32_t)(l >> 2), gn);
-            eta += sd * (gn[l & 3] - own[l]);
-        }
+        const float s1 = sqrtf(a.kT * a.M), s2 = sqrtf(0.5f * a.kT * a.M);  // sqrt(2 kT M a_l)
+        eta = s1 * ((zs[0][ly][lx - 1] - zs[0][ly][lx]) + (zs[1][ly - 1][lx] - zs[1][ly][lx])) +
+              s2 * ((zs[2][ly - 1][lx - 1] - zs[2][ly][lx]) + (zs[3][ly + 1][lx - 1] - zs[3][ly][lx]));
     } else {
         const float sd = sqrtf(2.f * a.kT * a.M);
-        float own[4];
-        normals4(a.key, a.step, (uint32_t)site, 1u, 0u, own);
-        const int nq = g.dim == 3 ? 18 : 8;
-        float acc = 0.f;
-        for (int i = 0; i < nq; ++i) {
-            int cx, cy, cz = 0;
-            float w;
-            if (g.dim == 3) {
-                cx = kC19[i][0]; cy = kC19[i][1]; cz = kC19[i][2];
-                w = (abs(cx) + abs(cy) + abs(cz)) == 1 ? 1.f / 18.f : 1.f / 36.f;
-            } else {
-                cx = kC9[i][0]; cy = kC9[i][1];
-                w = (abs(cx) + abs(cy)) == 1 ? 1.f / 9.f : 1.f / 36.f;
-            }
-            const long long nb = g.sidx(wrapi(x + cx, g.nx), wrapi(y + cy, g.ny), g.dim == 3 ? wrapi(z + cz, g.nz) : 0);
-            float gn[4];
-            normals4(a.key, a.step, (uint32_t)nb, 1u, 0u, gn);
-            float link = cx * (own[0] + gn[0]) + cy * (own[1] + gn[1]);
-            if (g.dim == 3) link += cz * (own[2] + gn[2]);
-            acc += w * link;
-        }
-        eta = 3.f * sd * acc;  // (2/c_s^2) * (1/2) * sum_i w_i c_i.(xi(r) + xi(r+c_i))
+        const float ox = zs[0][ly][lx], oy = zs[1][ly][lx];
+        // axis links (w = 1/9) and diagonal links (w = 1/36), c . (xi(r) + xi(r + c))
+        const float ax = ((ox + zs[0][ly][lx + 1]) - (ox + zs[0][ly][lx - 1])) +
+                         ((oy + zs[1][ly + 1][lx]) - (oy + zs[1][ly - 1][lx]));
+        const float dg = ((ox + zs[0][ly + 1][lx + 1]) + (oy + zs[1][ly + 1][lx + 1])) -
+                         ((ox + zs[0][ly - 1][lx - 1]) + (oy + zs[1][ly - 1][lx - 1])) +
+                         ((ox + zs[0][ly - 1][lx + 1]) - (oy + zs[1][ly - 1][lx + 1])) -
+                         ((ox + zs[0][ly + 1][lx - 1]) - (oy + zs[1][ly + 1][lx - 1]));
+        eta = 3.f * sd * ((1.f / 9.f) * ax + (1.f / 36.f) * dg);
     }
-    a.eta[site] = eta;
+    a.eta[x + g.nx * y] = eta;
 }
 
 // FV deterministic node flux J = M grad_FV mu - u psi on the interior and one ghost layer.
@@ -265,7 +260,9 @@ cudaError_t launch_sigma2(const Geom &g, const float *psi, float *sig, float A, 
 
 cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s)
 {
-    noise_kernel<<<blocks_for(a.g.n, 256), 256, 0, s>>>(a);
+    if (a.g.dim != 2) return cudaErrorInvalidValue;  // 3D stages draw their noise themselves
+    const dim3 grid((a.g.nx + 31) / 32, (a.g.ny + 15) / 16);
+    noise2_kernel<<<grid, dim3(32, 16), 0, s>>>(a);
     return cudaGetLastError();
 }
 
