@@ -145,10 +145,17 @@ int ora_lattice(int32_t dim, int32_t q, int32_t *c, double *w)
 /* ordered monomials below; b_k = <e_k, e_k>.  Classes: mass {0}, momentum    */
 /* {1..d}, stress {d+1 .. d+d(d+1)/2}, ghosts = the rest.                     */
 /* ------------------------------------------------------------------------- */
-static double monomial(int dim, int k, const int32_t *cv)
+static double monomial(int dim, int q, int k, const int32_t *cv)
 {
     double cx = cv[0], cy = cv[1], cz = cv[2];
     double c2 = cx * cx + cy * cy + cz * cz;
+    if (dim == 3 && q == 15) {
+        /* D3Q15: the stress and c^2 c_a rows as for D3Q19; the remaining
+         * independent monomials on this set are c_x c_y c_z and c^4
+         * (c_a(c_b^2 - c_g^2) vanishes and c^2(3c_x^2 - c^2) repeats 3c_x^2 - c^2) */
+        if (k == 13) return cx * cy * cz;
+        if (k == 14) return c2 * c2;
+    }
     if (dim == 3) {
         switch (k) {
         case 0: return 1.0;
@@ -191,11 +198,11 @@ int ora_moment_basis(int32_t dim, int32_t q, double *E, double *b)
 {
     int32_t c[3 * 19];
     double w[19];
-    if (!((dim == 3 && q == 19) || (dim == 2 && q == 9))) return -1;
+    if (!((dim == 3 && (q == 19 || q == 15)) || (dim == 2 && q == 9))) return -1;
     if (ora_lattice(dim, q, c, w)) return -1;
     for (int k = 0; k < q; ++k) {
         double *ek = E + (size_t)k * q;
-        for (int i = 0; i < q; ++i) ek[i] = monomial(dim, k, c + 3 * i);
+        for (int i = 0; i < q; ++i) ek[i] = monomial(dim, q, k, c + 3 * i);
         for (int l = 0; l < k; ++l) {
             const double *el = E + (size_t)l * q;
             double dot = 0.0;
@@ -462,7 +469,8 @@ void ora_force(const ora_params *p, const double *psi, const double *mu, double 
 /* ------------------------------------------------------------------------- */
 /* Fluctuating lattice Boltzmann step (Sec. IV, App. B)                        */
 /* ------------------------------------------------------------------------- */
-static int noisy_mode_count(int dim) { return dim == 3 ? 15 : 6; }
+/* stress and ghost modes: every mode but mass and momentum */
+static int noisy_mode_count(int dim, int q) { return q - dim - 1; }
 
 /* One collision at every site followed by streaming.  F is the force density
  * (3 x N; may be NULL).  u_out (d x N) receives the velocity of the streamed
@@ -500,7 +508,7 @@ static void lb_collide_stream(const ora_params *p, const box_t *g, double *f, co
     const double gamma_g = p->gamma_ghost;
     const int nstress = d * (d + 1) / 2;
     const int first_noisy = d + 1;
-    const int nnoisy = noisy_mode_count(d);
+    const int nnoisy = noisy_mode_count(d, q);
     const size_t N = g->n;
 
     double *fnew = (double *)malloc(sizeof(double) * (size_t)q * N);
@@ -793,7 +801,7 @@ static void psi_step(const ora_params *p, const box_t *g, double *psi, const dou
 /* ------------------------------------------------------------------------- */
 int ora_step(const ora_params *p, double *f, double *psi, double *u, int64_t step0, int64_t nsteps)
 {
-    if (!((p->dim == 3 && p->q == 19) || (p->dim == 2 && p->q == 9))) return -1;
+    if (!((p->dim == 3 && (p->q == 19 || p->q == 15)) || (p->dim == 2 && p->q == 9))) return -1;
     if (p->nx <= 0 || p->ny <= 0 || (p->dim == 3 && p->nz <= 0)) return -1;
     if (!(p->tau > 0.0) || !(p->integrator == 1 || p->integrator == 2 || p->integrator == 4) || p->scheme < 0 ||
         p->scheme > 1)

@@ -22,7 +22,7 @@ def _coords(p):
 
 
 # ----------------------------------------------------------------- LB half
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_rest_and_uniform_flow_are_fixed_points(dim, q):
     p = O.Params(dim=dim, q=q, nx=5, ny=4, nz=3, kT=0.0, tau=0.7, coupling=2, A=0.1, K=0.02)
     s = O.State.rest(p)
@@ -37,7 +37,7 @@ def test_rest_and_uniform_flow_are_fixed_points(dim, q):
     assert np.allclose(s.u[:dim], u0[:dim, None], atol=1e-15)
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 @pytest.mark.parametrize("tau", [0.3, 0.8, 1.0])
 def test_shear_wave_decay(dim, q, tau):
     # u_x = U sin(k y) decays as exp(-nu k^2 t) with nu = c_s^2 tau (paper's tau, App. B)
@@ -61,7 +61,7 @@ def test_shear_wave_decay(dim, q, tau):
     assert abs(rate / (CS2 * tau * k * k) - 1) < 5e-3
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_shear_wave_advected_by_uniform_flow(dim, q):
     # Galilean check of streaming: a transverse wave u_y = eps sin(k x) on a uniform
     # flow U along x travels at U and decays at nu k^2 (Sec. VI.B at low Mach)
@@ -142,7 +142,7 @@ def test_body_force_momentum_and_stress():
         assert np.abs(d0).max() > 1e-9 and abs(t0) > 1e-9
 
 
-@pytest.mark.parametrize("dim,q,scheme", [(2, 9, 0), (3, 19, 1), (3, 19, 0)])
+@pytest.mark.parametrize("dim,q,scheme", [(2, 9, 0), (3, 19, 1), (3, 19, 0), (3, 15, 0), (3, 15, 1)])
 def test_conservation_with_noise_and_coupling(dim, q, scheme):
     # mass, psi and (for B = 0) momentum are conserved to round-off (Sec. I);
     # for B != 0 the momentum changes by exactly the summed force
@@ -166,7 +166,7 @@ def test_conservation_with_noise_and_coupling(dim, q, scheme):
         assert np.allclose(j1 - j0, F, atol=1e-13 * p.n)
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_equipartition_all_modes(dim, q):
     # linear FLBE at rest: every non-conserved mode has <m_k^2> = mu b_k with
     # mu = rho kT / c_s^2, and <u_a^2> = kT / rho0 (adhikari2005, Sec. III)
@@ -237,7 +237,7 @@ def test_lyapunov_noise_free_coupled(scheme):
 
 
 # ----------------------------------------------------------------- psi half
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("integrator", [1, 2, 4])
 def test_single_mode_exact_amplification(dim, q, scheme, integrator):

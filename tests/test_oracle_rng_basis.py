@@ -67,10 +67,12 @@ def test_lattice_isotropy(dim, q):
 NORMS = {
     (3, 19): "1 1/3 1/3 1/3 2/3 4/3 4/9 1/9 1/9 1/9 2/27 2/27 2/27 2/9 2/9 2/9 2/9 1/3 1/9",
     (2, 9): "1 1/3 1/3 4/9 4/9 1/9 2/27 2/27 16/81",
+    # D3Q15 (w 2/9, 1/9, 1/72): c_x(c^2 - 5/3) has 8/27, c_x c_y c_z 1/9, c^4 - 3c^2 + 4/3 has 8/9
+    (3, 15): "1 1/3 1/3 1/3 2/3 4/3 4/9 1/9 1/9 1/9 8/27 8/27 8/27 1/9 8/9",
 }
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_moment_basis(dim, q):
     E, b = O.moment_basis(dim, q)
     c, w = O.lattice(dim, q)
