@@ -208,8 +208,8 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
 def path_variants(F, I, local, steps, peak):
     """Throughput of the other forms of the path, each on its own handle after 3
     warm-up steps, inputs larger than L2: the FD psi scheme, the FP16 storage
-    variant, the RK4 integrator and the stress-form force on the 512^3 quench,
-    and the D2Q9 path on a 4096^2 quench (same free energy, FD as in the 2D
+    variant, the RK4 integrator, the stress-form force and the D3Q15 lattice (FD)
+    on the 512^3 quench, and the D2Q9 path on a 4096^2 quench (same free energy, FD as in the 2D
     workload).  MLUPS and the fraction of the HBM roofline on the algorithmic
     bytes of that form."""
     import torch
@@ -219,6 +219,7 @@ def path_variants(F, I, local, steps, peak):
         ("fp16_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, storage=F.FLB_F16_DEV), 84),
         ("rk4_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, integrator=F.FLB_RK4), 160),
         ("stress_force_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, force_grad=F.FLB_FORCE_STRESS), 160),
+        ("d3q15_fd_512", dict(q=15, nx=512, ny=512, nz=512, psi_scheme=F.FLB_FD), 128),
         ("d2q9_4096", dict(dim=2, q=9, nx=4096, ny=4096, nz=1, psi_scheme=F.FLB_FD), 80),
     ]
     out = {}

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libflb.so")
 
 FLB_OK, FLB_EINVAL, FLB_ENOSPC, FLB_ECUDA, FLB_ENONFINITE, FLB_ETIMEOUT, FLB_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FLB_FD, FLB_FV = 0, 1
-FLB_EULER, FLB_HEUN = 1, 2
+FLB_EULER, FLB_HEUN, FLB_RK4 = 1, 2, 4
 FLB_F32_DEV, FLB_F16_DEV = 0, 1
 FLB_COUPLE_FORCE, FLB_COUPLE_ADVECT = 1, 2
 FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV, FLB_FORCE_STRESS = 0, 1, 2, 3

@@ -24,21 +24,27 @@ namespace {
 const int C19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
                         {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
                         {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+const int C15[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                        {0, 0, 1},  {0, 0, -1}, {1, 1, 1},   {-1, -1, -1}, {1, 1, -1},
+                        {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, 1, 1}};
 const int C9[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
                       {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
 
-inline const int *cvec(int q, int i) { return q == 19 ? C19[i] : C9[i]; }
+inline const int *cvec(int q, int i) { return q == 19 ? C19[i] : q == 15 ? C15[i] : C9[i]; }
 inline double wgt(int q, int i)
 {
     const int *c = cvec(q, i);
     const int l2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
     if (q == 19) return l2 == 0 ? 1.0 / 3.0 : l2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
+    if (q == 15) return l2 == 0 ? 2.0 / 9.0 : l2 == 1 ? 1.0 / 9.0 : 1.0 / 72.0;
     return l2 == 0 ? 4.0 / 9.0 : l2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0;
 }
 
 // norms of the noisy modes in noise order (hand-derived from the monomials)
 const double NORM19[15] = {2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 2.0 / 27, 2.0 / 27,
                            2.0 / 27, 2.0 / 9, 2.0 / 9, 2.0 / 9, 2.0 / 9, 1.0 / 3, 1.0 / 9};
+// D3Q15 ghosts: c_a(c^2 - 5/3) (8/27 each), c_x c_y c_z (1/9), c^4 - 3c^2 + 4/3 (8/9)
+const double NORM15[11] = {2.0 / 3, 4.0 / 3, 4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 8.0 / 27, 8.0 / 27, 8.0 / 27, 1.0 / 9, 8.0 / 9};
 const double NORM9[6] = {4.0 / 9, 4.0 / 9, 1.0 / 9, 2.0 / 27, 2.0 / 27, 16.0 / 81};
 
 constexpr long long WIN_MAX = 32768;  // sites of one flb_get_window call
@@ -86,7 +92,11 @@ int axis_K(int n, int kmax) { return (kmax <= 0 || 2 * kmax + 1 >= n) ? n : 2 * 
 
 bool valid(const flb_params &p)
 {
-    if (!((p.dim == 3 && p.q == 19) || (p.dim == 2 && p.q == 9))) return false;
+    if (!((p.dim == 3 && (p.q == 19 || p.q == 15)) || (p.dim == 2 && p.q == 9))) return false;
+    // D3Q15: the finite-difference psi scheme (lattice independent) and the
+    // central-difference or stress force; the FV operators on the D3Q15
+    // neighbourhood are not built on the device
+    if (p.q == 15 && (p.psi_scheme != FLB_FD || p.force_grad == FLB_FORCE_FV)) return false;
     const long long nz = p.dim == 3 ? p.nz : 1;
     if (p.nx < 4 || p.ny < 4 || (p.dim == 3 && p.nz < 4)) return false;
     if ((long long)p.nx * p.ny * nz >= (1LL << 31)) return false;
@@ -170,11 +180,11 @@ void init_rep_consts(Rep &r, const flb_params &p)
     r.omega_s = (float)ws;
     r.omega_b = (float)(1.0 - gb);
     r.gamma_g = (float)p.gamma_ghost;
-    const int nn = p.q == 19 ? 15 : 6;
-    const int nstress = p.q == 19 ? 6 : 3;
+    const int nn = p.q - p.dim - 1;
+    const int nstress = p.dim == 3 ? 6 : 3;
     for (int t = 0; t < nn; ++t) {
         const double gam = t == 0 ? gb : (t < nstress ? gs : p.gamma_ghost);
-        const double b = p.q == 19 ? NORM19[t] : NORM9[t];
+        const double b = p.q == 19 ? NORM19[t] : p.q == 15 ? NORM15[t] : NORM9[t];
         r.namp[t] = (float)std::sqrt((1.0 - gam * gam) / b);
     }
 }
@@ -470,10 +480,10 @@ int step_rep3(flb_handle *h, Rep &r)
             FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
     }
     cudaEvent_t e1 = mark(h);
-    FLB_TRY(launch_lb3d(la, p.storage, st));
+    FLB_TRY(r.q == 15 ? launch_lb15(la, p.storage, st) : launch_lb3d(la, p.storage, st));
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
-    FLB_TRY(launch_vel3(la, p.storage, st));
+    FLB_TRY(r.q == 15 ? launch_vel15(la, p.storage, st) : launch_vel3(la, p.storage, st));
     const int rc = launch_psi_stages(h, r);
     if (rc != FLB_OK) return rc;
     cudaEvent_t e3 = mark(h);
@@ -659,7 +669,7 @@ int take_status(flb_handle *h)
 bool batch_supported(const flb_handle *h)
 {
     for (const Rep &r : h->reps)
-        if (r.dim != 3 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4) return false;
+        if (r.dim != 3 || r.q != 19 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4) return false;
     return !h->reps.empty();
 }
 

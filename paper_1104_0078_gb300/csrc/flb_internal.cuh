@@ -287,6 +287,8 @@ cudaError_t launch_sigma3(const Geom &g, const float *psi, float *sig, float A, 
 cudaError_t launch_sigma2(const Geom &g, const float *psi, float *sig, float A, float B, float K, cudaStream_t st);
 // velocity of the streamed state after a step, written to a.u (flb_aux3d.cu, flb_lb.cu)
 cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t s);
+cudaError_t launch_lb15(const LBArgs &a, int storage, cudaStream_t s);   // D3Q15 collide-stream
+cudaError_t launch_vel15(const LBArgs &a, int storage, cudaStream_t s);  // D3Q15 velocity of the new state
 // batched mu and velocity over the work lists (flb_aux3d.cu)
 cudaError_t launch_mu3_batch(const BatchLists &L, cudaStream_t st);
 cudaError_t launch_vel3_batch(const BatchLists &L, int storage, bool force, cudaStream_t st);

@@ -193,6 +193,9 @@ __constant__ int8_t kEq19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 
                                     {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
                                     {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
                                     {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+__constant__ int8_t kEq15[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                                    {0, 0, 1},  {0, 0, -1}, {1, 1, 1},   {-1, -1, -1}, {1, 1, -1},
+                                    {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, 1, 1}};
 __constant__ int8_t kEq9[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
                                   {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
 
@@ -231,15 +234,16 @@ __global__ void init_eq_kernel(const Geom g, int q, const float *__restrict__ rh
     const int y = (int)((site / g.nx) % g.ny);
     const int z = (int)(site / ((long long)g.nx * g.ny));
     for (int i = 0; i < q; ++i) {
-        const int8_t *c = q == 19 ? kEq19[i] : kEq9[i];
+        const int8_t *c = q == 19 ? kEq19[i] : q == 15 ? kEq15[i] : kEq9[i];
         const long long pi = g.pidx(x + c[0], y + c[1], z + c[2]);
         const float r = rho ? rho[pi] : rho0;
         const float ux = u[pi], uy = u[g.pn + pi], uz = g.dim == 3 ? u[2 * g.pn + pi] : 0.f;
         const float cu = c[0] * ux + c[1] * uy + c[2] * uz;
         const float u2 = ux * ux + uy * uy + uz * uz;
         const float l2 = (float)(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-        const float w = q == 19 ? (l2 == 0.f ? 1.f / 3.f : l2 == 1.f ? 1.f / 18.f : 1.f / 36.f)
-                                : (l2 == 0.f ? 4.f / 9.f : l2 == 1.f ? 1.f / 9.f : 1.f / 36.f);
+        const float w = q == 19   ? (l2 == 0.f ? 1.f / 3.f : l2 == 1.f ? 1.f / 18.f : 1.f / 36.f)
+                        : q == 15 ? (l2 == 0.f ? 2.f / 9.f : l2 == 1.f ? 1.f / 9.f : 1.f / 72.f)
+                                  : (l2 == 0.f ? 4.f / 9.f : l2 == 1.f ? 1.f / 9.f : 1.f / 36.f);
         stpop(fout, (long long)i * g.n + site, w * ((r - rho0) + r * (3.f * cu + 4.5f * cu * cu - 1.5f * u2)));
     }
 }

@@ -49,6 +49,14 @@ __global__ void __launch_bounds__(RED_BS) totals_kernel(const Geom g, int q, con
             jx = (fi[1] - fi[2]) + (fi[7] - fi[8]) + (fi[9] - fi[10]) + (fi[11] - fi[12]) + (fi[13] - fi[14]);
             jy = (fi[3] - fi[4]) + (fi[7] - fi[8]) - (fi[9] - fi[10]) + (fi[15] - fi[16]) + (fi[17] - fi[18]);
             jz = (fi[5] - fi[6]) + (fi[11] - fi[12]) - (fi[13] - fi[14]) + (fi[15] - fi[16]) - (fi[17] - fi[18]);
+        } else if (q == 15) {
+            m = fi[0];
+            for (int i = 1; i < 15; ++i) m += fi[i];
+            // corner pairs (7,8) +(1,1,1), (9,10) +(1,1,-1), (11,12) +(1,-1,1), (13,14) +(1,-1,-1)
+            const float d4 = fi[7] - fi[8], d5 = fi[9] - fi[10], d6 = fi[11] - fi[12], d7 = fi[13] - fi[14];
+            jx = (fi[1] - fi[2]) + (d4 + d5) + (d6 + d7);
+            jy = (fi[3] - fi[4]) + (d4 + d5) - (d6 + d7);
+            jz = (fi[5] - fi[6]) + (d4 - d5) + (d6 - d7);
         } else {
             m = fi[0];
             for (int i = 1; i < 9; ++i) m += fi[i];
@@ -283,6 +291,9 @@ __constant__ int8_t kWin19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1,
                                      {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
                                      {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
                                      {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+__constant__ int8_t kWin15[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                                     {0, 0, 1},  {0, 0, -1}, {1, 1, 1},   {-1, -1, -1}, {1, 1, -1},
+                                     {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, 1, 1}};
 __constant__ int8_t kWin9[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
                                    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
 
@@ -298,7 +309,7 @@ __global__ void window_kernel(const Geom g, int q, const T *__restrict__ f, cons
     const int y = (y0 + (int)((k / wx) % wy)) % g.ny;
     const int z = (z0 + (int)(k / ((long long)wx * wy))) % g.nz;
     for (int i = 0; i < q; ++i) {
-        const int8_t *c = q == 19 ? kWin19[i] : kWin9[i];
+        const int8_t *c = q == 19 ? kWin19[i] : q == 15 ? kWin15[i] : kWin9[i];
         const long long src = g.sidx(wrapi(x - c[0], g.nx), wrapi(y - c[1], g.ny), g.dim == 3 ? wrapi(z - c[2], g.nz) : 0);
         out[(long long)i * W + k] = ldv(f, (long long)i * g.n + src);
     }

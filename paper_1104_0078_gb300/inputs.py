@@ -16,6 +16,10 @@ Workloads (lattice units, periodic):
              [1e-5, 1e-4], seeds 1 + r, A 0.05, B 0, K 0.04, M 0.1.
   quench     D3Q19 512^3 spinodal quench, A -0.0625, B 0.0625, K 0.04, M 0.1,
              kT 1e-5, psi0 uniform in [-0.01, 0.01], u0 = 0.
+  fluct_d3q15  D3Q15 32^3, tau 1.1, kT 1/3000, A 0.625, B = K = 0, M 0.095, FD:
+             the lattice and parameters of the paper's own order-parameter
+             fluctuation test (Sec. VI), a Gaussian free energy with
+             S(q) = kT/A at every q.
 """
 from __future__ import annotations
 
@@ -30,6 +34,8 @@ WORKLOADS = {
                     scheme=1, seed=1),
     "slab": dict(dim=3, q=19, nx=256, ny=256, nz=64, rho0=1.0, tau=0.8, kT=2e-5, A=-0.0625, B=0.0625, K=0.04,
                  M=0.1, scheme=1, seed=1),
+    "fluct_d3q15": dict(dim=3, q=15, nx=32, ny=32, nz=32, rho0=1.0, tau=1.1, kT=1.0 / 3000.0, A=0.625, B=0.0,
+                        K=0.0, M=0.095, scheme=0, seed=1),
     "quench": dict(dim=3, q=19, nx=512, ny=512, nz=512, rho0=1.0, tau=0.8, kT=1e-5, A=-0.0625, B=0.0625,
                    K=0.04, M=0.1, scheme=1, seed=1),
 }

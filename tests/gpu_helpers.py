@@ -47,5 +47,5 @@ def field_error(gpu, ora, eq=0.0):
 
 
 def weights_column(q):
-    _, w = O.lattice(3 if q == 19 else 2, q)
+    _, w = O.lattice(2 if q == 9 else 3, q)
     return w[:, None]

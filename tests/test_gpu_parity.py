@@ -40,8 +40,9 @@ def _run_pair(d, nsteps, amp_f=2e-3, amp_psi=0.05, seed=7):
 
 
 CASES = []
-for dim, q, shape in ((2, 9, (13, 10, 1)), (3, 19, (11, 7, 9)), (3, 19, (37, 23, 19))):
-    for scheme in (0, 1):
+for dim, q, shape in ((2, 9, (13, 10, 1)), (3, 19, (11, 7, 9)), (3, 19, (37, 23, 19)), (3, 15, (11, 7, 9)),
+                      (3, 15, (37, 23, 19))):
+    for scheme in ((0,) if q == 15 else (0, 1)):    # D3Q15: the FD psi scheme on the device
         for integ in (1, 2, 4):
             if shape == (37, 23, 19) and integ == 1:
                 continue
@@ -59,9 +60,11 @@ def test_coupled_step_matches_oracle(dim, q, shape, scheme, integ):
     assert s.get_step() == 25
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
-@pytest.mark.parametrize("scheme", [0, 1])
-@pytest.mark.parametrize("force_grad", [1, 2, 3])
+FORCE_CASES = [(dim, q, scheme, fg) for dim, q in ((2, 9), (3, 19)) for scheme in (0, 1) for fg in (1, 2, 3)]
+FORCE_CASES += [(3, 15, 0, 1), (3, 15, 0, 3)]
+
+
+@pytest.mark.parametrize("dim,q,scheme,force_grad", FORCE_CASES)
 def test_force_gradient_choices_match_oracle(dim, q, scheme, force_grad):
     # both lattice gradients in the force with both psi schemes (the matched pair
     # is the default of the cases above); a deep quench so the force is large
@@ -74,14 +77,14 @@ def test_force_gradient_choices_match_oracle(dim, q, scheme, force_grad):
     assert field_error(ug[:dim], st.u[:dim]) < TOL
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_relaxation_variants_match_oracle(dim, q):
     # bulk rate different from shear, partially relaxed ghosts, only advection coupling
     shape = (9, 8, 6)
     for extra in (dict(gamma_bulk=-0.4, gamma_ghost=0.35), dict(coupling=2, gamma_ghost=-0.2),
                   dict(coupling=0, kT=0.0), dict(M=0.0, coupling=1)):
         d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.6, kT=2e-4, A=-0.02, B=0.1, K=0.03,
-                 M=0.2, scheme=1, integrator=2, coupling=3, seed=11)
+                 M=0.2, scheme=0 if q == 15 else 1, integrator=2, coupling=3, seed=11)
         d.update(extra)
         s, (fg, pg, ug), st, feq = _run_pair(d, 15)
         assert field_error(fg, st.f, feq) < TOL, extra
@@ -107,9 +110,10 @@ def test_bulk_3d_100_steps_from_rest():
     assert field_error(ug, st.u) < TOL
 
 
-def test_conserved_totals_drift():
+@pytest.mark.parametrize("q", [19, 15])
+def test_conserved_totals_drift(q):
     # mass, momentum (B = 0) and psi drift over 400 steps on the GPU, reduced in FP64
-    d = dict(I.WORKLOADS["bulk_3d"], nx=32, ny=32, nz=32, kT=1e-4)
+    d = dict(I.WORKLOADS["bulk_3d"], nx=32, ny=32, nz=32, kT=1e-4, q=q, scheme=0 if q == 15 else 1)
     s = F.Solver(flb_params(d))
     N = 32 ** 3
     s.set_fields(psi=I.random_field(N, 0.1, 5))
@@ -118,7 +122,7 @@ def test_conserved_totals_drift():
     t1, u2, rc1 = s.moments()
     assert rc0 == rc1 == F.FLB_OK
     f = s.get_populations()
-    c, _ = O.lattice(3, 19)
+    c, _ = O.lattice(3, q)
     jabs = np.abs(np.einsum("ia,in->an", c.astype(float), f)).sum()
     psi, _ = s.get_psi_u()
     assert abs(t1[0] - t0[0]) / (N * 1.0) < 1e-6
@@ -279,15 +283,36 @@ def test_determinism_two_runs():
 
 
 def test_minimum_box_and_errors():
-    # the smallest admitted box (4^3) still matches; invalid calls return codes
-    d = dict(dim=3, q=19, nx=4, ny=4, nz=4, tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1, scheme=0,
-             integrator=2, seed=3)
-    s, (fg, pg, ug), st, feq = _run_pair(d, 10)
-    assert field_error(fg, st.f, feq) < TOL and field_error(pg, st.psi) < TOL
+    # the smallest admitted box (4^3) still matches, on both 3D lattices; invalid
+    # calls return codes
+    for q in (15, 19):
+        d = dict(dim=3, q=q, nx=4, ny=4, nz=4, tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1, scheme=0,
+                 integrator=2, seed=3)
+        s, (fg, pg, ug), st, feq = _run_pair(d, 10)
+        assert field_error(fg, st.f, feq) < TOL and field_error(pg, st.psi) < TOL, q
     lib = F.load_library()
     assert lib.flb_step(s.h, -1) == F.FLB_EINVAL
     assert lib.flb_get_window(s.h, 0, 0, 0, 0, 64, 64, 64, None, None) == F.FLB_ENOSPC
     assert lib.flb_set_mode(s.h, 7) == F.FLB_EINVAL
+
+
+def test_d3q15_fp16_storage_tracks_fp32():
+    # FP16 deviations on D3Q15: the same seeded start advanced 40 steps stays within
+    # the half-precision rounding of the FP32 path (unit roundoff 2^-11 on
+    # deviations of ~2e-3, re-rounded every step)
+    d = dict(dim=3, q=15, nx=20, ny=18, nz=16, tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1, scheme=0,
+             integrator=2, coupling=3, seed=6)
+    N = 20 * 18 * 16
+    out = {}
+    for stg in (F.FLB_F32_DEV, F.FLB_F16_DEV):
+        s = F.Solver(flb_params(d, storage=stg))
+        s.set_fields(psi=I.random_field(N, 0.05, 2))
+        s.set_populations(weights_column(15) + I.random_deviations(15, N, 2e-3, 3))
+        s.step(40)
+        out[stg] = (s.get_populations(), s.get_psi_u()[0])
+    feq = weights_column(15)
+    assert field_error(out[F.FLB_F16_DEV][0], out[F.FLB_F32_DEV][0], feq) < 5e-2
+    assert field_error(out[F.FLB_F16_DEV][1], out[F.FLB_F32_DEV][1]) < 1e-3
 
 
 def test_nonfinite_is_reported():

@@ -2,7 +2,8 @@
 equipartition <u_a^2> = kT/rho0 and the lattice static structure factor
 S(q) = kT/(A - K L_SO(q)) (Eq. test2 with the SO symbol), including the exact
 discrete-time factor of the integrator and the transient from psi0 = 0, on the
-bulk 2D (D2Q9, FD) and bulk 3D (D3Q19, FV) workloads, and the acceptance test of
+bulk 2D (D2Q9, FD) and bulk 3D (D3Q19, FV) workloads and the paper's D3Q15
+order-parameter fluctuation run, and the acceptance test of
 FP16 population storage against the same theory."""
 import numpy as np
 import pytest
@@ -92,6 +93,19 @@ def test_bulk_3d_structure_factor_and_equipartition():
     th, n_ind, qg = _theory(d, times)
     _shell_check(S.reshape(64, 64, 64), th, n_ind, qg, tol=0.02)
     assert np.all(np.abs(u2 / d["kT"] - 1) < 0.01)
+
+
+@pytest.mark.parametrize("coupling", [0, 3])
+def test_d3q15_order_parameter_fluctuations(coupling):
+    # the paper's own validation run (Sec. VI): D3Q15 32^3, tau 1.1, kT 1/3000,
+    # Gaussian free energy A 0.625, B = K = 0, M 0.095, FD scheme, diffusion alone
+    # and coupled to the fluid: the equilibrium ratio S(q) / (kT/A) is one at
+    # every q, and the fluid obeys equipartition <u_a^2> = kT/rho0
+    d = dict(I.WORKLOADS["fluct_d3q15"], integrator=2, coupling=coupling)
+    S, ns, u2, times = _measure(d, 10000, 1000, 10)
+    th, n_ind, qg = _theory(d, times)
+    _shell_check(S.reshape(32, 32, 32), th, n_ind, qg, tol=0.02)
+    assert np.all(np.abs(u2 / d["kT"] - 1) < 0.02)
 
 
 def test_galilean_invariance_small_mach():
