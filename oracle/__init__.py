@@ -53,6 +53,7 @@ class OraParams(ctypes.Structure):
         ("gnx", ctypes.c_int32), ("gny", ctypes.c_int32), ("gnz", ctypes.c_int32),
         ("ox", ctypes.c_int32), ("oy", ctypes.c_int32), ("oz", ctypes.c_int32),
         ("force_grad", ctypes.c_int32),
+        ("laplacian", ctypes.c_int32),
     ]
 
 
@@ -73,6 +74,7 @@ def lib():
         L.ora_lattice.argtypes = [ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), dp]
         L.ora_moment_basis.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp]
         L.ora_laplacian_so.argtypes = [ctypes.c_int32] * 4 + [dp, dp]
+        L.ora_laplacian.argtypes = [ctypes.c_int32] * 5 + [dp, dp]
         L.ora_fv_laplacian.argtypes = [ctypes.c_int32] * 5 + [dp, dp]
         L.ora_mu.argtypes = [P(OraParams), dp, dp]
         L.ora_force.argtypes = [P(OraParams), dp, dp, dp]
@@ -81,7 +83,7 @@ def lib():
         L.ora_step.argtypes = [P(OraParams), dp, dp, dp, ctypes.c_int64, ctypes.c_int64]
         L.ora_moments.argtypes = [P(OraParams), dp, dp, dp, dp]
         L.ora_equilibrium.argtypes = [P(OraParams), dp, dp, dp]
-        for name in ("ora_lattice", "ora_moment_basis", "ora_fv_laplacian", "ora_psi_rhs", "ora_step",
+        for name in ("ora_lattice", "ora_moment_basis", "ora_laplacian", "ora_fv_laplacian", "ora_psi_rhs", "ora_step",
                      "ora_moments", "ora_equilibrium"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -110,7 +112,7 @@ class Params:
     B: float = 0.0
     K: float = 0.04
     M: float = 0.1
-    scheme: int = 1          # 0 FD, 1 FV
+    scheme: int = 1          # 0 FD, 1 FV, 2 the naive contrast scheme (Sec. III)
     integrator: int = 2      # 1 Euler, 2 Heun
     coupling: int = 3
     lb_on: int = 1
@@ -119,6 +121,7 @@ class Params:
     gdims: tuple = (0, 0, 0)
     origin: tuple = (0, 0, 0)
     force_grad: int = 0      # 1 central difference (Sec. IV), 2 FV gradient (Eq. fvgrad), 0 matched to scheme
+    laplacian: int = 0       # App. A stencil: 0 SO, 1 CD, 2 PK, 3 LB
 
     @property
     def n(self) -> int:
@@ -142,6 +145,7 @@ class Params:
         p.gnx, p.gny, p.gnz = self.gdims
         p.ox, p.oy, p.oz = self.origin
         p.force_grad = self.force_grad
+        p.laplacian = self.laplacian
         return p
 
 
@@ -185,6 +189,16 @@ def laplacian_so(dim: int, field_: np.ndarray) -> np.ndarray:
     nz, ny, nx = a.shape if a.ndim == 3 else (1,) + a.shape
     out = np.zeros_like(a)
     lib().ora_laplacian_so(dim, nx, ny, nz, _dp(a), _dp(out))
+    return out
+
+
+def laplacian(dim: int, kind: int, field_: np.ndarray) -> np.ndarray:
+    """The App. A stencil `kind` (0 SO, 1 CD, 2 PK, 3 LB) applied to a periodic field."""
+    a = np.ascontiguousarray(field_, dtype=np.float64)
+    nz, ny, nx = a.shape if a.ndim == 3 else (1,) + a.shape
+    out = np.zeros_like(a)
+    if lib().ora_laplacian(dim, kind, nx, ny, nz, _dp(a), _dp(out)):
+        raise ValueError("no such stencil in this dimension")
     return out
 
 
@@ -342,9 +356,9 @@ def height_spectrum(h: np.ndarray) -> np.ndarray:
 
 def free_energy(p: Params, psi: np.ndarray) -> float:
     """Discrete Landau free energy whose variation is mu (Eqs. Feng, feng):
-    sum_r [A psi^2/2 + B psi^4/4 - (K/2) psi lap_SO psi]."""
+    sum_r [A psi^2/2 + B psi^4/4 - (K/2) psi lap psi], lap the stencil of mu."""
     a = np.asarray(psi, dtype=np.float64).reshape(p.shape)
-    lap = laplacian_so(p.dim, a if p.dim == 3 else a[0]).reshape(p.shape)
+    lap = laplacian(p.dim, p.laplacian, a if p.dim == 3 else a[0]).reshape(p.shape)
     return float(np.sum(0.5 * p.A * a ** 2 + 0.25 * p.B * a ** 4 - 0.5 * p.K * a * lap))
 
 

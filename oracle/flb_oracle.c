@@ -263,37 +263,66 @@ static inline uint32_t rng_site(const ora_params *p, int x, int y, int z)
 /* Laplacian stencils of App. A and the finite-volume operators of Sec. V.B   */
 /* ------------------------------------------------------------------------- */
 
-/* Shinozaki-Oono Laplacian, Eq. (solap): 6/22 on the 6 nearest neighbours,
- * 3/22 on the 12 next-nearest, 1/22 on the 8 corners, -80/22 at the centre.
- * In 2D the paper gives no stencil; reading: 1/4 [2 sum N1 + sum N2 - 12 psi],
- * the planar stencil with the same N1:N2 = 2:1 weighting. */
-void ora_laplacian_so(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out)
+/* The Laplacian stencils of App. A on the 3D cubic neighbourhood, written by
+ * neighbour class: a1 on the 6 nearest neighbours (N1), a2 on the 12 next
+ * nearest (N2), a3 on the 8 corners (N3), and -(6 a1 + 12 a2 + 8 a3) at the
+ * centre:
+ *   kind 0 Shinozaki-Oono, Eq. (solap):  6/22, 3/22, 1/22 (centre -80/22)
+ *   kind 1 central difference, Eq. (fdlap): 1, 0, 0 (centre -6)
+ *   kind 2 Patra-Karttunen, Eq. (pklap): 14/30, 3/30, 1/30 (centre -128/30)
+ *   kind 3 lattice Boltzmann, Eq. (lblap): 1/9 on all 26 (centre -26/9)
+ * In 2D the paper gives no stencil; readings: SO 1/4 [2 sum N1 + sum N2 - 12 psi]
+ * (the planar stencil with the same N1:N2 = 2:1 weighting) and CD the 5-point
+ * stencil.  Returns -1 for a kind without a 2D form. */
+static int lap_class_weights(int dim, int kind, double a[4])
 {
+    a[3] = 0.0;
+    if (dim == 3) {
+        switch (kind) {
+        case 0: a[1] = 6.0 / 22.0; a[2] = 3.0 / 22.0; a[3] = 1.0 / 22.0; break;
+        case 1: a[1] = 1.0; a[2] = 0.0; a[3] = 0.0; break;
+        case 2: a[1] = 14.0 / 30.0; a[2] = 3.0 / 30.0; a[3] = 1.0 / 30.0; break;
+        case 3: a[1] = 1.0 / 9.0; a[2] = 1.0 / 9.0; a[3] = 1.0 / 9.0; break;
+        default: return -1;
+        }
+        a[0] = -(6.0 * a[1] + 12.0 * a[2] + 8.0 * a[3]);
+        return 0;
+    }
+    switch (kind) {
+    case 0: a[1] = 0.5; a[2] = 0.25; break;
+    case 1: a[1] = 1.0; a[2] = 0.0; break;
+    default: return -1;
+    }
+    a[0] = -(4.0 * a[1] + 4.0 * a[2]);
+    return 0;
+}
+
+int ora_laplacian(int32_t dim, int32_t kind, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out)
+{
+    double a[4];
+    if (lap_class_weights(dim, kind, a)) return -1;
     box_t g; g.dim = dim; g.nx = nx; g.ny = ny; g.nz = dim == 2 ? 1 : nz;
     g.n = (size_t)g.nx * g.ny * g.nz;
+    const int zr = dim == 3 ? 1 : 0;
 #pragma omp parallel for schedule(static)
     for (long long s = 0; s < (long long)g.n; ++s) {
         int x, y, z;
         coords(&g, (size_t)s, &x, &y, &z);
         double acc = 0.0;
-        if (dim == 3) {
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int cls = abs(dx) + abs(dy) + abs(dz);
-                        double wgt = cls == 0 ? -80.0 / 22.0 : cls == 1 ? 6.0 / 22.0 : cls == 2 ? 3.0 / 22.0 : 1.0 / 22.0;
-                        acc += wgt * in[site_at(&g, x + dx, y + dy, z + dz)];
-                    }
-        } else {
+        for (int dz = -zr; dz <= zr; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
-                    int cls = abs(dx) + abs(dy);
-                    double wgt = cls == 0 ? -3.0 : cls == 1 ? 0.5 : 0.25;
-                    acc += wgt * in[site_at(&g, x + dx, y + dy, 0)];
+                    int cls = abs(dx) + abs(dy) + abs(dz);
+                    acc += a[cls] * in[site_at(&g, x + dx, y + dy, z + dz)];
                 }
-        }
         out[s] = acc;
     }
+    return 0;
+}
+
+void ora_laplacian_so(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out)
+{
+    ora_laplacian(dim, 0, nx, ny, nz, in, out);
 }
 
 /* Finite-volume gradient, Eq. (fvgrad): grad m(r) = (1/c_s^2) sum_i w_i c_i m(r + c_i).
@@ -359,12 +388,13 @@ int ora_fv_laplacian(int32_t dim, int32_t q, int32_t nx, int32_t ny, int32_t nz,
 /* Chemical potential and force                                                */
 /* ------------------------------------------------------------------------- */
 
-/* mu = A psi + B psi^3 - K lap_SO psi (Sec. II.A, with the SO Laplacian of App. A). */
+/* mu = A psi + B psi^3 - K lap psi (Sec. II.A), lap the App. A stencil chosen
+ * by p->laplacian (the paper's runs: SO). */
 void ora_mu(const ora_params *p, const double *psi, double *mu)
 {
     box_t g = box_of(p);
     double *lap = (double *)malloc(sizeof(double) * g.n);
-    ora_laplacian_so(p->dim, p->nx, p->ny, p->nz, psi, lap);
+    ora_laplacian(p->dim, p->laplacian, p->nx, p->ny, p->nz, psi, lap);
     for (size_t s = 0; s < g.n; ++s) {
         double ps = psi[s];
         mu[s] = p->A * ps + p->B * ps * ps * ps - p->K * lap[s];
@@ -378,7 +408,7 @@ void ora_mu(const ora_params *p, const double *psi, double *mu)
  *            + delta_ab [A/2 psi^2 + 3B/4 psi^4 - K psi lap psi - K/2 |grad psi|^2]
  * (psi f' - f = A/2 psi^2 + 3B/4 psi^4 for f = A/2 psi^2 + B/4 psi^4), whose
  * continuum divergence is psi grad mu.  Reading: gradients by the symmetric
- * central difference, lap by the SO stencil (as in mu), and the divergence by
+ * central difference, lap by the stencil of mu, and the divergence by
  * the central difference, so that sum_r F = 0 exactly (momentum is conserved
  * for B != 0 too) while F = -psi grad mu + O(h^2). */
 static void stress_force(const ora_params *p, const box_t *g, const double *psi, double *F)
@@ -387,7 +417,7 @@ static void stress_force(const ora_params *p, const box_t *g, const double *psi,
     const int d = g->dim;
     double *lap = (double *)malloc(sizeof(double) * N);
     double *sig = (double *)malloc(sizeof(double) * 9 * N);
-    ora_laplacian_so(p->dim, p->nx, p->ny, p->nz, psi, lap);
+    ora_laplacian(p->dim, p->laplacian, p->nx, p->ny, p->nz, psi, lap);
     for (size_t s = 0; s < N; ++s) {
         int x, y, z;
         coords(g, s, &x, &y, &z);
@@ -617,20 +647,22 @@ static void lb_collide_stream(const ora_params *p, const box_t *g, double *f, co
 /* Stochastic method of lines for psi (Sec. V)                                 */
 /* ------------------------------------------------------------------------- */
 
-/* Half-links of the finite-difference scheme: one of each +-c pair of the SO
- * stencil, in the order x, y, z; (1,1,0), (1,-1,0), (1,0,1), (1,0,-1), (0,1,1),
- * (0,1,-1); (1,1,1), (1,1,-1), (1,-1,1), (1,-1,-1).  2D: (1,0), (0,1), (1,1), (1,-1).
- * Their weights are the SO coefficients a_l (6/22, 3/22, 1/22; 2D 1/2, 1/4). */
+/* Half-links of the finite-difference scheme: one of each +-c pair of the 3x3x3
+ * neighbourhood, in the order x, y, z; (1,1,0), (1,-1,0), (1,0,1), (1,0,-1),
+ * (0,1,1), (0,1,-1); (1,1,1), (1,1,-1), (1,-1,1), (1,-1,-1).  2D: (1,0), (0,1),
+ * (1,1), (1,-1).  Their weights a_l are the class coefficients of the chosen
+ * Laplacian (SO: 6/22, 3/22, 1/22; 2D 1/2, 1/4); a link of weight 0 carries no
+ * noise. */
 static const int FD_LINKS3[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
                                      {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
                                      {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
 static const int FD_LINKS2[4][3] = {{1, 0, 0}, {0, 1, 0}, {1, 1, 0}, {1, -1, 0}};
 
-static double fd_link_weight(int dim, const int *cl)
+static double fd_link_weight(const ora_params *p, const int *cl)
 {
-    int cls = abs(cl[0]) + abs(cl[1]) + abs(cl[2]);
-    if (dim == 3) return cls == 1 ? 6.0 / 22.0 : cls == 2 ? 3.0 / 22.0 : 1.0 / 22.0;
-    return cls == 1 ? 0.5 : 0.25;
+    double a[4];
+    lap_class_weights(p->dim, p->laplacian, a);
+    return a[abs(cl[0]) + abs(cl[1]) + abs(cl[2])];
 }
 
 /* Finite-difference noise eta(r) of Eq. (etafdt).  The paper builds eta in
@@ -638,7 +670,8 @@ static double fd_link_weight(int dim, const int *cl)
  * law is produced in real space by independent link noises
  * zeta_l ~ N(0, 2 kT M a_l / dt) on the half-links, eta(r) = sum_l
  * [zeta_l(r - c_l) - zeta_l(r)], whose spectrum is sum_l 2 var_l (1 - cos q.c_l)
- * = -2 kT M L_SO(q); it is conservative by construction and needs no FFT. */
+ * = -2 kT M L(q) for the Laplacian L of class weights a_l (SO in the paper);
+ * it is conservative by construction and needs no FFT. */
 void ora_fd_noise(const ora_params *p, int64_t step, double *eta)
 {
     box_t g = box_of(p);
@@ -652,7 +685,7 @@ void ora_fd_noise(const ora_params *p, int64_t step, double *eta)
         double gs[16];
         ora_gaussians(p->seed, step, rng_site(p, x, y, z), 1u, (nl + 3) / 4, gs);
         for (int l = 0; l < nl; ++l)
-            zeta[(size_t)l * g.n + (size_t)s] = sqrt(2.0 * p->kT * p->M * fd_link_weight(p->dim, L[l])) * gs[l];
+            zeta[(size_t)l * g.n + (size_t)s] = sqrt(2.0 * p->kT * p->M * fd_link_weight(p, L[l])) * gs[l];
     }
     for (size_t s = 0; s < g.n; ++s) {
         int x, y, z;
@@ -680,10 +713,19 @@ static void fv_node_noise(const ora_params *p, const box_t *g, int64_t step, dou
 }
 
 /* Right-hand side of the semi-discrete order-parameter equation (advdiff).
- * noise: eta (FD) or xi (FV) held fixed over the step; u: frozen velocity.
- *  FD: R = M lap_SO(mu) - div_CD(u psi) + eta, with the conservative
+ * noise: eta (FD) or xi (FV, contrast) held fixed over the step; u: frozen velocity.
+ *  FD: R = M lap(mu) - div_CD(u psi) + eta, with the conservative
  *      central-difference advection of Sec. V.A.
- *  FV: R = div_FV(J), J = M grad_FV(mu) - u psi + xi (Eqs. fvdiff-fvgrad). */
+ *  FV: R = div_FV(J), J = M grad_FV(mu) - u psi + xi (Eqs. fvdiff-fvgrad).
+ *  Contrast (Sec. III, the Petschek-Metiu discretisation): R = M lap(mu)
+ *      - div_CD(u psi) + div_CD(xi), the node noise xi ~ N(0, 2 kT M) taken
+ *      through the central-difference divergence [div xi](r) = (1/2) sum_a
+ *      [xi_a(r + e_a) - xi_a(r - e_a)].  Reading: the paper names the method
+ *      but not its stencils; we take the plain nearest-neighbour ones, the
+ *      central difference for the divergence and the Laplacian chosen by
+ *      p->laplacian (CD, Eq. fdlap, for the method as published).  Its noise
+ *      spectrum 2 kT M sum_a sin^2 q_a differs from -2 kT M L(q), so the
+ *      equilibrium ratio is sum_a sin^2 q_a / (-L(q)) instead of 1. */
 static void psi_rhs(const ora_params *p, const box_t *g, const double *psi, const double *u, const double *noise,
                     double *R)
 {
@@ -691,23 +733,23 @@ static void psi_rhs(const ora_params *p, const box_t *g, const double *psi, cons
     const int advect = (p->coupling & 2) != 0;
     double *mu = (double *)malloc(sizeof(double) * N);
     ora_mu(p, psi, mu);
-    if (p->scheme == 0) {
+    if (p->scheme == 0 || p->scheme == 2) {
         double *lapmu = (double *)malloc(sizeof(double) * N);
-        ora_laplacian_so(p->dim, p->nx, p->ny, p->nz, mu, lapmu);
+        ora_laplacian(p->dim, p->laplacian, p->nx, p->ny, p->nz, mu, lapmu);
         for (size_t s = 0; s < N; ++s) {
             int x, y, z;
             coords(g, s, &x, &y, &z);
-            double adv = 0.0;
-            if (advect) {
-                for (int a = 0; a < g->dim; ++a) {
-                    int e[3] = {0, 0, 0};
-                    e[a] = 1;
-                    size_t sp = site_at(g, x + e[0], y + e[1], z + e[2]);
-                    size_t sm = site_at(g, x - e[0], y - e[1], z - e[2]);
-                    adv += 0.5 * (u[(size_t)a * N + sp] * psi[sp] - u[(size_t)a * N + sm] * psi[sm]);
-                }
+            double adv = 0.0, nz = 0.0;
+            for (int a = 0; a < g->dim; ++a) {
+                int e[3] = {0, 0, 0};
+                e[a] = 1;
+                size_t sp = site_at(g, x + e[0], y + e[1], z + e[2]);
+                size_t sm = site_at(g, x - e[0], y - e[1], z - e[2]);
+                if (advect) adv += 0.5 * (u[(size_t)a * N + sp] * psi[sp] - u[(size_t)a * N + sm] * psi[sm]);
+                if (p->scheme == 2 && noise) nz += 0.5 * (noise[(size_t)a * N + sp] - noise[(size_t)a * N + sm]);
             }
-            R[s] = p->M * lapmu[s] - adv + (noise ? noise[s] : 0.0);
+            if (p->scheme == 0 && noise) nz = noise[s];
+            R[s] = p->M * lapmu[s] - adv + nz;
         }
         free(lapmu);
     } else {
@@ -804,8 +846,10 @@ int ora_step(const ora_params *p, double *f, double *psi, double *u, int64_t ste
     if (!((p->dim == 3 && (p->q == 19 || p->q == 15)) || (p->dim == 2 && p->q == 9))) return -1;
     if (p->nx <= 0 || p->ny <= 0 || (p->dim == 3 && p->nz <= 0)) return -1;
     if (!(p->tau > 0.0) || !(p->integrator == 1 || p->integrator == 2 || p->integrator == 4) || p->scheme < 0 ||
-        p->scheme > 1)
+        p->scheme > 2)
         return -1;
+    double lw[4];
+    if (lap_class_weights(p->dim, p->laplacian, lw)) return -1;
     box_t g = box_of(p);
     const size_t N = g.n;
     double *mu = (double *)malloc(sizeof(double) * N);

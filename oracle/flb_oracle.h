@@ -19,7 +19,8 @@ typedef struct {
     double gamma_bulk;      /* NaN: same as shear (1 - omega) */
     double gamma_ghost;     /* 0: ghosts projected out before thermalisation */
     double kT, A, B, K, M;
-    int32_t scheme;         /* 0 finite difference, 1 finite volume */
+    int32_t scheme;         /* 0 finite difference, 1 finite volume, 2 the naive contrast
+                               scheme (node noise under a central-difference divergence) */
     int32_t integrator;     /* 1 Euler, 2 Heun */
     int32_t coupling;       /* bit 0: force -psi grad mu on the fluid; bit 1: advection of psi */
     int32_t lb_on;          /* 0: skip the lattice Boltzmann half (u stays as given) */
@@ -30,6 +31,8 @@ typedef struct {
     int32_t force_grad;     /* gradient of mu in the force: 1 central difference, 2 FV lattice
                                gradient, 0 the one matched to the psi scheme; 3 the
                                divergence of the order-parameter stress instead */
+    int32_t laplacian;      /* App. A stencil of mu and of the FD/contrast psi equation:
+                               0 SO, 1 CD, 2 PK, 3 LB (2D: SO or CD) */
 } ora_params;
 
 int ora_threads(void);
@@ -38,6 +41,7 @@ void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream, 
 int ora_lattice(int32_t dim, int32_t q, int32_t *c, double *w);
 int ora_moment_basis(int32_t dim, int32_t q, double *E, double *b);
 void ora_laplacian_so(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out);
+int ora_laplacian(int32_t dim, int32_t kind, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out);
 int ora_fv_laplacian(int32_t dim, int32_t q, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out);
 void ora_mu(const ora_params *p, const double *psi, double *mu);
 void ora_force(const ora_params *p, const double *psi, const double *mu, double *F);

@@ -52,6 +52,26 @@ def L_so_2d(q):
     return cx + cy + cx * cy - 3.0
 
 
+def L_cd_2d(q):
+    """5-point planar stencil (2D reading of Eq. fdlap): 2(c_x + c_y) - 4."""
+    cx, cy, _ = _cs(q)
+    return 2.0 * (cx + cy) - 4.0
+
+
+def L_kind(q, dim, kind):
+    """Symbol of the App. A stencil `kind` (0 SO, 1 CD, 2 PK, 3 LB) in dimension dim."""
+    if dim == 2:
+        return (L_so_2d, L_cd_2d)[kind](q)
+    return (L_so, L_cd, L_pk, L_lb)[kind](q)
+
+
+def cd_divergence_power(q, dim):
+    """|Gamma(q)|^2 of the central-difference divergence of Sec. III (omega_i = +-1/2
+    on the nearest neighbours, Gamma_a = i sin q_a): sum_a sin^2 q_a."""
+    sx, sy, sz = _sn(q)
+    return sx * sx + sy * sy + (sz * sz if dim == 3 else 0.0)
+
+
 def L_fv_d3q15(q):
     """Eq. (fvlapft), printed for the paper's D3Q15 lattice:
     -(1/9){[2 s_x + s_x c_y c_z]^2 + [2 s_y + s_y c_x c_z]^2 + [2 s_z + s_z c_x c_y]^2}."""
@@ -77,9 +97,10 @@ def L_fv(q, c, w):
 # ---- Sec. V: linearised psi dynamics ----------------------------------------
 def lam(q, p, L_mob):
     """Decay rate per step of a Fourier mode for B = 0 (Eq. strf):
-    lambda = M (-L_mob(q)) (A - K L_SO(q)) dt."""
-    Lso = L_so_2d(q) if p.dim == 2 else L_so(q)
-    return p.M * (-L_mob) * (p.A - p.K * Lso)
+    lambda = M (-L_mob(q)) (A - K L_mu(q)) dt, L_mu the stencil of mu (SO unless
+    p.laplacian says otherwise)."""
+    Lmu = L_kind(q, p.dim, getattr(p, "laplacian", 0))
+    return p.M * (-L_mob) * (p.A - p.K * Lmu)
 
 
 def amplification(z, integrator):
@@ -111,12 +132,17 @@ def discrete_variance_factor(lmb, integrator):
     return np.where(small, 1.0, 2.0 * lmb * S * S / np.where(small, 1.0, den))
 
 
-def static_structure_factor(q, p, L_mob, steps=None):
-    """<|psi~(q)|^2> = kT/(A - K L_SO(q)) (Eq. test2 with the lattice Laplacian),
+def static_structure_factor(q, p, L_mob, steps=None, noise_power=None):
+    """<|psi~(q)|^2> = kT/(A - K L_mu(q)) (Eq. test2 with the lattice Laplacian),
     times the discrete-time factor of the integrator; with a start from psi = 0
-    after `steps` steps, times (1 - g^(2 steps))."""
-    Lso = L_so_2d(q) if p.dim == 2 else L_so(q)
-    S = p.kT / (p.A - p.K * Lso)
+    after `steps` steps, times (1 - g^(2 steps)).  noise_power: the symbol P(q)
+    of a noise whose spectrum is 2 kT M P(q) rather than the -2 kT M L_mob(q)
+    that the fluctuation-dissipation theorem asks for (Sec. III, Eq.
+    FTorderpara); the spectrum then carries the equilibrium ratio P/(-L_mob)."""
+    Lmu = L_kind(q, p.dim, getattr(p, "laplacian", 0))
+    S = p.kT / (p.A - p.K * Lmu)
+    if noise_power is not None:
+        S = S * noise_power / np.where(L_mob == 0, 1.0, -L_mob)
     lmb = lam(q, p, L_mob)
     S = S * discrete_variance_factor(lmb, p.integrator)
     if steps is not None:

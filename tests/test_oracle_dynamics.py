@@ -237,16 +237,22 @@ def test_lyapunov_noise_free_coupled(scheme):
 
 
 # ----------------------------------------------------------------- psi half
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
-@pytest.mark.parametrize("scheme", [0, 1])
-@pytest.mark.parametrize("integrator", [1, 2, 4])
-def test_single_mode_exact_amplification(dim, q, scheme, integrator):
+AMP_CASES = [(dim, q, scheme, integ, 0) for dim, q in ((2, 9), (3, 19), (3, 15)) for scheme in (0, 1)
+             for integ in (1, 2, 4)]
+AMP_CASES += [(2, 9, 0, 2, 1), (3, 19, 0, 2, 1), (3, 19, 0, 4, 2), (3, 15, 0, 2, 3), (3, 19, 1, 2, 2),
+              (2, 9, 2, 2, 1), (3, 19, 2, 1, 1), (3, 15, 2, 4, 0)]
+
+
+@pytest.mark.parametrize("dim,q,scheme,integrator,lap", AMP_CASES)
+def test_single_mode_exact_amplification(dim, q, scheme, integrator, lap):
     # B = 0, no noise, u uniform: psi = Re[eps e^{iq.r}] is multiplied each step by
     # 1 + z (Euler), 1 + z + z^2/2 (Heun) or 1 + z + z^2/2 + z^3/6 + z^4/24 (RK4) with
-    # z = M L_mob(q) (A - K L_SO(q)) - i theta(q);  theta = sum_a u_a sin q_a (FD,
-    # central-difference advection) or u . G(q) (FV, Eq. fvft)
+    # z = M L_mob(q) (A - K L_mu(q)) - i theta(q);  theta = sum_a u_a sin q_a (FD
+    # and the contrast scheme, central-difference advection) or u . G(q) (FV, Eq.
+    # fvft); L_mu the App. A stencil of mu, L_mob that stencil (FD, contrast) or
+    # the FV Laplacian
     p = O.Params(dim=dim, q=q, nx=8, ny=6, nz=4, kT=0.0, A=0.07, B=0.0, K=0.05, M=0.3, scheme=scheme,
-                 integrator=integrator, coupling=2, tau=0.9)
+                 integrator=integrator, coupling=2, tau=0.9, laplacian=lap)
     c, w = O.lattice(dim, q)
     z, y, x = _coords(p)
     u0 = np.array([0.04, -0.03, 0.02 if dim == 3 else 0.0])
@@ -254,14 +260,14 @@ def test_single_mode_exact_amplification(dim, q, scheme, integrator):
         qv = 2 * np.pi * np.array([kv[0] / p.shape[2], kv[1] / p.shape[1], (kv[2] / p.shape[0]) if dim == 3 else 0.0])
         phase = qv[0] * x + qv[1] * y + qv[2] * z
         s = O.State.rest(p, psi=(1e-3 * np.cos(phase)).reshape(-1), u=np.repeat(u0[:, None], p.n, axis=1))
-        Lso = T.L_so(qv) if dim == 3 else T.L_so_2d(qv)
-        if scheme == 0:
-            Lm = Lso
+        Lmu = T.L_kind(qv, dim, lap)
+        if scheme != 1:
+            Lm = Lmu
             theta = float(np.sum(u0[:dim] * np.sin(qv[:dim])))
         else:
             Lm = T.L_fv(qv, c, w)
             theta = float(np.dot(u0, T.fv_gradient_symbol(qv, c, w)))
-        zz = p.M * Lm * (p.A - p.K * Lso) - 1j * theta
+        zz = p.M * Lm * (p.A - p.K * Lmu) - 1j * theta
         g = T.amplification(zz, integrator)
         nst = 7
         s.advance(nst)
@@ -327,6 +333,44 @@ def test_static_structure_factor_2d(scheme, integrator):
             sel = (qm >= lo) & (qm < lo + 0.6)
             if sel.sum() > 20:
                 assert abs(r[sel].mean() - 1) < 0.05, (lo, r[sel].mean())
+
+
+@pytest.mark.parametrize("dim,scheme", [(2, 2), (3, 2), (3, 0)])
+def test_contrast_scheme_equilibrium_ratio(dim, scheme):
+    # Sec. III (Fig. test1wrong): the naive discretisation (scheme 2, central-
+    # difference divergence of node noise with the CD Laplacian) gives the
+    # equilibrium ratio ER = S(q) / (kT/A) = sum_a sin^2 q_a / (-L_CD(q)), one only
+    # as q -> 0 (cos^2(q/2) along the diagonal); the FD scheme with the same
+    # Laplacian (scheme 0, link noise) keeps ER = 1.  Harmonic free energy
+    # (B = K = 0), diffusion alone, the paper's A and M.
+    n = 32 if dim == 2 else 10
+    p = O.Params(dim=dim, q=9 if dim == 2 else 19, nx=n, ny=n, nz=n, kT=1.0 / 3000.0, A=0.625, B=0.0, K=0.0,
+                 M=0.095, scheme=scheme, laplacian=1, integrator=2, coupling=0, lb_on=0, seed=5)
+    s = O.State.rest(p)
+    s.advance(300)
+    S = np.zeros(p.shape)
+    ns = 1200 if dim == 2 else 800
+    for _ in range(ns):
+        s.advance(2)
+        S += O.structure_factor(p, s.psi)
+    S /= ns
+    qg = T.q_grid(p.shape)
+    if dim == 2:
+        qg[..., 2] = 0
+    L = T.L_kind(qg, dim, 1)
+    P = T.cd_divergence_power(qg, dim) if scheme == 2 else None
+    th = T.static_structure_factor(qg, p, L, steps=s.step, noise_power=P)
+    mask = (-L > 1.0) & (th > 0.05 * p.kT / p.A)
+    r = S[mask] / th[mask]
+    assert abs(r.mean() - 1) < 0.03, r.mean()
+    er = (S * p.A / p.kT)[mask]
+    er_theory = (T.cd_divergence_power(qg, dim)[mask] / -L[mask]) if scheme == 2 else np.ones(mask.sum())
+    hi = er_theory < 0.6
+    if scheme == 2:
+        # where the naive theory predicts ER < 0.6 the measured ratio is far from 1
+        assert hi.sum() > 20 and er[hi].mean() < 0.65
+    else:
+        assert abs(er.mean() - 1) < 0.05
 
 
 @pytest.mark.slow

@@ -32,6 +32,27 @@ def test_so_laplacian_symbol_2d():
         assert np.allclose(out, T.L_so_2d(qv) * wave[0], atol=1e-13)
 
 
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_app_a_laplacian_symbols_3d(kind):
+    # each stencil of App. A (SO, CD, PK, LB) applied to cos(q.r) multiplies it by its
+    # printed Fourier transform, Eqs. (solapft), (fdlapft), (pklapft), (lblapft)
+    shape = (4, 6, 8)
+    for qv, wave in _plane_waves(shape):
+        out = O.laplacian(3, kind, wave)
+        assert np.allclose(out, T.L_kind(qv, 3, kind) * wave, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_planar_laplacian_symbols(kind):
+    # 2D readings: the planar SO stencil and the 5-point CD stencil
+    shape = (1, 6, 8)
+    for qv, wave in _plane_waves(shape):
+        out = O.laplacian(2, kind, wave[0])
+        assert np.allclose(out, T.L_kind(qv, 2, kind) * wave[0], atol=1e-13)
+    with pytest.raises(ValueError):
+        O.laplacian(2, 2, wave[0])
+
+
 def test_laplacian_symbols_limit():
     # every admissible stencil tends to -q^2 (Sec. III); the SO one to O(q^4)
     for qv in ([1e-3, 0, 0], [1e-3, 2e-3, -1e-3], [7e-4, 7e-4, 7e-4]):
@@ -76,11 +97,12 @@ def test_fv_laplacian_symbol_d3q19_d2q9(dim, q):
     assert abs(T.L_fv(qv, c, w) + np.dot(qv, qv)) < 1e-5 * np.dot(qv, qv)
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_fd_noise_covariance(dim):
-    # <|eta~(q)|^2> = -2 kT M L_SO(q)   (Eq. etafdt), estimated over 400 steps;
-    # each mode's estimator has relative s.d. 1/sqrt(400) (real-field pairs aside)
-    p = O.Params(dim=dim, q=19 if dim == 3 else 9, nx=8, ny=6, nz=4, kT=0.7, M=0.3)
+@pytest.mark.parametrize("dim,kind", [(2, 0), (3, 0), (2, 1), (3, 1), (3, 2), (3, 3)])
+def test_fd_noise_covariance(dim, kind):
+    # <|eta~(q)|^2> = -2 kT M L(q)   (Eq. etafdt with the chosen App. A stencil),
+    # estimated over 400 steps; each mode's estimator has relative s.d.
+    # 1/sqrt(400) (real-field pairs aside)
+    p = O.Params(dim=dim, q=19 if dim == 3 else 9, nx=8, ny=6, nz=4, kT=0.7, M=0.3, laplacian=kind)
     acc = np.zeros(p.shape)
     nsamp = 400
     for step in range(nsamp):
@@ -89,13 +111,38 @@ def test_fd_noise_covariance(dim):
         assert abs(eta.sum()) < 1e-12 * np.abs(eta).sum()     # conservative by construction
     acc /= nsamp
     qg = T.q_grid(p.shape)
-    L = T.L_so(qg) if dim == 3 else T.L_so_2d(qg)
+    L = T.L_kind(qg, dim, kind)
     expect = -2 * p.kT * p.M * L
     mask = np.abs(L) > 1e-12
     ratio = acc[mask] / expect[mask]
     assert abs(ratio.mean() - 1) < 4 / np.sqrt(nsamp * mask.sum() / 2)
     assert np.all(np.abs(ratio - 1) < 6 / np.sqrt(nsamp / 2))
     assert acc[0, 0, 0] < 1e-20
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_contrast_scheme_noise_covariance(dim):
+    # the naive scheme of Sec. III: node noise through the central-difference
+    # divergence, Gamma(q) = i sin q, so <|eta~(q)|^2> = 2 kT M sum_a sin^2 q_a
+    # (Eq. FTorderpara) -- not -2 kT M L(q); it vanishes where every q_a is 0 or pi
+    p = O.Params(dim=dim, q=19 if dim == 3 else 9, nx=8, ny=6, nz=4, kT=0.7, M=0.3, scheme=2, laplacian=1,
+                 A=0.0, K=0.0, coupling=0)
+    acc = np.zeros(p.shape)
+    nsamp = 400
+    zero = np.zeros(p.n)
+    u = np.zeros((3, p.n))
+    for step in range(nsamp):
+        eta = O.psi_rhs(p, zero, u, step=step, with_noise=True).reshape(p.shape)
+        acc += np.abs(np.fft.fftn(eta)) ** 2 / p.n
+        assert abs(eta.sum()) < 1e-12 * np.abs(eta).sum()
+    acc /= nsamp
+    qg = T.q_grid(p.shape)
+    expect = 2 * p.kT * p.M * T.cd_divergence_power(qg, dim)
+    mask = expect > 1e-12
+    ratio = acc[mask] / expect[mask]
+    assert abs(ratio.mean() - 1) < 4 / np.sqrt(nsamp * mask.sum() / 2)
+    assert np.all(np.abs(ratio - 1) < 6 / np.sqrt(nsamp / 2))
+    assert np.all(acc[~mask] < 1e-20)
 
 
 def test_mu_and_force():
