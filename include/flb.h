@@ -51,6 +51,7 @@ extern "C" {
 /* ---- enumerations ---- */
 #define FLB_FD 0               /* finite-difference psi scheme, Sec. V.A */
 #define FLB_FV 1               /* finite-volume psi scheme, Sec. V.B */
+#define FLB_NAIVE 2            /* the naive contrast scheme of Sec. III (see psi_scheme) */
 #define FLB_EULER 1            /* one-stage integrator */
 #define FLB_HEUN 2             /* two-stage (RK2) integrator, noise held fixed */
 #define FLB_RK4 4              /* classical fourth-order Runge-Kutta, noise held fixed */
@@ -65,6 +66,10 @@ extern "C" {
 #define FLB_FORCE_CD 1          /* central difference of Sec. IV */
 #define FLB_FORCE_FV 2          /* FV lattice gradient of Eq. (fvgrad) */
 #define FLB_FORCE_STRESS 3      /* F = -div sigma, the order-parameter stress of Eq. (muf) */
+#define FLB_LAP_SO 0           /* Shinozaki-Oono Laplacian, Eq. (solap) (the paper's runs) */
+#define FLB_LAP_CD 1           /* central-difference Laplacian, Eq. (fdlap) */
+#define FLB_LAP_PK 2           /* Patra-Karttunen Laplacian, Eq. (pklap) (3D only) */
+#define FLB_LAP_LB 3           /* lattice-Boltzmann Laplacian, Eq. (lblap) (3D only) */
 #define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
 #define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
 #define FLB_MODE_PERSISTENT 2  /* all replicas, n steps, one cooperative launch (FV, FP32 storage) */
@@ -72,7 +77,8 @@ extern "C" {
 
 /*
  * Parameters of one lattice (one replica).  Names follow the paper.
- *   dim, q      : 2 and 9 (D2Q9) or 3 and 19 (D3Q19).
+ *   dim, q      : 2 and 9 (D2Q9), 3 and 19 (D3Q19) or 3 and 15 (D3Q15, the
+ *                 lattice of the paper's own runs, Sec. VI).
  *   nx, ny, nz  : lattice size, each in [4, 4096] (nz is ignored and taken as 1
  *                 in 2D); nx*ny*nz < 2^31.
  *   rho0        : reference density, > 0 (the populations are stored as
@@ -86,7 +92,14 @@ extern "C" {
  *   kT          : temperature, >= 0 (0 switches all noise off).
  *   A, B, K, M  : free energy f = A/2 psi^2 + B/4 psi^4 + K/2 |grad psi|^2
  *                 (Eqs. Feng, feng) and mobility M >= 0.
- *   psi_scheme  : FLB_FD or FLB_FV.
+ *   psi_scheme  : FLB_FD, FLB_FV or FLB_NAIVE.  FLB_NAIVE is the Petschek-Metiu
+ *                 discretisation Sec. III contrasts with: node noise
+ *                 xi ~ N(0, 2 kT M) through the central-difference divergence,
+ *                 dpsi/dt = M lap mu - div_CD(u psi) + div_CD xi.  Its noise
+ *                 spectrum 2 kT M sum_a sin^2 q_a is not -2 kT M L(q), so it
+ *                 breaks the fluctuation-dissipation theorem at high q (the
+ *                 equilibrium ratio falls to sum_a sin^2 q_a / (-L(q))); it is
+ *                 there to show that failure.
  *   integrator  : FLB_EULER, FLB_HEUN or FLB_RK4 (the noise is drawn once per
  *                 step and held fixed in every stage, Sec. V).  FLB_RK4 runs in
  *                 FLB_MODE_PLAIN only.
@@ -112,7 +125,17 @@ extern "C" {
  *                 total momentum is then conserved exactly for B != 0 as well,
  *                 F = -psi grad mu + O(h^2), but the force is not the adjoint
  *                 of the psi advection (with FLB_FV, rough fields of amplitude
- *                 ~0.5 can go non-finite).
+ *                 ~0.5 can go non-finite).  Needs laplacian FLB_LAP_SO.
+ *   laplacian   : the App. A stencil of mu = A psi + B psi^3 - K lap psi and of
+ *                 the diffusion M lap mu of FLB_FD and FLB_NAIVE (whose link
+ *                 noise follows it, so FLB_FD keeps the fluctuation-dissipation
+ *                 theorem with any of them): FLB_LAP_SO (default), FLB_LAP_CD,
+ *                 FLB_LAP_PK or FLB_LAP_LB; 2D takes SO or CD.
+ * D3Q19 with FLB_LAP_SO and FLB_FD or FLB_FV, and D3Q15 with FLB_LAP_SO and
+ * FLB_FD, run the tiled 3D kernels; every other 3D combination (another
+ * Laplacian, FLB_NAIVE, FV on D3Q15) runs one-thread-per-site stencil kernels
+ * that keep mu, the noise increment and the FV flux in HBM, in
+ * FLB_MODE_PLAIN only.
  */
 typedef struct flb_params {
     int32_t dim, q;
@@ -125,14 +148,15 @@ typedef struct flb_params {
     int32_t sq_kmax;
     int32_t force_grad;
     int32_t sq_lags;
-    int32_t reserved;        /* set to 0 */
+    int32_t laplacian;
 } flb_params;
 
 typedef struct flb_handle flb_handle;
 
 /* Fill *p with the defaults: D3Q19 32^3, rho0 1, tau 0.8, gamma_bulk NaN,
  * gamma_ghost 0, kT 0, A 0.05, B 0, K 0.04, M 0.1, FV, Heun, FP32, coupling 3,
- * seed 1, sq_kmax 0, force_grad FLB_FORCE_MATCHED, sq_lags 0. */
+ * seed 1, sq_kmax 0, force_grad FLB_FORCE_MATCHED, sq_lags 0, laplacian
+ * FLB_LAP_SO. */
 void flb_params_default(flb_params *p);
 
 /* Device workspace needed for nrep replicas p[0..nrep-1]; 0 if any parameter

@@ -22,7 +22,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libflb.so")
 
 FLB_OK, FLB_EINVAL, FLB_ENOSPC, FLB_ECUDA, FLB_ENONFINITE, FLB_ETIMEOUT, FLB_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-FLB_FD, FLB_FV = 0, 1
+FLB_FD, FLB_FV, FLB_NAIVE = 0, 1, 2
+FLB_LAP_SO, FLB_LAP_CD, FLB_LAP_PK, FLB_LAP_LB = 0, 1, 2, 3
 FLB_EULER, FLB_HEUN, FLB_RK4 = 1, 2, 4
 FLB_F32_DEV, FLB_F16_DEV = 0, 1
 FLB_COUPLE_FORCE, FLB_COUPLE_ADVECT = 1, 2
@@ -45,7 +46,7 @@ class FlbParams(ctypes.Structure):
         ("storage", ctypes.c_int32), ("coupling", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("sq_kmax", ctypes.c_int32), ("force_grad", ctypes.c_int32),
-        ("sq_lags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("sq_lags", ctypes.c_int32), ("laplacian", ctypes.c_int32),
     ]
 
 

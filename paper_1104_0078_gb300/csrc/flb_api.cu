@@ -93,10 +93,9 @@ int axis_K(int n, int kmax) { return (kmax <= 0 || 2 * kmax + 1 >= n) ? n : 2 * 
 bool valid(const flb_params &p)
 {
     if (!((p.dim == 3 && (p.q == 19 || p.q == 15)) || (p.dim == 2 && p.q == 9))) return false;
-    // D3Q15: the finite-difference psi scheme (lattice independent) and the
-    // central-difference or stress force; the FV operators on the D3Q15
-    // neighbourhood are not built on the device
-    if (p.q == 15 && (p.psi_scheme != FLB_FD || p.force_grad == FLB_FORCE_FV)) return false;
+    if (p.laplacian < FLB_LAP_SO || p.laplacian > (p.dim == 3 ? FLB_LAP_LB : FLB_LAP_CD)) return false;
+    // the stress kernels evaluate lap psi with the SO stencil
+    if (p.force_grad == FLB_FORCE_STRESS && p.laplacian != FLB_LAP_SO) return false;
     const long long nz = p.dim == 3 ? p.nz : 1;
     if (p.nx < 4 || p.ny < 4 || (p.dim == 3 && p.nz < 4)) return false;
     if ((long long)p.nx * p.ny * nz >= (1LL << 31)) return false;
@@ -106,15 +105,49 @@ bool valid(const flb_params &p)
     if (!(std::fabs(p.gamma_ghost) < 1.0)) return false;
     if (!(p.kT >= 0) || !(p.M >= 0) || !std::isfinite(p.kT) || !std::isfinite(p.M)) return false;
     if (!std::isfinite(p.A) || !std::isfinite(p.B) || !std::isfinite(p.K)) return false;
-    if (p.psi_scheme != FLB_FD && p.psi_scheme != FLB_FV) return false;
+    if (p.psi_scheme != FLB_FD && p.psi_scheme != FLB_FV && p.psi_scheme != FLB_NAIVE) return false;
     if (p.integrator != FLB_EULER && p.integrator != FLB_HEUN && p.integrator != FLB_RK4) return false;
     if (p.storage != FLB_F32_DEV && p.storage != FLB_F16_DEV) return false;
     if (p.coupling < 0 || p.coupling > 3) return false;
     if (p.force_grad < FLB_FORCE_MATCHED || p.force_grad > FLB_FORCE_STRESS) return false;
     if (p.sq_kmax < 0) return false;
-    if (p.sq_lags < 0 || p.sq_lags > 4096 || p.reserved != 0) return false;
+    if (p.sq_lags < 0 || p.sq_lags > 4096) return false;
     if (p.nx > 4096 || p.ny > 4096 || (p.dim == 3 && p.nz > 4096)) return false;  // DFT twiddle tables
     return true;
+}
+
+// 3D combinations outside the tiled kernels (another Laplacian, the naive
+// scheme, FV on D3Q15) run the one-thread-per-site kernels of the 2D path.
+bool general_path(const flb_params &p)
+{
+    return p.dim == 3 && (p.laplacian != FLB_LAP_SO || p.psi_scheme == FLB_NAIVE ||
+                          (p.q == 15 && p.psi_scheme == FLB_FV));
+}
+
+// Class weights of the App. A Laplacians (faces, edges, corners; 2D axes and
+// diagonals), the centre weight closing the sum to zero.
+LapW lap_weights(int dim, int kind)
+{
+    LapW w{0.f, 0.f, 0.f, 0.f};
+    double a1, a2, a3 = 0.0, a0;
+    if (dim == 3) {
+        switch (kind) {
+        case FLB_LAP_CD: a1 = 1.0; a2 = 0.0; a3 = 0.0; break;
+        case FLB_LAP_PK: a1 = 14.0 / 30.0; a2 = 3.0 / 30.0; a3 = 1.0 / 30.0; break;
+        case FLB_LAP_LB: a1 = 1.0 / 9.0; a2 = 1.0 / 9.0; a3 = 1.0 / 9.0; break;
+        default: a1 = 6.0 / 22.0; a2 = 3.0 / 22.0; a3 = 1.0 / 22.0; break;
+        }
+        a0 = -(6.0 * a1 + 12.0 * a2 + 8.0 * a3);
+    } else {
+        if (kind == FLB_LAP_CD) { a1 = 1.0; a2 = 0.0; }
+        else { a1 = 0.5; a2 = 0.25; }
+        a0 = -(4.0 * a1 + 4.0 * a2);
+    }
+    w.c0 = (float)a0;
+    w.c1 = (float)a1;
+    w.c2 = (float)a2;
+    w.c3 = (float)a3;
+    return w;
 }
 
 Geom make_geom(const flb_params &p)
@@ -149,7 +182,7 @@ void carve_rep(Rep &r, Carver &cv)
         r.E = cv.take<float>(N);
     }
     if (r.p.integrator == FLB_RK4 && r.dim == 3) r.Dn = cv.take<float>(N);
-    if (r.dim == 2) {  // the 2D path keeps mu*, the noise increment and the FV flux in HBM
+    if (r.dim == 2 || general_path(r.p)) {  // the per-site path keeps mu*, the noise increment and the FV flux in HBM
         r.eta = cv.take<float>(N);
         if (r.p.integrator != FLB_EULER) r.mus = cv.take<float>(P);
         if (r.p.psi_scheme == FLB_FV) r.J = cv.take<float>((size_t)r.dim * P);
@@ -421,9 +454,9 @@ LBArgs lb_args(const Rep &r, float *psi_n)
     la.kT = (float)p.kT;
     std::memcpy(la.namp, r.namp, sizeof(la.namp));
     la.coupling = p.coupling;
-    la.force_kind = p.force_grad == FLB_FORCE_STRESS ? 2
-                    : (p.force_grad == FLB_FORCE_FV || (p.force_grad == FLB_FORCE_MATCHED && p.psi_scheme == FLB_FV)) ? 1
-                                                                                                                   : 0;
+    const bool fv_grad =
+        p.force_grad == FLB_FORCE_FV || (p.force_grad == FLB_FORCE_MATCHED && p.psi_scheme == FLB_FV);
+    la.force_kind = p.force_grad == FLB_FORCE_STRESS ? 2 : fv_grad ? (p.q == 15 ? 3 : 1) : 0;
     la.sig = r.sig;
     la.key = philox_key(p.seed);
     la.step = r.step;
@@ -498,23 +531,29 @@ int step_rep3(flb_handle *h, Rep &r)
 
 int step_rep(flb_handle *h, Rep &r)
 {
-    if (r.dim == 3) return step_rep3(h, r);
+    if (r.dim == 3 && !general_path(r.p)) return step_rep3(h, r);
+    // one-thread-per-site path: 2D, and the 3D combinations of general_path()
     const Geom &g = r.g;
     const flb_params &p = r.p;
     cudaStream_t st = h->st;
+    const LapW lw = lap_weights(r.dim, p.laplacian);
     float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
     const int64_t l0 = h->launches;
     cudaEvent_t e0 = mark(h);
-    FLB_TRY(launch_mu(g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
-    if ((p.coupling & FLB_COUPLE_FORCE) && p.force_grad == FLB_FORCE_STRESS)
-        FLB_TRY(launch_sigma2(g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
+    FLB_TRY(launch_mu(g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, lw, st));
+    if ((p.coupling & FLB_COUPLE_FORCE) && p.force_grad == FLB_FORCE_STRESS) {
+        if (r.dim == 3) FLB_TRY(launch_sigma3(g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
+        else FLB_TRY(launch_sigma2(g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
+    }
     cudaEvent_t e1 = mark(h);
 
     const LBArgs la = lb_args(r, psi_n);
-    FLB_TRY(launch_lb(la, r.q, p.storage, st));
+    if (r.dim == 3) FLB_TRY(r.q == 15 ? launch_lb15(la, p.storage, st) : launch_lb3d(la, p.storage, st));
+    else FLB_TRY(launch_lb(la, r.q, p.storage, st));
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
-    FLB_TRY(launch_vel2(la, p.storage, st));
+    if (r.dim == 3) FLB_TRY(r.q == 15 ? launch_vel15(la, p.storage, st) : launch_vel3(la, p.storage, st));
+    else FLB_TRY(launch_vel2(la, p.storage, st));
 
     const bool noisy = p.kT > 0 && p.M > 0;
     if (noisy) {
@@ -524,6 +563,8 @@ int step_rep(flb_handle *h, Rep &r)
         na.kT = (float)p.kT;
         na.M = (float)p.M;
         na.scheme = p.psi_scheme;
+        na.q = r.q;
+        na.lw = lw;
         na.key = philox_key(p.seed);
         na.step = r.step;
         FLB_TRY(launch_noise(na, st));
@@ -531,6 +572,8 @@ int step_rep(flb_handle *h, Rep &r)
     if (p.psi_scheme == FLB_FV) FLB_TRY(launch_flux(g, r.q, psi_n, r.mu, r.u, r.J, (float)p.M, p.coupling, st));
     PsiArgs pa;
     pa.g = g;
+    pa.lw = lw;
+    pa.q = r.q;
     pa.psi = psi_n;
     pa.mu = r.mu;
     pa.u = r.u;
@@ -553,7 +596,7 @@ int step_rep(flb_handle *h, Rep &r)
         float *in[3] = {r.psis, psi_np1, r.psis};
         float *out[3] = {psi_np1, r.psis, psi_np1};
         for (int s = 0; s < 3; ++s) {
-            FLB_TRY(launch_mu(g, in[s], r.mus, (float)p.A, (float)p.B, (float)p.K, st));
+            FLB_TRY(launch_mu(g, in[s], r.mus, (float)p.A, (float)p.B, (float)p.K, lw, st));
             if (p.psi_scheme == FLB_FV)
                 FLB_TRY(launch_flux(g, r.q, in[s], r.mus, r.u, r.J, (float)p.M, p.coupling, st));
             pa.psi = in[s];
@@ -564,7 +607,7 @@ int step_rep(flb_handle *h, Rep &r)
         }
     }
     if (p.integrator == FLB_HEUN) {
-        FLB_TRY(launch_mu(g, r.psis, r.mus, (float)p.A, (float)p.B, (float)p.K, st));
+        FLB_TRY(launch_mu(g, r.psis, r.mus, (float)p.A, (float)p.B, (float)p.K, lw, st));
         if (p.psi_scheme == FLB_FV)
             FLB_TRY(launch_flux(g, r.q, r.psis, r.mus, r.u, r.J, (float)p.M, p.coupling, st));
         pa.psi = r.psis;
@@ -669,7 +712,9 @@ int take_status(flb_handle *h)
 bool batch_supported(const flb_handle *h)
 {
     for (const Rep &r : h->reps)
-        if (r.dim != 3 || r.q != 19 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4) return false;
+        if (r.dim != 3 || r.q != 19 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4 ||
+            r.p.laplacian != FLB_LAP_SO)
+            return false;
     return !h->reps.empty();
 }
 
@@ -1408,7 +1453,7 @@ int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
     } else {
         std::map<std::string, int> done;
         for (Rep &r : h->reps) {
-            if (r.dim != 3) continue;
+            if (r.dim != 3 || general_path(r.p)) continue;
             const std::string key = "plain|" + dk + "|" + rep_key(r);
             auto d = done.find(key);
             if (d != done.end()) {

@@ -178,14 +178,23 @@ struct LBArgs {
     float kT;
     float namp[16];            // sqrt((1 - gamma_k^2)/b_k) of the noisy modes, in noise order
     int coupling;
-    int force_kind;            // 0: -psi grad_CD mu, 1: -psi grad_FV mu, 2: -div sigma (stress form)
+    int force_kind;            // 0: -psi grad_CD mu, 1: -psi grad_FV mu (D3Q19), 2: -div sigma (stress
+                               // form), 3: -psi grad_FV mu on the D3Q15 neighbourhood
     const float *sig;          // stress form: padded sigma planes xx, yy, zz, xy, xz, yz (2D: xx, yy, xy)
     PhiloxKey key;
     int64_t step;
 };
 
+// A Laplacian stencil of App. A by neighbour class: c0 at the centre, c1 on the
+// faces, c2 on the edges, c3 on the corners (2D: c1 axes, c2 diagonals).
+struct LapW {
+    float c0, c1, c2, c3;
+};
+
 struct PsiArgs {
     Geom g;
+    LapW lw;               // FD / naive: the Laplacian of mu and of M lap mu
+    int q;                 // FV: the lattice of the gradient and divergence (9, 15 or 19)
     const float *psi;      // padded psi at the stage input
     const float *mu;       // padded mu of that psi, valid to halo 2
     const float *u;        // padded u, valid to halo 1
@@ -207,6 +216,8 @@ struct NoiseArgs {
     float *eta;            // [N]
     float kT, M;
     int scheme;
+    int q;                 // FV: lattice of the noise divergence
+    LapW lw;               // FD: link weights are the Laplacian's class coefficients
     PhiloxKey key;
     int64_t step;
 };
@@ -302,7 +313,8 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,
                            cudaStream_t st);
-cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t s);
+cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, const LapW &lw,
+                      cudaStream_t s);
 cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s);
 cudaError_t launch_flux(const Geom &g, int q, const float *psi, const float *mu, const float *u, float *J, float M,
                         int coupling, cudaStream_t s);

@@ -104,7 +104,21 @@ __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, flo
     const float dx = ldf<COH>(mu + pi + 1) - ldf<COH>(mu + pi - 1);
     const float dy = ldf<COH>(mu + pi + sy) - ldf<COH>(mu + pi - sy);
     const float dz = ldf<COH>(mu + pi + sz) - ldf<COH>(mu + pi - sz);
-    if (a.force_kind == 1) {
+    if (a.force_kind == 3) {
+        // FV gradient on the D3Q15 neighbourhood: w = 1/9 (faces), 1/72 (corners),
+        // so (1/c_s^2) sum_i w_i c_i mu(r + c_i) = (face difference)/3 + (sum of
+        // the 8 corners signed by c_a)/24
+        const float ppp = ldf<COH>(mu + pi + 1 + sy + sz), ppm = ldf<COH>(mu + pi + 1 + sy - sz);
+        const float pmp = ldf<COH>(mu + pi + 1 - sy + sz), pmm = ldf<COH>(mu + pi + 1 - sy - sz);
+        const float mpp = ldf<COH>(mu + pi - 1 + sy + sz), mpm = ldf<COH>(mu + pi - 1 + sy - sz);
+        const float mmp = ldf<COH>(mu + pi - 1 - sy + sz), mmm = ldf<COH>(mu + pi - 1 - sy - sz);
+        const float cx = ((ppp + ppm) + (pmp + pmm)) - ((mpp + mpm) + (mmp + mmm));
+        const float cy = ((ppp + ppm) + (mpp + mpm)) - ((pmp + pmm) + (mmp + mmm));
+        const float cz = ((ppp + pmp) + (mpp + mmp)) - ((ppm + pmm) + (mpm + mmm));
+        Fx = -ps * (dx * (1.0f / 3.0f) + cx * (1.0f / 24.0f));
+        Fy = -ps * (dy * (1.0f / 3.0f) + cy * (1.0f / 24.0f));
+        Fz = -ps * (dz * (1.0f / 3.0f) + cz * (1.0f / 24.0f));
+    } else if (a.force_kind == 1) {
         // FV gradient (1/c_s^2) sum_i w_i c_i mu(r + c_i), Eq. (fvgrad): with
         // w = 1/18 (faces), 1/36 (edges) it is [2 (face difference) + sum of
         // the 8 edge neighbours signed by c_a] / 12

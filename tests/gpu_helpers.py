@@ -21,6 +21,7 @@ def flb_params(d: dict, **kw) -> F.FlbParams:
     p.psi_scheme = d.get("scheme", 1)
     p.integrator = d.get("integrator", 2)
     p.storage = d.get("storage", F.FLB_F32_DEV)
+    p.laplacian = d.get("laplacian", 0)
     p.coupling = d.get("coupling", 3)
     p.seed = d.get("seed", 1)
     p.sq_kmax = d.get("sq_kmax", 0)
@@ -35,7 +36,7 @@ def oracle_params(d: dict, **kw) -> O.Params:
                     rho0=d.get("rho0", 1.0), tau=d["tau"], gamma_bulk=d.get("gamma_bulk", float("nan")),
                     gamma_ghost=d.get("gamma_ghost", 0.0), kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
                     scheme=d.get("scheme", 1), integrator=d.get("integrator", 2), coupling=d.get("coupling", 3),
-                    seed=d.get("seed", 1), force_grad=d.get("force_grad", 0))
+                    seed=d.get("seed", 1), force_grad=d.get("force_grad", 0), laplacian=d.get("laplacian", 0))
 
 
 def field_error(gpu, ora, eq=0.0):

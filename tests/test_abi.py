@@ -82,23 +82,33 @@ def test_defaults_and_workspace_sizing(lib):
 
 
 @pytest.mark.parametrize("field,value", [("nx", 3), ("q", 17), ("q", 27), ("tau", 0.0), ("gamma_ghost", 1.0), ("kT", -1.0),
-                                         ("psi_scheme", 2), ("integrator", 3), ("storage", 2), ("coupling", 4),
+                                         ("psi_scheme", 3), ("integrator", 3), ("storage", 2), ("coupling", 4),
                                          ("M", -0.1), ("sq_kmax", -1), ("force_grad", 4), ("force_grad", -1),
-                                         ("sq_lags", -1), ("sq_lags", 5000), ("reserved", 1)])
+                                         ("sq_lags", -1), ("sq_lags", 5000), ("laplacian", 4),
+                                         ("laplacian", -1), ("psi_scheme", -1)])
 def test_invalid_parameters_rejected(lib, field, value):
     p = F.flb_params_default(**{field: value})
     assert F.flb_workspace_bytes(p) == 0
 
 
-def test_d3q15_accepted_with_the_fd_scheme_only(lib):
+def test_d3q15_and_stencil_options(lib):
     fd = dict(q=15, psi_scheme=F.FLB_FD)
     assert F.flb_workspace_bytes(F.flb_params_default(**fd)) > 2 * 15 * 32 ** 3 * 4
     assert F.flb_workspace_bytes(F.flb_params_default(**fd, force_grad=F.FLB_FORCE_STRESS)) > 0
     assert F.flb_workspace_bytes(F.flb_params_default(**fd, integrator=F.FLB_RK4)) > 0
-    # the FV operators on the D3Q15 neighbourhood are not on the device
-    assert F.flb_workspace_bytes(F.flb_params_default(q=15)) == 0
-    assert F.flb_workspace_bytes(F.flb_params_default(**fd, force_grad=F.FLB_FORCE_FV)) == 0
+    assert F.flb_workspace_bytes(F.flb_params_default(**fd, force_grad=F.FLB_FORCE_FV)) > 0
+    assert F.flb_workspace_bytes(F.flb_params_default(q=15)) > 0             # FV on D3Q15: per-site kernels
     assert F.flb_workspace_bytes(F.flb_params_default(**fd, dim=2, nz=1)) == 0
+    # every App. A Laplacian in 3D, SO and CD in 2D; the naive scheme in both
+    for lap in (F.FLB_LAP_CD, F.FLB_LAP_PK, F.FLB_LAP_LB):
+        assert F.flb_workspace_bytes(F.flb_params_default(laplacian=lap)) > 0
+    d2 = dict(dim=2, q=9, nz=1)
+    assert F.flb_workspace_bytes(F.flb_params_default(**d2, laplacian=F.FLB_LAP_CD)) > 0
+    assert F.flb_workspace_bytes(F.flb_params_default(**d2, laplacian=F.FLB_LAP_PK)) == 0
+    assert F.flb_workspace_bytes(F.flb_params_default(**d2, psi_scheme=F.FLB_NAIVE)) > 0
+    assert F.flb_workspace_bytes(F.flb_params_default(psi_scheme=F.FLB_NAIVE, laplacian=F.FLB_LAP_CD)) > 0
+    # the stress kernels use the SO stencil
+    assert F.flb_workspace_bytes(F.flb_params_default(force_grad=F.FLB_FORCE_STRESS, laplacian=F.FLB_LAP_CD)) == 0
     # D3Q15 needs fewer population planes than D3Q19
     assert F.flb_workspace_bytes(F.flb_params_default(**fd)) < \
         F.flb_workspace_bytes(F.flb_params_default(psi_scheme=F.FLB_FD))

@@ -296,6 +296,28 @@ def test_minimum_box_and_errors():
     assert lib.flb_set_mode(s.h, 7) == F.FLB_EINVAL
 
 
+# The one-thread-per-site path: another App. A Laplacian, the naive scheme of
+# Sec. III, FV on D3Q15; and the tiled D3Q15 FD path with the explicit FV force
+STENCIL_CASES = [
+    (3, 19, 0, 2, dict(laplacian=1)), (3, 19, 0, 2, dict(laplacian=2)), (3, 19, 0, 4, dict(laplacian=3)),
+    (3, 19, 1, 2, dict(laplacian=1)), (3, 19, 2, 2, dict(laplacian=1)), (3, 19, 2, 1, dict(laplacian=0)),
+    (3, 15, 1, 2, {}), (3, 15, 1, 4, {}), (3, 15, 1, 1, dict(laplacian=2)), (3, 15, 2, 2, dict(laplacian=1)),
+    (3, 15, 0, 2, dict(force_grad=2)), (3, 15, 0, 2, dict(laplacian=3)),
+    (2, 9, 0, 2, dict(laplacian=1)), (2, 9, 2, 2, dict(laplacian=1)), (2, 9, 2, 4, {}),
+]
+
+
+@pytest.mark.parametrize("dim,q,scheme,integ,extra", STENCIL_CASES)
+def test_stencil_options_match_oracle(dim, q, scheme, integ, extra):
+    shape = (13, 10, 1) if dim == 2 else (11, 9, 7)
+    d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.8, kT=1e-4, A=-0.05, B=0.3, K=0.04, M=0.1,
+             scheme=scheme, integrator=integ, coupling=3, seed=17, **extra)
+    s, (fg, pg, ug), st, feq = _run_pair(d, 20, amp_psi=0.2)
+    assert field_error(fg, st.f, feq) < TOL
+    assert field_error(pg, st.psi) < TOL
+    assert field_error(ug[:dim], st.u[:dim]) < TOL
+
+
 def test_d3q15_fp16_storage_tracks_fp32():
     # FP16 deviations on D3Q15: the same seeded start advanced 40 steps stays within
     # the half-precision rounding of the FP32 path (unit roundoff 2^-11 on

@@ -108,6 +108,39 @@ def test_d3q15_order_parameter_fluctuations(coupling):
     assert np.all(np.abs(u2 / d["kT"] - 1) < 0.02)
 
 
+@pytest.mark.parametrize("scheme,lap", [(2, 1), (0, 1), (0, 2), (0, 3)])
+def test_equilibrium_ratio_by_scheme_and_laplacian(scheme, lap):
+    # Sec. III and App. A on the paper's D3Q15 32^3 fluctuation run (diffusion
+    # alone, Gaussian free energy): the naive scheme (central-difference divergence
+    # of node noise, CD Laplacian) follows ER = sum_a sin^2 q_a / (-L_CD(q)) and
+    # falls far below one at high q (Fig. test1wrong), while the FD scheme keeps
+    # ER = 1 with every App. A Laplacian (its link noise follows the stencil)
+    d = dict(I.WORKLOADS["fluct_d3q15"], integrator=2, coupling=0, scheme=scheme, laplacian=lap)
+    S, ns, u2, times = _measure(d, 10000, 1000, 10)
+    op = oracle_params(d)
+    qg = T.q_grid(op.shape)
+    L = T.L_kind(qg, 3, lap)
+    P = T.cd_divergence_power(qg, 3) if scheme == 2 else None
+    lmb = T.lam(qg, op, L)
+    g = T.amplification(-lmb, op.integrator)
+    trans = np.mean([1.0 - g ** (2 * t) for t in times], axis=0)
+    th = T.static_structure_factor(qg, op, L, noise_power=P) * trans
+    n_ind = np.minimum(2 * lmb * (times[-1] - times[0]), len(times))
+    S = S.reshape(32, 32, 32)
+    live = th > 0.05 * op.kT / op.A
+    _shell_check(np.where(live, S, 1.0), np.where(live, th, 1.0), np.where(live, n_ind, 0.0), qg, tol=0.03)
+    er = S * op.A / op.kT
+    if scheme == 2:
+        low = live & ((P / np.where(L == 0, 1, -L)) < 0.5)
+        assert low.sum() > 1000 and er[low].mean() < 0.55
+    else:
+        # the high-q half of the spectrum matches theory as a whole (ER = 1 up to
+        # the integrator's discrete-time factor, which th carries)
+        qm = np.sqrt((qg ** 2).sum(-1))
+        hi = qm > 2.0
+        assert abs((S[hi] / th[hi]).mean() - 1) < 0.02
+
+
 def test_galilean_invariance_small_mach():
     # Sec. VI.B: a uniform flow along the x = y diagonal at Ma = |u|/c_s = 0.08
     # leaves the static structure factor on the equilibrium theory (the bulk 3D
