@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default psi tile depth (64 planes)")
+    ap.add_argument("--variant-size", type=int, default=512,
+                    help="edge of the cubic box of the path variants (2D variant: 8x this edge)")
+    ap.add_argument("--variants", default="",
+                    help="comma-separated variant names to run (default: all)")
     ap.add_argument("--variant-steps", type=int, default=10,
                     help="steps timed for each variant of the path (FD scheme, FP16 storage, D2Q9); 0 skips them")
     ap.add_argument("--ensemble-steps", type=int, default=40,
@@ -205,23 +209,26 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
     return out
 
 
-def path_variants(F, I, local, steps, peak):
+def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
     """Throughput of the other forms of the path, each on its own handle after 3
-    warm-up steps, inputs larger than L2: the FD psi scheme, the FP16 storage
-    variant, the RK4 integrator, the stress-form force and the D3Q15 lattice (FD)
-    on the 512^3 quench, and the D2Q9 path on a 4096^2 quench (same free energy, FD as in the 2D
-    workload).  MLUPS and the fraction of the HBM roofline on the algorithmic
-    bytes of that form."""
+    warm-up steps, inputs larger than L2 at the default n = 512: the FD psi
+    scheme, the FP16 storage variant, the RK4 integrator, the stress-form force
+    and the D3Q15 lattice (FD) on the n^3 quench, and the D2Q9 path on an
+    (8n)^2 quench (same free energy, FD as in the 2D workload).  MLUPS and the
+    fraction of the HBM roofline on the algorithmic bytes of that form."""
     import torch
     d = dict(I.WORKLOADS["quench"])
+    cube = dict(nx=n, ny=n, nz=n)
     forms = [
-        ("fd_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FD), 160),
-        ("fp16_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, storage=F.FLB_F16_DEV), 84),
-        ("rk4_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, integrator=F.FLB_RK4), 160),
-        ("stress_force_512", dict(nx=512, ny=512, nz=512, psi_scheme=F.FLB_FV, force_grad=F.FLB_FORCE_STRESS), 160),
-        ("d3q15_fd_512", dict(q=15, nx=512, ny=512, nz=512, psi_scheme=F.FLB_FD), 128),
-        ("d2q9_4096", dict(dim=2, q=9, nx=4096, ny=4096, nz=1, psi_scheme=F.FLB_FD), 80),
+        (f"fd_{n}", dict(cube, psi_scheme=F.FLB_FD), 160),
+        (f"fp16_{n}", dict(cube, psi_scheme=F.FLB_FV, storage=F.FLB_F16_DEV), 84),
+        (f"rk4_{n}", dict(cube, psi_scheme=F.FLB_FV, integrator=F.FLB_RK4), 160),
+        (f"stress_force_{n}", dict(cube, psi_scheme=F.FLB_FV, force_grad=F.FLB_FORCE_STRESS), 160),
+        (f"d3q15_fd_{n}", dict(cube, q=15, psi_scheme=F.FLB_FD), 128),
+        (f"d2q9_{8 * n}", dict(dim=2, q=9, nx=8 * n, ny=8 * n, nz=1, psi_scheme=F.FLB_FD), 80),
     ]
+    if only:
+        forms = [f for f in forms if f[0].rsplit("_", 1)[0] in only]
     out = {}
     for key, kw, alg in forms:
         kw = {"integrator": F.FLB_HEUN, **kw}
@@ -230,7 +237,7 @@ def path_variants(F, I, local, steps, peak):
         N = p.nx * p.ny * p.nz
         s = F.Solver(p, device=f"cuda:{local}")
         s.set_fields(psi=I.uniform_field(N, -0.01, 0.01, 11))
-        if p.dim == 3:
+        if p.dim == 3 and autotune:
             s.autotune()
         s.step(3)
         s.synchronize()
@@ -362,7 +369,9 @@ def run_ours(args):
         ens = ensemble_batched_vs_plain(F, I, args.ensemble_steps, local, rank, autotune=not args.no_autotune)
     variants = None
     if args.variant_steps > 0 and rank == 0:
-        variants = path_variants(F, I, local, args.variant_steps, peak)
+        only = tuple(v for v in args.variants.split(",") if v)
+        variants = path_variants(F, I, local, args.variant_steps, peak, n=args.variant_size, only=only,
+                                 autotune=not args.no_autotune)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)

@@ -132,6 +132,33 @@ def discrete_variance_factor(lmb, integrator):
     return np.where(small, 1.0, 2.0 * lmb * S * S / np.where(small, 1.0, den))
 
 
+def noise_gain(z, integrator):
+    """Gain S of the step psi_{n+1} = R psi_n + S eta for dpsi/dt = z psi + eta with
+    eta held fixed over the step: S = (R - 1)/z, i.e. 1 (Euler), 1 + z/2 (Heun),
+    1 + z/2 + z^2/6 + z^3/24 (RK4)."""
+    if integrator == 1:
+        return np.ones_like(z)
+    if integrator == 4:
+        return 1.0 + z / 2.0 + z * z / 6.0 + z ** 3 / 24.0
+    return 1.0 + z / 2.0
+
+
+def advected_variance_factor(lmb, theta, integrator):
+    """Stationary variance of a mode with z = -lambda - i theta (decay lambda,
+    advection phase theta = u . Gamma(q) per step in a uniform flow, Sec. VI.B)
+    over the continuous-time equilibrium value: 2 lambda |S|^2 / (1 - |R|^2).
+    theta = 0 gives discrete_variance_factor; theta != 0 makes the factor depend
+    on the direction of q relative to the flow -- the anisotropy of the
+    high-Mach runs of Sec. VI.B."""
+    lmb = np.asarray(lmb, dtype=np.float64)
+    z = -lmb - 1j * np.asarray(theta, dtype=np.float64)
+    R = amplification(z, integrator)
+    S = noise_gain(z, integrator)
+    den = 1.0 - np.abs(R) ** 2
+    small = np.abs(lmb) < 1e-12
+    return np.where(small, 1.0, 2.0 * lmb * np.abs(S) ** 2 / np.where(small, 1.0, den))
+
+
 def static_structure_factor(q, p, L_mob, steps=None, noise_power=None):
     """<|psi~(q)|^2> = kT/(A - K L_mu(q)) (Eq. test2 with the lattice Laplacian),
     times the discrete-time factor of the integrator; with a start from psi = 0

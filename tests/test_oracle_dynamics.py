@@ -373,6 +373,39 @@ def test_contrast_scheme_equilibrium_ratio(dim, scheme):
         assert abs(er.mean() - 1) < 0.05
 
 
+def test_uniform_flow_fluctuations_follow_advected_theory():
+    # Sec. VI.B at high Mach number, psi alone in a frozen uniform flow along x = y
+    # (Ma 0.57): the stationary spectrum follows kT/(A - K L) times the advected
+    # discrete factor 2 lambda |S|^2/(1 - |R|^2), z = -lambda - i u.sin q (FD), and
+    # is anisotropic -- modes along the flow sit well above those across it
+    u = 0.57 * np.sqrt(1.0 / 3.0) / np.sqrt(2.0)
+    p = O.Params(dim=2, q=9, nx=32, ny=32, kT=1.0 / 3000.0, A=0.065, B=0.0, K=0.04, M=0.095, scheme=0,
+                 integrator=2, coupling=2, lb_on=0, seed=8)
+    s = O.State.rest(p, u=np.repeat(np.array([[u], [u], [0.0]]), p.n, axis=1))
+    s.advance(600)
+    S = np.zeros(p.shape)
+    ns = 2000
+    for _ in range(ns):
+        s.advance(2)
+        S += O.structure_factor(p, s.psi)
+    S /= ns
+    qg = T.q_grid(p.shape)
+    qg[..., 2] = 0
+    L = T.L_so_2d(qg)
+    lmb = T.lam(qg, p, L)
+    theta = u * (np.sin(qg[..., 0]) + np.sin(qg[..., 1]))
+    base = p.kT / (p.A - p.K * L)
+    g = T.amplification(-lmb - 1j * theta, 2)
+    th = base * T.advected_variance_factor(lmb, theta, 2) * (1.0 - np.abs(g) ** (2 * s.step))
+    mask = lmb > 0.01
+    r = S[mask] / th[mask]
+    assert abs(r.mean() - 1) < 0.02, r.mean()
+    excess = (th / (base * T.discrete_variance_factor(lmb, 2)))[mask]
+    along = excess > 1.08
+    assert along.sum() > 20
+    assert (S[mask][along] / (base * T.discrete_variance_factor(lmb, 2))[mask][along]).mean() > 1.06
+
+
 @pytest.mark.slow
 def test_static_structure_factor_coupled_3d():
     # full model H (FLBE + FV psi, Heun) on 10^3: S(q) within 3% of theory on

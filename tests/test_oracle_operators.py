@@ -281,6 +281,36 @@ def test_stress_force_second_order_consistency():
     assert errs[0] < 0.2 and 3.0 < errs[0] / errs[1] < 5.0, errs
 
 
+def test_advected_variance_factor_reduces_and_matches_iteration():
+    # theta = 0 is the plain discrete factor
+    lmb = np.linspace(0.001, 0.5, 40)
+    for integ in (1, 2, 4):
+        assert np.allclose(T.advected_variance_factor(lmb, 0.0, integ), T.discrete_variance_factor(lmb, integ),
+                           rtol=1e-12)
+    # brute force: iterate E|psi|^2 <- |R|^2 E|psi|^2 + |S|^2 for psi <- R psi + S eta
+    # with unit-variance eta, R and S from the stage formulas written out directly
+    for integ in (1, 2, 4):
+        for lm, th in ((0.05, 0.2), (0.02, 0.3), (0.3, 0.6), (0.01, 0.05)):
+            z = -lm - 1j * th
+            if integ == 1:
+                R, S = 1 + z, 1.0
+            elif integ == 2:
+                R, S = 1 + z + z * z / 2, 1 + z / 2
+            else:
+                R, S = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24, 1 + z / 2 + z * z / 6 + z ** 3 / 24
+            if abs(R) >= 1:        # Euler amplifies advected modes: no stationary state
+                assert integ == 1
+                continue
+            v = 0.0
+            for _ in range(20000):
+                v = abs(R) ** 2 * v + abs(S) ** 2
+            assert abs(v * 2 * lm - T.advected_variance_factor(lm, th, integ)) < 1e-9
+    # Heun: for small lambda the phase first lowers the factor, then theta^4/4 in
+    # |R|^2 raises it above one
+    f = T.advected_variance_factor(0.02, np.array([0.0, 0.1, 0.3]), 2)
+    assert f[1] < f[0] < 1.0 < f[2]
+
+
 def test_discrete_variance_factor_general_form():
     # The general stationary factor 2 lambda S^2 / (1 - R^2) (R the amplification,
     # S = (R - 1)/z the noise gain) reduces to the hand-derived Euler and Heun forms
