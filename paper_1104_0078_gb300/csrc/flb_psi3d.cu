@@ -27,6 +27,15 @@
 
 namespace flb {
 
+// The first two normals of one Philox block (only the (x,y) Box-Muller pair).
+__device__ __forceinline__ void normals2(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
+                                         uint32_t block, float g[2])
+{
+    const u32x4 r = philox4x32_10(
+        u32x4{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)}, K);
+    box_muller(r.x, r.y, g[0], g[1]);
+}
+
 __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 __device__ __forceinline__ int ring4(int p) { return p & 3; }  // two's complement: correct for negative p
 
@@ -91,8 +100,10 @@ __constant__ int8_t kFDL[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}
                                    {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
                                    {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
 
+// Two 512-thread blocks per SM (64 registers): with one, the noisy stage ran at
+// 25% of the warp slots and half of the issue rate.
 template <int STAGE, bool NOISE>
-__global__ void __launch_bounds__(PS_NT) psi3_fd_kernel(const Psi3Args a)
+__global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
 {
     extern __shared__ float smem[];
     float *sps = smem;           // [4][H3N]
@@ -133,21 +144,21 @@ __global__ void __launch_bounds__(PS_NT) psi3_fd_kernel(const Psi3Args a)
             }
             if (NOISE) {
                 const int zid = g.nx * g.ny * wrapi(q, g.nz);
+                // sqrt(2 kT M a_l) for the face, edge and corner half-links
+                const float s1 = sqrtf(2.0f * a.kT * a.M * (6.f / 22.f)), s2 = sqrtf(2.0f * a.kT * a.M * (3.f / 22.f));
+                const float s3 = sqrtf(2.0f * a.kT * a.M * (1.f / 22.f));
 #pragma unroll
                 for (int j = 0; j < S1; ++j) {
                     if (R.c1[j] < 0) continue;
                     const int k = threadIdx.x + j * PS_NT;
                     const uint32_t sid = (uint32_t)(R.n1[j] + zid);
-                    float G[16];
+                    float G[14];  // normals 0-12 of blocks 0-3 (block 3: its first pair only)
                     normals4(a.key, a.step, sid, 1u, 0u, G);
                     normals4(a.key, a.step, sid, 1u, 1u, G + 4);
                     normals4(a.key, a.step, sid, 1u, 2u, G + 8);
-                    normals4(a.key, a.step, sid, 1u, 3u, G + 12);
+                    normals2(a.key, a.step, sid, 1u, 3u, G + 12);
 #pragma unroll
-                    for (int l = 0; l < 13; ++l) {
-                        const float al = l < 3 ? 6.f / 22.f : (l < 9 ? 3.f / 22.f : 1.f / 22.f);
-                        sZ[l * H1N + k] = sqrtf(2.0f * a.kT * a.M * al) * G[l];
-                    }
+                    for (int l = 0; l < 13; ++l) sZ[l * H1N + k] = (l < 3 ? s1 : (l < 9 ? s2 : s3)) * G[l];
                 }
             }
         }
