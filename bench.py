@@ -61,6 +61,28 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The step time of the job: the slowest rank's (an all-reduce MAX of one
+    float; NCCL on the GPUs, any backend the process group has)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_sites: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job MLUPS: every rank advances its own n_sites replica `steps`
+    times (weak scaling), over the slowest rank's time in ms."""
+    return n_sites * steps * world / (ms / 1e3) / 1e6
+
+
+def replica_seeds(base_seed: int, rank: int):
+    """(Philox seed, psi0 seed) of this rank's replica: independent per rank."""
+    return base_seed + rank, 11 + rank
+
+
 def workload(size: int, storage: int):
     from paper_1104_0078_gb300 import inputs as I
     d = dict(I.WORKLOADS["quench"])
@@ -296,10 +318,10 @@ def run_ours(args):
     d, name = workload(args.size, storage)
     p = F.flb_params_default(nx=d["nx"], ny=d["ny"], nz=d["nz"], tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"],
                              K=d["K"], M=d["M"], psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, storage=storage,
-                             seed=d["seed"] + rank, sq_kmax=8)
+                             seed=replica_seeds(d["seed"], rank)[0], sq_kmax=8)
     N = p.nx * p.ny * p.nz
     s = F.Solver(p, device=f"cuda:{local}")
-    psi0 = I.uniform_field(N, -0.01, 0.01, 11 + rank)
+    psi0 = I.uniform_field(N, -0.01, 0.01, replica_seeds(d["seed"], rank)[1])
     s.set_fields(psi=psi0)
     zchunk = s.autotune()[0] if not args.no_autotune else s.get_tuning(0)
     s.set_sampling(10, 1)
@@ -329,11 +351,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     sampler.stop()
     clocks = sampler.summary(tw0, tw1)
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * args.steps * ws / (ms / 1e3) / 1e6
+    ms = max_over_ranks(ms, dist, f"cuda:{local}")
+    value = job_value(N, args.steps, ws, ms)
 
     # live per-kernel timing on the library's stream (CUDA events around each launch)
     s.set_profiling(True)

@@ -191,9 +191,10 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
                 const int pi = g.pidx32(x, y, z);
                 const int sy = g.px, sz = g.px * g.py;
                 const float *u = a.u;
-                const float adv = (u[pi + 1] * P0[cp + 1] - u[pi - 1] * P0[cp - 1]) +
-                                  (u[g.pn + pi + sy] * P0[cp + H3X] - u[g.pn + pi - sy] * P0[cp - H3X]) +
-                                  (u[2 * g.pn + pi + sz] * Pp[cp] - u[2 * g.pn + pi - sz] * Pm[cp]);
+                // u is read-only here: the read-only path keeps the row neighbours' lines
+                const float adv = (__ldg(u + pi + 1) * P0[cp + 1] - __ldg(u + pi - 1) * P0[cp - 1]) +
+                                  (__ldg(u + g.pn + pi + sy) * P0[cp + H3X] - __ldg(u + g.pn + pi - sy) * P0[cp - H3X]) +
+                                  (__ldg(u + 2 * g.pn + pi + sz) * Pp[cp] - __ldg(u + 2 * g.pn + pi - sz) * Pm[cp]);
                 D -= 0.5f * adv;
             }
             const int si = x + g.nx * (y + g.ny * z);
