@@ -342,6 +342,22 @@ int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts);
 int flb_structure_factor_noalloc(const float *psi_dev, int32_t nx, int32_t ny, int32_t nz, int32_t kmax,
                                  double *S_dev, void *cuda_stream);
 
+/* The standard normals the kernels draw (reading of the paper's noise: Philox
+ * counter-based normals, held fixed over each step's Runge-Kutta stages), for
+ * tests and for users who reproduce a run's noise elsewhere.  For sites
+ * site0 .. site0+nsites-1 and Philox blocks 0 .. nblocks-1 of (seed, step,
+ * stream) it writes dev_out[s*4*nblocks + 4*b + j], j = 0..3: Box-Muller on
+ * the words (x0, x1) and (x2, x3) of block b, each uniform ((x >> 9) + 1/2)
+ * 2^-23, g = sqrt(-2 ln u0) (cos, sin)(2 pi u1).  Stream 0 feeds the
+ * collide-stream (mode noise), stream 1 the psi equation; the site id of a
+ * lattice point is x + nx*(y + ny*z).
+ *   dev_out     : device pointer, FP32, nsites*4*nblocks values (caller-owned).
+ *   cuda_stream : cudaStream_t (NULL: legacy default stream); asynchronous.
+ * Errors: EINVAL (null dev_out, nsites < 0, nblocks outside [1, 16], stream >
+ * 0xFFFF, site0 + nsites > 2^32), ECUDA. */
+int flb_gaussians(uint64_t seed, int64_t step, uint32_t stream, uint32_t site0, int64_t nsites, int32_t nblocks,
+                  float *dev_out, void *cuda_stream);
+
 const char *flb_strerror(int code);
 
 /* Release the handle (not the caller's workspace or stream). */

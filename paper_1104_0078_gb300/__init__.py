@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH):
         "flb_kernel_times": (c_int, [H, dp, P(c_i64)]),
         "flb_structure_factor_noalloc": (c_int, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, vp, vp]),
+        "flb_gaussians": (c_int, [ctypes.c_uint64, c_i64, ctypes.c_uint32, ctypes.c_uint32, c_i64, ctypes.c_int32,
+                                  vp, vp]),
         "flb_strerror": (ctypes.c_char_p, [c_int]),
         "flb_destroy": (None, [H]),
     }
@@ -181,6 +183,17 @@ def flb_structure_factor(h, rep: int, which: int):
 
 
 # ---- convenience owner ------------------------------------------------------
+def gaussians(seed: int, step: int, stream: int, site0: int, nsites: int, nblocks: int, device="cuda"):
+    """The standard normals the kernels draw (flb_gaussians) as a torch tensor
+    (nsites, 4*nblocks) on `device`, computed on that device's current stream."""
+    import torch
+    out = torch.empty((nsites, 4 * nblocks), dtype=torch.float32, device=device)
+    st = torch.cuda.current_stream(out.device).cuda_stream
+    _check(load_library().flb_gaussians(seed, step, stream, site0, nsites, nblocks, out.data_ptr(), st),
+           "flb_gaussians")
+    return out
+
+
 class Solver:
     """One handle over nrep replicas, with its torch-owned workspace and stream."""
 

@@ -1595,6 +1595,37 @@ int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts)
     return FLB_OK;
 }
 
+namespace {
+__global__ void gaussians_kernel(const PhiloxKey K, int64_t step, uint32_t stream, uint32_t site0, long long n,
+                                 int nblocks, float *__restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int b = 0; b < nblocks; ++b) {
+        float G[4];
+        normals4(K, step, site0 + (uint32_t)i, stream, (uint32_t)b, G);
+        float *o = out + i * 4 * nblocks + 4 * b;
+        o[0] = G[0];
+        o[1] = G[1];
+        o[2] = G[2];
+        o[3] = G[3];
+    }
+}
+}  // namespace
+
+int flb_gaussians(uint64_t seed, int64_t step, uint32_t stream, uint32_t site0, int64_t nsites, int32_t nblocks,
+                  float *dev_out, void *cuda_stream)
+{
+    if (!dev_out || nsites < 0 || nblocks < 1 || nblocks > 16 || stream > 0xFFFFu ||
+        (uint64_t)site0 + (uint64_t)nsites > (1ull << 32))
+        return FLB_EINVAL;
+    if (nsites == 0) return FLB_OK;
+    const unsigned grid = (unsigned)((nsites + 255) / 256);
+    gaussians_kernel<<<grid, 256, 0, (cudaStream_t)cuda_stream>>>(philox_key(seed), step, stream, site0, nsites,
+                                                                   nblocks, dev_out);
+    return cuerr(cudaGetLastError());
+}
+
 const char *flb_strerror(int code)
 {
     switch (code) {

@@ -61,13 +61,144 @@ __device__ __forceinline__ float u01(uint32_t x)
     return __int_as_float((x >> 9) | 0x3f800000u) - __int_as_float(0x3f7fffffu);
 }
 
+// ---- Box-Muller by table lookup --------------------------------------------
+// The two transcendental steps of Box-Muller, specialised to the uniforms
+// above (24-bit odd multiples of 2^-24 for the radius, 23-bit ones for the
+// angle) and evaluated from small tables, to single-precision accuracy with
+// fewer instructions than the general logf and sincospif:
+//  * ln u, u = (2k+1) 2^-24: the table-driven method of P. T. P. Tang (ACM
+//    TOMS 16(4), 1990).  2k+1 = 2^e f with f in [sqrt(1/2), sqrt(2)); the bits
+//    of f select one of 32 cells; ln f = -ln r_j + ln(1 + d) with d = f r_j - 1
+//    formed by one FMA (|d| < 1/64) and ln(1 + d) by its series to d^5 (error
+//    < 3e-12).  r_j is near 1/(cell centre) and exactly 1 in the cell holding 1,
+//    where d = f - 1 is exact, so u near 1 keeps its relative accuracy.
+//  * sin, cos of 2 pi t, t = (m + 1/2) 2^-23: t = j/64 + t_lo, the table of
+//    sin, cos(2 pi j/64) and the angle-addition formulas with sin b, cos b of
+//    b = 2 pi t_lo < 2 pi/64 by their series (to b^5 and b^4; error < 2e-9).
+// The tables are computed at compile time in double precision from the same
+// series and rounded to float.
+namespace bm {
+
+struct alignas(8) SinCos {
+    float s, c;
+};
+struct alignas(8) LogCell {
+    float r, nlr;  // r_j and -ln r_j
+};
+struct Tables {
+    SinCos sc[64];
+    LogCell lg[32];
+};
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr uint32_t kSqrtHalfBits = 0x3F3504F3u;  // bits of sqrt(1/2) in binary32
+
+// sin and cos of x in [0, pi/2] by their Taylor series (x^31 terms: < 1e-25)
+constexpr double taylor_sin(double x)
+{
+    double term = x, sum = x;
+    for (int n = 1; n < 16; ++n) {
+        term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double taylor_cos(double x)
+{
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n < 16; ++n) {
+        term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+// ln x for x in [0.5, 2] as 2 atanh((x - 1)/(x + 1)) (|s| <= 1/3; 40 terms)
+constexpr double series_log(double x)
+{
+    const double s = (x - 1.0) / (x + 1.0);
+    double p = s, sum = 0.0;
+    for (int n = 0; n < 40; ++n) {
+        sum += p / (2.0 * n + 1.0);
+        p *= s * s;
+    }
+    return 2.0 * sum;
+}
+// the binary32 value with bits b, for b in [0x3F000000, 0x40000000)
+constexpr double f32_of_bits(uint32_t b)
+{
+    return b < 0x3F800000u ? 0.5 * (1.0 + (double)(b - 0x3F000000u) / 8388608.0)
+                           : 1.0 + (double)(b - 0x3F800000u) / 8388608.0;
+}
+constexpr Tables make_tables()
+{
+    Tables T{};
+    for (int j = 0; j < 64; ++j) {
+        const int q = j / 16;  // quadrant of 2 pi j/64
+        const double x = 2.0 * kPi * (j % 16) / 64.0;
+        const double s = taylor_sin(x), c = taylor_cos(x);
+        const double sq[4] = {s, c, -s, -c}, cq[4] = {c, -s, -c, s};
+        T.sc[j].s = (float)sq[q];
+        T.sc[j].c = (float)cq[q];
+    }
+    const int one = (int)((0x3F800000u - kSqrtHalfBits) >> 18);  // the cell holding 1
+    for (int j = 0; j < 32; ++j) {
+        if (j == one) {
+            T.lg[j].r = 1.0f;
+            T.lg[j].nlr = 0.0f;
+            continue;
+        }
+        const double lo = f32_of_bits(kSqrtHalfBits + ((uint32_t)j << 18));
+        const double hi = f32_of_bits(kSqrtHalfBits + ((uint32_t)(j + 1) << 18));
+        const float r = (float)(2.0 / (lo + hi));
+        T.lg[j].r = r;
+        T.lg[j].nlr = (float)(-series_log((double)r));
+    }
+    return T;
+}
+
+}  // namespace bm
+
+// one copy per translation unit, read through the read-only cache
+static __device__ const bm::Tables kBM = bm::make_tables();
+
+// ln u01-style radius uniform: ln(((a >> 9) + 1/2) 2^-23) = ln((2k+1) 2^-24)
+__device__ __forceinline__ float bm_log_u(uint32_t a)
+{
+    const float fn = __uint2float_rn(((a >> 9) << 1) | 1u);  // 2k+1 < 2^24, exact
+    const int bits = __float_as_int(fn);
+    const int t = bits - (int)bm::kSqrtHalfBits;
+    const int e = t >> 23;                                  // 2k+1 = 2^e f
+    const float f = __int_as_float(bits - (e << 23));       // f in [sqrt(1/2), sqrt(2))
+    const float2 L = __ldg(reinterpret_cast<const float2 *>(&kBM.lg[(t >> 18) & 31]));  // (r_j, -ln r_j)
+    const float d = fmaf(f, L.x, -1.0f);
+    float p = fmaf(d, 0.2f, -0.25f);
+    p = fmaf(d, p, 1.0f / 3.0f);
+    p = fmaf(d, p, -0.5f);
+    p = fmaf(d, p, 1.0f);
+    return fmaf((float)(e - 24), 0.693147180559945f, L.y) + d * p;
+}
+
+// sin and cos of 2 pi ((b >> 9) + 1/2) 2^-23
+__device__ __forceinline__ void bm_sincos_2pi_u(uint32_t b, float &s, float &c)
+{
+    const uint32_t m = b >> 9;
+    const float2 A = __ldg(reinterpret_cast<const float2 *>(&kBM.sc[m >> 17]));  // (sin, cos)(2 pi j/64)
+    const float x = fmaf((float)(m & 0x1FFFFu), (float)(2.0 * bm::kPi / 8388608.0), (float)(bm::kPi / 8388608.0));
+    const float x2 = x * x;
+    const float cb = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), 1.0f);
+    const float sb = x * fmaf(x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    const float sa = A.x, ca = A.y;
+    s = fmaf(sa, cb, ca * sb);
+    c = fmaf(ca, cb, -(sa * sb));
+}
+
 // Box-Muller: r = sqrt(-2 ln a), (r cos 2 pi b, r sin 2 pi b).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
 {
-    const float e = -2.0f * logf(u01(a));  // e >= 1.19e-7 > 0
+    const float e = -2.0f * bm_log_u(a);  // e >= 1.19e-7 > 0
     const float rad = e * rsqrtf(e);
     float s, c;
-    sincospif(2.0f * u01(b), &s, &c);
+    bm_sincos_2pi_u(b, s, c);
     g0 = rad * c;
     g1 = rad * s;
 }

@@ -34,7 +34,7 @@ __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int b
 }
 
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_kernel(const LBArgs a)
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, GHOST_RELAX ? 5 : 6) lb3_kernel(const LBArgs a)
 {
     lb3_block<T, GHOST_RELAX, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }

@@ -171,10 +171,8 @@ template <typename T, bool GHOST_RELAX, bool COH = false>
 __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
 {
     const Geom &g = a.g;
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int N = (int)g.n;
-    const int row = nx, pl = nx * ny;
-    const int s = x + row * y + pl * z;
+    const int s = x + g.nx * y + g.nx * g.ny * z;
     T *fout = (T *)a.fout;
 
     float f[19];
