@@ -1058,23 +1058,30 @@ int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *
     if (!r) return FLB_EINVAL;
     const Geom &g = r->g;
     const long long N = g.n;
+    cudaStream_t st = h->st;
+    // psi and u go up as interior FP32 fields, staged in the mu plane (free
+    // scratch between steps), and are padded with their images on the device
     std::vector<float> tmp((size_t)N);
-    for (long long s = 0; s < N; ++s) tmp[(size_t)s] = psi ? (float)psi[s] : 0.f;
-    int rc = upload_padded(h, g, r->psi[r->pcur], tmp.data());
-    for (int a = 0; a < r->dim && rc == FLB_OK; ++a) {
-        for (long long s = 0; s < N; ++s) tmp[(size_t)s] = u ? (float)u[a * N + s] : 0.f;
-        rc = upload_padded(h, g, r->u + (size_t)a * g.pn, tmp.data());
-    }
+    auto put = [&](const double *src, float *dst) -> int {
+        for (long long s = 0; s < N; ++s) tmp[(size_t)s] = (float)src[s];
+        int rc = cuerr(cudaMemcpyAsync(r->mu, tmp.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+        if (rc == FLB_OK) rc = cuerr(launch_pad(g, r->mu, dst, st));
+        ++h->launches;
+        return rc == FLB_OK ? cuerr(cudaStreamSynchronize(st)) : rc;  // tmp is reused
+    };
+    int rc = psi ? put(psi, r->psi[r->pcur]) : cuerr(cudaMemsetAsync(r->psi[r->pcur], 0, (size_t)g.pn * 4, st));
+    if (rc == FLB_OK && !u) rc = cuerr(cudaMemsetAsync(r->u, 0, (size_t)r->dim * g.pn * 4, st));
+    for (int a = 0; a < r->dim && rc == FLB_OK && u; ++a) rc = put(u + (size_t)a * N, r->u + (size_t)a * g.pn);
     if (rc == FLB_OK && rho) {
         for (long long s = 0; s < N; ++s) tmp[(size_t)s] = (float)rho[s];
-        rc = upload_padded(h, g, r->mu, tmp.data());  // mu is free scratch between steps
+        rc = upload_padded(h, g, r->mu, tmp.data());  // padded rho in the mu plane for init_eq
     }
     if (rc != FLB_OK) return rc;
     const cudaError_t e = launch_init_eq(g, r->q, r->p.storage, rho ? r->mu : nullptr, r->u, (float)r->p.rho0,
-                                         r->f[r->cur], h->st);
+                                         r->f[r->cur], st);
     ++h->launches;
     if (e != cudaSuccess) return FLB_ECUDA;
-    return cuerr(cudaStreamSynchronize(h->st));
+    return cuerr(cudaStreamSynchronize(st));
 }
 
 int flb_get_populations(flb_handle *h, int32_t rep, double *f)

@@ -248,6 +248,24 @@ __global__ void init_eq_kernel(const Geom g, int q, const float *__restrict__ rh
     }
 }
 
+// Padded plane (every ghost column, row and plane included) from an interior
+// field [N], x fastest: each padded cell takes its periodic image.
+__global__ void pad_kernel(const Geom g, const float *__restrict__ in, float *__restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.pn) return;
+    const int xp = (int)(i % g.px), yp = (int)((i / g.px) % g.py), zp = (int)(i / ((long long)g.px * g.py));
+    const int x = ((xp - GX) % g.nx + g.nx) % g.nx, y = ((yp - GY) % g.ny + g.ny) % g.ny;
+    const int z = g.dim == 3 ? ((zp - g.gz) % g.nz + g.nz) % g.nz : 0;
+    out[i] = in[x + (long long)g.nx * (y + (long long)g.ny * z)];
+}
+
+cudaError_t launch_pad(const Geom &g, const float *interior, float *padded, cudaStream_t st)
+{
+    pad_kernel<<<(unsigned)((g.pn + 255) / 256), 256, 0, st>>>(g, interior, padded);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,
                            cudaStream_t st)
 {
