@@ -337,6 +337,34 @@ def test_d3q15_fp16_storage_tracks_fp32():
     assert field_error(out[F.FLB_F16_DEV][1], out[F.FLB_F32_DEV][1]) < 1e-3
 
 
+@pytest.mark.parametrize("dim,q,shape", [(3, 19, (13, 9, 7)), (3, 15, (8, 11, 6)), (2, 9, (17, 6, 1))])
+def test_set_fields_equilibrium_and_fields(dim, q, shape):
+    # flb_set_fields with rho, u and psi: the populations are the second-order
+    # equilibrium of (rho, u) (Sec. IV) element by element, psi and u come back
+    # as given (FP32), and a coupled step from there still matches the oracle
+    d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1,
+             scheme=0, integrator=2, coupling=3, seed=23)
+    op = oracle_params(d)
+    N = op.n
+    rho = I.f32(1.0 + I.random_field(N, 0.01, 31))       # binary32-exact inputs on both sides
+    u = np.zeros((3, N))
+    u[:dim] = I.random_field(dim * N, 0.02, 32).reshape(dim, N)
+    psi = I.random_field(N, 0.1, 33)
+    s = F.Solver(flb_params(d))
+    s.set_fields(rho=rho, u=u[:dim], psi=psi)
+    feq = O.equilibrium(op, rho=rho, u=u)
+    w = weights_column(q) * op.rho0
+    # the device evaluates the equilibrium deviations in FP32 (a few ulp)
+    assert field_error(s.get_populations(), feq, w) < 2e-6
+    pg, ug = s.get_psi_u()
+    assert np.array_equal(pg, I.f32(psi)) and np.array_equal(ug[:dim], I.f32(u[:dim]))
+    s.step(5)
+    st = O.State(op, feq.copy(), psi.copy(), u.copy(), 0)
+    st.advance(5)
+    assert field_error(s.get_populations(), st.f, w) < TOL
+    assert field_error(s.get_psi_u()[0], st.psi) < TOL
+
+
 def test_nonfinite_is_reported():
     d = dict(dim=2, q=9, nx=8, ny=8, tau=1.0, kT=0.0, A=0.05, B=0.0, K=0.04, M=0.1, scheme=0, integrator=1)
     s = F.Solver(flb_params(d))
