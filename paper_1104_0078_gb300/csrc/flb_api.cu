@@ -18,6 +18,11 @@
 
 using namespace flb;
 
+namespace flb {
+// flb_lb.cu: padded plane (ghost frame of periodic images) from an interior field
+cudaError_t launch_pad(const Geom &g, const float *interior, float *padded, cudaStream_t st);
+}  // namespace flb
+
 namespace {
 
 // ---- velocity sets in the kernels' plane order ----------------------------

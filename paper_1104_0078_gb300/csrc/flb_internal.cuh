@@ -442,7 +442,6 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
                         int *status, cudaStream_t st);
 // mu on the interior and one ghost layer of a 3D box (flb_lb3d.cu)
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
-cudaError_t launch_pad(const Geom &g, const float *interior, float *padded, cudaStream_t st);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,
                            cudaStream_t st);
 cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, const LapW &lw,
