@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, GHOST_RELAX ? 5 : 6) lb3_
 
 // ---- batched variant: block b of the launch works on L.lb[b] -------
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb3_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, 4) lb3_batch_kernel(const BatchLists L)
 {
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
