@@ -54,6 +54,22 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxKey &K)
     return c;
 }
 
+// The same ten rounds with the round keys formed from round 0's (the seed
+// words) by one add per key and round: for kernels whose arguments sit in
+// shared memory, where reading the twenty stored keys costs a load each.
+__device__ __forceinline__ u32x4 philox4x32_10_r0(u32x4 c, uint32_t a, uint32_t b)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = u32x4{(uint32_t)(p1 >> 32) ^ c.y ^ a, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ b, (uint32_t)p0};
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return c;
+}
+
 // Uniform in (0,1): ((x >> 9) + 1/2) 2^-23, exact in binary32.  Built from the
 // bits: 1 + k 2^-23 (k = x >> 9) minus (1 - 2^-24) is exactly k 2^-23 + 2^-24.
 __device__ __forceinline__ float u01(uint32_t x)
@@ -204,11 +220,13 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, fl
 }
 
 // Four standard normals of one Philox block (Box-Muller on (x,y) and (z,w)).
+// KEY_R0: form the round keys from K's round-0 keys (arguments in shared memory).
+template <bool KEY_R0 = false>
 __device__ __forceinline__ void normals4(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
                                          uint32_t block, float g[4])
 {
-    const u32x4 r = philox4x32_10(
-        u32x4{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)}, K);
+    const u32x4 c{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)};
+    const u32x4 r = KEY_R0 ? philox4x32_10_r0(c, K.k0[0], K.k1[0]) : philox4x32_10(c, K);
     box_muller(r.x, r.y, g[0], g[1]);
     box_muller(r.z, r.w, g[2], g[3]);
 }

@@ -20,7 +20,7 @@ namespace flb {
 // consecutive x, so every population plane is read and written in full rows).
 
 // One block of the collide-stream (block coordinates bx, by, bz of the 32 x 4 x 2 grid).
-template <typename T, bool GHOST_RELAX, bool FORCE>
+template <typename T, bool GHOST_RELAX, bool FORCE, bool KEY_R0 = false>
 __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int bz)
 {
     const Geom &g = a.g;
@@ -30,7 +30,7 @@ __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int b
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3<false>(a, x, y, z, Fx, Fy, Fz);
-    lb_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
+    lb_site<T, GHOST_RELAX, false, KEY_R0>(a, x, y, z, Fx, Fy, Fz);
 }
 
 template <typename T, bool GHOST_RELAX, bool FORCE>
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, 4) lb3_batch_kernel(const
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
     batch_lb_args(L, L.reps[b.rep], sa);
-    lb3_block<T, GHOST_RELAX, FORCE>(sa, b.bx, b.by, b.bz);
+    lb3_block<T, GHOST_RELAX, FORCE, true>(sa, b.bx, b.by, b.bz);
 }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)

@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
                     if (task.phase == PH_LB) {
                         float Fx = 0.f, Fy = 0.f, Fz = 0.f;
                         if (force) force3<true>(sla, x, y, z, Fx, Fy, Fz);
-                        if (sla.gamma_g != 0.f) lb_site<float, true, true>(sla, x, y, z, Fx, Fy, Fz);
-                        else lb_site<float, false, true>(sla, x, y, z, Fx, Fy, Fz);
+                        if (sla.gamma_g != 0.f) lb_site<float, true, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                        else lb_site<float, false, true, true>(sla, x, y, z, Fx, Fy, Fz);
                     } else {
                         if (force) vel3_site<float, true, true>(sla, x, y, z);
                         else vel3_site<float, false, true>(sla, x, y, z);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
             __syncthreads();
             if (stage == 1) {
                 const CUtensorMap *pm = &r.map_psi[(int)(ds & 1)];
-                if (r.noise) psi3_fv_tma_block<1, true, true>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                if (r.noise) psi3_fv_tma_block<1, true, true, true>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
                 else psi3_fv_tma_block<1, false, true>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
             } else {
                 psi3_fv_tma_block<2, false, true>(&r.map_psis, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
     if (threadIdx.x == 0) psi_batch_args(r, ds, STAGE, sa);
     __syncthreads();
     const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[(int)(ds & 1)] : &r.map_psis;
-    psi3_fv_tma_block<STAGE, NOISE>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
+    psi3_fv_tma_block<STAGE, NOISE, false, true>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
 }
 
 __global__ void advance_kernel(long long *dstep) { *dstep += 1; }

@@ -117,7 +117,7 @@ constexpr int FV_NOISE_FLOATS = 6 * H1N;
 // Shared memory then holds only the current mu, flux and noise planes (two of
 // each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
 // formed, the flux of plane p-2, and the output of plane p-3 completes.
-template <int STAGE, bool NOISE, bool COH = false>
+template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false>
 __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
                                                   const Psi3Args &a, int *status, int bx, int by, int bz,
                                                   float *tsmem)
@@ -293,7 +293,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     J[2 * H1N + k] = jz;
                     if (NOISE) {
                         float Gn[4];
-                        normals4(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn);
+                        normals4<KEY_R0>(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn);
                         X[k] = sdx * Gn[0];
                         X[H1N + k] = sdx * Gn[1];
                         X[2 * H1N + k] = sdx * Gn[2];

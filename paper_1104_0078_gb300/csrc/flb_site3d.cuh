@@ -167,7 +167,8 @@ __device__ __forceinline__ void batch_lb_args(const BatchLists &L, const BatchRe
 }
 
 // One D3Q19 site: pull, moments, relaxation with force and noise, store.
-template <typename T, bool GHOST_RELAX, bool COH = false>
+// KEY_R0: the arguments sit in shared memory (batched and persistent kernels).
+template <typename T, bool GHOST_RELAX, bool COH = false, bool KEY_R0 = false>
 __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
 {
     const Geom &g = a.g;
@@ -239,10 +240,10 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     if (a.kT > 0.f) {
         float G[16];
         const uint32_t sid = (uint32_t)s;
-        normals4(a.key, a.step, sid, 0u, 0u, G);
-        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
-        normals4(a.key, a.step, sid, 0u, 2u, G + 8);
-        normals4(a.key, a.step, sid, 0u, 3u, G + 12);
+        normals4<KEY_R0>(a.key, a.step, sid, 0u, 0u, G);
+        normals4<KEY_R0>(a.key, a.step, sid, 0u, 1u, G + 4);
+        normals4<KEY_R0>(a.key, a.step, sid, 0u, 2u, G + 8);
+        normals4<KEY_R0>(a.key, a.step, sid, 0u, 3u, G + 12);
         const float mun = 3.0f * rho * a.kT;
         const float sq = mun * rsqrtf(mun);  // sqrt(rho kT / c_s^2), ~2 ulp
         float n[15];
