@@ -396,6 +396,41 @@ struct BatchBlock {
     int rep, bx, by, bz;
 };
 
+// Site of thread t of a row-packed block (the batched collide-stream and
+// velocity lists): the block's entry holds (x0, y0, z0) of its first site; a
+// box with nx <= 256 packs 256/nx whole x-rows into the block, a wider box takes
+// a 256-site chunk of one row.  Rows run y-fastest and are contiguous in the
+// population planes, so a warp's loads stay coalesced.  False for an idle thread.
+__device__ __forceinline__ bool packed_site(const Geom &g, const BatchBlock &b, int t, int &x, int &y, int &z)
+{
+    int rl = 0;
+    if (g.nx <= 256) {
+        rl = t / g.nx;
+        if (rl >= 256 / g.nx) return false;
+        x = t - rl * g.nx;
+    } else {
+        x = b.bx + t;
+        if (x >= g.nx) return false;
+    }
+    y = b.by + rl;
+    z = b.bz;
+    while (y >= g.ny) {
+        y -= g.ny;
+        ++z;
+    }
+    return z < g.nz;
+}
+
+// Entries of the row-packed list of one box (see packed_site).
+inline int packed_blocks(const Geom &g)
+{
+    if (g.nx <= 256) {
+        const int rpb = 256 / g.nx;
+        return (int)(((long long)g.ny * g.nz + rpb - 1) / rpb);
+    }
+    return g.ny * g.nz * ((g.nx + 255) / 256);
+}
+
 struct BatchLists {
     const BatchRep *reps;
     const BatchBlock *mu, *lb, *psi;

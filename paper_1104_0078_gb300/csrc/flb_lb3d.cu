@@ -20,7 +20,7 @@ namespace flb {
 // consecutive x, so every population plane is read and written in full rows).
 
 // One block of the collide-stream (block coordinates bx, by, bz of the 32 x 4 x 2 grid).
-template <typename T, bool GHOST_RELAX, bool FORCE, bool KEY_R0 = false>
+template <typename T, bool GHOST_RELAX, bool FORCE>
 __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int bz)
 {
     const Geom &g = a.g;
@@ -30,7 +30,7 @@ __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int b
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3<false>(a, x, y, z, Fx, Fy, Fz);
-    lb_site<T, GHOST_RELAX, false, KEY_R0>(a, x, y, z, Fx, Fy, Fz);
+    lb_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
 }
 
 template <typename T, bool GHOST_RELAX, bool FORCE>
@@ -39,14 +39,19 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, GHOST_RELAX ? 5 : 6) lb3_
     lb3_block<T, GHOST_RELAX, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// ---- batched variant: block b of the launch works on L.lb[b] -------
+// ---- batched variant: block b of the launch works on the row-packed entry L.lb[b] ----
 template <typename T, bool GHOST_RELAX, bool FORCE>
 __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, 4) lb3_batch_kernel(const BatchLists L)
 {
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
     batch_lb_args(L, L.reps[b.rep], sa);
-    lb3_block<T, GHOST_RELAX, FORCE, true>(sa, b.bx, b.by, b.bz);
+    int x, y, z;
+    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
+    if (!packed_site(sa.g, b, tid, x, y, z)) return;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if (FORCE && (sa.coupling & FLB_COUPLE_FORCE)) force3<false>(sa, x, y, z, Fx, Fy, Fz);
+    lb_site<T, GHOST_RELAX, false, true>(sa, x, y, z, Fx, Fy, Fz);
 }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)

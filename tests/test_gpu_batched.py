@@ -55,6 +55,21 @@ def test_batched_equals_plain(integrator):
         assert np.array_equal(pa, s.get_psi_u(r)[0])
 
 
+def test_batched_row_packing_of_wide_and_narrow_boxes_equals_plain():
+    # the batched collide-stream and velocity pack 256/nx whole rows per block
+    # (nx <= 256, here 4, 5 and 100: rows wrap into the next plane inside a
+    # block) or take 256-site chunks of a row (nx = 300: a full and a partial
+    # chunk); every field must still agree bitwise with the plain launches
+    shapes = [(4, 4, 5), (5, 7, 4), (100, 6, 5), (300, 4, 4)]
+    ps = [flb_params(dict(dim=3, q=19, nx=nx, ny=ny, nz=nz, tau=0.8, kT=2e-5, A=0.05, B=0.2, K=0.04, M=0.1,
+                          scheme=1, integrator=2, seed=300 + r)) for r, (nx, ny, nz) in enumerate(shapes)]
+    plain, _, _ = _run(F.FLB_MODE_PLAIN, ps, 5)
+    batched, _, _ = _run(F.FLB_MODE_BATCHED, ps, 5)
+    for (fa, pa, _), (fb, pb, _) in zip(plain, batched):
+        assert np.array_equal(fa, fb)
+        assert np.array_equal(pa, pb)
+
+
 def test_batched_stress_force_equals_plain():
     ps = _replicas(A=-0.05, B=0.3, force_grad=3)
     plain, _, _ = _run(F.FLB_MODE_PLAIN, ps, 6)
