@@ -299,7 +299,7 @@ size_t carve_all(flb_handle &h, char *base)
         if (r.dim != 3) continue;
         const Geom &g = r.g;
         nmu += ((g.nx + 2 + MU_BX - 1) / MU_BX) * ((g.ny + 2 + MU_BY - 1) / MU_BY) * ((g.nz + 2 + MU_ZC - 1) / MU_ZC);
-        nlb += packed_blocks(g);
+        nlb += packed_blocks(g, LB_BX * LB_BY * LB_BZ);
         npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC_MIN - 1) / PS_ZC_MIN);
     }
     h.b_nmu = nmu;
@@ -734,18 +734,9 @@ int batch_upload_lists(flb_handle *h)
                 for (int bx = 0; bx < (g.nx + 2 + MU_BX - 1) / MU_BX; ++bx) v.push_back({r, bx, by, bz});
     }
     const size_t nmu = v.size();
-    for (int r = 0; r < (int)h->reps.size(); ++r) {  // row-packed collide-stream / velocity blocks
-        const Geom &g = h->reps[(size_t)r].g;
-        if (g.nx <= 256) {
-            const int rpb = 256 / g.nx;
-            for (long long row = 0; row < (long long)g.ny * g.nz; row += rpb)
-                v.push_back({r, 0, (int)(row % g.ny), (int)(row / g.ny)});
-        } else {
-            for (int z = 0; z < g.nz; ++z)
-                for (int y = 0; y < g.ny; ++y)
-                    for (int x0 = 0; x0 < g.nx; x0 += 256) v.push_back({r, x0, y, z});
-        }
-    }
+    for (int r = 0; r < (int)h->reps.size(); ++r)  // row-packed collide-stream / velocity blocks
+        for_packed_blocks(h->reps[(size_t)r].g, LB_BX * LB_BY * LB_BZ,
+                          [&](int x0, int y0, int z0) { v.push_back({r, x0, y0, z0}); });
     const size_t nlb = v.size() - nmu;
     for (int r = 0; r < (int)h->reps.size(); ++r) {
         const Geom &g = h->reps[(size_t)r].g;

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_batch_kernel(const B
     batch_lb_args(L, L.reps[b.rep], sa);
     int x, y, z;
     const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    if (packed_site(sa.g, b, tid, x, y, z)) vel3_site<T, FORCE, false>(sa, x, y, z);
+    if (packed_site<LB_BX * LB_BY * LB_BZ>(sa.g, b.bx, b.by, b.bz, tid, x, y, z)) vel3_site<T, FORCE, false>(sa, x, y, z);
 }
 
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)

@@ -396,24 +396,27 @@ struct BatchBlock {
     int rep, bx, by, bz;
 };
 
-// Site of thread t of a row-packed block (the batched collide-stream and
-// velocity lists): the block's entry holds (x0, y0, z0) of its first site; a
-// box with nx <= 256 packs 256/nx whole x-rows into the block, a wider box takes
-// a 256-site chunk of one row.  Rows run y-fastest and are contiguous in the
-// population planes, so a warp's loads stay coalesced.  False for an idle thread.
-__device__ __forceinline__ bool packed_site(const Geom &g, const BatchBlock &b, int t, int &x, int &y, int &z)
+// Site k (0 <= k < B) of a row-packed block of B sites (the batched
+// collide-stream and velocity lists: B = 256, one site per thread; the
+// persistent kernel's tasks: B = 2048, four per thread).  The block starts at
+// (x0, y0, z0); a box with nx <= B packs B/nx whole x-rows into the block, a
+// wider box takes a B-site chunk of one row.  Rows run y-fastest and are
+// contiguous in the population planes, so a warp's loads stay coalesced.
+// False for an idle slot.
+template <int B>
+__device__ __forceinline__ bool packed_site(const Geom &g, int x0, int y0, int z0, int k, int &x, int &y, int &z)
 {
     int rl = 0;
-    if (g.nx <= 256) {
-        rl = t / g.nx;
-        if (rl >= 256 / g.nx) return false;
-        x = t - rl * g.nx;
+    if (g.nx <= B) {
+        rl = k / g.nx;
+        if (rl >= B / g.nx) return false;
+        x = k - rl * g.nx;
     } else {
-        x = b.bx + t;
+        x = x0 + k;
         if (x >= g.nx) return false;
     }
-    y = b.by + rl;
-    z = b.bz;
+    y = y0 + rl;
+    z = z0;
     while (y >= g.ny) {
         y -= g.ny;
         ++z;
@@ -421,14 +424,29 @@ __device__ __forceinline__ bool packed_site(const Geom &g, const BatchBlock &b, 
     return z < g.nz;
 }
 
-// Entries of the row-packed list of one box (see packed_site).
-inline int packed_blocks(const Geom &g)
+// Entries of the row-packed list of one box for blocks of B sites (see packed_site).
+inline int packed_blocks(const Geom &g, int B)
 {
-    if (g.nx <= 256) {
-        const int rpb = 256 / g.nx;
+    if (g.nx <= B) {
+        const int rpb = B / g.nx;
         return (int)(((long long)g.ny * g.nz + rpb - 1) / rpb);
     }
-    return g.ny * g.nz * ((g.nx + 255) / 256);
+    return g.ny * g.nz * ((g.nx + B - 1) / B);
+}
+
+// The entries themselves, as (x0, y0, z0), in list order.
+template <class F>
+inline void for_packed_blocks(const Geom &g, int B, F &&emit)
+{
+    if (g.nx <= B) {
+        const int rpb = B / g.nx;
+        for (long long row = 0; row < (long long)g.ny * g.nz; row += rpb)
+            emit(0, (int)(row % g.ny), (int)(row / g.ny));
+    } else {
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x0 = 0; x0 < g.nx; x0 += B) emit(x0, y, z);
+    }
 }
 
 struct BatchLists {

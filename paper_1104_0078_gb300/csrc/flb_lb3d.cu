@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, 4) lb3_batch_kernel(const
     batch_lb_args(L, L.reps[b.rep], sa);
     int x, y, z;
     const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    if (!packed_site(sa.g, b, tid, x, y, z)) return;
+    if (!packed_site<LB_BX * LB_BY * LB_BZ>(sa.g, b.bx, b.by, b.bz, tid, x, y, z)) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if (FORCE && (sa.coupling & FLB_COUPLE_FORCE)) force3<false>(sa, x, y, z, Fx, Fy, Fz);
     lb_site<T, GHOST_RELAX, false, true>(sa, x, y, z, Fx, Fy, Fz);

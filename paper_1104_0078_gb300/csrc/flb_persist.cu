@@ -25,8 +25,8 @@ namespace flb {
 
 namespace {
 
-constexpr int PB_NT = PS_NT;  // 512 threads: one psi tile, 32 x 4 x 16 LB sites, 32 x 16 mu columns
-constexpr int PL_BZ = 16;     // z extent of a collide-stream / velocity tile (4 sites per thread)
+constexpr int PB_NT = PS_NT;  // 512 threads: one psi tile, 2048 row-packed LB sites, 32 x 16 mu columns
+constexpr int PL_SITES = 2048; // sites of a row-packed collide-stream / velocity task (4 per thread)
 constexpr int PM_BY = 16;     // y extent of a mu tile
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -122,23 +122,19 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
             }
         } else if (task.phase == PH_LB || task.phase == PH_VEL) {
             lb_args_at(r, ds, sla);
-            const Geom &g = sla.g;
-            const int x = task.bx * 32 + (t & 31), y = task.by * 4 + ((t >> 5) & 3);
             const bool force = (sla.coupling & FLB_COUPLE_FORCE) != 0;
-            if (x < g.nx && y < g.ny) {
 #pragma unroll 1
-                for (int j = 0; j < PL_BZ / 4; ++j) {
-                    const int z = task.bz * PL_BZ + 4 * j + (t >> 7);
-                    if (z >= g.nz) break;
-                    if (task.phase == PH_LB) {
-                        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-                        if (force) force3<true>(sla, x, y, z, Fx, Fy, Fz);
-                        if (sla.gamma_g != 0.f) lb_site<float, true, true, true>(sla, x, y, z, Fx, Fy, Fz);
-                        else lb_site<float, false, true, true>(sla, x, y, z, Fx, Fy, Fz);
-                    } else {
-                        if (force) vel3_site<float, true, true>(sla, x, y, z);
-                        else vel3_site<float, false, true>(sla, x, y, z);
-                    }
+            for (int j = 0; j < PL_SITES / PB_NT; ++j) {
+                int x, y, z;
+                if (!packed_site<PL_SITES>(sla.g, task.bx, task.by, task.bz, t + PB_NT * j, x, y, z)) continue;
+                if (task.phase == PH_LB) {
+                    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+                    if (force) force3<true>(sla, x, y, z, Fx, Fy, Fz);
+                    if (sla.gamma_g != 0.f) lb_site<float, true, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                    else lb_site<float, false, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                } else {
+                    if (force) vel3_site<float, true, true>(sla, x, y, z);
+                    else vel3_site<float, false, true>(sla, x, y, z);
                 }
             }
         } else {
@@ -172,7 +168,7 @@ void persist_tiles(const Geom &g, int zc, int coupling, int heun, int counts[PH_
     counts[PH_MU] = (coupling & FLB_COUPLE_FORCE)
                         ? ((g.nx + 2 + 31) / 32) * ((g.ny + 2 + PM_BY - 1) / PM_BY) * ((g.nz + 2 + MU_ZC - 1) / MU_ZC)
                         : 0;
-    counts[PH_LB] = counts[PH_VEL] = cx * ((g.ny + 3) / 4) * ((g.nz + PL_BZ - 1) / PL_BZ);
+    counts[PH_LB] = counts[PH_VEL] = packed_blocks(g, PL_SITES);
     counts[PH_S1] = cx * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + zc - 1) / zc);
     counts[PH_S2] = heun ? counts[PH_S1] : 0;
 }
@@ -180,31 +176,33 @@ void persist_tiles(const Geom &g, int zc, int coupling, int heun, int counts[PH_
 // Append the tasks of phase ph of replica rep (need = tasks of rep listed before).
 void persist_tasks(std::vector<PTask> &v, int rep, int ph, const Geom &g, int zc, int need)
 {
+    auto push = [&](int bx, int by, int bz) {
+        PTask k;
+        k.rep = rep;
+        k.need = need;
+        k.bx = (short)bx;
+        k.by = (short)by;
+        k.bz = (short)bz;
+        k.phase = (char)ph;
+        k.pad = 0;
+        v.push_back(k);
+    };
+    if (ph == PH_LB || ph == PH_VEL) {  // row-packed: (x0, y0, z0) of each task's first site
+        for_packed_blocks(g, PL_SITES, push);
+        return;
+    }
     int ny, nz, nxb = (g.nx + 31) / 32;
     if (ph == PH_MU) {
         nxb = (g.nx + 2 + 31) / 32;
         ny = (g.ny + 2 + PM_BY - 1) / PM_BY;
         nz = (g.nz + 2 + MU_ZC - 1) / MU_ZC;
-    } else if (ph == PH_LB || ph == PH_VEL) {
-        ny = (g.ny + 3) / 4;
-        nz = (g.nz + PL_BZ - 1) / PL_BZ;
     } else {
         ny = (g.ny + PS_TY - 1) / PS_TY;
         nz = (g.nz + zc - 1) / zc;
     }
     for (int bz = 0; bz < nz; ++bz)
         for (int by = 0; by < ny; ++by)
-            for (int bx = 0; bx < nxb; ++bx) {
-                PTask k;
-                k.rep = rep;
-                k.need = need;
-                k.bx = (short)bx;
-                k.by = (short)by;
-                k.bz = (short)bz;
-                k.phase = (char)ph;
-                k.pad = 0;
-                v.push_back(k);
-            }
+            for (int bx = 0; bx < nxb; ++bx) push(bx, by, bz);
 }
 
 cudaError_t launch_persist(const PersistArgs &a, cudaStream_t st)

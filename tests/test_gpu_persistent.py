@@ -47,6 +47,23 @@ def _same(a, b):
             assert np.array_equal(x, y)
 
 
+def test_persistent_row_packing_equals_plain():
+    # collide-stream and velocity tasks are row-packed blocks of 2048 sites:
+    # narrow boxes pack 2048/nx rows that wrap into the next planes (nx = 4, 5,
+    # 100), a box wider than 2048 takes chunks of a row (nx = 2100: a full and a
+    # partial chunk)
+    shapes = [(4, 4, 5), (5, 7, 4), (100, 6, 5), (2100, 4, 4)]
+    ps = [flb_params(dict(dim=3, q=19, nx=nx, ny=ny, nz=nz, tau=0.8, kT=2e-5, A=0.05, B=0.2, K=0.04, M=0.1,
+                          scheme=1, integrator=2, seed=400 + r)) for r, (nx, ny, nz) in enumerate(shapes)]
+    out = {}
+    for mode in (F.FLB_MODE_PLAIN, F.FLB_MODE_PERSISTENT):
+        s = _solver(mode, ps)
+        s.step(5)
+        s.synchronize()
+        out[mode] = _fields(s, len(ps))
+    _same(out[F.FLB_MODE_PLAIN], out[F.FLB_MODE_PERSISTENT])
+
+
 @pytest.mark.parametrize("integrator", [1, 2])
 def test_persistent_equals_plain(integrator):
     ps = _replicas(integrator=integrator)
