@@ -209,6 +209,11 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
         const int s3 = s2 == 0 ? T_PSI_DEPTH - 1 : s2 - 1;
         (void)s1;
+        // Heun stage 2: the accumulator E of this iteration's output plane p-3 is
+        // loaded now, so that its latency hides behind the plane's work
+        float e_pre = 0.f;
+        if (STAGE == 2 && !a.rk4 && active && p - 3 >= z0)
+            e_pre = COH ? __ldcg(a.E + x + g.nx * (y + g.ny * (p - 3))) : a.E[x + g.nx * (y + g.ny * (p - 3))];
         // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
         if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
         waited_p = p;
@@ -334,7 +339,9 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 const int si = x + g.nx * (y + g.ny * z);
                 const float Dn = (STAGE == 1 && NOISE) ? dn * (1.f / 12.f) : 0.f;
                 const float pv = STAGE == 1 ? tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)] : 0.f;
-                store_padded(a.out, g, x, y, z, rk_stage_out<STAGE, COH>(a, x, y, z, si, pv, Dd, Dn), 3);
+                const float out = (STAGE == 2 && !a.rk4) ? e_pre + 0.5f * Dd
+                                                         : rk_stage_out<STAGE, COH>(a, x, y, z, si, pv, Dd, Dn);
+                store_padded(a.out, g, x, y, z, out, 3);
             }
         }
         r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
