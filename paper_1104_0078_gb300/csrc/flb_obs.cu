@@ -165,6 +165,60 @@ __global__ void dft_x_kernel(DftArgs a)
     a.X1[t] = make_float2(re, im);
 }
 
+// The same X1 for windows of Kx <= 32 on rows of nx <= 1024, one warp per
+// (y, z) row: the lanes load the row once (x = lane + 32 j, kept in
+// registers); for each kept k a lane starts from e^{-i k lane 2pi/nx} (a table
+// built per block) and steps to x + 32 by one complex rotation by
+// e^{-i 2pi 32 k / nx}; a shuffle reduction over the lanes completes X1.  The
+// rotations add ~1e-6 relative error after 32 steps, far below the FP64 S(q)
+// accumulation's statistical use.
+constexpr int DXW_KMAX = 32, DXW_NJ = 32, DXW_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * DXW_WARPS) dft_x_warp_kernel(DftArgs a)
+{
+    __shared__ float2 w0[DXW_KMAX][32];  // e^{-i 2pi k lane / nx} of every kept k
+    __shared__ float2 rot[DXW_KMAX];     // e^{-i 2pi 32 k / nx}
+    for (int e = threadIdx.x; e < a.Kx * 32; e += blockDim.x) {
+        const int jx = e / 32, l = e % 32, k = kval(jx, a.nx, a.Kx);
+        w0[jx][l] = twiddle(k, l, a.nx);
+        if (l == 0) rot[jx] = twiddle(k, 32, a.nx);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long row = (long long)blockIdx.x * DXW_WARPS + (threadIdx.x >> 5);
+    if (row >= (long long)a.ny * a.nz) return;
+    const int y = (int)(row % a.ny), z = (int)(row / a.ny);
+    const float *src = a.in + a.off + (long long)y * a.sy + (long long)z * a.sz;
+    float v[DXW_NJ];
+#pragma unroll
+    for (int j = 0; j < DXW_NJ; ++j) {
+        const int x = lane + 32 * j;
+        v[j] = x < a.nx ? src[x] : 0.f;
+    }
+    const int nj = (a.nx + 31) / 32;
+    for (int jx = 0; jx < a.Kx; ++jx) {
+        float2 w = w0[jx][lane];
+        const float2 r = rot[jx];
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int j = 0; j < DXW_NJ; ++j) {
+            if (j < nj) {
+                re = fmaf(v[j], w.x, re);
+                im = fmaf(v[j], w.y, im);
+                const float wx = w.x * r.x - w.y * r.y;
+                w.y = w.x * r.y + w.y * r.x;
+                w.x = wx;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) a.X1[row * a.Kx + jx] = make_float2(re, im);
+    }
+}
+
 // X2[(z*Ky + jy)*Kx + jx] = sum_y X1[(z*ny + y)*Kx + jx] e^{-i qy y}
 __global__ void dft_y_kernel(DftArgs a)
 {
@@ -245,7 +299,12 @@ cudaError_t launch_dft_accumulate(const DftArgs &a, cudaStream_t s)
     const int bs = 256;
     long long n1 = (long long)a.Kx * a.ny * a.nz, n2 = (long long)a.Kx * a.Ky * a.nz, n3 = (long long)a.Kx * a.Ky * a.Kz;
     if (a.nx > TW_MAX || a.ny > TW_MAX || a.nz > TW_MAX) return cudaErrorInvalidValue;
-    dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, sizeof(float2) * a.nx, s>>>(a);
+    if (a.Kx <= DXW_KMAX && a.nx <= 32 * DXW_NJ) {
+        const long long rows = (long long)a.ny * a.nz;
+        dft_x_warp_kernel<<<(unsigned)((rows + DXW_WARPS - 1) / DXW_WARPS), 32 * DXW_WARPS, 0, s>>>(a);
+    } else {
+        dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, sizeof(float2) * a.nx, s>>>(a);
+    }
     dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, sizeof(float2) * a.ny, s>>>(a);
     dft_z_acc_kernel<<<(unsigned)((n3 + bs - 1) / bs), bs, sizeof(float2) * a.nz, s>>>(a);
     return cudaGetLastError();
