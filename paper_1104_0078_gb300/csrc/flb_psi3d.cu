@@ -122,6 +122,25 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
     float accm = 0.f, acc0 = 0.f, accp = 0.f;  // eta of planes p-2, p-1, p
 
     for (int p = z0 - 2; p <= z1 + 1; ++p) {
+        // this iteration's output plane p-2: its global inputs (the Heun
+        // accumulator and the six advecting velocities) are loaded now, so that
+        // their latency hides behind the plane's stencil work
+        const int zo = p - 2;
+        const bool out_here = zo >= z0 && active;
+        float e_pre = 0.f, u_pre[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (out_here) {
+            if (STAGE == 2 && !a.rk4) e_pre = a.E[x + g.nx * (y + g.ny * zo)];
+            if (a.advect) {
+                const int pi = g.pidx32(x, y, zo);
+                const int sy = g.px, sz = g.px * g.py;
+                u_pre[0] = __ldg(a.u + pi + 1);
+                u_pre[1] = __ldg(a.u + pi - 1);
+                u_pre[2] = __ldg(a.u + g.pn + pi + sy);
+                u_pre[3] = __ldg(a.u + g.pn + pi - sy);
+                u_pre[4] = __ldg(a.u + 2 * g.pn + pi + sz);
+                u_pre[5] = __ldg(a.u + 2 * g.pn + pi - sz);
+            }
+        }
         __syncthreads();
         {
             const float *src = a.psi + (size_t)plane * (p + g.gz);
@@ -180,27 +199,24 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
             acc0 += in0 - own;
             accp += up;
         }
-        const int z = p - 2;
-        if (z >= z0 && active) {
+        const int z = zo;
+        if (out_here) {
             const float *mm = smu + ring3(z - 1) * H2N, *m0 = smu + ring3(z) * H2N, *mp = smu + ring3(z + 1) * H2N;
             const int c = (tx + 2) + H2X * (ty + 2);
             float D = a.M * mu_point<H2X>(mm, m0, mp, c, 0.f, 0.f, -1.0f / 22.0f);
             if (a.advect) {
                 const float *P0 = sps + ring4(z) * H3N, *Pm = sps + ring4(z - 1) * H3N, *Pp = sps + ring4(z + 1) * H3N;
                 const int cp = (tx + 3) + H3X * (ty + 3);
-                const int pi = g.pidx32(x, y, z);
-                const int sy = g.px, sz = g.px * g.py;
-                const float *u = a.u;
-                // u is read-only here: the read-only path keeps the row neighbours' lines
-                const float adv = (__ldg(u + pi + 1) * P0[cp + 1] - __ldg(u + pi - 1) * P0[cp - 1]) +
-                                  (__ldg(u + g.pn + pi + sy) * P0[cp + H3X] - __ldg(u + g.pn + pi - sy) * P0[cp - H3X]) +
-                                  (__ldg(u + 2 * g.pn + pi + sz) * Pp[cp] - __ldg(u + 2 * g.pn + pi - sz) * Pm[cp]);
+                const float adv = (u_pre[0] * P0[cp + 1] - u_pre[1] * P0[cp - 1]) +
+                                  (u_pre[2] * P0[cp + H3X] - u_pre[3] * P0[cp - H3X]) +
+                                  (u_pre[4] * Pp[cp] - u_pre[5] * Pm[cp]);
                 D -= 0.5f * adv;
             }
             const int si = x + g.nx * (y + g.ny * z);
             const float eta = (STAGE == 1 && NOISE) ? accm : 0.f;
             const float pv = STAGE == 1 ? sps[ring4(z) * H3N + (tx + 3) + H3X * (ty + 3)] : 0.f;
-            store_padded(a.out, g, x, y, z, rk_stage_out<STAGE, false>(a, x, y, z, si, pv, D, eta), 3);
+            const float out = (STAGE == 2 && !a.rk4) ? e_pre + 0.5f * D : rk_stage_out<STAGE, false>(a, x, y, z, si, pv, D, eta);
+            store_padded(a.out, g, x, y, z, out, 3);
         }
         accm = acc0;
         acc0 = accp;
