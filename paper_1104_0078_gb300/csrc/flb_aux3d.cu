@@ -8,7 +8,7 @@
 // velocity (sum fbar c + F/2)/rho of the new fluid state, which advects psi
 // (Gauss-Seidel coupling: the psi step follows the fluid step).  Both have a
 // batched variant that walks a block work list over all replicas.
-#include "flb_site3d.cuh"
+#include "flb_mu3d.cuh"
 
 namespace flb {
 

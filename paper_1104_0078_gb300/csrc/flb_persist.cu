@@ -19,7 +19,7 @@
 // and a waiting block orders its acquire before its TMA reads with a
 // generic-to-async proxy fence.
 #include "flb_psi3d.cuh"
-#include "flb_site3d.cuh"
+#include "flb_mu3d.cuh"
 
 namespace flb {
 
