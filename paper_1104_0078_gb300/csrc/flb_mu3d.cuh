@@ -17,7 +17,6 @@ __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restric
     const float k22 = K * (1.0f / 22.0f);
     int c = g.pidx32(x, y, zb - 1);
     float a0 = 0.f, b0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, d1 = 0.f;  // planes p-2, p-1
-#pragma unroll 2
     for (int p = zb - 1; p <= ze; ++p, c += Z) {
         const float a2 = ldf<COH>(psi + c);
         const float b2 = (ldf<COH>(psi + c - 1) + ldf<COH>(psi + c + 1)) + (ldf<COH>(psi + c - Y) + ldf<COH>(psi + c + Y));
