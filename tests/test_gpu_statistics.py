@@ -143,6 +143,57 @@ def test_equilibrium_ratio_by_scheme_and_laplacian(scheme, lap, coupling):
         assert abs((S[hi] / th[hi]).mean() - 1) < 0.02
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_d3q15_no_psi_velocity_cross_correlation_and_isotropy(scheme):
+    # Sec. VI (Figs. test1upsi and test1b) on the paper's coupled D3Q15 run:
+    # (i) the order parameter and the velocity, fields of different tensorial
+    # nature, stay uncorrelated: the normalised <psi~(q) u~_a*(q)> averages to
+    # zero within its sampling error; (ii) the equilibrium ratio is isotropic:
+    # at fixed |q| the modes along the axes, the face diagonals and the body
+    # diagonals all give S/theory = 1 within their sampling errors
+    d = dict(I.WORKLOADS["fluct_d3q15"], integrator=2, coupling=3, scheme=scheme)
+    p = flb_params(d)
+    op = oracle_params(d)
+    s = F.Solver(p)
+    s.step(2000)
+    n = 32
+    cross = np.zeros((3, n, n, n), dtype=complex)
+    pp = np.zeros((n, n, n))
+    uu = np.zeros((3, n, n, n))
+    ns = 300
+    for _ in range(ns):
+        s.step(20)
+        psi, u = s.get_psi_u()
+        ps = np.fft.fftn(psi.reshape(n, n, n))
+        us = np.fft.fftn(u.reshape(3, n, n, n), axes=(1, 2, 3))
+        cross += ps[None] * np.conj(us)
+        pp += np.abs(ps) ** 2
+        uu += np.abs(us) ** 2
+    rho = cross / ns / np.sqrt((pp / ns)[None] * (uu / ns))
+    qg = T.q_grid(op.shape)
+    live = (qg ** 2).sum(-1) > 0
+    # each mode's normalised cross term has s.d. ~ 1/sqrt(2 n_eff); pooled over
+    # all live modes and components the mean of |Re| stays far below one
+    assert np.abs(rho.real[:, live]).mean() < 0.1
+    assert abs(rho.real[:, live].mean()) < 0.01
+    # isotropy of the equilibrium ratio: directions at |q| ~ 1.1 (n_ind >~ 30 each)
+    c, w = O.lattice(3, 15)
+    L = T.L_so(qg) if scheme == 0 else T.L_fv(qg, c, w)
+    lmb = T.lam(qg, op, L)
+    th = T.static_structure_factor(qg, op, L)
+    S = pp / ns / n ** 3
+    k = np.rint(qg * n / (2 * np.pi)).astype(int)
+    ratios = {}
+    for name, sel in (("axis", (np.abs(k) == [6, 0, 0]).all(-1) | (np.abs(k) == [0, 6, 0]).all(-1)
+                       | (np.abs(k) == [0, 0, 6]).all(-1)),
+                      ("face", (np.sort(np.abs(k), -1) == [0, 4, 4]).all(-1)),
+                      ("body", (np.abs(k) == [3, 3, 3]).all(-1))):
+        ratios[name] = (S[sel] / th[sel]).mean(), sel.sum()
+    for name, (r, cnt) in ratios.items():
+        # lambda ~ 0.05 per step: ~300 independent samples per mode
+        assert abs(r - 1) < 4 / np.sqrt(300 * cnt / 2) + 0.01, (name, r, cnt)
+
+
 def test_galilean_invariance_small_mach():
     # Sec. VI.B: a uniform flow along the x = y diagonal at Ma = |u|/c_s = 0.08
     # leaves the static structure factor on the equilibrium theory (the bulk 3D
