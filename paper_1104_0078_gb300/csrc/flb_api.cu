@@ -13,10 +13,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "flb_internal.cuh"
 #include "flb_obs.cuh"
 
 using namespace flb;
+
+namespace {
+// NVTX range over a scope (the calls are no-ops unless a profiler is attached):
+// flb_step, and per replica step its mu, collide-stream, velocity, psi and
+// sampling phases, name the launches in a trace.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 namespace flb {
 // flb_lb.cu: padded plane (ghost frame of periodic images) from an interior field
@@ -512,17 +526,28 @@ int step_rep3(flb_handle *h, Rep &r)
     const LBArgs la = lb_args(r, psi_n);
     cudaEvent_t e0 = mark(h);
     if (p.coupling & FLB_COUPLE_FORCE) {
+        const Range range("mu");
         if (p.force_grad == FLB_FORCE_STRESS)
             FLB_TRY(launch_sigma3(r.g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
         else
             FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
     }
     cudaEvent_t e1 = mark(h);
-    FLB_TRY(r.q == 15 ? launch_lb15(la, p.storage, st) : launch_lb3d(la, p.storage, st));
+    {
+        const Range range("collide-stream");
+        FLB_TRY(r.q == 15 ? launch_lb15(la, p.storage, st) : launch_lb3d(la, p.storage, st));
+    }
     cudaEvent_t e2 = mark(h);
     const int64_t l2 = h->launches;
-    FLB_TRY(r.q == 15 ? launch_vel15(la, p.storage, st) : launch_vel3(la, p.storage, st));
-    const int rc = launch_psi_stages(h, r);
+    {
+        const Range range("velocity");
+        FLB_TRY(r.q == 15 ? launch_vel15(la, p.storage, st) : launch_vel3(la, p.storage, st));
+    }
+    int rc;
+    {
+        const Range range("psi");
+        rc = launch_psi_stages(h, r);
+    }
     if (rc != FLB_OK) return rc;
     cudaEvent_t e3 = mark(h);
     span(h, 0, e1, e2, 1);
@@ -537,6 +562,7 @@ int step_rep3(flb_handle *h, Rep &r)
 int step_rep(flb_handle *h, Rep &r)
 {
     if (r.dim == 3 && !general_path(r.p)) return step_rep3(h, r);
+    const Range range("step (per-site kernels)");
     // one-thread-per-site path: 2D, and the 3D combinations of general_path()
     const Geom &g = r.g;
     const flb_params &p = r.p;
@@ -635,6 +661,7 @@ int step_rep(flb_handle *h, Rep &r)
 
 int sample_rep(flb_handle *h, Rep &r, int mask)
 {
+    const Range range("sample");
     const Geom &g = r.g;
     cudaEvent_t e0 = mark(h);
     const int64_t l0 = h->launches;
@@ -1171,6 +1198,7 @@ int flb_get_window(flb_handle *h, int32_t rep, int32_t x0, int32_t y0, int32_t z
 int flb_step(flb_handle *h, int64_t n)
 {
     if (!h || n < 0) return FLB_EINVAL;
+    const Range range("flb_step");
     if (h->mode == FLB_MODE_BATCHED) return n > 0 ? step_batched(h, n) : FLB_OK;
     if (h->mode == FLB_MODE_PERSISTENT) return n > 0 ? step_persistent(h, n) : FLB_OK;
     for (int64_t k = 0; k < n; ++k) {
