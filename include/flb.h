@@ -206,6 +206,18 @@ int flb_get_step(flb_handle *h, int32_t rep, int64_t *step);
  * any population, psi or u value was NaN or Inf. */
 int flb_moments(flb_handle *h, int32_t rep, double *totals, double *u2);
 
+/* Per-mode mean squares of replica rep: msq[k] = (1/N) sum_r m_k(r)^2, k = 0..q-1,
+ * with m_k(r) = sum_i E_ki (fbar_i(r) - w_i rho0) the projections of the
+ * physical populations on the moment basis E (Gram-Schmidt under sum_i w_i a_i
+ * b_i on the ordered monomials 1; c; c^2; 3c_x^2 - c^2; c_y^2 - c_z^2; c_x c_y;
+ * c_y c_z; c_z c_x; c^2 c; c_x(c_y^2 - c_z^2), c_y(c_z^2 - c_x^2), c_z(c_x^2 - c_y^2);
+ * c^4; c^2(3c_x^2 - c^2); c^2(c_y^2 - c_z^2) for D3Q19; D3Q15 ends c_x c_y c_z, c^4
+ * after the c^2 c rows; D2Q9: 1; c; c^2; c_x^2 - c_y^2; c_x c_y; c^2 c; c^4).  In
+ * equilibrium every non-conserved mode has <m_k^2> = (rho kT / c_s^2) b_k, b_k =
+ * sum_i w_i E_ki^2 (Sec. III).  msq: host FP64 [q].  Reduced in FP64 on the device;
+ * synchronising; returns ENONFINITE if any population was NaN or Inf. */
+int flb_mode_variances(flb_handle *h, int32_t rep, double *msq);
+
 /* Sampling of the structure factors during flb_step: every every_m steps
  * (0 = never) the psi spectrum (mask bit 1), the interface-height spectrum
  * (mask bit 2) and/or the dynamic structure factor (mask bit 4: the psi

@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "flb_step": (c_int, [H, c_i64]),
         "flb_get_step": (c_int, [H, ctypes.c_int32, P(c_i64)]),
         "flb_moments": (c_int, [H, ctypes.c_int32, dp, dp]),
+        "flb_mode_variances": (c_int, [H, ctypes.c_int32, dp]),
         "flb_set_sampling": (c_int, [H, ctypes.c_int32, ctypes.c_int32]),
         "flb_sample": (c_int, [H, ctypes.c_int32]),
         "flb_structure_factor": (c_int, [H, ctypes.c_int32, ctypes.c_int32, dp, P(c_i64)]),
@@ -258,6 +259,12 @@ class Solver:
 
     def moments(self, rep=0):
         return flb_moments(self.h, rep, self.params[rep].dim)
+
+    def mode_variances(self, rep=0):
+        """(1/N) sum_r m_k(r)^2 of every moment mode k (flb_mode_variances), FP64 [q]."""
+        out = np.zeros(self.params[rep].q)
+        _check(self.lib.flb_mode_variances(self.h, rep, _dp(out)), "flb_mode_variances")
+        return out
 
     def set_sampling(self, every_m, mask=1):
         _check(self.lib.flb_set_sampling(self.h, every_m, mask), "flb_set_sampling")

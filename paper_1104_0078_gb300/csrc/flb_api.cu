@@ -338,8 +338,8 @@ size_t carve_all(flb_handle &h, char *base)
     h.p_ticket = cv.take<unsigned>(1);
     h.p_abort = cv.take<int>(1);
     h.p_done = cv.take<unsigned>(h.reps.size());
-    h.red_partial = cv.take<double>((size_t)RED_MAX_BLOCKS * NRED);
-    h.red_out = cv.take<double>(NRED);
+    h.red_partial = cv.take<double>((size_t)RED_MAX_BLOCKS * std::max(NRED, NMSQ));
+    h.red_out = cv.take<double>(std::max(NRED, NMSQ));
     h.status = cv.take<int>(1);
     h.X1 = cv.take<float2>(cap1);
     h.X2 = cv.take<float2>(cap2);
@@ -1212,6 +1212,67 @@ int flb_step(flb_handle *h, int64_t n)
         }
     }
     return FLB_OK;
+}
+
+namespace {
+// Moment basis of the lattice (App. B leaves it open): Gram-Schmidt under
+// <a, b> = sum_i w_i a_i b_i on the ordered monomials 1; c; c^2; 3c_x^2 - c^2;
+// c_y^2 - c_z^2; c_x c_y; c_y c_z; c_z c_x; c^2 c; c_x(c_y^2 - c_z^2), c_y(c_z^2 - c_x^2),
+// c_z(c_x^2 - c_y^2); c^4; c^2(3c_x^2 - c^2); c^2(c_y^2 - c_z^2) (D3Q19; D3Q15 ends
+// c_x c_y c_z, c^4 after the c^2 c rows; D2Q9: 1; c; c^2; c_x^2 - c_y^2; c_x c_y;
+// c^2 c; c^4), in plane order.
+double mode_monomial(int dim, int q, int k, const int *cv)
+{
+    const double x = cv[0], y = cv[1], z = cv[2], c2 = x * x + y * y + z * z;
+    if (dim == 2) {
+        const double m[9] = {1, x, y, c2, x * x - y * y, x * y, c2 * x, c2 * y, c2 * c2};
+        return m[k];
+    }
+    if (q == 15 && k >= 13) return k == 13 ? x * y * z : c2 * c2;
+    const double m[19] = {1, x, y, z, c2, 3 * x * x - c2, y * y - z * z, x * y, y * z, z * x, c2 * x, c2 * y, c2 * z,
+                          x * (y * y - z * z), y * (z * z - x * x), z * (x * x - y * y), c2 * c2,
+                          c2 * (3 * x * x - c2), c2 * (y * y - z * z)};
+    return m[k];
+}
+
+ModeBasis mode_basis(int dim, int q)
+{
+    double E[19][19];
+    for (int k = 0; k < q; ++k) {
+        for (int i = 0; i < q; ++i) E[k][i] = mode_monomial(dim, q, k, cvec(q, i));
+        for (int l = 0; l < k; ++l) {
+            double dot = 0.0, nl = 0.0;
+            for (int i = 0; i < q; ++i) {
+                dot += wgt(q, i) * E[k][i] * E[l][i];
+                nl += wgt(q, i) * E[l][i] * E[l][i];
+            }
+            for (int i = 0; i < q; ++i) E[k][i] -= dot / nl * E[l][i];
+        }
+    }
+    ModeBasis B;
+    B.q = q;
+    for (int k = 0; k < q; ++k)
+        for (int i = 0; i < q; ++i) B.E[k * q + i] = (float)E[k][i];
+    return B;
+}
+}  // namespace
+
+int flb_mode_variances(flb_handle *h, int32_t rep, double *msq)
+{
+    Rep *r = get_rep(h, rep);
+    if (!r || !msq) return FLB_EINVAL;
+    const Geom &g = r->g;
+    const int nb = (int)std::min<long long>(RED_MAX_BLOCKS, (g.n + 255) / 256);
+    const cudaError_t e = launch_mode_msq(g, r->p.storage, mode_basis(r->dim, r->q), r->f[r->cur], h->red_partial,
+                                          nb, h->red_out, h->st);
+    h->launches += 2;
+    if (e != cudaSuccess) return FLB_ECUDA;
+    double out[NMSQ];
+    int rc = cuerr(cudaMemcpyAsync(out, h->red_out, sizeof(out), cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    for (int k = 0; k < r->q; ++k) msq[k] = out[k] / (double)g.n;
+    return out[NMSQ - 1] > 0.0 ? FLB_ENONFINITE : FLB_OK;
 }
 
 int flb_get_step(flb_handle *h, int32_t rep, int64_t *step)

@@ -114,6 +114,84 @@ cudaError_t launch_totals(const Geom &g, int q, int storage, const void *f, cons
 }
 
 // ---------------------------------------------------------------------------
+// Per-mode mean squares (Sec. III: every non-conserved mode carries
+// <m_k^2> = (rho kT / c_s^2) b_k in equilibrium): each site pulls its physical
+// populations fbar_i(r) = stored_i(r - c_i) (deviations from w_i rho0), projects
+// them on the moment basis and adds m_k^2 in FP64; blocks reduce as for the totals.
+// ---------------------------------------------------------------------------
+__constant__ int8_t kMsq19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                     {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                     {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                     {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+__constant__ int8_t kMsq15[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                                     {0, 0, 1},  {0, 0, -1}, {1, 1, 1},   {-1, -1, -1}, {1, 1, -1},
+                                     {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {1, -1, -1}, {-1, 1, 1}};
+__constant__ int8_t kMsq9[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                   {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+
+template <typename T>
+__global__ void __launch_bounds__(RED_BS) mode_msq_kernel(const Geom g, const ModeBasis B, const T *__restrict__ f,
+                                                          double *__restrict__ partial)
+{
+    const int q = B.q;
+    double acc[NMSQ];
+#pragma unroll
+    for (int k = 0; k < NMSQ; ++k) acc[k] = 0.0;
+    const long long N = g.n;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+        float d[19];
+        int bad = 0;
+        for (int i = 0; i < q; ++i) {
+            const int8_t *c = q == 19 ? kMsq19[i] : q == 15 ? kMsq15[i] : kMsq9[i];
+            const long long src =
+                g.sidx(wrapi(x - c[0], g.nx), wrapi(y - c[1], g.ny), g.dim == 3 ? wrapi(z - c[2], g.nz) : 0);
+            d[i] = ldv(f, (long long)i * N + src);
+            bad |= !isfinite(d[i]);
+        }
+        for (int k = 0; k < q; ++k) {
+            float m = 0.f;
+            for (int i = 0; i < q; ++i) m = fmaf(B.E[k * q + i], d[i], m);
+            acc[k] += (double)m * m;
+        }
+        acc[NMSQ - 1] += bad;
+    }
+    __shared__ double sh[RED_BS / 32][NMSQ];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NMSQ; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NMSQ) {
+        double t = 0.0;
+        for (int w = 0; w < RED_BS / 32; ++w) t += sh[w][threadIdx.x];
+        partial[(long long)blockIdx.x * NMSQ + threadIdx.x] = t;
+    }
+}
+
+__global__ void msq_final_kernel(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
+{
+    const int k = threadIdx.x;
+    if (k >= NMSQ) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[(long long)b * NMSQ + k];
+    out[k] = t;
+}
+
+cudaError_t launch_mode_msq(const Geom &g, int storage, const ModeBasis &B, const void *f, double *partial,
+                            int nblocks, double *out, cudaStream_t s)
+{
+    if (storage == FLB_F16_DEV)
+        mode_msq_kernel<__half><<<nblocks, RED_BS, 0, s>>>(g, B, (const __half *)f, partial);
+    else
+        mode_msq_kernel<float><<<nblocks, RED_BS, 0, s>>>(g, B, (const float *)f, partial);
+    msq_final_kernel<<<1, 32, 0, s>>>(partial, nblocks, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Separable DFT.  Axis lists: index j of an axis of length n with window kmax
 // (K = 2 kmax + 1 < n) is k = j for j <= kmax and n - (K - j) otherwise; with
 // K = n every k is kept.

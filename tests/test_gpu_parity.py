@@ -365,6 +365,20 @@ def test_set_fields_equilibrium_and_fields(dim, q, shape):
     assert field_error(s.get_psi_u()[0], st.psi) < TOL
 
 
+@pytest.mark.parametrize("dim,q,shape", [(3, 19, (11, 9, 7)), (3, 15, (10, 8, 9)), (2, 9, (17, 12, 1))])
+def test_mode_variances_match_oracle(dim, q, shape):
+    # flb_mode_variances against the oracle's projection of its own trajectory:
+    # the mean over sites of m_k^2, m = E (fbar - w rho0), for every mode k
+    d = dict(dim=dim, q=q, nx=shape[0], ny=shape[1], nz=shape[2], tau=0.8, kT=1e-4, A=0.05, B=0.3, K=0.04, M=0.1,
+             scheme=0, integrator=2, coupling=3, seed=19, gamma_ghost=0.2)
+    s, (fg, pg, ug), st, feq = _run_pair(d, 12)
+    E, b = O.moment_basis(dim, q)
+    m = E @ (st.f - feq)
+    ref = np.mean(m ** 2, axis=1)
+    got = s.mode_variances()
+    assert np.allclose(got, ref, rtol=1e-4, atol=0), (got, ref)
+
+
 def test_nonfinite_is_reported():
     d = dict(dim=2, q=9, nx=8, ny=8, tau=1.0, kT=0.0, A=0.05, B=0.0, K=0.04, M=0.1, scheme=0, integrator=1)
     s = F.Solver(flb_params(d))

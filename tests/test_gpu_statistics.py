@@ -194,6 +194,28 @@ def test_d3q15_no_psi_velocity_cross_correlation_and_isotropy(scheme):
         assert abs(r - 1) < 4 / np.sqrt(300 * cnt / 2) + 0.01, (name, r, cnt)
 
 
+@pytest.mark.parametrize("dim,q", [(3, 19), (3, 15), (2, 9)])
+def test_equipartition_of_every_mode(dim, q):
+    # Sec. III (adhikari2005): with the noise on every stress and ghost mode the
+    # fluid at rest reaches <m_k^2> = (rho0 kT / c_s^2) b_k for every mode but the
+    # conserved mass, momentum included, whatever the bulk and ghost relaxation;
+    # reduced on the device by flb_mode_variances
+    n = 32 if dim == 3 else 128
+    d = dict(dim=dim, q=q, nx=n, ny=n, nz=n if dim == 3 else 1, tau=0.6, kT=2e-4, A=0.05, B=0.0, K=0.04, M=0.1,
+             scheme=0, integrator=2, coupling=0, gamma_bulk=-0.5, gamma_ghost=0.3, seed=5)
+    s = F.Solver(flb_params(d))
+    s.step(300)
+    _, b = O.moment_basis(dim, q)
+    acc = np.zeros(q)
+    ns = 200
+    for _ in range(ns):
+        s.step(2)
+        acc += s.mode_variances()
+    ratio = acc / ns / (1.0 * d["kT"] * 3.0 * b)
+    assert np.all(np.abs(ratio[1:] - 1) < 0.02), ratio
+    assert np.all(np.abs(ratio[dim + 1:] - 1) < 0.01), ratio
+
+
 def test_galilean_invariance_small_mach():
     # Sec. VI.B: a uniform flow along the x = y diagonal at Ma = |u|/c_s = 0.08
     # leaves the static structure factor on the equilibrium theory (the bulk 3D
