@@ -120,6 +120,14 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
     Regions R;
     make_regions(R, g, x0, y0);
     float accm = 0.f, acc0 = 0.f, accp = 0.f;  // eta of planes p-2, p-1, p
+    // psi planes are double-buffered in registers: plane p+1 is loaded while
+    // plane p is worked on, and stored to its ring slot at the next iteration
+    float nxt[S3];
+    {
+        const float *src = a.psi + (size_t)plane * (z0 - 2 + g.gz);
+#pragma unroll
+        for (int j = 0; j < S3; ++j) nxt[j] = R.g3[j] >= 0 ? __ldg(src + R.g3[j]) : 0.f;
+    }
 
     for (int p = z0 - 2; p <= z1 + 1; ++p) {
         // this iteration's output plane p-2: its global inputs (the Heun
@@ -143,11 +151,16 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
         }
         __syncthreads();
         {
-            const float *src = a.psi + (size_t)plane * (p + g.gz);
             float *dst = sps + ring4(p) * H3N;
 #pragma unroll
             for (int j = 0; j < S3; ++j)
-                if (R.g3[j] >= 0) dst[threadIdx.x + j * PS_NT] = __ldg(src + R.g3[j]);
+                if (R.g3[j] >= 0) dst[threadIdx.x + j * PS_NT] = nxt[j];
+            if (p + 1 <= z1 + 1) {
+                const float *src = a.psi + (size_t)plane * (p + 1 + g.gz);
+#pragma unroll
+                for (int j = 0; j < S3; ++j)
+                    if (R.g3[j] >= 0) nxt[j] = __ldg(src + R.g3[j]);
+            }
         }
         __syncthreads();
         const int q = p - 1;
