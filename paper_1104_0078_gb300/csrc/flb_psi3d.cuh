@@ -209,11 +209,19 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
         const int s3 = s2 == 0 ? T_PSI_DEPTH - 1 : s2 - 1;
         (void)s1;
-        // Heun stage 2: the accumulator E of this iteration's output plane p-3 is
-        // loaded now, so that its latency hides behind the plane's work
-        float e_pre = 0.f;
-        if (STAGE == 2 && !a.rk4 && active && p - 3 >= z0)
-            e_pre = COH ? __ldcg(a.E + x + g.nx * (y + g.ny * (p - 3))) : a.E[x + g.nx * (y + g.ny * (p - 3))];
+        // Heun stage 2 and RK4 stages 2-4: the accumulator E (and for RK4 stages 2
+        // and 3 the noise increment and psi^n) of this iteration's output plane
+        // p-3 are loaded now, so that their latency hides behind the plane's work
+        float e_pre = 0.f, n_pre = 0.f, b_pre = 0.f;
+        if (STAGE == 2 && active && p - 3 >= z0) {
+            const int sp = x + g.nx * (y + g.ny * (p - 3));
+            if (!a.rk4 || a.rk4 > 1) e_pre = COH ? __ldcg(a.E + sp) : a.E[sp];
+            if (a.rk4 == 2 || a.rk4 == 3) {
+                const int bp = g.pidx32(x, y, p - 3);
+                n_pre = COH ? __ldcg(a.Dn + sp) : a.Dn[sp];
+                b_pre = COH ? __ldcg(a.base + bp) : a.base[bp];
+            }
+        }
         // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
         if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
         waited_p = p;
@@ -339,8 +347,17 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 const int si = x + g.nx * (y + g.ny * z);
                 const float Dn = (STAGE == 1 && NOISE) ? dn * (1.f / 12.f) : 0.f;
                 const float pv = STAGE == 1 ? tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)] : 0.f;
-                const float out = (STAGE == 2 && !a.rk4) ? e_pre + 0.5f * Dd
-                                                         : rk_stage_out<STAGE, COH>(a, x, y, z, si, pv, Dd, Dn);
+                float out;
+                if (STAGE == 2 && !a.rk4) {
+                    out = e_pre + 0.5f * Dd;
+                } else if (STAGE == 2 && a.rk4 == 4) {
+                    out = e_pre + (1.f / 6.f) * Dd;
+                } else if (STAGE == 2 && a.rk4 >= 2) {  // stages 2 and 3: E += D/3, out = psi^n + c (D + eta)
+                    a.E[si] = e_pre + (1.f / 3.f) * Dd;
+                    out = a.rk4 == 2 ? b_pre + 0.5f * (Dd + n_pre) : b_pre + Dd + n_pre;
+                } else {
+                    out = rk_stage_out<STAGE, COH>(a, x, y, z, si, pv, Dd, Dn);
+                }
                 store_padded(a.out, g, x, y, z, out, 3);
             }
         }
