@@ -1,10 +1,11 @@
 """Parity at the full 512^3 quench size, in the launch configuration bench.py
-times: after two steps from the seeded start (rest populations, psi0 uniform in
-[-0.01, 0.01]) sampled sites are compared with the FP64 oracle run on a 32^3
-window around each (periodic window, counter ids of the global lattice).  Two
-steps of the FV/Heun path depend on psi0 within 12 cells and on the populations
-within 11, so the central 8^3 of each window is exact; plus conservation of mass
-and psi over the run."""
+times (D3Q19, FV, Heun) and in that of its D3Q15/FD variant: after two steps
+from the seeded start (rest populations, psi0 uniform in [-0.01, 0.01]) sampled
+sites are compared with the FP64 oracle run on a 32^3 window around each
+(periodic window, counter ids of the global lattice).  Two steps of either
+path depend on psi0 within 12 cells and on the populations within 11, so the
+central 8^3 of each window is exact; plus conservation of mass and psi over the
+run."""
 import numpy as np
 import pytest
 
@@ -19,12 +20,13 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def test_quench_512_windows_match_oracle():
+@pytest.mark.parametrize("q,scheme", [(19, 1), (15, 0)])
+def test_quench_512_windows_match_oracle(q, scheme):
     d = dict(I.WORKLOADS["quench"])
     n = 512
     N = n ** 3
-    p = F.flb_params_default(nx=n, ny=n, nz=n, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
-                             psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, seed=d["seed"], sq_kmax=8)
+    p = F.flb_params_default(q=q, nx=n, ny=n, nz=n, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"],
+                             M=d["M"], psi_scheme=scheme, integrator=F.FLB_HEUN, seed=d["seed"], sq_kmax=8)
     psi0 = I.uniform_field(N, -0.01, 0.01, 11)
     s = F.Solver(p)
     s.set_fields(psi=psi0)
@@ -36,20 +38,20 @@ def test_quench_512_windows_match_oracle():
     psi_cube = psi0.reshape(n, n, n)
     rng = np.random.default_rng(5)
     W = 32
-    _, w = O.lattice(3, 19)
+    _, w = O.lattice(3, q)
     for origin in [(0, 0, 0), (n - 16, 100, 250), (240, 496, 8)] + [tuple(rng.integers(0, n, 3)) for _ in range(3)]:
         x0, y0, z0 = (int(v) for v in origin)
         fg, pg = s.get_window((x0, y0, z0), (W, W, W))
         idx = [(np.arange(W) + o) % n for o in (z0, y0, x0)]
         win_psi = psi_cube[np.ix_(*idx)].reshape(-1)
-        op = O.Params(dim=3, q=19, nx=W, ny=W, nz=W, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"],
-                      M=d["M"], scheme=1, integrator=2, coupling=3, seed=d["seed"], gdims=(n, n, n),
+        op = O.Params(dim=3, q=q, nx=W, ny=W, nz=W, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"],
+                      M=d["M"], scheme=scheme, integrator=2, coupling=3, seed=d["seed"], gdims=(n, n, n),
                       origin=(x0, y0, z0))
         st = O.State.rest(op, psi=win_psi)
         st.advance(2)
         c = slice(12, 20)
-        f_o = st.f.reshape(19, W, W, W)[:, c, c, c].reshape(19, -1)
-        f_g = fg.reshape(19, W, W, W)[:, c, c, c].reshape(19, -1)
+        f_o = st.f.reshape(q, W, W, W)[:, c, c, c].reshape(q, -1)
+        f_g = fg.reshape(q, W, W, W)[:, c, c, c].reshape(q, -1)
         p_o = st.psi.reshape(W, W, W)[c, c, c].reshape(-1)
         p_g = pg.reshape(W, W, W)[c, c, c].reshape(-1)
         assert field_error(f_g, f_o, w[:, None]) < TOL
