@@ -11,6 +11,7 @@
 #include <functional>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -1081,6 +1082,25 @@ int flb_init(const flb_params *p, int32_t nrep, void *dev_ws, size_t ws_bytes, v
     return FLB_OK;
 }
 
+// dst[s] = (float)src[s], split over the host's cores for large fields
+static void to_float(const double *src, float *dst, long long n)
+{
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const long long nt = n < (1 << 20) ? 1 : std::min<long long>(hw, 32);
+    auto part = [&](long long t) {
+        const long long a = n * t / nt, b = n * (t + 1) / nt;
+        for (long long s = a; s < b; ++s) dst[s] = (float)src[s];
+    };
+    if (nt == 1) {
+        part(0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (long long t = 1; t < nt; ++t) pool.emplace_back(part, t);
+    part(0);
+    for (auto &th : pool) th.join();
+}
+
 int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *u, const double *psi)
 {
     Rep *r = get_rep(h, rep);
@@ -1092,7 +1112,7 @@ int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *
     // scratch between steps), and are padded with their images on the device
     std::vector<float> tmp((size_t)N);
     auto put = [&](const double *src, float *dst) -> int {
-        for (long long s = 0; s < N; ++s) tmp[(size_t)s] = (float)src[s];
+        to_float(src, tmp.data(), N);
         int rc = cuerr(cudaMemcpyAsync(r->mu, tmp.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
         if (rc == FLB_OK) rc = cuerr(launch_pad(g, r->mu, dst, st));
         ++h->launches;
