@@ -1,10 +1,11 @@
 /*
  * flb.h -- C ABI of the GB300 library for the hybrid model-H solver of
  * Sumesh, Pagonabarraga & Adhikari, "Lattice Boltzmann - Langevin simulations
- * of binary mixtures" (arXiv:1104.0078).
+ * of binary mixtures" (arXiv:1104.0078), on D2Q9, D3Q19 and the paper's own
+ * D3Q15 lattice.
  *
- * One time step advances, in this order and both from the state at time n
- * (Sec. VI, "alternate marching"):
+ * One time step advances, in this order (Sec. VI, "alternate marching"; the
+ * psi step uses the velocity of the fluid state the LB step produced):
  *   1. the fluctuating lattice Boltzmann equation for the momentum (Sec. IV,
  *      App. B): pull-streaming of the auxiliary populations fbar, moments
  *      rho = sum fbar, rho v = sum fbar c + F/2, moment-space relaxation with
@@ -12,9 +13,11 @@
  *      every stress and ghost mode (Eq. bab, adhikari2005);
  *   2. the stochastic method-of-lines step of the order parameter psi
  *      (Sec. V): d psi/dt = -div(u psi) + M lap mu + div xi, with
- *      mu = A psi + B psi^3 - K lap_SO psi (Sec. II.A, App. A), in the
- *      finite-difference (Sec. V.A) or finite-volume (Sec. V.B) form, noise
- *      held fixed over a Runge-Kutta step (Sec. V, wilkie2004).
+ *      mu = A psi + B psi^3 - K lap psi (Sec. II.A, lap one of the App. A
+ *      stencils, SO by default), in the finite-difference (Sec. V.A) or
+ *      finite-volume (Sec. V.B) form, or the naive discretisation Sec. III
+ *      contrasts with; noise held fixed over a Runge-Kutta step (Sec. V,
+ *      wilkie2004).
  *
  * Units: lattice units, dx = dt = 1, c_s^2 = 1/3, periodic boundaries.
  * Threading: a handle is not thread-safe; calls on one handle must be
@@ -174,29 +177,33 @@ int flb_init(const flb_params *p, int32_t nrep, void *dev_ws, size_t ws_bytes, v
 /* Equilibrium initialisation of replica rep from host fields (FP64, site-major
  * s = x + nx*(y + ny*z)): rho[N] (NULL: rho0), u[dim][N] (NULL: 0), psi[N]
  * (NULL: 0).  fbar = w (rho + rho u.c/c_s^2 + rho uu:Q/(2 c_s^4)).  Also sets
- * the stored velocity to u.  Synchronising. */
+ * the stored velocity to u.  The step counter is kept.  Synchronising.
+ * Errors: EINVAL (no such replica), ECUDA. */
 int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *u, const double *psi);
 
 /* Physical populations fbar_i(x, t) after streaming, FP64 [q][N], the state the
  * paper's App. B evolves; set replaces the populations (psi and u are kept).
- * Synchronising. */
+ * Synchronising.  Errors: EINVAL (no such replica, NULL f), ECUDA. */
 int flb_get_populations(flb_handle *h, int32_t rep, double *f);
 int flb_set_populations(flb_handle *h, int32_t rep, const double *f);
 
 /* Order parameter psi(t) [N] and the velocity u [dim][N] that the last psi
  * step used (time t-1; the initial field before the first step).  Either pointer
- * may be NULL.  Synchronising. */
+ * may be NULL.  Synchronising.  Errors: EINVAL (no such replica), ECUDA. */
 int flb_get_psi_u(flb_handle *h, int32_t rep, double *psi, double *u);
 
 /* A periodic window of replica rep: origin (x0,y0,z0), size wx*wy*wz, populations
- * f[q][W] and psi[W] in window site order (either may be NULL).  Synchronising. */
+ * f[q][W] and psi[W] in window site order (either may be NULL).  Synchronising.
+ * Errors: EINVAL (no such replica, sizes < 1), ENOSPC (W above 32768), ECUDA. */
 int flb_get_window(flb_handle *h, int32_t rep, int32_t x0, int32_t y0, int32_t z0, int32_t wx, int32_t wy,
                    int32_t wz, double *f, double *psi);
 
-/* Advance every replica by n >= 0 steps.  Asynchronous on the stream. */
+/* Advance every replica by n >= 0 steps.  Asynchronous on the stream.
+ * Errors: EINVAL (n < 0), EUNSUPPORTED (replicas outside the chosen mode),
+ * ECUDA; device-side faults are reported by the next synchronising call. */
 int flb_step(flb_handle *h, int64_t n);
 
-/* Current step counter of replica rep. */
+/* Current step counter of replica rep.  Errors: EINVAL. */
 int flb_get_step(flb_handle *h, int32_t rep, int64_t *step);
 
 /* Conserved totals and velocity variance of replica rep, reduced on the device
@@ -294,17 +301,19 @@ int flb_set_wait_limit(flb_handle *h, double seconds);
  * its SM count and the configuration: entries found there are applied without
  * timing (unless flags has FLB_TUNE_FORCE), new results are appended.  An
  * unreadable or unwritable file only disables the cache.  Synchronising; call
- * with the handle's device current and outside stream capture.  2D replicas are
- * left as they are.
+ * with the handle's device current and outside stream capture.  2D replicas and
+ * the 3D combinations on one-thread-per-site kernels (see laplacian) are left as
+ * they are.
  */
 int flb_get_tuning(flb_handle *h, int32_t rep, int32_t *psi_zchunk);
 int flb_set_tuning(flb_handle *h, int32_t rep, int32_t psi_zchunk);
 int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags);
 
 /* Bitwise checkpoint of replica rep: flb_state_bytes() bytes holding the step
- * counter, the stored populations and psi exactly as kept on the device.
- * Restoring gives a bitwise-identical continuation (the noise is
- * counter-based).  Synchronising. */
+ * counter, the stored populations (in the storage precision), psi and u exactly
+ * as kept on the device.  Restoring gives a bitwise-identical continuation (the
+ * noise is counter-based).  Synchronising.  Errors: EINVAL (no such replica,
+ * NULL buffer), ENOSPC (bytes too small), ECUDA. */
 size_t flb_state_bytes(flb_handle *h, int32_t rep);
 int flb_get_state(flb_handle *h, int32_t rep, void *host, size_t bytes);
 int flb_set_state(flb_handle *h, int32_t rep, const void *host, size_t bytes);
