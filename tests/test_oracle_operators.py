@@ -169,7 +169,7 @@ def test_mu_and_force():
         assert np.allclose(F[:, z, y, x], -psi[z, y, x] * np.array([gx, gy, gz]), atol=1e-12)
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_fv_force_gradient_symbol(dim, q):
     # force_grad 2: F = -psi G mu with G the FV gradient of Eq. (fvgrad), whose
     # Fourier symbol is i (1/c_s^2) sum_i w_i c_i sin(q.c_i) (Eq. fvft); the
@@ -193,7 +193,7 @@ def test_fv_force_gradient_symbol(dim, q):
     assert np.array_equal(Fd, O.force(O.Params(**{**p.__dict__, "force_grad": 1}), psi))
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_force_advection_energy_exchange(dim, q, scheme):
     # Work done by the force on the fluid, sum u.F, equals the free energy the
@@ -248,7 +248,7 @@ def test_dynamic_structure_factor_exact_decay(dim, q, scheme):
     assert np.allclose(S[0], np.mean(P, axis=0), rtol=1e-13)
 
 
-@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
 def test_stress_force_sums_to_zero(dim, q):
     # force_grad 3: F = -div sigma (Sec. IV, Eq. muf) with a central-difference
     # divergence telescopes to sum_r F = 0 for any psi, also for B != 0, where
