@@ -169,6 +169,15 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def measured_sm_max_mhz() -> float:
+    """Maximum SM clock recorded beside the measured peaks (2070 MHz if absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return 2070.0
+
+
 LB_SOURCES = ("flb_lb3d.cu", "flb_site3d.cuh", "flb_internal.cuh")
 
 
@@ -180,17 +189,44 @@ def lb_source_sha():
     return h.hexdigest()
 
 
-def lb_traffic(storage: int, n_sites: int):
-    """DRAM bytes per LB launch from the committed ncu summary, if it was taken on
-    the current kernel sources; scaled by sites when the capture was smaller."""
+def lb_record(storage: int):
+    """The committed ncu record of the LB kernel, if it was taken on the current
+    kernel sources and storage, else None."""
     path = os.path.join(ROOT, "profiles", "lb_kernel_traffic.json")
     try:
         rec = json.load(open(path))
-        if rec.get("source_sha256") != lb_source_sha() or rec.get("storage") != storage:
-            return None
-        return rec["dram_bytes_per_launch"] * n_sites / rec["sites"]
-    except (OSError, KeyError, ValueError):
+    except (OSError, ValueError):
         return None
+    if rec.get("source_sha256") != lb_source_sha() or rec.get("storage") != storage:
+        return None
+    return rec
+
+
+def lb_traffic(storage: int, n_sites: int):
+    """DRAM bytes per LB launch from the committed ncu record, scaled by sites
+    when the capture was smaller."""
+    rec = lb_record(storage)
+    try:
+        return rec["dram_bytes_per_launch"] * n_sites / rec["sites"] if rec else None
+    except KeyError:
+        return None
+
+
+def lb_issue_roofline(storage: int, n_sites: int, lb_ms: float, n_sm: int, sm_max_mhz: float):
+    """Secondary (ALU) roofline of the LB kernel: its executed instructions per
+    launch (ncu record, scaled by sites; every lane of every warp is active) over
+    its live launch time, against the issue peak of one warp-instruction per
+    scheduler and cycle: SMs x 4 schedulers x 32 lanes x the maximum SM clock."""
+    rec = lb_record(storage)
+    if not rec or "warp_inst_per_launch" not in rec or not lb_ms:
+        return None
+    warp_inst = rec["warp_inst_per_launch"] * n_sites / rec["sites"]
+    achieved = 32 * warp_inst / (lb_ms / 1e3) / 1e12
+    peak = n_sm * 4 * 32 * sm_max_mhz * 1e6 / 1e12
+    return {"bound": "alu", "kernel": "LB collide-stream", "achieved": achieved, "peak": peak,
+            "unit": "T thread-instructions/s", "frac": achieved / peak,
+            "inst_per_site": 32 * warp_inst / n_sites,
+            "peak_from": f"{n_sm} SMs x 4 schedulers x 1 warp-instruction/cycle x 32 lanes x {sm_max_mhz:.0f} MHz"}
 
 
 def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
@@ -366,6 +402,8 @@ def run_ours(args):
     achieved = lb_bytes / (lb_ms / 1e3) / 1e9
     step_ms = ms / args.steps
     step_gbs = ALG_BYTES_SITE[storage] * N / (step_ms / 1e3) / 1e9
+    sm_max = (clocks or {}).get("sm_max_mhz") or measured_sm_max_mhz()
+    issue = lb_issue_roofline(storage, N, lb_ms, torch.cuda.get_device_properties(local).multi_processor_count, sm_max)
 
     # end to end through the public API: upload the initial field, step, read totals
     e2e = None
@@ -410,6 +448,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": lb_traffic(storage, N),
                          "kernel": "LB collide-stream", "peak_kind": peak_kind,
                          "alg_bytes_per_site": LB_ALG_BYTES_SITE[storage], "kernel_ms": lb_ms},
+            "issue_roofline": issue,
             "step_roofline": {"alg_bytes_per_site": ALG_BYTES_SITE[storage], "achieved_gbs": step_gbs,
                               "frac": step_gbs / peak, "kernel_ms_per_step": {k: v / kp for k, v in kms.items()}},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,

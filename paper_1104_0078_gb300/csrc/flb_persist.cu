@@ -143,10 +143,10 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
             __syncthreads();
             if (stage == 1) {
                 const CUtensorMap *pm = &r.map_psi[(int)(ds & 1)];
-                if (r.noise) psi3_fv_tma_block<1, true, true, true>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
-                else psi3_fv_tma_block<1, false, true>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                if (r.noise) psi3_fv_tma_block<1, true, true, true, false>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                else psi3_fv_tma_block<1, false, true, false, false>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
             } else {
-                psi3_fv_tma_block<2, false, true>(&r.map_psis, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                psi3_fv_tma_block<2, false, true, false, false>(&r.map_psis, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
             }
         }
         __syncthreads();

@@ -242,13 +242,13 @@ struct TmaArgs {
     int *status;
 };
 
-template <int STAGE, bool NOISE>
+template <int STAGE, bool NOISE, bool RK>
 __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
                                                             const __grid_constant__ CUtensorMap u_map,
                                                             const TmaArgs ta)
 {
     extern __shared__ __align__(1024) float tsmem[];
-    psi3_fv_tma_block<STAGE, NOISE>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x, blockIdx.y, blockIdx.z, tsmem);
+    psi3_fv_tma_block<STAGE, NOISE, false, false, RK>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x, blockIdx.y, blockIdx.z, tsmem);
 }
 
 // batched: block b of the launch works on L.psi[b]
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
     if (threadIdx.x == 0) psi_batch_args(r, ds, STAGE, sa);
     __syncthreads();
     const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[(int)(ds & 1)] : &r.map_psis;
-    psi3_fv_tma_block<STAGE, NOISE, false, true>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
+    psi3_fv_tma_block<STAGE, NOISE, false, true, false>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
 }
 
 __global__ void advance_kernel(long long *dstep) { *dstep += 1; }
@@ -358,11 +358,13 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
         kernel<<<grid, PS_NT, bytes, st>>>(pm, um, ta);
         return cudaGetLastError();
     };
-    if (stage == 1) {
-        if (noise) return go(psi3_fv_tma_kernel<1, true>, sm + sizeof(float) * FV_NOISE_FLOATS);
-        return go(psi3_fv_tma_kernel<1, false>, sm);
+    const size_t smn = sm + sizeof(float) * FV_NOISE_FLOATS;
+    if (a.rk4) {
+        if (stage == 1) return noise ? go(psi3_fv_tma_kernel<1, true, true>, smn) : go(psi3_fv_tma_kernel<1, false, true>, sm);
+        return go(psi3_fv_tma_kernel<2, false, true>, sm);
     }
-    return go(psi3_fv_tma_kernel<2, false>, sm);
+    if (stage == 1) return noise ? go(psi3_fv_tma_kernel<1, true, false>, smn) : go(psi3_fv_tma_kernel<1, false, false>, sm);
+    return go(psi3_fv_tma_kernel<2, false, false>, sm);
 }
 
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,

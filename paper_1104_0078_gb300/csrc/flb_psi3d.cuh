@@ -39,11 +39,12 @@ struct Psi3Args {
 //   RK4: k_s = D_s + eta; stage 1 writes psi + k1/2 and E = psi + eta + D1/6 and
 //     keeps eta; stages 2, 3 write psi^n + k2/2, psi^n + k3 and add D_s/3 to E;
 //     stage 4 writes E + D4/6 = psi^n + (k1 + 2 k2 + 2 k3 + k4)/6.
-template <int STAGE, bool COH>
+//   RK false compiles the RK4 branches out (only for launches with a.rk4 == 0).
+template <int STAGE, bool COH, bool RK = true>
 __device__ __forceinline__ float rk_stage_out(const Psi3Args &a, int x, int y, int z, int si, float pv, float D,
                                               float eta)
 {
-    if (a.rk4) {
+    if (RK && a.rk4) {
         constexpr float sixth = 1.f / 6.f, third = 1.f / 3.f;
         if (a.rk4 == 1) {
             a.E[si] = pv + eta + sixth * D;
@@ -117,12 +118,13 @@ constexpr int FV_NOISE_FLOATS = 6 * H1N;
 // Shared memory then holds only the current mu, flux and noise planes (two of
 // each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
 // formed, the flux of plane p-2, and the output of plane p-3 completes.
-template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false>
+template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false, bool RK = true>
 __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
                                                   const Psi3Args &a, int *status, int bx, int by, int bz,
                                                   float *tsmem)
 {
     if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
+    const int rk4 = RK ? a.rk4 : 0;                       // RK false: a launch without RK4
     float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
     float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
     float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][H2N]     mu plane, by parity
@@ -215,8 +217,8 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         float e_pre = 0.f, n_pre = 0.f, b_pre = 0.f;
         if (STAGE == 2 && active && p - 3 >= z0) {
             const int sp = x + g.nx * (y + g.ny * (p - 3));
-            if (!a.rk4 || a.rk4 > 1) e_pre = COH ? __ldcg(a.E + sp) : a.E[sp];
-            if (a.rk4 == 2 || a.rk4 == 3) {
+            if (!rk4 || rk4 > 1) e_pre = COH ? __ldcg(a.E + sp) : a.E[sp];
+            if (rk4 == 2 || rk4 == 3) {
                 const int bp = g.pidx32(x, y, p - 3);
                 n_pre = COH ? __ldcg(a.Dn + sp) : a.Dn[sp];
                 b_pre = COH ? __ldcg(a.base + bp) : a.base[bp];
@@ -348,15 +350,15 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 const float Dn = (STAGE == 1 && NOISE) ? dn * (1.f / 12.f) : 0.f;
                 const float pv = STAGE == 1 ? tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)] : 0.f;
                 float out;
-                if (STAGE == 2 && !a.rk4) {
+                if (STAGE == 2 && !rk4) {
                     out = e_pre + 0.5f * Dd;
-                } else if (STAGE == 2 && a.rk4 == 4) {
+                } else if (STAGE == 2 && rk4 == 4) {
                     out = e_pre + (1.f / 6.f) * Dd;
-                } else if (STAGE == 2 && a.rk4 >= 2) {  // stages 2 and 3: E += D/3, out = psi^n + c (D + eta)
+                } else if (STAGE == 2 && rk4 >= 2) {  // stages 2 and 3: E += D/3, out = psi^n + c (D + eta)
                     a.E[si] = e_pre + (1.f / 3.f) * Dd;
-                    out = a.rk4 == 2 ? b_pre + 0.5f * (Dd + n_pre) : b_pre + Dd + n_pre;
+                    out = rk4 == 2 ? b_pre + 0.5f * (Dd + n_pre) : b_pre + Dd + n_pre;
                 } else {
-                    out = rk_stage_out<STAGE, COH>(a, x, y, z, si, pv, Dd, Dn);
+                    out = rk_stage_out<STAGE, COH, RK>(a, x, y, z, si, pv, Dd, Dn);
                 }
                 store_padded(a.out, g, x, y, z, out, 3);
             }
