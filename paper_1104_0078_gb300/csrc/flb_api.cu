@@ -486,12 +486,14 @@ LBArgs lb_args(const Rep &r, float *psi_n)
 // The Runge-Kutta stages of psi (3D) for the current step of replica r, advected
 // by the velocity in r.u.  They write only step scratch (psi*, E) and the other
 // psi buffer, so repeating them leaves the state unchanged (the autotuner relies
-// on it).
+// on it).  Stage 1 takes mu of psi^n from r.mu when the step formed it there for
+// the force (FV stage 1 then skips forming it).
 int launch_psi_stages(flb_handle *h, Rep &r)
 {
     const flb_params &p = r.p;
     cudaStream_t st = h->st;
     float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
+    const float *mu_n = (p.coupling & FLB_COUPLE_FORCE) && p.force_grad != FLB_FORCE_STRESS ? r.mu : nullptr;
     const bool noisy = p.kT > 0 && p.M > 0;
     const bool heun = p.integrator == FLB_HEUN;
     const int advect = (p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
@@ -503,16 +505,16 @@ int launch_psi_stages(flb_handle *h, Rep &r)
         for (int s = 0; s < 4; ++s)
             FLB_TRY(launch_psi3(r.g, p.psi_scheme, s == 0 ? 1 : 2, s == 0 && noisy, in[s], r.u, out[s], r.E,
                                 (float)p.A, (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, 0, key, r.step,
-                                r.zc, s + 1, psi_n, r.Dn, h->status, st));
+                                r.zc, s + 1, psi_n, r.Dn, s == 0 ? mu_n : nullptr, h->status, st));
         return FLB_OK;
     }
     FLB_TRY(launch_psi3(r.g, p.psi_scheme, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
                         (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, r.zc, 0,
-                        nullptr, nullptr, h->status, st));
+                        nullptr, nullptr, mu_n, h->status, st));
     if (heun)
         FLB_TRY(launch_psi3(r.g, p.psi_scheme, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
                             (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, r.zc, 0, nullptr, nullptr,
-                            h->status, st));
+                            nullptr, h->status, st));
     return FLB_OK;
 }
 

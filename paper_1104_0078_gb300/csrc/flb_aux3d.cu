@@ -1,9 +1,10 @@
 // flb_aux3d.cu -- the D3Q19 step kernels around the collide-stream.
 //
 // mu3_kernel writes the chemical potential mu = A psi + B psi^3 - K lap_SO psi
-// (Sec. II.A; SO stencil of App. A) on the interior and one ghost layer, for the
-// force density of the collide-stream; with the stress-form force sigma3_kernel
-// writes the order-parameter stress (Eq. muf) there instead.  vel3_kernel runs after it: it gathers
+// (Sec. II.A; SO stencil of App. A) on the interior and MU3_HALO = 2 ghost
+// layers, for the force density of the collide-stream (1 layer) and the FV psi
+// stage 1 of the same step (2 layers); with the stress-form force sigma3_kernel
+// writes the order-parameter stress (Eq. muf) on 1 ghost layer instead.  vel3_kernel runs after it: it gathers
 // the populations the next step pulls (the planes just written) and writes the
 // velocity (sum fbar c + F/2)/rho of the new fluid state, which advects psi
 // (Gauss-Seidel coupling: the psi step follows the fluid step).  Both have a
@@ -33,22 +34,24 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_kernel(const LBArgs 
     vel3_block<T, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// mu = A psi + B psi^3 - K lap_SO psi on the interior and one ghost layer.  A
-// block owns a 32 x 4 column of (x, y) in [-1, nx] x [-1, ny] and marches
-// MU_ZC planes of z in [-1, nz]; each thread keeps, for the planes below and
+// mu = A psi + B psi^3 - K lap_SO psi on the interior and HALO ghost layers
+// (psi holds images to 3 layers, so HALO <= 2).  A block owns a 32 x 4 column
+// of (x, y) in [-HALO, nx + HALO) x [-HALO, ny + HALO) and marches MU_ZC planes
+// of z in [-HALO, nz + HALO); each thread keeps, for the planes below and
 // at z, the centre a, the 4 in-plane faces b and the 4 in-plane diagonals d of
 // psi, so that (Eq. solap)
 //   22 lap_SO psi(z) = 6 [b(z) + a(z-1) + a(z+1)] + 3 [d(z) + b(z-1) + b(z+1)]
 //                      + d(z-1) + d(z+1) - 80 a(z)
 // takes 9 loads per plane instead of 27.
+template <int HALO = 1>
 __device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
                                           float B, float K, int bx, int by, int bz)
 {
-    const int x = bx * MU_BX + (int)threadIdx.x - 1;
-    const int y = by * MU_BY + (int)threadIdx.y - 1;
-    const int zb = bz * MU_ZC - 1;                          // first output plane
-    const int ze = min(zb + MU_ZC, g.nz + 1);               // one past the last
-    if (x > g.nx || y > g.ny || zb >= ze) return;
+    const int x = bx * MU_BX + (int)threadIdx.x - HALO;
+    const int y = by * MU_BY + (int)threadIdx.y - HALO;
+    const int zb = bz * MU_ZC - HALO;                       // first output plane
+    const int ze = min(zb + MU_ZC, g.nz + HALO);            // one past the last
+    if (x >= g.nx + HALO || y >= g.ny + HALO || zb >= ze) return;
     mu3_column<false>(g, psi, mu, A, B, K, x, y, zb, ze);
 }
 
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(MU_BX *MU_BY) sigma3_kernel(const Geom g, cons
 __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,
                                                           float *__restrict__ mu, float A, float B, float K)
 {
-    mu3_block(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
+    mu3_block<MU3_HALO>(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
@@ -100,7 +103,8 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_batch_kernel(const B
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)
 {
     const dim3 block(MU_BX, MU_BY, 1);
-    const dim3 grid((g.nx + 2 + MU_BX - 1) / MU_BX, (g.ny + 2 + MU_BY - 1) / MU_BY, (g.nz + 2 + MU_ZC - 1) / MU_ZC);
+    constexpr int E = 2 * MU3_HALO;
+    const dim3 grid((g.nx + E + MU_BX - 1) / MU_BX, (g.ny + E + MU_BY - 1) / MU_BY, (g.nz + E + MU_ZC - 1) / MU_ZC);
     mu3_kernel<<<grid, block, 0, st>>>(g, psi, mu, A, B, K);
     return cudaGetLastError();
 }

@@ -311,6 +311,16 @@ __device__ __forceinline__ void store_padded(float *a, const Geom &g, int x, int
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// mu = A psi + B psi^3 - K lap_SO psi (Sec. II.A) from the partial sums of the SO
+// stencil (Eq. solap): 22 lap_SO psi = 6 n1 + 3 n2 + n3 - 80 psi, with n1, n2, n3
+// the sums over the faces, edges and corners.  Every operation is rounded
+// explicitly, so the mu field and the FV stage's own mu get the same bits.
+__device__ __forceinline__ float mu_so(float A, float B, float k22, float ps, float n1, float n2, float n3)
+{
+    const float l22 = __fmaf_rn(6.f, n1, __fmaf_rn(3.f, n2, __fmaf_rn(-80.f, ps, n3)));
+    return __fmaf_rn(-k22, l22, __fmaf_rn(__fmul_rn(B, __fmul_rn(ps, ps)), ps, __fmul_rn(A, ps)));
+}
+
 // ---------------------------------------------------------------------------
 // Argument blocks
 // ---------------------------------------------------------------------------
@@ -506,12 +516,14 @@ cudaError_t launch_vel15(const LBArgs &a, int storage, cudaStream_t s);  // D3Q1
 cudaError_t launch_mu3_batch(const BatchLists &L, cudaStream_t st);
 cudaError_t launch_vel3_batch(const BatchLists &L, int storage, bool force, cudaStream_t st);
 cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
-// one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu)
+// one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu); mu_in: the mu
+// of the stage input on the interior and 2 ghost layers, or null (FV stage 1 then
+// forms it)
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
                         const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
-                        int *status, cudaStream_t st);
-// mu on the interior and one ghost layer of a 3D box (flb_lb3d.cu)
+                        const float *mu_in, int *status, cudaStream_t st);
+// mu on the interior and MU3_HALO = 2 ghost layers of a 3D box (flb_aux3d.cu)
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,
                            cudaStream_t st);

@@ -8,6 +8,10 @@
 
 namespace flb {
 
+// Ghost layers of the per-replica mu field: 1 for the force's gradient, 2 for
+// the FV psi stage 1, which reads mu on its flux region + 1.
+constexpr int MU3_HALO = 2;
+
 // The column (x, y), output planes zb .. ze-1 of the mu field.
 template <bool COH = false>
 __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
@@ -23,7 +27,7 @@ __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restric
         const float d2 = (ldf<COH>(psi + c - 1 - Y) + ldf<COH>(psi + c + 1 - Y)) + (ldf<COH>(psi + c - 1 + Y) + ldf<COH>(psi + c + 1 + Y));
         if (p - 1 >= zb) {
             const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
-            mu[c - Z] = A * a1 + B * a1 * a1 * a1 - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * a1);
+            mu[c - Z] = mu_so(A, B, k22, a1, n1, n2, n3);
         }
         a0 = a1; b0 = b1; d0 = d1;
         a1 = a2; b1 = b2; d1 = d2;

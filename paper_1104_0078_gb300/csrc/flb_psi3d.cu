@@ -242,13 +242,16 @@ struct TmaArgs {
     int *status;
 };
 
-template <int STAGE, bool NOISE, bool RK>
+// MU_IN: stage 1 reads mu of its input from mu_map instead of forming it
+template <int STAGE, bool NOISE, bool RK, bool MU_IN>
 __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
                                                             const __grid_constant__ CUtensorMap u_map,
+                                                            const __grid_constant__ CUtensorMap mu_map,
                                                             const TmaArgs ta)
 {
     extern __shared__ __align__(1024) float tsmem[];
-    psi3_fv_tma_block<STAGE, NOISE, false, false, RK>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x, blockIdx.y, blockIdx.z, tsmem);
+    psi3_fv_tma_block<STAGE, NOISE, false, false, RK, MU_IN>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x, blockIdx.y,
+                                                            blockIdx.z, tsmem, &mu_map);
 }
 
 // batched: block b of the launch works on L.psi[b]
@@ -333,7 +336,8 @@ cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *status, cudaStream_t st)
+static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, const float *mu_in, int *status,
+                                 cudaStream_t st)
 {
     const Geom &g = a.g;
     CUtensorMap pm, um;
@@ -347,6 +351,13 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
     const uint32_t ub[4] = {(uint32_t)TB_X, (uint32_t)H1Y, 1, 3};
     e = encode_tensor_map_f32(&um, a.u, 4, ud, us, ub);
     if (e != cudaSuccess) return e;
+    CUtensorMap mm = pm;  // unused unless stage 1 reads mu
+    const bool mu = stage == 1 && mu_in != nullptr;
+    if (mu) {
+        const uint32_t mb[3] = {(uint32_t)TB_X, (uint32_t)H2Y, 1};
+        e = encode_tensor_map_f32(&mm, mu_in, 3, pd, ps, mb);
+        if (e != cudaSuccess) return e;
+    }
     TmaArgs ta;
     ta.a = a;
     ta.status = status;
@@ -355,22 +366,28 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, int *
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
-        kernel<<<grid, PS_NT, bytes, st>>>(pm, um, ta);
+        kernel<<<grid, PS_NT, bytes, st>>>(pm, um, mm, ta);
         return cudaGetLastError();
     };
     const size_t smn = sm + sizeof(float) * FV_NOISE_FLOATS;
-    if (a.rk4) {
-        if (stage == 1) return noise ? go(psi3_fv_tma_kernel<1, true, true>, smn) : go(psi3_fv_tma_kernel<1, false, true>, sm);
-        return go(psi3_fv_tma_kernel<2, false, true>, sm);
+    const size_t smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS, smmn = smm + sizeof(float) * FV_NOISE_FLOATS;
+    if (stage == 2) return a.rk4 ? go(psi3_fv_tma_kernel<2, false, true, false>, sm)
+                                 : go(psi3_fv_tma_kernel<2, false, false, false>, sm);
+    if (mu) {
+        if (a.rk4) return noise ? go(psi3_fv_tma_kernel<1, true, true, true>, smmn)
+                                : go(psi3_fv_tma_kernel<1, false, true, true>, smm);
+        return noise ? go(psi3_fv_tma_kernel<1, true, false, true>, smmn)
+                     : go(psi3_fv_tma_kernel<1, false, false, true>, smm);
     }
-    if (stage == 1) return noise ? go(psi3_fv_tma_kernel<1, true, false>, smn) : go(psi3_fv_tma_kernel<1, false, false>, sm);
-    return go(psi3_fv_tma_kernel<2, false, false>, sm);
+    if (a.rk4) return noise ? go(psi3_fv_tma_kernel<1, true, true, false>, smn)
+                            : go(psi3_fv_tma_kernel<1, false, true, false>, sm);
+    return noise ? go(psi3_fv_tma_kernel<1, true, false, false>, smn) : go(psi3_fv_tma_kernel<1, false, false, false>, sm);
 }
 
 cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
                         const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
-                        int *status, cudaStream_t st)
+                        const float *mu_in, int *status, cudaStream_t st)
 {
     if (zc < PS_ZC_MIN) return cudaErrorInvalidValue;
     Psi3Args a;
@@ -394,7 +411,7 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
     a.step = step;
     const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + zc - 1) / zc);
     const size_t smem = sizeof(float) * (4 * H3N + 3 * H2N);
-    if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, status, st);
+    if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, mu_in, status, st);
     if (stage == 1) {
         if (noise) return launch_dyn(psi3_fd_kernel<1, true>, grid, smem + sizeof(float) * 13 * H1N, st, a);
         return launch_dyn(psi3_fd_kernel<1, false>, grid, smem, st, a);

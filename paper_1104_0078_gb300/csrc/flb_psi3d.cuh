@@ -93,9 +93,12 @@ constexpr int TP_N = TB_X * H3Y;                           // psi slot floats
 constexpr int TP_SLOT = ((TP_N * 4 + 127) / 128) * 32;     // floats, 128-byte multiple
 constexpr int TU_N = 3 * TB_X * H1Y;                       // u slot floats
 constexpr int TU_SLOT = ((TU_N * 4 + 127) / 128) * 32;
-constexpr int T_PSI_DEPTH = 6, T_U_DEPTH = 3;
+constexpr int TM_N = TB_X * H2Y;                           // mu slot floats (MU_IN)
+constexpr int TM_SLOT = ((TM_N * 4 + 127) / 128) * 32;
+constexpr int T_PSI_DEPTH = 6, T_U_DEPTH = 3, T_MU_DEPTH = 3;
 
 constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * H2N + 6 * H1N;
+constexpr int FV_MU_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + T_MU_DEPTH * TM_SLOT + 6 * H1N;
 constexpr int FV_NOISE_FLOATS = 6 * H1N;
 
 // One block (tile bx, by; z chunk bz).  psi_map / u_map: tensor maps of the stage
@@ -118,19 +121,26 @@ constexpr int FV_NOISE_FLOATS = 6 * H1N;
 // Shared memory then holds only the current mu, flux and noise planes (two of
 // each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
 // formed, the flux of plane p-2, and the output of plane p-3 completes.
-template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false, bool RK = true>
+//
+// MU_IN (stage 1 only): mu of the stage input psi^n already sits in the mu field
+// (mu_map, valid to 2 ghost layers), written for the force of the same step.  Its
+// planes then come by TMA, like psi and u, into a third ring ([TY+4][TX+8], column
+// c <-> x = x0 - 4 + c, row r <-> y = y0 - 2 + r), and the block skips forming mu.
+template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false, bool RK = true, bool MU_IN = false>
 __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
                                                   const Psi3Args &a, int *status, int bx, int by, int bz,
-                                                  float *tsmem)
+                                                  float *tsmem, const CUtensorMap *mu_map = nullptr)
 {
+    static_assert(!MU_IN || STAGE == 1, "mu of psi^n is the input of stage 1 only");
     if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
     const int rk4 = RK ? a.rk4 : 0;                       // RK false: a launch without RK4
     float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
     float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
     float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][H2N]     mu plane, by parity
-    float *sJ = smu + 2 * H2N;                           // [2][3][H1N]  flux plane, by parity
+    float *tms = smu;                                    // MU_IN: [T_MU_DEPTH][TM_SLOT] instead
+    float *sJ = smu + (MU_IN ? T_MU_DEPTH * TM_SLOT : 2 * H2N);  // [2][3][H1N]  flux plane, by parity
     float *sX = sJ + 6 * H1N;                            // [2][3][H1N]  noise plane, by parity (NOISE)
-    __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH];
+    __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH], bar_m[T_MU_DEPTH];
     __shared__ int s_bad;
     const Geom &g = a.g;
     const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
@@ -141,13 +151,14 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const float k22 = a.K * (1.0f / 22.0f);
     const float sdx = sqrtf(2.0f * a.kT * a.M);
     const float m12 = a.M * (1.0f / 12.0f);
-    const int pbase = z0 - 3, ubase = z0 - 1;             // first psi / u plane of the chunk
+    const int pbase = z0 - 3, ubase = z0 - 1, mbase = z0 - 2;  // first psi / u / mu plane of the chunk
     // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
-    // psi-slot centre, u-slot offset, noise counter id
+    // psi-slot centre (-1 off the region; the u slot holds the same point 2 rows
+    // up, the MU_IN mu slot 1 row up), noise counter id
     // Region points are dealt to threads row segment by row segment: the first
     // 32 columns of every row (a full warp reads 32 consecutive words, free of
     // bank conflicts), then the few remaining columns of all rows.
-    int c2[S2], d2[S2], c1[S1], d1[S1], p1[S1], u1[S1], n1[S1];
+    int c2[S2], d2[S2], c1[S1], d1[S1], p1[S1], n1[S1];
 #pragma unroll
     for (int j = 0; j < S2; ++j) {
         int lx, ly;
@@ -163,8 +174,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         const bool ok = threadIdx.x + j * PS_NT < H1N;
         c1[j] = ok ? (lx + 1) + H2X * (ly + 1) : -1;
         d1[j] = lx + H1X * ly;
-        p1[j] = (lx + 3) + TB_X * (ly + 2);
-        u1[j] = (lx + 3) + TB_X * ly;
+        p1[j] = ok ? (lx + 3) + TB_X * (ly + 2) : -1;
         n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
     }
     // per-plane partial sums carried between planes (registers)
@@ -181,6 +191,8 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     if (threadIdx.x == 0) {
         for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
         for (int s = 0; s < T_U_DEPTH; ++s) mbar_init(&bar_u[s], 1);
+        if (MU_IN)
+            for (int s = 0; s < T_MU_DEPTH; ++s) mbar_init(&bar_m[s], 1);
         s_bad = 0;
         fence_barrier_init();
     }
@@ -195,17 +207,22 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         mbar_expect_tx(&bar_u[s], TU_N * 4);
         tma_load_4d(tus + s * TU_SLOT, u_map, &bar_u[s], x0, y0 + GY - 1, qq + g.gz, 0);
     };
+    auto issue_mu = [&](int mm) {
+        const int s = (mm - mbase) % T_MU_DEPTH;
+        mbar_expect_tx(&bar_m[s], TM_N * 4);
+        tma_load_3d(tms + s * TM_SLOT, mu_map, &bar_m[s], x0, y0 + GY - 2, mm + g.gz);
+    };
     if (threadIdx.x == 0) {
         issue_psi(pbase);
         issue_psi(pbase + 1);
     }
-    int last_p = pbase + 1, last_u = ubase - 1;  // highest plane issued (thread 0)
-    int waited_p = pbase - 1, waited_u = ubase - 1;
+    int last_p = pbase + 1, last_u = ubase - 1, last_m = mbase - 1;  // highest plane issued (thread 0)
+    int waited_p = pbase - 1, waited_u = ubase - 1, waited_m = mbase - 1;
 
     // Rotating ring positions, advanced once per plane (no divisions in the loop):
     // psi plane p sits in slot r6 of phase ph6; the velocity of the next flux plane
     // in slot ru of phase uph.
-    int r6 = 0, ph6 = 0, ru = 0, uph = 0;
+    int r6 = 0, ph6 = 0, ru = 0, uph = 0, rm = 0, mph = 0;
     for (int p = z0 - 3; p <= z1 + 2; ++p) {
         const int s1 = r6 == 0 ? T_PSI_DEPTH - 1 : r6 - 1;  // psi slots of p-1, p-2, p-3
         const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
@@ -227,7 +244,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
         if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
         waited_p = p;
-        {
+        if (!MU_IN) {
             const float *P = tps + r6 * TP_SLOT;
             float *dst = smu + ((p - 1) & 1) * H2N;
             const bool emit = p - 1 >= z0 - 2;
@@ -243,7 +260,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     const float nn1 = pb[j][1] + (pa[j][0] + ac);
                     const float nn2 = pd[j][1] + (pb[j][0] + bc);
                     const float nn3 = pd[j][0] + dc;
-                    dst[d2[j]] = a.A * ps + a.B * ps * ps * ps - k22 * (6.f * nn1 + 3.f * nn2 + nn3 - 80.f * ps);
+                    dst[d2[j]] = mu_so(a.A, a.B, k22, ps, nn1, nn2, nn3);
                 }
                 pa[j][0] = pa[j][1];
                 pb[j][0] = pb[j][1];
@@ -255,10 +272,11 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         }
         __syncthreads();  // mu plane p-1 complete; every read of the psi slot of p-4 and of the u slot of p-3 done
         if (s_bad) break;
-        if (threadIdx.x == 0) {  // refill those slots: psi plane p+2 (used at p+2), u plane p (used at p+2)
-            fence_proxy_async();
+        if (threadIdx.x == 0) {  // refill those slots: psi plane p+2 (used at p+2), u plane p (used at p+2),
+            fence_proxy_async();  // mu plane p+1 (used at p+2)
             if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
             if (a.advect && p >= ubase && p <= z1) { issue_u(p); last_u = p; }
+            if (MU_IN && p + 1 >= mbase && p + 1 <= z1 + 1) { issue_mu(p + 1); last_m = p + 1; }
         }
         // (B) mu partials of plane m = p-1 at the flux points; flux (and noise) of plane m-1
         const int m = p - 1;
@@ -273,17 +291,25 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 uph ^= ru == 0;
             }
             const float *Mu = smu + (m & 1) * H2N;
+            if (MU_IN) {  // mu plane m has landed in its ring slot
+                if (!mbar_wait(&bar_m[rm], mph, status)) s_bad = 1;
+                waited_m = m;
+                Mu = tms + rm * TM_SLOT;
+                rm = rm == T_MU_DEPTH - 1 ? 0 : rm + 1;
+                mph ^= rm == 0;
+            }
+            constexpr int MP = MU_IN ? TB_X : H2X;  // row pitch of the mu plane
             const float *ps = tps + s2 * TP_SLOT;  // psi plane m-1
             float *J = sJ + ((m - 1) & 1) * 3 * H1N;
             float *X = sX + ((m - 1) & 1) * 3 * H1N;
             const int zid = g.nx * g.ny * wrapi(m - 1, g.nz);
 #pragma unroll
             for (int j = 0; j < S1; ++j) {
-                const int c = c1[j];
-                if (c < 0) continue;
-                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + H2X], mym = Mu[c - H2X];
-                const float mpp = Mu[c + 1 + H2X], mpm = Mu[c + 1 - H2X], mmp = Mu[c - 1 + H2X],
-                            mmm = Mu[c - 1 - H2X];
+                if ((MU_IN ? p1[j] : c1[j]) < 0) continue;
+                const int c = MU_IN ? p1[j] - TB_X : c1[j];
+                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + MP], mym = Mu[c - MP];
+                const float mpp = Mu[c + 1 + MP], mpm = Mu[c + 1 - MP], mmp = Mu[c - 1 + MP],
+                            mmm = Mu[c - 1 - MP];
                 const float ex = mxp - mxm, ey = myp - mym;
                 const float Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
                 const float Zp = 2.f * Mu[c] + ((mxp + mxm) + (myp + mym));
@@ -299,9 +325,10 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     float jx = m12 * gx, jy = m12 * gy, jz = m12 * gz;
                     if (a.advect) {
                         const float pv = ps[p1[j]];
-                        jx -= uq[u1[j]] * pv;
-                        jy -= uq[TB_X * H1Y + u1[j]] * pv;
-                        jz -= uq[2 * TB_X * H1Y + u1[j]] * pv;
+                        const int uo = p1[j] - 2 * TB_X;
+                        jx -= uq[uo] * pv;
+                        jy -= uq[TB_X * H1Y + uo] * pv;
+                        jz -= uq[2 * TB_X * H1Y + uo] * pv;
                     }
                     J[k] = jx;
                     J[H1N + k] = jy;
@@ -372,9 +399,14 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             mbar_wait(&bar_p[(pp - pbase) % T_PSI_DEPTH], ((pp - pbase) / T_PSI_DEPTH) & 1, nullptr);
         for (int qq = waited_u + 1; qq <= last_u; ++qq)
             mbar_wait(&bar_u[(qq - ubase) % T_U_DEPTH], ((qq - ubase) / T_U_DEPTH) & 1, nullptr);
+        if (MU_IN)
+            for (int mm = waited_m + 1; mm <= last_m; ++mm)
+                mbar_wait(&bar_m[(mm - mbase) % T_MU_DEPTH], ((mm - mbase) / T_MU_DEPTH) & 1, nullptr);
         // the barriers may be initialised again by a later task of a persistent block
         for (int k = 0; k < T_PSI_DEPTH; ++k) mbar_inval(&bar_p[k]);
         for (int k = 0; k < T_U_DEPTH; ++k) mbar_inval(&bar_u[k]);
+        if (MU_IN)
+            for (int k = 0; k < T_MU_DEPTH; ++k) mbar_inval(&bar_m[k]);
     }
 }
 

@@ -34,3 +34,33 @@ def test_device_normals_argument_checks():
     assert lib.flb_gaussians(1, 0, 0, 0xFFFFFFFF, 4, 1, buf.data_ptr(), None) == F.FLB_EINVAL
     assert lib.flb_gaussians(1, 0, 0, 0, 4, 1, None, None) == F.FLB_EINVAL
     assert lib.flb_gaussians(1, 0, 0, 0, 0, 1, buf.data_ptr(), None) == F.FLB_OK
+
+
+def test_device_normals_moments_and_tails_1e8():
+    """10^8 device normals (6.25e6 sites x 16, one LB stream): mean 0, variance 1,
+    skewness 0 and kurtosis 3 within 5 sigma of their sampling errors, and the
+    frequencies of |z| > 3, 4, 5 within 5 sigma of the normal law's.  The tails
+    come from the smallest radius uniforms (u down to 2^-24, |z| <= 5.77), where
+    the table-driven ln u works on the lowest cells."""
+    import math
+    import torch
+    nsites, nb = 6_250_000, 4
+    g = F.gaussians(20240601, 12345, 0, 7, nsites, nb).double().flatten()
+    n = g.numel()
+    assert n == 100_000_000 and bool(torch.isfinite(g).all())
+    m1 = g.mean().item()
+    c = g - m1
+    m2 = (c * c).mean().item()
+    m3 = (c * c * c).mean().item() / m2**1.5
+    m4 = ((c * c) ** 2).mean().item() / m2**2
+    assert abs(m1) < 5 * math.sqrt(1 / n), m1
+    assert abs(m2 - 1) < 5 * math.sqrt(2 / n), m2
+    assert abs(m3) < 5 * math.sqrt(6 / n), m3
+    assert abs(m4 - 3) < 5 * math.sqrt(24 / n), m4
+    a = g.abs()
+    for t in (3.0, 4.0, 5.0):
+        p = math.erfc(t / math.sqrt(2))  # P(|z| > t)
+        k = int((a > t).sum().item())
+        assert abs(k - n * p) < 5 * math.sqrt(n * p * (1 - p)) + 1, (t, k, n * p)
+    # 24-bit radius uniforms bound the draws by sqrt(-2 ln 2^-24) = 5.768
+    assert a.max().item() <= math.sqrt(48 * math.log(2)) + 1e-5
