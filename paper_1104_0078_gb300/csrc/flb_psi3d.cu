@@ -102,9 +102,12 @@ __constant__ int8_t kFDL[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}
 
 // Two 512-thread blocks per SM (64 registers): with one, the noisy stage ran at
 // 25% of the warp slots and half of the issue rate.
-template <int STAGE, bool NOISE>
-__global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
+// MU_IN (stage 1): mu of psi^n on tile + 1 is read from the force's mu field
+// (mu_in, same padded layout as u), one plane ahead, instead of formed from psi.
+template <int STAGE, bool NOISE, bool MU_IN = false>
+__global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a, const float *__restrict__ mu_in)
 {
+    static_assert(!MU_IN || STAGE == 1, "mu of psi^n is the input of stage 1 only");
     extern __shared__ float smem[];
     float *sps = smem;           // [4][H3N]
     float *smu = sps + 4 * H3N;  // [3][H2N]
@@ -128,6 +131,10 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
 #pragma unroll
         for (int j = 0; j < S3; ++j) nxt[j] = R.g3[j] >= 0 ? __ldg(src + R.g3[j]) : 0.f;
     }
+    // MU_IN: mu of plane q = p - 1 (loaded the iteration before) and of plane p
+    float mcur[S1], mnx[S1];
+#pragma unroll
+    for (int j = 0; j < S1; ++j) mcur[j] = mnx[j] = 0.f;
 
     for (int p = z0 - 2; p <= z1 + 1; ++p) {
         // this iteration's output plane p-2: its global inputs (the Heun
@@ -136,6 +143,11 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
         const int zo = p - 2;
         const bool out_here = zo >= z0 && active;
         float e_pre = 0.f, u_pre[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (MU_IN && p >= z0 - 1 && p <= z1) {
+            const float *src = mu_in + (size_t)plane * (p + g.gz);
+#pragma unroll
+            for (int j = 0; j < S1; ++j) mnx[j] = R.c1[j] >= 0 ? __ldg(src + R.u1[j]) : 0.f;
+        }
         if (out_here) {
             if (STAGE == 2 && !a.rk4) e_pre = a.E[x + g.nx * (y + g.ny * zo)];
             if (a.advect) {
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
             for (int j = 0; j < S1; ++j) {
                 const int c = R.c1[j];
                 if (c < 0) continue;
-                dst[c] = mu_point<H3X>(pm, p0, pp, R.p1[j], a.A, a.B, k22);
+                dst[c] = MU_IN ? mcur[j] : mu_point<H3X>(pm, p0, pp, R.p1[j], a.A, a.B, k22);
             }
             if (NOISE) {
                 const int zid = g.nx * g.ny * wrapi(q, g.nz);
@@ -234,6 +246,10 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a)
         accm = acc0;
         acc0 = accp;
         accp = 0.f;
+        if (MU_IN) {
+#pragma unroll
+            for (int j = 0; j < S1; ++j) mcur[j] = mnx[j];
+        }
     }
 }
 
@@ -301,11 +317,11 @@ cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool
 }
 
 template <typename K>
-static cudaError_t launch_dyn(K kernel, dim3 grid, size_t smem, cudaStream_t st, const Psi3Args &a)
+static cudaError_t launch_dyn(K kernel, dim3 grid, size_t smem, cudaStream_t st, const Psi3Args &a, const float *mu_in)
 {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kernel<<<grid, PS_NT, smem, st>>>(a);
+    kernel<<<grid, PS_NT, smem, st>>>(a, mu_in);
     return cudaGetLastError();
 }
 
@@ -412,11 +428,16 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
     const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + zc - 1) / zc);
     const size_t smem = sizeof(float) * (4 * H3N + 3 * H2N);
     if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, mu_in, status, st);
-    if (stage == 1) {
-        if (noise) return launch_dyn(psi3_fd_kernel<1, true>, grid, smem + sizeof(float) * 13 * H1N, st, a);
-        return launch_dyn(psi3_fd_kernel<1, false>, grid, smem, st, a);
+    const size_t smn = smem + sizeof(float) * 13 * H1N;
+    if (stage == 1 && mu_in) {
+        if (noise) return launch_dyn(psi3_fd_kernel<1, true, true>, grid, smn, st, a, mu_in);
+        return launch_dyn(psi3_fd_kernel<1, false, true>, grid, smem, st, a, mu_in);
     }
-    return launch_dyn(psi3_fd_kernel<2, false>, grid, smem, st, a);
+    if (stage == 1) {
+        if (noise) return launch_dyn(psi3_fd_kernel<1, true>, grid, smn, st, a, nullptr);
+        return launch_dyn(psi3_fd_kernel<1, false>, grid, smem, st, a, nullptr);
+    }
+    return launch_dyn(psi3_fd_kernel<2, false>, grid, smem, st, a, nullptr);
 }
 
 }  // namespace flb

@@ -60,6 +60,21 @@ def test_coupled_step_matches_oracle(dim, q, shape, scheme, integ):
     assert s.get_step() == 25
 
 
+@pytest.mark.parametrize("integ", [1, 2, 4])
+def test_noise_free_coupled_fv_matches_oracle(integ):
+    # kT = 0 with the force coupled: FV stage 1 without noise, taking mu of psi^n
+    # from the force's mu field, on a box of several ragged tiles.  A > 0: a large
+    # psi relaxes and drives the fluid (in a quench the FP32 trajectory separates
+    # from the FP64 one exponentially, and without noise the deviations the error
+    # is measured against stay small)
+    d = dict(dim=3, q=19, nx=37, ny=23, nz=19, tau=0.8, kT=0.0, A=0.05, B=0.3, K=0.04, M=0.1, scheme=1,
+             integrator=integ, coupling=3, seed=21)
+    s, (fg, pg, ug), st, feq = _run_pair(d, 20, amp_psi=0.3)
+    assert field_error(fg, st.f, feq) < TOL
+    assert field_error(pg, st.psi) < TOL
+    assert field_error(ug, st.u) < TOL
+
+
 FORCE_CASES = [(dim, q, scheme, fg) for dim, q in ((2, 9), (3, 19)) for scheme in (0, 1) for fg in (1, 2, 3)]
 FORCE_CASES += [(3, 15, 0, 1), (3, 15, 0, 3)]
 
@@ -250,6 +265,17 @@ def test_interface_heights_match_oracle():
     dh = 2e-5
     assert np.all(np.abs(H_gpu - H) <= 2 * np.sqrt(H) * dh + dh * dh)
     assert H.max() > 1e-4
+    # the same surfaces located by the oracle in the device's own FP32 psi: the
+    # crossing cells are decided on the same values, so what remains is the FP32
+    # arithmetic of the device's heights and of its DFT, which transforms the raw
+    # heights (|h| < 32, mean included) with FP32 products and lane sums: ~1e-5
+    # per mode, the same bound as above, now without the trajectories' divergence
+    pg, _ = s.get_psi_u()
+    g1, g2 = O.interface_heights(op, pg.astype(np.float64))
+    assert not np.isnan(g1).any() and not np.isnan(g2).any()
+    Hs = 0.5 * (O.height_spectrum(g1) + O.height_spectrum(g2))
+    Hs[0, 0] = 0.0
+    assert np.all(np.abs(H_gpu - Hs) <= 2 * np.sqrt(Hs) * dh + dh * dh)
 
 
 def test_checkpoint_resume_bitwise():
