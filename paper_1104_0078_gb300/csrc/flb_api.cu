@@ -313,7 +313,8 @@ size_t carve_all(flb_handle &h, char *base)
     for (Rep &r : h.reps) {
         if (r.dim != 3) continue;
         const Geom &g = r.g;
-        nmu += ((g.nx + 2 + MU_BX - 1) / MU_BX) * ((g.ny + 2 + MU_BY - 1) / MU_BY) * ((g.nz + 2 + MU_ZC - 1) / MU_ZC);
+        constexpr int E = 2 * MU3_HALO;
+        nmu += ((g.nx + E + MU_BX - 1) / MU_BX) * ((g.ny + E + MU_BY - 1) / MU_BY) * ((g.nz + E + MU_ZC - 1) / MU_ZC);
         nlb += packed_blocks(g, LB_BX * LB_BY * LB_BZ);
         npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC_MIN - 1) / PS_ZC_MIN);
     }
@@ -759,9 +760,10 @@ int batch_upload_lists(flb_handle *h)
     v.clear();
     for (int r = 0; r < (int)h->reps.size(); ++r) {
         const Geom &g = h->reps[(size_t)r].g;
-        for (int bz = 0; bz < (g.nz + 2 + MU_ZC - 1) / MU_ZC; ++bz)
-            for (int by = 0; by < (g.ny + 2 + MU_BY - 1) / MU_BY; ++by)
-                for (int bx = 0; bx < (g.nx + 2 + MU_BX - 1) / MU_BX; ++bx) v.push_back({r, bx, by, bz});
+        constexpr int E = 2 * MU3_HALO;
+        for (int bz = 0; bz < (g.nz + E + MU_ZC - 1) / MU_ZC; ++bz)
+            for (int by = 0; by < (g.ny + E + MU_BY - 1) / MU_BY; ++by)
+                for (int bx = 0; bx < (g.nx + E + MU_BX - 1) / MU_BX; ++bx) v.push_back({r, bx, by, bz});
     }
     const size_t nmu = v.size();
     for (int r = 0; r < (int)h->reps.size(); ++r)  // row-packed collide-stream / velocity blocks
@@ -810,6 +812,7 @@ int batch_upload_table(flb_handle *h)
         d.heun = r.p.integrator == FLB_HEUN;
         d.advect = (r.p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
         d.noise = r.p.kT > 0 && r.p.M > 0;
+        d.mu_in = (r.p.coupling & FLB_COUPLE_FORCE) && r.p.force_grad != FLB_FORCE_STRESS;
         d.zc = r.zc;
         d.pstep_tasks = k < h->p_pstep.size() ? h->p_pstep[k] : 0;
         const uint64_t pd[3] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz};
@@ -822,6 +825,8 @@ int batch_upload_table(flb_handle *h)
         const uint64_t us[3] = {(uint64_t)g.px * 4, (uint64_t)g.px * g.py * 4, (uint64_t)g.pn * 4};
         const uint32_t ub[4] = {(uint32_t)(PS_TX + 8), (uint32_t)(PS_TY + 2), 1, 3};
         if (encode_tensor_map_f32(&d.map_u, r.u, 4, ud, us, ub) != cudaSuccess) return FLB_ECUDA;
+        const uint32_t mb[3] = {(uint32_t)(PS_TX + 8), (uint32_t)(PS_TY + 4), 1};
+        if (encode_tensor_map_f32(&d.map_mu, r.mu, 3, pd, ps, mb) != cudaSuccess) return FLB_ECUDA;
     }
     int rc = cuerr(cudaMemcpyAsync(h->b_reps, t.data(), t.size() * sizeof(BatchRep), cudaMemcpyHostToDevice, h->st));
     if (rc == FLB_OK) rc = cuerr(cudaMemsetAsync(h->b_dstep, 0, sizeof(long long), h->st));
@@ -853,6 +858,15 @@ int batch_kernels_per_step(const flb_handle *h)
     return (force ? 1 : 0) + 1 + 1 + 1 + (p.integrator == FLB_HEUN ? 1 : 0) + 1;
 }
 
+// Every replica's step forms mu of psi^n for its force, so the batched FV
+// stage 1 may read it instead of forming it.
+bool batch_mu_in(const flb_handle *h)
+{
+    for (const Rep &r : h->reps)
+        if (!(r.p.coupling & FLB_COUPLE_FORCE) || r.p.force_grad == FLB_FORCE_STRESS) return false;
+    return true;
+}
+
 // Capture one batched step into a CUDA graph (once per handle).
 int batch_capture(flb_handle *h)
 {
@@ -868,7 +882,8 @@ int batch_capture(flb_handle *h)
     // the kernels' attributes are set by one launch outside the capture on a zero-block list
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return FLB_ECUDA;
-    const cudaError_t e = launch_batch_step(L, p0.storage, ghost, force, 1, p0.integrator == FLB_HEUN, noise, h->st);
+    const cudaError_t e =
+        launch_batch_step(L, p0.storage, ghost, force, 1, p0.integrator == FLB_HEUN, noise, batch_mu_in(h), h->st);
     const cudaError_t e2 = cudaStreamEndCapture(h->st, &gr);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (gr) cudaGraphDestroy(gr);
@@ -1559,7 +1574,7 @@ int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
                 const BatchLists L = batch_lists(h);
                 const float t = time_launches(h, [&]() {
                     h->launches += heun ? 2 : 1;
-                    return cuerr(launch_batch_psi(L, heun, noise, h->st));
+                    return cuerr(launch_batch_psi(L, heun, noise, batch_mu_in(h), h->st));
                 }, reps);
                 if (t < 0.f) return FLB_ECUDA;
                 if (tbest == 0.f || t < tbest) {

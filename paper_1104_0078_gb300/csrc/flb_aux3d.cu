@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchList
             sigma3_column<false>(g, r.psi[par], const_cast<float *>(r.lb.sig), r.A, r.B, r.K, x, y, zb, ze);
         return;
     }
-    mu3_block(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
+    mu3_block<MU3_HALO>(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
 }
 
 template <typename T, bool FORCE>

@@ -242,7 +242,11 @@ constexpr int GZ3 = 3;
 
 // launch geometry of the 3D kernels (shared with the host for the batched block lists)
 constexpr int LB_BX = 32, LB_BY = 4, LB_BZ = 2;   // collide-stream and mu: one thread per site
-constexpr int MU_BX = 32, MU_BY = 4, MU_ZC = 16;  // mu: column tile and planes of a block (interior + 1)
+constexpr int MU_BX = 32, MU_BY = 4, MU_ZC = 16;  // mu: column tile and planes of a block
+// Ghost layers of the mu field written by the per-phase and batched mu kernels:
+// 1 for the force's gradient, 2 for the FV psi stage 1, which reads mu on its
+// flux region + 1.
+constexpr int MU3_HALO = 2;
 constexpr int PS_TX = 32, PS_TY = 16;  // psi stage: column tile of a block
 constexpr int PS_ZC = 64;              // psi stage: default planes per block (the z chunk), tunable per replica
 constexpr int PS_ZC_MIN = 1;           // smallest z chunk (sizes the batched block lists)
@@ -393,11 +397,13 @@ struct alignas(128) BatchRep {
     CUtensorMap map_psi[2];  // tensor maps of psiA, psiB
     CUtensorMap map_psis;    // tensor map of psi* (Heun)
     CUtensorMap map_u;       // tensor map of u (3 components)
+    CUtensorMap map_mu;      // tensor map of mu (FV stage 1 reads it when mu_in)
     LBArgs lb;               // fin = fA, fout = fB, psi = psiA; step = step0
     float *psi[2];           // psiA, psiB
     float *psis, *E;
     float A, B, K, M;
     int heun, advect, noise;
+    int mu_in;               // the step forms mu of psi^n for the force (FV stage 1 may read it)
     int zc;                  // planes per psi block
     int pstep_tasks;         // persistent mode: tasks of this replica per step
 };
@@ -469,10 +475,11 @@ struct BatchLists {
 
 cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
                                   const uint64_t *strides_bytes, const uint32_t *box);
+// mu_in: every replica's step forms mu of psi^n, so FV stage 1 reads it (map_mu)
 cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
-                              bool noise, cudaStream_t st);
+                              bool noise, bool mu_in, cudaStream_t st);
 // the psi stage launches of a batched step alone (no state change: the autotuner times them)
-cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, cudaStream_t st);
+cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, cudaStream_t st);
 
 // ---- persistent batched mode (flb_persist.cu) --------------------------------
 enum { PH_MU = 0, PH_LB = 1, PH_VEL = 2, PH_S1 = 3, PH_S2 = 4, PH_COUNT = 5 };

@@ -8,10 +8,6 @@
 
 namespace flb {
 
-// Ghost layers of the per-replica mu field: 1 for the force's gradient, 2 for
-// the FV psi stage 1, which reads mu on its flux region + 1.
-constexpr int MU3_HALO = 2;
-
 // The column (x, y), output planes zb .. ze-1 of the mu field.
 template <bool COH = false>
 __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,

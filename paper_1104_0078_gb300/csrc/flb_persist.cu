@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
         const long long ds = P.ds0 + s;
         if (task.phase == PH_MU) {
             const Geom &g = r.lb.g;
-            const int x = task.bx * 32 + (t & 31) - 1, y = task.by * PM_BY + (t >> 5) - 1;
-            const int zb = task.bz * MU_ZC - 1, ze = min(zb + MU_ZC, g.nz + 1);
-            if (x <= g.nx && y <= g.ny) {
+            // MU3_HALO ghost layers: stage 1 reads mu on its flux region + 1
+            const int x = task.bx * 32 + (t & 31) - MU3_HALO, y = task.by * PM_BY + (t >> 5) - MU3_HALO;
+            const int zb = task.bz * MU_ZC - MU3_HALO, ze = min(zb + MU_ZC, g.nz + MU3_HALO);
+            if (x < g.nx + MU3_HALO && y < g.ny + MU3_HALO) {
                 if (r.lb.force_kind == 2)
                     sigma3_column<true>(g, r.psi[ds & 1], const_cast<float *>(r.lb.sig), r.A, r.B, r.K, x, y, zb, ze);
                 else
@@ -143,8 +144,18 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
             __syncthreads();
             if (stage == 1) {
                 const CUtensorMap *pm = &r.map_psi[(int)(ds & 1)];
-                if (r.noise) psi3_fv_tma_block<1, true, true, true, false>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
-                else psi3_fv_tma_block<1, false, true, false, false>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                if (r.mu_in) {  // mu of psi^n from this step's mu tasks
+                    if (r.noise)
+                        psi3_fv_tma_block<1, true, true, true, false, true>(pm, &r.map_u, spa, P.status, task.bx,
+                                                                            task.by, task.bz, tsmem, &r.map_mu);
+                    else
+                        psi3_fv_tma_block<1, false, true, false, false, true>(pm, &r.map_u, spa, P.status, task.bx,
+                                                                              task.by, task.bz, tsmem, &r.map_mu);
+                } else if (r.noise) {
+                    psi3_fv_tma_block<1, true, true, true, false>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                } else {
+                    psi3_fv_tma_block<1, false, true, false, false>(pm, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
+                }
             } else {
                 psi3_fv_tma_block<2, false, true, false, false>(&r.map_psis, &r.map_u, spa, P.status, task.bx, task.by, task.bz, tsmem);
             }
@@ -159,14 +170,19 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
 
 }  // namespace
 
-size_t persist_smem_bytes() { return sizeof(float) * ((size_t)FV_SMEM_FLOATS + (size_t)FV_NOISE_FLOATS); }
+size_t persist_smem_bytes()
+{
+    const size_t f = FV_SMEM_FLOATS > FV_MU_SMEM_FLOATS ? FV_SMEM_FLOATS : FV_MU_SMEM_FLOATS;
+    return sizeof(float) * (f + (size_t)FV_NOISE_FLOATS);
+}
 
 // Tiles of one replica's phases in the persistent task list.
 void persist_tiles(const Geom &g, int zc, int coupling, int heun, int counts[PH_COUNT])
 {
     const int cx = (g.nx + 31) / 32;
     counts[PH_MU] = (coupling & FLB_COUPLE_FORCE)
-                        ? ((g.nx + 2 + 31) / 32) * ((g.ny + 2 + PM_BY - 1) / PM_BY) * ((g.nz + 2 + MU_ZC - 1) / MU_ZC)
+                        ? ((g.nx + 2 * MU3_HALO + 31) / 32) * ((g.ny + 2 * MU3_HALO + PM_BY - 1) / PM_BY) *
+                              ((g.nz + 2 * MU3_HALO + MU_ZC - 1) / MU_ZC)
                         : 0;
     counts[PH_LB] = counts[PH_VEL] = packed_blocks(g, PL_SITES);
     counts[PH_S1] = cx * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + zc - 1) / zc);
@@ -193,9 +209,9 @@ void persist_tasks(std::vector<PTask> &v, int rep, int ph, const Geom &g, int zc
     }
     int ny, nz, nxb = (g.nx + 31) / 32;
     if (ph == PH_MU) {
-        nxb = (g.nx + 2 + 31) / 32;
-        ny = (g.ny + 2 + PM_BY - 1) / PM_BY;
-        nz = (g.nz + 2 + MU_ZC - 1) / MU_ZC;
+        nxb = (g.nx + 2 * MU3_HALO + 31) / 32;
+        ny = (g.ny + 2 * MU3_HALO + PM_BY - 1) / PM_BY;
+        nz = (g.nz + 2 * MU3_HALO + MU_ZC - 1) / MU_ZC;
     } else {
         ny = (g.ny + PS_TY - 1) / PS_TY;
         nz = (g.nz + zc - 1) / zc;

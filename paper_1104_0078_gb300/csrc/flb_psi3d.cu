@@ -270,8 +270,9 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
                                                             blockIdx.z, tsmem, &mu_map);
 }
 
-// batched: block b of the launch works on L.psi[b]
-template <int STAGE, bool NOISE>
+// batched: block b of the launch works on L.psi[b]; MU_IN: stage 1 reads mu of
+// psi^n from the replica's mu field (every replica's step formed it)
+template <int STAGE, bool NOISE, bool MU_IN = false>
 __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLists L)
 {
     extern __shared__ __align__(1024) float tsmem[];
@@ -282,35 +283,39 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
     if (threadIdx.x == 0) psi_batch_args(r, ds, STAGE, sa);
     __syncthreads();
     const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[(int)(ds & 1)] : &r.map_psis;
-    psi3_fv_tma_block<STAGE, NOISE, false, true, false>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem);
+    psi3_fv_tma_block<STAGE, NOISE, false, true, false, MU_IN>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem,
+                                                              &r.map_mu);
 }
 
 __global__ void advance_kernel(long long *dstep) { *dstep += 1; }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st);
 
-cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, cudaStream_t st)
+cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, cudaStream_t st)
 {
-    const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS;
+    const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS, smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS;
+    const size_t nb = sizeof(float) * FV_NOISE_FLOATS;
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
         kernel<<<L.npsi, PS_NT, bytes, st>>>(L);
         return cudaGetLastError();
     };
-    cudaError_t e = noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + sizeof(float) * FV_NOISE_FLOATS)
-                          : go(psi3_fv_tma_batch_kernel<1, false>, sm);
+    cudaError_t e = mu_in ? (noise ? go(psi3_fv_tma_batch_kernel<1, true, true>, smm + nb)
+                                   : go(psi3_fv_tma_batch_kernel<1, false, true>, smm))
+                          : (noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + nb)
+                                   : go(psi3_fv_tma_batch_kernel<1, false>, sm));
     if (e != cudaSuccess || !heun) return e;
     return go(psi3_fv_tma_batch_kernel<2, false>, sm);
 }
 
 cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
-                              bool noise, cudaStream_t st)
+                              bool noise, bool mu_in, cudaStream_t st)
 {
     if (!scheme_fv) return cudaErrorNotSupported;
     cudaError_t e = launch_lb3_batch(L, storage, ghost, force, st);
     if (e != cudaSuccess) return e;
-    e = launch_batch_psi(L, heun, noise, st);
+    e = launch_batch_psi(L, heun, noise, mu_in, st);
     if (e != cudaSuccess) return e;
     advance_kernel<<<1, 1, 0, st>>>(const_cast<long long *>(L.dstep));
     return cudaGetLastError();
