@@ -271,7 +271,10 @@ def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
     """Throughput of the other forms of the path, each on its own handle after 3
     warm-up steps, inputs larger than L2 at the default n = 512: the FD psi
     scheme, the FP16 storage variant, the RK4 integrator, the stress-form force
-    and the D3Q15 lattice (FD) on the n^3 quench, and the D2Q9 path on an
+    and the D3Q15 lattice (FD) on the n^3 quench; the quench with S(q) and the
+    dynamic S(q, tau) (8 lags) sampled every 10 steps; the per-site general
+    path of the paper's stencil studies: FD with the PK Laplacian, the naive
+    contrast scheme with the CD Laplacian, FV on D3Q15; and the D2Q9 path on an
     (8n)^2 quench (same free energy, FD as in the 2D workload).  MLUPS and the
     fraction of the HBM roofline on the algorithmic bytes of that form."""
     import torch
@@ -283,12 +286,16 @@ def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
         (f"rk4_{n}", dict(cube, psi_scheme=F.FLB_FV, integrator=F.FLB_RK4), 160),
         (f"stress_force_{n}", dict(cube, psi_scheme=F.FLB_FV, force_grad=F.FLB_FORCE_STRESS), 160),
         (f"d3q15_fd_{n}", dict(cube, q=15, psi_scheme=F.FLB_FD), 128),
+        (f"sq_dynamic_{n}", dict(cube, psi_scheme=F.FLB_FV, sq_kmax=8, sq_lags=8), 160, (10, 1 | 4)),
+        (f"pk_laplacian_fd_{n}", dict(cube, psi_scheme=F.FLB_FD, laplacian=F.FLB_LAP_PK), 160),
+        (f"naive_cd_{n}", dict(cube, psi_scheme=F.FLB_NAIVE, laplacian=F.FLB_LAP_CD), 160),
+        (f"d3q15_fv_{n}", dict(cube, q=15, psi_scheme=F.FLB_FV), 128),
         (f"d2q9_{8 * n}", dict(dim=2, q=9, nx=8 * n, ny=8 * n, nz=1, psi_scheme=F.FLB_FD), 80),
     ]
     if only:
         forms = [f for f in forms if f[0].rsplit("_", 1)[0] in only]
     out = {}
-    for key, kw, alg in forms:
+    for key, kw, alg, *sampling in forms:
         kw = {"integrator": F.FLB_HEUN, **kw}
         p = F.flb_params_default(tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
                                  seed=d["seed"], **kw)
@@ -297,6 +304,8 @@ def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
         s.set_fields(psi=I.uniform_field(N, -0.01, 0.01, 11))
         if p.dim == 3 and autotune:
             s.autotune()
+        if sampling:
+            s.set_sampling(*sampling[0])
         s.step(3)
         s.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
