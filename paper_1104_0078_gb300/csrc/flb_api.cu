@@ -137,11 +137,10 @@ bool valid(const flb_params &p)
 }
 
 // 3D combinations outside the tiled kernels (another Laplacian, the naive
-// scheme, FV on D3Q15) run the one-thread-per-site kernels of the 2D path.
+// scheme) run the one-thread-per-site kernels of the 2D path.
 bool general_path(const flb_params &p)
 {
-    return p.dim == 3 && (p.laplacian != FLB_LAP_SO || p.psi_scheme == FLB_NAIVE ||
-                          (p.q == 15 && p.psi_scheme == FLB_FV));
+    return p.dim == 3 && (p.laplacian != FLB_LAP_SO || p.psi_scheme == FLB_NAIVE);
 }
 
 // Class weights of the App. A Laplacians (faces, edges, corners; 2D axes and
@@ -504,16 +503,16 @@ int launch_psi_stages(flb_handle *h, Rep &r)
         const float *in[4] = {psi_n, r.psis, psi_np1, r.psis};
         float *out[4] = {r.psis, psi_np1, r.psis, psi_np1};
         for (int s = 0; s < 4; ++s)
-            FLB_TRY(launch_psi3(r.g, p.psi_scheme, s == 0 ? 1 : 2, s == 0 && noisy, in[s], r.u, out[s], r.E,
+            FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, s == 0 ? 1 : 2, s == 0 && noisy, in[s], r.u, out[s], r.E,
                                 (float)p.A, (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, 0, key, r.step,
                                 r.zc, s + 1, psi_n, r.Dn, s == 0 ? mu_n : nullptr, h->status, st));
         return FLB_OK;
     }
-    FLB_TRY(launch_psi3(r.g, p.psi_scheme, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
+    FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
                         (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, r.zc, 0,
                         nullptr, nullptr, mu_n, h->status, st));
     if (heun)
-        FLB_TRY(launch_psi3(r.g, p.psi_scheme, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
+        FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
                             (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, r.zc, 0, nullptr, nullptr,
                             nullptr, h->status, st));
     return FLB_OK;

@@ -523,10 +523,10 @@ cudaError_t launch_vel15(const LBArgs &a, int storage, cudaStream_t s);  // D3Q1
 cudaError_t launch_mu3_batch(const BatchLists &L, cudaStream_t st);
 cudaError_t launch_vel3_batch(const BatchLists &L, int storage, bool force, cudaStream_t st);
 cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
-// one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu); mu_in: the mu
-// of the stage input on the interior and 2 ghost layers, or null (FV stage 1 then
-// forms it)
-cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
+// one fused Runge-Kutta stage of psi on a 3D box (flb_psi3d.cu); q: the lattice
+// of the FV operators (19 or 15); mu_in: the mu of the stage input on the
+// interior and 2 ghost layers, or null (stage 1 then forms it)
+cudaError_t launch_psi3(const Geom &g, int scheme, int q, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
                         const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
                         const float *mu_in, int *status, cudaStream_t st);

@@ -258,16 +258,17 @@ struct TmaArgs {
     int *status;
 };
 
-// MU_IN: stage 1 reads mu of its input from mu_map instead of forming it
-template <int STAGE, bool NOISE, bool RK, bool MU_IN>
+// MU_IN: stage 1 reads mu of its input from mu_map instead of forming it; Q15:
+// the FV operators of D3Q15
+template <int STAGE, bool NOISE, bool RK, bool MU_IN, bool Q15 = false>
 __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
                                                             const __grid_constant__ CUtensorMap u_map,
                                                             const __grid_constant__ CUtensorMap mu_map,
                                                             const TmaArgs ta)
 {
     extern __shared__ __align__(1024) float tsmem[];
-    psi3_fv_tma_block<STAGE, NOISE, false, false, RK, MU_IN>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x, blockIdx.y,
-                                                            blockIdx.z, tsmem, &mu_map);
+    psi3_fv_tma_block<STAGE, NOISE, false, false, RK, MU_IN, Q15>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x,
+                                                                 blockIdx.y, blockIdx.z, tsmem, &mu_map);
 }
 
 // batched: block b of the launch works on L.psi[b]; MU_IN: stage 1 reads mu of
@@ -357,7 +358,7 @@ cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, const float *mu_in, int *status,
+static cudaError_t launch_fv_tma(const Psi3Args &a, int q, int stage, bool noise, const float *mu_in, int *status,
                                  cudaStream_t st)
 {
     const Geom &g = a.g;
@@ -392,6 +393,13 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, const
     };
     const size_t smn = sm + sizeof(float) * FV_NOISE_FLOATS;
     const size_t smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS, smmn = smm + sizeof(float) * FV_NOISE_FLOATS;
+    if (q == 15) {  // D3Q15: the RK4 branches stay runtime tests
+        if (stage == 2) return go(psi3_fv_tma_kernel<2, false, true, false, true>, sm);
+        if (mu) return noise ? go(psi3_fv_tma_kernel<1, true, true, true, true>, smmn)
+                             : go(psi3_fv_tma_kernel<1, false, true, true, true>, smm);
+        return noise ? go(psi3_fv_tma_kernel<1, true, true, false, true>, smn)
+                     : go(psi3_fv_tma_kernel<1, false, true, false, true>, sm);
+    }
     if (stage == 2) return a.rk4 ? go(psi3_fv_tma_kernel<2, false, true, false>, sm)
                                  : go(psi3_fv_tma_kernel<2, false, false, false>, sm);
     if (mu) {
@@ -405,7 +413,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int stage, bool noise, const
     return noise ? go(psi3_fv_tma_kernel<1, true, false, false>, smn) : go(psi3_fv_tma_kernel<1, false, false, false>, sm);
 }
 
-cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const float *psi, const float *u,
+cudaError_t launch_psi3(const Geom &g, int scheme, int q, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
                         const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
                         const float *mu_in, int *status, cudaStream_t st)
@@ -432,7 +440,7 @@ cudaError_t launch_psi3(const Geom &g, int scheme, int stage, bool noise, const 
     a.step = step;
     const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + zc - 1) / zc);
     const size_t smem = sizeof(float) * (4 * H3N + 3 * H2N);
-    if (scheme == FLB_FV) return launch_fv_tma(a, stage, noise, mu_in, status, st);
+    if (scheme == FLB_FV) return launch_fv_tma(a, q, stage, noise, mu_in, status, st);
     const size_t smn = smem + sizeof(float) * 13 * H1N;
     if (stage == 1 && mu_in) {
         if (noise) return launch_dyn(psi3_fd_kernel<1, true, true>, grid, smn, st, a, mu_in);

@@ -122,11 +122,18 @@ constexpr int FV_NOISE_FLOATS = 6 * H1N;
 // each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
 // formed, the flux of plane p-2, and the output of plane p-3 completes.
 //
+// Q15: the FV operators of D3Q15 (faces w = 1/9, corners 1/72), in units of 1/24:
+//   24 grad mu (q): x: 8 ex(q) + Dx(q-1) + Dx(q+1),  y: likewise,
+//     z: Zq(q+1) - Zq(q-1) with Zq = 8 mu + the 4 in-plane corners;
+//   24 div J (z) = 8 Hxy(z) + 8 (Zc(z+1) - Zc(z-1)) + Dg(z+1) + Dg(z-1) + C4(z+1) - C4(z-1)
+//     with Dg the corners' c_x Jx + c_y Jy and C4 the corners' Jz of a plane.
+//
 // MU_IN (stage 1 only): mu of the stage input psi^n already sits in the mu field
 // (mu_map, valid to 2 ghost layers), written for the force of the same step.  Its
 // planes then come by TMA, like psi and u, into a third ring ([TY+4][TX+8], column
 // c <-> x = x0 - 4 + c, row r <-> y = y0 - 2 + r), and the block skips forming mu.
-template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false, bool RK = true, bool MU_IN = false>
+template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false, bool RK = true, bool MU_IN = false,
+          bool Q15 = false>
 __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
                                                   const Psi3Args &a, int *status, int bx, int by, int bz,
                                                   float *tsmem, const CUtensorMap *mu_map = nullptr)
@@ -150,7 +157,8 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const bool active = x < g.nx && y < g.ny;
     const float k22 = a.K * (1.0f / 22.0f);
     const float sdx = sqrtf(2.0f * a.kT * a.M);
-    const float m12 = a.M * (1.0f / 12.0f);
+    const float mg = a.M * (Q15 ? 1.0f / 24.0f : 1.0f / 12.0f);  // M over the gradient's unit
+    constexpr float DIV = Q15 ? 1.0f / 24.0f : 1.0f / 12.0f;      // the divergence's unit
     const int pbase = z0 - 3, ubase = z0 - 1, mbase = z0 - 2;  // first psi / u / mu plane of the chunk
     // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
     // psi-slot centre (-1 off the region; the u slot holds the same point 2 rows
@@ -186,7 +194,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     for (int j = 0; j < S1; ++j)
 #pragma unroll
         for (int k = 0; k < 3; ++k) G0[j][k] = G1[j][k] = 0.f;
-    float D0 = 0.f, D1 = 0.f, N0 = 0.f, N1 = 0.f;  // 12 div of the flux / noise of planes q-1 and q
+    float D0 = 0.f, D1 = 0.f, N0 = 0.f, N1 = 0.f;  // 12 (24) div of the flux / noise of planes q-1 and q
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
@@ -312,17 +320,33 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                             mmm = Mu[c - 1 - MP];
                 const float ex = mxp - mxm, ey = myp - mym;
                 const float Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
-                const float Zp = 2.f * Mu[c] + ((mxp + mxm) + (myp + mym));
-                const float gx = G0[j][0] + ex, gy = G0[j][1] + ey, gz = G0[j][2] + Zp;  // plane m-1, complete
-                G0[j][0] = G1[j][0] + (2.f * ex + Dx);
-                G0[j][1] = G1[j][1] + (2.f * ey + Dy);
-                G0[j][2] = G1[j][2];
-                G1[j][0] = ex;
-                G1[j][1] = ey;
-                G1[j][2] = -Zp;
+                float gx, gy, gz;  // plane m-1, complete
+                if (Q15) {
+                    const float Zq = 8.f * Mu[c] + ((mpp + mpm) + (mmp + mmm));
+                    gx = G0[j][0] + Dx;
+                    gy = G0[j][1] + Dy;
+                    gz = G0[j][2] + Zq;
+                    G0[j][0] = G1[j][0] + 8.f * ex;
+                    G0[j][1] = G1[j][1] + 8.f * ey;
+                    G0[j][2] = G1[j][2];
+                    G1[j][0] = Dx;
+                    G1[j][1] = Dy;
+                    G1[j][2] = -Zq;
+                } else {
+                    const float Zp = 2.f * Mu[c] + ((mxp + mxm) + (myp + mym));
+                    gx = G0[j][0] + ex;
+                    gy = G0[j][1] + ey;
+                    gz = G0[j][2] + Zp;
+                    G0[j][0] = G1[j][0] + (2.f * ex + Dx);
+                    G0[j][1] = G1[j][1] + (2.f * ey + Dy);
+                    G0[j][2] = G1[j][2];
+                    G1[j][0] = ex;
+                    G1[j][1] = ey;
+                    G1[j][2] = -Zp;
+                }
                 if (emit) {
                     const int k = d1[j];
-                    float jx = m12 * gx, jy = m12 * gy, jz = m12 * gz;
+                    float jx = mg * gx, jy = mg * gy, jz = mg * gz;
                     if (a.advect) {
                         const float pv = ps[p1[j]];
                         const int uo = p1[j] - 2 * TB_X;
@@ -354,10 +378,18 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             const float dg = ((Jx[c + 1 + H1X] + Jy[c + 1 + H1X]) - (Jx[c - 1 - H1X] + Jy[c - 1 - H1X])) +
                              ((Jx[c + 1 - H1X] - Jy[c + 1 - H1X]) - (Jx[c - 1 + H1X] - Jy[c - 1 + H1X]));
             const float zc = Jz[c];
-            const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + H1X] + Jz[c - H1X]);
-            const float dd = D0 + (2.f * zc + hxy + z4);  // plane q-1, complete
-            D0 = D1 + (2.f * hxy + dg);
-            D1 = hxy - z4 - 2.f * zc;
+            float dd;  // plane q-1, complete
+            if (Q15) {
+                const float c4 = (Jz[c + 1 + H1X] + Jz[c + 1 - H1X]) + (Jz[c - 1 + H1X] + Jz[c - 1 - H1X]);
+                dd = D0 + (8.f * zc + dg + c4);
+                D0 = D1 + 8.f * hxy;
+                D1 = (dg - c4) - 8.f * zc;
+            } else {
+                const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + H1X] + Jz[c - H1X]);
+                dd = D0 + (2.f * zc + hxy + z4);
+                D0 = D1 + (2.f * hxy + dg);
+                D1 = hxy - z4 - 2.f * zc;
+            }
             float dn = 0.f;
             if (NOISE) {
                 const float *Xx = sX + (q & 1) * 3 * H1N, *Xy = Xx + H1N, *Xz = Xy + H1N;
@@ -365,16 +397,23 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 const float ng = ((Xx[c + 1 + H1X] + Xy[c + 1 + H1X]) - (Xx[c - 1 - H1X] + Xy[c - 1 - H1X])) +
                                  ((Xx[c + 1 - H1X] - Xy[c + 1 - H1X]) - (Xx[c - 1 + H1X] - Xy[c - 1 + H1X]));
                 const float nzc = Xz[c];
-                const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + H1X] + Xz[c - H1X]);
-                dn = N0 + (2.f * nzc + nxy + nz4);
-                N0 = N1 + (2.f * nxy + ng);
-                N1 = nxy - nz4 - 2.f * nzc;
+                if (Q15) {
+                    const float n4 = (Xz[c + 1 + H1X] + Xz[c + 1 - H1X]) + (Xz[c - 1 + H1X] + Xz[c - 1 - H1X]);
+                    dn = N0 + (8.f * nzc + ng + n4);
+                    N0 = N1 + 8.f * nxy;
+                    N1 = (ng - n4) - 8.f * nzc;
+                } else {
+                    const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + H1X] + Xz[c - H1X]);
+                    dn = N0 + (2.f * nzc + nxy + nz4);
+                    N0 = N1 + (2.f * nxy + ng);
+                    N1 = nxy - nz4 - 2.f * nzc;
+                }
             }
             const int z = q - 1;
             if (z >= z0 && active) {
-                const float Dd = dd * (1.f / 12.f);
+                const float Dd = dd * DIV;
                 const int si = x + g.nx * (y + g.ny * z);
-                const float Dn = (STAGE == 1 && NOISE) ? dn * (1.f / 12.f) : 0.f;
+                const float Dn = (STAGE == 1 && NOISE) ? dn * DIV : 0.f;
                 const float pv = STAGE == 1 ? tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)] : 0.f;
                 float out;
                 if (STAGE == 2 && !rk4) {

@@ -27,9 +27,9 @@ def _fields(s, rep=0):
     return s.get_populations(rep), psi, u
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
-def test_zchunk_changes_no_bit(scheme):
-    d = dict(RAGGED, scheme=scheme)
+@pytest.mark.parametrize("q,scheme", [(19, 0), (19, 1), (15, 1)])
+def test_zchunk_changes_no_bit(q, scheme):
+    d = dict(RAGGED, q=q, scheme=scheme)
     ref = None
     for zc in (64, 1, 3, 8, 19):
         s = F.Solver(flb_params(d))
