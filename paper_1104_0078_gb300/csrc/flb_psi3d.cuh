@@ -93,13 +93,14 @@ constexpr int TP_N = TB_X * H3Y;                           // psi slot floats
 constexpr int TP_SLOT = ((TP_N * 4 + 127) / 128) * 32;     // floats, 128-byte multiple
 constexpr int TU_N = 3 * TB_X * H1Y;                       // u slot floats
 constexpr int TU_SLOT = ((TU_N * 4 + 127) / 128) * 32;
-constexpr int TM_N = TB_X * H2Y;                           // mu slot floats (MU_IN)
+constexpr int TM_N = TB_X * H2Y;                           // mu plane / slot floats
 constexpr int TM_SLOT = ((TM_N * 4 + 127) / 128) * 32;
+constexpr int TJ_N = TB_X * H1Y;                           // flux / noise plane floats (one component)
 constexpr int T_PSI_DEPTH = 6, T_U_DEPTH = 3, T_MU_DEPTH = 3;
 
-constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * H2N + 6 * H1N;
-constexpr int FV_MU_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + T_MU_DEPTH * TM_SLOT + 6 * H1N;
-constexpr int FV_NOISE_FLOATS = 6 * H1N;
+constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * TM_N + 6 * TJ_N;
+constexpr int FV_MU_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + T_MU_DEPTH * TM_SLOT + 6 * TJ_N;
+constexpr int FV_NOISE_FLOATS = 6 * TJ_N;
 
 // One block (tile bx, by; z chunk bz).  psi_map / u_map: tensor maps of the stage
 // input psi and of the velocity (kernel parameters or global memory); tsmem: the
@@ -120,7 +121,10 @@ constexpr int FV_NOISE_FLOATS = 6 * H1N;
 //     2 Hxy(z) + Dg(z) + 2 (Zc(z+1) - Zc(z-1)) + Hxy(z+1) + Hxy(z-1) + Z4(z+1) - Z4(z-1).
 // Shared memory then holds only the current mu, flux and noise planes (two of
 // each, by parity) besides the TMA rings: psi plane p arrives, mu of plane p-1 is
-// formed, the flux of plane p-2, and the output of plane p-3 completes.
+// formed, the flux of plane p-2, and the output of plane p-3 completes.  Every
+// plane keeps the psi slot's row pitch TB_X and columns (x = x0 - 4 + c); the mu
+// plane starts at y = y0 - 2 and the flux, noise and u planes at y = y0 - 1, so a
+// point's index in each is its psi-slot index less TB_X or 2 TB_X.
 //
 // Q15: the FV operators of D3Q15 (faces w = 1/9, corners 1/72), in units of 1/24:
 //   24 grad mu (q): x: 8 ex(q) + Dx(q-1) + Dx(q+1),  y: likewise,
@@ -143,10 +147,10 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const int rk4 = RK ? a.rk4 : 0;                       // RK false: a launch without RK4
     float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
     float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
-    float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][H2N]     mu plane, by parity
+    float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][TM_N]    mu plane, by parity
     float *tms = smu;                                    // MU_IN: [T_MU_DEPTH][TM_SLOT] instead
-    float *sJ = smu + (MU_IN ? T_MU_DEPTH * TM_SLOT : 2 * H2N);  // [2][3][H1N]  flux plane, by parity
-    float *sX = sJ + 6 * H1N;                            // [2][3][H1N]  noise plane, by parity (NOISE)
+    float *sJ = smu + (MU_IN ? T_MU_DEPTH * TM_SLOT : 2 * TM_N);  // [2][3][TJ_N] flux plane, by parity
+    float *sX = sJ + 6 * TJ_N;                           // [2][3][TJ_N] noise plane, by parity (NOISE)
     __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH], bar_m[T_MU_DEPTH];
     __shared__ int s_bad;
     const Geom &g = a.g;
@@ -160,28 +164,24 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const float mg = a.M * (Q15 ? 1.0f / 24.0f : 1.0f / 12.0f);  // M over the gradient's unit
     constexpr float DIV = Q15 ? 1.0f / 24.0f : 1.0f / 12.0f;      // the divergence's unit
     const int pbase = z0 - 3, ubase = z0 - 1, mbase = z0 - 2;  // first psi / u / mu plane of the chunk
-    // mu region: psi-slot offset of every slot point; flux region: mu-frame centre,
-    // psi-slot centre (-1 off the region; the u slot holds the same point 2 rows
-    // up, the MU_IN mu slot 1 row up), noise counter id
+    // psi-slot index of every mu-region point (c2) and flux-region point (p1), -1
+    // off the region; noise counter id of every flux-region point.
     // Region points are dealt to threads row segment by row segment: the first
     // 32 columns of every row (a full warp reads 32 consecutive words, free of
     // bank conflicts), then the few remaining columns of all rows.
-    int c2[S2], d2[S2], c1[S1], d1[S1], p1[S1], n1[S1];
+    int c2[S2], p1[S1], n1[S1];
 #pragma unroll
     for (int j = 0; j < S2; ++j) {
         int lx, ly;
         region_point(threadIdx.x + j * PS_NT, H2X, H2Y, lx, ly);
         const bool ok = threadIdx.x + j * PS_NT < H2N;
         c2[j] = ok ? (lx + 2) + TB_X * (ly + 1) : -1;
-        d2[j] = lx + H2X * ly;
     }
 #pragma unroll
     for (int j = 0; j < S1; ++j) {
         int lx, ly;
         region_point(threadIdx.x + j * PS_NT, H1X, H1Y, lx, ly);
         const bool ok = threadIdx.x + j * PS_NT < H1N;
-        c1[j] = ok ? (lx + 1) + H2X * (ly + 1) : -1;
-        d1[j] = lx + H1X * ly;
         p1[j] = ok ? (lx + 3) + TB_X * (ly + 2) : -1;
         n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
     }
@@ -254,7 +254,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         waited_p = p;
         if (!MU_IN) {
             const float *P = tps + r6 * TP_SLOT;
-            float *dst = smu + ((p - 1) & 1) * H2N;
+            float *dst = smu + ((p - 1) & 1) * TM_N;
             const bool emit = p - 1 >= z0 - 2;
 #pragma unroll
             for (int j = 0; j < S2; ++j) {
@@ -268,7 +268,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     const float nn1 = pb[j][1] + (pa[j][0] + ac);
                     const float nn2 = pd[j][1] + (pb[j][0] + bc);
                     const float nn3 = pd[j][0] + dc;
-                    dst[d2[j]] = mu_so(a.A, a.B, k22, ps, nn1, nn2, nn3);
+                    dst[c - TB_X] = mu_so(a.A, a.B, k22, ps, nn1, nn2, nn3);  // mu plane row 0 <-> psi-slot row 1
                 }
                 pa[j][0] = pa[j][1];
                 pb[j][0] = pb[j][1];
@@ -298,7 +298,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 ru = ru == T_U_DEPTH - 1 ? 0 : ru + 1;
                 uph ^= ru == 0;
             }
-            const float *Mu = smu + (m & 1) * H2N;
+            const float *Mu = smu + (m & 1) * TM_N;
             if (MU_IN) {  // mu plane m has landed in its ring slot
                 if (!mbar_wait(&bar_m[rm], mph, status)) s_bad = 1;
                 waited_m = m;
@@ -306,18 +306,17 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 rm = rm == T_MU_DEPTH - 1 ? 0 : rm + 1;
                 mph ^= rm == 0;
             }
-            constexpr int MP = MU_IN ? TB_X : H2X;  // row pitch of the mu plane
             const float *ps = tps + s2 * TP_SLOT;  // psi plane m-1
-            float *J = sJ + ((m - 1) & 1) * 3 * H1N;
-            float *X = sX + ((m - 1) & 1) * 3 * H1N;
+            float *J = sJ + ((m - 1) & 1) * 3 * TJ_N;
+            float *X = sX + ((m - 1) & 1) * 3 * TJ_N;
             const int zid = g.nx * g.ny * wrapi(m - 1, g.nz);
 #pragma unroll
             for (int j = 0; j < S1; ++j) {
-                if ((MU_IN ? p1[j] : c1[j]) < 0) continue;
-                const int c = MU_IN ? p1[j] - TB_X : c1[j];
-                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + MP], mym = Mu[c - MP];
-                const float mpp = Mu[c + 1 + MP], mpm = Mu[c + 1 - MP], mmp = Mu[c - 1 + MP],
-                            mmm = Mu[c - 1 - MP];
+                if (p1[j] < 0) continue;
+                const int c = p1[j] - TB_X;  // in the mu plane
+                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + TB_X], mym = Mu[c - TB_X];
+                const float mpp = Mu[c + 1 + TB_X], mpm = Mu[c + 1 - TB_X], mmp = Mu[c - 1 + TB_X],
+                            mmm = Mu[c - 1 - TB_X];
                 const float ex = mxp - mxm, ey = myp - mym;
                 const float Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
                 float gx, gy, gz;  // plane m-1, complete
@@ -345,24 +344,23 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     G1[j][2] = -Zp;
                 }
                 if (emit) {
-                    const int k = d1[j];
+                    const int k = p1[j] - 2 * TB_X;  // in the flux, noise and u planes
                     float jx = mg * gx, jy = mg * gy, jz = mg * gz;
                     if (a.advect) {
                         const float pv = ps[p1[j]];
-                        const int uo = p1[j] - 2 * TB_X;
-                        jx -= uq[uo] * pv;
-                        jy -= uq[TB_X * H1Y + uo] * pv;
-                        jz -= uq[2 * TB_X * H1Y + uo] * pv;
+                        jx -= uq[k] * pv;
+                        jy -= uq[TB_X * H1Y + k] * pv;
+                        jz -= uq[2 * TB_X * H1Y + k] * pv;
                     }
                     J[k] = jx;
-                    J[H1N + k] = jy;
-                    J[2 * H1N + k] = jz;
+                    J[TJ_N + k] = jy;
+                    J[2 * TJ_N + k] = jz;
                     if (NOISE) {
                         float Gn[4];
                         normals4<KEY_R0>(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn);
                         X[k] = sdx * Gn[0];
-                        X[H1N + k] = sdx * Gn[1];
-                        X[2 * H1N + k] = sdx * Gn[2];
+                        X[TJ_N + k] = sdx * Gn[1];
+                        X[2 * TJ_N + k] = sdx * Gn[2];
                     }
                 }
             }
@@ -372,38 +370,38 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         // (C) flux partials of plane q = p-2 at the tile point; the output of plane q-1 completes
         const int q = p - 2;
         if (q >= z0 - 1) {
-            const int c = (tx + 1) + H1X * (ty + 1);
-            const float *Jx = sJ + (q & 1) * 3 * H1N, *Jy = Jx + H1N, *Jz = Jy + H1N;
-            const float hxy = (Jx[c + 1] - Jx[c - 1]) + (Jy[c + H1X] - Jy[c - H1X]);
-            const float dg = ((Jx[c + 1 + H1X] + Jy[c + 1 + H1X]) - (Jx[c - 1 - H1X] + Jy[c - 1 - H1X])) +
-                             ((Jx[c + 1 - H1X] - Jy[c + 1 - H1X]) - (Jx[c - 1 + H1X] - Jy[c - 1 + H1X]));
+            const int c = (tx + 4) + TB_X * (ty + 1);  // the tile point in the flux plane
+            const float *Jx = sJ + (q & 1) * 3 * TJ_N, *Jy = Jx + TJ_N, *Jz = Jy + TJ_N;
+            const float hxy = (Jx[c + 1] - Jx[c - 1]) + (Jy[c + TB_X] - Jy[c - TB_X]);
+            const float dg = ((Jx[c + 1 + TB_X] + Jy[c + 1 + TB_X]) - (Jx[c - 1 - TB_X] + Jy[c - 1 - TB_X])) +
+                             ((Jx[c + 1 - TB_X] - Jy[c + 1 - TB_X]) - (Jx[c - 1 + TB_X] - Jy[c - 1 + TB_X]));
             const float zc = Jz[c];
             float dd;  // plane q-1, complete
             if (Q15) {
-                const float c4 = (Jz[c + 1 + H1X] + Jz[c + 1 - H1X]) + (Jz[c - 1 + H1X] + Jz[c - 1 - H1X]);
+                const float c4 = (Jz[c + 1 + TB_X] + Jz[c + 1 - TB_X]) + (Jz[c - 1 + TB_X] + Jz[c - 1 - TB_X]);
                 dd = D0 + (8.f * zc + dg + c4);
                 D0 = D1 + 8.f * hxy;
                 D1 = (dg - c4) - 8.f * zc;
             } else {
-                const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + H1X] + Jz[c - H1X]);
+                const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + TB_X] + Jz[c - TB_X]);
                 dd = D0 + (2.f * zc + hxy + z4);
                 D0 = D1 + (2.f * hxy + dg);
                 D1 = hxy - z4 - 2.f * zc;
             }
             float dn = 0.f;
             if (NOISE) {
-                const float *Xx = sX + (q & 1) * 3 * H1N, *Xy = Xx + H1N, *Xz = Xy + H1N;
-                const float nxy = (Xx[c + 1] - Xx[c - 1]) + (Xy[c + H1X] - Xy[c - H1X]);
-                const float ng = ((Xx[c + 1 + H1X] + Xy[c + 1 + H1X]) - (Xx[c - 1 - H1X] + Xy[c - 1 - H1X])) +
-                                 ((Xx[c + 1 - H1X] - Xy[c + 1 - H1X]) - (Xx[c - 1 + H1X] - Xy[c - 1 + H1X]));
+                const float *Xx = sX + (q & 1) * 3 * TJ_N, *Xy = Xx + TJ_N, *Xz = Xy + TJ_N;
+                const float nxy = (Xx[c + 1] - Xx[c - 1]) + (Xy[c + TB_X] - Xy[c - TB_X]);
+                const float ng = ((Xx[c + 1 + TB_X] + Xy[c + 1 + TB_X]) - (Xx[c - 1 - TB_X] + Xy[c - 1 - TB_X])) +
+                                 ((Xx[c + 1 - TB_X] - Xy[c + 1 - TB_X]) - (Xx[c - 1 + TB_X] - Xy[c - 1 + TB_X]));
                 const float nzc = Xz[c];
                 if (Q15) {
-                    const float n4 = (Xz[c + 1 + H1X] + Xz[c + 1 - H1X]) + (Xz[c - 1 + H1X] + Xz[c - 1 - H1X]);
+                    const float n4 = (Xz[c + 1 + TB_X] + Xz[c + 1 - TB_X]) + (Xz[c - 1 + TB_X] + Xz[c - 1 - TB_X]);
                     dn = N0 + (8.f * nzc + ng + n4);
                     N0 = N1 + 8.f * nxy;
                     N1 = (ng - n4) - 8.f * nzc;
                 } else {
-                    const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + H1X] + Xz[c - H1X]);
+                    const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + TB_X] + Xz[c - TB_X]);
                     dn = N0 + (2.f * nzc + nxy + nz4);
                     N0 = N1 + (2.f * nxy + ng);
                     N1 = nxy - nz4 - 2.f * nzc;
