@@ -393,12 +393,19 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int q, int stage, bool noise
     };
     const size_t smn = sm + sizeof(float) * FV_NOISE_FLOATS;
     const size_t smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS, smmn = smm + sizeof(float) * FV_NOISE_FLOATS;
-    if (q == 15) {  // D3Q15: the RK4 branches stay runtime tests
-        if (stage == 2) return go(psi3_fv_tma_kernel<2, false, true, false, true>, sm);
-        if (mu) return noise ? go(psi3_fv_tma_kernel<1, true, true, true, true>, smmn)
-                             : go(psi3_fv_tma_kernel<1, false, true, true, true>, smm);
-        return noise ? go(psi3_fv_tma_kernel<1, true, true, false, true>, smn)
-                     : go(psi3_fv_tma_kernel<1, false, true, false, true>, sm);
+    if (q == 15) {  // D3Q15 (the RK4 branches compiled into RK4 launches only, as below)
+        if (stage == 2) return a.rk4 ? go(psi3_fv_tma_kernel<2, false, true, false, true>, sm)
+                                     : go(psi3_fv_tma_kernel<2, false, false, false, true>, sm);
+        if (a.rk4) {
+            if (mu) return noise ? go(psi3_fv_tma_kernel<1, true, true, true, true>, smmn)
+                                 : go(psi3_fv_tma_kernel<1, false, true, true, true>, smm);
+            return noise ? go(psi3_fv_tma_kernel<1, true, true, false, true>, smn)
+                         : go(psi3_fv_tma_kernel<1, false, true, false, true>, sm);
+        }
+        if (mu) return noise ? go(psi3_fv_tma_kernel<1, true, false, true, true>, smmn)
+                             : go(psi3_fv_tma_kernel<1, false, false, true, true>, smm);
+        return noise ? go(psi3_fv_tma_kernel<1, true, false, false, true>, smn)
+                     : go(psi3_fv_tma_kernel<1, false, false, false, true>, sm);
     }
     if (stage == 2) return a.rk4 ? go(psi3_fv_tma_kernel<2, false, true, false>, sm)
                                  : go(psi3_fv_tma_kernel<2, false, false, false>, sm);
