@@ -16,7 +16,9 @@ namespace flb {
 // Velocity of the streamed state after the step: u = (sum fbar c + F/2)/rho
 // with fbar the populations the next step pulls (the planes just written, a.fout)
 // and F this step's force density -- the velocity that advects psi (Gauss-Seidel
-// coupling of Sec. VI: the psi step follows the fluid step).
+// coupling of Sec. VI: the psi step follows the fluid step).  The planes'
+// addresses are formed from a.fout: with a table of them (as the collide-stream
+// takes) this memory-bound gather ran 5% slower at 256^3 (283 against 269 us).
 template <typename T, bool FORCE>
 __device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int bz)
 {

@@ -24,32 +24,31 @@ namespace flb {
 namespace {
 
 // fbar_i(r) = stored_i(r - c_i) for the 15 planes of site (x, y, z).
-template <typename T>
-__device__ __forceinline__ void pull15(const T *fi, const Geom &g, int x, int y, int z, float f[15])
+template <typename T, class PL>
+__device__ __forceinline__ void pull15(const PL &P, const Geom &g, int x, int y, int z, float f[15])
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int N = (int)g.n;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const int row = nx, pl = nx * ny;
     const int sY0 = row * y, sYm = row * ym, sYp = row * yp;
     const int sZ0 = pl * z, sZm = pl * zm, sZp = pl * zp;
-    f[0] = ld3<false>(fi, x + sY0 + sZ0);
-    f[1] = ld3<false>(fi + 1ll * N, xm + sY0 + sZ0);
-    f[2] = ld3<false>(fi + 2ll * N, xp + sY0 + sZ0);
-    f[3] = ld3<false>(fi + 3ll * N, x + sYm + sZ0);
-    f[4] = ld3<false>(fi + 4ll * N, x + sYp + sZ0);
-    f[5] = ld3<false>(fi + 5ll * N, x + sY0 + sZm);
-    f[6] = ld3<false>(fi + 6ll * N, x + sY0 + sZp);
-    f[7] = ld3<false>(fi + 7ll * N, xm + sYm + sZm);    // (1,1,1)
-    f[8] = ld3<false>(fi + 8ll * N, xp + sYp + sZp);
-    f[9] = ld3<false>(fi + 9ll * N, xm + sYm + sZp);    // (1,1,-1)
-    f[10] = ld3<false>(fi + 10ll * N, xp + sYp + sZm);
-    f[11] = ld3<false>(fi + 11ll * N, xm + sYp + sZm);  // (1,-1,1)
-    f[12] = ld3<false>(fi + 12ll * N, xp + sYm + sZp);
-    f[13] = ld3<false>(fi + 13ll * N, xm + sYp + sZp);  // (1,-1,-1)
-    f[14] = ld3<false>(fi + 14ll * N, xp + sYm + sZm);
+    f[0] = ld3<false>(P.in(0), x + sY0 + sZ0);
+    f[1] = ld3<false>(P.in(1), xm + sY0 + sZ0);
+    f[2] = ld3<false>(P.in(2), xp + sY0 + sZ0);
+    f[3] = ld3<false>(P.in(3), x + sYm + sZ0);
+    f[4] = ld3<false>(P.in(4), x + sYp + sZ0);
+    f[5] = ld3<false>(P.in(5), x + sY0 + sZm);
+    f[6] = ld3<false>(P.in(6), x + sY0 + sZp);
+    f[7] = ld3<false>(P.in(7), xm + sYm + sZm);    // (1,1,1)
+    f[8] = ld3<false>(P.in(8), xp + sYp + sZp);
+    f[9] = ld3<false>(P.in(9), xm + sYm + sZp);    // (1,1,-1)
+    f[10] = ld3<false>(P.in(10), xp + sYp + sZm);
+    f[11] = ld3<false>(P.in(11), xm + sYp + sZm);  // (1,-1,1)
+    f[12] = ld3<false>(P.in(12), xp + sYm + sZp);
+    f[13] = ld3<false>(P.in(13), xm + sYp + sZp);  // (1,-1,-1)
+    f[14] = ld3<false>(P.in(14), xp + sYm + sZm);
 }
 
 // Mass deviation and momentum of 15 populations; sp/dp the pair sums and differences.
@@ -67,15 +66,16 @@ __device__ __forceinline__ void moments15(const float f[15], float sp[8], float 
     jz = dp[3] + ((dp[4] - dp[5]) + (dp[6] - dp[7]));
 }
 
-template <typename T, bool GHOST_RELAX>
-__device__ __forceinline__ void lb15_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
+// P: the planes it pulls from (P.in) and stores to (P.out).
+template <typename T, bool GHOST_RELAX, class PL>
+__device__ __forceinline__ void lb15_site(const LBArgs &a, const PL &P, int x, int y, int z, float Fx, float Fy,
+                                          float Fz)
 {
     const Geom &g = a.g;
-    const int N = (int)g.n;
     const int s = x + g.nx * (y + g.ny * z);
 
     float f[15];
-    pull15<T>((const T *)a.fin, g, x, y, z, f);
+    pull15<T>(P, g, x, y, z, f);
     float sp[8], dp[8], drho, jx, jy, jz;
     moments15(f, sp, dp, drho, jx, jy, jz);
     const float C = (sp[4] + sp[5]) + (sp[6] + sp[7]);
@@ -147,45 +147,45 @@ __device__ __forceinline__ void lb15_site(const LBArgs &a, int x, int y, int z, 
 
     const float trB = Bxx + Byy + Bzz;
     const float e0 = 1.5f * trB;  // 9/2 trB/3
-    T *fo = (T *)a.fout;
     const float h2 = 2.f / 3.f, h4 = 4.f / 3.f;
-    st3(fo, s, (2.f / 9.f) * (drho - e0 + h4 * g4));
+    st3(P.out(0), s, (2.f / 9.f) * (drho - e0 + h4 * g4));
     const float w1 = 1.f / 9.f, w3 = 1.f / 72.f;
     float E, O;
     E = drho + 4.5f * Bxx - e0 - h2 * g4;
     O = 3.f * Ax - h2 * gx;
-    st3(fo + 1ll * N, s, w1 * (E + O));
-    st3(fo + 2ll * N, s, w1 * (E - O));
+    st3(P.out(1), s, w1 * (E + O));
+    st3(P.out(2), s, w1 * (E - O));
     E = drho + 4.5f * Byy - e0 - h2 * g4;
     O = 3.f * Ay - h2 * gy;
-    st3(fo + 3ll * N, s, w1 * (E + O));
-    st3(fo + 4ll * N, s, w1 * (E - O));
+    st3(P.out(3), s, w1 * (E + O));
+    st3(P.out(4), s, w1 * (E - O));
     E = drho + 4.5f * Bzz - e0 - h2 * g4;
     O = 3.f * Az - h2 * gz;
-    st3(fo + 5ll * N, s, w1 * (E + O));
-    st3(fo + 6ll * N, s, w1 * (E - O));
+    st3(P.out(5), s, w1 * (E + O));
+    st3(P.out(6), s, w1 * (E - O));
     // corners c = (1, a, b) and their opposites: B:cc = trB + 2(a Bxy + b Bxz + ab Byz)
     const float Ec = drho + 3.f * trB + h4 * g4;  // 9/2 trB - e0 = 3 trB
     E = Ec + 9.f * (Bxy + Bxz + Byz);
     O = 3.f * (Ax + Ay + Az) + h4 * (gx + gy + gz) + gq;
-    st3(fo + 7ll * N, s, w3 * (E + O));
-    st3(fo + 8ll * N, s, w3 * (E - O));
+    st3(P.out(7), s, w3 * (E + O));
+    st3(P.out(8), s, w3 * (E - O));
     E = Ec + 9.f * (Bxy - Bxz - Byz);
     O = 3.f * (Ax + Ay - Az) + h4 * (gx + gy - gz) - gq;
-    st3(fo + 9ll * N, s, w3 * (E + O));
-    st3(fo + 10ll * N, s, w3 * (E - O));
+    st3(P.out(9), s, w3 * (E + O));
+    st3(P.out(10), s, w3 * (E - O));
     E = Ec + 9.f * (-Bxy + Bxz - Byz);
     O = 3.f * (Ax - Ay + Az) + h4 * (gx - gy + gz) - gq;
-    st3(fo + 11ll * N, s, w3 * (E + O));
-    st3(fo + 12ll * N, s, w3 * (E - O));
+    st3(P.out(11), s, w3 * (E + O));
+    st3(P.out(12), s, w3 * (E - O));
     E = Ec + 9.f * (-Bxy - Bxz + Byz);
     O = 3.f * (Ax - Ay - Az) + h4 * (gx - gy - gz) + gq;
-    st3(fo + 13ll * N, s, w3 * (E + O));
-    st3(fo + 14ll * N, s, w3 * (E - O));
+    st3(P.out(13), s, w3 * (E + O));
+    st3(P.out(14), s, w3 * (E - O));
 }
 
+// P: the population planes (in: a.fin, out: a.fout), a table of addresses.
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb15_kernel(const LBArgs a)
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb15_kernel(const LBArgs a, const __grid_constant__ PlaneTable<T> P)
 {
     const Geom &g = a.g;
     const int x = blockIdx.x * LB_BX + threadIdx.x;
@@ -194,10 +194,11 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb15_kernel(const LBArgs 
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if (FORCE) force3<false>(a, x, y, z, Fx, Fy, Fz);
-    lb15_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
+    lb15_site<T, GHOST_RELAX>(a, P, x, y, z, Fx, Fy, Fz);
 }
 
-// u = (sum fbar c + F/2)/rho of the streamed state, F this step's force.
+// u = (sum fbar c + F/2)/rho of the streamed state, F this step's force (plane
+// addresses formed from a.fout, as in the D3Q19 velocity gather).
 template <typename T, bool FORCE>
 __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel15_kernel(const LBArgs a)
 {
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel15_kernel(const LBArgs
     const int z = blockIdx.z * LB_BZ + threadIdx.z;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float f[15];
-    pull15<T>((const T *)a.fout, g, x, y, z, f);
+    pull15<T>(PlanesFromBase<T>{(const T *)a.fout, nullptr, g.n}, g, x, y, z, f);
     float sp[8], dp[8], drho, jx, jy, jz;
     moments15(f, sp, dp, drho, jx, jy, jz);
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
@@ -226,7 +227,7 @@ cudaError_t launch_lb15(const LBArgs &a, int storage, cudaStream_t st)
     const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
     const bool gr = a.gamma_g != 0.0f;
     const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;
-#define FLB_LB15(T, G, F) lb15_kernel<T, G, F><<<grid, block, 0, st>>>(a)
+#define FLB_LB15(T, G, F) lb15_kernel<T, G, F><<<grid, block, 0, st>>>(a, plane_table<T>(a.fin, a.fout, a.g.n, 15))
     if (storage == FLB_F16_DEV) {
         if (gr) { if (force) FLB_LB15(__half, true, true); else FLB_LB15(__half, true, false); }
         else { if (force) FLB_LB15(__half, false, true); else FLB_LB15(__half, false, false); }

@@ -19,9 +19,10 @@ namespace flb {
 // One thread per site on a 3D grid of 32 x 4 x 2 blocks (a warp covers 32
 // consecutive x, so every population plane is read and written in full rows).
 
-// One block of the collide-stream (block coordinates bx, by, bz of the 32 x 4 x 2 grid).
+// One block of the collide-stream (block coordinates bx, by, bz of the 32 x 4 x 2
+// grid) on the population planes of the table P.
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int bz)
+__device__ __forceinline__ void lb3_block(const LBArgs &a, const PlaneTable<T> &P, int bx, int by, int bz)
 {
     const Geom &g = a.g;
     const int x = bx * LB_BX + threadIdx.x;
@@ -30,14 +31,16 @@ __device__ __forceinline__ void lb3_block(const LBArgs &a, int bx, int by, int b
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
     if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3<false>(a, x, y, z, Fx, Fy, Fz);
-    lb_site<T, GHOST_RELAX>(a, x, y, z, Fx, Fy, Fz);
+    lb_site_on<T, GHOST_RELAX, false, false>(a, P, x, y, z, Fx, Fy, Fz);
 }
 
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, GHOST_RELAX ? 5 : 6) lb3_kernel(const LBArgs a)
+__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, GHOST_RELAX ? 5 : 6)
+    lb3_kernel(const LBArgs a, const __grid_constant__ PlaneTable<T> P)
 {
-    lb3_block<T, GHOST_RELAX, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    lb3_block<T, GHOST_RELAX, FORCE>(a, P, blockIdx.x, blockIdx.y, blockIdx.z);
 }
+
 
 // ---- batched variant: block b of the launch works on the row-packed entry L.lb[b] ----
 template <typename T, bool GHOST_RELAX, bool FORCE>
@@ -81,7 +84,7 @@ cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t st)
     const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
     const bool gr = a.gamma_g != 0.0f;
     const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;
-#define FLB_LB3(T, G, F) lb3_kernel<T, G, F><<<grid, block, 0, st>>>(a)
+#define FLB_LB3(T, G, F) lb3_kernel<T, G, F><<<grid, block, 0, st>>>(a, plane_table<T>(a.fin, a.fout, a.g.n, 19))
     if (storage == FLB_F16_DEV) {
         if (gr) { if (force) FLB_LB3(__half, true, true); else FLB_LB3(__half, true, false); }
         else { if (force) FLB_LB3(__half, false, true); else FLB_LB3(__half, false, false); }

@@ -43,38 +43,71 @@ __device__ __forceinline__ void st3<float>(float *p, int i, float v) { p[i] = v;
 template <>
 __device__ __forceinline__ void st3<__half>(__half *p, int i, float v) { p[i] = __float2half_rn(v); }
 
+// Addresses of the 19 population planes (plane i of N sites).  PlanesFromBase
+// forms them from the buffers' bases, as the batched and persistent kernels must
+// (their buffers swap with the device step); PlaneTable holds them, as a kernel
+// parameter of the plain collide-stream, so a plane's address is one constant
+// load instead of 64-bit arithmetic in every warp.
+template <typename T>
+struct PlanesFromBase {
+    const T *fi;
+    T *fo;
+    long long N;
+    __device__ __forceinline__ const T *in(int i) const { return fi + i * N; }
+    __device__ __forceinline__ T *out(int i) const { return fo + i * N; }
+};
+template <typename T>
+struct PlaneTable {
+    const T *in_[19];
+    T *out_[19];
+    __device__ __forceinline__ const T *in(int i) const { return in_[i]; }
+    __device__ __forceinline__ T *out(int i) const { return out_[i]; }
+};
+
+// The table of q planes of n sites from the buffers in and out (either may be
+// null) (host).
+template <typename T>
+inline PlaneTable<T> plane_table(const void *in, void *out, long long n, int q)
+{
+    PlaneTable<T> P{};
+    for (int i = 0; i < q; ++i) {
+        P.in_[i] = in ? (const T *)in + i * n : nullptr;
+        P.out_[i] = out ? (T *)out + i * n : nullptr;
+    }
+    return P;
+}
+
 // Pull of the 19 populations of site (x, y, z) from stored post-collision
-// planes fi: fbar_i(r) = stored_i(r - c_i).
-template <typename T, bool COH = false>
-__device__ __forceinline__ void pull19(const T *fi, const Geom &g, int x, int y, int z, float f[19])
+// planes P.in(i): fbar_i(r) = stored_i(r - c_i).
+template <typename T, bool COH = false, class PL>
+__device__ __forceinline__ void pull19(const PL &P, const Geom &g, int x, int y, int z, float f[19])
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int N = (int)g.n;
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
     const int row = nx, pl = nx * ny;
     const int sY0 = row * y, sYm = row * ym, sYp = row * yp;
     const int sZ0 = pl * z, sZm = pl * zm, sZp = pl * zp;
-    f[0] = ld3<COH>(fi, x + sY0 + sZ0);
-    f[1] = ld3<COH>(fi + 1ll * N, xm + sY0 + sZ0);
-    f[2] = ld3<COH>(fi + 2ll * N, xp + sY0 + sZ0);
-    f[3] = ld3<COH>(fi + 3ll * N, x + sYm + sZ0);
-    f[4] = ld3<COH>(fi + 4ll * N, x + sYp + sZ0);
-    f[5] = ld3<COH>(fi + 5ll * N, x + sY0 + sZm);
-    f[6] = ld3<COH>(fi + 6ll * N, x + sY0 + sZp);
-    f[7] = ld3<COH>(fi + 7ll * N, xm + sYm + sZ0);
-    f[8] = ld3<COH>(fi + 8ll * N, xp + sYp + sZ0);
-    f[9] = ld3<COH>(fi + 9ll * N, xm + sYp + sZ0);
-    f[10] = ld3<COH>(fi + 10ll * N, xp + sYm + sZ0);
-    f[11] = ld3<COH>(fi + 11ll * N, xm + sY0 + sZm);
-    f[12] = ld3<COH>(fi + 12ll * N, xp + sY0 + sZp);
-    f[13] = ld3<COH>(fi + 13ll * N, xm + sY0 + sZp);
-    f[14] = ld3<COH>(fi + 14ll * N, xp + sY0 + sZm);
-    f[15] = ld3<COH>(fi + 15ll * N, x + sYm + sZm);
-    f[16] = ld3<COH>(fi + 16ll * N, x + sYp + sZp);
-    f[17] = ld3<COH>(fi + 17ll * N, x + sYm + sZp);
-    f[18] = ld3<COH>(fi + 18ll * N, x + sYp + sZm);
+    f[0] = ld3<COH>(P.in(0), x + sY0 + sZ0);
+    f[1] = ld3<COH>(P.in(1), xm + sY0 + sZ0);
+    f[2] = ld3<COH>(P.in(2), xp + sY0 + sZ0);
+    f[3] = ld3<COH>(P.in(3), x + sYm + sZ0);
+    f[4] = ld3<COH>(P.in(4), x + sYp + sZ0);
+    f[5] = ld3<COH>(P.in(5), x + sY0 + sZm);
+    f[6] = ld3<COH>(P.in(6), x + sY0 + sZp);
+    f[7] = ld3<COH>(P.in(7), xm + sYm + sZ0);
+    f[8] = ld3<COH>(P.in(8), xp + sYp + sZ0);
+    f[9] = ld3<COH>(P.in(9), xm + sYp + sZ0);
+    f[10] = ld3<COH>(P.in(10), xp + sYm + sZ0);
+    f[11] = ld3<COH>(P.in(11), xm + sY0 + sZm);
+    f[12] = ld3<COH>(P.in(12), xp + sY0 + sZp);
+    f[13] = ld3<COH>(P.in(13), xm + sY0 + sZp);
+    f[14] = ld3<COH>(P.in(14), xp + sY0 + sZm);
+    f[15] = ld3<COH>(P.in(15), x + sYm + sZm);
+    f[16] = ld3<COH>(P.in(16), x + sYp + sZp);
+    f[17] = ld3<COH>(P.in(17), x + sYm + sZp);
+    f[18] = ld3<COH>(P.in(18), x + sYp + sZm);
 }
 
 // Force density of Sec. IV at an interior site: F = -psi grad mu with the
@@ -169,16 +202,16 @@ __device__ __forceinline__ void batch_lb_args(const BatchLists &L, const BatchRe
 
 // One D3Q19 site: pull, moments, relaxation with force and noise, store.
 // KEY_R0: the arguments sit in shared memory (batched and persistent kernels).
-template <typename T, bool GHOST_RELAX, bool COH = false, bool KEY_R0 = false>
-__device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
+// P: the planes it pulls from (P.in) and stores to (P.out).
+template <typename T, bool GHOST_RELAX, bool COH, bool KEY_R0, class PL>
+__device__ __forceinline__ void lb_site_on(const LBArgs &a, const PL &P, int x, int y, int z, float Fx, float Fy,
+                                           float Fz)
 {
     const Geom &g = a.g;
-    const int N = (int)g.n;
     const int s = x + g.nx * y + g.nx * g.ny * z;
-    T *fout = (T *)a.fout;
 
     float f[19];
-    pull19<T, COH>((const T *)a.fin, g, x, y, z, f);
+    pull19<T, COH>(P, g, x, y, z, f);
 
     float sp[10], dp[10];
 #pragma unroll
@@ -272,56 +305,64 @@ __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, fl
     const float e0 = 4.5f * tb;
     const float h1 = 1.f / 3.f, h2 = 2.f / 3.f;
     const float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
-    T *fo = fout;
-    st3(fo, s, (1.f / 3.f) * (drho - e0 + h1 * g16));
+    st3(P.out(0), s, (1.f / 3.f) * (drho - e0 + h1 * g16));
     float E, O;
     E = drho + 4.5f * Bxx - e0 - h2 * g16 - g17;
     O = 3.f * Ax - h2 * g10;
-    st3(fo + 1ll * N, s, w1 * (E + O));
-    st3(fo + 2ll * N, s, w1 * (E - O));
+    st3(P.out(1), s, w1 * (E + O));
+    st3(P.out(2), s, w1 * (E - O));
     E = drho + 4.5f * Byy - e0 - h2 * g16 + 0.5f * g17 - 0.5f * g18;
     O = 3.f * Ay - h2 * g11;
-    st3(fo + 3ll * N, s, w1 * (E + O));
-    st3(fo + 4ll * N, s, w1 * (E - O));
+    st3(P.out(3), s, w1 * (E + O));
+    st3(P.out(4), s, w1 * (E - O));
     E = drho + 4.5f * Bzz - e0 - h2 * g16 + 0.5f * g17 + 0.5f * g18;
     O = 3.f * Az - h2 * g12;
-    st3(fo + 5ll * N, s, w1 * (E + O));
-    st3(fo + 6ll * N, s, w1 * (E - O));
+    st3(P.out(5), s, w1 * (E + O));
+    st3(P.out(6), s, w1 * (E - O));
     const float Gev = h1 * g16 + 0.5f * g17;
     E = drho + 4.5f * (Bxx + Byy + 2.f * Bxy) - e0 + Gev + 0.5f * g18;
     O = 3.f * (Ax + Ay) + h1 * (g10 + g11) + g13 - g14;
-    st3(fo + 7ll * N, s, w2 * (E + O));
-    st3(fo + 8ll * N, s, w2 * (E - O));
+    st3(P.out(7), s, w2 * (E + O));
+    st3(P.out(8), s, w2 * (E - O));
     E = drho + 4.5f * (Bxx + Byy - 2.f * Bxy) - e0 + Gev + 0.5f * g18;
     O = 3.f * (Ax - Ay) + h1 * (g10 - g11) + g13 + g14;
-    st3(fo + 9ll * N, s, w2 * (E + O));
-    st3(fo + 10ll * N, s, w2 * (E - O));
+    st3(P.out(9), s, w2 * (E + O));
+    st3(P.out(10), s, w2 * (E - O));
     E = drho + 4.5f * (Bxx + Bzz + 2.f * Bxz) - e0 + Gev - 0.5f * g18;
     O = 3.f * (Ax + Az) + h1 * (g10 + g12) - g13 + g15;
-    st3(fo + 11ll * N, s, w2 * (E + O));
-    st3(fo + 12ll * N, s, w2 * (E - O));
+    st3(P.out(11), s, w2 * (E + O));
+    st3(P.out(12), s, w2 * (E - O));
     E = drho + 4.5f * (Bxx + Bzz - 2.f * Bxz) - e0 + Gev - 0.5f * g18;
     O = 3.f * (Ax - Az) + h1 * (g10 - g12) - g13 - g15;
-    st3(fo + 13ll * N, s, w2 * (E + O));
-    st3(fo + 14ll * N, s, w2 * (E - O));
+    st3(P.out(13), s, w2 * (E + O));
+    st3(P.out(14), s, w2 * (E - O));
     E = drho + 4.5f * (Byy + Bzz + 2.f * Byz) - e0 + h1 * g16 - g17;
     O = 3.f * (Ay + Az) + h1 * (g11 + g12) + g14 - g15;
-    st3(fo + 15ll * N, s, w2 * (E + O));
-    st3(fo + 16ll * N, s, w2 * (E - O));
+    st3(P.out(15), s, w2 * (E + O));
+    st3(P.out(16), s, w2 * (E - O));
     E = drho + 4.5f * (Byy + Bzz - 2.f * Byz) - e0 + h1 * g16 - g17;
     O = 3.f * (Ay - Az) + h1 * (g11 - g12) + g14 + g15;
-    st3(fo + 17ll * N, s, w2 * (E + O));
-    st3(fo + 18ll * N, s, w2 * (E - O));
+    st3(P.out(17), s, w2 * (E + O));
+    st3(P.out(18), s, w2 * (E - O));
+}
+
+// The same site on the planes of a.fin and a.fout.
+template <typename T, bool GHOST_RELAX, bool COH = false, bool KEY_R0 = false>
+__device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
+{
+    lb_site_on<T, GHOST_RELAX, COH, KEY_R0>(a, PlanesFromBase<T>{(const T *)a.fin, (T *)a.fout, a.g.n}, x, y, z,
+                                             Fx, Fy, Fz);
 }
 
 // Velocity of the streamed state at (x, y, z): u = (sum fbar c + F/2)/rho with
 // fbar the populations the next step pulls (a.fout) and F this step's force.
-template <typename T, bool FORCE, bool COH = false>
-__device__ __forceinline__ void vel3_site(const LBArgs &a, int x, int y, int z)
+// P.in: the planes of a.fout.
+template <typename T, bool FORCE, bool COH, class PL>
+__device__ __forceinline__ void vel3_site_on(const LBArgs &a, const PL &P, int x, int y, int z)
 {
     const Geom &g = a.g;
     float f[19];
-    pull19<T, COH>((const T *)a.fout, g, x, y, z, f);
+    pull19<T, COH>(P, g, x, y, z, f);
     float sp[10], dp[10];
 #pragma unroll
     for (int p = 1; p <= 9; ++p) {
@@ -338,6 +379,13 @@ __device__ __forceinline__ void vel3_site(const LBArgs &a, int x, int y, int z)
     store_padded(a.u, g, x, y, z, (jx + 0.5f * Fx) * irho, 1);
     store_padded(a.u + g.pn, g, x, y, z, (jy + 0.5f * Fy) * irho, 1);
     store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
+}
+
+// The same on the planes of a.fout.
+template <typename T, bool FORCE, bool COH = false>
+__device__ __forceinline__ void vel3_site(const LBArgs &a, int x, int y, int z)
+{
+    vel3_site_on<T, FORCE, COH>(a, PlanesFromBase<T>{(const T *)a.fout, nullptr, a.g.n}, x, y, z);
 }
 
 }  // namespace flb
