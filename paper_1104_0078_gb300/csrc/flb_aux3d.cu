@@ -17,8 +17,16 @@ namespace flb {
 // with fbar the populations the next step pulls (the planes just written, a.fout)
 // and F this step's force density -- the velocity that advects psi (Gauss-Seidel
 // coupling of Sec. VI: the psi step follows the fluid step).  The planes'
-// addresses are formed from a.fout: with a table of them (as the collide-stream
-// takes) this memory-bound gather ran 5% slower at 256^3 (283 against 269 us).
+// addresses are formed from a.fout with a 32-bit plane stride (N < 2^31): with
+// a table of them (as the collide-stream takes) this memory-bound gather ran 5%
+// slower at 256^3 (283 against 269 us).
+template <typename T>
+struct PlanesStride32 {
+    const T *fi;
+    int N;
+    __device__ __forceinline__ const T *in(int i) const { return fi + (long long)i * N; }
+};
+
 template <typename T, bool FORCE>
 __device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int bz)
 {
@@ -27,7 +35,7 @@ __device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int 
     const int y = by * LB_BY + threadIdx.y;
     const int z = bz * LB_BZ + threadIdx.z;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-    vel3_site<T, FORCE, false>(a, x, y, z);
+    vel3_site_on<T, FORCE, false>(a, PlanesStride32<T>{(const T *)a.fout, (int)g.n}, x, y, z);
 }
 
 template <typename T, bool FORCE>
