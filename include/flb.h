@@ -134,11 +134,10 @@ extern "C" {
  *                 noise follows it, so FLB_FD keeps the fluctuation-dissipation
  *                 theorem with any of them): FLB_LAP_SO (default), FLB_LAP_CD,
  *                 FLB_LAP_PK or FLB_LAP_LB; 2D takes SO or CD.
- * D3Q19 with FLB_LAP_SO and FLB_FD or FLB_FV, and D3Q15 with FLB_LAP_SO and
- * FLB_FD, run the tiled 3D kernels; every other 3D combination (another
- * Laplacian, FLB_NAIVE, FV on D3Q15) runs one-thread-per-site stencil kernels
- * that keep mu, the noise increment and the FV flux in HBM, in
- * FLB_MODE_PLAIN only.
+ * D3Q19 and D3Q15 with FLB_LAP_SO and FLB_FD or FLB_FV run the tiled 3D
+ * kernels; every other 3D combination (another Laplacian, FLB_NAIVE) runs
+ * one-thread-per-site stencil kernels that keep mu, the noise increment and
+ * the FV flux in HBM, in FLB_MODE_PLAIN only.
  */
 typedef struct flb_params {
     int32_t dim, q;
@@ -258,10 +257,11 @@ int flb_sq_reset(flb_handle *h, int32_t rep);
  * Launch mode for flb_step:
  *   FLB_MODE_PLAIN       every replica's kernels launched one replica after another;
  *   FLB_MODE_BATCHED     all replicas in one launch per phase (mu, collide-stream,
- *                        velocity, psi stages), replayed as a CUDA graph (3D, FV);
+ *                        velocity, psi stages), replayed as a CUDA graph (D3Q19,
+ *                        FV, FLB_LAP_SO, Euler or Heun);
  *   FLB_MODE_PERSISTENT  all replicas advanced the n steps of one flb_step call
  *                        by one cooperative launch per stretch between sampling
- *                        steps (3D, FV, FP32 storage).  Its blocks take tile tasks
+ *                        steps (as FLB_MODE_BATCHED, with FP32 storage).  Its blocks take tile tasks
  *                        from a list in order and wait, per replica, for the
  *                        previous phase of that replica only (a per-replica phase
  *                        barrier), each wait bounded by flb_set_wait_limit.
