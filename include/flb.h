@@ -351,10 +351,12 @@ int flb_kernel_times(flb_handle *h, double *ms, int64_t *counts);
  * Limit: Kx*ny*nz and Kx*Ky*nz must each be <= FLB_NOALLOC_MAX_VALUES, else the
  * call returns FLB_ENOSPC without launching anything (e.g. 64^3 whole grid fits;
  * 128^3 needs kmax <= 15).  Other errors: EINVAL (null pointer, size < 1, kmax < 0,
- * N >= 2^31), ECUDA.  The call allocates nothing: no cudaMalloc, cudaFree or
- * allocating library routine.  Its first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls on a device share the array,
+ * N >= 2^31), ECUDA (also, before any launch, when an earlier CUDA error is
+ * still pending on the calling thread; that error is left for its owner).  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first call on a device may load the library's
+ * device code there, so make it before any stream capture.  All calls on a device share the array,
  * which keeps the last call's contents; calls that overlap on the GPU (on
  * different streams, or from several threads) race on it and must be ordered by
  * the caller.

@@ -473,6 +473,20 @@ LBArgs lb_args(const Rep &r, float *psi_n)
     la.gamma_g = r.gamma_g;
     la.kT = (float)p.kT;
     std::memcpy(la.namp, r.namp, sizeof(la.namp));
+    {
+        const double ws = r.omega_s, wb = r.omega_b, cs = 1.0 - 0.5 * ws, cb = 1.0 - 0.5 * wb;
+        la.rq[0] = (float)(4.5 * (1.0 - ws));
+        la.rq[1] = (float)(4.5 * ws);
+        la.rq[2] = (float)(4.5 * cs);
+        la.rq[3] = (float)(1.5 * (wb - ws));
+        la.rq[4] = (float)(3.0 * (cb - cs));
+        la.iso = r.omega_s != r.omega_b;
+        la.k3T = (float)(3.0 * p.kT);
+        // Q = 4.5 B takes the stress noise at 4.5 x (2/9, 1/9); the ghosts G10-G12,
+        // G16 are g/3 and G17, G18 are g/2
+        const double sc[15] = {1, 1, 1, 0.5, 0.5, 0.5, 1.0 / 3, 1.0 / 3, 1.0 / 3, 1, 1, 1, 1.0 / 3, 0.5, 0.5};
+        for (int t = 0; t < 15; ++t) la.nq[t] = (float)(sc[t] * (double)r.namp[t]);
+    }
     la.coupling = p.coupling;
     const bool fv_grad =
         p.force_grad == FLB_FORCE_FV || (p.force_grad == FLB_FORCE_MATCHED && p.psi_scheme == FLB_FV);

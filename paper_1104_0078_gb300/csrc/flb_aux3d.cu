@@ -27,21 +27,18 @@ struct PlanesStride32 {
     __device__ __forceinline__ const T *in(int i) const { return fi + (long long)i * N; }
 };
 
+// Two sites per thread, (x, y, z) and (x, y, z + 1), as in the collide-stream.
 template <typename T, bool FORCE>
-__device__ __forceinline__ void vel3_block(const LBArgs &a, int bx, int by, int bz)
+__global__ void __launch_bounds__(LB_BX *LB_BY) vel3_kernel(const LBArgs a)
 {
     const Geom &g = a.g;
-    const int x = bx * LB_BX + threadIdx.x;
-    const int y = by * LB_BY + threadIdx.y;
-    const int z = bz * LB_BZ + threadIdx.z;
+    const int x = blockIdx.x * LB_BX + threadIdx.x;
+    const int y = blockIdx.y * LB_BY + threadIdx.y;
+    const int z = blockIdx.z * LB_BZ;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-    vel3_site_on<T, FORCE, false>(a, PlanesStride32<T>{(const T *)a.fout, (int)g.n}, x, y, z);
-}
-
-template <typename T, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_kernel(const LBArgs a)
-{
-    vel3_block<T, FORCE>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    const int nl = z + 1 < g.nz ? 2 : 1;
+    const int zl[2] = {z, z + nl - 1};
+    vel3_sites<F2, T, FORCE, false>(a, PlanesStride32<T>{(const T *)a.fout, (int)g.n}, x, y, zl, nl);
 }
 
 // mu = A psi + B psi^3 - K lap_SO psi on the interior and HALO ghost layers
@@ -129,7 +126,7 @@ cudaError_t launch_sigma3(const Geom &g, const float *psi, float *sig, float A, 
 
 cudaError_t launch_vel3(const LBArgs &a, int storage, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 block(LB_BX, LB_BY, 1);
     const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
     const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;
     if (storage == FLB_F16_DEV) {

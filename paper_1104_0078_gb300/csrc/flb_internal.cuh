@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "../../include/flb.h"
+#include "flb_lane.cuh"
 
 namespace flb {
 
@@ -87,7 +88,9 @@ __device__ __forceinline__ float u01(uint32_t x)
 //    of f select one of 32 cells; ln f = -ln r_j + ln(1 + d) with d = f r_j - 1
 //    formed by one FMA (|d| < 1/64) and ln(1 + d) by its series to d^5 (error
 //    < 3e-12).  r_j is near 1/(cell centre) and exactly 1 in the cell holding 1,
-//    where d = f - 1 is exact, so u near 1 keeps its relative accuracy.
+//    where d = f - 1 is exact, so u near 1 keeps its relative accuracy.  The
+//    radius needs -2 ln u: the series and the table carry the factor -2, which
+//    is exact in binary arithmetic.
 //  * sin, cos of 2 pi t, t = (m + 1/2) 2^-23: t = j/64 + t_lo, the table of
 //    sin, cos(2 pi j/64) and the angle-addition formulas with sin b, cos b of
 //    b = 2 pi t_lo < 2 pi/64 by their series (to b^5 and b^4; error < 2e-9).
@@ -95,11 +98,11 @@ __device__ __forceinline__ float u01(uint32_t x)
 // series and rounded to float.
 namespace bm {
 
-struct alignas(8) SinCos {
-    float s, c;
+struct alignas(16) SinCos {
+    float s, c, ns, pad;  // sin, cos and -sin of 2 pi j/64
 };
 struct alignas(8) LogCell {
-    float r, nlr;  // r_j and -ln r_j
+    float r, l2r;  // r_j and 2 ln r_j
 };
 struct Tables {
     SinCos sc[64];
@@ -155,19 +158,21 @@ constexpr Tables make_tables()
         const double sq[4] = {s, c, -s, -c}, cq[4] = {c, -s, -c, s};
         T.sc[j].s = (float)sq[q];
         T.sc[j].c = (float)cq[q];
+        T.sc[j].ns = -(float)sq[q];
+        T.sc[j].pad = 0.0f;
     }
     const int one = (int)((0x3F800000u - kSqrtHalfBits) >> 18);  // the cell holding 1
     for (int j = 0; j < 32; ++j) {
         if (j == one) {
             T.lg[j].r = 1.0f;
-            T.lg[j].nlr = 0.0f;
+            T.lg[j].l2r = 0.0f;
             continue;
         }
         const double lo = f32_of_bits(kSqrtHalfBits + ((uint32_t)j << 18));
         const double hi = f32_of_bits(kSqrtHalfBits + ((uint32_t)(j + 1) << 18));
         const float r = (float)(2.0 / (lo + hi));
         T.lg[j].r = r;
-        T.lg[j].nlr = (float)(-series_log((double)r));
+        T.lg[j].l2r = -2.0f * (float)(-series_log((double)r));  // -2 x (the binary32 -ln r_j)
     }
     return T;
 }
@@ -177,58 +182,88 @@ constexpr Tables make_tables()
 // one copy per translation unit, read through the read-only cache
 static __device__ const bm::Tables kBM = bm::make_tables();
 
-// ln u01-style radius uniform: ln(((a >> 9) + 1/2) 2^-23) = ln((2k+1) 2^-24)
-__device__ __forceinline__ float bm_log_u(uint32_t a)
+// Box-Muller on V::L independent pairs at once, one per lane (F2: two pairs in
+// Blackwell's packed FP32 registers): lane l takes the radius word a[l] and the
+// angle word b[l] and returns g0 = r cos 2 pi v, g1 = r sin 2 pi v with
+// r = sqrt(-2 ln u), u = ((a >> 9) + 1/2) 2^-23, v = ((b >> 9) + 1/2) 2^-23.
+// SCALED: r is multiplied by sc first (lane-wise), so the outputs come scaled.
+// The integer steps, table loads and the reciprocal square root run per lane;
+// every FP32 step is one lane-generic operation, so a pair gets the same bits
+// in either lane type.
+template <class V, bool SCALED = false>
+__device__ __forceinline__ void bm_eval(const uint32_t *a, const uint32_t *b, V sc, V &g0, V &g1)
 {
-    const float fn = __uint2float_rn(((a >> 9) << 1) | 1u);  // 2k+1 < 2^24, exact
-    const int bits = __float_as_int(fn);
-    const int t = bits - (int)bm::kSqrtHalfBits;
-    const int e = t >> 23;                                  // 2k+1 = 2^e f
-    const float f = __int_as_float(bits - (e << 23));       // f in [sqrt(1/2), sqrt(2))
-    const float2 L = __ldg(reinterpret_cast<const float2 *>(&kBM.lg[(t >> 18) & 31]));  // (r_j, -ln r_j)
-    const float d = fmaf(f, L.x, -1.0f);
-    float p = fmaf(d, 0.2f, -0.25f);
-    p = fmaf(d, p, 1.0f / 3.0f);
-    p = fmaf(d, p, -0.5f);
-    p = fmaf(d, p, 1.0f);
-    return fmaf((float)(e - 24), 0.693147180559945f, L.y) + d * p;
-}
-
-// sin and cos of 2 pi ((b >> 9) + 1/2) 2^-23
-__device__ __forceinline__ void bm_sincos_2pi_u(uint32_t b, float &s, float &c)
-{
-    const uint32_t m = b >> 9;
-    const float2 A = __ldg(reinterpret_cast<const float2 *>(&kBM.sc[m >> 17]));  // (sin, cos)(2 pi j/64)
-    const float x = fmaf((float)(m & 0x1FFFFu), (float)(2.0 * bm::kPi / 8388608.0), (float)(bm::kPi / 8388608.0));
-    const float x2 = x * x;
-    const float cb = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), 1.0f);
-    const float sb = x * fmaf(x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
-    const float sa = A.x, ca = A.y;
-    s = fmaf(sa, cb, ca * sb);
-    c = fmaf(ca, cb, -(sa * sb));
+    constexpr int L = V::L;
+    float f[L], lr[L], l2r[L], eb[L], xm[L], sa[L], ca[L], nsa[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const float fn = __uint2float_rn((a[l] >> 8) | 1u);   // 2k+1 < 2^24, exact
+        const int bits = __float_as_int(fn);
+        const int t = bits - (int)bm::kSqrtHalfBits;
+        const int e = t >> 23;                                // 2k+1 = 2^e f
+        f[l] = __int_as_float(bits - (e << 23));              // f in [sqrt(1/2), sqrt(2))
+        const float2 C = __ldg(reinterpret_cast<const float2 *>(&kBM.lg[(t >> 18) & 31]));  // (r_j, 2 ln r_j)
+        lr[l] = C.x;
+        l2r[l] = C.y;
+        eb[l] = __int_as_float(0x4B400000 + e - 24);          // 1.5 2^23 + (e - 24), exact
+        const uint32_t m = b[l] >> 9;
+        const float4 A = __ldg(reinterpret_cast<const float4 *>(&kBM.sc[m >> 17]));  // (sin, cos, -sin)(2 pi j/64)
+        sa[l] = A.x;
+        ca[l] = A.y;
+        nsa[l] = A.z;
+        xm[l] = __int_as_float(0x4B000000u | (m & 0x1FFFFu));  // 2^23 + (m mod 2^17), exact
+    }
+    // -2 ln u = -2 (e - 24) ln 2 + 2 ln r_j - 2 ln(1 + d)
+    const V d = vfma(vmake<V>(f), vmake<V>(lr), V::bc(-1.0f));
+    V p = vfma(d, V::bc(-0.4f), V::bc(0.5f));  // -2 x the series of ln(1 + d)/d, Horner form
+    p = vfma(d, p, V::bc(-2.0f / 3.0f));
+    p = vfma(d, p, V::bc(1.0f));
+    p = vfma(d, p, V::bc(-2.0f));
+    const V em = vmake<V>(eb) - V::bc(12582912.0f);       // e - 24, exact
+    const V e2 = vfma(d, p, vfma(em, V::bc(-2.0f * 0.693147180559945f), vmake<V>(l2r)));  // >= 1.19e-7
+    float rs[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) rs[l] = rsqrtf(e2.lane(l));
+    V rad = e2 * vmake<V>(rs);
+    if (SCALED) rad = rad * sc;
+    // sin, cos of 2 pi v by angle addition
+    const V x = vfma(vmake<V>(xm) - V::bc(8388608.0f), V::bc((float)(2.0 * bm::kPi / 8388608.0)),
+                     V::bc((float)(bm::kPi / 8388608.0)));
+    const V x2 = x * x;
+    const V cb = vfma(x2, vfma(x2, V::bc(1.0f / 24.0f), V::bc(-0.5f)), V::bc(1.0f));
+    const V sb = x * vfma(x2, vfma(x2, V::bc(1.0f / 120.0f), V::bc(-1.0f / 6.0f)), V::bc(1.0f));
+    const V s = vfma(vmake<V>(sa), cb, vmake<V>(ca) * sb);
+    const V c = vfma(vmake<V>(ca), cb, vmake<V>(nsa) * sb);
+    g0 = rad * c;
+    g1 = rad * s;
 }
 
 // Box-Muller: r = sqrt(-2 ln a), (r cos 2 pi b, r sin 2 pi b).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
 {
-    const float e = -2.0f * bm_log_u(a);  // e >= 1.19e-7 > 0
-    const float rad = e * rsqrtf(e);
-    float s, c;
-    bm_sincos_2pi_u(b, s, c);
-    g0 = rad * c;
-    g1 = rad * s;
+    F1 r0, r1;
+    bm_eval<F1>(&a, &b, F1{1.0f}, r0, r1);
+    g0 = r0.v;
+    g1 = r1.v;
 }
 
-// Four standard normals of one Philox block (Box-Muller on (x,y) and (z,w)).
+// Four standard normals of one Philox block (Box-Muller on (x,y) and (z,w),
+// the two pairs evaluated together in the lanes of one packed register).
 // KEY_R0: form the round keys from K's round-0 keys (arguments in shared memory).
-template <bool KEY_R0 = false>
+// SCALED: every normal multiplied by sc.
+template <bool KEY_R0 = false, bool SCALED = false>
 __device__ __forceinline__ void normals4(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
-                                         uint32_t block, float g[4])
+                                         uint32_t block, float g[4], float sc = 1.0f)
 {
     const u32x4 c{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)};
     const u32x4 r = KEY_R0 ? philox4x32_10_r0(c, K.k0[0], K.k1[0]) : philox4x32_10(c, K);
-    box_muller(r.x, r.y, g[0], g[1]);
-    box_muller(r.z, r.w, g[2], g[3]);
+    const uint32_t a[2] = {r.x, r.z}, b[2] = {r.y, r.w};
+    F2 c0, s0;
+    bm_eval<F2, SCALED>(a, b, F2::bc(sc), c0, s0);
+    g[0] = c0.v.x;
+    g[1] = s0.v.x;
+    g[2] = c0.v.y;
+    g[3] = s0.v.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -340,6 +375,14 @@ struct LBArgs {
     float gamma_g;             // ghost relaxation factor
     float kT;
     float namp[16];            // sqrt((1 - gamma_k^2)/b_k) of the noisy modes, in noise order
+    // D3Q19 collide-stream, in the units of its scaled stress Q = 4.5 B and scaled
+    // ghosts: rq = 4.5 (1 - ws), 4.5 ws, 4.5 cs (cs = 1 - ws/2), 1.5 (wb - ws),
+    // 3 (cb - cs); iso: wb != ws; k3T = kT / c_s^2; nq: the noise amplitudes
+    // namp scaled to those units
+    float rq[5];
+    int iso;
+    float k3T;
+    float nq[15];
     int coupling;
     int force_kind;            // 0: -psi grad_CD mu, 1: -psi grad_FV mu (D3Q19), 2: -div sigma (stress
                                // form), 3: -psi grad_FV mu on the D3Q15 neighbourhood

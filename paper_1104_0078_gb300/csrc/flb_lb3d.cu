@@ -1,4 +1,5 @@
-// flb_lb3d.cu -- D3Q19 fused collide-stream, one thread per site.
+// flb_lb3d.cu -- D3Q19 fused collide-stream, two sites per thread (plain mode)
+// or one (batched mode).
 //
 // The kernel forms the force density of Sec. IV, F = -psi grad mu, from the mu
 // field (central difference, or the FV gradient of Eq. (fvgrad) when psi moves
@@ -9,38 +10,36 @@
 // advects psi from vel3_kernel (flb_aux3d.cu).
 //
 // Indices are 32-bit (N and the padded planes are < 2^31); population plane i
-// of N sites starts at fin + i*N.  Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2,
+// of N sites starts at fin + i*N.  The plain kernel runs seven 128-thread blocks
+// per SM (72 registers): with 96 registers (five blocks) it ran 4.85 ms at
+// 512^3, with 80 (six) 4.68 ms, with 72 (seven, 20 bytes spilled) 4.52 ms and
+// with 64 (eight, 84 bytes spilled) 4.63 ms.  Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2,
 // xy, yz, zx, three c^2 c_a ghosts, three c_a(c_b^2-c_g^2) ghosts, c^4,
 // c^2(3c_x^2-c^2), c^2(c_y^2-c_z^2).
 #include "flb_site3d.cuh"
 
 namespace flb {
 
-// One thread per site on a 3D grid of 32 x 4 x 2 blocks (a warp covers 32
-// consecutive x, so every population plane is read and written in full rows).
-
-// One block of the collide-stream (block coordinates bx, by, bz of the 32 x 4 x 2
-// grid) on the population planes of the table P.
+// Two sites per thread: a 32 x 4 block of threads covers a 32 x 4 x 2 tile of
+// sites, thread (x, y) working on (x, y, z) and (x, y, z + 1) in the two lanes
+// of Blackwell's packed FP32 registers (one issue slot for both sites' FP32
+// arithmetic).  A warp covers 32 consecutive x, so every population plane is
+// read and written in full rows.
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__device__ __forceinline__ void lb3_block(const LBArgs &a, const PlaneTable<T> &P, int bx, int by, int bz)
-{
-    const Geom &g = a.g;
-    const int x = bx * LB_BX + threadIdx.x;
-    const int y = by * LB_BY + threadIdx.y;
-    const int z = bz * LB_BZ + threadIdx.z;
-    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3<false>(a, x, y, z, Fx, Fy, Fz);
-    lb_site_on<T, GHOST_RELAX, false, false>(a, P, x, y, z, Fx, Fy, Fz);
-}
-
-template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, GHOST_RELAX ? 5 : 6)
+__global__ void __launch_bounds__(LB_BX *LB_BY, 7)
     lb3_kernel(const LBArgs a, const __grid_constant__ PlaneTable<T> P)
 {
-    lb3_block<T, GHOST_RELAX, FORCE>(a, P, blockIdx.x, blockIdx.y, blockIdx.z);
+    const Geom &g = a.g;
+    const int x = blockIdx.x * LB_BX + threadIdx.x;
+    const int y = blockIdx.y * LB_BY + threadIdx.y;
+    const int z = blockIdx.z * LB_BZ;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+    const int nl = z + 1 < g.nz ? 2 : 1;
+    const int zl[2] = {z, z + nl - 1};  // a lane past the box repeats lane 0's site
+    F2 Fx = F2::bc(0.f), Fy = F2::bc(0.f), Fz = F2::bc(0.f);
+    if (FORCE && (a.coupling & FLB_COUPLE_FORCE)) force3v<false>(a, x, y, zl, Fx, Fy, Fz);
+    lb_sites<F2, T, GHOST_RELAX, false, false>(a, P, x, y, zl, nl, Fx, Fy, Fz);
 }
-
 
 // ---- batched variant: block b of the launch works on the row-packed entry L.lb[b] ----
 template <typename T, bool GHOST_RELAX, bool FORCE>
@@ -80,7 +79,7 @@ cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool 
 
 cudaError_t launch_lb3d(const LBArgs &a, int storage, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 block(LB_BX, LB_BY, 1);
     const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
     const bool gr = a.gamma_g != 0.0f;
     const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;

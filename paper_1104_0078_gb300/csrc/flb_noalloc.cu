@@ -10,8 +10,6 @@
 // file-scope __device__ array of fixed size that every GPU loading the library
 // holds until the process exits, so a call needs no memory beyond the caller's
 // own input and output.
-#include <mutex>
-
 #include "flb_internal.cuh"
 
 namespace flb {
@@ -92,25 +90,15 @@ __global__ void na_dft_z(NaArgs a)
     a.S[t] = a.scale * (re * re + im * im);  // written, not accumulated
 }
 
-// Device address of the scratch array, resolved once per device.
-constexpr int NA_MAX_DEVICES = 64;
-std::mutex g_na_mutex;
-float2 *g_na_addr[NA_MAX_DEVICES] = {nullptr};
-
+// Device address of the scratch array on the current device, looked up on every
+// call (the lookup allocates nothing), so the address stays right after the
+// device's context was reset and the module loaded again.
 cudaError_t scratch_address(float2 **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_addr[dev] = (float2 *)p;
-    }
-    *out = g_na_addr[dev];
+    *out = (float2 *)p;
     return cudaSuccess;
 }
 
@@ -135,6 +123,9 @@ extern "C" int flb_structure_factor_noalloc(const float *psi_dev, int32_t nx, in
     a.Kz = axis_keep(nz, kmax);
     const long long n1 = (long long)a.Kx * ny * nz, n2 = (long long)a.Kx * a.Ky * nz, n3 = (long long)a.Kx * a.Ky * a.Kz;
     if (n1 > NOALLOC_HALF || n2 > NOALLOC_HALF) return FLB_ENOSPC;
+    // an error left pending by earlier work on this thread is not this call's:
+    // report it without clearing it, and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return FLB_ECUDA;
     float2 *base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return FLB_ECUDA;
     a.X1 = base;
@@ -144,7 +135,9 @@ extern "C" int flb_structure_factor_noalloc(const float *psi_dev, int32_t nx, in
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int bs = 256;
     na_dft_x<<<(unsigned)((n1 + bs - 1) / bs), bs, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return FLB_ECUDA;
     na_dft_y<<<(unsigned)((n2 + bs - 1) / bs), bs, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return FLB_ECUDA;
     na_dft_z<<<(unsigned)((n3 + bs - 1) / bs), bs, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? FLB_OK : FLB_ECUDA;
 }

@@ -356,11 +356,11 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     J[TJ_N + k] = jy;
                     J[2 * TJ_N + k] = jz;
                     if (NOISE) {
-                        float Gn[4];
-                        normals4<KEY_R0>(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn);
-                        X[k] = sdx * Gn[0];
-                        X[TJ_N + k] = sdx * Gn[1];
-                        X[2 * TJ_N + k] = sdx * Gn[2];
+                        float Gn[4];  // N(0, 2 kT M): the radius carries the factor sqrt(2 kT M)
+                        normals4<KEY_R0, true>(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn, sdx);
+                        X[k] = Gn[0];
+                        X[TJ_N + k] = Gn[1];
+                        X[2 * TJ_N + k] = Gn[2];
                     }
                 }
             }

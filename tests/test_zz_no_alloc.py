@@ -55,8 +55,32 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
     big = torch.zeros(128 ** 3, dtype=torch.float32, device="cuda:0")
     out = torch.zeros(128 ** 3, dtype=torch.float64, device="cuda:0")
     assert _noalloc(big, (128, 128, 128), 0, out, st) == F.FLB_ENOSPC
-    assert _noalloc(big, (128, 128, 128), 15, out, st) == F.FLB_OK
     st.synchronize()
     lib = F.load_library()
     assert lib.flb_structure_factor_noalloc(None, 4, 4, 4, 0, ctypes.c_void_p(out.data_ptr()), None) == F.FLB_EINVAL
     assert _noalloc(big, (128, 128, 128), -1, out, st) == F.FLB_EINVAL
+
+
+def test_noalloc_near_limit_window_matches_handle_path():
+    """The largest accepted layout: 128^3 with kmax = 15 fills Kx*ny*nz =
+    507,904 of the 524,288 scratch values; its values are compared twice with
+    the handle path on the same field."""
+    import torch
+    n, kmax = 128, 15
+    p = F.flb_params_default(nx=n, ny=n, nz=n, sq_kmax=kmax)
+    psi0 = I.random_field(n ** 3, 0.3, 23)
+    s = F.Solver(p)
+    s.set_fields(psi=psi0)
+    s.sample(1)
+    ref, ns = s.structure_factor()
+    assert ns == 1 and ref.size == (2 * kmax + 1) ** 3
+    del s
+    psi_t = torch.tensor(psi0, dtype=torch.float32, device="cuda:0")
+    S_t = torch.full((ref.size,), -1.0, dtype=torch.float64, device="cuda:0")
+    st = torch.cuda.Stream()
+    for _ in range(2):
+        assert _noalloc(psi_t, (n, n, n), kmax, S_t, st) == F.FLB_OK
+        st.synchronize()
+        got = S_t.cpu().numpy()
+        assert np.allclose(got, ref, rtol=RTOL, atol=1e-12 * ref.max())
+        S_t.fill_(-1.0)
