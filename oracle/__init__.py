@@ -311,6 +311,27 @@ def structure_factor(p: Params, psi: np.ndarray) -> np.ndarray:
     return np.abs(np.fft.fftn(a)) ** 2 / p.n
 
 
+def structure_factor_at(p: Params, psi: np.ndarray, ks) -> np.ndarray:
+    """|psi~(q)|^2 / N at the integer wavevectors ks = [(kx, ky, kz), ...],
+    q_a = 2 pi k_a / n_a, straight from the definition psi~(q) = sum_r psi(r)
+    e^{-i q.r} (Eqs. test1, test2), summed axis by axis in FP64 -- for fields too
+    large for a full FFT, where only some wavevectors are wanted."""
+    a = np.asarray(psi, dtype=np.float64).reshape(p.shape)   # (nz, ny, nx)
+    nz, ny, nx = p.shape
+    out = []
+    cache = {}
+    for kx, ky, kz in ks:
+        if kx not in cache:   # sum over x: (nz, ny) complex
+            ph = 2.0 * math.pi * kx * np.arange(nx) / nx
+            cache[kx] = a @ np.cos(ph) - 1j * (a @ np.sin(ph))
+        t = cache[kx]
+        ey = np.exp(-2j * math.pi * ky * np.arange(ny) / ny)
+        ez = np.exp(-2j * math.pi * kz * np.arange(nz) / nz)
+        v = ez @ (t @ ey)
+        out.append(abs(v) ** 2 / p.n)
+    return np.array(out)
+
+
 def dynamic_structure_factor(p: Params, psis, nlags: int) -> np.ndarray:
     """S(q, l) = mean over samples t with t >= l of Re[psi~(q, t) conj(psi~(q, t - l))],
     psi~(q) = N^-1/2 sum_r psi(r) e^{-iq.r}: the paper's S(q, tau) of Sec. VI.A

@@ -56,3 +56,60 @@ def test_quench_512_windows_match_oracle(q, scheme):
         p_g = pg.reshape(W, W, W)[c, c, c].reshape(-1)
         assert field_error(f_g, f_o, w[:, None]) < TOL
         assert field_error(p_g, p_o, p_o.mean()) < TOL
+
+
+def test_structure_factor_512_sampled_wavevectors():
+    # the S(q) window the bench samples on the 512^3 quench (|k_a| <= 8, FFT
+    # order), on the seeded initial field: sampled wavevectors of the window,
+    # negative and zero components included, against the oracle's direct sum
+    # of the definition over all 512^3 sites
+    d = dict(I.WORKLOADS["quench"])
+    n, kmax = 512, 8
+    p = F.flb_params_default(nx=n, ny=n, nz=n, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
+                             psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, seed=d["seed"], sq_kmax=kmax)
+    psi0 = I.uniform_field(n ** 3, -0.01, 0.01, 11)
+    s = F.Solver(p)
+    s.set_fields(psi=psi0)
+    s.sample(1)
+    S_gpu, ns = s.structure_factor()
+    del s
+    K = 2 * kmax + 1
+    S_gpu = S_gpu.reshape(K, K, K)
+    slot = lambda k: k if k >= 0 else K + k   # window index of k in FFT order
+    ks = [(1, 0, 0), (0, 0, 1), (8, 8, 8), (-8, 3, -5), (2, -7, 0), (-1, -1, -1), (5, 1, 8), (0, 6, -3)]
+    op = O.Params(dim=3, q=19, nx=n, ny=n, nz=n, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"])
+    ref = O.structure_factor_at(op, psi0, ks)
+    got = np.array([S_gpu[slot(kz), slot(ky), slot(kx)] for kx, ky, kz in ks])
+    assert np.allclose(got, ref, rtol=1e-4, atol=1e-6 * ref.max()), (got, ref)
+
+
+def test_fp16_storage_on_the_512_quench():
+    # the FP16-deviation storage form on the 512^3 spinodal quench (A -0.0625,
+    # B 0.0625, K 0.04, M 0.1, kT 1e-5, psi0 uniform in [-0.01, 0.01]), 2000 steps
+    # beside FP32 from the same seed and start.  The run is out of equilibrium,
+    # so equipartition is checked where it must hold: every ghost mode of the
+    # stored populations keeps <m_g^2> = (rho0 kT / c_s^2) b_g within 1% (the
+    # ghosts are projected and re-drawn each step, Sec. III); mass and psi are
+    # conserved within 1e-6; and <u_a^2> of FP16 matches FP32 within 1%
+    d = dict(I.WORKLOADS["quench"])
+    n = 512
+    N = n ** 3
+    psi0 = I.uniform_field(N, -0.01, 0.01, 11)
+    _, b = O.moment_basis(3, 19)
+    u2 = {}
+    for st in (F.FLB_F32_DEV, F.FLB_F16_DEV):
+        p = F.flb_params_default(nx=n, ny=n, nz=n, tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"],
+                                 M=d["M"], psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, storage=st, seed=d["seed"])
+        s = F.Solver(p)
+        s.set_fields(psi=psi0)
+        t0, _, _ = s.moments()
+        s.step(2000)
+        t1, uu, rc = s.moments()
+        assert rc == F.FLB_OK
+        assert abs(t1[0] - t0[0]) / (N * p.rho0) < 1e-6
+        assert abs(t1[4] - t0[4]) / np.abs(psi0).sum() < 1e-6
+        ratio = s.mode_variances() / (p.rho0 * d["kT"] * 3.0 * b)
+        assert np.all(np.abs(ratio[10:] - 1) < 0.01), (st, ratio)
+        u2[st] = uu
+        del s
+    assert np.all(np.abs(u2[F.FLB_F16_DEV] / u2[F.FLB_F32_DEV] - 1) < 0.01), u2

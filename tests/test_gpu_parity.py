@@ -413,3 +413,23 @@ def test_nonfinite_is_reported():
     s.set_fields(psi=psi)
     _, _, rc = s.moments()
     assert rc == F.FLB_ENONFINITE
+
+
+def test_structure_factor_long_rows():
+    # the x pass of the windowed DFT keeps a whole row in registers (one warp
+    # per row) for windows of K_x <= 32 and rows up to 1024: rows of 512 as in
+    # the 512^3 workload, kmax = 8 as the bench samples, a seeded field at step
+    # 0, every value of the window against the oracle's FFT of the same field
+    d = dict(dim=3, q=19, nx=512, ny=48, nz=40, tau=0.8, kT=1e-4, A=0.1, B=0.0, K=0.04, M=0.2, scheme=1,
+             integrator=2, seed=4, sq_kmax=8)
+    s = F.Solver(flb_params(d))
+    N = 512 * 48 * 40
+    psi0 = I.uniform_field(N, -0.01, 0.01, 31)
+    s.set_fields(psi=psi0)
+    s.sample(1)
+    S_gpu, ns = s.structure_factor()
+    assert ns == 1 and S_gpu.size == 17 ** 3
+    full = O.structure_factor(oracle_params(d), psi0)
+    ks = lambda n: list(range(0, 9)) + list(range(n - 8, n))
+    ref = full[np.ix_(ks(40), ks(48), ks(512))]
+    assert np.allclose(S_gpu.reshape(17, 17, 17), ref, rtol=1e-4, atol=1e-6 * ref.max())

@@ -81,10 +81,10 @@ def _shell_check(S, th, n_ind, qg, tol, min_eff=1e4):
 
 def test_bulk_2d_structure_factor_and_equipartition():
     d = dict(I.WORKLOADS["bulk_2d"], integrator=2)
-    S, ns, u2, times = _measure(d, 20000, 2000, 10)
+    S, ns, u2, times = _measure(d, 80000, 2000, 10)
     th, n_ind, qg = _theory(d, times)
-    _shell_check(S.reshape(1, 64, 64), th, n_ind, qg, tol=0.03)
-    assert np.all(np.abs(u2 / d["kT"] - 1) < 0.02)
+    _shell_check(S.reshape(1, 64, 64), th, n_ind, qg, tol=0.02, min_eff=4e4)
+    assert np.all(np.abs(u2 / d["kT"] - 1) < 0.01), u2 / d["kT"]
 
 
 def test_bulk_3d_structure_factor_and_equipartition():
@@ -265,20 +265,20 @@ def test_galilean_invariance_high_mach_anisotropy():
 
 
 def test_fp16_storage_acceptance():
-    # FP16 deviations are accepted if equipartition and S(q) stay within the
-    # tolerances of the FP32 path: against theory, and shell by shell against an
-    # FP32 run of the same workload (bulk 3D parameters on 32^3)
-    d = dict(I.WORKLOADS["bulk_3d"], nx=32, ny=32, nz=32, integrator=2)
+    # FP16 deviations are accepted at the bars of the FP32 path: S(q) within 2% per
+    # |q| shell and <u_a^2> within 1%, against the lattice theory and against an
+    # FP32 run of the same workload and seed (the bulk 3D workload, 64^3)
+    d = dict(I.WORKLOADS["bulk_3d"], integrator=2)
     res = {}
     for st in (F.FLB_F32_DEV, F.FLB_F16_DEV):
-        S, ns, u2, times = _measure(d, 12000, 1000, 10, storage=st)
-        res[st] = (S.reshape(32, 32, 32), u2)
+        S, ns, u2, times = _measure(d, 10000, 1000, 10, storage=st)
+        res[st] = (S.reshape(64, 64, 64), u2)
     th, n_ind, qg = _theory(d, times)
     for st in res:
-        _shell_check(res[st][0], th, n_ind, qg, tol=0.03)
-        assert np.all(np.abs(res[st][1] / d["kT"] - 1) < 0.03)
-    _shell_check(res[F.FLB_F16_DEV][0], res[F.FLB_F32_DEV][0], n_ind, qg, tol=0.03)
-    assert np.all(np.abs(res[F.FLB_F16_DEV][1] / res[F.FLB_F32_DEV][1] - 1) < 0.03)
+        _shell_check(res[st][0], th, n_ind, qg, tol=0.02)
+        assert np.all(np.abs(res[st][1] / d["kT"] - 1) < 0.01), (st, res[st][1] / d["kT"])
+    _shell_check(res[F.FLB_F16_DEV][0], res[F.FLB_F32_DEV][0], n_ind, qg, tol=0.02)
+    assert np.all(np.abs(res[F.FLB_F16_DEV][1] / res[F.FLB_F32_DEV][1] - 1) < 0.01)
 
 
 @pytest.mark.parametrize("scheme,coupling", [(1, 0), (1, 3), (0, 3)])

@@ -502,3 +502,30 @@ def test_stress_force_conserves_momentum_in_coupled_run(scheme, amp):
     j1 = O.moments(p, s.f)[1].sum(axis=1)
     assert np.isfinite(s.psi).all()
     assert np.abs(j1 - j0).max() < 1e-13 * p.n
+
+
+def test_structure_factor_at_wavevectors():
+    # the definition |sum_r psi(r) e^{-iq.r}|^2 / N evaluated axis by axis at
+    # chosen wavevectors: a brute-force triple loop on a small field (every
+    # wavevector, negative and aliased ones included), the FFT grid of
+    # structure_factor, and the closed form of a plane wave (N/4 at +-k, zero
+    # elsewhere)
+    p = O.Params(dim=3, q=19, nx=6, ny=5, nz=4, tau=0.8, kT=0.0, A=0.1, B=0.0, K=0.04, M=0.1)
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal(p.n)
+    a = psi.reshape(p.shape)
+    ks = [(kx, ky, kz) for kz in range(-1, 4) for ky in range(5) for kx in (0, 1, 5, -2, 7)]
+    got = O.structure_factor_at(p, psi, ks)
+    full = O.structure_factor(p, psi)
+    for (kx, ky, kz), v in zip(ks, got):
+        acc = 0j
+        for z in range(4):
+            for y in range(5):
+                for x in range(6):
+                    acc += a[z, y, x] * np.exp(-2j * np.pi * (kx * x / 6 + ky * y / 5 + kz * z / 4))
+        assert abs(v - abs(acc) ** 2 / p.n) < 1e-12 * max(1.0, v)
+        assert abs(v - full[kz % 4, ky % 5, kx % 6]) < 1e-12 * max(1.0, v)
+    z, y, x = np.meshgrid(np.arange(4), np.arange(5), np.arange(6), indexing="ij")
+    wave = np.cos(2 * np.pi * (2 * x / 6 + 1 * y / 5 + 3 * z / 4)).ravel()
+    s = O.structure_factor_at(p, wave, [(2, 1, 3), (-2, -1, -3), (4, 4, 1), (1, 1, 3)])
+    assert np.allclose(s, [p.n / 4, p.n / 4, p.n / 4, 0.0], atol=1e-12)
