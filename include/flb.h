@@ -76,6 +76,9 @@ extern "C" {
 #define FLB_MODE_PLAIN 0       /* per-replica launch sequence */
 #define FLB_MODE_BATCHED 1     /* all replicas in one launch per phase, CUDA-graph replay */
 #define FLB_MODE_PERSISTENT 2  /* all replicas, n steps, one cooperative launch (FV, FP32 storage) */
+#define FLB_INIT_REST 0        /* flb_init leaves every replica at rest */
+#define FLB_INIT_EQUILIBRIUM 1 /* ... in the equilibrium of the Gaussian model (Sec. VI) */
+#define FLB_INIT_USER 2        /* ... at rest, for the caller to set (flb_set_fields, flb_set_state) */
 #define FLB_TUNE_FORCE 1       /* flb_autotune: time every candidate even if the cache has an entry */
 
 /*
@@ -151,6 +154,7 @@ typedef struct flb_params {
     int32_t force_grad;
     int32_t sq_lags;
     int32_t laplacian;
+    int32_t init;
 } flb_params;
 
 typedef struct flb_handle flb_handle;
@@ -158,7 +162,7 @@ typedef struct flb_handle flb_handle;
 /* Fill *p with the defaults: D3Q19 32^3, rho0 1, tau 0.8, gamma_bulk NaN,
  * gamma_ghost 0, kT 0, A 0.05, B 0, K 0.04, M 0.1, FV, Heun, FP32, coupling 3,
  * seed 1, sq_kmax 0, force_grad FLB_FORCE_MATCHED, sq_lags 0, laplacian
- * FLB_LAP_SO. */
+ * FLB_LAP_SO, init FLB_INIT_REST. */
 void flb_params_default(flb_params *p);
 
 /* Device workspace needed for nrep replicas p[0..nrep-1]; 0 if any parameter
@@ -168,8 +172,19 @@ size_t flb_workspace_bytes(const flb_params *p, int32_t nrep);
 
 /* Create a handle.  dev_ws: device pointer, 256-byte aligned, ws_bytes >=
  * flb_workspace_bytes(p, nrep), caller-owned.  cuda_stream: a cudaStream_t
- * (NULL = legacy default stream).  Every replica starts at rest (fbar = w rho0,
- * u = 0, psi = 0) at step 0.  Synchronising.  Errors: EINVAL, ENOSPC, ECUDA. */
+ * (NULL = legacy default stream).  Every replica starts at step 0 in the state
+ * its flb_params.init names:
+ *   FLB_INIT_REST, FLB_INIT_USER: at rest (fbar = w rho0, u = 0, psi = 0); USER
+ *     marks that the caller sets the fields next (flb_set_fields, flb_set_state).
+ *   FLB_INIT_EQUILIBRIUM: the equilibrium of the Gaussian model, as the paper's
+ *     runs start (Sec. VI).  Population deviations independent N(0, rho0 kT w_i /
+ *     c_s^2), the stationary law of the linearised fluctuating LB (Sec. III;
+ *     Philox stream 3, step 0, counter = site); psi Gaussian with S(q) =
+ *     kT/(A - K L(q)) on every q != 0 (Eq. test2; L the symbol of the chosen
+ *     Laplacian; B is not part of it) and zero mean, drawn mode by mode (Philox
+ *     stream 4, counter = the mode's FFT-order index) and summed on the device by
+ *     an inverse DFT; u the velocity of those populations.  Needs A > 0, K >= 0.
+ * Synchronising.  Errors: EINVAL, ENOSPC, ECUDA. */
 int flb_init(const flb_params *p, int32_t nrep, void *dev_ws, size_t ws_bytes, void *cuda_stream,
              flb_handle **out);
 

@@ -71,6 +71,8 @@ def lib():
         L.ora_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
         L.ora_gaussians.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_int32, dp]
+        L.ora_gaussians_sites.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64,
+                                          ctypes.c_uint32, ctypes.c_int32, dp]
         L.ora_lattice.argtypes = [ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), dp]
         L.ora_moment_basis.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp]
         L.ora_laplacian_so.argtypes = [ctypes.c_int32] * 4 + [dp, dp]
@@ -166,6 +168,13 @@ def gaussians(seed: int, step: int, site: int, stream: int, nblocks: int) -> np.
     g = np.zeros(4 * nblocks)
     lib().ora_gaussians(seed, step, site, stream, nblocks, _dp(g))
     return g
+
+
+def gaussians_sites(seed: int, step: int, site0: int, nsites: int, stream: int, nblocks: int) -> np.ndarray:
+    """The normals of `gaussians` for counter sites site0 .. site0 + nsites - 1, shape (nsites, 4 nblocks)."""
+    g = np.zeros(nsites * 4 * nblocks)
+    lib().ora_gaussians_sites(seed, step, site0, nsites, stream, nblocks, _dp(g))
+    return g.reshape(nsites, 4 * nblocks)
 
 
 def lattice(dim: int, q: int):
@@ -283,6 +292,47 @@ class State:
         if u is not None:
             uu[:] = np.asarray(u, dtype=np.float64).reshape(3, -1)
         return cls(p, f, ps, uu, 0)
+
+    @classmethod
+    def equilibrium(cls, p: Params) -> "State":
+        """The equilibrium start of the Gaussian model (Sec. VI's runs start from
+        equilibrium; B is not part of it).
+        Fluid: the stationary law of the linearised fluctuating LB is independent
+        normal population deviations of variance mu_n w_i, mu_n = rho0 kT / c_s^2
+        (Sec. III); the stored post-collision deviation of population i at site s
+        is sqrt(mu_n w_i) g_i(s), with g_0..g_{q-1} the normals of Philox stream 3,
+        step 0, counter site s; after streaming f_i(r) = w_i rho0 + that value at
+        r - c_i.
+        Order parameter: the Gibbs law of the Gaussian free energy A/2 psi^2 +
+        K/2 |grad psi|^2 on the lattice gives S(q) = kT/(A - K L(q)) with L the
+        symbol of the Laplacian in mu (Eq. test2).  psi = Re W with W(r) = sum_q
+        X(q) e^{iq.r}, X(q) = sqrt(S(q)/N) (a + i b) for q != 0 and X(0) = 0
+        (the conserved mean), (a, b) the first two normals of Philox stream 4,
+        step 0, counter = the mode's index kx + nx (ky + ny kz) in FFT order; then
+        <|psi~(q)|^2> = N S(q) on every q != 0.
+        u: the velocity sum fbar c / rho of those populations."""
+        from . import theory as T
+        c, w = lattice(p.dim, p.q)
+        shape = p.shape
+        nb = (p.q + 3) // 4
+        G = gaussians_sites(p.seed, 0, 0, p.n, 3, nb)[:, :p.q].T          # (q, N)
+        dev = np.sqrt(p.rho0 * p.kT * 3.0 * w)[:, None] * G
+        f = np.empty((p.q, p.n))
+        for i in range(p.q):
+            d = dev[i].reshape(shape)
+            f[i] = w[i] * p.rho0 + np.roll(d, shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2)).reshape(-1)
+        qg = T.q_grid(shape)
+        if p.dim == 2:
+            qg[..., 2] = 0.0
+        L = T.L_kind(qg, p.dim, p.laplacian)
+        S = p.kT / (p.A - p.K * L)
+        Gq = gaussians_sites(p.seed, 0, 0, p.n, 4, 1)
+        X = np.sqrt(S / p.n) * (Gq[:, 0] + 1j * Gq[:, 1]).reshape(shape)
+        X[0, 0, 0] = 0.0
+        psi = np.real(np.fft.ifftn(X) * p.n).reshape(-1)
+        rho, j, _ = moments(p, f)
+        u = j / rho[None, :]
+        return cls(p, f, psi, u, 0)
 
     def advance(self, nsteps: int) -> "State":
         cp = self.p.c()

@@ -95,6 +95,15 @@ void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream,
     }
 }
 
+/* The normals of ora_gaussians for nsites consecutive counter sites
+ * site0 .. site0 + nsites - 1: g[s * 4 nblocks + k]. */
+void ora_gaussians_sites(uint64_t seed, int64_t step, uint32_t site0, int64_t nsites, uint32_t stream,
+                         int32_t nblocks, double *g)
+{
+    for (int64_t s = 0; s < nsites; ++s)
+        ora_gaussians(seed, step, site0 + (uint32_t)s, stream, nblocks, g + (size_t)s * 4 * (size_t)nblocks);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Velocity sets and weights (Sec. IV; D3Q15 is the paper's own, Sec. VI).    */
 /* Plane order: rest first, then opposite pairs (i, i+1).                     */

@@ -38,6 +38,8 @@ typedef struct {
 int ora_threads(void);
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream, int32_t nblocks, double *g);
+void ora_gaussians_sites(uint64_t seed, int64_t step, uint32_t site0, int64_t nsites, uint32_t stream,
+                         int32_t nblocks, double *g);
 int ora_lattice(int32_t dim, int32_t q, int32_t *c, double *w);
 int ora_moment_basis(int32_t dim, int32_t q, double *E, double *b);
 void ora_laplacian_so(int32_t dim, int32_t nx, int32_t ny, int32_t nz, const double *in, double *out);

@@ -31,6 +31,7 @@ FLB_FORCE_MATCHED, FLB_FORCE_CD, FLB_FORCE_FV, FLB_FORCE_STRESS = 0, 1, 2, 3
 FLB_SQ_PSI, FLB_SQ_HEIGHT, FLB_SQ_DYNAMIC = 0, 1, 2
 FLB_MODE_PLAIN, FLB_MODE_BATCHED, FLB_MODE_PERSISTENT = 0, 1, 2
 FLB_TUNE_FORCE = 1
+FLB_INIT_REST, FLB_INIT_EQUILIBRIUM, FLB_INIT_USER = 0, 1, 2
 
 
 class FlbParams(ctypes.Structure):
@@ -47,6 +48,7 @@ class FlbParams(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("sq_kmax", ctypes.c_int32), ("force_grad", ctypes.c_int32),
         ("sq_lags", ctypes.c_int32), ("laplacian", ctypes.c_int32),
+        ("init", ctypes.c_int32),
     ]
 
 

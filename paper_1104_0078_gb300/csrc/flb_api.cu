@@ -118,6 +118,9 @@ bool valid(const flb_params &p)
     if (p.force_grad == FLB_FORCE_STRESS && p.laplacian != FLB_LAP_SO) return false;
     const long long nz = p.dim == 3 ? p.nz : 1;
     if (p.nx < 4 || p.ny < 4 || (p.dim == 3 && p.nz < 4)) return false;
+    if (p.init < FLB_INIT_REST || p.init > FLB_INIT_USER) return false;
+    // the equilibrium start draws psi from the Gaussian law kT/(A - K L(q))
+    if (p.init == FLB_INIT_EQUILIBRIUM && !(p.A > 0 && p.K >= 0 && p.kT >= 0)) return false;
     if ((long long)p.nx * p.ny * nz >= (1LL << 31)) return false;
     if ((long long)(p.nx + 2 * GX + 3) * (p.ny + 2 * GY) * (nz + (p.dim == 3 ? 2 * GZ3 : 0)) >= (1LL << 31)) return false;
     if (!(p.rho0 > 0) || !(p.tau > 0) || !std::isfinite(p.tau) || !std::isfinite(p.rho0)) return false;
@@ -1060,6 +1063,7 @@ void flb_params_default(flb_params *p)
     p->seed = 1;
     p->sq_kmax = 0;
     p->force_grad = FLB_FORCE_MATCHED;
+    p->init = FLB_INIT_REST;
 }
 
 static bool valid_set(const flb_params *p, int32_t nrep)
@@ -1101,8 +1105,24 @@ int flb_init(const flb_params *p, int32_t nrep, void *dev_ws, size_t ws_bytes, v
     h->ws_bytes = ws_bytes;
     h->st = (cudaStream_t)cuda_stream;
     carve_all(*h, (char *)dev_ws);
-    // zero the whole workspace, then every replica starts at rest
+    // zero the whole workspace: every replica at rest; then the equilibrium starts
     int rc = cuerr(cudaMemsetAsync(dev_ws, 0, need, h->st));
+    for (Rep &r : h->reps) {
+        if (rc != FLB_OK || r.p.init != FLB_INIT_EQUILIBRIUM) continue;
+        const flb_params &p = r.p;
+        float *psi = r.psi[r.pcur];
+        rc = cuerr(launch_equilibrium_start(r.g, r.q, p.storage, lap_weights(r.dim, p.laplacian), p.rho0, p.kT, p.A,
+                                            p.K, p.seed, r.f[r.cur], r.f[r.cur ^ 1], psi, h->st));
+        if (rc != FLB_OK) break;
+        // u: the velocity of the drawn populations (they sit where a step leaves them)
+        LBArgs la = lb_args(r, psi);
+        la.fout = r.f[r.cur];
+        la.coupling = 0;
+        rc = cuerr(r.dim == 2 ? launch_vel2(la, p.storage, h->st)
+                              : r.q == 15 ? launch_vel15(la, p.storage, h->st) : launch_vel3(la, p.storage, h->st));
+        if (rc == FLB_OK)
+            rc = cuerr(cudaMemsetAsync(r.f[r.cur ^ 1], 0, (size_t)r.q * (size_t)r.g.n * (size_t)r.pop_elem, h->st));
+    }
     if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
     if (rc != FLB_OK) {
         delete h;

@@ -579,6 +579,12 @@ cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, 
                            cudaStream_t st);
 cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, const LapW &lw,
                       cudaStream_t s);
+// equilibrium start (flb_init.cu): populations into f (the current buffer), psi
+// (padded) through an inverse DFT whose intermediates use `spare` (>= 16 bytes
+// per site: the other population buffer)
+cudaError_t launch_equilibrium_start(const Geom &g, int q, int storage, const LapW &lw, double rho0, double kT,
+                                     double A, double K, uint64_t seed, void *f, void *spare, float *psi,
+                                     cudaStream_t st);
 cudaError_t launch_noise(const NoiseArgs &a, cudaStream_t s);
 cudaError_t launch_flux(const Geom &g, int q, const float *psi, const float *mu, const float *u, float *J, float M,
                         int coupling, cudaStream_t s);

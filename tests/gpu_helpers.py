@@ -27,6 +27,7 @@ def flb_params(d: dict, **kw) -> F.FlbParams:
     p.sq_kmax = d.get("sq_kmax", 0)
     p.sq_lags = d.get("sq_lags", 0)
     p.force_grad = d.get("force_grad", 0)
+    p.init = d.get("init", 0)
     return p
 
 

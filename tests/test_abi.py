@@ -129,3 +129,16 @@ def test_init_argument_checks_without_device(lib):
     assert lib.flb_init(arr, 1, ctypes.c_void_p(0x100000), 16, None, ctypes.byref(h)) == F.FLB_ENOSPC
     assert lib.flb_step(None, 1) == F.FLB_EINVAL
     assert F.flb_strerror(F.FLB_ENONFINITE).startswith("non-finite")
+
+
+def test_init_field_defaults_and_validation(lib):
+    # flb_params.init: REST by default; EQUILIBRIUM needs the Gaussian free energy
+    # to be stable (A > 0, K >= 0), checked before any device work
+    p = F.flb_params_default(nx=8, ny=8, nz=8)
+    assert p.init == F.FLB_INIT_REST
+    assert F.flb_workspace_bytes(p) > 0
+    for init, A, ok in [(F.FLB_INIT_EQUILIBRIUM, 0.05, True), (F.FLB_INIT_EQUILIBRIUM, -0.0625, False),
+                        (F.FLB_INIT_EQUILIBRIUM, 0.0, False), (F.FLB_INIT_USER, -0.0625, True), (3, 0.05, False),
+                        (-1, 0.05, False)]:
+        q = F.flb_params_default(nx=8, ny=8, nz=8, A=A, init=init)
+        assert (F.flb_workspace_bytes(q) > 0) == ok, (init, A)
