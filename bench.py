@@ -290,18 +290,23 @@ def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
         (f"pk_laplacian_fd_{n}", dict(cube, psi_scheme=F.FLB_FD, laplacian=F.FLB_LAP_PK), 160),
         (f"naive_cd_{n}", dict(cube, psi_scheme=F.FLB_NAIVE, laplacian=F.FLB_LAP_CD), 160),
         (f"d3q15_fv_{n}", dict(cube, q=15, psi_scheme=F.FLB_FV), 128),
+        (f"heun_fused_{n}", dict(cube, psi_scheme=F.FLB_FV), 160, None, True),
         (f"d2q9_{8 * n}", dict(dim=2, q=9, nx=8 * n, ny=8 * n, nz=1, psi_scheme=F.FLB_FD), 80),
     ]
     if only:
         forms = [f for f in forms if f[0].rsplit("_", 1)[0] in only]
     out = {}
-    for key, kw, alg, *sampling in forms:
+    for key, kw, alg, *extra in forms:
+        sampling = extra[:1] if extra and extra[0] is not None else []
+        fused = len(extra) > 1 and extra[1]
         kw = {"integrator": F.FLB_HEUN, **kw}
         p = F.flb_params_default(tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"], K=d["K"], M=d["M"],
                                  seed=d["seed"], **kw)
         N = p.nx * p.ny * p.nz
         s = F.Solver(p, device=f"cuda:{local}")
         s.set_fields(psi=I.uniform_field(N, -0.01, 0.01, 11))
+        if fused:   # both Heun stages of psi in one launch (halo recompute); tuned as such
+            s.set_psi_fused(True)
         if p.dim == 3 and autotune:
             s.autotune()
         if sampling:

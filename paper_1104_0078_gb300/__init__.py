@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "flb_set_mode": (c_int, [H, ctypes.c_int32]),
         "flb_get_tuning": (c_int, [H, ctypes.c_int32, P(ctypes.c_int32)]),
         "flb_set_tuning": (c_int, [H, ctypes.c_int32, ctypes.c_int32]),
+        "flb_set_psi_fused": (c_int, [H, ctypes.c_int32]),
         "flb_autotune": (c_int, [H, ctypes.c_char_p, ctypes.c_int32]),
         "flb_set_wait_limit": (c_int, [H, ctypes.c_double]),
         "flb_state_bytes": (c_sz, [H, ctypes.c_int32]),
@@ -294,6 +295,10 @@ class Solver:
 
     def set_tuning(self, psi_zchunk: int, rep: int = -1):
         _check(self.lib.flb_set_tuning(self.h, rep, int(psi_zchunk)), "flb_set_tuning")
+
+    def set_psi_fused(self, on=True):
+        """Single-pass Heun psi step (flb_set_psi_fused)."""
+        _check(self.lib.flb_set_psi_fused(self.h, 1 if on else 0), "flb_set_psi_fused")
 
     def autotune(self, cache=None, force=False):
         """Time the psi z-chunk candidates on this handle (see flb_autotune); returns

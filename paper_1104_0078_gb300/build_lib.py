@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libflb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["flb_api.cu", "flb_lb.cu", "flb_psi.cu", "flb_obs.cu", "flb_noalloc.cu", "flb_lb3d.cu", "flb_aux3d.cu", "flb_psi3d.cu", "flb_persist.cu", "flb_lb15.cu", "flb_init.cu"]
+SOURCES = ["flb_api.cu", "flb_lb.cu", "flb_psi.cu", "flb_obs.cu", "flb_noalloc.cu", "flb_lb3d.cu", "flb_aux3d.cu", "flb_psi3d.cu", "flb_persist.cu", "flb_lb15.cu", "flb_init.cu", "flb_heun1.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

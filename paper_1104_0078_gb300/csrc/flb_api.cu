@@ -93,6 +93,7 @@ struct Rep {
     float omega_s = 0, omega_b = 0, gamma_g = 0;
     float namp[16] = {0};
     int zc = PS_ZC;  // planes per psi block (3D), set by flb_set_tuning / flb_autotune
+    int fused = 0;   // single-pass Heun psi step (flb_set_psi_fused)
 };
 
 struct Carver {
@@ -523,6 +524,11 @@ int launch_psi_stages(flb_handle *h, Rep &r)
             FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, s == 0 ? 1 : 2, s == 0 && noisy, in[s], r.u, out[s], r.E,
                                 (float)p.A, (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, 0, key, r.step,
                                 r.zc, s + 1, psi_n, r.Dn, s == 0 ? mu_n : nullptr, h->status, st));
+        return FLB_OK;
+    }
+    if (r.fused && heun) {  // both stages in one launch (flb_set_psi_fused)
+        FLB_TRY(launch_psi3_heun1(r.g, psi_n, r.u, psi_np1, (float)p.A, (float)p.B, (float)p.K, (float)p.M,
+                                  (float)p.kT, advect, noisy, key, r.step, r.zc, st));
         return FLB_OK;
     }
     FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
@@ -1664,6 +1670,23 @@ int flb_set_mode(flb_handle *h, int32_t mode)
 {
     if (!h || (mode != FLB_MODE_PLAIN && mode != FLB_MODE_BATCHED && mode != FLB_MODE_PERSISTENT)) return FLB_EINVAL;
     h->mode = mode;
+    for (Rep &r : h->reps) r.fused = 0;
+    return FLB_OK;
+}
+
+int flb_set_psi_fused(flb_handle *h, int32_t on)
+{
+    if (!h) return FLB_EINVAL;
+    if (on) {
+        if (h->mode != FLB_MODE_PLAIN) return FLB_EUNSUPPORTED;
+        for (const Rep &r : h->reps) {
+            const flb_params &p = r.p;
+            if (r.dim != 3 || r.q != 19 || p.psi_scheme != FLB_FV || p.integrator != FLB_HEUN ||
+                p.laplacian != FLB_LAP_SO)
+                return FLB_EUNSUPPORTED;
+        }
+    }
+    for (Rep &r : h->reps) r.fused = on ? 1 : 0;
     return FLB_OK;
 }
 
