@@ -108,6 +108,36 @@ def oracle_mlups(d: dict, box: int, budget_s: float, nsteps=None):
     return p.n * n / dt / 1e6, n, dt, O.threads()
 
 
+def cpu_baselines(d: dict) -> dict:
+    """The FP64 checker on the host cores, bounded to about half a minute: on all
+    cores and on one thread, on samples of the quench workload (64^3 and 32^3
+    boxes, same parameters), and the 2D bulk workload (D2Q9 64^2, FD, Heun) as a
+    full 2000-step run on all cores."""
+    import oracle as O
+    from paper_1104_0078_gb300 import inputs as I
+    mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)
+    out = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{n} coupled steps of a 64^3 box with the workload's parameters, FP64, all host cores",
+           "build": "gcc -O3 -fopenmp -ffp-contract=off (no -march=native: host code builds alike on both machines)"}
+    O.set_threads(1)
+    try:
+        m1, n1, _, _ = oracle_mlups(d, 32, 8.0)
+    finally:
+        O.set_threads(cores)
+    out["single_thread"] = {"value": m1, "unit": "MLUPS", "cores": 1,
+                            "sample": f"{n1} coupled steps of a 32^3 box with the workload's parameters"}
+    b = dict(I.WORKLOADS["bulk_2d"])
+    p = O.Params(dim=2, q=9, nx=b["nx"], ny=b["ny"], nz=1, tau=b["tau"], kT=b["kT"], A=b["A"], B=b["B"], K=b["K"],
+                 M=b["M"], scheme=0, integrator=2, coupling=3, seed=1)
+    st = O.State.rest(p)
+    t0 = time.perf_counter()
+    st.advance(2000)
+    dt2 = time.perf_counter() - t0
+    out["bulk_2d_full_run"] = {"value": p.n * 2000 / dt2 / 1e6, "unit": "MLUPS", "cores": cores,
+                               "sample": "D2Q9 64^2, FD, Heun, 2000 steps (the whole run)", "seconds": dt2}
+    return out
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -178,7 +208,7 @@ def measured_sm_max_mhz() -> float:
         return 2070.0
 
 
-LB_SOURCES = ("flb_lb3d.cu", "flb_site3d.cuh", "flb_internal.cuh")
+LB_SOURCES = ("flb_lb3d.cu", "flb_site3d.cuh", "flb_internal.cuh", "flb_lane.cuh")
 
 
 def lb_source_sha():
@@ -419,7 +449,8 @@ def run_ours(args):
     sm_max = (clocks or {}).get("sm_max_mhz") or measured_sm_max_mhz()
     issue = lb_issue_roofline(storage, N, lb_ms, torch.cuda.get_device_properties(local).multi_processor_count, sm_max)
 
-    # end to end through the public API: upload the initial field, step, read totals
+    # end to end through the public API: upload the initial field, step, read the
+    # totals and the final psi field back
     e2e = None
     if not args.no_e2e:
         s2 = s  # reuse the handle and workspace; set_fields re-initialises the state
@@ -428,11 +459,14 @@ def run_ours(args):
         s2.set_fields(psi=psi0)
         s2.step(args.steps)
         tot, u2, rc = s2.moments()
+        psi_end = s2.get_psi()
         t1 = time.perf_counter()
+        assert psi_end.shape == (N,)
         e2e_ms = max_over_ranks((t1 - t0) * 1e3, dist, f"cuda:{local}")
         h2d = 4 * N  # psi0 as interior FP32 values (padded on the device; u0 = 0 is a device memset)
+        d2h = 72 + 4 * N  # the totals, and psi as interior FP32 values (gathered on the device)
         e2e = {"value": job_value(N, args.steps, ws, e2e_ms), "unit": "MLUPS",
-               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 72 / args.steps}
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
     ens = None
     if args.ensemble_steps > 0:
         del s
@@ -445,9 +479,7 @@ def run_ours(args):
                                  autotune=not args.no_autotune)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        mlups, n, dt, cores = oracle_mlups(d, 64, 15.0)
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{n} coupled steps of a 64^3 box with the workload's parameters, FP64"}
+        cpu = cpu_baselines(d)
     if rank == 0:
         line = {
             "metric": "coupled lattice-site updates/s", "value": value, "unit": "MLUPS", "n_gpus": ws,

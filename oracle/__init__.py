@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
                                                    os.path.getmtime(os.path.join(_HERE, "flb_oracle.h")))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O3", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
            "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
@@ -68,6 +68,7 @@ def lib():
         P = ctypes.POINTER
         dp = P(ctypes.c_double)
         L.ora_threads.restype = ctypes.c_int
+        L.ora_set_threads.argtypes = [ctypes.c_int32]
         L.ora_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
         L.ora_gaussians.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32,
                                     ctypes.c_int32, dp]
@@ -154,6 +155,11 @@ class Params:
 def threads() -> int:
     """OpenMP threads the oracle's site loops use."""
     return int(lib().ora_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads the oracle's site loops use from now on."""
+    lib().ora_set_threads(int(n))
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

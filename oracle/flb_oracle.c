@@ -42,6 +42,16 @@ int ora_threads(void)
 #endif
 }
 
+/* Threads of the site loops from now on (n >= 1). */
+void ora_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   */
 /* easy as 1, 2, 3", SC'11): ten rounds of a multiply-hi/lo bijection with a  */

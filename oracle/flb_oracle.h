@@ -36,6 +36,7 @@ typedef struct {
 } ora_params;
 
 int ora_threads(void);
+void ora_set_threads(int32_t n);
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream, int32_t nblocks, double *g);
 void ora_gaussians_sites(uint64_t seed, int64_t step, uint32_t site0, int64_t nsites, uint32_t stream,

@@ -245,6 +245,12 @@ class Solver:
         _check(self.lib.flb_get_psi_u(self.h, rep, _dp(psi), _dp(u)), "flb_get_psi_u")
         return psi, u
 
+    def get_psi(self, rep=0):
+        """psi [N] alone (flb_get_psi_u with no velocity)."""
+        psi = np.zeros(self.n(rep))
+        _check(self.lib.flb_get_psi_u(self.h, rep, _dp(psi), None), "flb_get_psi_u")
+        return psi
+
     def get_window(self, origin, size, rep=0):
         W = size[0] * size[1] * size[2]
         f = np.zeros((self.params[rep].q, W))

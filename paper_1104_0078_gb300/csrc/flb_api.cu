@@ -36,6 +36,7 @@ struct Range {
 namespace flb {
 // flb_lb.cu: padded plane (ghost frame of periodic images) from an interior field
 cudaError_t launch_pad(const Geom &g, const float *interior, float *padded, cudaStream_t st);
+cudaError_t launch_unpad(const Geom &g, const float *padded, float *interior, cudaStream_t st);
 }  // namespace flb
 
 namespace {
@@ -1222,23 +1223,49 @@ int flb_set_populations(flb_handle *h, int32_t rep, const double *f)
     return rc == FLB_OK ? cuerr(cudaStreamSynchronize(h->st)) : rc;
 }
 
+// dst[s] = src[s] (FP32 to FP64), split over the host's cores for large fields
+static void to_double(const float *src, double *dst, long long n)
+{
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const long long nt = n < (1 << 20) ? 1 : std::min<long long>(hw, 32);
+    auto part = [&](long long t) {
+        const long long a = n * t / nt, b = n * (t + 1) / nt;
+        for (long long s = a; s < b; ++s) dst[s] = (double)src[s];
+    };
+    if (nt == 1) {
+        part(0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (long long t = 1; t < nt; ++t) pool.emplace_back(part, t);
+    part(0);
+    for (auto &th : pool) th.join();
+}
+
+// psi and u: the interiors are gathered on the device into the spare population
+// buffer (scratch between steps, >= 18 bytes per site), copied as N floats per
+// field and converted on the host's cores
 int flb_get_psi_u(flb_handle *h, int32_t rep, double *psi, double *u)
 {
     Rep *r = get_rep(h, rep);
     if (!r) return FLB_EINVAL;
     const Geom &g = r->g;
-    std::vector<float> tmp;
-    if (psi) {
-        const int rc = download_interior(h, g, r->psi[r->pcur], tmp);
-        if (rc != FLB_OK) return rc;
-        for (long long s = 0; s < g.n; ++s) psi[s] = tmp[(size_t)s];
-    }
+    if (!psi && !u) return FLB_OK;
+    float *scratch = (float *)r->f[r->cur ^ 1];
+    const int nf = (psi ? 1 : 0) + (u ? r->dim : 0);
+    int k = 0, rc = FLB_OK;
+    if (psi) rc = cuerr(launch_unpad(g, r->psi[r->pcur], scratch + (size_t)g.n * k++, h->st));
     if (u)
-        for (int a = 0; a < r->dim; ++a) {
-            const int rc = download_interior(h, g, r->u + (size_t)a * g.pn, tmp);
-            if (rc != FLB_OK) return rc;
-            for (long long s = 0; s < g.n; ++s) u[a * g.n + s] = tmp[(size_t)s];
-        }
+        for (int a = 0; a < r->dim && rc == FLB_OK; ++a)
+            rc = cuerr(launch_unpad(g, r->u + (size_t)a * g.pn, scratch + (size_t)g.n * k++, h->st));
+    if (rc != FLB_OK) return rc;
+    std::vector<float> tmp((size_t)g.n * nf);
+    rc = cuerr(cudaMemcpyAsync(tmp.data(), scratch, tmp.size() * 4, cudaMemcpyDeviceToHost, h->st));
+    if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
+    if (rc != FLB_OK) return rc;
+    k = 0;
+    if (psi) to_double(tmp.data() + (size_t)g.n * k++, psi, g.n);
+    if (u) to_double(tmp.data() + (size_t)g.n * k, u, (long long)r->dim * g.n);
     return FLB_OK;
 }
 

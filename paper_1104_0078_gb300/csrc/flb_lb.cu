@@ -260,6 +260,21 @@ __global__ void pad_kernel(const Geom g, const float *__restrict__ in, float *__
     out[i] = in[x + (long long)g.nx * (y + (long long)g.ny * z)];
 }
 
+// the interior of a padded field, site-major (the inverse of pad_kernel's copy)
+__global__ void unpad_kernel(const Geom g, const float *__restrict__ padded, float *__restrict__ out)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    out[s] = padded[g.pidx(x, y, z)];
+}
+
+cudaError_t launch_unpad(const Geom &g, const float *padded, float *interior, cudaStream_t st)
+{
+    unpad_kernel<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(g, padded, interior);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pad(const Geom &g, const float *interior, float *padded, cudaStream_t st)
 {
     pad_kernel<<<(unsigned)((g.pn + 255) / 256), 256, 0, st>>>(g, interior, padded);
