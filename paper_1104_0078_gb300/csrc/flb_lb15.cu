@@ -1,5 +1,6 @@
-// flb_lb15.cu -- D3Q15 fused collide-stream and the velocity of the new fluid
-// state, one thread per site (the lattice of the paper's own runs, Sec. VI).
+// flb_lb15.cu -- D3Q15 fused collide-stream (two sites per thread in packed
+// FP32) and the velocity of the new fluid state (one thread per site), the
+// lattice of the paper's own runs (Sec. VI).
 //
 // Plane order: 0 rest; pairs (1,2) +-x, (3,4) +-y, (5,6) +-z, (7,8) +-(1,1,1),
 // (9,10) +-(1,1,-1), (11,12) +-(1,-1,1), (13,14) +-(1,-1,-1).  Weights 2/9,
@@ -66,53 +67,88 @@ __device__ __forceinline__ void moments15(const float f[15], float sp[8], float 
     jz = dp[3] + ((dp[4] - dp[5]) + (dp[6] - dp[7]));
 }
 
+// The collide-stream of the D3Q15 sites (x, y, zl[l]) of the lanes of V (the
+// first nl stored; a lane past the box repeats lane 0's site and is dropped).
+// The second moment is carried as Q = 9/2 B, with the relaxation coefficients
+// a.rq of the D3Q19 kernel (they do not depend on the lattice); the ghost
+// amplitudes g_k stay in the units above.
 // P: the planes it pulls from (P.in) and stores to (P.out).
-template <typename T, bool GHOST_RELAX, class PL>
-__device__ __forceinline__ void lb15_site(const LBArgs &a, const PL &P, int x, int y, int z, float Fx, float Fy,
-                                          float Fz)
+template <class V, typename T, bool GHOST_RELAX, class PL>
+__device__ __forceinline__ void lb15_sites(const LBArgs &a, const PL &P, int x, int y, const int *zl, int nl, V Fx,
+                                           V Fy, V Fz)
 {
+    constexpr int L = V::L;
     const Geom &g = a.g;
-    const int s = x + g.nx * (y + g.ny * z);
+    int s[L];
+    V f[15];
+    {
+        float fl[L][15];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            s[l] = x + g.nx * (y + g.ny * zl[l]);
+            pull15<T>(P, g, x, y, zl[l], fl[l]);
+        }
+#pragma unroll
+        for (int i = 0; i < 15; ++i) {
+            float t[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) t[l] = fl[l][i];
+            f[i] = vmake<V>(t);
+        }
+    }
+    V sp[8], dp[8];
+#pragma unroll
+    for (int p = 1; p <= 7; ++p) {
+        sp[p] = f[2 * p - 1] + f[2 * p];
+        dp[p] = f[2 * p - 1] - f[2 * p];
+    }
+    const V C = (sp[4] + sp[5]) + (sp[6] + sp[7]);
+    const V drho = f[0] + ((sp[1] + sp[2] + sp[3]) + C);
+    const V jx = dp[1] + ((dp[4] + dp[5]) + (dp[6] + dp[7]));
+    const V jy = dp[2] + ((dp[4] + dp[5]) - (dp[6] + dp[7]));
+    const V jz = dp[3] + ((dp[4] - dp[5]) + (dp[6] - dp[7]));
+    const V third = drho * (1.0f / 3.0f);
+    const V Sxx = sp[1] + C - third, Syy = sp[2] + C - third, Szz = sp[3] + C - third;
+    const V Sxy = (sp[4] + sp[5]) - (sp[6] + sp[7]);
+    const V Sxz = (sp[4] - sp[5]) + (sp[6] - sp[7]);
+    const V Syz = (sp[4] - sp[5]) - (sp[6] - sp[7]);
 
-    float f[15];
-    pull15<T>(P, g, x, y, z, f);
-    float sp[8], dp[8], drho, jx, jy, jz;
-    moments15(f, sp, dp, drho, jx, jy, jz);
-    const float C = (sp[4] + sp[5]) + (sp[6] + sp[7]);
-    const float third = drho * (1.0f / 3.0f);
-    const float Sxx = sp[1] + C - third, Syy = sp[2] + C - third, Szz = sp[3] + C - third;
-    const float Sxy = (sp[4] + sp[5]) - (sp[6] + sp[7]);
-    const float Sxz = (sp[4] - sp[5]) + (sp[6] - sp[7]);
-    const float Syz = (sp[4] - sp[5]) - (sp[6] - sp[7]);
+    const V rho = drho + a.rho0;
+    float ir[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) ir[l] = __fdividef(1.0f, rho.lane(l));
+    const V irho = vmake<V>(ir);
+    const V vx = vfma(Fx, 0.5f, jx) * irho, vy = vfma(Fy, 0.5f, jy) * irho, vz = vfma(Fz, 0.5f, jz) * irho;
 
-    const float rho = a.rho0 + drho;
-    const float irho = __fdividef(1.0f, rho);
-    const float vx = (jx + 0.5f * Fx) * irho, vy = (jy + 0.5f * Fy) * irho, vz = (jz + 0.5f * Fz) * irho;
-
-    const float ws = a.omega_s, wb = a.omega_b;
-    const float cs = 1.0f - 0.5f * ws, cb = 1.0f - 0.5f * wb;
-    const float Xxx = rho * vx * vx - Sxx, Xyy = rho * vy * vy - Syy, Xzz = rho * vz * vz - Szz;
-    const float trX3 = (Xxx + Xyy + Xzz) * (1.0f / 3.0f);
-    const float Txx = 2.f * vx * Fx, Tyy = 2.f * vy * Fy, Tzz = 2.f * vz * Fz;
-    const float trT3 = (Txx + Tyy + Tzz) * (1.0f / 3.0f);
-    const float isoB = (wb - ws) * trX3 + (cb - cs) * trT3;
-    float Bxx = Sxx + ws * Xxx + cs * Txx + isoB;
-    float Byy = Syy + ws * Xyy + cs * Tyy + isoB;
-    float Bzz = Szz + ws * Xzz + cs * Tzz + isoB;
-    float Bxy = Sxy + ws * (rho * vx * vy - Sxy) + cs * (vx * Fy + Fx * vy);
-    float Bxz = Sxz + ws * (rho * vx * vz - Sxz) + cs * (vx * Fz + Fx * vz);
-    float Byz = Syz + ws * (rho * vy * vz - Syz) + cs * (vy * Fz + Fy * vz);
-    const float Ax = jx + Fx, Ay = jy + Fy, Az = jz + Fz;
+    // Q = 4.5 [(1 - ws) S + ws rho v v + cs (v F + F v)] + the bulk correction
+    const V cFx = Fx * a.rq[2], cFy = Fy * a.rq[2], cFz = Fz * a.rq[2];
+    const V wr = rho * a.rq[1];
+    const V hx = vfma(wr, vx, cFx), hy = vfma(wr, vy, cFy), hz = vfma(wr, vz, cFz);
+    V Qxx = vfma(Sxx, a.rq[0], vx * (hx + cFx));
+    V Qyy = vfma(Syy, a.rq[0], vy * (hy + cFy));
+    V Qzz = vfma(Szz, a.rq[0], vz * (hz + cFz));
+    if (a.iso) {
+        const V P2 = vfma(vz, vz, vfma(vy, vy, vx * vx));
+        const V vF = vfma(vz, Fz, vfma(vy, Fy, vx * Fx));
+        const V trS = Sxx + Syy + Szz;
+        const V isoq = vfma(vfma(rho, P2, trS * -1.0f), a.rq[3], vF * a.rq[4]);
+        Qxx = Qxx + isoq;
+        Qyy = Qyy + isoq;
+        Qzz = Qzz + isoq;
+    }
+    V Qxy = vfma(Sxy, a.rq[0], vfma(vy, hx, vx * cFy));
+    V Qxz = vfma(Sxz, a.rq[0], vfma(vz, hx, vx * cFz));
+    V Qyz = vfma(Syz, a.rq[0], vfma(vz, hy, vy * cFz));
 
     // ghost amplitudes g_k (already divided by b_k)
-    float gx = 0.f, gy = 0.f, gz = 0.f, gq = 0.f, g4 = 0.f;
+    V gx = V::bc(0.f), gy = V::bc(0.f), gz = V::bc(0.f), gq = V::bc(0.f), g4 = V::bc(0.f);
     if (GHOST_RELAX) {
-        const float gg = a.gamma_g;
-        const float mx = (4.f / 3.f) * ((dp[4] + dp[5]) + (dp[6] + dp[7])) - (2.f / 3.f) * dp[1];
-        const float my = (4.f / 3.f) * ((dp[4] + dp[5]) - (dp[6] + dp[7])) - (2.f / 3.f) * dp[2];
-        const float mz = (4.f / 3.f) * ((dp[4] - dp[5]) + (dp[6] - dp[7])) - (2.f / 3.f) * dp[3];
-        const float mq = (dp[4] - dp[5]) - (dp[6] - dp[7]);
-        const float m4 = (4.f / 3.f) * (f[0] + C) - (2.f / 3.f) * (sp[1] + sp[2] + sp[3]);
+        const V gg = V::bc(a.gamma_g);
+        const V mx = ((dp[4] + dp[5]) + (dp[6] + dp[7])) * (4.f / 3.f) - dp[1] * (2.f / 3.f);
+        const V my = ((dp[4] + dp[5]) - (dp[6] + dp[7])) * (4.f / 3.f) - dp[2] * (2.f / 3.f);
+        const V mz = ((dp[4] - dp[5]) + (dp[6] - dp[7])) * (4.f / 3.f) - dp[3] * (2.f / 3.f);
+        const V mq = (dp[4] - dp[5]) - (dp[6] - dp[7]);
+        const V m4 = (f[0] + C) * (4.f / 3.f) - (sp[1] + sp[2] + sp[3]) * (2.f / 3.f);
         gx = gg * mx * 3.375f;
         gy = gg * my * 3.375f;
         gz = gg * mz * 3.375f;
@@ -120,81 +156,120 @@ __device__ __forceinline__ void lb15_site(const LBArgs &a, const PL &P, int x, i
         g4 = gg * m4 * 1.125f;
     }
     if (a.kT > 0.f) {
-        float G[12];
-        const uint32_t sid = (uint32_t)s;
-        normals4(a.key, a.step, sid, 0u, 0u, G);
-        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
-        normals4(a.key, a.step, sid, 0u, 2u, G + 8);
-        const float mun = 3.0f * rho * a.kT;
-        const float sq = mun * rsqrtf(mun);
-        float n[11];
+        // 11 normals from three Philox blocks, scaled by sqrt(rho kT / c_s^2) lane-wise
+        const V mun = rho * a.k3T;
+        float sq[L];
 #pragma unroll
-        for (int t = 0; t < 11; ++t) n[t] = sq * a.namp[t] * G[t];
-        // the six stress modes enter B exactly as on D3Q19 (same polynomials)
-        const float two9 = 2.0f / 9.0f, one9 = 1.0f / 9.0f;
-        Bxx += two9 * (n[0] + 2.f * n[1]);
-        Byy += two9 * (n[0] - n[1] + n[2]);
-        Bzz += two9 * (n[0] - n[1] - n[2]);
-        Bxy += one9 * n[3];
-        Byz += one9 * n[4];
-        Bxz += one9 * n[5];
-        gx += n[6];
-        gy += n[7];
-        gz += n[8];
-        gq += n[9];
-        g4 += n[10];
+        for (int l = 0; l < L; ++l) sq[l] = mun.lane(l) * rsqrtf(mun.lane(l));
+        V n[12];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            u32x4 r[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+                r[l] = philox4x32_10(u32x4{(uint32_t)s[l], (uint32_t)(uint64_t)a.step, (uint32_t)b,
+                                           (uint32_t)((uint64_t)a.step >> 32)},
+                                     a.key);
+            if constexpr (L == 2) {
+                const uint32_t a0[2] = {r[0].x, r[1].x}, b0[2] = {r[0].y, r[1].y};
+                const uint32_t a1[2] = {r[0].z, r[1].z}, b1[2] = {r[0].w, r[1].w};
+                const V sc = vmake<V>(sq);
+                bm_eval<V, true>(a0, b0, sc, n[4 * b], n[4 * b + 1]);
+                bm_eval<V, true>(a1, b1, sc, n[4 * b + 2], n[4 * b + 3]);
+            } else {
+                const uint32_t a0[2] = {r[0].x, r[0].z}, b0[2] = {r[0].y, r[0].w};
+                F2 c0, s0;
+                bm_eval<F2, true>(a0, b0, F2::bc(sq[0]), c0, s0);
+                const float o[4] = {c0.v.x, s0.v.x, c0.v.y, s0.v.y};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) n[4 * b + k] = V::bc(o[k]);
+            }
+        }
+        // the six stress modes enter Q as on D3Q19 (4.5 x 2/9 = 1, 4.5 x 1/9 = 1/2)
+        const V m0 = n[0] * a.namp[0], m1 = n[1] * a.namp[1], m2 = n[2] * a.namp[2];
+        const V t01 = m0 - m1;
+        Qxx = Qxx + vfma(m1, 2.0f, m0);
+        Qyy = Qyy + (t01 + m2);
+        Qzz = Qzz + (t01 - m2);
+        Qxy = vfma(n[3], 0.5f * a.namp[3], Qxy);
+        Qyz = vfma(n[4], 0.5f * a.namp[4], Qyz);
+        Qxz = vfma(n[5], 0.5f * a.namp[5], Qxz);
+        gx = vfma(n[6], a.namp[6], gx);
+        gy = vfma(n[7], a.namp[7], gy);
+        gz = vfma(n[8], a.namp[8], gz);
+        gq = vfma(n[9], a.namp[9], gq);
+        g4 = vfma(n[10], a.namp[10], g4);
     }
 
-    const float trB = Bxx + Byy + Bzz;
-    const float e0 = 1.5f * trB;  // 9/2 trB/3
+    auto store = [&](int i, V v) {
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            if (l < nl) st3(P.out(i), s[l], v.lane(l));
+    };
+    // B = Q / 4.5: e0 = 9/2 trB / 3 = trQ / 3, 9/2 B_aa = Q_aa, 9/2 trB - e0 = (2/3) trQ, 9 B_ab = 2 Q_ab
+    const V trQ = Qxx + Qyy + Qzz;
+    const V d = vfma(trQ, -1.0f / 3.0f, drho);  // drho - e0
     const float h2 = 2.f / 3.f, h4 = 4.f / 3.f;
-    st3(P.out(0), s, (2.f / 9.f) * (drho - e0 + h4 * g4));
+    store(0, vfma(g4, h4, d) * (2.f / 9.f));
     const float w1 = 1.f / 9.f, w3 = 1.f / 72.f;
-    float E, O;
-    E = drho + 4.5f * Bxx - e0 - h2 * g4;
-    O = 3.f * Ax - h2 * gx;
-    st3(P.out(1), s, w1 * (E + O));
-    st3(P.out(2), s, w1 * (E - O));
-    E = drho + 4.5f * Byy - e0 - h2 * g4;
-    O = 3.f * Ay - h2 * gy;
-    st3(P.out(3), s, w1 * (E + O));
-    st3(P.out(4), s, w1 * (E - O));
-    E = drho + 4.5f * Bzz - e0 - h2 * g4;
-    O = 3.f * Az - h2 * gz;
-    st3(P.out(5), s, w1 * (E + O));
-    st3(P.out(6), s, w1 * (E - O));
+    const V Dm = vfma(g4, -h2, d);
+    const V a3x = (jx + Fx) * 3.0f, a3y = (jy + Fy) * 3.0f, a3z = (jz + Fz) * 3.0f;
+    {
+        const V Ex = Dm + Qxx, Ey = Dm + Qyy, Ez = Dm + Qzz;
+        const V Ox = vfma(gx, -h2, a3x), Oy = vfma(gy, -h2, a3y), Oz = vfma(gz, -h2, a3z);
+        store(1, (Ex + Ox) * w1);
+        store(2, (Ex - Ox) * w1);
+        store(3, (Ey + Oy) * w1);
+        store(4, (Ey - Oy) * w1);
+        store(5, (Ez + Oz) * w1);
+        store(6, (Ez - Oz) * w1);
+    }
     // corners c = (1, a, b) and their opposites: B:cc = trB + 2(a Bxy + b Bxz + ab Byz)
-    const float Ec = drho + 3.f * trB + h4 * g4;  // 9/2 trB - e0 = 3 trB
-    E = Ec + 9.f * (Bxy + Bxz + Byz);
-    O = 3.f * (Ax + Ay + Az) + h4 * (gx + gy + gz) + gq;
-    st3(P.out(7), s, w3 * (E + O));
-    st3(P.out(8), s, w3 * (E - O));
-    E = Ec + 9.f * (Bxy - Bxz - Byz);
-    O = 3.f * (Ax + Ay - Az) + h4 * (gx + gy - gz) - gq;
-    st3(P.out(9), s, w3 * (E + O));
-    st3(P.out(10), s, w3 * (E - O));
-    E = Ec + 9.f * (-Bxy + Bxz - Byz);
-    O = 3.f * (Ax - Ay + Az) + h4 * (gx - gy + gz) - gq;
-    st3(P.out(11), s, w3 * (E + O));
-    st3(P.out(12), s, w3 * (E - O));
-    E = Ec + 9.f * (-Bxy - Bxz + Byz);
-    O = 3.f * (Ax - Ay - Az) + h4 * (gx - gy - gz) + gq;
-    st3(P.out(13), s, w3 * (E + O));
-    st3(P.out(14), s, w3 * (E - O));
+    const V Ec = vfma(trQ, 2.0f / 3.0f, vfma(g4, h4, drho));
+    const V gs = (gx + gy) * h4, gd = (gx - gy) * h4, gzh = gz * h4;
+    const V sxy = a3x + a3y, dxy = a3x - a3y;
+    {
+        const V E = vfma(Qxy + Qxz + Qyz, 2.0f, Ec);
+        const V O = ((sxy + a3z) + (gs + gzh)) + gq;
+        store(7, (E + O) * w3);
+        store(8, (E - O) * w3);
+    }
+    {
+        const V E = vfma(Qxy - Qxz - Qyz, 2.0f, Ec);
+        const V O = ((sxy - a3z) + (gs - gzh)) - gq;
+        store(9, (E + O) * w3);
+        store(10, (E - O) * w3);
+    }
+    {
+        const V E = vfma(Qxz - Qxy - Qyz, 2.0f, Ec);
+        const V O = ((dxy + a3z) + (gd + gzh)) - gq;
+        store(11, (E + O) * w3);
+        store(12, (E - O) * w3);
+    }
+    {
+        const V E = vfma(Qyz - Qxy - Qxz, 2.0f, Ec);
+        const V O = ((dxy - a3z) + (gd - gzh)) + gq;
+        store(13, (E + O) * w3);
+        store(14, (E - O) * w3);
+    }
 }
 
-// P: the population planes (in: a.fin, out: a.fout), a table of addresses.
+// P: the population planes (in: a.fin, out: a.fout), a table of addresses.  Two
+// sites per thread, (x, y, z) and (x, y, z + 1), in packed FP32 (as the D3Q19
+// collide-stream).
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) lb15_kernel(const LBArgs a, const __grid_constant__ PlaneTable<T> P)
+__global__ void __launch_bounds__(LB_BX *LB_BY, 7) lb15_kernel(const LBArgs a, const __grid_constant__ PlaneTable<T> P)
 {
     const Geom &g = a.g;
     const int x = blockIdx.x * LB_BX + threadIdx.x;
     const int y = blockIdx.y * LB_BY + threadIdx.y;
-    const int z = blockIdx.z * LB_BZ + threadIdx.z;
+    const int z = blockIdx.z * LB_BZ;
     if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE) force3<false>(a, x, y, z, Fx, Fy, Fz);
-    lb15_site<T, GHOST_RELAX>(a, P, x, y, z, Fx, Fy, Fz);
+    const int nl = z + 1 < g.nz ? 2 : 1;
+    const int zl[2] = {z, z + nl - 1};
+    F2 Fx = F2::bc(0.f), Fy = F2::bc(0.f), Fz = F2::bc(0.f);
+    if (FORCE) force3v<false>(a, x, y, zl, Fx, Fy, Fz);
+    lb15_sites<F2, T, GHOST_RELAX>(a, P, x, y, zl, nl, Fx, Fy, Fz);
 }
 
 // u = (sum fbar c + F/2)/rho of the streamed state, F this step's force (plane
@@ -223,7 +298,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel15_kernel(const LBArgs
 
 cudaError_t launch_lb15(const LBArgs &a, int storage, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 block(LB_BX, LB_BY, 1);
     const dim3 grid((a.g.nx + LB_BX - 1) / LB_BX, (a.g.ny + LB_BY - 1) / LB_BY, (a.g.nz + LB_BZ - 1) / LB_BZ);
     const bool gr = a.gamma_g != 0.0f;
     const bool force = (a.coupling & FLB_COUPLE_FORCE) != 0;

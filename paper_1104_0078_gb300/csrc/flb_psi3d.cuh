@@ -159,6 +159,10 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     const int z1 = min(z0 + a.zc, g.nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < g.nx && y < g.ny;
+    // the output column has no periodic image within 3 cells in x and y: its
+    // interior planes are stored with one plain store
+    const bool col_inner = x >= 3 && x < g.nx - 3 && y >= 3 && y < g.ny - 3;
+    const int col_off = (x + GX) + g.px * (y + GY);
     const float k22 = a.K * (1.0f / 22.0f);
     const float sdx = sqrtf(2.0f * a.kT * a.M);
     const float mg = a.M * (Q15 ? 1.0f / 24.0f : 1.0f / 12.0f);  // M over the gradient's unit
@@ -424,7 +428,10 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 } else {
                     out = rk_stage_out<STAGE, COH, RK>(a, x, y, z, si, pv, Dd, Dn);
                 }
-                store_padded(a.out, g, x, y, z, out, 3);
+                if (col_inner && z >= 3 && z < g.nz - 3)
+                    a.out[col_off + g.px * g.py * (z + g.gz)] = out;
+                else
+                    store_padded(a.out, g, x, y, z, out, 3);
             }
         }
         r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
