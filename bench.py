@@ -297,6 +297,44 @@ def ensemble_batched_vs_plain(F, I, steps, local, rank, autotune=True):
     return out
 
 
+def ensemble_d3q15(F, I, steps, local, rank, autotune=True):
+    """25 replicas of the paper's own fluctuation run on its lattice (Sec. VI:
+    D3Q15 32^3, tau 1.1, kT 1/3000, A 0.625, B = K = 0, M 0.095; seeds 1..25),
+    with the FV psi scheme (the batched modes run the FV stage): aggregate MLUPS
+    of the plain per-replica launches, the batched graph and the persistent
+    launch, same state, same number of steps."""
+    import torch
+    d = dict(I.WORKLOADS["fluct_d3q15"])
+    ps = [F.flb_params_default(q=15, nx=d["nx"], ny=d["ny"], nz=d["nz"], tau=d["tau"], kT=d["kT"], A=d["A"], B=d["B"],
+                               K=d["K"], M=d["M"], psi_scheme=F.FLB_FV, integrator=F.FLB_HEUN, seed=1 + r + 1000 * rank)
+          for r in range(25)]
+    sites = sum(p.nx * p.ny * p.nz for p in ps)
+    out = {"workload": "25 D3Q15 32^3 replicas, the paper's fluctuation run (tau 1.1, kT 1/3000, A 0.625, "
+                       "M 0.095), FV, Heun", "sites": sites, "steps": steps}
+    for mode, key in ((F.FLB_MODE_PLAIN, "plain"), (F.FLB_MODE_BATCHED, "batched"),
+                      (F.FLB_MODE_PERSISTENT, "persistent")):
+        s = F.Solver(ps, device=f"cuda:{local}")
+        s.set_mode(mode)
+        if autotune:
+            out[key + "_psi_zchunk"] = sorted(set(s.autotune()))
+        s.step(3)
+        s.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[key + "_mlups"] = sites * steps / (ms / 1e3) / 1e6
+        out[key + "_ms_per_step"] = ms / steps
+        del s
+        torch.cuda.empty_cache()
+    out["ratio"] = out["batched_mlups"] / out["plain_mlups"]
+    out["persistent_vs_plain"] = out["persistent_mlups"] / out["plain_mlups"]
+    return out
+
+
 def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
     """Throughput of the other forms of the path, each on its own handle after 3
     warm-up steps, inputs larger than L2 at the default n = 512: the FD psi
@@ -472,6 +510,8 @@ def run_ours(args):
         del s
         torch.cuda.empty_cache()
         ens = ensemble_batched_vs_plain(F, I, args.ensemble_steps, local, rank, autotune=not args.no_autotune)
+        ens["d3q15_paper_ensemble"] = ensemble_d3q15(F, I, args.ensemble_steps, local, rank,
+                                                     autotune=not args.no_autotune)
     variants = None
     if args.variant_steps > 0 and rank == 0:
         only = tuple(v for v in args.variants.split(",") if v)

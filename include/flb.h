@@ -272,8 +272,8 @@ int flb_sq_reset(flb_handle *h, int32_t rep);
  * Launch mode for flb_step:
  *   FLB_MODE_PLAIN       every replica's kernels launched one replica after another;
  *   FLB_MODE_BATCHED     all replicas in one launch per phase (mu, collide-stream,
- *                        velocity, psi stages), replayed as a CUDA graph (D3Q19,
- *                        FV, FLB_LAP_SO, Euler or Heun);
+ *                        velocity, psi stages), replayed as a CUDA graph (D3Q19
+ *                        or D3Q15, FV, FLB_LAP_SO, Euler or Heun);
  *   FLB_MODE_PERSISTENT  all replicas advanced the n steps of one flb_step call
  *                        by one cooperative launch per stretch between sampling
  *                        steps (as FLB_MODE_BATCHED, with FP32 storage).  Its blocks take tile tasks

@@ -771,8 +771,7 @@ int take_status(flb_handle *h)
 bool batch_supported(const flb_handle *h)
 {
     for (const Rep &r : h->reps)
-        if (r.dim != 3 || r.q != 19 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4 ||
-            r.p.laplacian != FLB_LAP_SO)
+        if (r.dim != 3 || r.p.psi_scheme != FLB_FV || r.p.integrator == FLB_RK4 || r.p.laplacian != FLB_LAP_SO)
             return false;
     return !h->reps.empty();
 }
@@ -836,6 +835,7 @@ int batch_upload_table(flb_handle *h)
         d.advect = (r.p.coupling & FLB_COUPLE_ADVECT) ? 1 : 0;
         d.noise = r.p.kT > 0 && r.p.M > 0;
         d.mu_in = (r.p.coupling & FLB_COUPLE_FORCE) && r.p.force_grad != FLB_FORCE_STRESS;
+        d.q15 = r.q == 15;
         d.zc = r.zc;
         d.pstep_tasks = k < h->p_pstep.size() ? h->p_pstep[k] : 0;
         const uint64_t pd[3] = {(uint64_t)g.px, (uint64_t)g.py, (uint64_t)g.pz};
@@ -906,7 +906,8 @@ int batch_capture(flb_handle *h)
     cudaGraph_t gr = nullptr;
     if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return FLB_ECUDA;
     const cudaError_t e =
-        launch_batch_step(L, p0.storage, ghost, force, 1, p0.integrator == FLB_HEUN, noise, batch_mu_in(h), h->st);
+        launch_batch_step(L, p0.storage, ghost, force, 1, p0.integrator == FLB_HEUN, noise, batch_mu_in(h),
+                          h->reps[0].q == 15, h->st);
     const cudaError_t e2 = cudaStreamEndCapture(h->st, &gr);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (gr) cudaGraphDestroy(gr);
@@ -1021,7 +1022,7 @@ int step_persistent(flb_handle *h, int64_t n)
         a.wait_ns = h->wait_ns;
         cudaEvent_t e0 = mark(h);
         ++h->launches;
-        if (launch_persist(a, h->st) != cudaSuccess) return FLB_ECUDA;
+        if (launch_persist(a, h->reps[0].q == 15, h->st) != cudaSuccess) return FLB_ECUDA;
         span(h, 0, e0, mark(h), 1);
         for (Rep &r : h->reps) {
             r.cur ^= (int)(k & 1);
@@ -1640,7 +1641,7 @@ int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
                 const BatchLists L = batch_lists(h);
                 const float t = time_launches(h, [&]() {
                     h->launches += heun ? 2 : 1;
-                    return cuerr(launch_batch_psi(L, heun, noise, batch_mu_in(h), h->st));
+                    return cuerr(launch_batch_psi(L, heun, noise, batch_mu_in(h), h->reps[0].q == 15, h->st));
                 }, reps);
                 if (t < 0.f) return FLB_ECUDA;
                 if (tbest == 0.f || t < tbest) {

@@ -447,6 +447,7 @@ struct alignas(128) BatchRep {
     float A, B, K, M;
     int heun, advect, noise;
     int mu_in;               // the step forms mu of psi^n for the force (FV stage 1 may read it)
+    int q15;                 // a D3Q15 replica
     int zc;                  // planes per psi block
     int pstep_tasks;         // persistent mode: tasks of this replica per step
 };
@@ -519,10 +520,11 @@ struct BatchLists {
 cudaError_t encode_tensor_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
                                   const uint64_t *strides_bytes, const uint32_t *box);
 // mu_in: every replica's step forms mu of psi^n, so FV stage 1 reads it (map_mu)
+// q15: D3Q15 replicas (collide-stream, velocity and the FV operators of D3Q15)
 cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
-                              bool noise, bool mu_in, cudaStream_t st);
+                              bool noise, bool mu_in, bool q15, cudaStream_t st);
 // the psi stage launches of a batched step alone (no state change: the autotuner times them)
-cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, cudaStream_t st);
+cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, bool q15, cudaStream_t st);
 
 // ---- persistent batched mode (flb_persist.cu) --------------------------------
 enum { PH_MU = 0, PH_LB = 1, PH_VEL = 2, PH_S1 = 3, PH_S2 = 4, PH_COUNT = 5 };
@@ -549,7 +551,7 @@ struct PersistArgs {
 size_t persist_smem_bytes();
 void persist_tiles(const Geom &g, int zc, int coupling, int heun, int counts[PH_COUNT]);
 void persist_tasks(std::vector<PTask> &v, int rep, int ph, const Geom &g, int zc, int need);
-cudaError_t launch_persist(const PersistArgs &a, cudaStream_t st);
+cudaError_t launch_persist(const PersistArgs &a, bool q15, cudaStream_t st);  // q15: D3Q15 replicas
 
 // host launchers (flb_lb.cu, flb_psi.cu, flb_obs.cu)
 cudaError_t launch_lb(const LBArgs &a, int q, int storage, cudaStream_t s);

@@ -20,6 +20,7 @@
 // generic-to-async proxy fence.
 #include "flb_psi3d.cuh"
 #include "flb_mu3d.cuh"
+#include "flb_site15.cuh"
 
 namespace flb {
 
@@ -77,6 +78,8 @@ __device__ __forceinline__ void lb_args_at(const BatchRep &r, long long ds, LBAr
     __syncthreads();
 }
 
+// Q15: every replica is D3Q15 (a handle's replicas share the lattice)
+template <bool Q15>
 __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
 {
     extern __shared__ __align__(1024) float tsmem[];
@@ -131,8 +134,17 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
                 if (task.phase == PH_LB) {
                     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
                     if (force) force3<true>(sla, x, y, z, Fx, Fy, Fz);
-                    if (sla.gamma_g != 0.f) lb_site<float, true, true, true>(sla, x, y, z, Fx, Fy, Fz);
-                    else lb_site<float, false, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                    if (Q15) {
+                        if (sla.gamma_g != 0.f) lb15_site<float, true, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                        else lb15_site<float, false, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                    } else if (sla.gamma_g != 0.f) {
+                        lb_site<float, true, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                    } else {
+                        lb_site<float, false, true, true>(sla, x, y, z, Fx, Fy, Fz);
+                    }
+                } else if (Q15) {
+                    if (force) vel15_site<float, true, true>(sla, x, y, z);
+                    else vel15_site<float, false, true>(sla, x, y, z);
                 } else {
                     if (force) vel3_site<float, true, true>(sla, x, y, z);
                     else vel3_site<float, false, true>(sla, x, y, z);
@@ -142,7 +154,26 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
             const int stage = task.phase == PH_S1 ? 1 : 2;
             if (t == 0) psi_batch_args(r, ds, stage, spa);
             __syncthreads();
-            if (stage == 1) {
+            if (Q15 && stage == 1) {  // the FV operators of D3Q15
+                const CUtensorMap *pm = &r.map_psi[(int)(ds & 1)];
+                if (r.mu_in) {
+                    if (r.noise)
+                        psi3_fv_tma_block<1, true, true, true, false, true, true>(pm, &r.map_u, spa, P.status, task.bx,
+                                                                                 task.by, task.bz, tsmem, &r.map_mu);
+                    else
+                        psi3_fv_tma_block<1, false, true, false, false, true, true>(pm, &r.map_u, spa, P.status, task.bx,
+                                                                                   task.by, task.bz, tsmem, &r.map_mu);
+                } else if (r.noise) {
+                    psi3_fv_tma_block<1, true, true, true, false, false, true>(pm, &r.map_u, spa, P.status, task.bx,
+                                                                              task.by, task.bz, tsmem);
+                } else {
+                    psi3_fv_tma_block<1, false, true, false, false, false, true>(pm, &r.map_u, spa, P.status, task.bx,
+                                                                                task.by, task.bz, tsmem);
+                }
+            } else if (Q15) {
+                psi3_fv_tma_block<2, false, true, false, false, false, true>(&r.map_psis, &r.map_u, spa, P.status, task.bx,
+                                                                            task.by, task.bz, tsmem);
+            } else if (stage == 1) {
                 const CUtensorMap *pm = &r.map_psi[(int)(ds & 1)];
                 if (r.mu_in) {  // mu of psi^n from this step's mu tasks
                     if (r.noise)
@@ -221,20 +252,21 @@ void persist_tasks(std::vector<PTask> &v, int rep, int ph, const Geom &g, int zc
             for (int bx = 0; bx < nxb; ++bx) push(bx, by, bz);
 }
 
-cudaError_t launch_persist(const PersistArgs &a, cudaStream_t st)
+cudaError_t launch_persist(const PersistArgs &a, bool q15, cudaStream_t st)
 {
     const size_t smem = persist_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *kernel = q15 ? (const void *)persist_kernel<true> : (const void *)persist_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persist_kernel, PB_NT, smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, PB_NT, smem)) != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     const long long total = (long long)a.ntask * a.nsteps;
     const unsigned grid = (unsigned)std::min<long long>((long long)per * sms, std::max<long long>(total, 1));
     void *args[] = {const_cast<PersistArgs *>(&a)};
-    return cudaLaunchCooperativeKernel((const void *)persist_kernel, dim3(grid), dim3(PB_NT), args, smem, st);
+    return cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(PB_NT), args, smem, st);
 }
 
 }  // namespace flb

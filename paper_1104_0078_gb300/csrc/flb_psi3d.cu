@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constan
 
 // batched: block b of the launch works on L.psi[b]; MU_IN: stage 1 reads mu of
 // psi^n from the replica's mu field (every replica's step formed it)
-template <int STAGE, bool NOISE, bool MU_IN = false>
+template <int STAGE, bool NOISE, bool MU_IN = false, bool Q15 = false>
 __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLists L)
 {
     extern __shared__ __align__(1024) float tsmem[];
@@ -284,15 +284,17 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
     if (threadIdx.x == 0) psi_batch_args(r, ds, STAGE, sa);
     __syncthreads();
     const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[(int)(ds & 1)] : &r.map_psis;
-    psi3_fv_tma_block<STAGE, NOISE, false, true, false, MU_IN>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz, tsmem,
-                                                              &r.map_mu);
+    psi3_fv_tma_block<STAGE, NOISE, false, true, false, MU_IN, Q15>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz,
+                                                                   tsmem, &r.map_mu);
 }
 
 __global__ void advance_kernel(long long *dstep) { *dstep += 1; }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st);
+cudaError_t launch_lb15_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st);
 
-cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, cudaStream_t st)
+template <bool Q15>
+static cudaError_t batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, cudaStream_t st)
 {
     const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS, smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS;
     const size_t nb = sizeof(float) * FV_NOISE_FLOATS;
@@ -302,21 +304,27 @@ cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu
         kernel<<<L.npsi, PS_NT, bytes, st>>>(L);
         return cudaGetLastError();
     };
-    cudaError_t e = mu_in ? (noise ? go(psi3_fv_tma_batch_kernel<1, true, true>, smm + nb)
-                                   : go(psi3_fv_tma_batch_kernel<1, false, true>, smm))
-                          : (noise ? go(psi3_fv_tma_batch_kernel<1, true>, sm + nb)
-                                   : go(psi3_fv_tma_batch_kernel<1, false>, sm));
+    cudaError_t e = mu_in ? (noise ? go(psi3_fv_tma_batch_kernel<1, true, true, Q15>, smm + nb)
+                                   : go(psi3_fv_tma_batch_kernel<1, false, true, Q15>, smm))
+                          : (noise ? go(psi3_fv_tma_batch_kernel<1, true, false, Q15>, sm + nb)
+                                   : go(psi3_fv_tma_batch_kernel<1, false, false, Q15>, sm));
     if (e != cudaSuccess || !heun) return e;
-    return go(psi3_fv_tma_batch_kernel<2, false>, sm);
+    return go(psi3_fv_tma_batch_kernel<2, false, false, Q15>, sm);
+}
+
+cudaError_t launch_batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, bool q15, cudaStream_t st)
+{
+    return q15 ? batch_psi<true>(L, heun, noise, mu_in, st) : batch_psi<false>(L, heun, noise, mu_in, st);
 }
 
 cudaError_t launch_batch_step(const BatchLists &L, int storage, bool ghost, bool force, int scheme_fv, bool heun,
-                              bool noise, bool mu_in, cudaStream_t st)
+                              bool noise, bool mu_in, bool q15, cudaStream_t st)
 {
     if (!scheme_fv) return cudaErrorNotSupported;
-    cudaError_t e = launch_lb3_batch(L, storage, ghost, force, st);
+    cudaError_t e = q15 ? launch_lb15_batch(L, storage, ghost, force, st)
+                        : launch_lb3_batch(L, storage, ghost, force, st);
     if (e != cudaSuccess) return e;
-    e = launch_batch_psi(L, heun, noise, mu_in, st);
+    e = launch_batch_psi(L, heun, noise, mu_in, q15, st);
     if (e != cudaSuccess) return e;
     advance_kernel<<<1, 1, 0, st>>>(const_cast<long long *>(L.dstep));
     return cudaGetLastError();

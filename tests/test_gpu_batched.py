@@ -96,3 +96,23 @@ def test_batched_rejects_fd():
     with pytest.raises(F.FlbError) as e:
         s.step(1)
     assert e.value.code == F.FLB_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("integrator,kT", [(1, 1e-4), (2, 1e-4), (2, 0.0)])
+def test_batched_d3q15_equals_plain(integrator, kT):
+    # D3Q15 replicas (the paper's lattice, Sec. VI), uneven sizes, FV: the batched
+    # launches (one site per thread on row-packed lists, the D3Q15 stage
+    # operators) against the plain two-sites-per-thread path, bitwise; and again
+    # after the step counter and buffer parity have advanced on the device
+    ps = _replicas(q=15, integrator=integrator, kT=kT)
+    plain, _, _ = _run(F.FLB_MODE_PLAIN, ps, 6)
+    batched, _, s = _run(F.FLB_MODE_BATCHED, ps, 6)
+    for (fa, pa, sa), (fb, pb, sb) in zip(plain, batched):
+        assert sa == sb == 6
+        assert np.array_equal(fa, fb)
+        assert np.array_equal(pa, pb)
+    s.step(3)
+    plain9, _, _ = _run(F.FLB_MODE_PLAIN, ps, 9)
+    for r, (fa, pa, _) in enumerate(plain9):
+        assert np.array_equal(fa, s.get_populations(r))
+        assert np.array_equal(pa, s.get_psi_u(r)[0])
