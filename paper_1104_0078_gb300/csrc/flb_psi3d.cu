@@ -260,21 +260,23 @@ struct TmaArgs {
 
 // MU_IN: stage 1 reads mu of its input from mu_map instead of forming it; Q15:
 // the FV operators of D3Q15
+// 256 threads, each on a pair of output rows in packed FP32 (F2)
+using StageV = F2;
 template <int STAGE, bool NOISE, bool RK, bool MU_IN, bool Q15 = false>
-__global__ void __launch_bounds__(PS_NT) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
-                                                            const __grid_constant__ CUtensorMap u_map,
-                                                            const __grid_constant__ CUtensorMap mu_map,
-                                                            const TmaArgs ta)
+__global__ void __launch_bounds__(stage_threads<StageV>(), 2) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,
+                                                                   const __grid_constant__ CUtensorMap u_map,
+                                                                   const __grid_constant__ CUtensorMap mu_map,
+                                                                   const TmaArgs ta)
 {
     extern __shared__ __align__(1024) float tsmem[];
-    psi3_fv_tma_block<STAGE, NOISE, false, false, RK, MU_IN, Q15>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x,
-                                                                 blockIdx.y, blockIdx.z, tsmem, &mu_map);
+    psi3_fv_tma_block<STAGE, NOISE, false, false, RK, MU_IN, Q15, StageV>(&psi_map, &u_map, ta.a, ta.status, blockIdx.x,
+                                                                     blockIdx.y, blockIdx.z, tsmem, &mu_map);
 }
 
 // batched: block b of the launch works on L.psi[b]; MU_IN: stage 1 reads mu of
 // psi^n from the replica's mu field (every replica's step formed it)
 template <int STAGE, bool NOISE, bool MU_IN = false, bool Q15 = false>
-__global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(stage_threads<StageV>(), 2) psi3_fv_tma_batch_kernel(const BatchLists L)
 {
     extern __shared__ __align__(1024) float tsmem[];
     __shared__ Psi3Args sa;
@@ -284,8 +286,8 @@ __global__ void __launch_bounds__(PS_NT) psi3_fv_tma_batch_kernel(const BatchLis
     if (threadIdx.x == 0) psi_batch_args(r, ds, STAGE, sa);
     __syncthreads();
     const CUtensorMap *pm = STAGE == 1 ? &r.map_psi[(int)(ds & 1)] : &r.map_psis;
-    psi3_fv_tma_block<STAGE, NOISE, false, true, false, MU_IN, Q15>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz,
-                                                                   tsmem, &r.map_mu);
+    psi3_fv_tma_block<STAGE, NOISE, false, true, false, MU_IN, Q15, StageV>(pm, &r.map_u, sa, L.status, b.bx, b.by, b.bz,
+                                                                       tsmem, &r.map_mu);
 }
 
 __global__ void advance_kernel(long long *dstep) { *dstep += 1; }
@@ -301,7 +303,7 @@ static cudaError_t batch_psi(const BatchLists &L, bool heun, bool noise, bool mu
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
-        kernel<<<L.npsi, PS_NT, bytes, st>>>(L);
+        kernel<<<L.npsi, stage_threads<StageV>(), bytes, st>>>(L);
         return cudaGetLastError();
     };
     cudaError_t e = mu_in ? (noise ? go(psi3_fv_tma_batch_kernel<1, true, true, Q15>, smm + nb)
@@ -396,7 +398,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int q, int stage, bool noise
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
-        kernel<<<grid, PS_NT, bytes, st>>>(pm, um, mm, ta);
+        kernel<<<grid, stage_threads<StageV>(), bytes, st>>>(pm, um, mm, ta);
         return cudaGetLastError();
     };
     const size_t smn = sm + sizeof(float) * FV_NOISE_FLOATS;

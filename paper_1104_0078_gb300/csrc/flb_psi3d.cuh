@@ -102,6 +102,37 @@ constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 *
 constexpr int FV_MU_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + T_MU_DEPTH * TM_SLOT + 6 * TJ_N;
 constexpr int FV_NOISE_FLOATS = 6 * TJ_N;
 
+// Lane-generic access to a shared-memory plane: lane l of the value at index c
+// sits at c + l * loff (the row pairs of a region lie loff apart).
+template <class V>
+__device__ __forceinline__ V lds_v(const float *P, int c, int loff)
+{
+    float t[V::L];
+#pragma unroll
+    for (int l = 0; l < V::L; ++l) t[l] = P[c + l * loff];
+    return vmake<V>(t);
+}
+template <class V>
+__device__ __forceinline__ void sts_v(float *P, int c, int loff, V v)
+{
+#pragma unroll
+    for (int l = 0; l < V::L; ++l) P[c + l * loff] = v.lane(l);
+}
+
+// mu_so of flb_internal.cuh in lane arithmetic (the same explicitly rounded
+// operations, so a lane gets mu_so's bits)
+template <class V>
+__device__ __forceinline__ V mu_so_v(float A, float B, float k22, V ps, V n1, V n2, V n3)
+{
+    const V l22 = vfma(n1, 6.f, vfma(n2, 3.f, vfma(ps, -80.f, n3)));
+    return vfma(l22, -k22, vfma((ps * ps) * B, ps, ps * A));
+}
+
+// Threads of a stage block: one output point per thread (F1: 512), or a pair of
+// output rows y and y + TY/2 per thread in the lanes of packed FP32 (F2: 256).
+template <class V>
+__host__ __device__ constexpr int stage_threads() { return V::L == 1 ? PS_NT : PS_NT / 2; }
+
 // One block (tile bx, by; z chunk bz).  psi_map / u_map: tensor maps of the stage
 // input psi and of the velocity (kernel parameters or global memory); tsmem: the
 // block's dynamic shared memory.
@@ -126,6 +157,12 @@ constexpr int FV_NOISE_FLOATS = 6 * TJ_N;
 // plane starts at y = y0 - 2 and the flux, noise and u planes at y = y0 - 1, so a
 // point's index in each is its psi-slot index less TB_X or 2 TB_X.
 //
+// Lanes: with V = F2 a thread works the point pairs (x, y) and (x, y + H/2) of
+// every region of height H (mu 20, flux 18, tile 16 rows) in the two lanes of
+// packed FP32 registers, and the block has 256 threads; with V = F1 one point
+// and 512 threads.  Every FP32 operation is explicitly rounded, so both give
+// the same bits; the random numbers, the loads and the stores run per lane.
+//
 // Q15: the FV operators of D3Q15 (faces w = 1/9, corners 1/72), in units of 1/24:
 //   24 grad mu (q): x: 8 ex(q) + Dx(q-1) + Dx(q+1),  y: likewise,
 //     z: Zq(q+1) - Zq(q-1) with Zq = 8 mu + the 4 in-plane corners;
@@ -137,12 +174,17 @@ constexpr int FV_NOISE_FLOATS = 6 * TJ_N;
 // planes then come by TMA, like psi and u, into a third ring ([TY+4][TX+8], column
 // c <-> x = x0 - 4 + c, row r <-> y = y0 - 2 + r), and the block skips forming mu.
 template <int STAGE, bool NOISE, bool COH = false, bool KEY_R0 = false, bool RK = true, bool MU_IN = false,
-          bool Q15 = false>
+          bool Q15 = false, class V = F1>
 __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, const CUtensorMap *u_map,
                                                   const Psi3Args &a, int *status, int bx, int by, int bz,
                                                   float *tsmem, const CUtensorMap *mu_map = nullptr)
 {
     static_assert(!MU_IN || STAGE == 1, "mu of psi^n is the input of stage 1 only");
+    constexpr int L = V::L, NT = stage_threads<V>();
+    constexpr int LO2 = (H2Y / 2) * TB_X, LO1 = (H1Y / 2) * TB_X, LO0 = (PS_TY / 2) * TB_X;  // lane 1's offsets
+    constexpr int LR2 = L == 1 ? 0 : LO2, LR1 = L == 1 ? 0 : LO1, LR0 = L == 1 ? 0 : LO0;
+    constexpr int HH2 = H2Y / L, HH1 = H1Y / L;  // rows of the mu and flux regions per lane
+    constexpr int SS2 = (H2X * HH2 + NT - 1) / NT, SS1 = (H1X * HH1 + NT - 1) / NT;
     if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
     const int rk4 = RK ? a.rk4 : 0;                       // RK false: a launch without RK4
     float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
@@ -154,51 +196,62 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH], bar_m[T_MU_DEPTH];
     __shared__ int s_bad;
     const Geom &g = a.g;
-    const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;
+    const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;  // lane l's output row: ty + l TY/2
     const int x0 = bx * PS_TX, y0 = by * PS_TY, z0 = bz * a.zc;
     const int z1 = min(z0 + a.zc, g.nz);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < g.nx && y < g.ny;
-    // the output column has no periodic image within 3 cells in x and y: its
-    // interior planes are stored with one plain store
-    const bool col_inner = x >= 3 && x < g.nx - 3 && y >= 3 && y < g.ny - 3;
-    const int col_off = (x + GX) + g.px * (y + GY);
+    const int x = x0 + tx;
+    int yl[L];
+    bool act[L], inner[L];
+    int coff[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        yl[l] = y0 + ty + l * (PS_TY / 2);
+        act[l] = x < g.nx && yl[l] < g.ny;
+        // the output column has no periodic image within 3 cells in x and y: its
+        // interior planes are stored with one plain store
+        inner[l] = x >= 3 && x < g.nx - 3 && yl[l] >= 3 && yl[l] < g.ny - 3;
+        coff[l] = (x + GX) + g.px * (yl[l] + GY);
+    }
     const float k22 = a.K * (1.0f / 22.0f);
     const float sdx = sqrtf(2.0f * a.kT * a.M);
     const float mg = a.M * (Q15 ? 1.0f / 24.0f : 1.0f / 12.0f);  // M over the gradient's unit
     constexpr float DIV = Q15 ? 1.0f / 24.0f : 1.0f / 12.0f;      // the divergence's unit
     const int pbase = z0 - 3, ubase = z0 - 1, mbase = z0 - 2;  // first psi / u / mu plane of the chunk
-    // psi-slot index of every mu-region point (c2) and flux-region point (p1), -1
-    // off the region; noise counter id of every flux-region point.
+    // psi-slot index of every mu-region point (c2) and flux-region point (p1) of
+    // lane 0, -1 off the region; noise counter id of every flux-region point.
     // Region points are dealt to threads row segment by row segment: the first
     // 32 columns of every row (a full warp reads 32 consecutive words, free of
     // bank conflicts), then the few remaining columns of all rows.
-    int c2[S2], p1[S1], n1[S1];
+    int c2[SS2], p1[SS1], n1[SS1][L];
 #pragma unroll
-    for (int j = 0; j < S2; ++j) {
+    for (int j = 0; j < SS2; ++j) {
         int lx, ly;
-        region_point(threadIdx.x + j * PS_NT, H2X, H2Y, lx, ly);
-        const bool ok = threadIdx.x + j * PS_NT < H2N;
+        region_point(threadIdx.x + j * NT, H2X, HH2, lx, ly);
+        const bool ok = threadIdx.x + j * NT < H2X * HH2;
         c2[j] = ok ? (lx + 2) + TB_X * (ly + 1) : -1;
     }
 #pragma unroll
-    for (int j = 0; j < S1; ++j) {
+    for (int j = 0; j < SS1; ++j) {
         int lx, ly;
-        region_point(threadIdx.x + j * PS_NT, H1X, H1Y, lx, ly);
-        const bool ok = threadIdx.x + j * PS_NT < H1N;
+        region_point(threadIdx.x + j * NT, H1X, HH1, lx, ly);
+        const bool ok = threadIdx.x + j * NT < H1X * HH1;
         p1[j] = ok ? (lx + 3) + TB_X * (ly + 2) : -1;
-        n1[j] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) + g.nx * wrapi(min(y0 - 1 + ly, g.ny + GY - 1), g.ny);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            n1[j][l] = wrapi(min(x0 - 1 + lx, g.nx + GX - 1), g.nx) +
+                       g.nx * wrapi(min(y0 - 1 + ly + l * HH1, g.ny + GY - 1), g.ny);
     }
     // per-plane partial sums carried between planes (registers)
-    float pa[S2][2], pb[S2][2], pd[S2][2];  // psi: centre, faces, diagonals of planes p-2 [0], p-1 [1]
-    float G0[S1][3], G1[S1][3];            // 12 grad mu of planes m-1 and m, partly summed
+    const V zero = V::bc(0.f);
+    V pa[SS2][2], pb[SS2][2], pd[SS2][2];  // psi: centre, faces, diagonals of planes p-2 [0], p-1 [1]
+    V G0[SS1][3], G1[SS1][3];            // 12 grad mu of planes m-1 and m, partly summed
 #pragma unroll
-    for (int j = 0; j < S2; ++j) pa[j][0] = pa[j][1] = pb[j][0] = pb[j][1] = pd[j][0] = pd[j][1] = 0.f;
+    for (int j = 0; j < SS2; ++j) pa[j][0] = pa[j][1] = pb[j][0] = pb[j][1] = pd[j][0] = pd[j][1] = zero;
 #pragma unroll
-    for (int j = 0; j < S1; ++j)
+    for (int j = 0; j < SS1; ++j)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) G0[j][k] = G1[j][k] = 0.f;
-    float D0 = 0.f, D1 = 0.f, N0 = 0.f, N1 = 0.f;  // 12 (24) div of the flux / noise of planes q-1 and q
+        for (int k = 0; k < 3; ++k) G0[j][k] = G1[j][k] = zero;
+    V D0 = zero, D1 = zero, N0 = zero, N1 = zero;  // 12 (24) div of the flux / noise of planes q-1 and q
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
@@ -243,14 +296,18 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         // Heun stage 2 and RK4 stages 2-4: the accumulator E (and for RK4 stages 2
         // and 3 the noise increment and psi^n) of this iteration's output plane
         // p-3 are loaded now, so that their latency hides behind the plane's work
-        float e_pre = 0.f, n_pre = 0.f, b_pre = 0.f;
-        if (STAGE == 2 && active && p - 3 >= z0) {
-            const int sp = x + g.nx * (y + g.ny * (p - 3));
-            if (!rk4 || rk4 > 1) e_pre = COH ? __ldcg(a.E + sp) : a.E[sp];
-            if (rk4 == 2 || rk4 == 3) {
-                const int bp = g.pidx32(x, y, p - 3);
-                n_pre = COH ? __ldcg(a.Dn + sp) : a.Dn[sp];
-                b_pre = COH ? __ldcg(a.base + bp) : a.base[bp];
+        float e_pre[L], n_pre[L], b_pre[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            e_pre[l] = n_pre[l] = b_pre[l] = 0.f;
+            if (STAGE == 2 && act[l] && p - 3 >= z0) {
+                const int sp = x + g.nx * (yl[l] + g.ny * (p - 3));
+                if (!rk4 || rk4 > 1) e_pre[l] = COH ? __ldcg(a.E + sp) : a.E[sp];
+                if (rk4 == 2 || rk4 == 3) {
+                    const int bp = g.pidx32(x, yl[l], p - 3);
+                    n_pre[l] = COH ? __ldcg(a.Dn + sp) : a.Dn[sp];
+                    b_pre[l] = COH ? __ldcg(a.base + bp) : a.base[bp];
+                }
             }
         }
         // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
@@ -261,18 +318,20 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             float *dst = smu + ((p - 1) & 1) * TM_N;
             const bool emit = p - 1 >= z0 - 2;
 #pragma unroll
-            for (int j = 0; j < S2; ++j) {
+            for (int j = 0; j < SS2; ++j) {
                 const int c = c2[j];
                 if (c < 0) continue;
-                const float ac = P[c];
-                const float bc = (P[c - 1] + P[c + 1]) + (P[c - TB_X] + P[c + TB_X]);
-                const float dc = (P[c - 1 - TB_X] + P[c + 1 - TB_X]) + (P[c - 1 + TB_X] + P[c + 1 + TB_X]);
+                const V ac = lds_v<V>(P, c, LR2);
+                const V bc = (lds_v<V>(P, c - 1, LR2) + lds_v<V>(P, c + 1, LR2)) +
+                             (lds_v<V>(P, c - TB_X, LR2) + lds_v<V>(P, c + TB_X, LR2));
+                const V dc = (lds_v<V>(P, c - 1 - TB_X, LR2) + lds_v<V>(P, c + 1 - TB_X, LR2)) +
+                             (lds_v<V>(P, c - 1 + TB_X, LR2) + lds_v<V>(P, c + 1 + TB_X, LR2));
                 if (emit) {
-                    const float ps = pa[j][1];
-                    const float nn1 = pb[j][1] + (pa[j][0] + ac);
-                    const float nn2 = pd[j][1] + (pb[j][0] + bc);
-                    const float nn3 = pd[j][0] + dc;
-                    dst[c - TB_X] = mu_so(a.A, a.B, k22, ps, nn1, nn2, nn3);  // mu plane row 0 <-> psi-slot row 1
+                    const V nn1 = pb[j][1] + (pa[j][0] + ac);
+                    const V nn2 = pd[j][1] + (pb[j][0] + bc);
+                    const V nn3 = pd[j][0] + dc;
+                    // mu plane row 0 <-> psi-slot row 1
+                    sts_v<V>(dst, c - TB_X, LR2, mu_so_v<V>(a.A, a.B, k22, pa[j][1], nn1, nn2, nn3));
                 }
                 pa[j][0] = pa[j][1];
                 pb[j][0] = pb[j][1];
@@ -315,56 +374,63 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
             float *X = sX + ((m - 1) & 1) * 3 * TJ_N;
             const int zid = g.nx * g.ny * wrapi(m - 1, g.nz);
 #pragma unroll
-            for (int j = 0; j < S1; ++j) {
+            for (int j = 0; j < SS1; ++j) {
                 if (p1[j] < 0) continue;
                 const int c = p1[j] - TB_X;  // in the mu plane
-                const float mxp = Mu[c + 1], mxm = Mu[c - 1], myp = Mu[c + TB_X], mym = Mu[c - TB_X];
-                const float mpp = Mu[c + 1 + TB_X], mpm = Mu[c + 1 - TB_X], mmp = Mu[c - 1 + TB_X],
-                            mmm = Mu[c - 1 - TB_X];
-                const float ex = mxp - mxm, ey = myp - mym;
-                const float Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
-                float gx, gy, gz;  // plane m-1, complete
+                const V mxp = lds_v<V>(Mu, c + 1, LR1), mxm = lds_v<V>(Mu, c - 1, LR1);
+                const V myp = lds_v<V>(Mu, c + TB_X, LR1), mym = lds_v<V>(Mu, c - TB_X, LR1);
+                const V mpp = lds_v<V>(Mu, c + 1 + TB_X, LR1), mpm = lds_v<V>(Mu, c + 1 - TB_X, LR1);
+                const V mmp = lds_v<V>(Mu, c - 1 + TB_X, LR1), mmm = lds_v<V>(Mu, c - 1 - TB_X, LR1);
+                const V ex = mxp - mxm, ey = myp - mym;
+                const V Dx = (mpp + mpm) - (mmp + mmm), Dy = (mpp + mmp) - (mpm + mmm);
+                V gx, gy, gz;  // plane m-1, complete
                 if (Q15) {
-                    const float Zq = 8.f * Mu[c] + ((mpp + mpm) + (mmp + mmm));
+                    const V Zq = vfma(lds_v<V>(Mu, c, LR1), 8.f, (mpp + mpm) + (mmp + mmm));
                     gx = G0[j][0] + Dx;
                     gy = G0[j][1] + Dy;
                     gz = G0[j][2] + Zq;
-                    G0[j][0] = G1[j][0] + 8.f * ex;
-                    G0[j][1] = G1[j][1] + 8.f * ey;
+                    G0[j][0] = vfma(ex, 8.f, G1[j][0]);
+                    G0[j][1] = vfma(ey, 8.f, G1[j][1]);
                     G0[j][2] = G1[j][2];
                     G1[j][0] = Dx;
                     G1[j][1] = Dy;
-                    G1[j][2] = -Zq;
+                    G1[j][2] = Zq * -1.0f;
                 } else {
-                    const float Zp = 2.f * Mu[c] + ((mxp + mxm) + (myp + mym));
+                    const V Zp = vfma(lds_v<V>(Mu, c, LR1), 2.f, (mxp + mxm) + (myp + mym));
                     gx = G0[j][0] + ex;
                     gy = G0[j][1] + ey;
                     gz = G0[j][2] + Zp;
-                    G0[j][0] = G1[j][0] + (2.f * ex + Dx);
-                    G0[j][1] = G1[j][1] + (2.f * ey + Dy);
+                    G0[j][0] = G1[j][0] + vfma(ex, 2.f, Dx);
+                    G0[j][1] = G1[j][1] + vfma(ey, 2.f, Dy);
                     G0[j][2] = G1[j][2];
                     G1[j][0] = ex;
                     G1[j][1] = ey;
-                    G1[j][2] = -Zp;
+                    G1[j][2] = Zp * -1.0f;
                 }
                 if (emit) {
                     const int k = p1[j] - 2 * TB_X;  // in the flux, noise and u planes
-                    float jx = mg * gx, jy = mg * gy, jz = mg * gz;
-                    if (a.advect) {
-                        const float pv = ps[p1[j]];
-                        jx -= uq[k] * pv;
-                        jy -= uq[TB_X * H1Y + k] * pv;
-                        jz -= uq[2 * TB_X * H1Y + k] * pv;
+                    V jx = gx * mg, jy = gy * mg, jz = gz * mg;
+                    if (a.advect) {  // J = M grad mu - u psi
+                        const V npv = lds_v<V>(ps, p1[j], LR1) * -1.0f;
+                        jx = vfma(lds_v<V>(uq, k, LR1), npv, jx);
+                        jy = vfma(lds_v<V>(uq, TB_X * H1Y + k, LR1), npv, jy);
+                        jz = vfma(lds_v<V>(uq, 2 * TB_X * H1Y + k, LR1), npv, jz);
                     }
-                    J[k] = jx;
-                    J[TJ_N + k] = jy;
-                    J[2 * TJ_N + k] = jz;
+                    sts_v<V>(J, k, LR1, jx);
+                    sts_v<V>(J, TJ_N + k, LR1, jy);
+                    sts_v<V>(J, 2 * TJ_N + k, LR1, jz);
                     if (NOISE) {
-                        float Gn[4];  // N(0, 2 kT M): the radius carries the factor sqrt(2 kT M)
-                        normals4<KEY_R0, true>(a.key, a.step, (uint32_t)(n1[j] + zid), 1u, 0u, Gn, sdx);
-                        X[k] = Gn[0];
-                        X[TJ_N + k] = Gn[1];
-                        X[2 * TJ_N + k] = Gn[2];
+                        // three N(0, 2 kT M) normals per node, the radius scaled by
+                        // sqrt(2 kT M): the (x, y) and (z, w) Box-Muller pairs of the
+                        // node's Philox block, one packed evaluation per node
+#pragma unroll
+                        for (int l = 0; l < L; ++l) {
+                            float Gn[4];
+                            normals4<KEY_R0, true>(a.key, a.step, (uint32_t)(n1[j][l] + zid), 1u, 0u, Gn, sdx);
+                            X[k + l * LR1] = Gn[0];
+                            X[TJ_N + k + l * LR1] = Gn[1];
+                            X[2 * TJ_N + k + l * LR1] = Gn[2];
+                        }
                     }
                 }
             }
@@ -374,64 +440,97 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         // (C) flux partials of plane q = p-2 at the tile point; the output of plane q-1 completes
         const int q = p - 2;
         if (q >= z0 - 1) {
-            const int c = (tx + 4) + TB_X * (ty + 1);  // the tile point in the flux plane
+            const int c = (tx + 4) + TB_X * (ty + 1);  // the tile point (lane 0) in the flux plane
             const float *Jx = sJ + (q & 1) * 3 * TJ_N, *Jy = Jx + TJ_N, *Jz = Jy + TJ_N;
-            const float hxy = (Jx[c + 1] - Jx[c - 1]) + (Jy[c + TB_X] - Jy[c - TB_X]);
-            const float dg = ((Jx[c + 1 + TB_X] + Jy[c + 1 + TB_X]) - (Jx[c - 1 - TB_X] + Jy[c - 1 - TB_X])) +
-                             ((Jx[c + 1 - TB_X] - Jy[c + 1 - TB_X]) - (Jx[c - 1 + TB_X] - Jy[c - 1 + TB_X]));
-            const float zc = Jz[c];
-            float dd;  // plane q-1, complete
+            const V hxy = (lds_v<V>(Jx, c + 1, LR0) - lds_v<V>(Jx, c - 1, LR0)) +
+                          (lds_v<V>(Jy, c + TB_X, LR0) - lds_v<V>(Jy, c - TB_X, LR0));
+            const V dg = ((lds_v<V>(Jx, c + 1 + TB_X, LR0) + lds_v<V>(Jy, c + 1 + TB_X, LR0)) -
+                          (lds_v<V>(Jx, c - 1 - TB_X, LR0) + lds_v<V>(Jy, c - 1 - TB_X, LR0))) +
+                         ((lds_v<V>(Jx, c + 1 - TB_X, LR0) - lds_v<V>(Jy, c + 1 - TB_X, LR0)) -
+                          (lds_v<V>(Jx, c - 1 + TB_X, LR0) - lds_v<V>(Jy, c - 1 + TB_X, LR0)));
+            const V zc = lds_v<V>(Jz, c, LR0);
+            V dd;  // plane q-1, complete
             if (Q15) {
-                const float c4 = (Jz[c + 1 + TB_X] + Jz[c + 1 - TB_X]) + (Jz[c - 1 + TB_X] + Jz[c - 1 - TB_X]);
-                dd = D0 + (8.f * zc + dg + c4);
-                D0 = D1 + 8.f * hxy;
-                D1 = (dg - c4) - 8.f * zc;
+                const V c4 = (lds_v<V>(Jz, c + 1 + TB_X, LR0) + lds_v<V>(Jz, c + 1 - TB_X, LR0)) +
+                             (lds_v<V>(Jz, c - 1 + TB_X, LR0) + lds_v<V>(Jz, c - 1 - TB_X, LR0));
+                dd = D0 + (vfma(zc, 8.f, dg) + c4);
+                D0 = vfma(hxy, 8.f, D1);
+                D1 = vfma(zc, -8.f, dg - c4);
             } else {
-                const float z4 = (Jz[c + 1] + Jz[c - 1]) + (Jz[c + TB_X] + Jz[c - TB_X]);
-                dd = D0 + (2.f * zc + hxy + z4);
-                D0 = D1 + (2.f * hxy + dg);
-                D1 = hxy - z4 - 2.f * zc;
+                const V z4 = (lds_v<V>(Jz, c + 1, LR0) + lds_v<V>(Jz, c - 1, LR0)) +
+                             (lds_v<V>(Jz, c + TB_X, LR0) + lds_v<V>(Jz, c - TB_X, LR0));
+                dd = D0 + (vfma(zc, 2.f, hxy) + z4);
+                D0 = D1 + vfma(hxy, 2.f, dg);
+                D1 = vfma(zc, -2.f, hxy - z4);
             }
-            float dn = 0.f;
+            V dn = zero;
             if (NOISE) {
                 const float *Xx = sX + (q & 1) * 3 * TJ_N, *Xy = Xx + TJ_N, *Xz = Xy + TJ_N;
-                const float nxy = (Xx[c + 1] - Xx[c - 1]) + (Xy[c + TB_X] - Xy[c - TB_X]);
-                const float ng = ((Xx[c + 1 + TB_X] + Xy[c + 1 + TB_X]) - (Xx[c - 1 - TB_X] + Xy[c - 1 - TB_X])) +
-                                 ((Xx[c + 1 - TB_X] - Xy[c + 1 - TB_X]) - (Xx[c - 1 + TB_X] - Xy[c - 1 + TB_X]));
-                const float nzc = Xz[c];
+                const V nxy = (lds_v<V>(Xx, c + 1, LR0) - lds_v<V>(Xx, c - 1, LR0)) +
+                              (lds_v<V>(Xy, c + TB_X, LR0) - lds_v<V>(Xy, c - TB_X, LR0));
+                const V ng = ((lds_v<V>(Xx, c + 1 + TB_X, LR0) + lds_v<V>(Xy, c + 1 + TB_X, LR0)) -
+                              (lds_v<V>(Xx, c - 1 - TB_X, LR0) + lds_v<V>(Xy, c - 1 - TB_X, LR0))) +
+                             ((lds_v<V>(Xx, c + 1 - TB_X, LR0) - lds_v<V>(Xy, c + 1 - TB_X, LR0)) -
+                              (lds_v<V>(Xx, c - 1 + TB_X, LR0) - lds_v<V>(Xy, c - 1 + TB_X, LR0)));
+                const V nzc = lds_v<V>(Xz, c, LR0);
                 if (Q15) {
-                    const float n4 = (Xz[c + 1 + TB_X] + Xz[c + 1 - TB_X]) + (Xz[c - 1 + TB_X] + Xz[c - 1 - TB_X]);
-                    dn = N0 + (8.f * nzc + ng + n4);
-                    N0 = N1 + 8.f * nxy;
-                    N1 = (ng - n4) - 8.f * nzc;
+                    const V n4 = (lds_v<V>(Xz, c + 1 + TB_X, LR0) + lds_v<V>(Xz, c + 1 - TB_X, LR0)) +
+                                 (lds_v<V>(Xz, c - 1 + TB_X, LR0) + lds_v<V>(Xz, c - 1 - TB_X, LR0));
+                    dn = N0 + (vfma(nzc, 8.f, ng) + n4);
+                    N0 = vfma(nxy, 8.f, N1);
+                    N1 = vfma(nzc, -8.f, ng - n4);
                 } else {
-                    const float nz4 = (Xz[c + 1] + Xz[c - 1]) + (Xz[c + TB_X] + Xz[c - TB_X]);
-                    dn = N0 + (2.f * nzc + nxy + nz4);
-                    N0 = N1 + (2.f * nxy + ng);
-                    N1 = nxy - nz4 - 2.f * nzc;
+                    const V nz4 = (lds_v<V>(Xz, c + 1, LR0) + lds_v<V>(Xz, c - 1, LR0)) +
+                                  (lds_v<V>(Xz, c + TB_X, LR0) + lds_v<V>(Xz, c - TB_X, LR0));
+                    dn = N0 + (vfma(nzc, 2.f, nxy) + nz4);
+                    N0 = N1 + vfma(nxy, 2.f, ng);
+                    N1 = vfma(nzc, -2.f, nxy - nz4);
                 }
             }
             const int z = q - 1;
-            if (z >= z0 && active) {
-                const float Dd = dd * DIV;
-                const int si = x + g.nx * (y + g.ny * z);
-                const float Dn = (STAGE == 1 && NOISE) ? dn * DIV : 0.f;
-                const float pv = STAGE == 1 ? tps[s3 * TP_SLOT + (tx + 4) + TB_X * (ty + 3)] : 0.f;
-                float out;
+            if (z >= z0) {
+                // Runge-Kutta stage output (Sec. V; the noise increment held fixed):
+                //   Euler / Heun: stage 1 psi + D + eta (Heun also E = psi + D/2 + eta),
+                //     stage 2 E + D/2;
+                //   RK4 (k_s = D_s + eta): stage 1 psi + k1/2 with E = psi + eta + D1/6
+                //     and the increment kept; stages 2, 3 psi^n + k2/2, psi^n + k3 with
+                //     E += D_s/3; stage 4 E + D4/6.
+                const V Dd = vmul_sep(dd, DIV);  // rounded before the adds below
+                const V Dn = (STAGE == 1 && NOISE) ? vmul_sep(dn, DIV) : zero;
+                const V pv = STAGE == 1 ? lds_v<V>(tps + s3 * TP_SLOT, (tx + 4) + TB_X * (ty + 3), LR0) : zero;
+                V out, Ew = zero;
+                bool wE = false, wN = false;
                 if (STAGE == 2 && !rk4) {
-                    out = e_pre + 0.5f * Dd;
+                    out = vfma(Dd, 0.5f, vmake<V>(e_pre));
                 } else if (STAGE == 2 && rk4 == 4) {
-                    out = e_pre + (1.f / 6.f) * Dd;
-                } else if (STAGE == 2 && rk4 >= 2) {  // stages 2 and 3: E += D/3, out = psi^n + c (D + eta)
-                    a.E[si] = e_pre + (1.f / 3.f) * Dd;
-                    out = rk4 == 2 ? b_pre + 0.5f * (Dd + n_pre) : b_pre + Dd + n_pre;
-                } else {
-                    out = rk_stage_out<STAGE, COH, RK>(a, x, y, z, si, pv, Dd, Dn);
+                    out = vfma(Dd, 1.f / 6.f, vmake<V>(e_pre));
+                } else if (STAGE == 2 && rk4 >= 2) {  // stages 2 and 3
+                    Ew = vfma(Dd, 1.f / 3.f, vmake<V>(e_pre));
+                    wE = true;
+                    const V bn = vmake<V>(b_pre), nn = vmake<V>(n_pre);
+                    out = rk4 == 2 ? vfma(Dd + nn, 0.5f, bn) : (bn + Dd) + nn;
+                } else if (RK && rk4 == 1) {  // RK4 stage 1
+                    Ew = vfma(Dd, 1.f / 6.f, pv + Dn);
+                    wE = wN = true;
+                    out = vfma(Dd + Dn, 0.5f, pv);
+                } else {  // Euler / Heun stage 1
+                    if (a.heun) {
+                        Ew = vfma(Dd, 0.5f, pv) + Dn;
+                        wE = true;
+                    }
+                    out = (pv + Dd) + Dn;
                 }
-                if (col_inner && z >= 3 && z < g.nz - 3)
-                    a.out[col_off + g.px * g.py * (z + g.gz)] = out;
-                else
-                    store_padded(a.out, g, x, y, z, out, 3);
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    if (!act[l]) continue;
+                    const int si = x + g.nx * (yl[l] + g.ny * z);
+                    if (wE) a.E[si] = Ew.lane(l);
+                    if (wN) a.Dn[si] = Dn.lane(l);
+                    if (inner[l] && z >= 3 && z < g.nz - 3)
+                        a.out[coff[l] + g.px * g.py * (z + g.gz)] = out.lane(l);
+                    else
+                        store_padded(a.out, g, x, yl[l], z, out.lane(l), 3);
+                }
             }
         }
         r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
