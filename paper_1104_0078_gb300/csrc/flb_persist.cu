@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(PB_NT, 2) persist_kernel(const PersistArgs P)
 
 size_t persist_smem_bytes()
 {
-    const size_t f = FV_SMEM_FLOATS > FV_MU_SMEM_FLOATS ? FV_SMEM_FLOATS : FV_MU_SMEM_FLOATS;
+    const size_t f = fv_smem_floats<F1>() > fv_mu_smem_floats<F1>() ? fv_smem_floats<F1>() : fv_mu_smem_floats<F1>();
     return sizeof(float) * (f + (size_t)FV_NOISE_FLOATS);
 }
 

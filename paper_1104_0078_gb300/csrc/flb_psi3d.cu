@@ -298,7 +298,8 @@ cudaError_t launch_lb15_batch(const BatchLists &L, int storage, bool ghost, bool
 template <bool Q15>
 static cudaError_t batch_psi(const BatchLists &L, bool heun, bool noise, bool mu_in, cudaStream_t st)
 {
-    const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS, smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS;
+    const size_t sm = sizeof(float) * (size_t)fv_smem_floats<StageV>();
+    const size_t smm = sizeof(float) * (size_t)fv_mu_smem_floats<StageV>();
     const size_t nb = sizeof(float) * FV_NOISE_FLOATS;
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -394,7 +395,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int q, int stage, bool noise
     ta.a = a;
     ta.status = status;
     const dim3 grid((g.nx + PS_TX - 1) / PS_TX, (g.ny + PS_TY - 1) / PS_TY, (g.nz + a.zc - 1) / a.zc);
-    const size_t sm = sizeof(float) * (size_t)FV_SMEM_FLOATS;
+    const size_t sm = sizeof(float) * (size_t)fv_smem_floats<StageV>();
     auto go = [&](auto kernel, size_t bytes) {
         cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (r != cudaSuccess) return r;
@@ -402,7 +403,7 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int q, int stage, bool noise
         return cudaGetLastError();
     };
     const size_t smn = sm + sizeof(float) * FV_NOISE_FLOATS;
-    const size_t smm = sizeof(float) * (size_t)FV_MU_SMEM_FLOATS, smmn = smm + sizeof(float) * FV_NOISE_FLOATS;
+    const size_t smm = sizeof(float) * (size_t)fv_mu_smem_floats<StageV>(), smmn = smm + sizeof(float) * FV_NOISE_FLOATS;
     if (q == 15) {  // D3Q15 (the RK4 branches compiled into RK4 launches only, as below)
         if (stage == 2) return a.rk4 ? go(psi3_fv_tma_kernel<2, false, true, false, true>, sm)
                                      : go(psi3_fv_tma_kernel<2, false, false, false, true>, sm);

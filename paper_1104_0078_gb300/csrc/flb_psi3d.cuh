@@ -96,10 +96,20 @@ constexpr int TU_SLOT = ((TU_N * 4 + 127) / 128) * 32;
 constexpr int TM_N = TB_X * H2Y;                           // mu plane / slot floats
 constexpr int TM_SLOT = ((TM_N * 4 + 127) / 128) * 32;
 constexpr int TJ_N = TB_X * H1Y;                           // flux / noise plane floats (one component)
-constexpr int T_PSI_DEPTH = 6, T_U_DEPTH = 3, T_MU_DEPTH = 3;
+constexpr int T_U_DEPTH = 3, T_MU_DEPTH = 3;
+// psi ring slots: planes p-2SK-1 .. p+2 of an iteration (SK, the phase skew of
+// psi3_fv_tma_block: 2 for row pairs, 1 for one point per thread)
+template <class V>
+__host__ __device__ constexpr int psi_ring() { return V::L == 2 ? 8 : 6; }
 
-constexpr int FV_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * TM_N + 6 * TJ_N;
-constexpr int FV_MU_SMEM_FLOATS = T_PSI_DEPTH * TP_SLOT + T_U_DEPTH * TU_SLOT + T_MU_DEPTH * TM_SLOT + 6 * TJ_N;
+// dynamic shared memory of a stage block (floats), without and with the mu ring
+template <class V>
+constexpr int fv_smem_floats() { return psi_ring<V>() * TP_SLOT + T_U_DEPTH * TU_SLOT + 2 * TM_N + 6 * TJ_N; }
+template <class V>
+constexpr int fv_mu_smem_floats()
+{
+    return psi_ring<V>() * TP_SLOT + T_U_DEPTH * TU_SLOT + T_MU_DEPTH * TM_SLOT + 6 * TJ_N;
+}
 constexpr int FV_NOISE_FLOATS = 6 * TJ_N;
 
 // Lane-generic access to a shared-memory plane: lane l of the value at index c
@@ -187,13 +197,14 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     constexpr int SS2 = (H2X * HH2 + NT - 1) / NT, SS1 = (H1X * HH1 + NT - 1) / NT;
     if (status && *(volatile int *)status != 0) return;  // an earlier block timed out: skip the work
     const int rk4 = RK ? a.rk4 : 0;                       // RK false: a launch without RK4
-    float *tps = tsmem;                                   // [T_PSI_DEPTH][TP_SLOT]
-    float *tus = tps + T_PSI_DEPTH * TP_SLOT;            // [T_U_DEPTH][TU_SLOT]
+    constexpr int TD = psi_ring<V>();
+    float *tps = tsmem;                                   // [TD][TP_SLOT]
+    float *tus = tps + TD * TP_SLOT;                     // [T_U_DEPTH][TU_SLOT]
     float *smu = tus + T_U_DEPTH * TU_SLOT;              // [2][TM_N]    mu plane, by parity
     float *tms = smu;                                    // MU_IN: [T_MU_DEPTH][TM_SLOT] instead
     float *sJ = smu + (MU_IN ? T_MU_DEPTH * TM_SLOT : 2 * TM_N);  // [2][3][TJ_N] flux plane, by parity
     float *sX = sJ + 6 * TJ_N;                           // [2][3][TJ_N] noise plane, by parity (NOISE)
-    __shared__ __align__(8) uint64_t bar_p[T_PSI_DEPTH], bar_u[T_U_DEPTH], bar_m[T_MU_DEPTH];
+    __shared__ __align__(8) uint64_t bar_p[TD], bar_u[T_U_DEPTH], bar_m[T_MU_DEPTH];
     __shared__ int s_bad;
     const Geom &g = a.g;
     const int tx = threadIdx.x % PS_TX, ty = threadIdx.x / PS_TX;  // lane l's output row: ty + l TY/2
@@ -254,7 +265,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     V D0 = zero, D1 = zero, N0 = zero, N1 = zero;  // 12 (24) div of the flux / noise of planes q-1 and q
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < T_PSI_DEPTH; ++s) mbar_init(&bar_p[s], 1);
+        for (int s = 0; s < TD; ++s) mbar_init(&bar_p[s], 1);
         for (int s = 0; s < T_U_DEPTH; ++s) mbar_init(&bar_u[s], 1);
         if (MU_IN)
             for (int s = 0; s < T_MU_DEPTH; ++s) mbar_init(&bar_m[s], 1);
@@ -263,7 +274,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
     }
     __syncthreads();
     auto issue_psi = [&](int pp) {
-        const int s = (pp - pbase) % T_PSI_DEPTH;
+        const int s = (pp - pbase) % TD;
         mbar_expect_tx(&bar_p[s], TP_N * 4);
         tma_load_3d(tps + s * TP_SLOT, psi_map, &bar_p[s], x0, y0, pp + g.gz);
     };
@@ -277,43 +288,60 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
         mbar_expect_tx(&bar_m[s], TM_N * 4);
         tma_load_3d(tms + s * TM_SLOT, mu_map, &bar_m[s], x0, y0 + GY - 2, mm + g.gz);
     };
-    if (threadIdx.x == 0) {
-        issue_psi(pbase);
-        issue_psi(pbase + 1);
-    }
-    int last_p = pbase + 1, last_u = ubase - 1, last_m = mbase - 1;  // highest plane issued (thread 0)
+    constexpr int SK = L == 2 ? 2 : 1;  // phase skew (below)
+    static_assert(TD >= 2 * SK + 4, "psi ring holds planes p-2SK-1 .. p+2");
+    if (threadIdx.x == 0)
+        for (int k = 0; k <= SK; ++k) issue_psi(pbase + k);
+    int last_p = pbase + SK, last_u = ubase - 1, last_m = mbase - 1;  // highest plane issued (thread 0)
     int waited_p = pbase - 1, waited_u = ubase - 1, waited_m = mbase - 1;
 
-    // Rotating ring positions, advanced once per plane (no divisions in the loop):
-    // psi plane p sits in slot r6 of phase ph6; the velocity of the next flux plane
-    // in slot ru of phase uph.
+    // Iteration p forms mu of plane p-1 (A), the flux of plane m-1 from mu of
+    // m = p-SK (B) and the output of plane q-1 from the flux of q = p-2 SK (C).
+    // SK = 2 (row pairs): each phase reads only what the previous iteration
+    // wrote, so one barrier per iteration suffices.  SK = 1 (one point per
+    // thread, the persistent kernel): two barriers per iteration, after A and
+    // after B, two planes fewer per z chunk and a ring of 6 slots.  Each refill
+    // (psi plane p+SK+1, u plane p+1-SK, mu plane p+2-SK) goes into slots read
+    // before the last barrier.  Ring positions rotate once per iteration (no
+    // divisions in the loop): psi plane p in slot r6 of phase ph6; the velocity
+    // and mu rings advance on use (slot ru / rm of phase uph / mph).
+    auto refill = [&](int p) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            const int pp = p + SK + 1, uu = p + 1 - SK, mm = p + 2 - SK;
+            if (pp <= z1 + 2) { issue_psi(pp); last_p = pp; }
+            if (a.advect && uu >= ubase && uu <= z1) { issue_u(uu); last_u = uu; }
+            if (MU_IN && mm >= mbase && mm <= z1 + 1) { issue_mu(mm); last_m = mm; }
+        }
+    };
     int r6 = 0, ph6 = 0, ru = 0, uph = 0, rm = 0, mph = 0;
-    for (int p = z0 - 3; p <= z1 + 2; ++p) {
-        const int s1 = r6 == 0 ? T_PSI_DEPTH - 1 : r6 - 1;  // psi slots of p-1, p-2, p-3
-        const int s2 = s1 == 0 ? T_PSI_DEPTH - 1 : s1 - 1;
-        const int s3 = s2 == 0 ? T_PSI_DEPTH - 1 : s2 - 1;
-        (void)s1;
+    for (int p = z0 - 3; p <= z1 + 2 * SK; ++p) {
+        const int s3 = r6 >= SK + 1 ? r6 - SK - 1 : r6 - SK - 1 + TD;  // psi slots of planes m-1 and q-1
+        const int s5 = r6 >= 2 * SK + 1 ? r6 - 2 * SK - 1 : r6 - 2 * SK - 1 + TD;
+        const int pe = p - 2 * SK - 1;  // this iteration's output plane
         // Heun stage 2 and RK4 stages 2-4: the accumulator E (and for RK4 stages 2
         // and 3 the noise increment and psi^n) of this iteration's output plane
-        // p-3 are loaded now, so that their latency hides behind the plane's work
+        // pe are loaded now, so that their latency hides behind the plane's work
         float e_pre[L], n_pre[L], b_pre[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             e_pre[l] = n_pre[l] = b_pre[l] = 0.f;
-            if (STAGE == 2 && act[l] && p - 3 >= z0) {
-                const int sp = x + g.nx * (yl[l] + g.ny * (p - 3));
+            if (STAGE == 2 && act[l] && pe >= z0) {
+                const int sp = x + g.nx * (yl[l] + g.ny * pe);
                 if (!rk4 || rk4 > 1) e_pre[l] = COH ? __ldcg(a.E + sp) : a.E[sp];
                 if (rk4 == 2 || rk4 == 3) {
-                    const int bp = g.pidx32(x, yl[l], p - 3);
+                    const int bp = g.pidx32(x, yl[l], pe);
                     n_pre[l] = COH ? __ldcg(a.Dn + sp) : a.Dn[sp];
                     b_pre[l] = COH ? __ldcg(a.base + bp) : a.base[bp];
                 }
             }
         }
         // (A) psi plane p has landed: its partials at the mu points, and mu of plane p-1
-        if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
-        waited_p = p;
-        if (!MU_IN) {
+        if (p <= z1 + 2) {
+            if (!mbar_wait(&bar_p[r6], ph6, status)) s_bad = 1;
+            waited_p = p;
+        }
+        if (!MU_IN && p <= z1 + 2) {
             const float *P = tps + r6 * TP_SLOT;
             float *dst = smu + ((p - 1) & 1) * TM_N;
             const bool emit = p - 1 >= z0 - 2;
@@ -341,17 +369,15 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 pd[j][1] = dc;
             }
         }
-        __syncthreads();  // mu plane p-1 complete; every read of the psi slot of p-4 and of the u slot of p-3 done
-        if (s_bad) break;
-        if (threadIdx.x == 0) {  // refill those slots: psi plane p+2 (used at p+2), u plane p (used at p+2),
-            fence_proxy_async();  // mu plane p+1 (used at p+2)
-            if (p + 2 <= z1 + 2) { issue_psi(p + 2); last_p = p + 2; }
-            if (a.advect && p >= ubase && p <= z1) { issue_u(p); last_u = p; }
-            if (MU_IN && p + 1 >= mbase && p + 1 <= z1 + 1) { issue_mu(p + 1); last_m = p + 1; }
+        if (SK == 1) {
+            __syncthreads();  // mu plane p-1 complete; the slots to refill read
+            if (s_bad) break;
+            refill(p);
         }
-        // (B) mu partials of plane m = p-1 at the flux points; flux (and noise) of plane m-1
-        const int m = p - 1;
-        if (m >= z0 - 2) {
+        // (B) mu partials of plane m = p-SK (complete since the last barrier) at the
+        // flux points; flux (and noise) of plane m-1
+        const int m = p - SK;
+        if (m >= z0 - 2 && m <= z1 + 1) {
             const bool emit = m - 1 >= z0 - 1;
             const float *uq = tus;
             if (emit && a.advect) {
@@ -369,7 +395,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 rm = rm == T_MU_DEPTH - 1 ? 0 : rm + 1;
                 mph ^= rm == 0;
             }
-            const float *ps = tps + s2 * TP_SLOT;  // psi plane m-1
+            const float *ps = tps + s3 * TP_SLOT;  // psi plane m-1
             float *J = sJ + ((m - 1) & 1) * 3 * TJ_N;
             float *X = sX + ((m - 1) & 1) * 3 * TJ_N;
             const int zid = g.nx * g.ny * wrapi(m - 1, g.nz);
@@ -435,10 +461,13 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 }
             }
         }
-        __syncthreads();  // flux plane p-2 complete
-        if (s_bad) break;
-        // (C) flux partials of plane q = p-2 at the tile point; the output of plane q-1 completes
-        const int q = p - 2;
+        if (SK == 1) {
+            __syncthreads();  // flux plane p-2 complete
+            if (s_bad) break;
+        }
+        // (C) flux partials of plane q = p-2 SK (complete since the last barrier) at
+        // the tile point; the output of plane q-1 completes
+        const int q = p - 2 * SK;
         if (q >= z0 - 1) {
             const int c = (tx + 4) + TB_X * (ty + 1);  // the tile point (lane 0) in the flux plane
             const float *Jx = sJ + (q & 1) * 3 * TJ_N, *Jy = Jx + TJ_N, *Jz = Jy + TJ_N;
@@ -497,7 +526,7 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 //     E += D_s/3; stage 4 E + D4/6.
                 const V Dd = vmul_sep(dd, DIV);  // rounded before the adds below
                 const V Dn = (STAGE == 1 && NOISE) ? vmul_sep(dn, DIV) : zero;
-                const V pv = STAGE == 1 ? lds_v<V>(tps + s3 * TP_SLOT, (tx + 4) + TB_X * (ty + 3), LR0) : zero;
+                const V pv = STAGE == 1 ? lds_v<V>(tps + s5 * TP_SLOT, (tx + 4) + TB_X * (ty + 3), LR0) : zero;
                 V out, Ew = zero;
                 bool wE = false, wN = false;
                 if (STAGE == 2 && !rk4) {
@@ -533,20 +562,27 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                 }
             }
         }
-        r6 = r6 == T_PSI_DEPTH - 1 ? 0 : r6 + 1;
+        if (SK == 2) {
+            // mu plane p-1 and flux plane p-3 complete; every read of the psi slot
+            // of p-5, of the u slot of p-3 and of the mu slot of p-2 done
+            __syncthreads();
+            if (s_bad) break;
+            refill(p);
+        }
+        r6 = r6 == TD - 1 ? 0 : r6 + 1;
         ph6 ^= r6 == 0;
     }
     // a bounded wait drains copies still in flight before the block exits
     if (threadIdx.x == 0) {
         for (int pp = waited_p + 1; pp <= last_p; ++pp)
-            mbar_wait(&bar_p[(pp - pbase) % T_PSI_DEPTH], ((pp - pbase) / T_PSI_DEPTH) & 1, nullptr);
+            mbar_wait(&bar_p[(pp - pbase) % TD], ((pp - pbase) / TD) & 1, nullptr);
         for (int qq = waited_u + 1; qq <= last_u; ++qq)
             mbar_wait(&bar_u[(qq - ubase) % T_U_DEPTH], ((qq - ubase) / T_U_DEPTH) & 1, nullptr);
         if (MU_IN)
             for (int mm = waited_m + 1; mm <= last_m; ++mm)
                 mbar_wait(&bar_m[(mm - mbase) % T_MU_DEPTH], ((mm - mbase) / T_MU_DEPTH) & 1, nullptr);
         // the barriers may be initialised again by a later task of a persistent block
-        for (int k = 0; k < T_PSI_DEPTH; ++k) mbar_inval(&bar_p[k]);
+        for (int k = 0; k < TD; ++k) mbar_inval(&bar_p[k]);
         for (int k = 0; k < T_U_DEPTH; ++k) mbar_inval(&bar_u[k]);
         if (MU_IN)
             for (int k = 0; k < T_MU_DEPTH; ++k) mbar_inval(&bar_m[k]);
