@@ -319,7 +319,7 @@ size_t carve_all(flb_handle &h, char *base)
         const Geom &g = r.g;
         constexpr int E = 2 * MU3_HALO;
         nmu += ((g.nx + E + MU_BX - 1) / MU_BX) * ((g.ny + E + MU_BY - 1) / MU_BY) * ((g.nz + E + MU_ZC - 1) / MU_ZC);
-        nlb += packed_blocks(g, LB_BX * LB_BY * LB_BZ);
+        nlb += packed_blocks(pair_geom(g), LBB_NT);
         npsi += ((g.nx + PS_TX - 1) / PS_TX) * ((g.ny + PS_TY - 1) / PS_TY) * ((g.nz + PS_ZC_MIN - 1) / PS_ZC_MIN);
     }
     h.b_nmu = nmu;
@@ -789,7 +789,7 @@ int batch_upload_lists(flb_handle *h)
     }
     const size_t nmu = v.size();
     for (int r = 0; r < (int)h->reps.size(); ++r)  // row-packed collide-stream / velocity blocks
-        for_packed_blocks(h->reps[(size_t)r].g, LB_BX * LB_BY * LB_BZ,
+        for_packed_blocks(pair_geom(h->reps[(size_t)r].g), LBB_NT,
                           [&](int x0, int y0, int z0) { v.push_back({r, x0, y0, z0}); });
     const size_t nlb = v.size() - nmu;
     for (int r = 0; r < (int)h->reps.size(); ++r) {

@@ -96,15 +96,16 @@ __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchList
     mu3_block<MU3_HALO>(r.lb.g, r.psi[par], const_cast<float *>(r.lb.mu), r.A, r.B, r.K, b.bx, b.by, b.bz);
 }
 
+// site pairs of the collide-stream's list, in packed FP32
 template <typename T, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel3_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(LBB_NT) vel3_batch_kernel(const BatchLists L)
 {
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
     batch_lb_args(L, L.reps[b.rep], sa);
-    int x, y, z;
-    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    if (packed_site<LB_BX * LB_BY * LB_BZ>(sa.g, b.bx, b.by, b.bz, tid, x, y, z)) vel3_site<T, FORCE, false>(sa, x, y, z);
+    int x, y, zl[2], nl;
+    if (packed_pair<LBB_NT>(sa.g, b.bx, b.by, b.bz, threadIdx.x, x, y, zl, nl))
+        vel3_sites<F2, T, FORCE, false>(sa, PlanesFromBase<T>{(const T *)sa.fout, nullptr, sa.g.n}, x, y, zl, nl);
 }
 
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)
@@ -147,7 +148,7 @@ cudaError_t launch_mu3_batch(const BatchLists &L, cudaStream_t st)
 
 cudaError_t launch_vel3_batch(const BatchLists &L, int storage, bool force, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 block(LBB_NT);
     if (storage == FLB_F16_DEV) {
         if (force) vel3_batch_kernel<__half, true><<<L.nlb, block, 0, st>>>(L);
         else vel3_batch_kernel<__half, false><<<L.nlb, block, 0, st>>>(L);

@@ -456,32 +456,61 @@ struct BatchBlock {
     int rep, bx, by, bz;
 };
 
-// Site k (0 <= k < B) of a row-packed block of B sites (the batched
-// collide-stream and velocity lists: B = 256, one site per thread; the
-// persistent kernel's tasks: B = 2048, four per thread).  The block starts at
-// (x0, y0, z0); a box with nx <= B packs B/nx whole x-rows into the block, a
-// wider box takes a B-site chunk of one row.  Rows run y-fastest and are
-// contiguous in the population planes, so a warp's loads stay coalesced.
-// False for an idle slot.
+// Site k (0 <= k < B) of a row-packed block of B sites (the persistent
+// kernel's tasks: B = 2048, four per thread).  The block starts at (x0, y0, z0);
+// a box with nx <= B packs B/nx whole x-rows into the block, a wider box takes
+// a B-site chunk of one row.  Rows run y-fastest and are contiguous in the
+// population planes, so a warp's loads stay coalesced.  False for an idle slot.
 template <int B>
-__device__ __forceinline__ bool packed_site(const Geom &g, int x0, int y0, int z0, int k, int &x, int &y, int &z)
+__device__ __forceinline__ bool packed_row(int nx, int ny, int nz, int x0, int y0, int z0, int k, int &x, int &y,
+                                           int &z)
 {
     int rl = 0;
-    if (g.nx <= B) {
-        rl = k / g.nx;
-        if (rl >= B / g.nx) return false;
-        x = k - rl * g.nx;
+    if (nx <= B) {
+        rl = k / nx;
+        if (rl >= B / nx) return false;
+        x = k - rl * nx;
     } else {
         x = x0 + k;
-        if (x >= g.nx) return false;
+        if (x >= nx) return false;
     }
     y = y0 + rl;
     z = z0;
-    while (y >= g.ny) {
-        y -= g.ny;
+    while (y >= ny) {
+        y -= ny;
         ++z;
     }
-    return z < g.nz;
+    return z < nz;
+}
+template <int B>
+__device__ __forceinline__ bool packed_site(const Geom &g, int x0, int y0, int z0, int k, int &x, int &y, int &z)
+{
+    return packed_row<B>(g.nx, g.ny, g.nz, x0, y0, z0, k, x, y, z);
+}
+
+// The batched collide-stream and velocity lists pack site pairs: the box's
+// planes taken two at a time, (z, z+1) for even z, so that a thread works two
+// sites in the lanes of packed FP32 as the plain kernels do.  Pair k of a block
+// of B pairs: lanes at planes zl[0] and zl[1] (= zl[0] for the last plane of an
+// odd nz, nl = 1).  The host builds the lists on pair_geom(g).
+constexpr int LBB_NT = LB_BX * LB_BY;  // pairs (threads) of a batched collide-stream block
+template <int B>
+__device__ __forceinline__ bool packed_pair(const Geom &g, int x0, int y0, int z0, int k, int &x, int &y, int zl[2],
+                                            int &nl)
+{
+    int zp;
+    if (!packed_row<B>(g.nx, g.ny, (g.nz + 1) >> 1, x0, y0, z0, k, x, y, zp)) return false;
+    const int z = 2 * zp;
+    nl = z + 1 < g.nz ? 2 : 1;
+    zl[0] = z;
+    zl[1] = z + nl - 1;
+    return true;
+}
+inline Geom pair_geom(const Geom &g)
+{
+    Geom h = g;
+    h.nz = (g.nz + 1) / 2;
+    return h;
 }
 
 // Entries of the row-packed list of one box for blocks of B sites (see packed_site).

@@ -1,5 +1,5 @@
-// flb_lb15.cu -- the D3Q15 collide-stream (plain mode: two sites per thread in
-// packed FP32; batched mode: one site per thread on row-packed lists) and the
+// flb_lb15.cu -- the D3Q15 collide-stream (two sites per thread in packed FP32,
+// on the box's tiles or on the batched mode's row-packed lists of site pairs) and the
 // velocity of the new fluid state, on the lattice of the paper's own runs (Sec.
 // VI).  The per-site work is in flb_site15.cuh.
 #include "flb_site15.cuh"
@@ -39,31 +39,32 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel15_kernel(const LBArgs
     vel15_site<T, FORCE>(a, x, y, z);
 }
 
-// ---- batched variants: block b of the launch works on the row-packed entry L.lb[b] ----
+// ---- batched variants: block b of the launch works on the row-packed entry L.lb[b]
+// of 128 site pairs (x, y, z), (x, y, z+1) ----
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, 4) lb15_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(LBB_NT, 7) lb15_batch_kernel(const BatchLists L)
 {
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
     batch_lb_args(L, L.reps[b.rep], sa);
-    int x, y, z;
-    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    if (!packed_site<LB_BX * LB_BY * LB_BZ>(sa.g, b.bx, b.by, b.bz, tid, x, y, z)) return;
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (sa.coupling & FLB_COUPLE_FORCE)) force3<false>(sa, x, y, z, Fx, Fy, Fz);
-    lb15_site<T, GHOST_RELAX, false, true>(sa, x, y, z, Fx, Fy, Fz);
+    int x, y, zl[2], nl;
+    if (!packed_pair<LBB_NT>(sa.g, b.bx, b.by, b.bz, threadIdx.x, x, y, zl, nl)) return;
+    F2 Fx = F2::bc(0.f), Fy = F2::bc(0.f), Fz = F2::bc(0.f);
+    if (FORCE && (sa.coupling & FLB_COUPLE_FORCE)) force3v<false>(sa, x, y, zl, Fx, Fy, Fz);
+    lb15_sites<F2, T, GHOST_RELAX, false, true>(sa, PlanesFromBase<T>{(const T *)sa.fin, (T *)sa.fout, sa.g.n}, x, y,
+                                                zl, nl, Fx, Fy, Fz);
 }
 
+// the velocity of the pair's sites, one after the other (one site per pass)
 template <typename T, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel15_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(LBB_NT) vel15_batch_kernel(const BatchLists L)
 {
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
     batch_lb_args(L, L.reps[b.rep], sa);
-    int x, y, z;
-    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    if (packed_site<LB_BX * LB_BY * LB_BZ>(sa.g, b.bx, b.by, b.bz, tid, x, y, z))
-        vel15_site<T, FORCE>(sa, x, y, z);
+    int x, y, zl[2], nl;
+    if (packed_pair<LBB_NT>(sa.g, b.bx, b.by, b.bz, threadIdx.x, x, y, zl, nl))
+        for (int l = 0; l < nl; ++l) vel15_site<T, FORCE>(sa, x, y, zl[l]);
 }
 
 }  // namespace
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ) vel15_batch_kernel(const 
 // the batched collide-stream and velocity of D3Q15 replicas (mu first when the force is coupled)
 cudaError_t launch_lb15_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 block(LBB_NT);
     if (force) {
         const cudaError_t e = launch_mu3_batch(L, st);
         if (e != cudaSuccess) return e;

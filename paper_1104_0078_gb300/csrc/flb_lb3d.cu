@@ -1,5 +1,5 @@
-// flb_lb3d.cu -- D3Q19 fused collide-stream, two sites per thread (plain mode)
-// or one (batched mode).
+// flb_lb3d.cu -- D3Q19 fused collide-stream, two sites per thread in packed FP32
+// (plain and batched modes).
 //
 // The kernel forms the force density of Sec. IV, F = -psi grad mu, from the mu
 // field (central difference, or the FV gradient of Eq. (fvgrad) when psi moves
@@ -41,24 +41,25 @@ __global__ void __launch_bounds__(LB_BX *LB_BY, 7)
     lb_sites<F2, T, GHOST_RELAX, false, false>(a, P, x, y, zl, nl, Fx, Fy, Fz);
 }
 
-// ---- batched variant: block b of the launch works on the row-packed entry L.lb[b] ----
+// ---- batched variant: block b of the launch works on the row-packed entry L.lb[b]
+// of 128 site pairs (x, y, z), (x, y, z+1), in packed FP32 as above ----
 template <typename T, bool GHOST_RELAX, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY *LB_BZ, 4) lb3_batch_kernel(const BatchLists L)
+__global__ void __launch_bounds__(LBB_NT, 7) lb3_batch_kernel(const BatchLists L)
 {
     __shared__ LBArgs sa;
     const BatchBlock b = L.lb[blockIdx.x];
     batch_lb_args(L, L.reps[b.rep], sa);
-    int x, y, z;
-    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
-    if (!packed_site<LB_BX * LB_BY * LB_BZ>(sa.g, b.bx, b.by, b.bz, tid, x, y, z)) return;
-    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    if (FORCE && (sa.coupling & FLB_COUPLE_FORCE)) force3<false>(sa, x, y, z, Fx, Fy, Fz);
-    lb_site<T, GHOST_RELAX, false, true>(sa, x, y, z, Fx, Fy, Fz);
+    int x, y, zl[2], nl;
+    if (!packed_pair<LBB_NT>(sa.g, b.bx, b.by, b.bz, threadIdx.x, x, y, zl, nl)) return;
+    F2 Fx = F2::bc(0.f), Fy = F2::bc(0.f), Fz = F2::bc(0.f);
+    if (FORCE && (sa.coupling & FLB_COUPLE_FORCE)) force3v<false>(sa, x, y, zl, Fx, Fy, Fz);
+    lb_sites<F2, T, GHOST_RELAX, false, true>(sa, PlanesFromBase<T>{(const T *)sa.fin, (T *)sa.fout, sa.g.n}, x, y,
+                                              zl, nl, Fx, Fy, Fz);
 }
 
 cudaError_t launch_lb3_batch(const BatchLists &L, int storage, bool ghost, bool force, cudaStream_t st)
 {
-    const dim3 block(LB_BX, LB_BY, LB_BZ);
+    const dim3 block(LBB_NT);
     if (force) {
         const cudaError_t e = launch_mu3_batch(L, st);
         if (e != cudaSuccess) return e;
