@@ -309,11 +309,14 @@ int flb_set_wait_limit(flb_handle *h, double seconds);
  * FLB_MODE_PLAIN per distinct replica configuration (box, lattice, scheme,
  * integrator, noise, advection) on that replica's psi stages; in
  * FLB_MODE_BATCHED and FLB_MODE_PERSISTENT one value for all replicas on the
- * batched psi launches.  The
+ * batched psi launches, then, deepest boxes first, one value per distinct box
+ * depth nz over the even splits ceil(nz / k), k = 1..16, the other depths held
+ * (kept when at least 1% faster).  The
  * timed launches write only step scratch and the spare psi buffer, so the state
  * (populations, psi, step counters, spectra) is unchanged.  cache_path (may be
  * NULL) names a text file of "key<TAB>planes" lines, keyed by the device name,
- * its SM count and the configuration: entries found there are applied without
+ * its SM count and the configuration (batched: one line for the shared value
+ * and one per box depth): entries found there are applied without
  * timing (unless flags has FLB_TUNE_FORCE), new results are appended.  An
  * unreadable or unwritable file only disables the cache.  Synchronising; call
  * with the handle's device current and outside stream capture.  2D replicas and

@@ -800,6 +800,14 @@ int batch_upload_lists(flb_handle *h)
                 for (int bx = 0; bx < (g.nx + PS_TX - 1) / PS_TX; ++bx) v.push_back({r, bx, by, bz});
     }
     const size_t npsi = v.size() - nmu - nlb;
+    // longest z chunks first: the block scheduler then ends the launch on short
+    // blocks instead of starting a long one last
+    auto planes = [&](const BatchBlock &b) {
+        const Rep &r = h->reps[(size_t)b.rep];
+        return std::min(r.zc, r.g.nz - b.bz * r.zc);
+    };
+    std::stable_sort(v.begin() + (std::ptrdiff_t)(nmu + nlb), v.end(),
+                     [&](const BatchBlock &a, const BatchBlock &b) { return planes(a) > planes(b); });
     if ((int)nmu != h->b_nmu || (int)nlb != h->b_nlb || (int)npsi > h->b_npsi_cap) return FLB_EINVAL;
     h->b_npsi = (int)npsi;
     int rc = cuerr(cudaMemcpyAsync(h->b_mu, v.data(), nmu * sizeof(BatchBlock), cudaMemcpyHostToDevice, h->st));
@@ -1626,32 +1634,68 @@ int flb_autotune(flb_handle *h, const char *cache_path, int32_t flags)
         char key[256];
         std::snprintf(key, sizeof key, "batched|%s|%zu|%016llx", dk.c_str(), h->reps.size(), (unsigned long long)hash);
         const bool heun = h->reps[0].p.integrator == FLB_HEUN;
-        int best = PS_ZC;
+        // the box depths present, deepest first
+        std::vector<int> depths;
+        for (const Rep &r : h->reps) depths.push_back(r.g.nz);
+        std::sort(depths.begin(), depths.end(), std::greater<int>());
+        depths.erase(std::unique(depths.begin(), depths.end()), depths.end());
+        auto set_depth = [&](int nz, int zc) {
+            for (Rep &r : h->reps)
+                if (r.g.nz == nz) r.zc = zc;
+        };
+        auto time_all = [&](float &t) {
+            batch_reset(h);
+            int e = batch_upload_lists(h);
+            if (e == FLB_OK) e = batch_upload_table(h);
+            if (e != FLB_OK) return e;
+            const BatchLists L = batch_lists(h);
+            t = time_launches(h, [&]() {
+                h->launches += heun ? 2 : 1;
+                return cuerr(launch_batch_psi(L, heun, noise, batch_mu_in(h), h->reps[0].q == 15, h->st));
+            }, reps);
+            return t < 0.f ? (int)FLB_ECUDA : (int)FLB_OK;
+        };
         const auto it = cache.find(key);
         if (it != cache.end()) {
-            best = it->second;
+            for (Rep &r : h->reps) r.zc = it->second;
+            for (int nz : depths) {  // per-depth refinements, where tuned
+                const auto d = cache.find(std::string(key) + "|nz" + std::to_string(nz));
+                if (d != cache.end()) set_depth(nz, d->second);
+            }
         } else {
+            // one value for every replica first
             float tbest = 0.f;
+            int best = PS_ZC;
             for (int zc : zc_candidates(nzmax)) {
                 for (Rep &r : h->reps) r.zc = zc;
-                batch_reset(h);
-                rc = batch_upload_lists(h);
-                if (rc == FLB_OK) rc = batch_upload_table(h);
-                if (rc != FLB_OK) return rc;
-                const BatchLists L = batch_lists(h);
-                const float t = time_launches(h, [&]() {
-                    h->launches += heun ? 2 : 1;
-                    return cuerr(launch_batch_psi(L, heun, noise, batch_mu_in(h), h->reps[0].q == 15, h->st));
-                }, reps);
-                if (t < 0.f) return FLB_ECUDA;
+                float t = 0.f;
+                if ((rc = time_all(t)) != FLB_OK) return rc;
                 if (tbest == 0.f || t < tbest) {
                     tbest = t;
                     best = zc;
                 }
             }
+            for (Rep &r : h->reps) r.zc = best;
             append_cache(cache_path, key, best);
+            // then each box depth on its own (the others held), over the chunk
+            // sizes that split it evenly, ceil(nz / k); kept when 1% faster
+            for (int nz : depths) {
+                int dbest = best;
+                for (int k = 1; k <= 16; ++k) {
+                    const int zc = (nz + k - 1) / k;
+                    if (zc < PS_ZC_MIN || zc == dbest || (k > 1 && zc == (nz + k - 2) / (k - 1))) continue;
+                    set_depth(nz, zc);
+                    float t = 0.f;
+                    if ((rc = time_all(t)) != FLB_OK) return rc;
+                    if (t < 0.99f * tbest) {
+                        tbest = t;
+                        dbest = zc;
+                    }
+                }
+                set_depth(nz, dbest);
+                append_cache(cache_path, std::string(key) + "|nz" + std::to_string(nz), dbest);
+            }
         }
-        for (Rep &r : h->reps) r.zc = best;
     } else {
         std::map<std::string, int> done;
         for (Rep &r : h->reps) {

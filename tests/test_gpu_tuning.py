@@ -83,9 +83,15 @@ def test_autotune_keeps_state_and_uses_cache(tmp_path, mode):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
     assert before[2] == after[2] == 2
-    assert all(c in (4, 8, 16, 32, 64) for c in chosen)
     lines = open(cache).read().splitlines()
-    assert len(lines) == (1 if mode == F.FLB_MODE_BATCHED else 2)
+    if mode == F.FLB_MODE_BATCHED:
+        # one shared value, then one per box depth: a listed value or an even split ceil(nz / k)
+        for c, p in zip(chosen, ps):
+            assert c in (4, 8, 16, 32, 64) or any(c == -(-p.nz // k) for k in range(1, 17))
+        assert len(lines) == 1 + len({p.nz for p in ps})
+    else:
+        assert all(c in (4, 8, 16, 32, 64) for c in chosen)
+        assert len(lines) == 2
     # a second handle of the same configuration takes the cached values without timing
     s2 = F.Solver(ps)
     s2.set_mode(mode)
