@@ -342,7 +342,8 @@ def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
     and the D3Q15 lattice (FD) on the n^3 quench; the quench with S(q) and the
     dynamic S(q, tau) (8 lags) sampled every 10 steps; the per-site general
     path of the paper's stencil studies: FD with the PK Laplacian, the naive
-    contrast scheme with the CD Laplacian, FV on D3Q15; and the D2Q9 path on an
+    contrast scheme with the CD Laplacian, FV on D3Q15; the single-pass Heun
+    step (both stages in one launch) of the FV and FD schemes; and the D2Q9 path on an
     (8n)^2 quench (same free energy, FD as in the 2D workload).  MLUPS and the
     fraction of the HBM roofline on the algorithmic bytes of that form."""
     import torch
@@ -359,6 +360,7 @@ def path_variants(F, I, local, steps, peak, n=512, only=(), autotune=True):
         (f"naive_cd_{n}", dict(cube, psi_scheme=F.FLB_NAIVE, laplacian=F.FLB_LAP_CD), 160),
         (f"d3q15_fv_{n}", dict(cube, q=15, psi_scheme=F.FLB_FV), 128),
         (f"heun_fused_{n}", dict(cube, psi_scheme=F.FLB_FV), 160, None, True),
+        (f"heun_fused_fd_{n}", dict(cube, psi_scheme=F.FLB_FD), 160, None, True),
         (f"d2q9_{8 * n}", dict(dim=2, q=9, nx=8 * n, ny=8 * n, nz=1, psi_scheme=F.FLB_FD), 80),
     ]
     if only:

@@ -328,11 +328,13 @@ int flb_set_tuning(flb_handle *h, int32_t rep, int32_t psi_zchunk);
 
 /* Single-pass Heun (tuning flag, default off): with on != 0 every replica's psi
  * step runs both Runge-Kutta stages of Sec. V in one launch by halo recompute:
- * stage 1 on the tile + 3 region, so that stage 2's stencils find psi* in the
- * block; psi* and the Heun accumulator stay in shared memory and only psi^n and u
- * are read.  The noise is the two-stage form's (same counters), so both forms
- * give the same step up to FP32 rounding.  Applies to D3Q19, FV, Heun, the SO
- * Laplacian, plain mode; the z chunk is flb_set_tuning's value.  Errors: EINVAL
+ * stage 1 on a halo of the tile (tile + 3 for the FV scheme, tile + 2 for FD),
+ * so that stage 2's stencils find psi* in the block; psi* and the Heun
+ * accumulator stay in shared memory and only psi^n and u are read.  The noise is
+ * the two-stage form's (same counters), so both forms give the same step up to
+ * FP32 rounding.  Applies to Heun with the SO Laplacian in plain mode: the FV
+ * scheme on D3Q19, the FD scheme on either lattice; the z chunk is
+ * flb_set_tuning's value.  Errors: EINVAL
  * (NULL handle), EUNSUPPORTED (on != 0 and some replica is not of that kind, or
  * the handle is not in plain mode).  Mode changes (flb_set_mode) turn it off. */
 int flb_set_psi_fused(flb_handle *h, int32_t on);

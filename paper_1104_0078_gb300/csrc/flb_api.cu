@@ -528,8 +528,8 @@ int launch_psi_stages(flb_handle *h, Rep &r)
         return FLB_OK;
     }
     if (r.fused && heun) {  // both stages in one launch (flb_set_psi_fused)
-        FLB_TRY(launch_psi3_heun1(r.g, psi_n, r.u, psi_np1, (float)p.A, (float)p.B, (float)p.K, (float)p.M,
-                                  (float)p.kT, advect, noisy, key, r.step, r.zc, st));
+        FLB_TRY(launch_psi3_heun1(r.g, p.psi_scheme, psi_n, r.u, psi_np1, (float)p.A, (float)p.B, (float)p.K,
+                                  (float)p.M, (float)p.kT, advect, noisy, key, r.step, r.zc, st));
         return FLB_OK;
     }
     FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
@@ -1753,8 +1753,9 @@ int flb_set_psi_fused(flb_handle *h, int32_t on)
         if (h->mode != FLB_MODE_PLAIN) return FLB_EUNSUPPORTED;
         for (const Rep &r : h->reps) {
             const flb_params &p = r.p;
-            if (r.dim != 3 || r.q != 19 || p.psi_scheme != FLB_FV || p.integrator != FLB_HEUN ||
-                p.laplacian != FLB_LAP_SO)
+            // FV: the D3Q19 operators; FD: either lattice (its operators are the SO stencils)
+            const bool fv = p.psi_scheme == FLB_FV && r.q == 19, fd = p.psi_scheme == FLB_FD;
+            if (r.dim != 3 || !(fv || fd) || p.integrator != FLB_HEUN || p.laplacian != FLB_LAP_SO)
                 return FLB_EUNSUPPORTED;
         }
     }

@@ -611,9 +611,9 @@ cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, 
 cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, const LapW &lw,
                       cudaStream_t s);
 // both Heun stages of the FV psi step in one launch by halo recompute (flb_heun1.cu)
-cudaError_t launch_psi3_heun1(const Geom &g, const float *psi, const float *u, float *out, float A, float B, float K,
-                              float M, float kT, int advect, bool noise, const PhiloxKey &key, int64_t step, int zc,
-                              cudaStream_t st);
+cudaError_t launch_psi3_heun1(const Geom &g, int scheme, const float *psi, const float *u, float *out, float A, float B,
+                              float K, float M, float kT, int advect, bool noise, const PhiloxKey &key, int64_t step,
+                              int zc, cudaStream_t st);
 // equilibrium start (flb_init.cu): populations into f (the current buffer), psi
 // (padded) through an inverse DFT whose intermediates use `spare` (>= 16 bytes
 // per site: the other population buffer)
