@@ -145,7 +145,9 @@ bool valid(const flb_params &p)
 // scheme) run the one-thread-per-site kernels of the 2D path.
 bool general_path(const flb_params &p)
 {
-    return p.dim == 3 && (p.laplacian != FLB_LAP_SO || p.psi_scheme == FLB_NAIVE);
+    // the tiled 3D kernels take the FD scheme with any Laplacian (class weights)
+    // and the FV scheme with the SO Laplacian
+    return p.dim == 3 && (p.psi_scheme == FLB_NAIVE || (p.laplacian != FLB_LAP_SO && p.psi_scheme != FLB_FD));
 }
 
 // Class weights of the App. A Laplacians (faces, edges, corners; 2D axes and
@@ -172,6 +174,15 @@ LapW lap_weights(int dim, int kind)
     w.c2 = (float)a2;
     w.c3 = (float)a3;
     return w;
+}
+
+// The class weights of a 3D replica's App. A Laplacian on the tiled FD path
+// (stored in w), or null for the SO Laplacian of the tiled kernels.
+const LapW *app_a_weights(const Rep &r, LapW &w)
+{
+    if (r.dim != 3 || r.p.laplacian == FLB_LAP_SO || r.p.psi_scheme != FLB_FD) return nullptr;
+    w = lap_weights(3, r.p.laplacian);
+    return &w;
 }
 
 Geom make_geom(const flb_params &p)
@@ -511,6 +522,8 @@ int launch_psi_stages(flb_handle *h, Rep &r)
 {
     const flb_params &p = r.p;
     cudaStream_t st = h->st;
+    LapW lwv{};
+    const LapW *lw = app_a_weights(r, lwv);
     float *psi_n = r.psi[r.pcur], *psi_np1 = r.psi[r.pcur ^ 1];
     const float *mu_n = (p.coupling & FLB_COUPLE_FORCE) && p.force_grad != FLB_FORCE_STRESS ? r.mu : nullptr;
     const bool noisy = p.kT > 0 && p.M > 0;
@@ -524,7 +537,7 @@ int launch_psi_stages(flb_handle *h, Rep &r)
         for (int s = 0; s < 4; ++s)
             FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, s == 0 ? 1 : 2, s == 0 && noisy, in[s], r.u, out[s], r.E,
                                 (float)p.A, (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, 0, key, r.step,
-                                r.zc, s + 1, psi_n, r.Dn, s == 0 ? mu_n : nullptr, h->status, st));
+                                r.zc, s + 1, psi_n, r.Dn, s == 0 ? mu_n : nullptr, h->status, st, lw));
         return FLB_OK;
     }
     if (r.fused && heun) {  // both stages in one launch (flb_set_psi_fused)
@@ -534,11 +547,11 @@ int launch_psi_stages(flb_handle *h, Rep &r)
     }
     FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, 1, noisy, psi_n, r.u, heun ? r.psis : psi_np1, r.E, (float)p.A,
                         (float)p.B, (float)p.K, (float)p.M, (float)p.kT, advect, heun ? 1 : 0, key, r.step, r.zc, 0,
-                        nullptr, nullptr, mu_n, h->status, st));
+                        nullptr, nullptr, mu_n, h->status, st, lw));
     if (heun)
         FLB_TRY(launch_psi3(r.g, p.psi_scheme, r.q, 2, false, r.psis, r.u, psi_np1, r.E, (float)p.A, (float)p.B,
                             (float)p.K, (float)p.M, (float)p.kT, advect, 1, key, r.step, r.zc, 0, nullptr, nullptr,
-                            nullptr, h->status, st));
+                            nullptr, h->status, st, lw));
     return FLB_OK;
 }
 
@@ -556,8 +569,10 @@ int step_rep3(flb_handle *h, Rep &r)
         const Range range("mu");
         if (p.force_grad == FLB_FORCE_STRESS)
             FLB_TRY(launch_sigma3(r.g, psi_n, r.sig, (float)p.A, (float)p.B, (float)p.K, st));
-        else
-            FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st));
+        else {
+            LapW lwv{};
+            FLB_TRY(launch_mu3(r.g, psi_n, r.mu, (float)p.A, (float)p.B, (float)p.K, st, app_a_weights(r, lwv)));
+        }
     }
     cudaEvent_t e1 = mark(h);
     {

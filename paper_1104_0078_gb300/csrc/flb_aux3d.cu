@@ -52,14 +52,14 @@ __global__ void __launch_bounds__(LB_BX *LB_BY) vel3_kernel(const LBArgs a)
 // takes 9 loads per plane instead of 27.
 template <int HALO = 1>
 __device__ __forceinline__ void mu3_block(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
-                                          float B, float K, int bx, int by, int bz)
+                                          float B, float K, int bx, int by, int bz, const LapW *lw = nullptr)
 {
     const int x = bx * MU_BX + (int)threadIdx.x - HALO;
     const int y = by * MU_BY + (int)threadIdx.y - HALO;
     const int zb = bz * MU_ZC - HALO;                       // first output plane
     const int ze = min(zb + MU_ZC, g.nz + HALO);            // one past the last
     if (x >= g.nx + HALO || y >= g.ny + HALO || zb >= ze) return;
-    mu3_column<false>(g, psi, mu, A, B, K, x, y, zb, ze);
+    mu3_column<false>(g, psi, mu, A, B, K, x, y, zb, ze, lw);
 }
 
 __global__ void __launch_bounds__(MU_BX *MU_BY) sigma3_kernel(const Geom g, const float *__restrict__ psi,
@@ -73,10 +73,12 @@ __global__ void __launch_bounds__(MU_BX *MU_BY) sigma3_kernel(const Geom g, cons
     sigma3_column<false>(g, psi, sig, A, B, K, x, y, zb, ze);
 }
 
+// W: the class weights lw of an App. A Laplacian (false: SO)
+template <bool W>
 __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const float *__restrict__ psi,
-                                                          float *__restrict__ mu, float A, float B, float K)
+                                                          float *__restrict__ mu, float A, float B, float K, const LapW lw)
 {
-    mu3_block<MU3_HALO>(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z);
+    mu3_block<MU3_HALO>(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z, W ? &lw : nullptr);
 }
 
 // ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
@@ -108,12 +110,14 @@ __global__ void __launch_bounds__(LBB_NT) vel3_batch_kernel(const BatchLists L)
         vel3_sites<F2, T, FORCE, false>(sa, PlanesFromBase<T>{(const T *)sa.fout, nullptr, sa.g.n}, x, y, zl, nl);
 }
 
-cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st)
+cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st,
+                       const LapW *lw)
 {
     const dim3 block(MU_BX, MU_BY, 1);
     constexpr int E = 2 * MU3_HALO;
     const dim3 grid((g.nx + E + MU_BX - 1) / MU_BX, (g.ny + E + MU_BY - 1) / MU_BY, (g.nz + E + MU_ZC - 1) / MU_ZC);
-    mu3_kernel<<<grid, block, 0, st>>>(g, psi, mu, A, B, K);
+    if (lw) mu3_kernel<true><<<grid, block, 0, st>>>(g, psi, mu, A, B, K, *lw);
+    else mu3_kernel<false><<<grid, block, 0, st>>>(g, psi, mu, A, B, K, LapW{0.f, 0.f, 0.f, 0.f});
     return cudaGetLastError();
 }
 

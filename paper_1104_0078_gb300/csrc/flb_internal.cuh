@@ -603,9 +603,11 @@ cudaError_t launch_vel2(const LBArgs &a, int storage, cudaStream_t s);
 cudaError_t launch_psi3(const Geom &g, int scheme, int q, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
                         const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
-                        const float *mu_in, int *status, cudaStream_t st);
+                        const float *mu_in, int *status, cudaStream_t st, const LapW *lw = nullptr);
 // mu on the interior and MU3_HALO = 2 ghost layers of a 3D box (flb_aux3d.cu)
-cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st);
+// lw: the class weights of an App. A Laplacian (null: SO)
+cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st,
+                       const LapW *lw = nullptr);
 cudaError_t launch_init_eq(const Geom &g, int q, int storage, const float *rho, const float *u, float rho0, void *f,
                            cudaStream_t st);
 cudaError_t launch_mu(const Geom &g, const float *psi, float *mu, float A, float B, float K, const LapW &lw,

@@ -8,10 +8,13 @@
 
 namespace flb {
 
-// The column (x, y), output planes zb .. ze-1 of the mu field.
+// The column (x, y), output planes zb .. ze-1 of the mu field.  lw (may be
+// null): the class weights of an App. A Laplacian instead of SO's,
+// mu = A psi + B psi^3 - K [(c1 n1 + c2 n2) + (c3 n3 + c0 psi)] over the faces
+// n1, edges n2 and corners n3 of the 3 x 3 x 3 neighbourhood.
 template <bool COH = false>
 __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restrict__ psi, float *__restrict__ mu, float A,
-                                           float B, float K, int x, int y, int zb, int ze)
+                                           float B, float K, int x, int y, int zb, int ze, const LapW *lw = nullptr)
 {
     const int Y = g.px, Z = g.px * g.py;
     const float k22 = K * (1.0f / 22.0f);
@@ -23,7 +26,8 @@ __device__ __forceinline__ void mu3_column(const Geom &g, const float *__restric
         const float d2 = (ldf<COH>(psi + c - 1 - Y) + ldf<COH>(psi + c + 1 - Y)) + (ldf<COH>(psi + c - 1 + Y) + ldf<COH>(psi + c + 1 + Y));
         if (p - 1 >= zb) {
             const float n1 = b1 + (a0 + a2), n2 = d1 + (b0 + b2), n3 = d0 + d2;
-            mu[c - Z] = mu_so(A, B, k22, a1, n1, n2, n3);
+            mu[c - Z] = lw ? A * a1 + B * a1 * a1 * a1 - K * ((lw->c1 * n1 + lw->c2 * n2) + (lw->c3 * n3 + lw->c0 * a1))
+                           : mu_so(A, B, k22, a1, n1, n2, n3);
         }
         a0 = a1; b0 = b1; d0 = d1;
         a1 = a2; b1 = b2; d1 = d2;

@@ -55,6 +55,22 @@ __device__ __forceinline__ float mu_point(const float *pm, const float *p0, cons
     return A * ps + B * ps * ps * ps - k22 * (6.f * n1 + 3.f * n2 + n3 - 80.f * ps);
 }
 
+// The same with the class weights w of an App. A Laplacian:
+// A psi + B psi^3 - K [(c1 n1 + c2 n2) + (c3 n3 + c0 psi)]
+template <int PX>
+__device__ __forceinline__ float mu_point_w(const float *pm, const float *p0, const float *pp, int c, float A, float B,
+                                            float K, const LapW &w)
+{
+    const float n1 = (p0[c - 1] + p0[c + 1]) + (p0[c - PX] + p0[c + PX]) + (pm[c] + pp[c]);
+    const float n2 = ((p0[c - 1 - PX] + p0[c + 1 - PX]) + (p0[c - 1 + PX] + p0[c + 1 + PX])) +
+                     ((pm[c - 1] + pm[c + 1]) + (pm[c - PX] + pm[c + PX])) +
+                     ((pp[c - 1] + pp[c + 1]) + (pp[c - PX] + pp[c + PX]));
+    const float n3 = ((pm[c - 1 - PX] + pm[c + 1 - PX]) + (pm[c - 1 + PX] + pm[c + 1 + PX])) +
+                     ((pp[c - 1 - PX] + pp[c + 1 - PX]) + (pp[c - 1 + PX] + pp[c + 1 + PX]));
+    const float ps = p0[c];
+    return A * ps + B * ps * ps * ps - K * ((w.c1 * n1 + w.c2 * n2) + (w.c3 * n3 + w.c0 * ps));
+}
+
 // Per-thread view of the block's halo regions, computed once: for every slot the
 // in-plane offset of the padded field it loads (psi, u) and the in-plane counter
 // id of its periodic image (noise).
@@ -184,13 +200,17 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a, con
             for (int j = 0; j < S1; ++j) {
                 const int c = R.c1[j];
                 if (c < 0) continue;
-                dst[c] = MU_IN ? mcur[j] : mu_point<H3X>(pm, p0, pp, R.p1[j], a.A, a.B, k22);
+                dst[c] = MU_IN      ? mcur[j]
+                         : a.lap_w ? mu_point_w<H3X>(pm, p0, pp, R.p1[j], a.A, a.B, a.K, a.lw)
+                                   : mu_point<H3X>(pm, p0, pp, R.p1[j], a.A, a.B, k22);
             }
             if (NOISE) {
                 const int zid = g.nx * g.ny * wrapi(q, g.nz);
-                // sqrt(2 kT M a_l) for the face, edge and corner half-links
-                const float s1 = sqrtf(2.0f * a.kT * a.M * (6.f / 22.f)), s2 = sqrtf(2.0f * a.kT * a.M * (3.f / 22.f));
-                const float s3 = sqrtf(2.0f * a.kT * a.M * (1.f / 22.f));
+                // sqrt(2 kT M a_l) for the face, edge and corner half-links (a_l the
+                // Laplacian's class weights: 6/22, 3/22, 1/22 for SO)
+                const float s1 = sqrtf(2.0f * a.kT * a.M * (a.lap_w ? a.lw.c1 : 6.f / 22.f));
+                const float s2 = sqrtf(2.0f * a.kT * a.M * (a.lap_w ? a.lw.c2 : 3.f / 22.f));
+                const float s3 = sqrtf(2.0f * a.kT * a.M * (a.lap_w ? a.lw.c3 : 1.f / 22.f));
 #pragma unroll
                 for (int j = 0; j < S1; ++j) {
                     if (R.c1[j] < 0) continue;
@@ -228,7 +248,8 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a, con
         if (out_here) {
             const float *mm = smu + ring3(z - 1) * H2N, *m0 = smu + ring3(z) * H2N, *mp = smu + ring3(z + 1) * H2N;
             const int c = (tx + 2) + H2X * (ty + 2);
-            float D = a.M * mu_point<H2X>(mm, m0, mp, c, 0.f, 0.f, -1.0f / 22.0f);
+            float D = a.M * (a.lap_w ? mu_point_w<H2X>(mm, m0, mp, c, 0.f, 0.f, -1.0f, a.lw)
+                                     : mu_point<H2X>(mm, m0, mp, c, 0.f, 0.f, -1.0f / 22.0f));
             if (a.advect) {
                 const float *P0 = sps + ring4(z) * H3N, *Pm = sps + ring4(z - 1) * H3N, *Pp = sps + ring4(z + 1) * H3N;
                 const int cp = (tx + 3) + H3X * (ty + 3);
@@ -434,10 +455,13 @@ static cudaError_t launch_fv_tma(const Psi3Args &a, int q, int stage, bool noise
 cudaError_t launch_psi3(const Geom &g, int scheme, int q, int stage, bool noise, const float *psi, const float *u,
                         float *out, float *E, float A, float B, float K, float M, float kT, int advect, int heun,
                         const PhiloxKey &key, int64_t step, int zc, int rk4, const float *base, float *Dn,
-                        const float *mu_in, int *status, cudaStream_t st)
+                        const float *mu_in, int *status, cudaStream_t st, const LapW *lw)
 {
     if (zc < PS_ZC_MIN) return cudaErrorInvalidValue;
+    if (lw && scheme != FLB_FD) return cudaErrorInvalidValue;  // App. A Laplacians: the FD stage only
     Psi3Args a;
+    a.lap_w = lw ? 1 : 0;
+    a.lw = lw ? *lw : LapW{0.f, 0.f, 0.f, 0.f};
     a.rk4 = rk4;
     a.base = base;
     a.Dn = Dn;

@@ -29,6 +29,8 @@ struct Psi3Args {
     float *Dn;         // RK4: [N] noise increment, written in stage 1, read in stages 2, 3
     PhiloxKey key;
     int64_t step;
+    LapW lw;           // FD: the class weights of an App. A Laplacian when lap_w (else SO's)
+    int lap_w;
 };
 
 // Output of a Runge-Kutta stage at interior site (x, y, z), site index si: pv the
@@ -611,6 +613,7 @@ __device__ __forceinline__ void psi_batch_args(const BatchRep &r, long long ds, 
     sa.Dn = nullptr;
     sa.key = r.lb.key;
     sa.step = r.lb.step + ds;
+    sa.lap_w = 0;
 }
 
 }  // namespace flb
