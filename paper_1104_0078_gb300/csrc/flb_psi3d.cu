@@ -281,7 +281,7 @@ struct TmaArgs {
 
 // MU_IN: stage 1 reads mu of its input from mu_map instead of forming it; Q15:
 // the FV operators of D3Q15
-// 256 threads, each on a pair of output rows in packed FP32 (F2)
+// 256 threads, each on point pairs (y, y + H/2) of every region in packed FP32 (F2)
 using StageV = F2;
 template <int STAGE, bool NOISE, bool RK, bool MU_IN, bool Q15 = false>
 __global__ void __launch_bounds__(stage_threads<StageV>(), 2) psi3_fv_tma_kernel(const __grid_constant__ CUtensorMap psi_map,

@@ -172,8 +172,10 @@ __host__ __device__ constexpr int stage_threads() { return V::L == 1 ? PS_NT : P
 // Lanes: with V = F2 a thread works the point pairs (x, y) and (x, y + H/2) of
 // every region of height H (mu 20, flux 18, tile 16 rows) in the two lanes of
 // packed FP32 registers, and the block has 256 threads; with V = F1 one point
-// and 512 threads.  Every FP32 operation is explicitly rounded, so both give
-// the same bits; the random numbers, the loads and the stores run per lane.
+// and 512 threads.  Every FP32 operation is explicitly rounded (a product by a
+// scalar that feeds an add is formed per lane, vmul_sep of flb_lane.cuh), so
+// both give the same bits; the random numbers, the loads and the stores run per
+// lane.
 //
 // Q15: the FV operators of D3Q15 (faces w = 1/9, corners 1/72), in units of 1/24:
 //   24 grad mu (q): x: 8 ex(q) + Dx(q-1) + Dx(q+1),  y: likewise,

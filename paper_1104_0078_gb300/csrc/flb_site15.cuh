@@ -275,8 +275,8 @@ __device__ __forceinline__ void vel15_site_on(const LBArgs &a, const PL &P, int 
     store_padded(a.u + 2 * g.pn, g, x, y, z, (jz + 0.5f * Fz) * irho, 1);
 }
 
-// One site's collide-stream on the planes of a.fin and a.fout (the batched and
-// persistent kernels, one site per thread).
+// One site's collide-stream on the planes of a.fin and a.fout (the persistent
+// kernel, one site per thread).
 template <typename T, bool GHOST_RELAX, bool COH = false, bool KEY_R0 = false>
 __device__ __forceinline__ void lb15_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
 {

@@ -198,7 +198,7 @@ __device__ __forceinline__ void force3v(const LBArgs &a, int x, int y, const int
     }
 }
 
-// One site's force (the kernels that work one site per thread).
+// One site's force (the persistent kernel, one site per thread).
 template <bool COH = false>
 __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, float &Fx, float &Fy, float &Fz)
 {
@@ -435,7 +435,7 @@ __device__ __forceinline__ void lb_sites(const LBArgs &a, const PL &P, int x, in
     }
 }
 
-// One site on the planes of a.fin and a.fout (one site per thread).
+// One site on the planes of a.fin and a.fout (the persistent kernel, one site per thread).
 template <typename T, bool GHOST_RELAX, bool COH = false, bool KEY_R0 = false>
 __device__ __forceinline__ void lb_site(const LBArgs &a, int x, int y, int z, float Fx, float Fy, float Fz)
 {
