@@ -62,7 +62,7 @@ def test_batched_row_packing_of_wide_and_narrow_boxes_equals_plain():
     # last pair with one plane) or take 128-pair chunks of a row (nx = 300: two
     # full chunks and a partial one; nx = 129: a full chunk and a 1-pair one);
     # every field must still agree bitwise with the plain launches
-    shapes = [(4, 4, 5), (5, 7, 4), (100, 6, 5), (300, 4, 4), (129, 3, 3)]
+    shapes = [(4, 4, 5), (5, 7, 4), (100, 6, 5), (300, 4, 4), (129, 4, 5)]
     ps = [flb_params(dict(dim=3, q=19, nx=nx, ny=ny, nz=nz, tau=0.8, kT=2e-5, A=0.05, B=0.2, K=0.04, M=0.1,
                           scheme=1, integrator=2, seed=300 + r)) for r, (nx, ny, nz) in enumerate(shapes)]
     plain, _, _ = _run(F.FLB_MODE_PLAIN, ps, 5)
