@@ -214,11 +214,13 @@ __device__ __forceinline__ void force3(const LBArgs &a, int x, int y, int z, flo
 // buffer of the step and the step's noise counter.
 __device__ __forceinline__ void batch_lb_args(const BatchLists &L, const BatchRep &r, LBArgs &sa)
 {
-    const int tid = threadIdx.x + LB_BX * (threadIdx.y + LB_BY * threadIdx.z);
+    // every thread of the block (whatever its shape) copies a strided share
+    const int nt = (int)(blockDim.x * blockDim.y * blockDim.z);
+    const int tid = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z));
     {
         const int *src = reinterpret_cast<const int *>(&r.lb);
         int *dst = reinterpret_cast<int *>(&sa);
-        for (int k = tid; k < (int)(sizeof(LBArgs) / sizeof(int)); k += LB_BX * LB_BY * LB_BZ) dst[k] = src[k];
+        for (int k = tid; k < (int)(sizeof(LBArgs) / sizeof(int)); k += nt) dst[k] = src[k];
     }
     __syncthreads();
     if (tid == 0) {
