@@ -274,7 +274,12 @@ __global__ void __launch_bounds__(32 * DXW_WARPS) dft_x_warp_kernel(DftArgs a)
         v[j] = x < a.nx ? src[x] : 0.f;
     }
     const int nj = (a.nx + 31) / 32;
+    // the input is real, so X(-k) = conj X(k): of each pair of kept indices with
+    // k and -k (mod nx) only the first is summed, the other written as its conjugate
     for (int jx = 0; jx < a.Kx; ++jx) {
+        const int k = kval(jx, a.nx, a.Kx), kn = k == 0 ? 0 : a.nx - k;
+        const int jp = a.Kx >= a.nx ? kn : (kn == 0 ? 0 : (kn <= a.Kx / 2 ? kn : a.Kx - (a.nx - kn)));
+        if (jp < jx) continue;  // summed as the partner's conjugate
         float2 w = w0[jx][lane];
         const float2 r = rot[jx];
         float re = 0.f, im = 0.f;
@@ -293,7 +298,10 @@ __global__ void __launch_bounds__(32 * DXW_WARPS) dft_x_warp_kernel(DftArgs a)
             re += __shfl_xor_sync(0xffffffffu, re, o);
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) a.X1[row * a.Kx + jx] = make_float2(re, im);
+        if (lane == 0) {
+            a.X1[row * a.Kx + jx] = make_float2(re, im);
+            if (jp != jx) a.X1[row * a.Kx + jp] = make_float2(re, -im);
+        }
     }
 }
 
