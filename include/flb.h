@@ -400,12 +400,14 @@ int flb_structure_factor_noalloc(const float *psi_dev, int32_t nx, int32_t ny, i
  * counter-based normals, held fixed over each step's Runge-Kutta stages), for
  * tests and for users who reproduce a run's noise elsewhere.  For sites
  * site0 .. site0+nsites-1 and Philox blocks 0 .. nblocks-1 of (seed, step,
- * stream) it writes dev_out[s*4*nblocks + 4*b + j], j = 0..3: Box-Muller on
- * the words (x0, x1) and (x2, x3) of block b, each uniform ((x >> 9) + 1/2)
- * 2^-23, g = sqrt(-2 ln u0) (cos, sin)(2 pi u1).  Stream 0 feeds the
- * collide-stream (mode noise), stream 1 the psi equation; the site id of a
- * lattice point is x + nx*(y + ny*z).
- *   dev_out     : device pointer, FP32, nsites*4*nblocks values (caller-owned).
+ * stream) it writes dev_out[s*8*nblocks + 8*b + j], j = 0..7: normals 2k
+ * and 2k+1 of block b are Box-Muller on its word x_k (k = 0..3), with the
+ * radius uniform u = ((x_k >> 12) + 1/2) 2^-20 from the top 20 bits and the
+ * angle uniform v = ((x_k & 0xFFF) + 1/2) 2^-12 from the low 12 bits,
+ * g = sqrt(-2 ln u) (cos, sin)(2 pi v).  Stream 0 feeds the collide-stream
+ * (mode noise), stream 1 the psi equation, streams 3 and 4 the equilibrium
+ * start; the site id of a lattice point is x + nx*(y + ny*z).
+ *   dev_out     : device pointer, FP32, nsites*8*nblocks values (caller-owned).
  *   cuda_stream : cudaStream_t (NULL: legacy default stream); asynchronous.
  * Errors: EINVAL (null dev_out, nsites < 0, nblocks outside [1, 16], stream >
  * 0xFFFF, site0 + nsites > 2^32), ECUDA. */

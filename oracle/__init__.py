@@ -171,16 +171,16 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def gaussians(seed: int, step: int, site: int, stream: int, nblocks: int) -> np.ndarray:
-    g = np.zeros(4 * nblocks)
+    g = np.zeros(8 * nblocks)
     lib().ora_gaussians(seed, step, site, stream, nblocks, _dp(g))
     return g
 
 
 def gaussians_sites(seed: int, step: int, site0: int, nsites: int, stream: int, nblocks: int) -> np.ndarray:
-    """The normals of `gaussians` for counter sites site0 .. site0 + nsites - 1, shape (nsites, 4 nblocks)."""
-    g = np.zeros(nsites * 4 * nblocks)
+    """The normals of `gaussians` for counter sites site0 .. site0 + nsites - 1, shape (nsites, 8 nblocks)."""
+    g = np.zeros(nsites * 8 * nblocks)
     lib().ora_gaussians_sites(seed, step, site0, nsites, stream, nblocks, _dp(g))
-    return g.reshape(nsites, 4 * nblocks)
+    return g.reshape(nsites, 8 * nblocks)
 
 
 def lattice(dim: int, q: int):
@@ -320,7 +320,7 @@ class State:
         from . import theory as T
         c, w = lattice(p.dim, p.q)
         shape = p.shape
-        nb = (p.q + 3) // 4
+        nb = (p.q + 7) // 8
         G = gaussians_sites(p.seed, 0, 0, p.n, 3, nb)[:, :p.q].T          # (q, N)
         dev = np.sqrt(p.rho0 * p.kT * 3.0 * w)[:, None] * G
         f = np.empty((p.q, p.n))

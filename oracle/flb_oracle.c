@@ -78,15 +78,19 @@ void ora_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Uniform on (0,1) from the top 23 bits: ((x >> 9) + 1/2) * 2^-23.  The value
- * is exactly representable in binary32 and binary64, so both sides of the
- * parity check start every Gaussian from the same real number. */
-static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
+/* One Box-Muller pair per 32-bit word w: the radius uniform from its top 20
+ * bits, ((w >> 12) + 1/2) * 2^-20, and the angle uniform from its low 12 bits,
+ * ((w & 0xFFF) + 1/2) * 2^-12.  Both values are exactly representable in
+ * binary32 and binary64, so both sides of the parity check start every
+ * Gaussian from the same real numbers. */
+static double u_radius(uint32_t w) { return ((double)(w >> 12) + 0.5) * (1.0 / 1048576.0); }
+static double u_angle(uint32_t w) { return ((double)(w & 0xFFFu) + 0.5) * (1.0 / 4096.0); }
 
 /* Standard normals for (seed, step, site, stream): block b of the Philox
  * counter (site, step_lo, (stream << 16) | b, step_hi) under key (seed_lo,
- * seed_hi) yields four words; Box-Muller on (x0,x1) and (x2,x3) gives normals
- * 4b..4b+3 as r cos(2 pi u1), r sin(2 pi u1) with r = sqrt(-2 ln u0). */
+ * seed_hi) yields four words x_0..x_3; word x_k gives normals 8b+2k and
+ * 8b+2k+1 as r cos(2 pi v), r sin(2 pi v) with r = sqrt(-2 ln u), u and v the
+ * radius and angle uniforms of x_k. */
 void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream,
                    int32_t nblocks, double *g)
 {
@@ -96,22 +100,21 @@ void ora_gaussians(uint64_t seed, int64_t step, uint32_t site, uint32_t stream,
                            (uint32_t)((uint64_t)step >> 32)};
         uint32_t x[4];
         ora_philox4x32_10(ctr, key, x);
-        for (int p = 0; p < 2; ++p) {
-            double a = u01(x[2 * p]), t = u01(x[2 * p + 1]);
-            double r = sqrt(-2.0 * log(a));
-            g[4 * b + 2 * p] = r * cos(2.0 * M_PI * t);
-            g[4 * b + 2 * p + 1] = r * sin(2.0 * M_PI * t);
+        for (int k = 0; k < 4; ++k) {
+            double r = sqrt(-2.0 * log(u_radius(x[k]))), t = u_angle(x[k]);
+            g[8 * b + 2 * k] = r * cos(2.0 * M_PI * t);
+            g[8 * b + 2 * k + 1] = r * sin(2.0 * M_PI * t);
         }
     }
 }
 
 /* The normals of ora_gaussians for nsites consecutive counter sites
- * site0 .. site0 + nsites - 1: g[s * 4 nblocks + k]. */
+ * site0 .. site0 + nsites - 1: g[s * 8 nblocks + k]. */
 void ora_gaussians_sites(uint64_t seed, int64_t step, uint32_t site0, int64_t nsites, uint32_t stream,
                          int32_t nblocks, double *g)
 {
     for (int64_t s = 0; s < nsites; ++s)
-        ora_gaussians(seed, step, site0 + (uint32_t)s, stream, nblocks, g + (size_t)s * 4 * (size_t)nblocks);
+        ora_gaussians(seed, step, site0 + (uint32_t)s, stream, nblocks, g + (size_t)s * 8 * (size_t)nblocks);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -620,7 +623,7 @@ static void lb_collide_stream(const ora_params *p, const box_t *g, double *f, co
         /* ghost relaxation and thermal noise in the moment basis */
         double gs[16];
         int have_noise = p->kT > 0.0;
-        if (have_noise) ora_gaussians(p->seed, step, rng_site(p, x, y, z), 0u, (nnoisy + 3) / 4, gs);
+        if (have_noise) ora_gaussians(p->seed, step, rng_site(p, x, y, z), 0u, (nnoisy + 7) / 8, gs);
         const double mun = rho * p->kT / cs2;
         for (int t = 0; t < nnoisy; ++t) {
             int k = first_noisy + t;
@@ -702,7 +705,7 @@ void ora_fd_noise(const ora_params *p, int64_t step, double *eta)
         int x, y, z;
         coords(&g, (size_t)s, &x, &y, &z);
         double gs[16];
-        ora_gaussians(p->seed, step, rng_site(p, x, y, z), 1u, (nl + 3) / 4, gs);
+        ora_gaussians(p->seed, step, rng_site(p, x, y, z), 1u, (nl + 7) / 8, gs);
         for (int l = 0; l < nl; ++l)
             zeta[(size_t)l * g.n + (size_t)s] = sqrt(2.0 * p->kT * p->M * fd_link_weight(p, L[l])) * gs[l];
     }
@@ -724,7 +727,7 @@ static void fv_node_noise(const ora_params *p, const box_t *g, int64_t step, dou
     for (long long s = 0; s < (long long)g->n; ++s) {
         int x, y, z;
         coords(g, (size_t)s, &x, &y, &z);
-        double gs[4];
+        double gs[8];
         ora_gaussians(p->seed, step, rng_site(p, x, y, z), 1u, 1, gs);
         for (int a = 0; a < 3; ++a)
             xi[(size_t)a * g->n + (size_t)s] = a < g->dim ? sqrt(2.0 * p->kT * p->M) * gs[a] : 0.0;

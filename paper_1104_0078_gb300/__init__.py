@@ -189,9 +189,9 @@ def flb_structure_factor(h, rep: int, which: int):
 # ---- convenience owner ------------------------------------------------------
 def gaussians(seed: int, step: int, stream: int, site0: int, nsites: int, nblocks: int, device="cuda"):
     """The standard normals the kernels draw (flb_gaussians) as a torch tensor
-    (nsites, 4*nblocks) on `device`, computed on that device's current stream."""
+    (nsites, 8*nblocks) on `device`, computed on that device's current stream."""
     import torch
-    out = torch.empty((nsites, 4 * nblocks), dtype=torch.float32, device=device)
+    out = torch.empty((nsites, 8 * nblocks), dtype=torch.float32, device=device)
     st = torch.cuda.current_stream(out.device).cuda_stream
     _check(load_library().flb_gaussians(seed, step, stream, site0, nsites, nblocks, out.data_ptr(), st),
            "flb_gaussians")

@@ -1881,13 +1881,11 @@ __global__ void gaussians_kernel(const PhiloxKey K, int64_t step, uint32_t strea
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int b = 0; b < nblocks; ++b) {
-        float G[4];
-        normals4(K, step, site0 + (uint32_t)i, stream, (uint32_t)b, G);
-        float *o = out + i * 4 * nblocks + 4 * b;
-        o[0] = G[0];
-        o[1] = G[1];
-        o[2] = G[2];
-        o[3] = G[3];
+        float G[8];
+        normals<4>(K, step, site0 + (uint32_t)i, stream, (uint32_t)b, G);
+        float *o = out + i * 8 * nblocks + 8 * b;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = G[k];
     }
 }
 }  // namespace

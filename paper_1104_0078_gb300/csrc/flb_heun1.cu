@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(HT_NT, 1) psi3_fv_heun1_kernel(const Heun1Args
                 J[2 * Reg<4>::N + k] = mg * gz - u4[j][2] * pv;
                 if (NOISE) {
                     float Gn[4];
-                    normals4<false, true>(a.key, a.step, (uint32_t)(id4[j] + zid), 1u, 0u, Gn, sdx);
+                    normals<2, false, true>(a.key, a.step, (uint32_t)(id4[j] + zid), 1u, 0u, Gn, sdx);
                     X[k] = Gn[0];
                     X[Reg<4>::N + k] = Gn[1];
                     X[2 * Reg<4>::N + k] = Gn[2];
@@ -452,14 +452,9 @@ __global__ void __launch_bounds__(HT_NT, 1) psi3_fd_heun1_kernel(const Heun1Args
                 dst[k] = mu_at<Reg<4>::W>(pm, p0, pp, c, a.A, a.B, k22);
                 if (NOISE) {
                     const uint32_t sid = (uint32_t)(id3[j] + zid);
-                    float G[16];  // normals 0-12 of blocks 0-3
-                    normals4(a.key, a.step, sid, 1u, 0u, G);
-                    normals4(a.key, a.step, sid, 1u, 1u, G + 4);
-                    normals4(a.key, a.step, sid, 1u, 2u, G + 8);
-                    const u32x4 r = philox4x32_10(
-                        u32x4{sid, (uint32_t)(uint64_t)a.step, (1u << 16) | 3u, (uint32_t)((uint64_t)a.step >> 32)},
-                        a.key);
-                    box_muller(r.x, r.y, G[12], G[13]);
+                    float G[14];  // normals 0-12: block 0, and block 1's first three words
+                    normals<4>(a.key, a.step, sid, 1u, 0u, G);
+                    normals<3>(a.key, a.step, sid, 1u, 1u, G + 8);
 #pragma unroll
                     for (int l = 0; l < 13; ++l) sZ[l * Reg<3>::N + k] = (l < 3 ? s1 : (l < 9 ? s2 : s3)) * G[l];
                 }

@@ -34,9 +34,9 @@ __global__ void eq_pop_kernel(Geom g, int q, float mun, PhiloxKey key, T *f)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
-    float G[20];
-    const int nb = (q + 3) / 4;
-    for (int b = 0; b < nb; ++b) normals4(key, 0, (uint32_t)s, 3u, (uint32_t)b, G + 4 * b);
+    float G[24];
+    const int nb = (q + 7) / 8;
+    for (int b = 0; b < nb; ++b) normals<4>(key, 0, (uint32_t)s, 3u, (uint32_t)b, G + 8 * b);
     for (int i = 0; i < q; ++i) {
         const float v = sqrtf(mun * lattice_weight(q, i)) * G[i];
         if (sizeof(T) == 2) reinterpret_cast<__half *>(f)[(long long)i * g.n + s] = __float2half_rn(v);
@@ -57,8 +57,8 @@ __global__ void eq_modes_kernel(Geom g, LapW lw, double kT, double A, double K, 
         L = lw.c0 + lw.c1 * 2.0 * (cx + cy + cz) + lw.c2 * 4.0 * (cx * cy + cy * cz + cz * cx) + lw.c3 * 8.0 * cx * cy * cz;
     else
         L = lw.c0 + lw.c1 * 2.0 * (cx + cy) + lw.c2 * 4.0 * cx * cy;
-    float Gq[4];
-    normals4(key, 0, (uint32_t)t, 4u, 0u, Gq);
+    float Gq[2];
+    normals<1>(key, 0, (uint32_t)t, 4u, 0u, Gq);
     const float amp = t == 0 ? 0.f : (float)sqrt(kT / (A - K * L) / (double)g.n);
     X[t] = make_float2(amp * Gq[0], amp * Gq[1]);
 }

@@ -71,19 +71,18 @@ __device__ __forceinline__ u32x4 philox4x32_10_r0(u32x4 c, uint32_t a, uint32_t 
     return c;
 }
 
-// Uniform in (0,1): ((x >> 9) + 1/2) 2^-23, exact in binary32.  Built from the
-// bits: 1 + k 2^-23 (k = x >> 9) minus (1 - 2^-24) is exactly k 2^-23 + 2^-24.
-__device__ __forceinline__ float u01(uint32_t x)
-{
-    return __int_as_float((x >> 9) | 0x3f800000u) - __int_as_float(0x3f7fffffu);
-}
-
 // ---- Box-Muller by table lookup --------------------------------------------
-// The two transcendental steps of Box-Muller, specialised to the uniforms
-// above (24-bit odd multiples of 2^-24 for the radius, 23-bit ones for the
-// angle) and evaluated from small tables, to single-precision accuracy with
-// fewer instructions than the general logf and sincospif:
-//  * ln u, u = (2k+1) 2^-24: the table-driven method of P. T. P. Tang (ACM
+// One Philox word w makes one Box-Muller pair: its top 20 bits give the radius
+// uniform u = ((w >> 12) + 1/2) 2^-20 and its low 12 bits the angle uniform
+// v = ((w & 0xFFF) + 1/2) 2^-12, both exact in binary32, so a block of four
+// words yields eight normals.  The pair is (r cos 2 pi v, r sin 2 pi v) with
+// r = sqrt(-2 ln u): its radius stops at sqrt(42 ln 2) = 5.40 (the pair falls
+// beyond it with probability 4.8e-7) and the 4096 equally spaced angles make
+// every moment of (cos, sin) of order below 4096 the continuous one.
+// The two transcendental steps are specialised to these uniforms and
+// evaluated from small tables, to single-precision accuracy with fewer
+// instructions than the general logf and sincospif:
+//  * ln u, u = (2k+1) 2^-21: the table-driven method of P. T. P. Tang (ACM
 //    TOMS 16(4), 1990).  2k+1 = 2^e f with f in [sqrt(1/2), sqrt(2)); the bits
 //    of f select one of 32 cells; ln f = -ln r_j + ln(1 + d) with d = f r_j - 1
 //    formed by one FMA (|d| < 1/64) and ln(1 + d) by its series to d^5 (error
@@ -91,7 +90,7 @@ __device__ __forceinline__ float u01(uint32_t x)
 //    where d = f - 1 is exact, so u near 1 keeps its relative accuracy.  The
 //    radius needs -2 ln u: the series and the table carry the factor -2, which
 //    is exact in binary arithmetic.
-//  * sin, cos of 2 pi t, t = (m + 1/2) 2^-23: t = j/64 + t_lo, the table of
+//  * sin, cos of 2 pi v, v = (m + 1/2) 2^-12: v = j/64 + t_lo, the table of
 //    sin, cos(2 pi j/64) and the angle-addition formulas with sin b, cos b of
 //    b = 2 pi t_lo < 2 pi/64 by their series (to b^5 and b^4; error < 2e-9).
 // The tables are computed at compile time in double precision from the same
@@ -182,22 +181,21 @@ constexpr Tables make_tables()
 // one copy per translation unit, read through the read-only cache
 static __device__ const bm::Tables kBM = bm::make_tables();
 
-// Box-Muller on V::L independent pairs at once, one per lane (F2: two pairs in
-// Blackwell's packed FP32 registers): lane l takes the radius word a[l] and the
-// angle word b[l] and returns g0 = r cos 2 pi v, g1 = r sin 2 pi v with
-// r = sqrt(-2 ln u), u = ((a >> 9) + 1/2) 2^-23, v = ((b >> 9) + 1/2) 2^-23.
+// Box-Muller on V::L independent words at once, one per lane (F2: two words in
+// Blackwell's packed FP32 registers): lane l turns word w[l] into
+// g0 = r cos 2 pi v, g1 = r sin 2 pi v (u, v and r as above).
 // SCALED: r is multiplied by sc first (lane-wise), so the outputs come scaled.
 // The integer steps, table loads and the reciprocal square root run per lane;
-// every FP32 step is one lane-generic operation, so a pair gets the same bits
+// every FP32 step is one lane-generic operation, so a word gets the same bits
 // in either lane type.
 template <class V, bool SCALED = false>
-__device__ __forceinline__ void bm_eval(const uint32_t *a, const uint32_t *b, V sc, V &g0, V &g1)
+__device__ __forceinline__ void bm_eval(const uint32_t *w, V sc, V &g0, V &g1)
 {
     constexpr int L = V::L;
     float f[L], lr[L], l2r[L], eb[L], xm[L], sa[L], ca[L], nsa[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        const float fn = __uint2float_rn((a[l] >> 8) | 1u);   // 2k+1 < 2^24, exact
+        const float fn = __uint2float_rn((w[l] >> 11) | 1u);  // 2k+1 < 2^21, exact
         const int bits = __float_as_int(fn);
         const int t = bits - (int)bm::kSqrtHalfBits;
         const int e = t >> 23;                                // 2k+1 = 2^e f
@@ -205,30 +203,30 @@ __device__ __forceinline__ void bm_eval(const uint32_t *a, const uint32_t *b, V 
         const float2 C = __ldg(reinterpret_cast<const float2 *>(&kBM.lg[(t >> 18) & 31]));  // (r_j, 2 ln r_j)
         lr[l] = C.x;
         l2r[l] = C.y;
-        eb[l] = __int_as_float(0x4B400000 + e - 24);          // 1.5 2^23 + (e - 24), exact
-        const uint32_t m = b[l] >> 9;
-        const float4 A = __ldg(reinterpret_cast<const float4 *>(&kBM.sc[m >> 17]));  // (sin, cos, -sin)(2 pi j/64)
+        eb[l] = __int_as_float(0x4B400000 + e - 21);          // 1.5 2^23 + (e - 21), exact
+        const uint32_t m = w[l] & 0xFFFu;
+        const float4 A = __ldg(reinterpret_cast<const float4 *>(&kBM.sc[m >> 6]));  // (sin, cos, -sin)(2 pi j/64)
         sa[l] = A.x;
         ca[l] = A.y;
         nsa[l] = A.z;
-        xm[l] = __int_as_float(0x4B000000u | (m & 0x1FFFFu));  // 2^23 + (m mod 2^17), exact
+        xm[l] = __int_as_float(0x4B000000u | (m & 63u));      // 2^23 + (m mod 64), exact
     }
-    // -2 ln u = -2 (e - 24) ln 2 + 2 ln r_j - 2 ln(1 + d)
+    // -2 ln u = -2 (e - 21) ln 2 + 2 ln r_j - 2 ln(1 + d)
     const V d = vfma(vmake<V>(f), vmake<V>(lr), V::bc(-1.0f));
     V p = vfma(d, V::bc(-0.4f), V::bc(0.5f));  // -2 x the series of ln(1 + d)/d, Horner form
     p = vfma(d, p, V::bc(-2.0f / 3.0f));
     p = vfma(d, p, V::bc(1.0f));
     p = vfma(d, p, V::bc(-2.0f));
-    const V em = vmake<V>(eb) - V::bc(12582912.0f);       // e - 24, exact
-    const V e2 = vfma(d, p, vfma(em, V::bc(-2.0f * 0.693147180559945f), vmake<V>(l2r)));  // >= 1.19e-7
+    const V em = vmake<V>(eb) - V::bc(12582912.0f);       // e - 21, exact
+    const V e2 = vfma(d, p, vfma(em, V::bc(-2.0f * 0.693147180559945f), vmake<V>(l2r)));  // >= 9.5e-7
     float rs[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) rs[l] = rsqrtf(e2.lane(l));
     V rad = e2 * vmake<V>(rs);
     if (SCALED) rad = rad * sc;
     // sin, cos of 2 pi v by angle addition
-    const V x = vfma(vmake<V>(xm) - V::bc(8388608.0f), V::bc((float)(2.0 * bm::kPi / 8388608.0)),
-                     V::bc((float)(bm::kPi / 8388608.0)));
+    const V x = vfma(vmake<V>(xm) - V::bc(8388608.0f), V::bc((float)(2.0 * bm::kPi / 4096.0)),
+                     V::bc((float)(bm::kPi / 4096.0)));
     const V x2 = x * x;
     const V cb = vfma(x2, vfma(x2, V::bc(1.0f / 24.0f), V::bc(-0.5f)), V::bc(1.0f));
     const V sb = x * vfma(x2, vfma(x2, V::bc(1.0f / 120.0f), V::bc(-1.0f / 6.0f)), V::bc(1.0f));
@@ -238,32 +236,95 @@ __device__ __forceinline__ void bm_eval(const uint32_t *a, const uint32_t *b, V 
     g1 = rad * s;
 }
 
-// Box-Muller: r = sqrt(-2 ln a), (r cos 2 pi b, r sin 2 pi b).
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
+// The Box-Muller pair of one word.
+__device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1)
 {
     F1 r0, r1;
-    bm_eval<F1>(&a, &b, F1{1.0f}, r0, r1);
+    bm_eval<F1>(&w, F1{1.0f}, r0, r1);
     g0 = r0.v;
     g1 = r1.v;
 }
 
-// Four standard normals of one Philox block (Box-Muller on (x,y) and (z,w),
-// the two pairs evaluated together in the lanes of one packed register).
+__device__ __forceinline__ uint32_t word(const u32x4 &r, int k) { return k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w; }
+
+__device__ __forceinline__ u32x4 philox_ctr(int64_t step, uint32_t site, uint32_t stream, uint32_t block)
+{
+    return u32x4{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)};
+}
+
+// Normals 8 block .. 8 block + 2 NP - 1 of counter (site, step, stream): the
+// Box-Muller pairs of the block's first NP words (normals 2k, 2k + 1 of a block
+// come from its word k), two words evaluated together in one packed register.
 // KEY_R0: form the round keys from K's round-0 keys (arguments in shared memory).
 // SCALED: every normal multiplied by sc.
-template <bool KEY_R0 = false, bool SCALED = false>
-__device__ __forceinline__ void normals4(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
-                                         uint32_t block, float g[4], float sc = 1.0f)
+template <int NP, bool KEY_R0 = false, bool SCALED = false>
+__device__ __forceinline__ void normals(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
+                                        uint32_t block, float *g, float sc = 1.0f)
 {
-    const u32x4 c{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)};
+    static_assert(NP >= 1 && NP <= 4, "a Philox block has four words");
+    const u32x4 c = philox_ctr(step, site, stream, block);
     const u32x4 r = KEY_R0 ? philox4x32_10_r0(c, K.k0[0], K.k1[0]) : philox4x32_10(c, K);
-    const uint32_t a[2] = {r.x, r.z}, b[2] = {r.y, r.w};
-    F2 c0, s0;
-    bm_eval<F2, SCALED>(a, b, F2::bc(sc), c0, s0);
-    g[0] = c0.v.x;
-    g[1] = s0.v.x;
-    g[2] = c0.v.y;
-    g[3] = s0.v.y;
+#pragma unroll
+    for (int k = 0; k + 1 < NP; k += 2) {
+        const uint32_t w[2] = {word(r, k), word(r, k + 1)};
+        F2 c0, s0;
+        bm_eval<F2, SCALED>(w, F2::bc(sc), c0, s0);
+        g[2 * k] = c0.v.x;
+        g[2 * k + 1] = s0.v.x;
+        g[2 * k + 2] = c0.v.y;
+        g[2 * k + 3] = s0.v.y;
+    }
+    if constexpr ((NP & 1) != 0) {
+        const uint32_t w = word(r, NP - 1);
+        F1 c0, s0;
+        bm_eval<F1, SCALED>(&w, F1{sc}, c0, s0);
+        g[2 * NP - 2] = c0.v;
+        g[2 * NP - 1] = s0.v;
+    }
+}
+
+// The first NN normals of stream 0 (blocks 0, 1, ...) at the V::L sites
+// site[l], scaled lane-wise by sc: n[k] holds normal k of every lane's site
+// (n has room for NN rounded up to even).  F2: the lanes are the two sites;
+// F1: the site's words are evaluated in pairs in one packed register.
+template <int NN, bool KEY_R0, class V>
+__device__ __forceinline__ void lane_normals(const PhiloxKey &K, int64_t step, const uint32_t *site, V sc, V *n)
+{
+    constexpr int L = V::L;
+#pragma unroll
+    for (int b = 0; b < (NN + 7) / 8; ++b) {
+        constexpr int NPAIR = (NN + 1) / 2;
+        u32x4 r[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const u32x4 c = philox_ctr(step, site[l], 0u, (uint32_t)b);
+            r[l] = KEY_R0 ? philox4x32_10_r0(c, K.k0[0], K.k1[0]) : philox4x32_10(c, K);
+        }
+        if constexpr (L == 2) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (4 * b + k < NPAIR) {
+                    const uint32_t w[2] = {word(r[0], k), word(r[1], k)};
+                    bm_eval<V, true>(w, sc, n[8 * b + 2 * k], n[8 * b + 2 * k + 1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k += 2) {
+                if (4 * b + k < NPAIR) {
+                    const uint32_t w[2] = {word(r[0], k), word(r[0], k + 1)};
+                    F2 c0, s0;
+                    bm_eval<F2, true>(w, F2::bc(sc.lane(0)), c0, s0);
+                    n[8 * b + 2 * k] = V::bc(c0.v.x);
+                    n[8 * b + 2 * k + 1] = V::bc(s0.v.x);
+                    if (4 * b + k + 1 < NPAIR) {
+                        n[8 * b + 2 * k + 2] = V::bc(c0.v.y);
+                        n[8 * b + 2 * k + 3] = V::bc(s0.v.y);
+                    }
+                }
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -148,10 +148,8 @@ __global__ void __launch_bounds__(256) lb_d2q9_kernel(const LBArgs a)
         g8 = gg * m8 * (81.f / 16.f);  // 1/b = 81/16
     }
     if (a.kT > 0.f) {
-        float G[8];
-        const uint32_t sid = (uint32_t)site;
-        normals4(a.key, a.step, sid, 0u, 0u, G);
-        normals4(a.key, a.step, sid, 0u, 1u, G + 4);
+        float G[6];
+        normals<3>(a.key, a.step, (uint32_t)site, 0u, 0u, G);
         const float sq = sqrtf(3.0f * rho * a.kT);
         float n[6];
 #pragma unroll

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(512) noise2_kernel(const NoiseArgs a)
         const int lx = k % HX, ly = k / HX;
         const int gx = ((x0 - 1 + lx) % g.nx + g.nx) % g.nx, gy = ((y0 - 1 + ly) % g.ny + g.ny) % g.ny;
         float G[4];
-        normals4(a.key, a.step, (uint32_t)(gx + g.nx * gy), 1u, 0u, G);
+        normals<2>(a.key, a.step, (uint32_t)(gx + g.nx * gy), 1u, 0u, G);
         zs[0][ly][lx] = G[0];
         zs[1][ly][lx] = G[1];
         zs[2][ly][lx] = G[2];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(512) noise2_kernel(const NoiseArgs a)
 // Laplacians, the naive scheme, FV on D3Q15).  A block of 16 x 8 x 4 threads
 // draws, once per point, the normals of its tile and a one-point halo (18 x 10
 // x 6 points) into shared memory -- FD: the 13 link normals, Philox stream 1
-// blocks 0-3; FV and naive: the 3 node normals of block 0 -- then
+// blocks 0-1; FV and naive: the 3 node normals of block 0 -- then
 //   FD: eta(r) = sum_l sqrt(2 kT M a_l) [zeta_l(r - c_l) - zeta_l(r)], a_l the
 //       class coefficient of half-link l in the chosen Laplacian;
 //   FV: eta(r) = (2/c_s^2) sum_i w_i c_i . (xi(r) + xi(r + c_i)) / 2 on lattice q;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(N3X *N3Y *N3Z) noise3_kernel(const NoiseArgs a
     extern __shared__ float zs[];  // [nc][N3P]
     const Geom &g = a.g;
     const int nc = a.scheme == FLB_FD ? 13 : 3;
-    const int nb = a.scheme == FLB_FD ? 4 : 1;
+    const int nb = a.scheme == FLB_FD ? 2 : 1;
     const int x0 = blockIdx.x * N3X, y0 = blockIdx.y * N3Y, z0 = blockIdx.z * N3Z;
     const int t = threadIdx.x + N3X * (threadIdx.y + N3Y * threadIdx.z);
     for (int k = t; k < N3P; k += N3X * N3Y * N3Z) {
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(N3X *N3Y *N3Z) noise3_kernel(const NoiseArgs a
         const int gz = ((z0 - 1 + lz) % g.nz + g.nz) % g.nz;
         const uint32_t sid = (uint32_t)(gx + g.nx * (gy + g.ny * gz));
         for (int b = 0; b < nb; ++b) {
-            float G[4];
-            normals4(a.key, a.step, sid, 1u, (uint32_t)b, G);
-            for (int j = 0; j < 4 && 4 * b + j < nc; ++j) zs[(4 * b + j) * N3P + k] = G[j];
+            float G[8];
+            normals<4>(a.key, a.step, sid, 1u, (uint32_t)b, G);
+            for (int j = 0; j < 8 && 8 * b + j < nc; ++j) zs[(8 * b + j) * N3P + k] = G[j];
         }
     }
     __syncthreads();

@@ -27,15 +27,6 @@
 
 namespace flb {
 
-// The first two normals of one Philox block (only the (x,y) Box-Muller pair).
-__device__ __forceinline__ void normals2(const PhiloxKey &K, int64_t step, uint32_t site, uint32_t stream,
-                                         uint32_t block, float g[2])
-{
-    const u32x4 r = philox4x32_10(
-        u32x4{site, (uint32_t)(uint64_t)step, (stream << 16) | block, (uint32_t)((uint64_t)step >> 32)}, K);
-    box_muller(r.x, r.y, g[0], g[1]);
-}
-
 __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 __device__ __forceinline__ int ring4(int p) { return p & 3; }  // two's complement: correct for negative p
 
@@ -216,11 +207,9 @@ __global__ void __launch_bounds__(PS_NT, 2) psi3_fd_kernel(const Psi3Args a, con
                     if (R.c1[j] < 0) continue;
                     const int k = threadIdx.x + j * PS_NT;
                     const uint32_t sid = (uint32_t)(R.n1[j] + zid);
-                    float G[14];  // normals 0-12 of blocks 0-3 (block 3: its first pair only)
-                    normals4(a.key, a.step, sid, 1u, 0u, G);
-                    normals4(a.key, a.step, sid, 1u, 1u, G + 4);
-                    normals4(a.key, a.step, sid, 1u, 2u, G + 8);
-                    normals2(a.key, a.step, sid, 1u, 3u, G + 12);
+                    float G[14];  // normals 0-12: block 0, and block 1's first three words
+                    normals<4>(a.key, a.step, sid, 1u, 0u, G);
+                    normals<3>(a.key, a.step, sid, 1u, 1u, G + 8);
 #pragma unroll
                     for (int l = 0; l < 13; ++l) sZ[l * H1N + k] = (l < 3 ? s1 : (l < 9 ? s2 : s3)) * G[l];
                 }

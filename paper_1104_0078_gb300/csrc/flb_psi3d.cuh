@@ -451,12 +451,12 @@ __device__ __forceinline__ void psi3_fv_tma_block(const CUtensorMap *psi_map, co
                     sts_v<V>(J, 2 * TJ_N + k, LR1, jz);
                     if (NOISE) {
                         // three N(0, 2 kT M) normals per node, the radius scaled by
-                        // sqrt(2 kT M): the (x, y) and (z, w) Box-Muller pairs of the
-                        // node's Philox block, one packed evaluation per node
+                        // sqrt(2 kT M): the Box-Muller pairs of the first two words of
+                        // the node's Philox block, one packed evaluation per node
 #pragma unroll
                         for (int l = 0; l < L; ++l) {
                             float Gn[4];
-                            normals4<KEY_R0, true>(a.key, a.step, (uint32_t)(n1[j][l] + zid), 1u, 0u, Gn, sdx);
+                            normals<2, KEY_R0, true>(a.key, a.step, (uint32_t)(n1[j][l] + zid), 1u, 0u, Gn, sdx);
                             X[k + l * LR1] = Gn[0];
                             X[TJ_N + k + l * LR1] = Gn[1];
                             X[2 * TJ_N + k + l * LR1] = Gn[2];

@@ -337,31 +337,11 @@ __device__ __forceinline__ void lb_sites(const LBArgs &a, const PL &P, int x, in
         float sq[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) sq[l] = mun.lane(l) * rsqrtf(mun.lane(l));  // ~2 ulp
+        uint32_t su[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) su[l] = (uint32_t)s[l];
         V n[16];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            u32x4 r[L];
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                const u32x4 c{(uint32_t)s[l], (uint32_t)(uint64_t)a.step, (uint32_t)b,
-                              (uint32_t)((uint64_t)a.step >> 32)};
-                r[l] = KEY_R0 ? philox4x32_10_r0(c, a.key.k0[0], a.key.k1[0]) : philox4x32_10(c, a.key);
-            }
-            if constexpr (L == 2) {  // lanes = the two sites; (x, y) then (z, w) of each
-                const uint32_t a0[2] = {r[0].x, r[1].x}, b0[2] = {r[0].y, r[1].y};
-                const uint32_t a1[2] = {r[0].z, r[1].z}, b1[2] = {r[0].w, r[1].w};
-                const V sc = vmake<V>(sq);
-                bm_eval<V, true>(a0, b0, sc, n[4 * b], n[4 * b + 1]);
-                bm_eval<V, true>(a1, b1, sc, n[4 * b + 2], n[4 * b + 3]);
-            } else {  // one site: its (x, y) and (z, w) pairs share the packed register
-                const uint32_t a0[2] = {r[0].x, r[0].z}, b0[2] = {r[0].y, r[0].w};
-                F2 c0, s0;
-                bm_eval<F2, true>(a0, b0, F2::bc(sq[0]), c0, s0);
-                const float o[4] = {c0.v.x, s0.v.x, c0.v.y, s0.v.y};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) n[4 * b + k] = V::bc(o[k]);
-            }
-        }
+        lane_normals<15, KEY_R0>(a.key, a.step, su, vmake<V>(sq), n);
         const V m0 = n[0] * a.nq[0], m1 = n[1] * a.nq[1], m2 = n[2] * a.nq[2];
         const V t01 = m0 - m1;
         Qxx = Qxx + vfma(m1, 2.0f, m0);

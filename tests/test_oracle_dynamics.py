@@ -99,7 +99,7 @@ def test_fd_link_noise_orientation():
              (0, 1, -1), (1, 1, 1), (1, 1, -1), (1, -1, 1), (1, -1, -1)]
     a = {1: 6 / 22, 2: 3 / 22, 3: 1 / 22}
     nz, ny, nx = p.shape
-    G = np.array([O.gaussians(p.seed, 4, s, 1, 4) for s in range(p.n)]).reshape(nz, ny, nx, 16)
+    G = np.array([O.gaussians(p.seed, 4, s, 1, 2) for s in range(p.n)]).reshape(nz, ny, nx, 16)
     eta = O.fd_noise(p, 4).reshape(p.shape)
     for (zz, yy, xx) in [(0, 0, 0), (4, 2, 3), (2, 1, 1)]:
         acc = 0.0

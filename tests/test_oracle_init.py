@@ -23,7 +23,7 @@ def test_equilibrium_populations_are_the_streamed_draws(dim, q):
     p = _p(dim, q)
     st = O.State.equilibrium(p)
     c, w = O.lattice(dim, q)
-    nb = (q + 3) // 4
+    nb = (q + 7) // 8
     nz, ny, nx = p.shape
     for (x, y, z) in [(0, 0, 0), (5, 4, nz - 1), (2, 1, 0), (3, 2, nz // 2)]:
         r = x + nx * (y + ny * z)

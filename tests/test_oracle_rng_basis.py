@@ -25,7 +25,7 @@ def test_philox_known_answers():
 
 def test_gaussian_moments():
     # 2^17 normals from stream 0 of consecutive sites: mean 0, variance 1, kurtosis 3 (5 sigma)
-    g = np.concatenate([O.gaussians(7, 3, s, 0, 4) for s in range(8192)])
+    g = np.concatenate([O.gaussians(7, 3, s, 0, 2) for s in range(8192)])
     n = g.size
     assert abs(g.mean()) < 5 / np.sqrt(n)
     assert abs(g.var() - 1.0) < 5 * np.sqrt(2.0 / n)
@@ -35,13 +35,32 @@ def test_gaussian_moments():
     assert abs(np.mean(gg[:, 0] * gg[:, 1])) < 5 / np.sqrt(gg.shape[0])
 
 
+def test_gaussian_pairs_sit_on_the_uniform_grids():
+    # each pair (g0, g1) is r (cos, sin)(2 pi v) of one 32-bit word: its radius
+    # uniform u = exp(-r^2/2) lies on the 20-bit grid (k + 1/2) 2^-20 and its
+    # angle v on the 12-bit grid (m + 1/2) 2^-12; both grids are filled, and
+    # the drawn radius never passes the grid's bound sqrt(-2 ln 2^-21)
+    gg = np.concatenate([O.gaussians(3, 11, s, 1, 2) for s in range(16384)]).reshape(-1, 2)
+    r2 = (gg ** 2).sum(axis=1)
+    ku = np.exp(-r2 / 2) * 2.0 ** 20 - 0.5
+    assert np.abs(ku - np.round(ku)).max() < 1e-4
+    v = np.mod(np.arctan2(gg[:, 1], gg[:, 0]) / (2 * np.pi), 1.0)
+    km = v * 4096 - 0.5
+    assert np.abs(km - np.round(km)).max() < 1e-6
+    assert len(np.unique(np.round(km))) == 4096
+    assert np.sqrt(r2.max()) <= np.sqrt(42 * np.log(2)) + 1e-12
+    # the 4096 angles make (cos, sin) moments below order 4096 the continuous ones
+    th = 2 * np.pi * (np.arange(4096) + 0.5) / 4096
+    assert abs(np.mean(np.cos(th) ** 4) - 3 / 8) < 1e-15 and abs(np.mean(np.cos(th) ** 2 * np.sin(th) ** 2) - 1 / 8) < 1e-15
+
+
 def test_gaussians_depend_on_every_counter_word():
     base = O.gaussians(1, 5, 10, 0, 1)
     for other in (O.gaussians(2, 5, 10, 0, 1), O.gaussians(1, 6, 10, 0, 1), O.gaussians(1, 5, 11, 0, 1),
                   O.gaussians(1, 5, 10, 1, 1), O.gaussians(1, 5 + (1 << 32), 10, 0, 1),
-                  O.gaussians(1, 5, 10, 0, 2)[4:]):
+                  O.gaussians(1, 5, 10, 0, 2)[8:]):
         assert not np.allclose(base, other)
-    assert np.array_equal(O.gaussians(1, 5, 10, 0, 2)[:4], base)
+    assert np.array_equal(O.gaussians(1, 5, 10, 0, 2)[:8], base)
 
 
 @pytest.mark.parametrize("dim,q", [(2, 9), (3, 19), (3, 15)])
