@@ -120,12 +120,14 @@ def test_fd_noise_covariance(dim, kind):
     assert acc[0, 0, 0] < 1e-20
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_contrast_scheme_noise_covariance(dim):
+@pytest.mark.parametrize("dim,nz", [(2, 4), (3, 4), (3, 5)])
+def test_contrast_scheme_noise_covariance(dim, nz):
     # the naive scheme of Sec. III: node noise through the central-difference
     # divergence, Gamma(q) = i sin q, so <|eta~(q)|^2> = 2 kT M sum_a sin^2 q_a
-    # (Eq. FTorderpara) -- not -2 kT M L(q); it vanishes where every q_a is 0 or pi
-    p = O.Params(dim=dim, q=19 if dim == 3 else 9, nx=8, ny=6, nz=4, kT=0.7, M=0.3, scheme=2, laplacian=1,
+    # (Eq. FTorderpara) -- not -2 kT M L(q); it vanishes where every q_a is 0 or pi.
+    # A normal shared between two nodes (a counter or word index gone wrong)
+    # would modulate the spectrum; an odd depth checks the periodic wrap.
+    p = O.Params(dim=dim, q=19 if dim == 3 else 9, nx=8, ny=6, nz=nz, kT=0.7, M=0.3, scheme=2, laplacian=1,
                  A=0.0, K=0.0, coupling=0)
     acc = np.zeros(p.shape)
     nsamp = 400
