@@ -243,64 +243,71 @@ __global__ void dft_x_kernel(DftArgs a)
     a.X1[t] = make_float2(re, im);
 }
 
-// The same X1 for windows of Kx <= 32 on rows of nx <= 1024, one warp per
-// (y, z) row: the lanes load the row once (x = lane + 32 j, kept in
-// registers); for each kept k a lane starts from e^{-i k lane 2pi/nx} (a table
-// built per block) and steps to x + 32 by one complex rotation by
-// e^{-i 2pi 32 k / nx}; a shuffle reduction over the lanes completes X1.  The
-// rotations add ~1e-6 relative error after 32 steps, far below the FP64 S(q)
-// accumulation's statistical use.
-constexpr int DXW_KMAX = 32, DXW_NJ = 32, DXW_WARPS = 8;
+// The same X1 for windows of Kx <= 32 on rows of nx <= 1024, as a small matrix
+// product over blocks of DXR_R rows.  The input is real, so X(-k) = conj X(k):
+// only the kept k = 0 .. Kx/2 are summed (nu of them), each written with its
+// partner.  A block builds the table e^{-2 pi i m / nx} once; for every chunk of
+// DXR_CX columns it stages the rows' values (coalesced) and the chunk's twiddles
+// e^{-2 pi i k x / nx} (k x reduced mod nx exactly, as twiddle() does) in shared
+// memory, and thread t sums row t against them, sequentially in x.
+constexpr int DXR_R = 128, DXR_CX = 32, DXR_NMAX = 1024;
 
-__global__ void __launch_bounds__(32 * DXW_WARPS) dft_x_warp_kernel(DftArgs a)
+__device__ __forceinline__ int conj_partner(int j, int n, int K) { return j == 0 ? 0 : (K >= n ? n - j : K - j); }
+
+template <int NUP>
+__global__ void __launch_bounds__(DXR_R) dft_x_rows_kernel(DftArgs a, long long nrows)
 {
-    __shared__ float2 w0[DXW_KMAX][32];  // e^{-i 2pi k lane / nx} of every kept k
-    __shared__ float2 rot[DXW_KMAX];     // e^{-i 2pi 32 k / nx}
-    for (int e = threadIdx.x; e < a.Kx * 32; e += blockDim.x) {
-        const int jx = e / 32, l = e % 32, k = kval(jx, a.nx, a.Kx);
-        w0[jx][l] = twiddle(k, l, a.nx);
-        if (l == 0) rot[jx] = twiddle(k, 32, a.nx);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const long long row = (long long)blockIdx.x * DXW_WARPS + (threadIdx.x >> 5);
-    if (row >= (long long)a.ny * a.nz) return;
-    const int y = (int)(row % a.ny), z = (int)(row / a.ny);
-    const float *src = a.in + a.off + (long long)y * a.sy + (long long)z * a.sz;
-    float v[DXW_NJ];
+    __shared__ float2 tw[DXR_NMAX];
+    __shared__ __align__(16) float2 Wc[DXR_CX][NUP];
+    __shared__ float P[DXR_R][DXR_CX + 1];
+    __shared__ long long roff[DXR_R];
+    const int n = a.nx, nu = a.Kx / 2 + 1, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    for (int m = t; m < n; m += DXR_R) tw[m] = twiddle(1, m, n);
+    for (long long r0 = (long long)blockIdx.x * DXR_R; r0 < nrows; r0 += (long long)gridDim.x * DXR_R) {
+        __syncthreads();  // the table is complete; the previous group is done with roff
+        {
+            const long long r = r0 + t;
+            roff[t] = r < nrows ? a.off + (r % a.ny) * a.sy + (r / a.ny) * a.sz : -1;
+        }
+        float re[NUP], im[NUP];
 #pragma unroll
-    for (int j = 0; j < DXW_NJ; ++j) {
-        const int x = lane + 32 * j;
-        v[j] = x < a.nx ? src[x] : 0.f;
-    }
-    const int nj = (a.nx + 31) / 32;
-    // the input is real, so X(-k) = conj X(k): of each pair of kept indices with
-    // k and -k (mod nx) only the first is summed, the other written as its conjugate
-    for (int jx = 0; jx < a.Kx; ++jx) {
-        const int k = kval(jx, a.nx, a.Kx), kn = k == 0 ? 0 : a.nx - k;
-        const int jp = a.Kx >= a.nx ? kn : (kn == 0 ? 0 : (kn <= a.Kx / 2 ? kn : a.Kx - (a.nx - kn)));
-        if (jp < jx) continue;  // summed as the partner's conjugate
-        float2 w = w0[jx][lane];
-        const float2 r = rot[jx];
-        float re = 0.f, im = 0.f;
+        for (int j = 0; j < NUP; ++j) re[j] = im[j] = 0.f;
+        for (int x0 = 0; x0 < n; x0 += DXR_CX) {
+            __syncthreads();  // roff written; the previous chunk's P and Wc are consumed
+            for (int e = t; e < DXR_CX * NUP; e += DXR_R) {
+                const int i = e / NUP, j = e % NUP, x = x0 + i;
+                Wc[i][j] = (j < nu && x < n) ? tw[(j * x) % n] : make_float2(0.f, 0.f);
+            }
+            for (int rr = wp; rr < DXR_R; rr += DXR_R / 32) {
+                const long long o = roff[rr];
+                const int x = x0 + lane;
+                P[rr][lane] = (o >= 0 && x < n) ? __ldg(a.in + o + x) : 0.f;
+            }
+            __syncthreads();
+            const int cx = min(DXR_CX, n - x0);
+            for (int i = 0; i < cx; ++i) {
+                const float v = P[t][i];
 #pragma unroll
-        for (int j = 0; j < DXW_NJ; ++j) {
-            if (j < nj) {
-                re = fmaf(v[j], w.x, re);
-                im = fmaf(v[j], w.y, im);
-                const float wx = w.x * r.x - w.y * r.y;
-                w.y = w.x * r.y + w.y * r.x;
-                w.x = wx;
+                for (int j = 0; j < NUP; j += 2) {
+                    const float4 w = *reinterpret_cast<const float4 *>(&Wc[i][j]);
+                    re[j] = fmaf(v, w.x, re[j]);
+                    im[j] = fmaf(v, w.y, im[j]);
+                    re[j + 1] = fmaf(v, w.z, re[j + 1]);
+                    im[j + 1] = fmaf(v, w.w, im[j + 1]);
+                }
             }
         }
+        const long long r = r0 + t;
+        if (r < nrows) {
+            float2 *o = a.X1 + r * a.Kx;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_xor_sync(0xffffffffu, re, o);
-            im += __shfl_xor_sync(0xffffffffu, im, o);
-        }
-        if (lane == 0) {
-            a.X1[row * a.Kx + jx] = make_float2(re, im);
-            if (jp != jx) a.X1[row * a.Kx + jp] = make_float2(re, -im);
+            for (int j = 0; j < NUP; ++j) {
+                if (j < nu) {
+                    o[j] = make_float2(re[j], im[j]);
+                    const int jp = conj_partner(j, n, a.Kx);
+                    if (jp != j) o[jp] = make_float2(re[j], -im[j]);
+                }
+            }
         }
     }
 }
@@ -317,43 +324,70 @@ __global__ void dft_y_kernel(DftArgs a)
     const int jy = (int)((t / a.Kx) % a.Ky);
     const int z = (int)(t / ((long long)a.Kx * a.Ky));
     const int k = kval(jy, a.ny, a.Ky);
-    float re = 0.f, im = 0.f;
-    int m = 0;
-    for (int y = 0; y < a.ny; ++y) {
-        const float2 v = a.X1[((long long)z * a.ny + y) * a.Kx + jx];
+    // four partial sums over y mod 4 (independent chains), added in a fixed order
+    float re4[4] = {0.f, 0.f, 0.f, 0.f}, im4[4] = {0.f, 0.f, 0.f, 0.f};
+    const float2 *src = a.X1 + (long long)z * a.ny * a.Kx + jx;
+    int m = 0, y = 0;
+    for (; y + 4 <= a.ny; y += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float2 v = src[(long long)(y + u) * a.Kx];
+            const float2 w = tw[m];
+            re4[u] += v.x * w.x - v.y * w.y;
+            im4[u] += v.x * w.y + v.y * w.x;
+            m += k;
+            if (m >= a.ny) m -= a.ny;
+        }
+    }
+    for (; y < a.ny; ++y) {
+        const float2 v = src[(long long)y * a.Kx];
         const float2 w = tw[m];
-        re += v.x * w.x - v.y * w.y;
-        im += v.x * w.y + v.y * w.x;
+        re4[0] += v.x * w.x - v.y * w.y;
+        im4[0] += v.x * w.y + v.y * w.x;
         m += k;
         if (m >= a.ny) m -= a.ny;
     }
+    const float re = (re4[0] + re4[1]) + (re4[2] + re4[3]), im = (im4[0] + im4[1]) + (im4[2] + im4[3]);
     a.X2[t] = make_float2(re, im);
 }
 
-// S[(jz*Ky + jy)*Kx + jx] += scale |sum_z X2[(z*Ky + jy)*Kx + jx] e^{-i qz z}|^2  (FP64)
-__global__ void dft_z_acc_kernel(DftArgs a)
+// S[(jz*Ky + jy)*Kx + jx] += scale |sum_z X2[(z*Ky + jy)*Kx + jx] e^{-i qz z}|^2  (FP64).
+// One warp per output: lane l sums z = l, l + 32, ... in FP64, then a
+// shuffle reduction in a fixed order.
+constexpr int DZ_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * DZ_WARPS) dft_z_acc_kernel(DftArgs a)
 {
     extern __shared__ float2 tw[];
     fill_twiddles(tw, a.nz);
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blockIdx.x * DZ_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     const long long tot = (long long)a.Kx * a.Ky * a.Kz;
     if (t >= tot) return;
     const long long plane = (long long)a.Kx * a.Ky;
     const long long xy = t % plane;
     const int jz = (int)(t / plane);
     const int k = kval(jz, a.nz, a.Kz);
+    const int step = (int)(((long long)k * 32) % a.nz);
+    int m = (int)(((long long)k * lane) % a.nz);
     double re = 0.0, im = 0.0;
-    int m = 0;
-    for (int z = 0; z < a.nz; ++z) {
+    for (int z = lane; z < a.nz; z += 32) {
         const float2 v = a.X2[(long long)z * plane + xy];
         const float2 w = tw[m];
         re += (double)v.x * w.x - (double)v.y * w.y;
         im += (double)v.x * w.y + (double)v.y * w.x;
-        m += k;
+        m += step;
         if (m >= a.nz) m -= a.nz;
     }
-    if (a.S) a.S[t] += a.scale * (re * re + im * im);
-    if (a.snap) a.snap[t] = make_float2((float)re, (float)im);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        if (a.S) a.S[t] += a.scale * (re * re + im * im);
+        if (a.snap) a.snap[t] = make_float2((float)re, (float)im);
+    }
 }
 
 // Dynamic structure factor: correlate the newest Fourier components with those
@@ -385,14 +419,20 @@ cudaError_t launch_dft_accumulate(const DftArgs &a, cudaStream_t s)
     const int bs = 256;
     long long n1 = (long long)a.Kx * a.ny * a.nz, n2 = (long long)a.Kx * a.Ky * a.nz, n3 = (long long)a.Kx * a.Ky * a.Kz;
     if (a.nx > TW_MAX || a.ny > TW_MAX || a.nz > TW_MAX) return cudaErrorInvalidValue;
-    if (a.Kx <= DXW_KMAX && a.nx <= 32 * DXW_NJ) {
+    if (a.Kx <= 32 && a.nx <= DXR_NMAX) {
         const long long rows = (long long)a.ny * a.nz;
-        dft_x_warp_kernel<<<(unsigned)((rows + DXW_WARPS - 1) / DXW_WARPS), 32 * DXW_WARPS, 0, s>>>(a);
+        const unsigned grid = (unsigned)((rows + DXR_R - 1) / DXR_R);
+        const int nu = a.Kx / 2 + 1;
+        if (nu <= 2) dft_x_rows_kernel<2><<<grid, DXR_R, 0, s>>>(a, rows);
+        else if (nu <= 4) dft_x_rows_kernel<4><<<grid, DXR_R, 0, s>>>(a, rows);
+        else if (nu <= 6) dft_x_rows_kernel<6><<<grid, DXR_R, 0, s>>>(a, rows);
+        else if (nu <= 10) dft_x_rows_kernel<10><<<grid, DXR_R, 0, s>>>(a, rows);
+        else dft_x_rows_kernel<18><<<grid, DXR_R, 0, s>>>(a, rows);
     } else {
         dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, sizeof(float2) * a.nx, s>>>(a);
     }
     dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, sizeof(float2) * a.ny, s>>>(a);
-    dft_z_acc_kernel<<<(unsigned)((n3 + bs - 1) / bs), bs, sizeof(float2) * a.nz, s>>>(a);
+    dft_z_acc_kernel<<<(unsigned)((n3 + DZ_WARPS - 1) / DZ_WARPS), 32 * DZ_WARPS, sizeof(float2) * a.nz, s>>>(a);
     return cudaGetLastError();
 }
 
