@@ -246,56 +246,89 @@ __global__ void dft_x_kernel(DftArgs a)
 // The same X1 for windows of Kx <= 32 on rows of nx <= 1024, as a small matrix
 // product over blocks of DXR_R rows.  The input is real, so X(-k) = conj X(k):
 // only the kept k = 0 .. Kx/2 are summed (nu of them), each written with its
-// partner.  A block builds the table e^{-2 pi i m / nx} once; for every chunk of
-// DXR_CX columns it stages the rows' values (coalesced) and the chunk's twiddles
-// e^{-2 pi i k x / nx} (k x reduced mod nx exactly, as twiddle() does) in shared
-// memory, and thread t sums row t against them, sequentially in x.
-constexpr int DXR_R = 128, DXR_CX = 32, DXR_NMAX = 1024;
+// partner.  A block builds the table e^{-2 pi i m / nx} once; chunks of DXR_CX
+// columns of its rows are copied into two shared-memory buffers by cp.async
+// (the next chunk in flight while the current one is summed), the chunk's
+// twiddles e^{-2 pi i k x / nx} (k x reduced mod nx exactly, as twiddle() does)
+// are taken from the table, and thread t sums row t, sequentially in x.
+constexpr int DXR_R = 128, DXR_CX = 32, DXR_NMAX = 1024, DXR_PS = DXR_R * (DXR_CX + 1);
 
 __device__ __forceinline__ int conj_partner(int j, int n, int K) { return j == 0 ? 0 : (K >= n ? n - j : K - j); }
+
+// 4-byte asynchronous copy global -> shared; src_bytes 0 writes a zero
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// dynamic shared memory of dft_x_rows_kernel<NUP> for rows of n
+template <int NUP>
+constexpr size_t dxr_smem(int n)
+{
+    return DXR_R * sizeof(long long) + DXR_CX * NUP * sizeof(float2) + 2 * DXR_PS * sizeof(float) + n * sizeof(float2);
+}
 
 template <int NUP>
 __global__ void __launch_bounds__(DXR_R) dft_x_rows_kernel(DftArgs a, long long nrows)
 {
-    __shared__ float2 tw[DXR_NMAX];
-    __shared__ __align__(16) float2 Wc[DXR_CX][NUP];
-    __shared__ float P[DXR_R][DXR_CX + 1];
-    __shared__ long long roff[DXR_R];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    long long *roff = reinterpret_cast<long long *>(dsm);                          // [DXR_R]
+    float2 *Wc = reinterpret_cast<float2 *>(roff + DXR_R);                           // [DXR_CX][NUP]
+    float *P = reinterpret_cast<float *>(Wc + DXR_CX * NUP);                        // [2][DXR_R][DXR_CX + 1]
+    float2 *tw = reinterpret_cast<float2 *>(P + 2 * DXR_PS);                         // [n]
     const int n = a.nx, nu = a.Kx / 2 + 1, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    const int nch = (n + DXR_CX - 1) / DXR_CX;
     for (int m = t; m < n; m += DXR_R) tw[m] = twiddle(1, m, n);
+    // this thread's copies of chunk c: rows wp, wp + 4, ..., column x0 + lane
+    auto stage = [&](int c) {
+        float *buf = P + (c & 1) * DXR_PS;
+        const int x = c * DXR_CX + lane;
+        for (int rr = wp; rr < DXR_R; rr += DXR_R / 32) {
+            const long long o = roff[rr];
+            const bool ok = o >= 0 && x < n;
+            cp_async4(buf + rr * (DXR_CX + 1) + lane, a.in + (ok ? o + x : 0), ok ? 4 : 0);
+        }
+    };
     for (long long r0 = (long long)blockIdx.x * DXR_R; r0 < nrows; r0 += (long long)gridDim.x * DXR_R) {
-        __syncthreads();  // the table is complete; the previous group is done with roff
+        __syncthreads();  // the table is complete; the previous group is done with roff and P
         {
             const long long r = r0 + t;
             roff[t] = r < nrows ? a.off + (r % a.ny) * a.sy + (r / a.ny) * a.sz : -1;
         }
+        __syncthreads();
+        stage(0);
+        cp_async_commit();
         float re[NUP], im[NUP];
 #pragma unroll
         for (int j = 0; j < NUP; ++j) re[j] = im[j] = 0.f;
-        for (int x0 = 0; x0 < n; x0 += DXR_CX) {
-            __syncthreads();  // roff written; the previous chunk's P and Wc are consumed
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) stage(c + 1);
+            cp_async_commit();
+            const int x0 = c * DXR_CX;
             for (int e = t; e < DXR_CX * NUP; e += DXR_R) {
                 const int i = e / NUP, j = e % NUP, x = x0 + i;
-                Wc[i][j] = (j < nu && x < n) ? tw[(j * x) % n] : make_float2(0.f, 0.f);
+                Wc[e] = (j < nu && x < n) ? tw[(j * x) % n] : make_float2(0.f, 0.f);
             }
-            for (int rr = wp; rr < DXR_R; rr += DXR_R / 32) {
-                const long long o = roff[rr];
-                const int x = x0 + lane;
-                P[rr][lane] = (o >= 0 && x < n) ? __ldg(a.in + o + x) : 0.f;
-            }
-            __syncthreads();
+            cp_async_wait1();  // this thread's copies of chunk c have landed
+            __syncthreads();   // everyone's copies of chunk c, and the chunk's twiddles
+            const float *Pc = P + (c & 1) * DXR_PS + t * (DXR_CX + 1);
             const int cx = min(DXR_CX, n - x0);
             for (int i = 0; i < cx; ++i) {
-                const float v = P[t][i];
+                const float v = Pc[i];
 #pragma unroll
                 for (int j = 0; j < NUP; j += 2) {
-                    const float4 w = *reinterpret_cast<const float4 *>(&Wc[i][j]);
+                    const float4 w = *reinterpret_cast<const float4 *>(&Wc[i * NUP + j]);
                     re[j] = fmaf(v, w.x, re[j]);
                     im[j] = fmaf(v, w.y, im[j]);
                     re[j + 1] = fmaf(v, w.z, re[j + 1]);
                     im[j + 1] = fmaf(v, w.w, im[j + 1]);
                 }
             }
+            __syncthreads();  // chunk c's buffer and twiddles are free again
         }
         const long long r = r0 + t;
         if (r < nrows) {
@@ -310,6 +343,44 @@ __global__ void __launch_bounds__(DXR_R) dft_x_rows_kernel(DftArgs a, long long 
             }
         }
     }
+}
+
+// The y pass for windows with Kx Ky <= 1024: one block per plane z, thread t
+// the output (jx, jy) = (t mod Kx, t / Kx); the plane's X1 rows (contiguous)
+// come into shared memory DYS_YC rows at a time, and each thread sums its
+// output sequentially in y.
+constexpr int DYS_YC = 32;
+
+__global__ void __launch_bounds__(1024) dft_y_slab_kernel(DftArgs a)
+{
+    extern __shared__ __align__(16) float2 ysm[];
+    float2 *tw = ysm;               // [ny]
+    float2 *Xs = ysm + a.ny;        // [DYS_YC][Kx]
+    fill_twiddles(tw, a.ny);
+    const int z = blockIdx.x, t = threadIdx.x, nout = a.Kx * a.Ky;
+    const bool act = t < nout;
+    const int jx = act ? t % a.Kx : 0, jy = act ? t / a.Kx : 0;
+    const int k = kval(jy, a.ny, a.Ky);
+    const float2 *src = a.X1 + (long long)z * a.ny * a.Kx;
+    float re = 0.f, im = 0.f;
+    int m = 0;
+    for (int y0 = 0; y0 < a.ny; y0 += DYS_YC) {
+        const int cy = min(DYS_YC, a.ny - y0);
+        __syncthreads();  // the previous rows are consumed
+        for (int e = t; e < cy * a.Kx; e += blockDim.x) Xs[e] = src[(long long)y0 * a.Kx + e];
+        __syncthreads();
+        if (act) {
+            for (int i = 0; i < cy; ++i) {
+                const float2 v = Xs[i * a.Kx + jx];
+                const float2 w = tw[m];
+                re += v.x * w.x - v.y * w.y;
+                im += v.x * w.y + v.y * w.x;
+                m += k;
+                if (m >= a.ny) m -= a.ny;
+            }
+        }
+    }
+    if (act) a.X2[((long long)z * a.Ky + jy) * a.Kx + jx] = make_float2(re, im);
 }
 
 // X2[(z*Ky + jy)*Kx + jx] = sum_y X1[(z*ny + y)*Kx + jx] e^{-i qy y}
@@ -423,15 +494,23 @@ cudaError_t launch_dft_accumulate(const DftArgs &a, cudaStream_t s)
         const long long rows = (long long)a.ny * a.nz;
         const unsigned grid = (unsigned)((rows + DXR_R - 1) / DXR_R);
         const int nu = a.Kx / 2 + 1;
-        if (nu <= 2) dft_x_rows_kernel<2><<<grid, DXR_R, 0, s>>>(a, rows);
-        else if (nu <= 4) dft_x_rows_kernel<4><<<grid, DXR_R, 0, s>>>(a, rows);
-        else if (nu <= 6) dft_x_rows_kernel<6><<<grid, DXR_R, 0, s>>>(a, rows);
-        else if (nu <= 10) dft_x_rows_kernel<10><<<grid, DXR_R, 0, s>>>(a, rows);
-        else dft_x_rows_kernel<18><<<grid, DXR_R, 0, s>>>(a, rows);
+#define FLB_DXR(NUP) dft_x_rows_kernel<NUP><<<grid, DXR_R, dxr_smem<NUP>(a.nx), s>>>(a, rows)
+        if (nu <= 2) FLB_DXR(2);
+        else if (nu <= 4) FLB_DXR(4);
+        else if (nu <= 6) FLB_DXR(6);
+        else if (nu <= 10) FLB_DXR(10);
+        else FLB_DXR(18);
+#undef FLB_DXR
     } else {
         dft_x_kernel<<<(unsigned)((n1 + bs - 1) / bs), bs, sizeof(float2) * a.nx, s>>>(a);
     }
-    dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, sizeof(float2) * a.ny, s>>>(a);
+    const size_t ysm = sizeof(float2) * ((size_t)a.ny + (size_t)DYS_YC * a.Kx);
+    if (a.Kx * a.Ky <= 1024 && ysm <= 48 * 1024) {
+        const int nt = ((a.Kx * a.Ky + 31) / 32) * 32;
+        dft_y_slab_kernel<<<(unsigned)a.nz, nt, ysm, s>>>(a);
+    } else {
+        dft_y_kernel<<<(unsigned)((n2 + bs - 1) / bs), bs, sizeof(float2) * a.ny, s>>>(a);
+    }
     dft_z_acc_kernel<<<(unsigned)((n3 + DZ_WARPS - 1) / DZ_WARPS), 32 * DZ_WARPS, sizeof(float2) * a.nz, s>>>(a);
     return cudaGetLastError();
 }
