@@ -327,6 +327,18 @@ __device__ __forceinline__ void lane_normals(const PhiloxKey &K, int64_t step, c
     }
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async); src_bytes 0 writes a
+// zero and reads nothing.  commit closes this thread's group of copies;
+// wait1 waits until at most the newest group is still in flight.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Geometry.  Populations: SoA planes [q][N], N = nx*ny*nz, unpadded, periodic
 // by index wrap.  psi, mu, u, J: padded planes with a ghost frame of GX (x)

@@ -255,16 +255,6 @@ constexpr int DXR_R = 128, DXR_CX = 32, DXR_NMAX = 1024, DXR_PS = DXR_R * (DXR_C
 
 __device__ __forceinline__ int conj_partner(int j, int n, int K) { return j == 0 ? 0 : (K >= n ? n - j : K - j); }
 
-// 4-byte asynchronous copy global -> shared; src_bytes 0 writes a zero
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
 // dynamic shared memory of dft_x_rows_kernel<NUP> for rows of n
 template <int NUP>
 constexpr size_t dxr_smem(int n)
