@@ -81,6 +81,58 @@ __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_kernel(const Geom g, const f
     mu3_block<MU3_HALO>(g, psi, mu, A, B, K, blockIdx.x, blockIdx.y, blockIdx.z, W ? &lw : nullptr);
 }
 
+// The same field (SO stencil) with four consecutive x per thread: x = xs ..
+// xs+3, xs = -4 + 4 i, so that xs is 16-byte aligned in the padded rows.  Per
+// plane a thread reads each of the rows y-1, y, y+1 as one 16-byte load and the
+// two cells beside it (3 x 3 loads for four points instead of 4 x 9), keeps the
+// per-plane partial sums of mu3_column for its four points and forms mu with
+// the same sums in the same order (mu_so), so the field is bitwise that of the
+// batched and persistent kernels.  Points x < -2 or x >= nx + 2 are not written,
+// and the side cells they alone would need are not read.
+constexpr int MV_TX = 16, MV_TY = 8, MV_ZC = 16;
+
+__global__ void __launch_bounds__(MV_TX *MV_TY) mu3_vec_kernel(const Geom g, const float *__restrict__ psi,
+                                                             float *__restrict__ mu, float A, float B, float K)
+{
+    const int xs = -4 + 4 * (int)(blockIdx.x * MV_TX + threadIdx.x);
+    const int y = (int)(blockIdx.y * MV_TY + threadIdx.y) - MU3_HALO;
+    const int zb = (int)blockIdx.z * MV_ZC - MU3_HALO, ze = min(zb + MV_ZC, g.nz + MU3_HALO);
+    const int xl = g.nx + MU3_HALO;  // one past the last output column
+    if (xs + 3 < -MU3_HALO || xs >= xl || y >= g.ny + MU3_HALO || zb >= ze) return;
+    const bool lo = xs - 1 >= -MU3_HALO - 1, hi = xs + 4 <= xl;  // side cells some point needs
+    const int Y = g.px, Z = g.px * g.py;
+    const float k22 = K * (1.0f / 22.0f);
+    float a0[4] = {}, b0[4] = {}, d0[4] = {}, a1[4] = {}, b1[4] = {}, d1[4] = {};  // planes p-2, p-1
+    int c = g.pidx32(xs, y, zb - 1);
+    for (int p = zb - 1; p <= ze; ++p, c += Z) {
+        float v[3][6];  // rows y-1, y, y+1; cells xs-1 .. xs+4
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int o = c + (r - 1) * Y;
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(psi + o));
+            v[r][0] = lo ? __ldg(psi + o - 1) : 0.f;
+            v[r][1] = q.x;
+            v[r][2] = q.y;
+            v[r][3] = q.z;
+            v[r][4] = q.w;
+            v[r][5] = hi ? __ldg(psi + o + 4) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float a2 = v[1][k + 1];
+            const float b2 = (v[1][k] + v[1][k + 2]) + (v[0][k + 1] + v[2][k + 1]);
+            const float d2 = (v[0][k] + v[0][k + 2]) + (v[2][k] + v[2][k + 2]);
+            const int x = xs + k;
+            if (p - 1 >= zb && x >= -MU3_HALO && x < xl) {
+                const float n1 = b1[k] + (a0[k] + a2), n2 = d1[k] + (b0[k] + b2), n3 = d0[k] + d2;
+                mu[c - Z + k] = mu_so(A, B, k22, a1[k], n1, n2, n3);
+            }
+            a0[k] = a1[k]; b0[k] = b1[k]; d0[k] = d1[k];
+            a1[k] = a2; b1[k] = b2; d1[k] = d2;
+        }
+    }
+}
+
 // ---- batched variants: block b of the launch works on L.mu[b] / L.lb[b] -------
 __global__ void __launch_bounds__(MU_BX *MU_BY) mu3_batch_kernel(const BatchLists L)
 {
@@ -113,8 +165,14 @@ __global__ void __launch_bounds__(LBB_NT) vel3_batch_kernel(const BatchLists L)
 cudaError_t launch_mu3(const Geom &g, const float *psi, float *mu, float A, float B, float K, cudaStream_t st,
                        const LapW *lw)
 {
-    const dim3 block(MU_BX, MU_BY, 1);
     constexpr int E = 2 * MU3_HALO;
+    if (!lw && g.dim == 3) {  // threads for x = -4 .. nx + 1 in fours
+        const int nxt = (g.nx + 2 + 4 + 3) / 4;
+        const dim3 vgrid((nxt + MV_TX - 1) / MV_TX, (g.ny + E + MV_TY - 1) / MV_TY, (g.nz + E + MV_ZC - 1) / MV_ZC);
+        mu3_vec_kernel<<<vgrid, dim3(MV_TX, MV_TY, 1), 0, st>>>(g, psi, mu, A, B, K);
+        return cudaGetLastError();
+    }
+    const dim3 block(MU_BX, MU_BY, 1);
     const dim3 grid((g.nx + E + MU_BX - 1) / MU_BX, (g.ny + E + MU_BY - 1) / MU_BY, (g.nz + E + MU_ZC - 1) / MU_ZC);
     if (lw) mu3_kernel<true><<<grid, block, 0, st>>>(g, psi, mu, A, B, K, *lw);
     else mu3_kernel<false><<<grid, block, 0, st>>>(g, psi, mu, A, B, K, LapW{0.f, 0.f, 0.f, 0.f});
