@@ -283,45 +283,41 @@ __device__ __forceinline__ void normals(const PhiloxKey &K, int64_t step, uint32
     }
 }
 
-// The first NN normals of stream 0 (blocks 0, 1, ...) at the V::L sites
-// site[l], scaled lane-wise by sc: n[k] holds normal k of every lane's site
-// (n has room for NN rounded up to even).  F2: the lanes are the two sites;
-// F1: the site's words are evaluated in pairs in one packed register.
-template <int NN, bool KEY_R0, class V>
-__device__ __forceinline__ void lane_normals(const PhiloxKey &K, int64_t step, const uint32_t *site, V sc, V *n)
+// Normals 8 b .. 8 b + NB - 1 (NB <= 8) of stream 0, block b, at the V::L sites
+// site[l], scaled lane-wise by sc: n[k] holds normal 8 b + k of every lane's
+// site (n has room for NB rounded up to even).  F2: the lanes are the two
+// sites; F1: the site's words are evaluated in pairs in one packed register.
+// A caller consumes one block's normals before drawing the next, so that at
+// most eight are live.
+template <int NB, bool KEY_R0, class V>
+__device__ __forceinline__ void lane_block(const PhiloxKey &K, int64_t step, const uint32_t *site, uint32_t b, V sc,
+                                           V *n)
 {
-    constexpr int L = V::L;
+    static_assert(NB >= 1 && NB <= 8, "a Philox block gives eight normals");
+    constexpr int L = V::L, NPAIR = (NB + 1) / 2;
+    u32x4 r[L];
 #pragma unroll
-    for (int b = 0; b < (NN + 7) / 8; ++b) {
-        constexpr int NPAIR = (NN + 1) / 2;
-        u32x4 r[L];
+    for (int l = 0; l < L; ++l) {
+        const u32x4 c = philox_ctr(step, site[l], 0u, b);
+        r[l] = KEY_R0 ? philox4x32_10_r0(c, K.k0[0], K.k1[0]) : philox4x32_10(c, K);
+    }
+    if constexpr (L == 2) {
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-            const u32x4 c = philox_ctr(step, site[l], 0u, (uint32_t)b);
-            r[l] = KEY_R0 ? philox4x32_10_r0(c, K.k0[0], K.k1[0]) : philox4x32_10(c, K);
+        for (int k = 0; k < NPAIR; ++k) {
+            const uint32_t w[2] = {word(r[0], k), word(r[1], k)};
+            bm_eval<V, true>(w, sc, n[2 * k], n[2 * k + 1]);
         }
-        if constexpr (L == 2) {
+    } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (4 * b + k < NPAIR) {
-                    const uint32_t w[2] = {word(r[0], k), word(r[1], k)};
-                    bm_eval<V, true>(w, sc, n[8 * b + 2 * k], n[8 * b + 2 * k + 1]);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k += 2) {
-                if (4 * b + k < NPAIR) {
-                    const uint32_t w[2] = {word(r[0], k), word(r[0], k + 1)};
-                    F2 c0, s0;
-                    bm_eval<F2, true>(w, F2::bc(sc.lane(0)), c0, s0);
-                    n[8 * b + 2 * k] = V::bc(c0.v.x);
-                    n[8 * b + 2 * k + 1] = V::bc(s0.v.x);
-                    if (4 * b + k + 1 < NPAIR) {
-                        n[8 * b + 2 * k + 2] = V::bc(c0.v.y);
-                        n[8 * b + 2 * k + 3] = V::bc(s0.v.y);
-                    }
-                }
+        for (int k = 0; k < NPAIR; k += 2) {
+            const uint32_t w[2] = {word(r[0], k), word(r[0], k + 1)};
+            F2 c0, s0;
+            bm_eval<F2, true>(w, F2::bc(sc.lane(0)), c0, s0);
+            n[2 * k] = V::bc(c0.v.x);
+            n[2 * k + 1] = V::bc(s0.v.x);
+            if (k + 1 < NPAIR) {
+                n[2 * k + 2] = V::bc(c0.v.y);
+                n[2 * k + 3] = V::bc(s0.v.y);
             }
         }
     }

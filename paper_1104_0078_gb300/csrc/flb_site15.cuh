@@ -166,8 +166,9 @@ __device__ __forceinline__ void lb15_sites(const LBArgs &a, const PL &P, int x, 
         uint32_t su[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) su[l] = (uint32_t)s[l];
-        V n[12];
-        lane_normals<11, KEY_R0>(a.key, a.step, su, vmake<V>(sq), n);
+        const V sc = vmake<V>(sq);
+        V n[8];
+        lane_block<8, KEY_R0>(a.key, a.step, su, 0u, sc, n);  // normals 0-7
         // the six stress modes enter Q as on D3Q19 (4.5 x 2/9 = 1, 4.5 x 1/9 = 1/2)
         const V m0 = n[0] * a.namp[0], m1 = n[1] * a.namp[1], m2 = n[2] * a.namp[2];
         const V t01 = m0 - m1;
@@ -179,9 +180,10 @@ __device__ __forceinline__ void lb15_sites(const LBArgs &a, const PL &P, int x, 
         Qxz = vfma(n[5], 0.5f * a.namp[5], Qxz);
         gx = vfma(n[6], a.namp[6], gx);
         gy = vfma(n[7], a.namp[7], gy);
-        gz = vfma(n[8], a.namp[8], gz);
-        gq = vfma(n[9], a.namp[9], gq);
-        g4 = vfma(n[10], a.namp[10], g4);
+        lane_block<3, KEY_R0>(a.key, a.step, su, 1u, sc, n);  // normals 8-10
+        gz = vfma(n[0], a.namp[8], gz);
+        gq = vfma(n[1], a.namp[9], gq);
+        g4 = vfma(n[2], a.namp[10], g4);
     }
 
     auto store = [&](int i, V v) {

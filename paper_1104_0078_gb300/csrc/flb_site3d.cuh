@@ -340,8 +340,9 @@ __device__ __forceinline__ void lb_sites(const LBArgs &a, const PL &P, int x, in
         uint32_t su[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) su[l] = (uint32_t)s[l];
-        V n[16];
-        lane_normals<15, KEY_R0>(a.key, a.step, su, vmake<V>(sq), n);
+        const V sc = vmake<V>(sq);
+        V n[8];
+        lane_block<8, KEY_R0>(a.key, a.step, su, 0u, sc, n);  // normals 0-7
         const V m0 = n[0] * a.nq[0], m1 = n[1] * a.nq[1], m2 = n[2] * a.nq[2];
         const V t01 = m0 - m1;
         Qxx = Qxx + vfma(m1, 2.0f, m0);
@@ -352,13 +353,14 @@ __device__ __forceinline__ void lb_sites(const LBArgs &a, const PL &P, int x, in
         Qxz = vfma(n[5], a.nq[5], Qxz);
         G10 = vfma(n[6], a.nq[6], G10);
         G11 = vfma(n[7], a.nq[7], G11);
-        G12 = vfma(n[8], a.nq[8], G12);
-        G13 = vfma(n[9], a.nq[9], G13);
-        G14 = vfma(n[10], a.nq[10], G14);
-        G15 = vfma(n[11], a.nq[11], G15);
-        G16 = vfma(n[12], a.nq[12], G16);
-        G17 = vfma(n[13], a.nq[13], G17);
-        G18 = vfma(n[14], a.nq[14], G18);
+        lane_block<7, KEY_R0>(a.key, a.step, su, 1u, sc, n);  // normals 8-14
+        G12 = vfma(n[0], a.nq[8], G12);
+        G13 = vfma(n[1], a.nq[9], G13);
+        G14 = vfma(n[2], a.nq[10], G14);
+        G15 = vfma(n[3], a.nq[11], G15);
+        G16 = vfma(n[4], a.nq[12], G16);
+        G17 = vfma(n[5], a.nq[13], G17);
+        G18 = vfma(n[6], a.nq[14], G18);
     }
 
     // back-transform f_i = w_i (E_i +- O_i), E even and O odd in c_i
