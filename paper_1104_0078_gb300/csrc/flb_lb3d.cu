@@ -11,9 +11,8 @@
 //
 // Indices are 32-bit (N and the padded planes are < 2^31); population plane i
 // of N sites starts at fin + i*N.  The plain kernel runs seven 128-thread blocks
-// per SM (72 registers): with 96 registers (five blocks) it ran 4.85 ms at
-// 512^3, with 80 (six) 4.68 ms, with 72 (seven, 20 bytes spilled) 4.52 ms and
-// with 64 (eight, 84 bytes spilled) 4.63 ms.  Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2,
+// per SM (72 registers, no spills): 4.08 ms at 512^3; six blocks (80 registers)
+// and eight (64, spilling) measured slower.  Noise order: bulk, 3c_x^2-c^2, c_y^2-c_z^2,
 // xy, yz, zx, three c^2 c_a ghosts, three c_a(c_b^2-c_g^2) ghosts, c^4,
 // c^2(3c_x^2-c^2), c^2(c_y^2-c_z^2).
 #include "flb_site3d.cuh"
