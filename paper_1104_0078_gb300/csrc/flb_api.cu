@@ -296,6 +296,15 @@ struct flb_handle {
     size_t ev_used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
     int64_t phase_launches[3] = {0, 0, 0};
+    // host staging of the FP32 fields that set_fields and get_psi_u move; kept
+    // between calls (grown, never shrunk) so that a call neither clears nor
+    // first-touches a fresh buffer
+    std::vector<float> hstage;
+    float *host_stage(size_t n)
+    {
+        if (hstage.size() < n) hstage.resize(n);
+        return hstage.data();
+    }
     ~flb_handle()
     {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -1191,10 +1200,10 @@ int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *
     cudaStream_t st = h->st;
     // psi and u go up as interior FP32 fields, staged in the mu plane (free
     // scratch between steps), and are padded with their images on the device
-    std::vector<float> tmp((size_t)N);
+    float *tmp = h->host_stage((size_t)N);
     auto put = [&](const double *src, float *dst) -> int {
-        to_float(src, tmp.data(), N);
-        int rc = cuerr(cudaMemcpyAsync(r->mu, tmp.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+        to_float(src, tmp, N);
+        int rc = cuerr(cudaMemcpyAsync(r->mu, tmp, (size_t)N * 4, cudaMemcpyHostToDevice, st));
         if (rc == FLB_OK) rc = cuerr(launch_pad(g, r->mu, dst, st));
         ++h->launches;
         return rc == FLB_OK ? cuerr(cudaStreamSynchronize(st)) : rc;  // tmp is reused
@@ -1203,8 +1212,8 @@ int flb_set_fields(flb_handle *h, int32_t rep, const double *rho, const double *
     if (rc == FLB_OK && !u) rc = cuerr(cudaMemsetAsync(r->u, 0, (size_t)r->dim * g.pn * 4, st));
     for (int a = 0; a < r->dim && rc == FLB_OK && u; ++a) rc = put(u + (size_t)a * N, r->u + (size_t)a * g.pn);
     if (rc == FLB_OK && rho) {
-        for (long long s = 0; s < N; ++s) tmp[(size_t)s] = (float)rho[s];
-        rc = upload_padded(h, g, r->mu, tmp.data());  // padded rho in the mu plane for init_eq
+        to_float(rho, tmp, N);
+        rc = upload_padded(h, g, r->mu, tmp);  // padded rho in the mu plane for init_eq
     }
     if (rc != FLB_OK) return rc;
     const cudaError_t e = launch_init_eq(g, r->q, r->p.storage, rho ? r->mu : nullptr, r->u, (float)r->p.rho0,
@@ -1283,13 +1292,13 @@ int flb_get_psi_u(flb_handle *h, int32_t rep, double *psi, double *u)
         for (int a = 0; a < r->dim && rc == FLB_OK; ++a)
             rc = cuerr(launch_unpad(g, r->u + (size_t)a * g.pn, scratch + (size_t)g.n * k++, h->st));
     if (rc != FLB_OK) return rc;
-    std::vector<float> tmp((size_t)g.n * nf);
-    rc = cuerr(cudaMemcpyAsync(tmp.data(), scratch, tmp.size() * 4, cudaMemcpyDeviceToHost, h->st));
+    float *tmp = h->host_stage((size_t)g.n * nf);
+    rc = cuerr(cudaMemcpyAsync(tmp, scratch, (size_t)g.n * nf * 4, cudaMemcpyDeviceToHost, h->st));
     if (rc == FLB_OK) rc = cuerr(cudaStreamSynchronize(h->st));
     if (rc != FLB_OK) return rc;
     k = 0;
-    if (psi) to_double(tmp.data() + (size_t)g.n * k++, psi, g.n);
-    if (u) to_double(tmp.data() + (size_t)g.n * k, u, (long long)r->dim * g.n);
+    if (psi) to_double(tmp + (size_t)g.n * k++, psi, g.n);
+    if (u) to_double(tmp + (size_t)g.n * k, u, (long long)r->dim * g.n);
     return FLB_OK;
 }
 
