@@ -416,10 +416,12 @@ def test_nonfinite_is_reported():
 
 
 def test_structure_factor_long_rows():
-    # the x pass of the windowed DFT keeps a whole row in registers (one warp
-    # per row) for windows of K_x <= 32 and rows up to 1024: rows of 512 as in
-    # the 512^3 workload, kmax = 8 as the bench samples, a seeded field at step
-    # 0, every value of the window against the oracle's FFT of the same field
+    # the x pass of the windowed DFT sums blocks of 128 rows against staged
+    # twiddles (only k >= 0, the rest as conjugates) for windows of K_x <= 32 and
+    # rows up to 1024, the y pass a plane per block: rows of 512 as in the 512^3
+    # workload (16 chunks of 32 columns), kmax = 8 as the bench samples, a seeded
+    # field at step 0, every value of the window against the oracle's FFT of the
+    # same field
     d = dict(dim=3, q=19, nx=512, ny=48, nz=40, tau=0.8, kT=1e-4, A=0.1, B=0.0, K=0.04, M=0.2, scheme=1,
              integrator=2, seed=4, sq_kmax=8)
     s = F.Solver(flb_params(d))
