@@ -435,3 +435,28 @@ def test_structure_factor_long_rows():
     ks = lambda n: list(range(0, 9)) + list(range(n - 8, n))
     ref = full[np.ix_(ks(40), ks(48), ks(512))]
     assert np.allclose(S_gpu.reshape(17, 17, 17), ref, rtol=1e-4, atol=1e-6 * ref.max())
+
+
+@pytest.mark.parametrize("shape,kmax", [((15, 13, 9), 0), ((33, 10, 7), 4), ((21, 17, 1), 0), ((40, 9, 1), 5)])
+def test_structure_factor_odd_and_planar_boxes(shape, kmax):
+    # the row-block x pass sums k >= 0 and writes the partners as conjugates:
+    # odd extents (no self-conjugate k = n/2), a window on a wider row, a
+    # ragged last block of rows, and planar boxes (one plane: the y pass alone
+    # in its block, the z pass over one plane); every value against the
+    # oracle's FFT of the same seeded field at step 0
+    nx, ny, nz = shape
+    dim = 2 if nz == 1 else 3
+    d = dict(dim=dim, q=9 if dim == 2 else 19, nx=nx, ny=ny, nz=nz, tau=0.8, kT=1e-4, A=0.1, B=0.0, K=0.04,
+             M=0.2, scheme=1, integrator=2, seed=4, sq_kmax=kmax)
+    s = F.Solver(flb_params(d))
+    N = nx * ny * nz
+    psi0 = I.uniform_field(N, -0.01, 0.01, 37)
+    s.set_fields(psi=psi0)
+    s.sample(1)
+    S_gpu, ns = s.structure_factor()
+    full = O.structure_factor(oracle_params(d), psi0)
+    keep = lambda n: list(range(n)) if kmax <= 0 or 2 * kmax + 1 >= n else list(range(kmax + 1)) + list(range(n - kmax, n))
+    kz, ky, kx = keep(nz), keep(ny), keep(nx)
+    assert ns == 1 and S_gpu.size == len(kx) * len(ky) * len(kz)
+    ref = full.reshape(nz, ny, nx)[np.ix_(kz, ky, kx)]
+    assert np.allclose(S_gpu.reshape(len(kz), len(ky), len(kx)), ref, rtol=1e-4, atol=1e-6 * ref.max())
