@@ -236,15 +236,6 @@ __device__ __forceinline__ void bm_eval(const uint32_t *w, V sc, V &g0, V &g1)
     g1 = rad * s;
 }
 
-// The Box-Muller pair of one word.
-__device__ __forceinline__ void box_muller(uint32_t w, float &g0, float &g1)
-{
-    F1 r0, r1;
-    bm_eval<F1>(&w, F1{1.0f}, r0, r1);
-    g0 = r0.v;
-    g1 = r1.v;
-}
-
 __device__ __forceinline__ uint32_t word(const u32x4 &r, int k) { return k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w; }
 
 __device__ __forceinline__ u32x4 philox_ctr(int64_t step, uint32_t site, uint32_t stream, uint32_t block)
