@@ -29,7 +29,7 @@ struct PlanesStride32 {
 
 // Two sites per thread, (x, y, z) and (x, y, z + 1), as in the collide-stream.
 template <typename T, bool FORCE>
-__global__ void __launch_bounds__(LB_BX *LB_BY) vel3_kernel(const LBArgs a)
+__global__ void __launch_bounds__(LB_BX *LB_BY, 10) vel3_kernel(const LBArgs a)
 {
     const Geom &g = a.g;
     const int x = blockIdx.x * LB_BX + threadIdx.x;
